@@ -1,0 +1,253 @@
+"""CPU oracle for the BBC large-k IVF search path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never imports, links or runs it, and this package never
+imports the product.
+
+The arithmetic lives in ``bbc_oracle.c`` (plain C, single-threaded, FP64
+except for the FP32 lookup-table recipe).  This module compiles it with gcc
+(``-ffp-contract=off``) into ``oracle/_build`` and wraps it with ctypes.
+Every function documents the passage of the paper it follows.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bbc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libbbc_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+L2, IP = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/libbbc_oracle.so``."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Index(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("nlist", C.c_int32), ("metric", C.c_int32),
+                ("M", C.c_int32), ("bits", C.c_int32),
+                ("centroids", C.c_void_p), ("list_offsets", C.c_void_p), ("ids", C.c_void_p),
+                ("codes", C.c_void_p), ("books", C.c_void_p), ("vectors", C.c_void_p)]
+
+
+class Codebook(C.Structure):
+    """Result-buffer codebook (Section 3.2) plus the collector's final state."""
+    _fields_ = [("d_min", C.c_uint32), ("d_max", C.c_uint32), ("sh", C.c_int32), ("m", C.c_int32),
+                ("sample_lists", C.c_int32), ("sample_size", C.c_int64), ("tau", C.c_int32),
+                ("pushed", C.c_int64), ("below", C.c_int64), ("map", C.c_uint8 * 256)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            vp, i32, i64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+            L.oracle_dist.restype = C.c_double
+            L.oracle_dist.argtypes = [vp, vp, i32, i32]
+            L.oracle_probe.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp]
+            L.oracle_lut_f32.argtypes = [vp, vp, i32, i32, i32, i32, vp]
+            L.oracle_lut16.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp]
+            L.oracle_adc.argtypes = [vp, vp, i64, i32, i32, vp]
+            for f in (L.oracle_topkc_sort, L.oracle_topkc_heap):
+                f.restype = i64
+                f.argtypes = [vp, vp, i64, i64, vp, vp]
+            L.oracle_update.restype = i32
+            L.oracle_update.argtypes = [vp, i32, i64]
+            L.oracle_build_codebook.argtypes = [vp, i64, i64, i32, C.POINTER(Codebook)]
+            L.oracle_bucket_collect.restype = i64
+            L.oracle_bucket_collect.argtypes = [vp, vp, vp, i32, i64, i32, i32,
+                                                C.POINTER(Codebook), vp, vp, vp]
+            L.oracle_rerank.argtypes = [vp, vp, i32, i32, vp, i64, vp]
+            L.oracle_topk_final.argtypes = [vp, vp, i64, i32, vp, vp]
+            L.oracle_search.restype = i32
+            L.oracle_search.argtypes = [C.POINTER(_Index), vp, i64, i32, i32, i64, i32, i32, i32,
+                                        vp, vp, vp]
+            L.oracle_bruteforce.argtypes = [vp, i64, vp, i64, i32, i32, i32, vp, vp]
+            _ = u32
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _metric(m) -> int:
+    return m if isinstance(m, int) else (L2 if m == "l2" else IP)
+
+
+# --------------------------------------------------------------------------
+# step-by-step entry points
+# --------------------------------------------------------------------------
+def dist(a, b, metric="l2") -> float:
+    """Squared L2 or negated inner product in FP64 (exact distance of Section 3.3)."""
+    a, b = _f32(a), _f32(b)
+    return lib().oracle_dist(_p(a), _p(b), a.shape[0], _metric(metric))
+
+
+def probe(q, centroids, nprobe: int, metric="l2"):
+    """IVF routing (Section 2): the nprobe nearest lists, nearest first, FP64 scores."""
+    q, c = _f32(q), _f32(centroids)
+    lists = np.empty(nprobe, dtype=np.int32)
+    scores = np.empty(nprobe, dtype=np.float64)
+    rc = lib().oracle_probe(_p(q), _p(c), c.shape[0], c.shape[1], _metric(metric), nprobe,
+                            _p(lists), _p(scores))
+    if rc:
+        raise ValueError("bad nprobe")
+    return lists, scores
+
+
+def lut_f32(q, books, metric="l2"):
+    """Per-sub-space query-to-codeword distances in FP32 (Section 2, step (1))."""
+    q, b = _f32(q), _f32(books)
+    M, K, ds = b.shape
+    out = np.empty((M, K), dtype=np.float32)
+    lib().oracle_lut_f32(_p(q), _p(b), M * ds, M, int(np.log2(K)), _metric(metric), _p(out))
+    return out
+
+
+def lut16(q, books, metric="l2"):
+    """uint16-quantised lookup table (offset per sub-space, one scale per query)."""
+    q, b = _f32(q), _f32(books)
+    M, K, ds = b.shape
+    out = np.empty((M, K), dtype=np.uint16)
+    lib().oracle_lut16(_p(q), _p(b), M * ds, M, int(np.log2(K)), _metric(metric), _p(out), None)
+    return out
+
+
+def adc(table16, codes, M: int, bits: int):
+    """Integer estimated distances sum_m LUT16[m][code_m] (Section 2, step (2))."""
+    t = np.ascontiguousarray(table16, dtype=np.uint16)
+    c = np.ascontiguousarray(codes, dtype=np.uint8)
+    out = np.empty(c.shape[0], dtype=np.uint32)
+    lib().oracle_adc(_p(t), _p(c), c.shape[0], M, bits, _p(out))
+    return out
+
+
+def topkc(e, ids, kc: int, how: str = "sort"):
+    """The kc smallest (e, id), ascending; ``how`` = "sort" or "heap"."""
+    e = np.ascontiguousarray(e, dtype=np.uint32)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    oi = np.empty(max(kc, 1), dtype=np.int64)
+    oe = np.empty(max(kc, 1), dtype=np.uint32)
+    f = lib().oracle_topkc_sort if how == "sort" else lib().oracle_topkc_heap
+    c = f(_p(e), _p(ids), e.shape[0], kc, _p(oi), _p(oe))
+    return oi[:c], oe[:c]
+
+
+def update(counts, kc: int) -> int:
+    """Algorithm 1 Update: first bucket whose running count reaches kc (m if none)."""
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    return int(lib().oracle_update(_p(c), c.shape[0], kc))
+
+
+def build_codebook(sample_e, kc: int, m: int) -> Codebook:
+    """Sampled equal-width -> equal-depth codebook of Section 3.2."""
+    s = np.ascontiguousarray(sample_e, dtype=np.uint32)
+    cb = Codebook()
+    lib().oracle_build_codebook(_p(s), s.shape[0], kc, m, C.byref(cb))
+    return cb
+
+
+def bucket_collect(e, ids, list_ofs, kc: int, m: int, sample_min: int = 8):
+    """Algorithm 1 Collect over lists in probe order.
+
+    Returns (ids, e, codebook, counts) with ids/e ascending by (e, id).
+    """
+    e = np.ascontiguousarray(e, dtype=np.uint32)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    lo = np.ascontiguousarray(list_ofs, dtype=np.int64)
+    cb = Codebook()
+    counts = np.empty(m, dtype=np.int64)
+    oi = np.empty(max(kc, 1), dtype=np.int64)
+    oe = np.empty(max(kc, 1), dtype=np.uint32)
+    c = lib().oracle_bucket_collect(_p(e), _p(ids), _p(lo), lo.shape[0] - 1, kc, m, sample_min,
+                                    C.byref(cb), _p(counts), _p(oi), _p(oe))
+    return oi[:c], oe[:c], cb, counts
+
+
+def rerank(q, vectors, ids, metric="l2"):
+    """Exact FP64 distances of the candidates."""
+    q, v = _f32(q), _f32(vectors)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    out = np.empty(ids.shape[0], dtype=np.float64)
+    lib().oracle_rerank(_p(q), _p(v), v.shape[1], _metric(metric), _p(ids), ids.shape[0], _p(out))
+    return out
+
+
+def topk_final(dist_, ids, k: int):
+    """The k smallest (dist, id), ascending; padded with (-1, +inf)."""
+    dd = np.ascontiguousarray(dist_, dtype=np.float64)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    oi = np.empty(k, dtype=np.int64)
+    od = np.empty(k, dtype=np.float64)
+    lib().oracle_topk_final(_p(dd), _p(ids), dd.shape[0], k, _p(oi), _p(od))
+    return oi, od
+
+
+COLLECTORS = {"sort": 0, "heap": 1, "bucket": 2}
+
+
+def search(index, queries, k: int, nprobe: int, kc: int, collector: str = "sort",
+           m: int = 64, sample_min: int = 8, with_stats: bool = False):
+    """The whole search path for a batch of queries (single-threaded).
+
+    ``index`` is a ``synth.IvfPqIndex``-like object.  Returns (ids [nq, k],
+    dists [nq, k] FP64) and, with ``with_stats``, per-query stats
+    [S_q, candidates, tau, pushed].
+    """
+    q = _f32(queries).reshape(-1, index.d)
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return _p(a)
+
+    ix = _Index(index.n, index.d, index.nlist, _metric(index.metric), index.pq_m, index.pq_bits,
+                arr(index.centroids, np.float32), arr(index.list_offsets, np.int64),
+                arr(index.ids, np.int64), arr(index.codes, np.uint8),
+                arr(index.codebooks, np.float32), arr(index.vectors, np.float32))
+    nq = q.shape[0]
+    oi = np.empty((nq, k), dtype=np.int64)
+    od = np.empty((nq, k), dtype=np.float64)
+    st = np.empty((nq, 4), dtype=np.int64)
+    rc = lib().oracle_search(C.byref(ix), _p(q), nq, k, nprobe, kc, COLLECTORS[collector], m,
+                             sample_min, _p(oi), _p(od), _p(st))
+    if rc:
+        raise ValueError(f"oracle_search: bad arguments (rc={rc})")
+    return (oi, od, st) if with_stats else (oi, od)
+
+
+def bruteforce(queries, x, k: int, metric="l2"):
+    """Exact kNN over the whole data set in FP64: (ids [nq, k], dists [nq, k])."""
+    q, xv = _f32(queries), _f32(x)
+    q = q.reshape(-1, xv.shape[1])
+    oi = np.empty((q.shape[0], k), dtype=np.int64)
+    od = np.empty((q.shape[0], k), dtype=np.float64)
+    lib().oracle_bruteforce(_p(q), q.shape[0], _p(xv), xv.shape[0], xv.shape[1], _metric(metric),
+                            k, _p(oi), _p(od))
+    return oi, od

@@ -1,0 +1,510 @@
+/*
+ * Plain CPU oracle for the BBC large-k IVF search path (arxiv 2604.01960).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline use it.  It shares no code with the CUDA library.
+ *
+ * Single-threaded, written for clarity over speed.  Floating point is FP64
+ * except where the method fixes FP32 (the PQ lookup table recipe).  Compile
+ * with -ffp-contract=off so that no multiply-add is fused.
+ *
+ * What each function follows:
+ *   oracle_probe          Section 2 "Quantization": IVF routes a query to the
+ *                         n_probe nearest centroids; Algorithm 4 visits them
+ *                         nearest first.  Ties go to the smaller list id.
+ *   oracle_lut_f32/16     Section 2 "Quantization", step (1): distances from
+ *                         the query to every codebook vector, per sub-space;
+ *                         then the uint16 integer quantisation of the table.
+ *   oracle_adc            step (2): estimated distance = sum over sub-spaces
+ *                         of the table entry picked by the code.
+ *   oracle_topkc_sort     the n_cand candidates by estimated distance
+ *                         (Section 2, unbounded methods), by a full sort.
+ *   oracle_topkc_heap     the same set through a binary max-heap collector,
+ *                         the baseline collector of Section 2 "Top-k Collector".
+ *   oracle_bucket_collect Algorithm 1 (Push, Update, Collect) with the
+ *                         sampled equal-width -> equal-depth codebook of
+ *                         Section 3.2 and the bucket id of Eq. (remap).
+ *   oracle_rerank         exact distances of the candidates (FP64).
+ *   oracle_topk_final     the k smallest exact distances, ascending.
+ *   oracle_search         the whole path for a batch of queries.
+ *   oracle_bruteforce     exact kNN over the whole data set (FP64).
+ *
+ * Orders: every "smallest" is by (value, id) ascending, id breaking ties.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_L2 0
+#define ORACLE_IP 1
+
+/* ------------------------------------------------------------------ */
+/* comparators                                                          */
+/* ------------------------------------------------------------------ */
+typedef struct { double s; int64_t id; } dkey;
+typedef struct { uint32_t e; int64_t id; } ukey;
+
+static int cmp_dkey(const void* a, const void* b) {
+    const dkey* x = (const dkey*)a;
+    const dkey* y = (const dkey*)b;
+    if (x->s < y->s) return -1;
+    if (x->s > y->s) return 1;
+    if (x->id < y->id) return -1;
+    if (x->id > y->id) return 1;
+    return 0;
+}
+
+static int cmp_ukey(const void* a, const void* b) {
+    const ukey* x = (const ukey*)a;
+    const ukey* y = (const ukey*)b;
+    if (x->e < y->e) return -1;
+    if (x->e > y->e) return 1;
+    if (x->id < y->id) return -1;
+    if (x->id > y->id) return 1;
+    return 0;
+}
+
+static int ukey_less(ukey a, ukey b) { return a.e < b.e || (a.e == b.e && a.id < b.id); }
+
+/* ------------------------------------------------------------------ */
+/* distances                                                            */
+/* ------------------------------------------------------------------ */
+/* Squared L2, or negated inner product, in FP64 over ascending dimension. */
+double oracle_dist(const float* a, const float* b, int32_t d, int32_t metric) {
+    double s = 0.0;
+    if (metric == ORACLE_L2) {
+        for (int32_t i = 0; i < d; ++i) {
+            double t = (double)a[i] - (double)b[i];
+            s = s + t * t;
+        }
+    } else {
+        for (int32_t i = 0; i < d; ++i) s = s + (double)a[i] * (double)b[i];
+        s = -s;
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------ */
+/* IVF probe                                                            */
+/* ------------------------------------------------------------------ */
+int oracle_probe(const float* q, const float* centroids, int32_t nlist, int32_t d,
+                 int32_t metric, int32_t nprobe, int32_t* out_lists, double* out_scores) {
+    if (nprobe < 1 || nprobe > nlist) return -1;
+    dkey* all = (dkey*)malloc(sizeof(dkey) * (size_t)nlist);
+    if (!all) return -4;
+    for (int32_t l = 0; l < nlist; ++l) {
+        all[l].s = oracle_dist(q, centroids + (size_t)l * d, d, metric);
+        all[l].id = l;
+    }
+    qsort(all, (size_t)nlist, sizeof(dkey), cmp_dkey);
+    for (int32_t j = 0; j < nprobe; ++j) {
+        out_lists[j] = (int32_t)all[j].id;
+        if (out_scores) out_scores[j] = all[j].s;
+    }
+    free(all);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* PQ lookup table                                                      */
+/* ------------------------------------------------------------------ */
+/* FP32 table: entry [m][j] = ||q_m - y_{m,j}||^2 (L2) or -<q_m, y_{m,j}> (IP),
+ * accumulated in FP32 over ascending dimension, one rounding per operation. */
+void oracle_lut_f32(const float* q, const float* books, int32_t d, int32_t M, int32_t bits,
+                    int32_t metric, float* lut) {
+    const int32_t K = 1 << bits, ds = d / M;
+    for (int32_t m = 0; m < M; ++m) {
+        const float* qm = q + (size_t)m * ds;
+        for (int32_t j = 0; j < K; ++j) {
+            const float* y = books + ((size_t)m * K + j) * ds;
+            float acc = 0.0f;
+            if (metric == ORACLE_L2) {
+                for (int32_t i = 0; i < ds; ++i) {
+                    float t = qm[i] - y[i];
+                    float t2 = t * t;
+                    acc = acc + t2;
+                }
+            } else {
+                for (int32_t i = 0; i < ds; ++i) {
+                    float p = qm[i] * y[i];
+                    acc = acc + p;
+                }
+                acc = -acc;
+            }
+            lut[(size_t)m * K + j] = acc;
+        }
+    }
+}
+
+/* uint16 table: per sub-space offset lo_m = min_j L[m][j]; one scale for the
+ * query, inv = 65535 / span with span = max_m (max_j L[m][j] - lo_m);
+ * entry = min(65535, floor((L - lo_m) * inv + 0.5)).  span == 0 gives zeros. */
+void oracle_lut16(const float* q, const float* books, int32_t d, int32_t M, int32_t bits,
+                  int32_t metric, uint16_t* lut16, float* lut_f32_out) {
+    const int32_t K = 1 << bits;
+    float* lut = (float*)malloc(sizeof(float) * (size_t)M * K);
+    float* lo = (float*)malloc(sizeof(float) * (size_t)M);
+    oracle_lut_f32(q, books, d, M, bits, metric, lut);
+    float span = 0.0f;
+    for (int32_t m = 0; m < M; ++m) {
+        float mn = lut[(size_t)m * K], mx = mn;
+        for (int32_t j = 1; j < K; ++j) {
+            float v = lut[(size_t)m * K + j];
+            if (v < mn) mn = v;
+            if (v > mx) mx = v;
+        }
+        lo[m] = mn;
+        float w = mx - mn;
+        if (w > span) span = w;
+    }
+    float inv = span > 0.0f ? 65535.0f / span : 0.0f;
+    for (int32_t m = 0; m < M; ++m) {
+        for (int32_t j = 0; j < K; ++j) {
+            float t = lut[(size_t)m * K + j] - lo[m];
+            float u = t * inv;
+            float v = floorf(u + 0.5f);
+            if (v > 65535.0f) v = 65535.0f;
+            lut16[(size_t)m * K + j] = (uint16_t)v;
+        }
+    }
+    if (lut_f32_out) memcpy(lut_f32_out, lut, sizeof(float) * (size_t)M * K);
+    free(lut);
+    free(lo);
+}
+
+/* ------------------------------------------------------------------ */
+/* ADC estimated distance                                               */
+/* ------------------------------------------------------------------ */
+static int32_t code_of(const uint8_t* row, int32_t m, int32_t bits) {
+    if (bits == 8) return row[m];
+    uint8_t b = row[m >> 1];
+    return (m & 1) ? (b >> 4) : (b & 0x0F);
+}
+
+void oracle_adc(const uint16_t* lut16, const uint8_t* codes, int64_t n, int32_t M, int32_t bits,
+                uint32_t* out_e) {
+    const int32_t K = 1 << bits, cb = M * bits / 8;
+    for (int64_t i = 0; i < n; ++i) {
+        const uint8_t* row = codes + (size_t)i * cb;
+        uint32_t e = 0;
+        for (int32_t m = 0; m < M; ++m) e += lut16[(size_t)m * K + code_of(row, m, bits)];
+        out_e[i] = e;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* candidate collectors                                                 */
+/* ------------------------------------------------------------------ */
+/* Sort-based: the Kc smallest (e, id); returns how many were written. */
+int64_t oracle_topkc_sort(const uint32_t* e, const int64_t* ids, int64_t n, int64_t Kc,
+                          int64_t* out_ids, uint32_t* out_e) {
+    ukey* a = (ukey*)malloc(sizeof(ukey) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) { a[i].e = e[i]; a[i].id = ids[i]; }
+    qsort(a, (size_t)n, sizeof(ukey), cmp_ukey);
+    int64_t c = n < Kc ? n : Kc;
+    for (int64_t i = 0; i < c; ++i) { out_ids[i] = a[i].id; if (out_e) out_e[i] = a[i].e; }
+    free(a);
+    return c;
+}
+
+/* Binary max-heap of capacity Kc keyed by (e, id); output in ascending order. */
+static void heap_sift_down(ukey* h, int64_t n, int64_t i) {
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, big = i;
+        if (l < n && ukey_less(h[big], h[l])) big = l;
+        if (r < n && ukey_less(h[big], h[r])) big = r;
+        if (big == i) return;
+        ukey t = h[i]; h[i] = h[big]; h[big] = t;
+        i = big;
+    }
+}
+
+static void heap_sift_up(ukey* h, int64_t i) {
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!ukey_less(h[p], h[i])) return;
+        ukey t = h[i]; h[i] = h[p]; h[p] = t;
+        i = p;
+    }
+}
+
+int64_t oracle_topkc_heap(const uint32_t* e, const int64_t* ids, int64_t n, int64_t Kc,
+                          int64_t* out_ids, uint32_t* out_e) {
+    if (Kc <= 0) return 0;
+    ukey* h = (ukey*)malloc(sizeof(ukey) * (size_t)Kc);
+    int64_t sz = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        ukey x = {e[i], ids[i]};
+        if (sz < Kc) { h[sz] = x; heap_sift_up(h, sz); ++sz; }
+        else if (ukey_less(x, h[0])) { h[0] = x; heap_sift_down(h, sz, 0); }
+    }
+    /* pop in descending order, write back to front */
+    int64_t c = sz;
+    while (sz > 0) {
+        out_ids[sz - 1] = h[0].id;
+        if (out_e) out_e[sz - 1] = h[0].e;
+        h[0] = h[sz - 1];
+        --sz;
+        heap_sift_down(h, sz, 0);
+    }
+    free(h);
+    return c;
+}
+
+/* ------------------------------------------------------------------ */
+/* Bucket-based result buffer (Algorithm 1)                             */
+/* ------------------------------------------------------------------ */
+/* Codebook of Section 3.2 on integer estimated distances.
+ *   sample   = the first lists in probe order: at least min(sample_min, P)
+ *              lists, extended until they hold min(Kc, S_q) objects;
+ *   t        = min(Kc, |sample|); d_min = smallest, d_max = t-th smallest
+ *              sampled estimated distance (the sample's local top-Kc);
+ *   delta    = 2^sh, the smallest power of two with (d_max - d_min) >> sh
+ *              <= 255, so n_ew = 256 equal-width bins cover [d_min, d_max];
+ *   bin(e)   = clamp(floor((e - d_min) / delta), 0, 255)          (Eq. remap)
+ *   h[b]     = sampled objects with e <= d_max in bin b, T = sum h;
+ *   map[b]   = min(m - 1, floor(m * sum_{b'<b} h[b'] / T)), a monotone
+ *              equal-width -> equal-depth remap;
+ *   bucket   = map[bin(e)] in [0, m).  tau = m stands for "infinity". */
+typedef struct {
+    uint32_t d_min, d_max;
+    int32_t sh;
+    int32_t m;
+    int32_t sample_lists;
+    int64_t sample_size;
+    int32_t tau;            /* final threshold bucket (Update on the final buffer) */
+    int64_t pushed;         /* objects appended to the buffer over the whole scan */
+    int64_t below;          /* objects in buckets < tau */
+    uint8_t map[256];
+} oracle_codebook;
+
+static int32_t bin_of(uint32_t e, const oracle_codebook* cb) {
+    if (e <= cb->d_min) return 0;
+    uint32_t b = (e - cb->d_min) >> cb->sh;
+    return b > 255u ? 255 : (int32_t)b;
+}
+
+static int32_t bucket_of(uint32_t e, const oracle_codebook* cb) { return cb->map[bin_of(e, cb)]; }
+
+/* Update (Algorithm 1, lines 5-11): first bucket whose running count reaches
+ * Kc ("reaches or exceeds", Section 3.2 text and the Figure 3 example). */
+int32_t oracle_update(const int64_t* counts, int32_t m, int64_t Kc) {
+    int64_t s = 0;
+    for (int32_t i = 0; i < m; ++i) {
+        s += counts[i];
+        if (s >= Kc) return i;
+    }
+    return m;
+}
+
+static int cmp_u32(const void* a, const void* b) {
+    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+void oracle_build_codebook(const uint32_t* sample_e, int64_t ns, int64_t Kc, int32_t m,
+                           oracle_codebook* cb) {
+    memset(cb->map, 0, sizeof(cb->map));
+    cb->m = m;
+    cb->sample_size = ns;
+    if (ns <= 0) { cb->d_min = cb->d_max = 0; cb->sh = 0; return; }
+    uint32_t* s = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)ns);
+    memcpy(s, sample_e, sizeof(uint32_t) * (size_t)ns);
+    qsort(s, (size_t)ns, sizeof(uint32_t), cmp_u32);            /* partial sort, done fully */
+    int64_t t = ns < Kc ? ns : Kc;
+    cb->d_min = s[0];
+    cb->d_max = s[t - 1];
+    int32_t sh = 0;
+    while (((cb->d_max - cb->d_min) >> sh) > 255u) ++sh;
+    cb->sh = sh;
+    int64_t h[256];
+    memset(h, 0, sizeof(h));
+    int64_t T = 0;
+    for (int64_t i = 0; i < ns; ++i) {
+        if (s[i] > cb->d_max) break;
+        h[bin_of(s[i], cb)]++;
+        ++T;
+    }
+    int64_t cum = 0;
+    for (int32_t b = 0; b < 256; ++b) {
+        int64_t v = (int64_t)m * cum / T;
+        cb->map[b] = (uint8_t)(v > m - 1 ? m - 1 : v);
+        cum += h[b];
+    }
+    free(s);
+}
+
+/* Collect (Algorithm 1, lines 12-24) over the scanned lists in probe order.
+ * e/ids hold the scanned objects list after list; list_ofs[j]..list_ofs[j+1]
+ * is list j.  Outputs the Kc candidates (ascending (e, id)), the codebook,
+ * the final bucket counts (counts[m]) and returns the number written. */
+int64_t oracle_bucket_collect(const uint32_t* e, const int64_t* ids, const int64_t* list_ofs,
+                              int32_t nl, int64_t Kc, int32_t m, int32_t sample_min,
+                              oracle_codebook* cb, int64_t* counts_out,
+                              int64_t* out_ids, uint32_t* out_e) {
+    const int64_t Sq = list_ofs[nl] - list_ofs[0];
+    const int64_t want = Kc < Sq ? Kc : Sq;
+    int32_t ns_lists = sample_min < nl ? sample_min : nl;
+    while (ns_lists < nl && list_ofs[ns_lists] - list_ofs[0] < want) ++ns_lists;
+    int64_t ns = list_ofs[ns_lists] - list_ofs[0];
+    oracle_build_codebook(e + list_ofs[0], ns, Kc, m, cb);
+    cb->sample_lists = ns_lists;
+
+    /* buckets: linear buffers appended at the tail (one shared arena, per-bucket chains) */
+    int64_t* cnt = (int64_t*)calloc((size_t)m, sizeof(int64_t));
+    int64_t* cap = (int64_t*)calloc((size_t)m, sizeof(int64_t));
+    ukey** B = (ukey**)calloc((size_t)m, sizeof(ukey*));
+    int32_t tau = m;                                  /* line 13: tau <- infinity */
+    int64_t pushed = 0;
+    for (int32_t j = 0; j < nl; ++j) {                /* line 15: each cluster in probe order */
+        for (int64_t i = list_ofs[j]; i < list_ofs[j + 1]; ++i) {
+            int32_t a = bucket_of(e[i], cb);           /* Push, line 2 */
+            if (a <= tau) {                            /* Push, line 3 */
+                if (cnt[a] == cap[a]) {
+                    cap[a] = cap[a] ? 2 * cap[a] : 64;
+                    B[a] = (ukey*)realloc(B[a], sizeof(ukey) * (size_t)cap[a]);
+                }
+                B[a][cnt[a]].e = e[i];
+                B[a][cnt[a]].id = ids[i];
+                cnt[a]++;
+                ++pushed;
+            }
+        }
+        tau = oracle_update(cnt, m, Kc);              /* line 18 */
+    }
+    int64_t nres = 0;
+    if (tau >= m) {                                    /* fewer than Kc objects in total */
+        ukey* all = (ukey*)malloc(sizeof(ukey) * (size_t)(pushed > 0 ? pushed : 1));
+        for (int32_t a = 0; a < m; ++a)
+            for (int64_t i = 0; i < cnt[a]; ++i) all[nres++] = B[a][i];
+        qsort(all, (size_t)nres, sizeof(ukey), cmp_ukey);
+        for (int64_t i = 0; i < nres; ++i) { out_ids[i] = all[i].id; if (out_e) out_e[i] = all[i].e; }
+        free(all);
+        cb->below = nres;
+    } else {
+        /* lines 19-21: buckets before tau; lines 22-23: top-s of bucket tau */
+        ukey* res = (ukey*)malloc(sizeof(ukey) * (size_t)Kc);
+        for (int32_t a = 0; a < tau; ++a)
+            for (int64_t i = 0; i < cnt[a]; ++i) res[nres++] = B[a][i];
+        cb->below = nres;
+        int64_t s = Kc - nres;
+        qsort(B[tau], (size_t)cnt[tau], sizeof(ukey), cmp_ukey);
+        for (int64_t i = 0; i < s; ++i) res[nres++] = B[tau][i];
+        qsort(res, (size_t)nres, sizeof(ukey), cmp_ukey);
+        for (int64_t i = 0; i < nres; ++i) { out_ids[i] = res[i].id; if (out_e) out_e[i] = res[i].e; }
+        free(res);
+    }
+    cb->tau = tau;
+    cb->pushed = pushed;
+    if (counts_out) for (int32_t a = 0; a < m; ++a) counts_out[a] = cnt[a];
+    for (int32_t a = 0; a < m; ++a) free(B[a]);
+    free(B); free(cnt); free(cap);
+    return nres;
+}
+
+/* ------------------------------------------------------------------ */
+/* re-rank and final top-k                                              */
+/* ------------------------------------------------------------------ */
+void oracle_rerank(const float* q, const float* vectors, int32_t d, int32_t metric,
+                   const int64_t* ids, int64_t n, double* out_d) {
+    for (int64_t i = 0; i < n; ++i)
+        out_d[i] = oracle_dist(q, vectors + (size_t)ids[i] * d, d, metric);
+}
+
+/* k smallest (dist, id) ascending; pads with id -1 and +inf when n < k. */
+void oracle_topk_final(const double* dist, const int64_t* ids, int64_t n, int32_t k,
+                       int64_t* out_ids, double* out_d) {
+    dkey* a = (dkey*)malloc(sizeof(dkey) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) { a[i].s = dist[i]; a[i].id = ids[i]; }
+    qsort(a, (size_t)n, sizeof(dkey), cmp_dkey);
+    for (int32_t i = 0; i < k; ++i) {
+        if (i < n) { out_ids[i] = a[i].id; out_d[i] = a[i].s; }
+        else { out_ids[i] = -1; out_d[i] = INFINITY; }
+    }
+    free(a);
+}
+
+/* ------------------------------------------------------------------ */
+/* whole path                                                           */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t n;
+    int32_t d, nlist, metric, M, bits;
+    const float* centroids;      /* [nlist*d] */
+    const int64_t* list_offsets; /* [nlist+1] */
+    const int64_t* ids;          /* [n] list order */
+    const uint8_t* codes;        /* [n*code_bytes] list order */
+    const float* books;          /* [M*2^bits*d/M] */
+    const float* vectors;        /* [n*d] id order */
+} oracle_ivfpq;
+
+/* collector: 0 = sort, 1 = heap, 2 = bucket (Algorithm 1).
+ * Kc = candidates kept for the re-rank (the paper's n_cand).
+ * stats (optional, per query): [0] S_q scanned, [1] candidates, [2] tau,
+ * [3] pushed (bucket collector only). */
+int oracle_search(const oracle_ivfpq* ix, const float* queries, int64_t nq, int32_t k,
+                  int32_t nprobe, int64_t Kc, int32_t collector, int32_t m, int32_t sample_min,
+                  int64_t* out_ids, double* out_d, int64_t* stats) {
+    if (k <= 0 || nprobe < 1 || nprobe > ix->nlist || Kc < 1) return -1;
+    const int32_t d = ix->d, K = 1 << ix->bits, cb = ix->M * ix->bits / 8;
+    int32_t* lists = (int32_t*)malloc(sizeof(int32_t) * (size_t)nprobe);
+    uint16_t* lut = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)ix->M * K);
+    int64_t sq_max = 0;
+    for (int32_t l = 0; l < ix->nlist; ++l) {
+        int64_t s = ix->list_offsets[l + 1] - ix->list_offsets[l];
+        sq_max += s;
+    }
+    uint32_t* e = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(sq_max + 1));
+    int64_t* sid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(sq_max + 1));
+    int64_t* lofs = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nprobe + 1));
+    int64_t* cand = (int64_t*)malloc(sizeof(int64_t) * (size_t)Kc);
+    double* cd = (double*)malloc(sizeof(double) * (size_t)Kc);
+    int64_t* cnts = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    for (int64_t qi = 0; qi < nq; ++qi) {
+        const float* q = queries + (size_t)qi * d;
+        oracle_probe(q, ix->centroids, ix->nlist, d, ix->metric, nprobe, lists, NULL);
+        oracle_lut16(q, ix->books, d, ix->M, ix->bits, ix->metric, lut, NULL);
+        int64_t sq = 0;
+        lofs[0] = 0;
+        for (int32_t j = 0; j < nprobe; ++j) {
+            int64_t a = ix->list_offsets[lists[j]], b = ix->list_offsets[lists[j] + 1];
+            oracle_adc(lut, ix->codes + (size_t)a * cb, b - a, ix->M, ix->bits, e + sq);
+            for (int64_t i = a; i < b; ++i) sid[sq + (i - a)] = ix->ids[i];
+            sq += b - a;
+            lofs[j + 1] = sq;
+        }
+        int64_t nc;
+        oracle_codebook cbk;
+        memset(&cbk, 0, sizeof(cbk));
+        if (collector == 0) nc = oracle_topkc_sort(e, sid, sq, Kc, cand, NULL);
+        else if (collector == 1) nc = oracle_topkc_heap(e, sid, sq, Kc, cand, NULL);
+        else nc = oracle_bucket_collect(e, sid, lofs, nprobe, Kc, m, sample_min, &cbk, cnts, cand, NULL);
+        oracle_rerank(q, ix->vectors, d, ix->metric, cand, nc, cd);
+        oracle_topk_final(cd, cand, nc, k, out_ids + (size_t)qi * k, out_d + (size_t)qi * k);
+        if (stats) {
+            stats[qi * 4 + 0] = sq;
+            stats[qi * 4 + 1] = nc;
+            stats[qi * 4 + 2] = collector == 2 ? cbk.tau : -1;
+            stats[qi * 4 + 3] = collector == 2 ? cbk.pushed : -1;
+        }
+    }
+    free(lists); free(lut); free(e); free(sid); free(lofs); free(cand); free(cd); free(cnts);
+    return 0;
+}
+
+/* Exact kNN over all n vectors, FP64. */
+void oracle_bruteforce(const float* queries, int64_t nq, const float* x, int64_t n, int32_t d,
+                       int32_t metric, int32_t k, int64_t* out_ids, double* out_d) {
+    double* dist = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int64_t* ids = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) ids[i] = i;
+    for (int64_t qi = 0; qi < nq; ++qi) {
+        for (int64_t i = 0; i < n; ++i)
+            dist[i] = oracle_dist(queries + (size_t)qi * d, x + (size_t)i * d, d, metric);
+        oracle_topk_final(dist, ids, n, k, out_ids + (size_t)qi * k, out_d + (size_t)qi * k);
+    }
+    free(dist);
+    free(ids);
+}

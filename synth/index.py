@@ -1,0 +1,248 @@
+"""Offline IVF index construction over synthetic data (seeded, deterministic).
+
+The index is an input to the search path, built once before any query runs:
+
+* IVF: k-means centroids (seed 3); every vector goes to its nearest centroid's
+  inverted list (the paper's indexing phase, Section 2 "Quantization").
+* PQ: non-residual product quantisation, M sub-spaces of d/M dimensions with
+  2^b codewords each, trained by k-means on raw sub-vectors (seed 4).
+* Sign codes: a seeded random rotation (seed 5) of each vector's residual to
+  its list centroid, kept as one sign bit per dimension plus per-vector
+  scalars (see ``build_ivf_sign``).
+
+Lists keep vectors in ascending id order.  The canonical code layout is one
+row per vector in list order; for 8-bit PQ byte m holds sub-space m, for
+4-bit PQ byte m/2 holds sub-space m in its low nibble when m is even and in
+its high nibble when m is odd.
+
+File format (little-endian, written by ``write_index``): a 64-byte header
+``b"BBCIDX01"``, u32 version, u32 quantizer (0 PQ, 1 sign), u32 metric
+(0 L2, 1 IP), u32 d, u64 n, u32 nlist, u32 pq_m, u32 pq_bits, then padding;
+followed by the arrays, each starting on a 64-byte boundary, in this order:
+centroids f32[nlist*d], list_offsets i64[nlist+1], ids i64[n] (list order),
+codes u8[n*code_bytes] (list order), codebooks f32[pq_m*2^b*(d/pq_m)],
+vectors f32[n*d] (id order).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import struct
+
+import numpy as np
+
+SEED_KMEANS = 3
+SEED_PQ = 4
+SEED_ROT = 5
+
+MAGIC = b"BBCIDX01"
+HEADER_FMT = "<8sIIIIQIII"  # magic, version, quantizer, metric, d, n, nlist, pq_m, pq_bits
+HEADER_BYTES = 64
+
+
+def _sqnorms(x: np.ndarray) -> np.ndarray:
+    return np.einsum("ij,ij->i", x, x, dtype=np.float32)
+
+
+def nearest(x: np.ndarray, c: np.ndarray, chunk: int = 1 << 16, device: str | None = None) -> np.ndarray:
+    """Index of the nearest row of ``c`` (squared L2) for each row of ``x``.
+
+    Runs through torch (multi-threaded on CPU, or on ``device``) in FP32;
+    the result only has to be deterministic for a given machine.
+    """
+    import torch
+    dev = torch.device(device or _DEVICE)
+    ct = torch.from_numpy(np.ascontiguousarray(c, dtype=np.float32)).to(dev)
+    cn = (ct * ct).sum(1)
+    out = np.empty(x.shape[0], dtype=np.int64)
+    for s in range(0, x.shape[0], chunk):
+        xs = torch.from_numpy(np.ascontiguousarray(x[s:s + chunk], dtype=np.float32)).to(dev)
+        dist = cn[None, :] - 2.0 * (xs @ ct.T)
+        out[s:s + chunk] = torch.argmin(dist, dim=1).cpu().numpy()
+    return out
+
+
+_DEVICE = "cpu"
+
+
+def set_build_device(device: str) -> None:
+    """Run the index builder's nearest-centroid searches on ``device`` (e.g. "cuda")."""
+    global _DEVICE
+    _DEVICE = device
+
+
+def kmeans(x: np.ndarray, k: int, iters: int = 12, seed: int = SEED_KMEANS,
+           sample: int | None = None) -> np.ndarray:
+    """Lloyd's k-means with a seeded initialisation from the data."""
+    rng = np.random.default_rng(seed)
+    n = x.shape[0]
+    if sample is not None and sample < n:
+        train = x[np.sort(rng.choice(n, size=sample, replace=False))]
+    else:
+        train = x
+    nt = train.shape[0]
+    if nt < k:
+        raise ValueError(f"k-means needs at least k={k} points, got {nt}")
+    cent = train[rng.choice(nt, size=k, replace=False)].astype(np.float32).copy()
+    for _ in range(iters):
+        assign = nearest(train, cent)
+        counts = np.bincount(assign, minlength=k)
+        sums = np.zeros((k, train.shape[1]), dtype=np.float64)
+        np.add.at(sums, assign, train) if nt < 4096 else _segment_sum(sums, assign, train)
+        nz = counts > 0
+        cent[nz] = (sums[nz] / counts[nz, None]).astype(np.float32)
+        empty = np.flatnonzero(~nz)
+        if empty.size:
+            cent[empty] = train[rng.choice(nt, size=empty.size, replace=False)]
+    return cent
+
+
+def _segment_sum(sums: np.ndarray, assign: np.ndarray, x: np.ndarray) -> None:
+    order = np.argsort(assign, kind="stable")
+    a = assign[order]
+    starts = np.flatnonzero(np.r_[True, a[1:] != a[:-1]])
+    red = np.add.reduceat(x[order].astype(np.float64), starts, axis=0)
+    sums[a[starts]] = red
+
+
+@dataclasses.dataclass
+class IvfPqIndex:
+    metric: str                 # "l2" or "ip"
+    d: int
+    nlist: int
+    pq_m: int
+    pq_bits: int
+    centroids: np.ndarray       # f32 [nlist, d]
+    list_offsets: np.ndarray    # i64 [nlist + 1]
+    ids: np.ndarray             # i64 [n], list order
+    codes: np.ndarray           # u8 [n, code_bytes], list order, canonical layout
+    codebooks: np.ndarray       # f32 [pq_m, 2^pq_bits, d / pq_m]
+    vectors: np.ndarray         # f32 [n, d], id order
+
+    @property
+    def n(self) -> int:
+        return int(self.vectors.shape[0])
+
+    @property
+    def code_bytes(self) -> int:
+        return self.pq_m * self.pq_bits // 8
+
+    @property
+    def list_sizes(self) -> np.ndarray:
+        return np.diff(self.list_offsets)
+
+
+def _pack4(codes: np.ndarray) -> np.ndarray:
+    lo = codes[:, 0::2].astype(np.uint8)
+    hi = codes[:, 1::2].astype(np.uint8)
+    return (lo | (hi << 4)).astype(np.uint8)
+
+
+def unpack_codes(codes: np.ndarray, pq_m: int, pq_bits: int) -> np.ndarray:
+    """Canonical code rows -> one integer code per sub-space, shape [n, pq_m]."""
+    if pq_bits == 8:
+        return codes.astype(np.int64)
+    out = np.empty((codes.shape[0], pq_m), dtype=np.int64)
+    out[:, 0::2] = codes & 0x0F
+    out[:, 1::2] = codes >> 4
+    return out
+
+
+def _inverted_lists(assign: np.ndarray, nlist: int):
+    order = np.argsort(assign, kind="stable")          # ascending id inside each list
+    counts = np.bincount(assign, minlength=nlist)
+    offsets = np.zeros(nlist + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    return order.astype(np.int64), offsets
+
+
+def build_ivf_pq(x: np.ndarray, nlist: int, pq_m: int, pq_bits: int, metric: str = "l2",
+                 kmeans_iters: int = 12, pq_iters: int = 12, kmeans_sample: int | None = None,
+                 pq_sample: int = 65536) -> IvfPqIndex:
+    """Build an IVF-PQ index (non-residual PQ) over ``x`` (f32 [n, d])."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n, d = x.shape
+    if d % pq_m:
+        raise ValueError("pq_m must divide d")
+    if pq_bits not in (4, 8):
+        raise ValueError("pq_bits must be 4 or 8")
+    if pq_bits == 4 and pq_m % 2:
+        raise ValueError("4-bit PQ needs an even pq_m")
+    if kmeans_sample is None:
+        kmeans_sample = min(n, 256 * nlist)
+    cent = kmeans(x, nlist, iters=kmeans_iters, seed=SEED_KMEANS, sample=kmeans_sample)
+    assign = nearest(x, cent)
+    ids, offsets = _inverted_lists(assign, nlist)
+
+    dsub = d // pq_m
+    ksub = 1 << pq_bits
+    rng = np.random.default_rng(SEED_PQ)
+    samp = x[np.sort(rng.choice(n, size=min(n, pq_sample), replace=False))]
+    books = np.empty((pq_m, ksub, dsub), dtype=np.float32)
+    codes_full = np.empty((n, pq_m), dtype=np.uint8)
+    for m in range(pq_m):
+        sub = np.ascontiguousarray(samp[:, m * dsub:(m + 1) * dsub])
+        books[m] = kmeans(sub, ksub, iters=pq_iters, seed=SEED_PQ + 17 * m)
+        codes_full[:, m] = nearest(np.ascontiguousarray(x[:, m * dsub:(m + 1) * dsub]), books[m])
+    codes_full = codes_full[ids]
+    codes = codes_full if pq_bits == 8 else _pack4(codes_full)
+    return IvfPqIndex(metric, d, nlist, pq_m, pq_bits, cent, offsets, ids,
+                      np.ascontiguousarray(codes), books, x)
+
+
+def _align(f, a: int = 64) -> None:
+    pos = f.tell()
+    pad = (-pos) % a
+    if pad:
+        f.write(b"\0" * pad)
+
+
+def write_index(path: str, idx: IvfPqIndex) -> None:
+    """Write an IVF-PQ index in the BBCIDX01 format described in the module docstring."""
+    with open(path, "wb") as f:
+        hdr = struct.pack(HEADER_FMT, MAGIC, 1, 0, 0 if idx.metric == "l2" else 1,
+                          idx.d, idx.n, idx.nlist, idx.pq_m, idx.pq_bits)
+        f.write(hdr + b"\0" * (HEADER_BYTES - len(hdr)))
+        for arr, dt in ((idx.centroids, np.float32), (idx.list_offsets, np.int64),
+                        (idx.ids, np.int64), (idx.codes, np.uint8),
+                        (idx.codebooks, np.float32), (idx.vectors, np.float32)):
+            _align(f)
+            f.write(np.ascontiguousarray(arr, dtype=dt).tobytes())
+
+
+# Placeholders for the sign-code index are filled in by build_ivf_sign below.
+@dataclasses.dataclass
+class IvfSignIndex:
+    metric: str
+    d: int
+    nlist: int
+    centroids: np.ndarray       # f32 [nlist, d]
+    list_offsets: np.ndarray    # i64 [nlist + 1]
+    ids: np.ndarray             # i64 [n], list order
+    rotation: np.ndarray        # f32 [d, d], orthonormal
+    signs: np.ndarray           # u8 [n, d / 8], list order, bit i of byte j = sign of dim 8j+i
+    vectors: np.ndarray         # f32 [n, d], id order
+
+
+def build_ivf_sign(x: np.ndarray, nlist: int, kmeans_iters: int = 12,
+                   kmeans_sample: int | None = None) -> IvfSignIndex:
+    """IVF with 1-bit sign codes of the rotated residual P_rot (o - c_l)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n, d = x.shape
+    if d % 8:
+        raise ValueError("d must be a multiple of 8 for sign codes")
+    if kmeans_sample is None:
+        kmeans_sample = min(n, 256 * nlist)
+    cent = kmeans(x, nlist, iters=kmeans_iters, seed=SEED_KMEANS, sample=kmeans_sample)
+    assign = nearest(x, cent)
+    ids, offsets = _inverted_lists(assign, nlist)
+    rng = np.random.default_rng(SEED_ROT)
+    rot, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    rot = rot.astype(np.float32)
+    signs = np.empty((n, d // 8), dtype=np.uint8)
+    chunk = 1 << 16
+    for s in range(0, n, chunk):
+        sel = ids[s:s + chunk]
+        r = (x[sel] - cent[assign[sel]]) @ rot.T
+        signs[s:s + chunk] = np.packbits(r > 0, axis=1, bitorder="little")
+    return IvfSignIndex("l2", d, nlist, cent, offsets, ids, rot, signs, x)

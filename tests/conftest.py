@@ -1,0 +1,68 @@
+"""Shared fixtures: seeded small workloads and their IVF-PQ indexes.
+
+Marker ``gpu``: the test needs a CUDA device and the compiled libbbc.so.
+"""
+
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled CUDA library")
+
+
+_CACHE = {}
+
+
+def small_workload(kind: str):
+    """Seeded small workloads spanning the configurations of the search path.
+
+    Each returns (index, queries).  Sizes keep the CPU oracle to seconds while
+    spanning several 32-vector blocks per list and ragged list tails.
+    """
+    if kind in _CACHE:
+        return _CACHE[kind]
+    from synth import build_ivf_pq
+    from synth.data import gaussian_mixture_tiny, sift_shaped, embedding_shaped
+    if kind == "tiny":        # FP32 Gaussian mixture, L2, PQ 16 x 8 bit
+        x, q = gaussian_mixture_tiny(12000, 24, d=64, n_centers=200, sigma=0.3)
+        idx = build_ivf_pq(x, 48, 16, 8, "l2", kmeans_iters=6, pq_iters=6, pq_sample=8000)
+    elif kind == "sift":      # integer [0,255] components, L2, PQ 32 x 8 bit
+        x, q = sift_shaped(12000, 24, d=128, n_centers=300)
+        idx = build_ivf_pq(x, 64, 32, 8, "l2", kmeans_iters=6, pq_iters=6, pq_sample=8000)
+    elif kind == "sift4":     # same data, PQ 64 x 4 bit
+        x, q = sift_shaped(12000, 24, d=128, n_centers=300)
+        idx = build_ivf_pq(x, 64, 64, 4, "l2", kmeans_iters=6, pq_iters=6, pq_sample=8000)
+    elif kind == "embed":     # unit norm, inner product, PQ 32 x 8 bit
+        x, q = embedding_shaped(12000, 24, d=64)
+        idx = build_ivf_pq(x, 48, 32, 8, "ip", kmeans_iters=6, pq_iters=6, pq_sample=8000)
+    elif kind == "ragged":    # few vectors, many short and empty lists
+        x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
+        idx = build_ivf_pq(x, 40, 8, 8, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700)
+    else:
+        raise KeyError(kind)
+    _CACHE[kind] = (idx, q)
+    return idx, q
+
+
+@pytest.fixture(scope="session")
+def oracle_lib():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def scanned_set(idx, lists):
+    """Positions of the probed lists in probe order and their list offsets."""
+    offs = idx.list_offsets
+    sel = [np.arange(offs[l], offs[l + 1]) for l in lists]
+    lofs = np.zeros(len(sel) + 1, dtype=np.int64)
+    lofs[1:] = np.cumsum([len(s) for s in sel])
+    return (np.concatenate(sel) if sel else np.zeros(0, np.int64)), lofs
