@@ -1,0 +1,200 @@
+/*
+ * bbc.h -- C ABI of the GB300 (sm_103a) search path for large-k ANN queries
+ * on IVF indexes with a bucket-based result collector (BBC, arxiv 2604.01960).
+ *
+ * Problem (Section 2, "Problem Statement"): given N d-dimensional vectors, an
+ * indexing phase builds a structure; a query q asks for the k nearest vectors
+ * under a metric.  Here the structure is an IVF partition with PQ codes, and
+ * the query path is: coarse probe -> PQ lookup table -> quantised-distance
+ * scan with the bucket-based result buffer (Algorithm 1) -> exact re-rank of
+ * the collected candidates -> final top-k.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: BBC_OK (0) or a negative BBC_ERR_*.
+ *    bbc_last_error() returns a thread-local message for the last failure.
+ *  - Argument errors are reported before anything is enqueued on the stream.
+ *  - "device" pointers are CUDA device (or managed) memory on the index's
+ *    device; "host" pointers are ordinary host memory.  The caller owns every
+ *    buffer it passes; the library owns the index and its workspaces.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device-pointer entry points are asynchronous: they return
+ *    after enqueuing work on `stream`.  Device-side faults that the kernels
+ *    detect (a collector region overrun) are latched in a per-index status
+ *    word that bbc_stream_status() reads after synchronising the stream.
+ *  - Distances are squared L2 (metric L2) or the negated inner product
+ *    -<q, v> (metric IP); results are ascending by (distance, id).  When fewer
+ *    than k vectors are scanned the tail is padded with id -1 and +inf
+ *    (Algorithm 1's Update returns "infinity" when fewer than k are buffered).
+ *  - Ties are broken by the smaller id everywhere: list id in the probe,
+ *    vector id among equal estimated distances and among equal exact ones.
+ */
+#ifndef BBC_H
+#define BBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BBC_OK 0
+#define BBC_ERR_ARG (-1)        /* invalid argument (null pointer, k <= 0, nprobe out of range, ...) */
+#define BBC_ERR_IO (-2)         /* index file cannot be opened or read */
+#define BBC_ERR_FORMAT (-3)     /* index file or arrays are malformed */
+#define BBC_ERR_OOM (-4)        /* host or device allocation failed */
+#define BBC_ERR_CUDA (-5)       /* a CUDA runtime call failed */
+#define BBC_ERR_CAPACITY (-6)   /* a device-side capacity check tripped */
+#define BBC_ERR_TIMEOUT (-7)    /* a bounded device-side wait ran out */
+#define BBC_ERR_BUSY (-8)       /* resource in use */
+#define BBC_ERR_UNSUPPORTED (-9) /* configuration this build does not handle */
+
+#define BBC_METRIC_L2 0
+#define BBC_METRIC_IP 1
+#define BBC_QUANT_PQ 0
+
+typedef struct bbc_index bbc_index;   /* opaque, owned by the library */
+
+/* Host-side description of an IVF-PQ index (Section 2, "Quantization"):
+ * nlist k-means centroids, inverted lists of vector ids, non-residual PQ with
+ * pq_m sub-spaces of d/pq_m dimensions and 2^pq_bits codewords each.
+ * All pointers are HOST pointers; bbc_index_create copies what it needs. */
+typedef struct {
+    int64_t n;                 /* number of vectors, 1 <= n < 2^32 - 1 */
+    int32_t d;                 /* dimension, multiple of pq_m */
+    int32_t nlist;             /* number of inverted lists */
+    int32_t metric;            /* BBC_METRIC_L2 or BBC_METRIC_IP */
+    int32_t pq_m;              /* sub-spaces: 8, 16, 32, 64, 96 or 128 (multiple of 32 above 32) */
+    int32_t pq_bits;           /* 8, or 4 with pq_m a multiple of 32 */
+    const float* centroids;    /* [nlist * d] row-major */
+    const int64_t* list_offsets; /* [nlist + 1], list l = positions [off[l], off[l+1]) */
+    const int64_t* ids;        /* [n] vector id at each list position */
+    const uint8_t* codes;      /* [n * pq_m * pq_bits / 8] one row per list position; 8-bit:
+                                  byte m = code of sub-space m; 4-bit: byte m/2, low nibble
+                                  for even m, high nibble for odd m */
+    const float* codebooks;    /* [pq_m * 2^pq_bits * (d/pq_m)], [m][j][i] */
+    const float* vectors;      /* [n * d] row-major by id (for the exact re-rank) */
+} bbc_index_host;
+
+typedef struct {
+    int64_t n;
+    int32_t d, nlist, metric, pq_m, pq_bits;
+    int32_t max_list_len;      /* longest inverted list */
+    int32_t vectors_u8_exact;  /* 1 if every component is an integer in [0,255] (exact u8 copy kept) */
+    int32_t device;
+    int64_t device_bytes;      /* bytes of device memory the index holds */
+} bbc_index_info_t;
+
+/* Build a device-resident index from host arrays (copied to `device`).
+ * Validates the arrays (offsets monotone and ending at n, ids in [0,n) and a
+ * permutation, pq shape supported): BBC_ERR_FORMAT / BBC_ERR_ARG otherwise. */
+int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out);
+
+/* Read an index file ("BBCIDX01" format: 64-byte header, then centroids,
+ * list_offsets, ids, codes, codebooks, vectors, each 64-byte aligned) and
+ * create the device index.  BBC_ERR_IO / BBC_ERR_FORMAT on a bad file. */
+int bbc_index_load(const char* path, int device, bbc_index** out);
+
+int bbc_index_free(bbc_index* ix);
+int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
+
+/* Search parameters, settable per index.  Keys:
+ *   "kc_ratio"     K_c = ceil(kc_ratio * k) candidates are collected by
+ *                  estimated distance and re-ranked (the paper's n_cand,
+ *                  Section 2 and Table 4).  Default 1.5; must be >= 1.
+ *   "buckets"      m, buckets of the result buffer (Section 3.2), 2..256.  Default 64.
+ *   "sample_lists" minimum number of nearest lists sampled to build the
+ *                  codebook (Section 3.2: "5-10 nearest clusters").  Default 8.
+ *   "rerank"       0 = FP32 vectors, 1 = exact u8 copy (only when
+ *                  vectors_u8_exact).  Default: 1 when available.
+ *   "workspace_mb" device workspace budget per call; queries are processed in
+ *                  chunks that fit.  Default 8192.
+ * Unknown key or out-of-range value: BBC_ERR_ARG. */
+int bbc_set_param(bbc_index* ix, const char* key, double value);
+int bbc_get_param(const bbc_index* ix, const char* key, double* value);
+
+/* Full search for nq queries (the hot path of Algorithms 1 and 4 with the
+ * sort-free re-rank of the collected candidates).
+ *   queries   device f32 [nq * d], row-major
+ *   k         results per query, >= 1
+ *   nprobe    lists probed per query, 1..nlist
+ *   out_ids   device i64 [nq * k], ascending by (dist, id); -1 padding
+ *   out_dists device f32 [nq * k]; +inf padding
+ * Asynchronous on `stream`.  The first call with a given shape may allocate
+ * the index's workspace (cudaMalloc); later calls of equal or smaller shape
+ * do not. */
+int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe,
+               int64_t* out_ids, float* out_dists, void* stream);
+
+/* Same as bbc_search with HOST query and output buffers: copies the queries
+ * to the device, searches, copies the results back, and synchronises
+ * `stream` before returning. */
+int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe,
+                    int64_t* out_ids, float* out_dists, void* stream);
+
+/* ---- stage entry points (each one row of the hot path; device pointers) ---- */
+
+/* Coarse probe (Section 2: route q to the n_probe nearest clusters;
+ * Algorithm 4 scans them nearest first).  out_lists: device i32
+ * [nq * nprobe], ascending by (FP64 score, list id), where the score is
+ * sum_i (q_i - c_i)^2 (L2) or -sum_i q_i c_i (IP) evaluated in FP64 in
+ * ascending dimension order. */
+int bbc_probe(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
+              int32_t* out_lists, void* stream);
+
+/* PQ lookup table (Section 2, step (1)) quantised to uint16:
+ * out_lut16 device u16 [nq * pq_m * 2^pq_bits], [q][m][j].
+ * FP32 entry L[m][j] = sum_i (q_i - y_i)^2 (or -sum_i q_i y_i) in ascending i,
+ * lo_m = min_j L[m][j], span = max_m (max_j L[m][j] - lo_m),
+ * entry = min(65535, floor((L - lo_m) * (65535 / span) + 0.5)), 0 when span = 0. */
+int bbc_lut(bbc_index* ix, const float* queries, int64_t nq, uint16_t* out_lut16, void* stream);
+
+/* Per-query state of the bucket-based result buffer after the scan. */
+typedef struct {
+    uint32_t d_min, d_max;     /* codebook range from the sampled lists */
+    int32_t sh;                /* equal-width bin width delta = 2^sh */
+    int32_t m;                 /* buckets */
+    int32_t sample_lists;      /* lists in the codebook sample */
+    int32_t tau;               /* final threshold bucket (m = infinity) */
+    int64_t sample_size;       /* objects in the sample */
+    int64_t scanned;           /* S_q, objects scanned */
+    int64_t pushed;            /* objects appended to the buffer */
+    int64_t below;             /* objects in buckets < tau */
+    int64_t kc;                /* candidates requested */
+    uint32_t hist[256];        /* per-bucket counts of appended objects */
+    uint8_t map[256];          /* equal-width bin -> equal-depth bucket */
+} bbc_collector_state;
+
+/* Probe + LUT + scan with the bucket-based result buffer + final selection
+ * (Algorithm 1: Push / Update / Collect).  Produces the K_c candidates with
+ * the smallest (estimated distance, id) among the scanned objects.
+ *   probe_lists   device i32 [nq * nprobe] from bbc_probe
+ *   kc            candidates per query (K_c >= 1)
+ *   out_ids       device u32 [nq * kc], unordered within a query
+ *   out_count     device i64 [nq], min(kc, S_q)
+ *   out_state     device bbc_collector_state [nq], or NULL */
+int bbc_collect(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
+                const int32_t* probe_lists, int64_t kc, uint32_t* out_ids, int64_t* out_count,
+                bbc_collector_state* out_state, void* stream);
+
+/* Exact re-rank of candidates and final top-k (Algorithm 4, last two lines).
+ *   cand_ids   device u32 [nq * kc]; cand_count device i64 [nq]
+ *   out_ids / out_dists as in bbc_search. */
+int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint32_t* cand_ids,
+                    const int64_t* cand_count, int64_t kc, int32_t k, int64_t* out_ids,
+                    float* out_dists, void* stream);
+
+/* Synchronise `stream`, then read and clear the index's device status word.
+ * Returns BBC_OK, or BBC_ERR_CAPACITY if a kernel latched an overrun. */
+int bbc_stream_status(bbc_index* ix, void* stream);
+
+/* Thread-local message describing the last error returned on this thread. */
+const char* bbc_last_error(void);
+
+/* Library version string. */
+const char* bbc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BBC_H */

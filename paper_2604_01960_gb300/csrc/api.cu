@@ -1,0 +1,592 @@
+// Host side of libbbc: the C ABI declared in include/bbc.h.
+//
+// Owns the device-resident index (layout described in bbc_internal.cuh), the
+// per-(index, stream) workspaces, argument checking and the launch sequence
+// of the search path:
+//   S1 probe scores -> S2 exact probe selection -> S3 uint16 LUT ->
+//   S4-S6 scan + bucket-based result buffer -> S7 final selection ->
+//   S8 exact re-rank -> S9 final top-k.
+// Queries are processed in chunks whose workspace fits the budget.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bbc_internal.cuh"
+
+namespace bbc {
+bool scan_supported(int M, int bits);
+}
+
+using namespace bbc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess)                                                          \
+            return fail(BBC_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e),  \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct Workspace {
+    char* base = nullptr;
+    size_t bytes = 0;
+};
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct bbc_index {
+    int device = 0;
+    bbc_index_info_t info{};
+    DevIndex dev{};
+    std::vector<void*> owned;
+    std::vector<int64_t> cap_prefix;     // cap_prefix[p] = sum of the p longest lists
+    // parameters
+    double kc_ratio = 1.5;
+    int buckets = 64;
+    int sample_lists = 8;
+    int rerank_u8 = 1;
+    double workspace_mb = 8192.0;
+    std::mutex mu;
+    std::map<cudaStream_t, Workspace> ws;
+
+    ~bbc_index() {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        cudaSetDevice(device);
+        for (auto& kv : ws) cudaFree(kv.second.base);
+        for (void* p : owned) cudaFree(p);
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+namespace {
+
+template <typename T>
+int upload(bbc_index* ix, const T* h, size_t count, T** out) {
+    void* p = nullptr;
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(BBC_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    ix->owned.push_back(p);
+    ix->info.device_bytes += (int64_t)bytes;
+    if (count) {
+        e = cudaMemcpy(p, h, count * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(BBC_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    *out = static_cast<T*>(p);
+    return BBC_OK;
+}
+
+// Workspace arena for one chunk of queries.
+struct Plan {
+    int64_t chunk;        // queries per chunk
+    int nprobe;
+    int64_t kc;
+    int k;
+    int64_t cap;
+    size_t off_scores, off_probe, off_lut, off_state, off_region, off_cand, off_count, off_cdist,
+        off_q, off_ids, off_dists, total;
+};
+
+Plan make_plan(const bbc_index* ix, int64_t nq, int nprobe, int64_t kc, int k, bool host_io) {
+    Plan p{};
+    p.nprobe = nprobe;
+    p.kc = kc;
+    p.k = k;
+    p.cap = ix->cap_prefix[nprobe];
+    const DevIndex& d = ix->dev;
+    auto per_query = [&](int64_t c) {
+        size_t o = 0;
+        p.off_scores = o; o = align_up(o + (size_t)c * d.nlist * 4);
+        p.off_probe = o; o = align_up(o + (size_t)c * nprobe * 4);
+        p.off_lut = o; o = align_up(o + (size_t)c * d.M * d.K * 2);
+        p.off_state = o; o = align_up(o + (size_t)c * sizeof(bbc_collector_state));
+        p.off_region = o; o = align_up(o + (size_t)c * p.cap * 8);
+        p.off_cand = o; o = align_up(o + (size_t)c * kc * 4);
+        p.off_count = o; o = align_up(o + (size_t)c * 8);
+        p.off_cdist = o; o = align_up(o + (size_t)c * kc * 4);
+        p.off_q = o; o = align_up(o + (host_io ? (size_t)c * d.d * 4 : 0));
+        p.off_ids = o; o = align_up(o + (host_io ? (size_t)c * k * 8 : 0));
+        p.off_dists = o; o = align_up(o + (host_io ? (size_t)c * k * 4 : 0));
+        return o;
+    };
+    const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
+    int64_t c = std::max<int64_t>(1, nq);
+    while (c > 1 && per_query(c) > budget) c = (c + 1) / 2;
+    p.chunk = c;
+    p.total = per_query(c);
+    return p;
+}
+
+int get_workspace(bbc_index* ix, cudaStream_t st, size_t bytes, char** base) {
+    std::lock_guard<std::mutex> lk(ix->mu);
+    Workspace& w = ix->ws[st];
+    if (w.bytes < bytes) {
+        if (w.base) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return fail(BBC_ERR_CUDA, "sync before workspace growth: %s", cudaGetErrorString(e));
+            cudaFree(w.base);
+            w.base = nullptr;
+            w.bytes = 0;
+        }
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return fail(BBC_ERR_OOM, "workspace cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        w.base = static_cast<char*>(p);
+        w.bytes = bytes;
+    }
+    *base = w.base;
+    return BBC_OK;
+}
+
+int64_t kc_for(const bbc_index* ix, int k) {
+    int64_t kc = (int64_t)std::ceil(ix->kc_ratio * (double)k - 1e-9);
+    return std::max<int64_t>(kc, k);
+}
+
+int check_search_args(const bbc_index* ix, const void* queries, int64_t nq, int k, int nprobe,
+                      const void* out_ids, const void* out_dists) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    if (nq < 0) return fail(BBC_ERR_ARG, "nq < 0");
+    if (nq > 0 && (!queries || !out_ids || !out_dists)) return fail(BBC_ERR_ARG, "null buffer");
+    if (k <= 0) return fail(BBC_ERR_ARG, "k must be >= 1 (got %d)", k);
+    if (nprobe < 1 || nprobe > ix->dev.nlist) return fail(BBC_ERR_ARG, "nprobe %d outside [1, %d]", nprobe, ix->dev.nlist);
+    if (nprobe > 2048) return fail(BBC_ERR_UNSUPPORTED, "nprobe %d > 2048", nprobe);
+    return BBC_OK;
+}
+
+// The launch sequence for one chunk.
+int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc, int64_t* out_ids,
+              float* out_dists, cudaStream_t st, int stop_after /* 9 = all */,
+              int32_t* probe_out = nullptr, const int32_t* probe_in = nullptr, uint32_t* cand_out = nullptr,
+              int64_t* count_out = nullptr, bbc_collector_state* state_out = nullptr) {
+    const DevIndex& d = ix->dev;
+    float* scores = reinterpret_cast<float*>(ws + p.off_scores);
+    int32_t* probe = probe_out ? probe_out : reinterpret_cast<int32_t*>(ws + p.off_probe);
+    uint16_t* lut = reinterpret_cast<uint16_t*>(ws + p.off_lut);
+    bbc_collector_state* state = state_out ? state_out : reinterpret_cast<bbc_collector_state*>(ws + p.off_state);
+    uint2* region = reinterpret_cast<uint2*>(ws + p.off_region);
+    uint32_t* cand = cand_out ? cand_out : reinterpret_cast<uint32_t*>(ws + p.off_cand);
+    int64_t* count = count_out ? count_out : reinterpret_cast<int64_t*>(ws + p.off_count);
+    float* cdist = reinterpret_cast<float*>(ws + p.off_cdist);
+    if (!probe_in) {
+        CUDA_TRY(launch_probe_scores(d, q, nc, scores, st));
+        CUDA_TRY(launch_probe_select(d, q, nc, p.nprobe, scores, probe, st));
+    }
+    if (stop_after <= 2) return BBC_OK;
+    CUDA_TRY(launch_lut16(d, q, nc, lut, st));
+    ScanArgs sa{lut, probe_in ? probe_in : probe, p.nprobe, p.kc, ix->buckets, ix->sample_lists,
+                region, p.cap, state};
+    CUDA_TRY(launch_scan(d, nc, sa, st));
+    SelectArgs se{region, p.cap, state, p.kc, cand, count, nullptr};
+    CUDA_TRY(launch_select(d, nc, se, st));
+    if (stop_after <= 7) return BBC_OK;
+    RerankArgs ra{q, cand, count, p.kc, ix->rerank_u8 && d.vec_u8 != nullptr, cdist, p.k, out_ids,
+                  out_dists, nullptr};
+    CUDA_TRY(launch_rerank(d, nc, ra, st));
+    CUDA_TRY(launch_topk(d, nc, ra, st));
+    return BBC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* bbc_last_error(void) { return g_err.c_str(); }
+
+const char* bbc_version(void) { return "bbc-gb300 0.1 (sm_103a)"; }
+
+int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out) {
+    if (!h || !out) return fail(BBC_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (h->n < 1 || h->n >= (int64_t)0xFFFFFFFFll) return fail(BBC_ERR_ARG, "n=%lld outside [1, 2^32-1)", (long long)h->n);
+    if (h->d < 4 || h->d % 4) return fail(BBC_ERR_ARG, "d=%d must be a positive multiple of 4", h->d);
+    if (h->nlist < 1) return fail(BBC_ERR_ARG, "nlist must be >= 1");
+    if (h->metric != BBC_METRIC_L2 && h->metric != BBC_METRIC_IP) return fail(BBC_ERR_ARG, "bad metric %d", h->metric);
+    if (h->pq_m < 1 || h->d % h->pq_m) return fail(BBC_ERR_ARG, "pq_m=%d must divide d=%d", h->pq_m, h->d);
+    if (!scan_supported(h->pq_m, h->pq_bits))
+        return fail(BBC_ERR_UNSUPPORTED, "pq_m=%d x %d bits not supported", h->pq_m, h->pq_bits);
+    if (!h->centroids || !h->list_offsets || !h->ids || !h->codes || !h->codebooks || !h->vectors)
+        return fail(BBC_ERR_ARG, "null array");
+    const int64_t n = h->n;
+    const int L = h->nlist, d = h->d, M = h->pq_m, bits = h->pq_bits, K = 1 << bits;
+    if (h->list_offsets[0] != 0 || h->list_offsets[L] != n) return fail(BBC_ERR_FORMAT, "list_offsets must run from 0 to n");
+    int32_t maxlen = 0;
+    for (int l = 0; l < L; ++l) {
+        int64_t len = h->list_offsets[l + 1] - h->list_offsets[l];
+        if (len < 0 || len > (1ll << 30)) return fail(BBC_ERR_FORMAT, "list %d has bad length %lld", l, (long long)len);
+        maxlen = std::max<int32_t>(maxlen, (int32_t)len);
+    }
+    {
+        std::vector<uint8_t> seen((size_t)n, 0);
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t id = h->ids[i];
+            if (id < 0 || id >= n || seen[(size_t)id]) return fail(BBC_ERR_FORMAT, "ids are not a permutation of [0, n)");
+            seen[(size_t)id] = 1;
+        }
+    }
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return fail(BBC_ERR_CUDA, "no CUDA device");
+    DeviceGuard g(device);
+    if (!g.ok) return fail(BBC_ERR_ARG, "cannot select device %d", device);
+
+    std::unique_ptr<bbc_index> ix(new bbc_index());
+    ix->device = device;
+    DevIndex& D = ix->dev;
+    D.d = d; D.nlist = L; D.metric = h->metric; D.M = M; D.bits = bits; D.K = K; D.dsub = d / M;
+    D.code_bytes = M * bits / 8;
+    D.cbp = (D.code_bytes + 15) / 16 * 16;
+    D.W = lut_row_words(M);
+    D.n = n;
+
+    // block layout
+    std::vector<int32_t> list_blk(L), list_len(L);
+    int64_t nblocks = 0;
+    for (int l = 0; l < L; ++l) {
+        list_len[l] = (int32_t)(h->list_offsets[l + 1] - h->list_offsets[l]);
+        list_blk[l] = (int32_t)nblocks;
+        nblocks += (list_len[l] + 31) / 32;
+    }
+    if (nblocks >= (1ll << 31) / 32) return fail(BBC_ERR_UNSUPPORTED, "too many blocks");
+    std::vector<uint8_t> codes((size_t)nblocks * 32 * D.cbp, 0);
+    std::vector<uint32_t> ids((size_t)nblocks * 32, kPadId);
+    const int cb = D.code_bytes;
+    std::vector<uint8_t> row(D.cbp);
+    for (int l = 0; l < L; ++l) {
+        const int64_t off = h->list_offsets[l];
+        for (int32_t p = 0; p < list_len[l]; ++p) {
+            const int64_t gb = list_blk[l] + p / 32;
+            const int t = p % 32;
+            const uint8_t* src = h->codes + (size_t)(off + p) * cb;
+            std::fill(row.begin(), row.end(), 0);
+            for (int s = 0; s < M; ++s) {
+                const int m = (s + t) % M;                       // rotated slot
+                int code;
+                if (bits == 8) code = src[m];
+                else code = (m & 1) ? (src[m >> 1] >> 4) : (src[m >> 1] & 0xF);
+                if (bits == 8) row[s] = (uint8_t)code;
+                else row[s >> 1] |= (uint8_t)((code & 0xF) << (4 * (s & 1)));
+            }
+            uint8_t* blk = codes.data() + (size_t)gb * 32 * D.cbp;
+            for (int b = 0; b < D.cbp; ++b) blk[(b / 16) * 512 + t * 16 + (b % 16)] = row[b];
+            ids[(size_t)gb * 32 + t] = (uint32_t)h->ids[off + p];
+        }
+    }
+    // centroid norms
+    std::vector<float> cnorm(L);
+    double cmax = 0.0;
+    for (int l = 0; l < L; ++l) {
+        double s = 0.0;
+        for (int i = 0; i < d; ++i) s += (double)h->centroids[(size_t)l * d + i] * h->centroids[(size_t)l * d + i];
+        cnorm[l] = (float)s;
+        cmax = std::max(cmax, std::sqrt(s));
+    }
+    D.cmax = (float)(cmax * (1.0 + 1e-6));
+    // exact u8 copy
+    bool u8 = (d % 16) == 0;
+    for (int64_t i = 0; u8 && i < n * (int64_t)d; ++i) {
+        float v = h->vectors[i];
+        if (!(v >= 0.f && v <= 255.f) || v != std::floor(v)) u8 = false;
+    }
+    int rc;
+    float* dc; float* dcn; int32_t* dlb; int32_t* dll; uint8_t* dcode; uint32_t* did; float* dbook; float* dvec;
+    unsigned int* dstat;
+    if ((rc = upload(ix.get(), h->centroids, (size_t)L * d, &dc))) return rc;
+    if ((rc = upload(ix.get(), cnorm.data(), (size_t)L, &dcn))) return rc;
+    if ((rc = upload(ix.get(), list_blk.data(), (size_t)L, &dlb))) return rc;
+    if ((rc = upload(ix.get(), list_len.data(), (size_t)L, &dll))) return rc;
+    if ((rc = upload(ix.get(), codes.data(), codes.size(), &dcode))) return rc;
+    if ((rc = upload(ix.get(), ids.data(), ids.size(), &did))) return rc;
+    if ((rc = upload(ix.get(), h->codebooks, (size_t)M * K * (d / M), &dbook))) return rc;
+    if ((rc = upload(ix.get(), h->vectors, (size_t)n * d, &dvec))) return rc;
+    unsigned int zero = 0;
+    if ((rc = upload(ix.get(), &zero, 1, &dstat))) return rc;
+    D.centroids = dc; D.cnorm = dcn; D.list_blk = dlb; D.list_len = dll; D.codes = dcode; D.ids = did;
+    D.books = dbook; D.vectors = dvec; D.status = dstat; D.vec_u8 = nullptr;
+    if (u8) {
+        std::vector<uint8_t> v8((size_t)n * d);
+        for (size_t i = 0; i < v8.size(); ++i) v8[i] = (uint8_t)h->vectors[i];
+        uint8_t* dv8;
+        if ((rc = upload(ix.get(), v8.data(), v8.size(), &dv8))) return rc;
+        D.vec_u8 = dv8;
+    }
+    // region capacity per query: the nprobe longest lists
+    std::vector<int64_t> lens(list_len.begin(), list_len.end());
+    std::sort(lens.begin(), lens.end(), std::greater<int64_t>());
+    ix->cap_prefix.assign(L + 1, 0);
+    for (int l = 0; l < L; ++l) ix->cap_prefix[l + 1] = ix->cap_prefix[l] + lens[l];
+
+    bbc_index_info_t& I = ix->info;
+    I.n = n; I.d = d; I.nlist = L; I.metric = h->metric; I.pq_m = M; I.pq_bits = bits;
+    I.max_list_len = maxlen; I.vectors_u8_exact = u8 ? 1 : 0; I.device = device;
+    *out = ix.release();
+    return BBC_OK;
+}
+
+int bbc_index_load(const char* path, int device, bbc_index** out) {
+    if (!path || !out) return fail(BBC_ERR_ARG, "null argument");
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(BBC_ERR_IO, "cannot open %s", path);
+    std::unique_ptr<FILE, int (*)(FILE*)> fc(f, fclose);
+    unsigned char hdr[64];
+    if (fread(hdr, 1, 64, f) != 64) return fail(BBC_ERR_FORMAT, "short header");
+    if (memcmp(hdr, "BBCIDX01", 8) != 0) return fail(BBC_ERR_FORMAT, "bad magic");
+    uint32_t version, quant, metric, d, nlist, pq_m, pq_bits;
+    uint64_t n;
+    memcpy(&version, hdr + 8, 4); memcpy(&quant, hdr + 12, 4); memcpy(&metric, hdr + 16, 4);
+    memcpy(&d, hdr + 20, 4); memcpy(&n, hdr + 24, 8); memcpy(&nlist, hdr + 32, 4);
+    memcpy(&pq_m, hdr + 36, 4); memcpy(&pq_bits, hdr + 40, 4);
+    if (version != 1) return fail(BBC_ERR_FORMAT, "unsupported version %u", version);
+    if (quant != BBC_QUANT_PQ) return fail(BBC_ERR_UNSUPPORTED, "quantizer %u not supported by this loader", quant);
+    if (d == 0 || d > 65536 || nlist == 0 || nlist > (1u << 24) || n == 0 || n >= 0xFFFFFFFFull ||
+        pq_m == 0 || pq_m > d || (pq_bits != 4 && pq_bits != 8))
+        return fail(BBC_ERR_FORMAT, "header fields out of range");
+    const size_t cb = (size_t)pq_m * pq_bits / 8;
+    auto rd = [&](void* dst, size_t bytes) -> bool {
+        long pos = ftell(f);
+        long pad = (64 - pos % 64) % 64;
+        if (pad && fseek(f, pad, SEEK_CUR) != 0) return false;
+        return fread(dst, 1, bytes, f) == bytes;
+    };
+    std::vector<float> cent((size_t)nlist * d);
+    std::vector<int64_t> offs(nlist + 1);
+    std::vector<int64_t> ids(n);
+    std::vector<uint8_t> codes(n * cb);
+    std::vector<float> books((size_t)pq_m * (1u << pq_bits) * (d / pq_m));
+    std::vector<float> vecs(n * d);
+    if (!rd(cent.data(), cent.size() * 4) || !rd(offs.data(), offs.size() * 8) || !rd(ids.data(), ids.size() * 8) ||
+        !rd(codes.data(), codes.size()) || !rd(books.data(), books.size() * 4) || !rd(vecs.data(), vecs.size() * 4))
+        return fail(BBC_ERR_FORMAT, "truncated index file");
+    bbc_index_host h{(int64_t)n, (int32_t)d, (int32_t)nlist, (int32_t)metric, (int32_t)pq_m, (int32_t)pq_bits,
+                     cent.data(), offs.data(), ids.data(), codes.data(), books.data(), vecs.data()};
+    return bbc_index_create(&h, device, out);
+}
+
+int bbc_index_free(bbc_index* ix) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    delete ix;
+    return BBC_OK;
+}
+
+int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out) {
+    if (!ix || !out) return fail(BBC_ERR_ARG, "null argument");
+    *out = ix->info;
+    return BBC_OK;
+}
+
+int bbc_set_param(bbc_index* ix, const char* key, double v) {
+    if (!ix || !key) return fail(BBC_ERR_ARG, "null argument");
+    std::string k(key);
+    if (k == "kc_ratio") {
+        if (!(v >= 1.0 && v <= 1e6)) return fail(BBC_ERR_ARG, "kc_ratio must be >= 1");
+        ix->kc_ratio = v;
+    } else if (k == "buckets") {
+        if (!(v >= 2 && v <= 256) || v != std::floor(v)) return fail(BBC_ERR_ARG, "buckets must be an integer in [2, 256]");
+        ix->buckets = (int)v;
+    } else if (k == "sample_lists") {
+        if (!(v >= 1 && v <= 1e6) || v != std::floor(v)) return fail(BBC_ERR_ARG, "sample_lists must be a positive integer");
+        ix->sample_lists = (int)v;
+    } else if (k == "rerank") {
+        if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "rerank must be 0 (fp32) or 1 (u8)");
+        if (v == 1 && !ix->dev.vec_u8) return fail(BBC_ERR_ARG, "no exact u8 copy for this index");
+        ix->rerank_u8 = (int)v;
+    } else if (k == "workspace_mb") {
+        if (!(v >= 1)) return fail(BBC_ERR_ARG, "workspace_mb must be >= 1");
+        ix->workspace_mb = v;
+    } else {
+        return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
+    }
+    return BBC_OK;
+}
+
+int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
+    if (!ix || !key || !v) return fail(BBC_ERR_ARG, "null argument");
+    std::string k(key);
+    if (k == "kc_ratio") *v = ix->kc_ratio;
+    else if (k == "buckets") *v = ix->buckets;
+    else if (k == "sample_lists") *v = ix->sample_lists;
+    else if (k == "rerank") *v = (ix->rerank_u8 && ix->dev.vec_u8) ? 1 : 0;
+    else if (k == "workspace_mb") *v = ix->workspace_mb;
+    else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
+    return BBC_OK;
+}
+
+int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe, int64_t* out_ids,
+               float* out_dists, void* stream) {
+    int rc = check_search_args(ix, queries, nq, k, nprobe, out_ids, out_dists);
+    if (rc) return rc;
+    const int64_t kc = kc_for(ix, k);
+    if (kc > 16384) return fail(BBC_ERR_UNSUPPORTED, "K_c=%lld above 16384 is not supported yet", (long long)kc);
+    if (nq == 0) return BBC_OK;
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan p = make_plan(ix, nq, nprobe, kc, k, false);
+    char* ws;
+    if ((rc = get_workspace(ix, st, p.total, &ws))) return rc;
+    for (int64_t q0 = 0; q0 < nq; q0 += p.chunk) {
+        const int64_t nc = std::min(p.chunk, nq - q0);
+        rc = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, out_ids + q0 * k, out_dists + q0 * k, st, 9);
+        if (rc) return rc;
+    }
+    return BBC_OK;
+}
+
+int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe, int64_t* out_ids,
+                    float* out_dists, void* stream) {
+    int rc = check_search_args(ix, queries, nq, k, nprobe, out_ids, out_dists);
+    if (rc) return rc;
+    const int64_t kc = kc_for(ix, k);
+    if (kc > 16384) return fail(BBC_ERR_UNSUPPORTED, "K_c=%lld above 16384 is not supported yet", (long long)kc);
+    if (nq == 0) return BBC_OK;
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan p = make_plan(ix, nq, nprobe, kc, k, true);
+    char* ws;
+    if ((rc = get_workspace(ix, st, p.total, &ws))) return rc;
+    const int d = ix->dev.d;
+    float* dq = reinterpret_cast<float*>(ws + p.off_q);
+    int64_t* di = reinterpret_cast<int64_t*>(ws + p.off_ids);
+    float* dd = reinterpret_cast<float*>(ws + p.off_dists);
+    for (int64_t q0 = 0; q0 < nq; q0 += p.chunk) {
+        const int64_t nc = std::min(p.chunk, nq - q0);
+        CUDA_TRY(cudaMemcpyAsync(dq, queries + q0 * d, (size_t)nc * d * 4, cudaMemcpyHostToDevice, st));
+        rc = run_chunk(ix, p, ws, dq, nc, di, dd, st, 9);
+        if (rc) return rc;
+        CUDA_TRY(cudaMemcpyAsync(out_ids + q0 * k, di, (size_t)nc * k * 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(out_dists + q0 * k, dd, (size_t)nc * k * 4, cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return BBC_OK;
+}
+
+int bbc_probe(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe, int32_t* out_lists, void* stream) {
+    int rc = check_search_args(ix, queries, nq, 1, nprobe, out_lists, out_lists);
+    if (rc) return rc;
+    if (nq == 0) return BBC_OK;
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan p = make_plan(ix, nq, nprobe, 1, 1, false);
+    char* ws;
+    if ((rc = get_workspace(ix, st, p.total, &ws))) return rc;
+    for (int64_t q0 = 0; q0 < nq; q0 += p.chunk) {
+        const int64_t nc = std::min(p.chunk, nq - q0);
+        rc = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, nullptr, nullptr, st, 2,
+                       out_lists + q0 * nprobe);
+        if (rc) return rc;
+    }
+    return BBC_OK;
+}
+
+int bbc_lut(bbc_index* ix, const float* queries, int64_t nq, uint16_t* out_lut16, void* stream) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    if (nq < 0 || (nq > 0 && (!queries || !out_lut16))) return fail(BBC_ERR_ARG, "bad buffers");
+    if (nq == 0) return BBC_OK;
+    DeviceGuard g(ix->device);
+    CUDA_TRY(launch_lut16(ix->dev, queries, nq, out_lut16, (cudaStream_t)stream));
+    return BBC_OK;
+}
+
+int bbc_collect(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe, const int32_t* probe_lists,
+                int64_t kc, uint32_t* out_ids, int64_t* out_count, bbc_collector_state* out_state, void* stream) {
+    int rc = check_search_args(ix, queries, nq, 1, nprobe, out_ids, out_count);
+    if (rc) return rc;
+    if (nq > 0 && !probe_lists) return fail(BBC_ERR_ARG, "null probe_lists");
+    if (kc < 1) return fail(BBC_ERR_ARG, "kc must be >= 1");
+    if (kc > (int64_t)0x7FFFFFFF) return fail(BBC_ERR_ARG, "kc too large");
+    if (nq == 0) return BBC_OK;
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan p = make_plan(ix, nq, nprobe, kc, 1, false);
+    char* ws;
+    if ((rc = get_workspace(ix, st, p.total, &ws))) return rc;
+    for (int64_t q0 = 0; q0 < nq; q0 += p.chunk) {
+        const int64_t nc = std::min(p.chunk, nq - q0);
+        rc = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, nullptr, nullptr, st, 7, nullptr,
+                       probe_lists + q0 * nprobe, out_ids + q0 * kc, out_count + q0,
+                       out_state ? out_state + q0 : nullptr);
+        if (rc) return rc;
+    }
+    return BBC_OK;
+}
+
+int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint32_t* cand_ids,
+                    const int64_t* cand_count, int64_t kc, int32_t k, int64_t* out_ids, float* out_dists,
+                    void* stream) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    if (nq < 0 || k < 1 || kc < 1) return fail(BBC_ERR_ARG, "bad sizes");
+    if (nq > 0 && (!queries || !cand_ids || !cand_count || !out_ids || !out_dists)) return fail(BBC_ERR_ARG, "null buffer");
+    if (kc > 16384) return fail(BBC_ERR_UNSUPPORTED, "kc above 16384 is not supported yet");
+    if (nq == 0) return BBC_OK;
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // cdist scratch: kc floats per query, in chunks
+    const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
+    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(budget / ((size_t)kc * 4 + 256))));
+    char* ws;
+    int rc = get_workspace(ix, st, align_up((size_t)chunk * kc * 4), &ws);
+    if (rc) return rc;
+    const int d = ix->dev.d;
+    for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+        const int64_t nc = std::min(chunk, nq - q0);
+        RerankArgs ra{queries + q0 * d, cand_ids + q0 * kc, cand_count + q0, kc,
+                      ix->rerank_u8 && ix->dev.vec_u8 != nullptr, reinterpret_cast<float*>(ws), k,
+                      out_ids + q0 * k, out_dists + q0 * k, nullptr};
+        CUDA_TRY(launch_rerank(ix->dev, nc, ra, st));
+        CUDA_TRY(launch_topk(ix->dev, nc, ra, st));
+    }
+    return BBC_OK;
+}
+
+int bbc_stream_status(bbc_index* ix, void* stream) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    DeviceGuard g(ix->device);
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned int s = 0;
+    CUDA_TRY(cudaMemcpy(&s, ix->dev.status, 4, cudaMemcpyDeviceToHost));
+    if (s) {
+        unsigned int z = 0;
+        CUDA_TRY(cudaMemcpy(ix->dev.status, &z, 4, cudaMemcpyHostToDevice));
+        return fail(BBC_ERR_CAPACITY, "device status 0x%x (1 region, 2 select, 4 top-k overrun)", s);
+    }
+    return BBC_OK;
+}
+
+}  // extern "C"

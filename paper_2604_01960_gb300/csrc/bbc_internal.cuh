@@ -1,0 +1,117 @@
+// Internal declarations shared by the CUDA translation units of libbbc.
+//
+// Device data layout of an IVF-PQ index (all resident in HBM):
+//   centroids  f32 [nlist][d]          probe operand (row-major)
+//   cnorm      f32 [nlist]             ||c_l||^2 for the probe epilogue
+//   list_blk   i32 [nlist]             first 32-vector block of list l
+//   list_len   i32 [nlist]             vectors in list l
+//   codes      u8  [nblocks][CBP/16][32][16]
+//              one block = 32 consecutive list positions ("lanes"); the code
+//              row of lane t is split in 16-byte chunks, chunk c of all 32
+//              lanes contiguous, so a warp reads each chunk with one fully
+//              coalesced 512-byte access.  Inside a row, code slot s of lane t
+//              holds sub-space (s + t) mod M (rotated rows), which makes the
+//              shared-memory lookup-table reads of a warp bank-conflict free.
+//   ids        u32 [nblocks*32]        vector id per position, 0xFFFFFFFF = pad
+//   books      f32 [M][K][d/M]         PQ codebooks
+//   vectors    f32 [n][d]              by id, for the exact re-rank
+//   vec_u8     u8  [n][d]              exact copy when all components are
+//                                      integers in [0,255] (else null)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bbc.h"
+
+namespace bbc {
+
+constexpr int kLanes = 32;                 // vectors per code block (one per lane)
+constexpr uint32_t kPadId = 0xFFFFFFFFu;   // id of padding slots in a block
+constexpr int kMaxBuckets = 256;
+
+// Status bits latched in the index's device status word.
+constexpr unsigned kStatusRegionOverrun = 1u;
+constexpr unsigned kStatusSelectOverrun = 2u;
+constexpr unsigned kStatusTopkOverrun = 4u;
+
+struct DevIndex {
+    int d, nlist, metric, M, bits, K, dsub;
+    int code_bytes;      // bytes of one canonical code row
+    int cbp;             // code row bytes padded to a multiple of 16
+    int W;               // words per row of the shared-memory LUT
+    int64_t n;
+    float cmax;          // max_l ||c_l||_2
+    const float* centroids;
+    const float* cnorm;
+    const int32_t* list_blk;
+    const int32_t* list_len;
+    const uint8_t* codes;
+    const uint32_t* ids;
+    const float* books;
+    const float* vectors;
+    const uint8_t* vec_u8;
+    unsigned int* status;
+};
+
+// Words per LUT row in shared memory: lane t at code slot s reads word t + s
+// of the row of its code value, so a row needs M + 31 words; rounding to a
+// multiple of 32 keeps bank(t, s) = (t + s) mod 32 for every row.
+inline int lut_row_words(int M) { return M <= 32 ? 64 : M + 32; }
+
+// ---- launchers (one per translation unit) ----
+
+// S1: approximate probe scores a[q][l] = ||c_l||^2 - 2<q,c_l> (L2) or -<q,c_l> (IP).
+cudaError_t launch_probe_scores(const DevIndex& ix, const float* q, int64_t nq, float* scores,
+                                cudaStream_t st);
+// S2: exact probe selection with FP64 re-score of every list whose score
+// can reach the nprobe-th.  scores from launch_probe_scores.
+cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, int nprobe,
+                                const float* scores, int32_t* lists, cudaStream_t st);
+// S3: uint16 PQ lookup tables [nq][M][K].
+cudaError_t launch_lut16(const DevIndex& ix, const float* q, int64_t nq, uint16_t* lut16,
+                         cudaStream_t st);
+
+struct ScanArgs {
+    const uint16_t* lut16;        // [nq][M][K]
+    const int32_t* lists;         // [nq][nprobe]
+    int nprobe;
+    int64_t kc;
+    int m;                        // buckets
+    int sample_min;               // minimum sampled lists
+    uint2* region;                // [nq][cap] (e, id)
+    int64_t cap;
+    bbc_collector_state* state;   // [nq]
+};
+// S4-S6: sample + codebook + scan + push/update, one CTA per query.
+cudaError_t launch_scan(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st);
+
+struct SelectArgs {
+    const uint2* region;
+    int64_t cap;
+    bbc_collector_state* state;
+    int64_t kc;
+    uint32_t* cand;               // [nq][kc]
+    int64_t* cand_count;          // [nq]
+    uint2* spill;                 // [nq][cap] scratch for large threshold buckets
+};
+// S7: exact threshold bucket, compaction, top-s of the threshold bucket.
+cudaError_t launch_select(const DevIndex& ix, int64_t nq, const SelectArgs& a, cudaStream_t st);
+
+struct RerankArgs {
+    const float* q;               // [nq][d]
+    const uint32_t* cand;         // [nq][kc]
+    const int64_t* cand_count;    // [nq]
+    int64_t kc;
+    int use_u8;
+    float* cdist;                 // [nq][kc]
+    int k;
+    int64_t* out_ids;             // [nq][k]
+    float* out_dists;             // [nq][k]
+    unsigned long long* keys;     // [nq][kc] scratch for the final top-k
+};
+// S8: exact distances of the candidates; S9: k smallest (dist, id), sorted.
+cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
+cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
+
+}  // namespace bbc

@@ -1,0 +1,389 @@
+// S4-S6: quantised-distance scan of the probed lists fused with the
+// bucket-based result buffer (Section 3.2, Algorithm 1), one CTA per query.
+//
+// Phase A  stage the query's uint16 lookup table in shared memory and lay out
+//          its probed lists (nearest first) as a sequence of 32-vector blocks.
+// Phase B  sample: scan the first lists in probe order -- at least
+//          min(sample_min, nprobe) of them, extended until they hold
+//          min(K_c, S_q) vectors -- and append every (estimated distance, id)
+//          to the query's region (threshold = infinity, Algorithm 1 line 13).
+// Phase C  codebook (Section 3.2, "Codebook Generation Based on Estimated
+//          Distance"): d_min = smallest, d_max = t-th smallest sampled
+//          distance with t = min(K_c, sample size); n_ew = 256 equal-width
+//          bins of width 2^sh over [d_min, d_max]; bin(e) = clamp((e - d_min)
+//          >> sh, 0, 255) (Eq. remap); an equal-depth remap map[256] -> [0, m)
+//          from the bins' cumulative counts; bucket counts of the sample and
+//          the threshold bucket tau (Update, Algorithm 1 lines 5-11: first
+//          bucket whose running count reaches K_c).
+// Phase D  scan the remaining lists: per vector, estimated distance
+//          e = sum_m LUT[m][code_m], bucket a = map[bin(e)], and Push
+//          (Algorithm 1 lines 1-4): append (e, id) and count it when a <= tau.
+//          Warps refresh tau from the shared bucket counts after every chunk
+//          (the paper updates once per cluster; tau only moves down, and a
+//          stale tau only admits extra objects, never drops a needed one).
+// The final selection (Algorithm 1 lines 19-23) runs in k_select.cu.
+//
+// GPU mapping: one lane per vector; the lane's code row sits in registers
+// (coalesced 512-byte chunk loads); each LUT read goes to bank (lane + slot)
+// mod 32, so the 32 reads of a warp never conflict.  Appends are warp-
+// aggregated (ballot + one shared atomic per warp) into a contiguous region.
+#include <climits>
+
+#include "bbc_internal.cuh"
+#include "dev_util.cuh"
+
+namespace bbc {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_CHUNK = 4;      // consecutive blocks per warp step
+
+template <int M, int BITS>
+struct ScanCfg {
+    static constexpr int K = 1 << BITS;
+    static constexpr int W = M <= 32 ? 64 : M + 32;
+    static constexpr int CB = M * BITS / 8;
+    static constexpr int CBP = (CB + 15) / 16 * 16;
+    static constexpr int NCH = CBP / 16;
+    static constexpr int LUT_WORDS = K * W;
+};
+
+template <int M, int BITS>
+__device__ __forceinline__ uint32_t adc_lane(const uint4 (&r)[ScanCfg<M, BITS>::NCH], const uint32_t* lutl) {
+    using C = ScanCfg<M, BITS>;
+    uint32_t e = 0;
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        uint32_t code;
+        if (BITS == 8) {
+            const uint4 v = r[s >> 4];
+            const int wi = (s >> 2) & 3;
+            const uint32_t w = wi == 0 ? v.x : (wi == 1 ? v.y : (wi == 2 ? v.z : v.w));
+            code = (w >> (8 * (s & 3))) & 0xFFu;
+        } else {
+            const int byte = s >> 1;
+            const uint4 v = r[byte >> 4];
+            const int wi = (byte >> 2) & 3;
+            const uint32_t w = wi == 0 ? v.x : (wi == 1 ? v.y : (wi == 2 ? v.z : v.w));
+            code = (w >> (8 * (byte & 3) + 4 * (s & 1))) & 0xFu;
+        }
+        e += lutl[code * C::W + s];
+    }
+    return e;
+}
+
+// Update on the shared bucket counts by one warp: first bucket whose running
+// count reaches kc, or m.
+__device__ __forceinline__ uint32_t warp_update(const uint32_t* hist, int m, int64_t kc) {
+    const unsigned ln = lane_id();
+    uint32_t h[8];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int b = (int)ln * 8 + i;
+        h[i] = b < m ? *(volatile const uint32_t*)&hist[b] : 0u;
+        s += h[i];
+    }
+    unsigned long long inc = warp_incl_scan64(s);
+    unsigned hit = __ballot_sync(0xFFFFFFFFu, inc >= (unsigned long long)kc);
+    if (!hit) return (uint32_t)m;
+    unsigned src = __ffs(hit) - 1;
+    uint32_t bk = 0;
+    if (ln == src) {
+        unsigned long long c = inc - s;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            c += h[i];
+            if (c >= (unsigned long long)kc) { bk = ln * 8 + i; break; }
+        }
+    }
+    return __shfl_sync(0xFFFFFFFFu, bk, src);
+}
+
+__device__ __forceinline__ uint32_t bin_of(uint32_t e, uint32_t dmin, int sh) {
+    if (e <= dmin) return 0u;
+    uint32_t b = (e - dmin) >> sh;
+    return b > 255u ? 255u : b;
+}
+
+struct ScanShared {
+    uint32_t hist[kMaxBuckets];
+    uint32_t ehist[256];
+    uint8_t bmap[256];
+    uint32_t sc[2];
+    uint32_t count;
+    uint32_t dmin, dmax;
+    uint32_t tau;
+    int sh;
+    int nsl;
+    long long sq;
+};
+
+template <int M, int BITS, bool MAIN>
+__device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& a, int64_t qi,
+                                            int g0, int g1, const uint32_t* lut, const int32_t* lpre,
+                                            const int32_t* lblk, const int32_t* llen, ScanShared& S) {
+    using C = ScanCfg<M, BITS>;
+    const int P = a.nprobe;
+    const unsigned ln = lane_id();
+    const int nw = blockDim.x >> 5;
+    const uint32_t* lutl = lut + ln;
+    uint2* region = a.region + qi * a.cap;
+    const unsigned lt_mask = (1u << ln) - 1u;
+    for (int cb = g0 + (int)warp_id() * SCAN_CHUNK; cb < g1; cb += nw * SCAN_CHUNK) {
+        const int ge = min(cb + SCAN_CHUNK, g1);
+        // list holding block cb: largest j with lpre[j] <= cb
+        int lo = 0, hi = P - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (lpre[mid] <= cb) lo = mid; else hi = mid - 1;
+        }
+        int j = lo;
+        int gbk[SCAN_CHUNK], nval[SCAN_CHUNK];
+        uint4 r[SCAN_CHUNK][C::NCH];
+#pragma unroll
+        for (int u = 0; u < SCAN_CHUNK; ++u) {
+            const int g = cb + u;
+            gbk[u] = -1;
+            nval[u] = 0;
+            if (g < ge) {
+                while (g >= lpre[j + 1]) ++j;
+                const int b = g - lpre[j];
+                gbk[u] = lblk[j] + b;
+                nval[u] = min(32, llen[j] - 32 * b);
+                const uint4* cp = reinterpret_cast<const uint4*>(ix.codes + (size_t)gbk[u] * 32 * C::CBP) + ln;
+#pragma unroll
+                for (int c = 0; c < C::NCH; ++c) r[u][c] = __ldg(cp + c * 32);
+            }
+        }
+        const uint32_t tau = MAIN ? *(volatile uint32_t*)&S.tau : 0u;
+        const uint32_t dmin = S.dmin;
+        const int sh = S.sh;
+#pragma unroll
+        for (int u = 0; u < SCAN_CHUNK; ++u) {
+            if (gbk[u] < 0) continue;
+            const uint32_t e = adc_lane<M, BITS>(r[u], lutl);
+            const bool valid = (int)ln < nval[u];
+            bool push;
+            uint32_t bk = 0;
+            if (MAIN) {
+                bk = S.bmap[bin_of(e, dmin, sh)];
+                push = valid && bk <= tau;
+            } else {
+                push = valid;
+                const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, valid ? e : 0xFFFFFFFFu);
+                if (ln == 0 && mn != 0xFFFFFFFFu) atomicMin(&S.dmin, mn);
+            }
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, push);
+            if (bal) {
+                uint32_t base = 0;
+                if (ln == 0) base = atomicAdd(&S.count, (uint32_t)__popc(bal));
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (push) {
+                    const uint32_t pos = base + (uint32_t)__popc(bal & lt_mask);
+                    const uint32_t id = __ldg(ix.ids + (size_t)gbk[u] * 32 + ln);
+                    if ((int64_t)pos < a.cap) region[pos] = make_uint2(e, id);
+                    else atomicOr(ix.status, kStatusRegionOverrun);
+                    if (MAIN) atomicAdd(&S.hist[bk], 1u);
+                }
+            }
+        }
+        if (MAIN) {
+            const uint32_t t = warp_update(S.hist, a.m, a.kc);
+            if (ln == 0 && t < *(volatile uint32_t*)&S.tau) atomicMin(&S.tau, t);
+        }
+    }
+}
+
+template <int M, int BITS>
+__global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(DevIndex ix, ScanArgs a) {
+    using C = ScanCfg<M, BITS>;
+    extern __shared__ uint4 dsm[];
+    uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
+    const int P = a.nprobe;
+    int32_t* lpre = reinterpret_cast<int32_t*>(lut + C::LUT_WORDS);   // [P+1]
+    int32_t* lblk = lpre + (P + 1);                                    // [P]
+    int32_t* llen = lblk + P;                                          // [P]
+    __shared__ ScanShared S;
+    const int64_t qi = blockIdx.x;
+    const int tid = threadIdx.x, bs = blockDim.x;
+
+    // ---- Phase A: LUT staging and list layout ----
+    const uint16_t* lq = a.lut16 + qi * (int64_t)M * C::K;
+    for (int w = tid; w < C::LUT_WORDS; w += bs) {
+        const int jj = w / C::W, c = w - jj * C::W;
+        lut[w] = lq[(c % M) * C::K + jj];
+    }
+    for (int i = tid; i < kMaxBuckets; i += bs) S.hist[i] = 0;
+    if (tid == 0) {
+        S.count = 0;
+        S.dmin = 0xFFFFFFFFu;
+        S.tau = (uint32_t)a.m;
+        S.sh = 0;
+    }
+    if (warp_id() == 0) {
+        const unsigned ln = lane_id();
+        int carry = 0;
+        long long carryv = 0;
+        for (int base = 0; base < P; base += 32) {
+            const int j = base + (int)ln;
+            int nb = 0, nv = 0;
+            if (j < P) {
+                const int l = a.lists[qi * P + j];
+                nv = ix.list_len[l];
+                nb = (nv + 31) >> 5;
+                lblk[j] = ix.list_blk[l];
+                llen[j] = nv;
+            }
+            const uint32_t inc = warp_incl_scan((uint32_t)nb);
+            const unsigned long long incv = warp_incl_scan64((unsigned long long)nv);
+            if (j < P) lpre[j + 1] = carry + (int)inc;
+            carry += (int)__shfl_sync(0xFFFFFFFFu, inc, 31);
+            carryv += (long long)__shfl_sync(0xFFFFFFFFu, incv, 31);
+        }
+        if (ln == 0) lpre[0] = 0;
+        // sample lists: at least min(sample_min, P), extended until min(K_c, S_q) vectors
+        const long long want = a.kc < carryv ? a.kc : carryv;
+        const int smin = a.sample_min < P ? a.sample_min : P;
+        long long cum = 0;
+        int nsl = P;
+        for (int base = 0; base < P; base += 32) {
+            const int j = base + (int)ln;
+            const int nv = j < P ? llen[j] : 0;
+            const unsigned long long incv = warp_incl_scan64((unsigned long long)nv);
+            const bool ok = j < P && (j + 1) >= smin && (long long)(cum + (long long)incv) >= want;
+            const unsigned hit = __ballot_sync(0xFFFFFFFFu, ok);
+            if (hit) { nsl = base + (int)(__ffs(hit) - 1) + 1; break; }
+            cum += (long long)__shfl_sync(0xFFFFFFFFu, incv, 31);
+        }
+        if (ln == 0) {
+            S.nsl = nsl;
+            S.sq = carryv;
+        }
+    }
+    __syncthreads();
+
+    // ---- Phase B: sample ----
+    const int gs = lpre[S.nsl];
+    scan_blocks<M, BITS, false>(ix, a, qi, 0, gs, lut, lpre, lblk, llen, S);
+    __syncthreads();
+
+    // ---- Phase C: codebook ----
+    const uint2* region = a.region + qi * a.cap;
+    const int64_t ns = (int64_t)min((long long)S.count, (long long)a.cap);
+    if (ns > 0) {
+        const int64_t t = ns < a.kc ? ns : a.kc;
+        const uint32_t dmax = cta_select_u32(ns, (uint32_t)(t - 1), [&](int64_t i) { return region[i].x; },
+                                             S.ehist, S.sc, 16);
+        if (tid == 0) {
+            S.dmax = dmax;
+            int sh = 0;
+            while (((dmax - S.dmin) >> sh) > 255u) ++sh;
+            S.sh = sh;
+        }
+        for (int i = tid; i < 256; i += bs) S.ehist[i] = 0;
+        __syncthreads();
+        const uint32_t dmin = S.dmin;
+        const int sh = S.sh;
+        for (int64_t i = tid; i < ns; i += bs) {
+            const uint32_t e = region[i].x;
+            if (e <= dmax) atomicAdd(&S.ehist[bin_of(e, dmin, sh)], 1u);
+        }
+        __syncthreads();
+        if (warp_id() == 0) {
+            const unsigned ln = lane_id();
+            uint32_t h[8], s = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { h[i] = S.ehist[ln * 8 + i]; s += h[i]; }
+            const unsigned long long inc = warp_incl_scan64(s);
+            const unsigned long long T = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            unsigned long long cum = inc - s;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                unsigned long long v = T ? ((unsigned long long)a.m * cum) / T : 0ull;
+                S.bmap[ln * 8 + i] = (uint8_t)(v > (unsigned long long)(a.m - 1) ? a.m - 1 : v);
+                cum += h[i];
+            }
+        }
+        __syncthreads();
+        for (int64_t i = tid; i < ns; i += bs) atomicAdd(&S.hist[S.bmap[bin_of(region[i].x, dmin, sh)]], 1u);
+        __syncthreads();
+        if (warp_id() == 0) {
+            const uint32_t t0 = warp_update(S.hist, a.m, a.kc);
+            if (lane_id() == 0) S.tau = t0;
+        }
+    } else {
+        if (tid == 0) { S.dmin = 0; S.dmax = 0; S.sh = 0; }
+        for (int i = tid; i < 256; i += bs) S.bmap[i] = 0;
+    }
+    __syncthreads();
+
+    // ---- Phase D: main scan ----
+    scan_blocks<M, BITS, true>(ix, a, qi, gs, lpre[P], lut, lpre, lblk, llen, S);
+    __syncthreads();
+
+    // ---- state out ----
+    bbc_collector_state* st = a.state + qi;
+    for (int i = tid; i < kMaxBuckets; i += bs) st->hist[i] = i < a.m ? S.hist[i] : 0u;
+    for (int i = tid; i < 256; i += bs) st->map[i] = S.bmap[i];
+    if (warp_id() == 0) {
+        const uint32_t t1 = warp_update(S.hist, a.m, a.kc);
+        if (lane_id() == 0) {
+            st->d_min = S.dmin;
+            st->d_max = S.dmax;
+            st->sh = S.sh;
+            st->m = a.m;
+            st->sample_lists = S.nsl;
+            st->tau = (int32_t)t1;
+            st->sample_size = ns;
+            st->scanned = S.sq;
+            st->pushed = (int64_t)S.count;
+            st->below = 0;
+            st->kc = a.kc;
+        }
+    }
+}
+
+template <int M, int BITS>
+static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st) {
+    using C = ScanCfg<M, BITS>;
+    const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)(3 * a.nprobe + 1) * 4;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(scan_kernel<M, BITS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    scan_kernel<M, BITS><<<(unsigned)nq, SCAN_THREADS, smem, st>>>(ix, a);
+    return cudaGetLastError();
+}
+
+bool scan_supported(int M, int bits) {
+    if (bits == 8) return M == 8 || M == 16 || M == 32 || M == 64 || M == 96 || M == 128;
+    if (bits == 4) return M == 32 || M == 64 || M == 128;
+    return false;
+}
+
+cudaError_t launch_scan(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    if (ix.bits == 8) {
+        switch (ix.M) {
+            case 8: return launch_scan_t<8, 8>(ix, nq, a, st);
+            case 16: return launch_scan_t<16, 8>(ix, nq, a, st);
+            case 32: return launch_scan_t<32, 8>(ix, nq, a, st);
+            case 64: return launch_scan_t<64, 8>(ix, nq, a, st);
+            case 96: return launch_scan_t<96, 8>(ix, nq, a, st);
+            case 128: return launch_scan_t<128, 8>(ix, nq, a, st);
+        }
+    } else if (ix.bits == 4) {
+        switch (ix.M) {
+            case 32: return launch_scan_t<32, 4>(ix, nq, a, st);
+            case 64: return launch_scan_t<64, 4>(ix, nq, a, st);
+            case 128: return launch_scan_t<128, 4>(ix, nq, a, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace bbc

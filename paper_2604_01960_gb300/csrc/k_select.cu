@@ -1,0 +1,178 @@
+// S7: final collection (Algorithm 1, lines 19-23), one CTA per query.
+//
+// The bucket counts of the appended objects give the exact threshold bucket
+// tau* = first bucket whose running count reaches K_c (Update on the final
+// buffer).  Every object whose bucket is below tau* is a candidate (buckets
+// are ordered by distance range, so they all precede the K_c-th); the
+// remaining s = K_c - below candidates are the s smallest (e, id) of bucket
+// tau*, found by a radix select on the 64-bit key (e << 32 | id).  When fewer
+// than K_c objects were scanned, all of them are candidates.
+//
+// Why this is the exact top-K_c by (e, id): bucket ids are a monotone
+// function of e, and an object is dropped during the scan only when its
+// bucket exceeds the current tau, which never falls below tau*; so every
+// object in buckets <= tau* was appended.
+#include "bbc_internal.cuh"
+#include "dev_util.cuh"
+
+namespace bbc {
+
+constexpr int SELK_THREADS = 512;
+constexpr int SELK_TCAP = 12288;   // threshold-bucket objects held in shared memory
+
+__device__ __forceinline__ uint32_t sel_bucket(uint32_t e, const bbc_collector_state& st, const uint8_t* map) {
+    uint32_t b = 0;
+    if (e > st.d_min) {
+        b = (e - st.d_min) >> st.sh;
+        b = b > 255u ? 255u : b;
+    }
+    return map[b];
+}
+
+__global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, SelectArgs a) {
+    extern __shared__ unsigned long long tkeys[];      // [SELK_TCAP]
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t sc[2];
+    __shared__ uint8_t map[256];
+    __shared__ uint32_t s_out, s_t;
+    __shared__ int s_tau;
+    __shared__ long long s_below;
+    const int64_t qi = blockIdx.x;
+    bbc_collector_state& st = a.state[qi];
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int m = st.m;
+    const int64_t n = st.pushed < a.cap ? st.pushed : a.cap;
+    const uint2* region = a.region + qi * a.cap;
+    uint32_t* cand = a.cand + qi * a.kc;
+    for (int i = tid; i < 256; i += bs) map[i] = st.map[i];
+    if (warp_id() == 0) {
+        // tau* and the count below it
+        const unsigned ln = lane_id();
+        uint32_t h[8], s = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int b = (int)ln * 8 + i;
+            h[i] = b < m ? st.hist[b] : 0u;
+            s += h[i];
+        }
+        const unsigned long long inc = warp_incl_scan64(s);
+        const unsigned hit = __ballot_sync(0xFFFFFFFFu, inc >= (unsigned long long)a.kc);
+        if (!hit) {
+            if (ln == 0) { s_tau = m; s_below = (long long)n; }
+        } else {
+            const unsigned src = __ffs(hit) - 1;
+            if (ln == src) {
+                unsigned long long c = inc - s;
+                for (int i = 0; i < 8; ++i) {
+                    if (c + h[i] >= (unsigned long long)a.kc) { s_tau = (int)(ln * 8 + i); s_below = (long long)c; break; }
+                    c += h[i];
+                }
+            }
+        }
+        if (ln == 0) { s_out = 0; s_t = 0; }
+    }
+    __syncthreads();
+    const int tau = s_tau;
+    const long long below = s_below;
+    const unsigned ln = lane_id();
+    const unsigned lt_mask = (1u << ln) - 1u;
+    if (tau >= m) {
+        // fewer than K_c objects: all appended objects are candidates
+        for (int64_t i = tid; i < n; i += bs) cand[i] = region[i].y;
+        if (tid == 0) {
+            a.cand_count[qi] = n;
+            st.tau = tau;
+            st.below = n;
+        }
+        return;
+    }
+    const uint32_t nt = st.hist[tau];
+    const bool in_smem = nt <= (uint32_t)SELK_TCAP;
+    // pass 1: buckets < tau* go straight out; bucket tau* is staged
+    for (int64_t i0 = 0; i0 < n; i0 += bs) {
+        const int64_t i = i0 + tid;
+        uint2 v = make_uint2(0, 0);
+        uint32_t b = 0xFFFFFFFFu;
+        if (i < n) {
+            v = region[i];
+            b = sel_bucket(v.x, st, map);
+        }
+        const bool take = b < (uint32_t)tau;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
+        if (bal) {
+            uint32_t base = 0;
+            if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (take) cand[base + __popc(bal & lt_mask)] = v.y;
+        }
+        if (in_smem && b == (uint32_t)tau) {
+            const uint32_t p = atomicAdd(&s_t, 1u);
+            if (p < (uint32_t)SELK_TCAP) tkeys[p] = ((unsigned long long)v.x << 32) | v.y;
+        }
+    }
+    __syncthreads();
+    const uint32_t s = (uint32_t)(a.kc - below);
+    unsigned long long kth;
+    if (in_smem) {
+        const uint32_t cnt = min(s_t, (uint32_t)SELK_TCAP);
+        kth = cta_select_u64(cnt, s - 1, [&](int64_t i) { return tkeys[i]; }, hist, sc, 56);
+        for (uint32_t i0 = 0; i0 < cnt; i0 += bs) {
+            const uint32_t i = i0 + tid;
+            const bool take = i < cnt && tkeys[i] <= kth;
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
+            if (bal) {
+                uint32_t base = 0;
+                if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (take) cand[base + __popc(bal & lt_mask)] = (uint32_t)(tkeys[i] & 0xFFFFFFFFu);
+            }
+        }
+    } else {
+        // large threshold bucket: select straight from the region (read-only passes)
+        kth = cta_select_u64(n, s - 1, [&](int64_t i) {
+            const uint2 v = region[i];
+            return sel_bucket(v.x, st, map) == (uint32_t)tau ? (((unsigned long long)v.x << 32) | v.y) : ~0ull;
+        }, hist, sc, 56);
+        for (int64_t i0 = 0; i0 < n; i0 += bs) {
+            const int64_t i = i0 + tid;
+            bool take = false;
+            uint32_t id = 0;
+            if (i < n) {
+                const uint2 v = region[i];
+                take = sel_bucket(v.x, st, map) == (uint32_t)tau &&
+                       (((unsigned long long)v.x << 32) | v.y) <= kth;
+                id = v.y;
+            }
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
+            if (bal) {
+                uint32_t base = 0;
+                if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (take) cand[base + __popc(bal & lt_mask)] = id;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if ((int64_t)s_out != a.kc) atomicOr(ix.status, kStatusSelectOverrun);
+        a.cand_count[qi] = a.kc;
+        st.tau = tau;
+        st.below = below;
+    }
+}
+
+cudaError_t launch_select(const DevIndex& ix, int64_t nq, const SelectArgs& a, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    const size_t smem = (size_t)SELK_TCAP * 8;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    select_kernel<<<(unsigned)nq, SELK_THREADS, smem, st>>>(ix, a);
+    return cudaGetLastError();
+}
+
+}  // namespace bbc

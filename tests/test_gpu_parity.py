@@ -1,0 +1,252 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Integer work (probe lists, uint16 tables, estimated distances, candidate sets,
+collector state) must match bit for bit.  Re-rank distances are FP32 and
+must lie within 1e-5 relative of the FP64 oracle; result ids may differ only
+among objects whose exact distances tie with the k-th within that tolerance.
+For integer-valued data the FP32 distances are exact, so results match bit
+for bit end to end.
+"""
+
+import numpy as np
+import pytest
+
+from conftest import scanned_set, small_workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def bbc():
+    import paper_2604_01960_gb300 as bbc
+    bbc.build()
+    assert torch.cuda.is_available(), "CUDA device required"
+    return bbc
+
+
+_IDX = {}
+
+
+def dev_index(bbc, kind):
+    if kind not in _IDX:
+        idx, q = small_workload(kind)
+        h = bbc.bbc_index_create(idx, 0)
+        _IDX[kind] = (h, idx, q)
+    return _IDX[kind]
+
+
+def cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to("cuda") if dtype is None else t.to("cuda", dtype)
+
+
+def sync_ok(bbc, h):
+    torch.cuda.synchronize()
+    bbc.bbc_stream_status(h)
+
+
+KINDS = ["tiny", "sift", "sift4", "embed", "ragged"]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_lut16_bit_exact(bbc, oracle_lib, kind):
+    h, idx, q = dev_index(bbc, kind)
+    nq = len(q)
+    K = 1 << idx.pq_bits
+    out = torch.empty((nq, idx.pq_m, K), dtype=torch.int16, device="cuda")
+    bbc.bbc_lut(h, cuda(q), nq, out)
+    sync_ok(bbc, h)
+    got = out.cpu().numpy().view(np.uint16)
+    for i in range(nq):
+        ref = oracle_lib.lut16(q[i], idx.codebooks, idx.metric)
+        assert np.array_equal(got[i], ref), f"query {i}"
+
+
+@pytest.mark.parametrize("kind,nprobe", [("tiny", 1), ("tiny", 13), ("sift", 32), ("embed", 48),
+                                         ("ragged", 40), ("sift4", 64)])
+def test_probe_exact_order(bbc, oracle_lib, kind, nprobe):
+    h, idx, q = dev_index(bbc, kind)
+    nq = len(q)
+    out = torch.empty((nq, nprobe), dtype=torch.int32, device="cuda")
+    bbc.bbc_probe(h, cuda(q), nq, nprobe, out)
+    sync_ok(bbc, h)
+    got = out.cpu().numpy()
+    for i in range(nq):
+        ref, _ = oracle_lib.probe(q[i], idx.centroids, nprobe, idx.metric)
+        assert np.array_equal(got[i], ref), f"query {i}"
+
+
+def _collect(bbc, h, idx, q, nprobe, kc):
+    nq = len(q)
+    qd = cuda(q)
+    lists = torch.empty((nq, nprobe), dtype=torch.int32, device="cuda")
+    bbc.bbc_probe(h, qd, nq, nprobe, lists)
+    ids = torch.full((nq, kc), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(nq, dtype=torch.int64, device="cuda")
+    st = torch.empty(nq * bbc.STATE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    bbc.bbc_collect(h, qd, nq, nprobe, lists, kc, ids, cnt, st)
+    sync_ok(bbc, h)
+    state = st.cpu().numpy().view(bbc.STATE_DTYPE)
+    return lists.cpu().numpy(), ids.cpu().numpy().view(np.uint32), cnt.cpu().numpy(), state
+
+
+@pytest.mark.parametrize("kind,nprobe,kc,m,smin", [
+    ("tiny", 12, 300, 64, 8), ("tiny", 48, 5000, 32, 8), ("sift", 16, 900, 64, 8),
+    ("sift4", 20, 1200, 256, 4), ("embed", 10, 400, 2, 8), ("ragged", 40, 300, 16, 3),
+    ("ragged", 2, 1000, 64, 8), ("sift", 64, 12000, 64, 8), ("tiny", 5, 1, 64, 8)])
+def test_collect_candidates_and_state(bbc, oracle_lib, kind, nprobe, kc, m, smin):
+    h, idx, q = dev_index(bbc, kind)
+    bbc.bbc_set_param(h, "buckets", m)
+    bbc.bbc_set_param(h, "sample_lists", smin)
+    try:
+        lists, ids, cnt, state = _collect(bbc, h, idx, q, nprobe, kc)
+    finally:
+        bbc.bbc_set_param(h, "buckets", 64)
+        bbc.bbc_set_param(h, "sample_lists", 8)
+    for i in range(len(q)):
+        ol, _ = oracle_lib.probe(q[i], idx.centroids, nprobe, idx.metric)
+        assert np.array_equal(lists[i], ol)
+        sel, lofs = scanned_set(idx, ol)
+        t16 = oracle_lib.lut16(q[i], idx.codebooks, idx.metric)
+        e = oracle_lib.adc(t16, idx.codes[sel], idx.pq_m, idx.pq_bits)
+        sid = idx.ids[sel]
+        ref_ids, _ = oracle_lib.topkc(e, sid, kc, "sort")
+        n = int(cnt[i])
+        assert n == min(kc, len(e))
+        assert np.array_equal(np.sort(ids[i, :n].astype(np.int64)), np.sort(ref_ids)), f"query {i}"
+        # collector state vs Algorithm 1 run by the oracle
+        _, _, cb, counts = oracle_lib.bucket_collect(e, sid, lofs, kc, m, sample_min=smin)
+        s = state[i]
+        assert s["scanned"] == len(e)
+        assert (s["d_min"], s["d_max"], s["sh"], s["sample_lists"]) == (cb.d_min, cb.d_max, cb.sh, cb.sample_lists)
+        assert s["sample_size"] == cb.sample_size
+        assert np.array_equal(s["map"], np.frombuffer(bytes(cb.map), dtype=np.uint8))
+        assert s["tau"] == cb.tau
+        t = min(cb.tau, m - 1) if cb.tau < m else m - 1
+        if cb.tau < m:
+            assert np.array_equal(s["hist"][:t + 1].astype(np.int64), counts[:t + 1])
+            assert s["below"] == cb.below
+        assert s["pushed"] >= min(kc, len(e))
+
+
+def _check_topk(oracle_lib, idx, qv, gi, gd, oi, od, exact):
+    k = len(oi)
+    valid = oi >= 0
+    assert np.array_equal(gi >= 0, valid)
+    assert np.all(np.isinf(gd[~valid]))
+    if exact:
+        assert np.array_equal(gi, oi)
+        assert np.array_equal(gd[valid].astype(np.float64), od[valid])
+        return
+    g = gi[valid]
+    d64 = oracle_lib.rerank(qv, idx.vectors, g, idx.metric)
+    scale = max(np.abs(od[valid]).max(), 1e-30)
+    tol = RTOL * np.maximum(np.abs(d64), 1e-3 * scale)
+    assert np.all(np.abs(gd[valid] - d64) <= tol)                      # FP32 vs FP64 per result
+    assert np.all(np.abs(d64 - od[valid]) <= 2 * tol + RTOL * np.abs(od[valid]))   # same order statistics
+    diff = set(g.tolist()) ^ set(oi[valid].tolist())
+    if diff:                                                           # only ties at the boundary
+        dk = od[valid][-1]
+        dd = oracle_lib.rerank(qv, idx.vectors, np.array(sorted(diff)), idx.metric)
+        assert np.all(np.abs(dd - dk) <= 2 * RTOL * max(abs(dk), 1e-3 * scale))
+
+
+@pytest.mark.parametrize("kind,k,nprobe,ratio", [("tiny", 100, 12, 2.0), ("sift", 500, 16, 1.5),
+                                                 ("sift4", 300, 24, 2.0), ("embed", 200, 10, 1.5),
+                                                 ("ragged", 50, 40, 1.0), ("tiny", 1, 3, 1.0),
+                                                 ("sift", 4000, 64, 1.0)])
+def test_search_end_to_end(bbc, oracle_lib, kind, k, nprobe, ratio):
+    h, idx, q = dev_index(bbc, kind)
+    bbc.bbc_set_param(h, "kc_ratio", ratio)
+    kc = max(k, int(np.ceil(ratio * k - 1e-9)))
+    nq = len(q)
+    ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    dd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_search(h, cuda(q), nq, k, nprobe, ids, dd)
+    sync_ok(bbc, h)
+    gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
+    oi, od = oracle_lib.search(idx, q, k, nprobe, kc, "sort")
+    exact = kind in ("sift", "sift4")
+    for i in range(nq):
+        _check_topk(oracle_lib, idx, q[i], gi[i], gd[i], oi[i], od[i], exact)
+
+
+def test_full_probe_full_candidates_is_exact_knn(bbc, oracle_lib):
+    h, idx, q = dev_index(bbc, "ragged")
+    k = 40
+    bbc.bbc_set_param(h, "kc_ratio", float(idx.n) / k + 1)
+    nq = len(q)
+    ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    dd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_search(h, cuda(q), nq, k, idx.nlist, ids, dd)
+    sync_ok(bbc, h)
+    bi, bd = oracle_lib.bruteforce(q, idx.vectors, k, idx.metric)
+    for i in range(nq):
+        _check_topk(oracle_lib, idx, q[i], ids[i].cpu().numpy(), dd[i].cpu().numpy(), bi[i], bd[i], False)
+
+
+def test_padding_when_fewer_than_k_scanned(bbc):
+    h, idx, q = dev_index(bbc, "ragged")
+    bbc.bbc_set_param(h, "kc_ratio", 1.0)
+    k = 300
+    ids = torch.empty((2, k), dtype=torch.int64, device="cuda")
+    dd = torch.empty((2, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_search(h, cuda(q[:2]), 2, k, 1, ids, dd)
+    sync_ok(bbc, h)
+    gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
+    lens = np.diff(idx.list_offsets)
+    for i in range(2):
+        n = int((gi[i] >= 0).sum())
+        assert n < k and n in set(lens.tolist())
+        assert (gi[i, n:] == -1).all() and np.isinf(gd[i, n:]).all()
+        assert np.all(np.diff(gd[i, :n]) >= 0)
+
+
+def test_host_entry_point_matches_device(bbc):
+    h, idx, q = dev_index(bbc, "sift")
+    bbc.bbc_set_param(h, "kc_ratio", 1.5)
+    nq, k = len(q), 200
+    ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    dd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_search(h, cuda(q), nq, k, 16, ids, dd)
+    hq = torch.from_numpy(q).pin_memory()
+    hi = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    hd = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    bbc.bbc_search_host(h, hq, nq, k, 16, hi, hd)
+    sync_ok(bbc, h)
+    assert torch.equal(hi, ids.cpu()) and torch.equal(hd, dd.cpu())
+
+
+def test_chunked_workspace_same_result(bbc):
+    h, idx, q = dev_index(bbc, "tiny")
+    bbc.bbc_set_param(h, "kc_ratio", 2.0)
+    nq, k = len(q), 64
+    outs = []
+    for mb in (8192, 1):
+        bbc.bbc_set_param(h, "workspace_mb", mb)
+        ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+        dd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+        bbc.bbc_search(h, cuda(q), nq, k, 12, ids, dd)
+        sync_ok(bbc, h)
+        outs.append((ids.cpu(), dd.cpu()))
+    bbc.bbc_set_param(h, "workspace_mb", 8192)
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+def test_argument_errors(bbc):
+    h, idx, q = dev_index(bbc, "tiny")
+    ids = torch.empty((1, 5), dtype=torch.int64, device="cuda")
+    dd = torch.empty((1, 5), dtype=torch.float32, device="cuda")
+    qd = cuda(q[:1])
+    for k, nprobe in ((0, 4), (5, 0), (5, idx.nlist + 1)):
+        with pytest.raises(bbc.BBCError) as ei:
+            bbc.bbc_search(h, qd, 1, k, nprobe, ids, dd)
+        assert ei.value.code == -1
+    with pytest.raises(bbc.BBCError):
+        bbc.bbc_set_param(h, "buckets", 1)
+    with pytest.raises(bbc.BBCError):
+        bbc.bbc_set_param(h, "no_such_key", 1)
+    bbc.bbc_search(h, qd, 0, 5, 4, ids, dd)      # nq = 0 is a no-op
