@@ -109,6 +109,7 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  vectors_u8_exact).  Default: 1 when available.
  *   "workspace_mb" device workspace budget per call; queries are processed in
  *                  chunks that fit.  Default 8192.
+ *   "profile"      1 = record per-stage CUDA events (see bbc_profile_read).  Default 0.
  * Unknown key or out-of-range value: BBC_ERR_ARG. */
 int bbc_set_param(bbc_index* ix, const char* key, double value);
 int bbc_get_param(const bbc_index* ix, const char* key, double* value);
@@ -183,6 +184,18 @@ int bbc_collect(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
 int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint32_t* cand_ids,
                     const int64_t* cand_count, int64_t kc, int32_t k, int64_t* out_ids,
                     float* out_dists, void* stream);
+
+/* Per-stage timing (the GPU counterpart of the paper's time breakdown,
+ * Figure 2).  With parameter "profile" = 1 the library records a CUDA event
+ * pair on the launch stream around every kernel it launches.  This call
+ * waits for the recorded events, adds their elapsed times per stage into
+ * stage_ms[BBC_NUM_STAGES] (host array, may be NULL), writes the number of
+ * kernels launched since the last reset into *launches (may be NULL; counted
+ * whether or not profiling is on), and clears both when reset != 0.
+ * Stages: 0 probe scores, 1 probe selection, 2 lookup table, 3 scan +
+ * result buffer, 4 final selection, 5 re-rank, 6 top-k. */
+#define BBC_NUM_STAGES 7
+int bbc_profile_read(bbc_index* ix, double* stage_ms, int64_t* launches, int reset);
 
 /* Synchronise `stream`, then read and clear the index's device status word.
  * Returns BBC_OK, or BBC_ERR_CAPACITY if a kernel latched an overrun. */

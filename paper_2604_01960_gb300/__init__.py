@@ -29,7 +29,9 @@ METRICS = {"l2": 0, "ip": 1}
 # Exported symbols declared in include/bbc.h (checked by the ABI test).
 SYMBOLS = ["bbc_index_create", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
            "bbc_get_param", "bbc_search", "bbc_search_host", "bbc_probe", "bbc_lut", "bbc_collect",
-           "bbc_rerank_topk", "bbc_stream_status", "bbc_last_error", "bbc_version"]
+           "bbc_rerank_topk", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
+NUM_STAGES = 7
+STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk"]
 
 
 class BBCError(RuntimeError):
@@ -98,6 +100,7 @@ def lib():
             L.bbc_collect.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp, vp, vp]
             L.bbc_rerank_topk.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, vp, vp]
             L.bbc_stream_status.argtypes = [vp, vp]
+            L.bbc_profile_read.argtypes = [vp, vp, vp, C.c_int]
             for name in SYMBOLS:
                 if getattr(L, name).restype is None and name not in ("bbc_last_error", "bbc_version"):
                     getattr(L, name).restype = C.c_int
@@ -202,6 +205,14 @@ def bbc_rerank_topk(handle: int, queries, nq: int, cand_ids, cand_count, kc: int
                     stream=None) -> None:
     _check(lib().bbc_rerank_topk(handle, _ptr(queries), nq, _ptr(cand_ids), _ptr(cand_count), kc, k,
                                  _ptr(out_ids), _ptr(out_dists), _stream(stream)))
+
+
+def bbc_profile_read(handle: int, reset: bool = True):
+    """(per-stage milliseconds dict, kernels launched) since the last reset."""
+    ms = (C.c_double * NUM_STAGES)()
+    n = C.c_int64()
+    _check(lib().bbc_profile_read(handle, ms, C.byref(n), 1 if reset else 0))
+    return dict(zip(STAGES, list(ms))), n.value
 
 
 def bbc_stream_status(handle: int, stream=None) -> None:

@@ -81,7 +81,13 @@ struct bbc_index {
     int sample_lists = 8;
     int rerank_u8 = 1;
     double workspace_mb = 8192.0;
+    int profile = 0;
     std::mutex mu;
+    // tracing
+    std::mutex prof_mu;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    int64_t launches = 0;
     std::map<cudaStream_t, Workspace> ws;
 
     ~bbc_index() {
@@ -89,6 +95,7 @@ struct bbc_index {
         cudaGetDevice(&prev);
         cudaSetDevice(device);
         for (auto& kv : ws) cudaFree(kv.second.base);
+        for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (void* p : owned) cudaFree(p);
         if (prev >= 0) cudaSetDevice(prev);
     }
@@ -190,6 +197,26 @@ int check_search_args(const bbc_index* ix, const void* queries, int64_t nq, int 
     return BBC_OK;
 }
 
+// Launch one stage, counting it and (when profiling) bracketing it with events.
+template <typename F>
+cudaError_t stage(bbc_index* ix, int id, cudaStream_t st, F&& launch) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ix->profile) {
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return cudaErrorMemoryAllocation;
+        cudaEventRecord(a, st);
+    }
+    cudaError_t e = launch();
+    {
+        std::lock_guard<std::mutex> lk(ix->prof_mu);
+        ix->launches += 1;
+        if (ix->profile) {
+            cudaEventRecord(b, st);
+            ix->recs.push_back({id, a, b});
+        }
+    }
+    return e;
+}
+
 // The launch sequence for one chunk.
 int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc, int64_t* out_ids,
               float* out_dists, cudaStream_t st, int stop_after /* 9 = all */,
@@ -205,21 +232,21 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
     int64_t* count = count_out ? count_out : reinterpret_cast<int64_t*>(ws + p.off_count);
     float* cdist = reinterpret_cast<float*>(ws + p.off_cdist);
     if (!probe_in) {
-        CUDA_TRY(launch_probe_scores(d, q, nc, scores, st));
-        CUDA_TRY(launch_probe_select(d, q, nc, p.nprobe, scores, probe, st));
+        CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores(d, q, nc, scores, st); }));
+        CUDA_TRY(stage(ix, 1, st, [&] { return launch_probe_select(d, q, nc, p.nprobe, scores, probe, st); }));
     }
     if (stop_after <= 2) return BBC_OK;
-    CUDA_TRY(launch_lut16(d, q, nc, lut, st));
+    CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(d, q, nc, lut, st); }));
     ScanArgs sa{lut, probe_in ? probe_in : probe, p.nprobe, p.kc, ix->buckets, ix->sample_lists,
                 region, p.cap, state};
-    CUDA_TRY(launch_scan(d, nc, sa, st));
+    CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan(d, nc, sa, st); }));
     SelectArgs se{region, p.cap, state, p.kc, cand, count, nullptr};
-    CUDA_TRY(launch_select(d, nc, se, st));
+    CUDA_TRY(stage(ix, 4, st, [&] { return launch_select(d, nc, se, st); }));
     if (stop_after <= 7) return BBC_OK;
     RerankArgs ra{q, cand, count, p.kc, ix->rerank_u8 && d.vec_u8 != nullptr, cdist, p.k, out_ids,
                   out_dists, nullptr};
-    CUDA_TRY(launch_rerank(d, nc, ra, st));
-    CUDA_TRY(launch_topk(d, nc, ra, st));
+    CUDA_TRY(stage(ix, 5, st, [&] { return launch_rerank(d, nc, ra, st); }));
+    CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(d, nc, ra, st); }));
     return BBC_OK;
 }
 
@@ -431,6 +458,9 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "workspace_mb") {
         if (!(v >= 1)) return fail(BBC_ERR_ARG, "workspace_mb must be >= 1");
         ix->workspace_mb = v;
+    } else if (k == "profile") {
+        if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "profile must be 0 or 1");
+        ix->profile = (int)v;
     } else {
         return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     }
@@ -445,6 +475,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "sample_lists") *v = ix->sample_lists;
     else if (k == "rerank") *v = (ix->rerank_u8 && ix->dev.vec_u8) ? 1 : 0;
     else if (k == "workspace_mb") *v = ix->workspace_mb;
+    else if (k == "profile") *v = ix->profile;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -520,7 +551,8 @@ int bbc_lut(bbc_index* ix, const float* queries, int64_t nq, uint16_t* out_lut16
     if (nq < 0 || (nq > 0 && (!queries || !out_lut16))) return fail(BBC_ERR_ARG, "bad buffers");
     if (nq == 0) return BBC_OK;
     DeviceGuard g(ix->device);
-    CUDA_TRY(launch_lut16(ix->dev, queries, nq, out_lut16, (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(ix->dev, queries, nq, out_lut16, st); }));
     return BBC_OK;
 }
 
@@ -569,8 +601,30 @@ int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint3
         RerankArgs ra{queries + q0 * d, cand_ids + q0 * kc, cand_count + q0, kc,
                       ix->rerank_u8 && ix->dev.vec_u8 != nullptr, reinterpret_cast<float*>(ws), k,
                       out_ids + q0 * k, out_dists + q0 * k, nullptr};
-        CUDA_TRY(launch_rerank(ix->dev, nc, ra, st));
-        CUDA_TRY(launch_topk(ix->dev, nc, ra, st));
+        CUDA_TRY(stage(ix, 5, st, [&] { return launch_rerank(ix->dev, nc, ra, st); }));
+        CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(ix->dev, nc, ra, st); }));
+    }
+    return BBC_OK;
+}
+
+int bbc_profile_read(bbc_index* ix, double* stage_ms, int64_t* launches, int reset) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    DeviceGuard g(ix->device);
+    std::lock_guard<std::mutex> lk(ix->prof_mu);
+    double acc[BBC_NUM_STAGES] = {0};
+    for (auto& r : ix->recs) {
+        CUDA_TRY(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+        if (r.stage >= 0 && r.stage < BBC_NUM_STAGES) acc[r.stage] += ms;
+    }
+    if (stage_ms)
+        for (int i = 0; i < BBC_NUM_STAGES; ++i) stage_ms[i] = acc[i];
+    if (launches) *launches = ix->launches;
+    if (reset) {
+        for (auto& r : ix->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        ix->recs.clear();
+        ix->launches = 0;
     }
     return BBC_OK;
 }

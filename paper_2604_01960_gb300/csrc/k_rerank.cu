@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     const int64_t cnt = a.cand_count[qi];
     const int row_bytes = d * (int)sizeof(T);
     const int nchunk = row_bytes / 16;                 // d * sizeof(T) is a multiple of 16
-    const int G = nchunk >= 32 ? 32 : nchunk;          // lanes per candidate (power of two divides 32 below)
+    int G = 1;                                         // lanes per candidate: a power of two <= 32
+    while (G * 2 <= nchunk && G < 32) G *= 2;
     const int per_warp = 32 / G;
     const int ln = (int)lane_id();
     const int grp = ln / G, gl = ln % G;
@@ -76,8 +77,9 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     for (int64_t c = c0 + (int64_t)warp_id() * per_warp + grp; c - grp < c1; c += (int64_t)(blockDim.x / 32) * per_warp) {
         float acc = 0.f;
         const bool live = c < c1;
-        if (live) {
-            const uint32_t id = cand[c];
+        const uint32_t id = live ? cand[c] : 0u;
+        if (live && (int64_t)id >= ix.n) atomicOr(ix.status, kStatusSelectOverrun);   // never expected
+        if (live && (int64_t)id < ix.n) {
             const uint4* row = reinterpret_cast<const uint4*>(vec + (size_t)id * d);
             for (int ch = gl; ch < nchunk; ch += G) add_chunk<T>(__ldg(row + ch), rq + ch * elems, ix.metric, acc);
         }

@@ -78,9 +78,9 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
     const unsigned lt_mask = (1u << ln) - 1u;
     if (tau >= m) {
         // fewer than K_c objects: all appended objects are candidates
-        for (int64_t i = tid; i < n; i += bs) cand[i] = region[i].y;
+        for (int64_t i = tid; i < n && i < a.kc; i += bs) cand[i] = region[i].y;
         if (tid == 0) {
-            a.cand_count[qi] = n;
+            a.cand_count[qi] = n < a.kc ? n : a.kc;
             st.tau = tau;
             st.below = n;
         }
@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
             uint32_t base = 0;
             if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
             base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            if (take) cand[base + __popc(bal & lt_mask)] = v.y;
+            const uint32_t pos = base + __popc(bal & lt_mask);
+            if (take && (int64_t)pos < a.kc) cand[pos] = v.y;
         }
         if (in_smem && b == (uint32_t)tau) {
             const uint32_t p = atomicAdd(&s_t, 1u);
@@ -124,7 +125,8 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
                 uint32_t base = 0;
                 if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                if (take) cand[base + __popc(bal & lt_mask)] = (uint32_t)(tkeys[i] & 0xFFFFFFFFu);
+                const uint32_t pos = base + __popc(bal & lt_mask);
+                if (take && (int64_t)pos < a.kc) cand[pos] = (uint32_t)(tkeys[i] & 0xFFFFFFFFu);
             }
         }
     } else {
@@ -148,14 +150,15 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
                 uint32_t base = 0;
                 if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                if (take) cand[base + __popc(bal & lt_mask)] = id;
+                const uint32_t pos = base + __popc(bal & lt_mask);
+                if (take && (int64_t)pos < a.kc) cand[pos] = id;
             }
         }
     }
     __syncthreads();
     if (tid == 0) {
         if ((int64_t)s_out != a.kc) atomicOr(ix.status, kStatusSelectOverrun);
-        a.cand_count[qi] = a.kc;
+        a.cand_count[qi] = min((int64_t)s_out, a.kc);
         st.tau = tau;
         st.below = below;
     }
