@@ -178,6 +178,27 @@ int bbc_collect(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
                 const int32_t* probe_lists, int64_t kc, uint32_t* out_ids, int64_t* out_count,
                 bbc_collector_state* out_state, void* stream);
 
+/* Allocation-free variant of bbc_collect.  The paper has no counterpart:
+ * it exists for callers that cannot call cudaMalloc -- programs that budget
+ * every byte of device memory themselves and forbid libraries to allocate
+ * (for example a server that splits HBM between models up front), and
+ * latency-critical threads, where a cudaMalloc can block in the driver and
+ * synchronise the device.  Same arguments and results as bbc_collect.  Its
+ * scratch (lookup tables, the collector state when out_state is NULL, and
+ * the appended (estimate, id) pairs) is one static device array of
+ * BBC_STATIC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits; the call allocates nothing.  A call that needs
+ * more scratch than that -- about nq * (2 * pq_m * 2^pq_bits + 1344 +
+ * 8 * cap) bytes, cap = total length of the nprobe longest lists -- returns
+ * BBC_ERR_ARG before launching anything.  The first call on a device looks
+ * up the array's device address with that device current; make that first
+ * call before any stream capture.  All calls share the array, so calls whose
+ * kernels overlap on the GPU race: order them on one stream. */
+#define BBC_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int bbc_collect_static(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
+                       const int32_t* probe_lists, int64_t kc, uint32_t* out_ids, int64_t* out_count,
+                       bbc_collector_state* out_state, void* stream);
+
 /* Exact re-rank of candidates and final top-k (Algorithm 4, last two lines).
  *   cand_ids   device u32 [nq * kc]; cand_count device i64 [nq]
  *   out_ids / out_dists as in bbc_search. */

@@ -28,7 +28,7 @@ METRICS = {"l2": 0, "ip": 1}
 
 # Exported symbols declared in include/bbc.h (checked by the ABI test).
 SYMBOLS = ["bbc_index_create", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
-           "bbc_get_param", "bbc_search", "bbc_search_host", "bbc_probe", "bbc_lut", "bbc_collect",
+           "bbc_get_param", "bbc_search", "bbc_search_host", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
            "bbc_rerank_topk", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
 NUM_STAGES = 7
 STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk"]
@@ -98,6 +98,7 @@ def lib():
             L.bbc_probe.argtypes = [vp, vp, i64, i32, vp, vp]
             L.bbc_lut.argtypes = [vp, vp, i64, vp, vp]
             L.bbc_collect.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp, vp, vp]
+            L.bbc_collect_static.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp, vp, vp]
             L.bbc_rerank_topk.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, vp, vp]
             L.bbc_stream_status.argtypes = [vp, vp]
             L.bbc_profile_read.argtypes = [vp, vp, vp, C.c_int]
@@ -199,6 +200,15 @@ def bbc_collect(handle: int, queries, nq: int, nprobe: int, probe_lists, kc: int
                 out_state=None, stream=None) -> None:
     _check(lib().bbc_collect(handle, _ptr(queries), nq, nprobe, _ptr(probe_lists), kc, _ptr(out_ids),
                              _ptr(out_count), _ptr(out_state), _stream(stream)))
+
+
+def bbc_collect_static(handle: int, queries, nq: int, nprobe: int, probe_lists, kc: int, out_ids, out_count,
+                       out_state=None, stream=None) -> None:
+    """bbc_collect without any allocation: scratch comes from the library's static device array.
+
+    For callers that must not allocate device memory (see include/bbc.h)."""
+    _check(lib().bbc_collect_static(handle, _ptr(queries), nq, nprobe, _ptr(probe_lists), kc, _ptr(out_ids),
+                                    _ptr(out_count), _ptr(out_state), _stream(stream)))
 
 
 def bbc_rerank_topk(handle: int, queries, nq: int, cand_ids, cand_count, kc: int, k: int, out_ids, out_dists,

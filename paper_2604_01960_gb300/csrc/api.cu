@@ -644,3 +644,19 @@ int bbc_stream_status(bbc_index* ix, void* stream) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Internal accessors for other translation units of the library.
+// ===========================================================================
+namespace bbc {
+int api_error(int code, const char* msg) { return fail(code, "%s", msg); }
+int api_check_search_args(const bbc_index* ix, const void* queries, int64_t nq, int k, int nprobe,
+                          const void* out_ids, const void* out_dists) {
+    return check_search_args(ix, queries, nq, k, nprobe, out_ids, out_dists);
+}
+const DevIndex& index_dev(const bbc_index* ix) { return ix->dev; }
+int index_device(const bbc_index* ix) { return ix->device; }
+int64_t index_cap(const bbc_index* ix, int nprobe) { return ix->cap_prefix[nprobe]; }
+int index_buckets(const bbc_index* ix) { return ix->buckets; }
+int index_sample_lists(const bbc_index* ix) { return ix->sample_lists; }
+}  // namespace bbc

@@ -115,3 +115,15 @@ cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, c
 cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
 
 }  // namespace bbc
+
+// Accessors into the host-side index object (defined in api.cu).
+namespace bbc {
+int api_error(int code, const char* msg);
+int api_check_search_args(const bbc_index* ix, const void* queries, int64_t nq, int k, int nprobe,
+                          const void* out_ids, const void* out_dists);
+const DevIndex& index_dev(const bbc_index* ix);
+int index_device(const bbc_index* ix);
+int64_t index_cap(const bbc_index* ix, int nprobe);
+int index_buckets(const bbc_index* ix);
+int index_sample_lists(const bbc_index* ix);
+}  // namespace bbc
