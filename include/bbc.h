@@ -110,6 +110,9 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *   "workspace_mb" device workspace budget per call; queries are processed in
  *                  chunks that fit.  Default 8192.
  *   "profile"      1 = record per-stage CUDA events (see bbc_profile_read).  Default 0.
+ *   "probe_gemm"   1 = approximate probe scores on the tensor cores (tcgen05 BF16
+ *                  GEMM with a 3-term split), 0 = FP32 SIMT.  Either way the
+ *                  probe result is exact (see bbc_probe).  Default 1.
  * Unknown key or out-of-range value: BBC_ERR_ARG. */
 int bbc_set_param(bbc_index* ix, const char* key, double value);
 int bbc_get_param(const bbc_index* ix, const char* key, double* value);
@@ -134,6 +137,12 @@ int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, 
                     int64_t* out_ids, float* out_dists, void* stream);
 
 /* ---- stage entry points (each one row of the hot path; device pointers) ---- */
+
+/* Approximate probe scores (the pruning step of the coarse probe):
+ * out_scores device f32 [nq * nlist], a[q][l] = ||c_l||^2 - 2<q, c_l> (L2) or
+ * -<q, c_l> (IP), from the tensor-core GEMM ("probe_gemm" = 1) or FP32 SIMT.
+ * |a + ||q||^2 - s| stays within the bound bbc_probe uses, s = the FP64 score. */
+int bbc_probe_scores(bbc_index* ix, const float* queries, int64_t nq, float* out_scores, void* stream);
 
 /* Coarse probe (Section 2: route q to the n_probe nearest clusters;
  * Algorithm 4 scans them nearest first).  out_lists: device i32

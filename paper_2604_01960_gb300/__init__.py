@@ -28,7 +28,7 @@ METRICS = {"l2": 0, "ip": 1}
 
 # Exported symbols declared in include/bbc.h (checked by the ABI test).
 SYMBOLS = ["bbc_index_create", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
-           "bbc_get_param", "bbc_search", "bbc_search_host", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
+           "bbc_get_param", "bbc_search", "bbc_search_host", "bbc_probe_scores", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
            "bbc_rerank_topk", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
 NUM_STAGES = 7
 STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk"]
@@ -96,6 +96,7 @@ def lib():
             L.bbc_search.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp]
             L.bbc_search_host.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp]
             L.bbc_probe.argtypes = [vp, vp, i64, i32, vp, vp]
+            L.bbc_probe_scores.argtypes = [vp, vp, i64, vp, vp]
             L.bbc_lut.argtypes = [vp, vp, i64, vp, vp]
             L.bbc_collect.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp, vp, vp]
             L.bbc_collect_static.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp, vp, vp]
@@ -186,6 +187,10 @@ def bbc_search(handle: int, queries, nq: int, k: int, nprobe: int, out_ids, out_
 def bbc_search_host(handle: int, queries, nq: int, k: int, nprobe: int, out_ids, out_dists, stream=None) -> None:
     _check(lib().bbc_search_host(handle, _ptr(queries), nq, k, nprobe, _ptr(out_ids), _ptr(out_dists),
                                  _stream(stream)))
+
+
+def bbc_probe_scores(handle: int, queries, nq: int, out_scores, stream=None) -> None:
+    _check(lib().bbc_probe_scores(handle, _ptr(queries), nq, _ptr(out_scores), _stream(stream)))
 
 
 def bbc_probe(handle: int, queries, nq: int, nprobe: int, out_lists, stream=None) -> None:

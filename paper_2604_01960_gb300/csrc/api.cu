@@ -67,6 +67,21 @@ struct Workspace {
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
+// FP32 -> BF16, round to nearest even (NaN kept quiet).
+uint16_t f32_to_bf16(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7FFFFFFFu) > 0x7F800000u) return 0x7FC0;
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_to_f32(uint16_t h) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 }  // namespace
 
 struct bbc_index {
@@ -80,6 +95,7 @@ struct bbc_index {
     int buckets = 64;
     int sample_lists = 8;
     int rerank_u8 = 1;
+    int probe_gemm = 1;
     double workspace_mb = 8192.0;
     int profile = 0;
     std::mutex mu;
@@ -127,7 +143,7 @@ struct Plan {
     int k;
     int64_t cap;
     size_t off_scores, off_probe, off_lut, off_state, off_region, off_cand, off_count, off_cdist,
-        off_q, off_ids, off_dists, total;
+        off_q, off_ids, off_dists, off_abf, total;
 };
 
 Plan make_plan(const bbc_index* ix, int64_t nq, int nprobe, int64_t kc, int k, bool host_io) {
@@ -150,6 +166,7 @@ Plan make_plan(const bbc_index* ix, int64_t nq, int nprobe, int64_t kc, int k, b
         p.off_q = o; o = align_up(o + (host_io ? (size_t)c * d.d * 4 : 0));
         p.off_ids = o; o = align_up(o + (host_io ? (size_t)c * k * 8 : 0));
         p.off_dists = o; o = align_up(o + (host_io ? (size_t)c * k * 4 : 0));
+        p.off_abf = o; o = align_up(o + (ix->probe_gemm ? probe_tc_workspace(d, c) : 0));
         return o;
     };
     const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
@@ -232,8 +249,13 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
     int64_t* count = count_out ? count_out : reinterpret_cast<int64_t*>(ws + p.off_count);
     float* cdist = reinterpret_cast<float*>(ws + p.off_cdist);
     if (!probe_in) {
-        CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores(d, q, nc, scores, st); }));
-        CUDA_TRY(stage(ix, 1, st, [&] { return launch_probe_select(d, q, nc, p.nprobe, scores, probe, st); }));
+        if (ix->probe_gemm)
+            CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores_tc(d, q, nc, scores, ws + p.off_abf, st); }));
+        else
+            CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores(d, q, nc, scores, st); }));
+        CUDA_TRY(stage(ix, 1, st, [&] {
+            return launch_probe_select(d, q, nc, p.nprobe, scores, probe, ix->probe_gemm, st);
+        }));
     }
     if (stop_after <= 2) return BBC_OK;
     CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(d, q, nc, lut, st); }));
@@ -366,6 +388,25 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out) {
     if ((rc = upload(ix.get(), h->vectors, (size_t)n * d, &dvec))) return rc;
     unsigned int zero = 0;
     if ((rc = upload(ix.get(), &zero, 1, &dstat))) return rc;
+    // tensor-core probe operand: [c_hi | c_lo | c_hi | 0-pad] in BF16, K padded to 64
+    D.kp = (3 * d + 63) / 64 * 64;
+    {
+        std::vector<uint16_t> b3((size_t)L * D.kp, 0);
+        for (int l = 0; l < L; ++l) {
+            uint16_t* r = b3.data() + (size_t)l * D.kp;
+            for (int i = 0; i < d; ++i) {
+                const float x = h->centroids[(size_t)l * d + i];
+                const uint16_t hi = f32_to_bf16(x);
+                const uint16_t lo = f32_to_bf16(x - bf16_to_f32(hi));
+                r[i] = hi;
+                r[d + i] = lo;
+                r[2 * d + i] = hi;
+            }
+        }
+        uint16_t* db3;
+        if ((rc = upload(ix.get(), b3.data(), b3.size(), &db3))) return rc;
+        D.cent_b3 = db3;
+    }
     D.centroids = dc; D.cnorm = dcn; D.list_blk = dlb; D.list_len = dll; D.codes = dcode; D.ids = did;
     D.books = dbook; D.vectors = dvec; D.status = dstat; D.vec_u8 = nullptr;
     if (u8) {
@@ -458,6 +499,9 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "workspace_mb") {
         if (!(v >= 1)) return fail(BBC_ERR_ARG, "workspace_mb must be >= 1");
         ix->workspace_mb = v;
+    } else if (k == "probe_gemm") {
+        if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "probe_gemm must be 0 (FP32 SIMT) or 1 (tensor cores)");
+        ix->probe_gemm = (int)v;
     } else if (k == "profile") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "profile must be 0 or 1");
         ix->profile = (int)v;
@@ -476,6 +520,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "rerank") *v = (ix->rerank_u8 && ix->dev.vec_u8) ? 1 : 0;
     else if (k == "workspace_mb") *v = ix->workspace_mb;
     else if (k == "profile") *v = ix->profile;
+    else if (k == "probe_gemm") *v = ix->probe_gemm;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -542,6 +587,31 @@ int bbc_probe(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe, i
         rc = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, nullptr, nullptr, st, 2,
                        out_lists + q0 * nprobe);
         if (rc) return rc;
+    }
+    return BBC_OK;
+}
+
+int bbc_probe_scores(bbc_index* ix, const float* queries, int64_t nq, float* out_scores, void* stream) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    if (nq < 0 || (nq > 0 && (!queries || !out_scores))) return fail(BBC_ERR_ARG, "bad buffers");
+    if (nq == 0) return BBC_OK;
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevIndex& d = ix->dev;
+    if (!ix->probe_gemm) {
+        CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores(d, queries, nq, out_scores, st); }));
+        return BBC_OK;
+    }
+    const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
+    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(budget / (probe_tc_workspace(d, 1) + 256))));
+    char* ws;
+    int rc = get_workspace(ix, st, align_up(probe_tc_workspace(d, chunk)), &ws);
+    if (rc) return rc;
+    for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+        const int64_t nc = std::min(chunk, nq - q0);
+        CUDA_TRY(stage(ix, 0, st, [&] {
+            return launch_probe_scores_tc(d, queries + q0 * d.d, nc, out_scores + q0 * d.nlist, ws, st);
+        }));
     }
     return BBC_OK;
 }

@@ -34,6 +34,7 @@ constexpr int kMaxBuckets = 256;
 constexpr unsigned kStatusRegionOverrun = 1u;
 constexpr unsigned kStatusSelectOverrun = 2u;
 constexpr unsigned kStatusTopkOverrun = 4u;
+constexpr unsigned kStatusTimeout = 8u;
 
 struct DevIndex {
     int d, nlist, metric, M, bits, K, dsub;
@@ -52,22 +53,30 @@ struct DevIndex {
     const float* vectors;
     const uint8_t* vec_u8;
     unsigned int* status;
+    const uint16_t* cent_b3;   // BF16 [nlist][kp]: [c_hi | c_lo | c_hi | 0-pad] for the tensor-core probe
+    int kp;                    // 3d rounded up to a multiple of 64
 };
 
 // Words per LUT row in shared memory: lane t at code slot s reads word t + s
-// of the row of its code value, so a row needs M + 31 words; rounding to a
-// multiple of 32 keeps bank(t, s) = (t + s) mod 32 for every row.
-inline int lut_row_words(int M) { return M <= 32 ? 64 : M + 32; }
+// of the row of its code value, so a row needs M + 31 words; a multiple of 32
+// keeps bank(t, s) = (t + s) mod 32 for every row (k_scan.cu rounds up to a
+// power of two where that costs little, to turn the row offset into a shift).
+inline int lut_row_words(int M) { return M <= 32 ? 64 : (M <= 96 ? 128 : M + 32); }
 
 // ---- launchers (one per translation unit) ----
 
 // S1: approximate probe scores a[q][l] = ||c_l||^2 - 2<q,c_l> (L2) or -<q,c_l> (IP).
 cudaError_t launch_probe_scores(const DevIndex& ix, const float* q, int64_t nq, float* scores,
                                 cudaStream_t st);
-// S2: exact probe selection with FP64 re-score of every list whose score
-// can reach the nprobe-th.  scores from launch_probe_scores.
+// S1 on the tensor cores (tcgen05 BF16 GEMM, 3-term split); abuf holds
+// probe_tc_workspace(ix, nq) bytes for the split queries.
+size_t probe_tc_workspace(const DevIndex& ix, int64_t nq);
+cudaError_t launch_probe_scores_tc(const DevIndex& ix, const float* q, int64_t nq, float* scores, void* abuf,
+                                   cudaStream_t st);
+// S2: exact probe selection (FP64 decides where the approximations cannot).
+// tc = 1 when the scores come from the tensor-core GEMM (wider error bound).
 cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, int nprobe,
-                                const float* scores, int32_t* lists, cudaStream_t st);
+                                const float* scores, int32_t* lists, int tc, cudaStream_t st);
 // S3: uint16 PQ lookup tables [nq][M][K].
 cudaError_t launch_lut16(const DevIndex& ix, const float* q, int64_t nq, uint16_t* lut16,
                          cudaStream_t st);

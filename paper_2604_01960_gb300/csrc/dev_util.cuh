@@ -80,9 +80,15 @@ __device__ uint32_t cta_select_u32(int64_t n, uint32_t r, Get get, uint32_t* his
     for (int sh = top; sh >= 0; sh -= 8) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            uint32_t k = get(i);
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> sh) & 255u], 1u);
+        // four loads in flight per thread before the shared atomics
+        const int64_t bs = blockDim.x;
+        for (int64_t i = threadIdx.x; i < n; i += 4 * bs) {
+            uint32_t k[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k[u] = i + u * bs < n ? get(i + u * bs) : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * bs < n && (k[u] & mask) == prefix) atomicAdd(&hist[(k[u] >> sh) & 255u], 1u);
         }
         __syncthreads();
         if (warp_id() == 0) warp_find_digit(hist, r, &sc[0], &sc[1]);

@@ -4,10 +4,10 @@
 // S1  approximate scores  a[q][l] = ||c_l||^2 - 2<q, c_l>   (L2)
 //                                   -<q, c_l>                (IP)
 //     (||q||^2 is constant per query and dropped.)
-// S2  exact selection: every list whose approximate score can still reach
-//     the nprobe-th is re-scored exactly in FP64 (ascending dimension order,
-//     no fused multiply-add), and the nprobe smallest (FP64 score, list id)
-//     are written nearest first.  The approximate scores only prune.
+// S2  exact selection: the nprobe smallest (FP64 score, list id), nearest
+//     first, where the FP64 score is evaluated in ascending dimension order
+//     with no fused multiply-add.  Approximate scores only prune and order;
+//     FP64 decides wherever the approximations cannot (see the kernel).
 #include <cfloat>
 #include <cmath>
 
@@ -106,19 +106,27 @@ __device__ double exact_score(const float* __restrict__ q, const float* __restri
     return s;
 }
 
+// Selection in three steps: (1) the approximate GEMM scores prune to every
+// list that can still reach the nprobe-th; (2) those lists are re-scored in
+// FP32 and sorted; (3) any run of neighbours whose FP32 scores are too close
+// for the FP32 error bound to order them is re-scored in FP64 and re-sorted
+// by (FP64 score, list id).  Lists outside runs are provably in exact order,
+// so the result equals sorting every list by its FP64 score.
 __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, const float* __restrict__ q,
                                                                     int nprobe,
                                                                     const float* __restrict__ scores,
-                                                                    int32_t* __restrict__ lists) {
+                                                                    int32_t* __restrict__ lists, int tc) {
     extern __shared__ unsigned long long psm[];
     const int L = ix.nlist, d = ix.d;
     unsigned long long* ckey = psm;                                  // [SEL_MAXC]
     uint32_t* cval = (uint32_t*)(ckey + SEL_MAXC);                   // [SEL_MAXC]
     uint32_t* keys = cval + SEL_MAXC;                                // [L]
+    float* fsc = (float*)keys;                                       // reuses keys after step 1
     __shared__ uint32_t hist[256];
     __shared__ uint32_t sc[2];
     __shared__ float red[SEL_THREADS / 32];
     __shared__ uint32_t ncand;
+    __shared__ float s_fmax;
 
     const int64_t qi = blockIdx.x;
     const float* qv = q + qi * d;
@@ -129,18 +137,32 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
     for (int i = threadIdx.x; i < d; i += blockDim.x) acc = fmaf(qv[i], qv[i], acc);
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if (lane_id() == 0) red[warp_id()] = acc;
-    if (threadIdx.x == 0) ncand = 0;
+    if (threadIdx.x == 0) { ncand = 0; s_fmax = 0.f; }
     __syncthreads();
     float qn2 = 0.f;
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) qn2 += red[w];
     const double qn = sqrt((double)qn2);
 
+    // step 1: prune with the approximate scores
     const uint32_t kth = cta_select_u32(L, (uint32_t)(nprobe - 1), [&](int64_t i) { return keys[i]; },
                                         hist, sc, 24);
-    // |a - (exact - ||q||^2)| <= eps for the FP32 score (dot product of length d
-    // plus ||c||^2 and the final subtraction), with a safety factor of 4.
+    // |a - (exact - ||q||^2)| <= eps for the approximate score.
+    //  FP32 SIMT GEMM: dot product of length d plus ||c||^2 and the final
+    //    subtraction, (d + 4) 2^-24 (||q|| + max||c||)^2, safety factor 4.
+    //  Tensor-core GEMM with the 3-term BF16 split: dropped terms
+    //    3.1 2^-16 ||q|| ||c||, FP32 accumulation of 3d products
+    //    3.06 d 2^-23 ||q|| ||c||, doubled for the factor 2 of the L2 score,
+    //    plus ||c||^2 and subtraction rounding; safety factor 2.
     const double cm = (double)ix.cmax;
-    const double eps = (double)(d + 4) * ldexp(1.0, -22) * (qn + cm) * (qn + cm);
+    double eps;
+    if (!tc) {
+        eps = (double)(d + 4) * ldexp(1.0, -22) * (qn + cm) * (qn + cm);
+    } else {
+        const double rel = 3.1 * ldexp(1.0, -16) + 3.06 * (double)d * ldexp(1.0, -23);
+        eps = ix.metric == BBC_METRIC_L2
+                  ? 2.0 * (2.0 * rel * qn * cm + ldexp(1.0, -23) * (cm * cm + 2.0 * qn * cm))
+                  : 2.0 * (rel * qn * cm + ldexp(1.0, -24) * qn * cm);
+    }
     const double thr = (double)key_f32(kth) + 2.0 * eps;
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
         if ((double)key_f32(keys[l]) <= thr) {
@@ -154,22 +176,69 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
         if (threadIdx.x == 0) atomicOr(ix.status, kStatusSelectOverrun);
         nc = SEL_MAXC;
     }
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-        uint32_t l = cval[i];
-        ckey[i] = f64_key(exact_score(qv, ix.centroids + (int64_t)l * d, d, ix.metric));
-    }
+    // step 2: FP32 re-score (one warp per list, lanes over dimensions, so the
+    // centroid rows are read coalesced) and sort by (FP32 score, list id)
     const int np2 = next_pow2(nc);
     for (int i = nc + threadIdx.x; i < np2; i += blockDim.x) {
         ckey[i] = ~0ull;
         cval[i] = 0xFFFFFFFFu;
     }
+    for (int i = warp_id(); i < nc; i += blockDim.x / 32) {
+        const float* cr = ix.centroids + (int64_t)cval[i] * d;
+        float part = 0.f;
+        if (ix.metric == BBC_METRIC_L2) {
+            for (int j = lane_id(); j < d; j += 32) {
+                const float t = qv[j] - cr[j];
+                part = fmaf(t, t, part);
+            }
+        } else {
+            for (int j = lane_id(); j < d; j += 32) part = fmaf(qv[j], cr[j], part);
+        }
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        const float f = ix.metric == BBC_METRIC_L2 ? part : -part;
+        if (lane_id() == 0) {
+            ckey[i] = (unsigned long long)f32_key(f);
+            atomicMax((int*)&s_fmax, __float_as_int(fabsf(f)));       // non-negative floats order as ints
+        }
+    }
     __syncthreads();
     cta_bitonic_kv(ckey, cval, np2);
+    // step 3: FP32 error bound (any summation order), uniform over the candidates:
+    //   L2: sum of squares, |f - s| <= (d + 2) 2^-24 max f;
+    //   IP: |f - s| <= (d + 2) 2^-24 ||q|| max ||c||;  safety factor 2.
+    const double e32 = (double)(d + 4) * ldexp(1.0, -23) *
+                       (ix.metric == BBC_METRIC_L2 ? (double)s_fmax : qn * cm) + 1e-30;
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) fsc[i] = key_f32((uint32_t)ckey[i]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        const bool link_prev = i > 0 && (double)fsc[i] - (double)fsc[i - 1] <= 2.0 * e32;
+        const bool link_next = i + 1 < nc && (double)fsc[i + 1] - (double)fsc[i] <= 2.0 * e32;
+        if (!link_prev && link_next) {
+            // run [i, j]: exact FP64 scores, insertion sort by (score, list id)
+            int j = i + 1;
+            while (j + 1 < nc && (double)fsc[j + 1] - (double)fsc[j] <= 2.0 * e32) ++j;
+            for (int t = i; t <= j; ++t)
+                ckey[t] = f64_key(exact_score(qv, ix.centroids + (int64_t)cval[t] * d, d, ix.metric));
+            for (int t = i + 1; t <= j; ++t) {
+                const unsigned long long kk = ckey[t];
+                const uint32_t vv = cval[t];
+                int u = t - 1;
+                while (u >= i && (ckey[u] > kk || (ckey[u] == kk && cval[u] > vv))) {
+                    ckey[u + 1] = ckey[u];
+                    cval[u + 1] = cval[u];
+                    --u;
+                }
+                ckey[u + 1] = kk;
+                cval[u + 1] = vv;
+            }
+        }
+    }
+    __syncthreads();
     for (int j = threadIdx.x; j < nprobe; j += blockDim.x) lists[qi * nprobe + j] = (int32_t)cval[j];
 }
 
 cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, int nprobe,
-                                const float* scores, int32_t* lists, cudaStream_t st) {
+                                const float* scores, int32_t* lists, int tc, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
     size_t smem = (size_t)SEL_MAXC * (8 + 4) + (size_t)ix.nlist * 4;
     static bool attr_set = false;
@@ -179,7 +248,7 @@ cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    probe_select_kernel<<<(unsigned)nq, SEL_THREADS, smem, st>>>(ix, q, nprobe, scores, lists);
+    probe_select_kernel<<<(unsigned)nq, SEL_THREADS, smem, st>>>(ix, q, nprobe, scores, lists, tc);
     return cudaGetLastError();
 }
 

@@ -9,8 +9,9 @@
 // integer in [0, 255] (then the FP32 distance is exact: all partial sums are
 // integers below 2^24).  Accumulation is FP32.
 //
-// Top-k: one CTA per query sorts 64-bit keys (order-preserving distance bits
-// << 32 | id) in shared memory and writes the first k.
+// Top-k: one CTA per query orders 64-bit keys (order-preserving distance bits
+// << 32 | id) with a counting sort into fine distance bins followed by exact
+// ranking inside each bin, and writes the first k.
 #include <cfloat>
 
 #include "bbc_internal.cuh"
@@ -19,79 +20,182 @@
 namespace bbc {
 
 constexpr int RR_THREADS = 256;
-constexpr int RR_CAND_PER_CTA = 256;
+constexpr int RR_CAND_PER_CTA = 1024;
 
-template <typename T>
-__device__ __forceinline__ void add_chunk(const uint4 raw, const float* qv, int metric, float& acc);
-
-template <>
-__device__ __forceinline__ void add_chunk<float>(const uint4 raw, const float* qv, int metric, float& acc) {
+// Float accumulation of one 16-byte chunk of a row against the query chunk.
+__device__ __forceinline__ void add_chunk_f32(const uint4 raw, const float4 q, int metric, float& acc) {
     const float v[4] = {__uint_as_float(raw.x), __uint_as_float(raw.y), __uint_as_float(raw.z),
                         __uint_as_float(raw.w)};
+    const float qq[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         if (metric == BBC_METRIC_L2) {
-            const float t = qv[i] - v[i];
+            const float t = qq[i] - v[i];
             acc = fmaf(t, t, acc);
         } else {
-            acc = fmaf(qv[i], v[i], acc);
+            acc = fmaf(qq[i], v[i], acc);
         }
     }
 }
 
-template <>
-__device__ __forceinline__ void add_chunk<uint8_t>(const uint4 raw, const float* qv, int metric, float& acc) {
+__device__ __forceinline__ void add_chunk_u8f(const uint4 raw, const float4* q4, int metric, float& acc) {
     const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const float v = (float)((w[i >> 2] >> (8 * (i & 3))) & 0xFFu);
-        if (metric == BBC_METRIC_L2) {
-            const float t = qv[i] - v;
-            acc = fmaf(t, t, acc);
-        } else {
-            acc = fmaf(qv[i], v, acc);
+    for (int j = 0; j < 4; ++j) {
+        const float4 q = q4[j];
+        const float qq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float v = (float)((w[j] >> (8 * i)) & 0xFFu);
+            if (metric == BBC_METRIC_L2) {
+                const float t = qq[i] - v;
+                acc = fmaf(t, t, acc);
+            } else {
+                acc = fmaf(qq[i], v, acc);
+            }
         }
     }
 }
 
+// One group of G lanes per candidate row; rows gathered with 16-byte loads.
+// Exact-u8 rows with a query whose components are integers in [0, 255] take
+// the integer path: <q, v> and <v, v> with dp4a, ||q - v||^2 = ||q||^2 +
+// ||v||^2 - 2 <q, v> in exact integer arithmetic.
 template <typename T>
 __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankArgs a, const T* __restrict__ vec) {
-    extern __shared__ float rq[];    // query, d floats
+    extern __shared__ uint4 rsm[];
     const int d = ix.d;
+    float* rq = reinterpret_cast<float*>(rsm);                 // d floats
+    uint8_t* q8 = reinterpret_cast<uint8_t*>(rsm + d / 4);     // d bytes (u8 rows only)
+    __shared__ int s_int, s_qn2;
     const int64_t qi = blockIdx.y;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) rq[i] = a.q[qi * d + i];
+    if (threadIdx.x == 0) { s_int = 1; s_qn2 = 0; }
     __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        const float v = a.q[qi * d + i];
+        rq[i] = v;
+        if (sizeof(T) == 1) {
+            const bool ok = v >= 0.f && v <= 255.f && v == floorf(v);
+            if (!ok) s_int = 0;
+            q8[i] = ok ? (uint8_t)v : 0;
+            if (ok) atomicAdd(&s_qn2, (int)v * (int)v);
+        }
+    }
+    __syncthreads();
+    const bool intpath = sizeof(T) == 1 && s_int;
+    const int qn2 = s_qn2;
     const int64_t cnt = a.cand_count[qi];
-    const int row_bytes = d * (int)sizeof(T);
-    const int nchunk = row_bytes / 16;                 // d * sizeof(T) is a multiple of 16
+    const int nchunk = d * (int)sizeof(T) / 16;        // d * sizeof(T) is a multiple of 16
     int G = 1;                                         // lanes per candidate: a power of two <= 32
     while (G * 2 <= nchunk && G < 32) G *= 2;
     const int per_warp = 32 / G;
     const int ln = (int)lane_id();
     const int grp = ln / G, gl = ln % G;
-    const int elems = 16 / (int)sizeof(T);
     const int64_t c0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
     const int64_t c1 = min(c0 + RR_CAND_PER_CTA, cnt);
     const uint32_t* cand = a.cand + qi * a.kc;
     float* out = a.cdist + qi * a.kc;
-    for (int64_t c = c0 + (int64_t)warp_id() * per_warp + grp; c - grp < c1; c += (int64_t)(blockDim.x / 32) * per_warp) {
-        float acc = 0.f;
-        const bool live = c < c1;
-        const uint32_t id = live ? cand[c] : 0u;
-        if (live && (int64_t)id >= ix.n) atomicOr(ix.status, kStatusSelectOverrun);   // never expected
-        if (live && (int64_t)id < ix.n) {
-            const uint4* row = reinterpret_cast<const uint4*>(vec + (size_t)id * d);
-            for (int ch = gl; ch < nchunk; ch += G) add_chunk<T>(__ldg(row + ch), rq + ch * elems, ix.metric, acc);
+    const float4* q4 = reinterpret_cast<const float4*>(rq);
+    const uint4* qb = reinterpret_cast<const uint4*>(q8);
+    // RR_U candidates per group per step, their row loads issued together
+    constexpr int RR_U = 4;
+    const int64_t stride = (int64_t)(blockDim.x / 32) * per_warp * RR_U;
+    for (int64_t cb = c0 + (int64_t)warp_id() * per_warp * RR_U; cb < c1; cb += stride) {
+        uint32_t id[RR_U];
+        bool ok[RR_U];
+#pragma unroll
+        for (int u = 0; u < RR_U; ++u) {
+            const int64_t c = cb + (int64_t)u * per_warp + grp;
+            const bool live = c < c1;
+            id[u] = live ? cand[c] : 0u;
+            ok[u] = live && (int64_t)id[u] < ix.n;
+            if (live && !ok[u]) atomicOr(ix.status, kStatusSelectOverrun);   // never expected
         }
-        for (int o = G >> 1; o; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-        if (live && gl == 0) out[c] = ix.metric == BBC_METRIC_L2 ? acc : -acc;
+        float dist[RR_U];
+        if (nchunk == G) {
+            // one 16-byte chunk per lane and candidate: all loads first
+            uint4 v[RR_U];
+#pragma unroll
+            for (int u = 0; u < RR_U; ++u)
+                v[u] = ok[u] ? __ldg(reinterpret_cast<const uint4*>(vec + (size_t)id[u] * d) + gl)
+                             : make_uint4(0, 0, 0, 0);
+            if (intpath) {
+                const uint4 qq = qb[gl];
+#pragma unroll
+                for (int u = 0; u < RR_U; ++u) {
+                    unsigned qv = 0, vv = 0;
+                    qv = __dp4a(v[u].x, qq.x, qv); qv = __dp4a(v[u].y, qq.y, qv);
+                    qv = __dp4a(v[u].z, qq.z, qv); qv = __dp4a(v[u].w, qq.w, qv);
+                    vv = __dp4a(v[u].x, v[u].x, vv); vv = __dp4a(v[u].y, v[u].y, vv);
+                    vv = __dp4a(v[u].z, v[u].z, vv); vv = __dp4a(v[u].w, v[u].w, vv);
+                    for (int o = G >> 1; o; o >>= 1) {
+                        qv += __shfl_xor_sync(0xFFFFFFFFu, qv, o);
+                        vv += __shfl_xor_sync(0xFFFFFFFFu, vv, o);
+                    }
+                    dist[u] = ix.metric == BBC_METRIC_L2
+                                  ? (float)((long long)qn2 + (long long)vv - 2ll * (long long)qv)
+                                  : -(float)qv;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < RR_U; ++u) {
+                    float acc = 0.f;
+                    if (sizeof(T) == 4) add_chunk_f32(v[u], q4[gl], ix.metric, acc);
+                    else add_chunk_u8f(v[u], q4 + 4 * gl, ix.metric, acc);
+                    for (int o = G >> 1; o; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+                    dist[u] = ix.metric == BBC_METRIC_L2 ? acc : -acc;
+                }
+            }
+        } else {
+            // several chunks per lane: loop over the row
+#pragma unroll
+            for (int u = 0; u < RR_U; ++u) {
+                const uint4* row = reinterpret_cast<const uint4*>(vec + (size_t)(ok[u] ? id[u] : 0u) * d);
+                if (intpath) {
+                    unsigned qv = 0, vv = 0;
+                    if (ok[u]) {
+                        for (int ch = gl; ch < nchunk; ch += G) {
+                            const uint4 v = __ldg(row + ch);
+                            const uint4 qq = qb[ch];
+                            qv = __dp4a(v.x, qq.x, qv); qv = __dp4a(v.y, qq.y, qv);
+                            qv = __dp4a(v.z, qq.z, qv); qv = __dp4a(v.w, qq.w, qv);
+                            vv = __dp4a(v.x, v.x, vv); vv = __dp4a(v.y, v.y, vv);
+                            vv = __dp4a(v.z, v.z, vv); vv = __dp4a(v.w, v.w, vv);
+                        }
+                    }
+                    for (int o = G >> 1; o; o >>= 1) {
+                        qv += __shfl_xor_sync(0xFFFFFFFFu, qv, o);
+                        vv += __shfl_xor_sync(0xFFFFFFFFu, vv, o);
+                    }
+                    dist[u] = ix.metric == BBC_METRIC_L2
+                                  ? (float)((long long)qn2 + (long long)vv - 2ll * (long long)qv)
+                                  : -(float)qv;
+                } else {
+                    float acc = 0.f;
+                    if (ok[u]) {
+                        for (int ch = gl; ch < nchunk; ch += G) {
+                            const uint4 v = __ldg(row + ch);
+                            if (sizeof(T) == 4) add_chunk_f32(v, q4[ch], ix.metric, acc);
+                            else add_chunk_u8f(v, q4 + 4 * ch, ix.metric, acc);
+                        }
+                    }
+                    for (int o = G >> 1; o; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+                    dist[u] = ix.metric == BBC_METRIC_L2 ? acc : -acc;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RR_U; ++u) {
+            const int64_t c = cb + (int64_t)u * per_warp + grp;
+            if (c < c1 && gl == 0) out[c] = dist[u];
+        }
     }
 }
 
 cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
     dim3 grid((unsigned)((a.kc + RR_CAND_PER_CTA - 1) / RR_CAND_PER_CTA), (unsigned)nq);
-    const size_t smem = sizeof(float) * ix.d;
+    const size_t smem = sizeof(float) * ix.d + ix.d + 16;
     if (a.use_u8 && ix.vec_u8)
         rerank_kernel<uint8_t><<<grid, RR_THREADS, smem, st>>>(ix, a, ix.vec_u8);
     else
@@ -100,32 +204,112 @@ cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, c
 }
 
 // ---------------------------------------------------------------------------
+// S9 top-k.  Keys: order-preserving distance bits << 32 | id (unique).
+// 1. min / max of the distance bits over the candidates;
+// 2. histogram over TK_BINS fine bins, bin = floor((bits - min) * TK_BINS /
+//    (max - min + 1)) -- a monotone function of the distance;
+// 3. exclusive scan -> bin starts; scatter keys into shared memory by bin;
+// 4. every key's final position = its bin's start + the number of keys of its
+//    bin that are smaller; positions < k are written straight to the output.
+// A bin with more than TK_BIG keys (many exactly equal distances) would make
+// step 4 quadratic; then the CTA sorts all keys with a bitonic network instead.
 constexpr int TK_THREADS = 1024;
-constexpr int TK_MAX = 16384;    // candidates sorted in shared memory per query
+constexpr int TK_MAX = 16384;    // candidates handled in shared memory per query
+constexpr int TK_BINS = 4096;
+constexpr int TK_BIG = 2048;
+
+__device__ __forceinline__ uint32_t tk_bin(uint32_t key, uint32_t kmin, float scale) {
+    uint32_t b = (uint32_t)(__uint2float_rz(key - kmin) * scale);
+    return b < (uint32_t)TK_BINS ? b : (uint32_t)(TK_BINS - 1);
+}
 
 __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArgs a) {
-    extern __shared__ unsigned long long keys[];   // [np2]
+    extern __shared__ unsigned long long keys[];   // [TK_MAX]
+    __shared__ uint32_t bins[TK_BINS];
+    __shared__ uint32_t wsum[TK_THREADS / 32];
+    __shared__ uint32_t s_min, s_max, s_big;
     const int64_t qi = blockIdx.x;
     const int64_t cnt = a.cand_count[qi];
     const int n = (int)(cnt < TK_MAX ? cnt : TK_MAX);
-    if (cnt > TK_MAX && threadIdx.x == 0) atomicOr(ix.status, kStatusTopkOverrun);
-    const int np2 = next_pow2(n > 1 ? n : 1);
+    const int tid = threadIdx.x;
+    if (cnt > TK_MAX && tid == 0) atomicOr(ix.status, kStatusTopkOverrun);
     const uint32_t* cand = a.cand + qi * a.kc;
     const float* cd = a.cdist + qi * a.kc;
-    for (int i = threadIdx.x; i < np2; i += blockDim.x)
-        keys[i] = i < n ? (((unsigned long long)f32_key(cd[i]) << 32) | cand[i]) : ~0ull;
+    int64_t* oid = a.out_ids + qi * a.k;
+    float* od = a.out_dists + qi * a.k;
+    for (int i = n + tid; i < a.k; i += blockDim.x) { oid[i] = -1; od[i] = INFINITY; }
+    if (n == 0) return;
+    if (tid == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_big = 0u; }
+    for (int i = tid; i < TK_BINS; i += blockDim.x) bins[i] = 0;
     __syncthreads();
-    cta_bitonic_u64(keys, np2);
-    for (int i = threadIdx.x; i < a.k; i += blockDim.x) {
-        int64_t id = -1;
-        float dv = INFINITY;
-        if (i < n) {
-            const unsigned long long kk = keys[i];
-            id = (int64_t)(kk & 0xFFFFFFFFull);
-            dv = key_f32((uint32_t)(kk >> 32));
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+    for (int i = tid; i < n; i += blockDim.x) {
+        const uint32_t kk = f32_key(cd[i]);
+        mn = min(mn, kk);
+        mx = max(mx, kk);
+    }
+    mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if (lane_id() == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
+    __syncthreads();
+    const uint32_t kmin = s_min;
+    const float scale = (float)TK_BINS / ((float)(s_max - kmin) + 1.0f);
+    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&bins[tk_bin(f32_key(cd[i]), kmin, scale)], 1u);
+    __syncthreads();
+    // exclusive scan of the bins: 4 consecutive bins per thread
+    constexpr int PER = TK_BINS / TK_THREADS;
+    uint32_t loc[PER], tot = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) { loc[j] = bins[tid * PER + j]; tot += loc[j]; }
+    const uint32_t winc = warp_incl_scan(tot);
+    if (lane_id() == 31) wsum[warp_id()] = winc;
+    __syncthreads();
+    if (warp_id() == 0) {
+        const uint32_t v = wsum[lane_id()];
+        wsum[lane_id()] = warp_incl_scan(v) - v;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp_id()] + winc - tot;
+    uint32_t big = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        bins[tid * PER + j] = run;        // start of bin; becomes its end after the scatter
+        run += loc[j];
+        big |= loc[j] > (uint32_t)TK_BIG ? 1u : 0u;
+    }
+    if (big) s_big = 1u;
+    __syncthreads();
+    if (s_big) {
+        // degenerate distribution: full bitonic sort of the n keys
+        const int np2 = next_pow2(n);
+        for (int i = tid; i < np2; i += blockDim.x)
+            keys[i] = i < n ? (((unsigned long long)f32_key(cd[i]) << 32) | cand[i]) : ~0ull;
+        __syncthreads();
+        cta_bitonic_u64(keys, np2);
+        for (int i = tid; i < a.k && i < n; i += blockDim.x) {
+            oid[i] = (int64_t)(keys[i] & 0xFFFFFFFFull);
+            od[i] = key_f32((uint32_t)(keys[i] >> 32));
         }
-        a.out_ids[qi * a.k + i] = id;
-        a.out_dists[qi * a.k + i] = dv;
+        return;
+    }
+    for (int i = tid; i < n; i += blockDim.x) {
+        const uint32_t kk = f32_key(cd[i]);
+        const uint32_t p = atomicAdd(&bins[tk_bin(kk, kmin, scale)], 1u);
+        keys[p] = ((unsigned long long)kk << 32) | cand[i];
+    }
+    __syncthreads();
+    for (int p = tid; p < n; p += blockDim.x) {
+        const unsigned long long me = keys[p];
+        const uint32_t b = tk_bin((uint32_t)(me >> 32), kmin, scale);
+        const int st = b ? (int)bins[b - 1] : 0;
+        const int en = (int)bins[b];
+        int rank = 0;
+        for (int j = st; j < en; ++j) rank += keys[j] < me ? 1 : 0;
+        const int pos = st + rank;
+        if (pos < a.k) {
+            oid[pos] = (int64_t)(me & 0xFFFFFFFFull);
+            od[pos] = key_f32((uint32_t)(me >> 32));
+        }
     }
 }
 
@@ -141,7 +325,8 @@ cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cud
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    topk_kernel<<<(unsigned)nq, TK_THREADS, smem, st>>>(ix, a);
+    (void)smem;
+    topk_kernel<<<(unsigned)nq, TK_THREADS, (size_t)TK_MAX * 8, st>>>(ix, a);
     return cudaGetLastError();
 }
 

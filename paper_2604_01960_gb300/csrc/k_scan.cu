@@ -25,7 +25,9 @@
 //
 // GPU mapping: one lane per vector; the lane's code row sits in registers
 // (coalesced 512-byte chunk loads); each LUT read goes to bank (lane + slot)
-// mod 32, so the 32 reads of a warp never conflict.  Appends are warp-
+// mod 32, so the 32 reads of a warp never conflict.  The region stores
+// (estimated distance, list position); positions become ids in k_select.cu,
+// so the hot loop never waits on an id load.  Appends are warp-
 // aggregated (ballot + one shared atomic per warp) into a contiguous region.
 #include <climits>
 
@@ -34,41 +36,71 @@
 
 namespace bbc {
 
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_CHUNK = 4;      // consecutive blocks per warp step
+constexpr int SCAN_THREADS = 512;
 
 template <int M, int BITS>
 struct ScanCfg {
     static constexpr int K = 1 << BITS;
-    static constexpr int W = M <= 32 ? 64 : M + 32;
+    // words per LUT row: >= M + 31 and a multiple of 32 (a power of two where that costs little)
+    static constexpr int W = M <= 32 ? 64 : (M <= 96 ? 128 : M + 32);
+    static constexpr int ROWB = W * 4;
     static constexpr int CB = M * BITS / 8;
     static constexpr int CBP = (CB + 15) / 16 * 16;
     static constexpr int NCH = CBP / 16;
     static constexpr int LUT_WORDS = K * W;
+    static constexpr int CHUNK = NCH <= 2 ? 4 : (NCH <= 4 ? 2 : 1);
 };
 
-template <int M, int BITS>
-__device__ __forceinline__ uint32_t adc_lane(const uint4 (&r)[ScanCfg<M, BITS>::NCH], const uint32_t* lutl) {
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int wi) {
+    return wi == 0 ? v.x : (wi == 1 ? v.y : (wi == 2 ? v.z : v.w));
+}
+
+// Shared-memory byte address of the LUT entry for code slot S of this lane,
+// without the slot's own offset 4 * S (added as the load's immediate):
+// code * ROWB + lane_base, lane_base = LUT base + 4 * lane.  For 8-bit codes
+// with 256-byte rows one byte permute yields code << 8 directly.
+template <int M, int BITS, int S>
+__device__ __forceinline__ uint32_t slot_addr(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane_base) {
     using C = ScanCfg<M, BITS>;
-    uint32_t e = 0;
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-        uint32_t code;
-        if (BITS == 8) {
-            const uint4 v = r[s >> 4];
-            const int wi = (s >> 2) & 3;
-            const uint32_t w = wi == 0 ? v.x : (wi == 1 ? v.y : (wi == 2 ? v.z : v.w));
-            code = (w >> (8 * (s & 3))) & 0xFFu;
-        } else {
-            const int byte = s >> 1;
-            const uint4 v = r[byte >> 4];
-            const int wi = (byte >> 2) & 3;
-            const uint32_t w = wi == 0 ? v.x : (wi == 1 ? v.y : (wi == 2 ? v.z : v.w));
-            code = (w >> (8 * (byte & 3) + 4 * (s & 1))) & 0xFu;
-        }
-        e += lutl[code * C::W + s];
+    if (BITS == 8) {
+        const uint32_t w = word_of(r[S >> 4], (S >> 2) & 3);
+        const uint32_t x = __byte_perm(w, 0u, 0x4404u | ((uint32_t)(S & 3) << 4));   // code << 8
+        if (C::ROWB == 256) return x + lane_base;
+        if (C::ROWB == 512) return (x << 1) + lane_base;
+        return (x >> 8) * (uint32_t)C::ROWB + lane_base;
+    } else {
+        const int byte = S >> 1;
+        const uint32_t w = word_of(r[byte >> 4], (byte >> 2) & 3);
+        const uint32_t code = (w >> (8 * (byte & 3) + 4 * (S & 1))) & 0xFu;
+        return code * (uint32_t)C::ROWB + lane_base;
     }
-    return e;
+}
+
+template <int OFF>
+__device__ __forceinline__ uint32_t lds(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+
+template <int M, int BITS, int S>
+struct AdcUnroll {
+    static __device__ __forceinline__ uint32_t run(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane_base) {
+        // two lookups per step, summed with one three-input add
+        const uint32_t v0 = lds<4 * S>(slot_addr<M, BITS, S>(r, lane_base));
+        const uint32_t v1 = lds<4 * (S + 1)>(slot_addr<M, BITS, S + 1>(r, lane_base));
+        return v0 + v1 + AdcUnroll<M, BITS, S + 2>::run(r, lane_base);
+    }
+};
+template <int M, int BITS>
+struct AdcUnroll<M, BITS, M> {
+    static __device__ __forceinline__ uint32_t run(const uint4 (&)[ScanCfg<M, BITS>::NCH], uint32_t) { return 0u; }
+};
+
+// Estimated distance of this lane's vector: sum over sub-spaces of its LUT entries.
+template <int M, int BITS>
+__device__ __forceinline__ uint32_t adc_lane(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane_base) {
+    return AdcUnroll<M, BITS, 0>::run(r, lane_base);
 }
 
 // Update on the shared bucket counts by one warp: first bucket whose running
@@ -126,11 +158,12 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
     const int P = a.nprobe;
     const unsigned ln = lane_id();
     const int nw = blockDim.x >> 5;
-    const uint32_t* lutl = lut + ln;
+    const uint32_t lane_base = (uint32_t)__cvta_generic_to_shared(lut) + 4u * ln;
     uint2* region = a.region + qi * a.cap;
     const unsigned lt_mask = (1u << ln) - 1u;
-    for (int cb = g0 + (int)warp_id() * SCAN_CHUNK; cb < g1; cb += nw * SCAN_CHUNK) {
-        const int ge = min(cb + SCAN_CHUNK, g1);
+    constexpr int CH = C::CHUNK;
+    for (int cb = g0 + (int)warp_id() * CH; cb < g1; cb += nw * CH) {
+        const int ge = min(cb + CH, g1);
         // list holding block cb: largest j with lpre[j] <= cb
         int lo = 0, hi = P - 1;
         while (lo < hi) {
@@ -138,10 +171,10 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
             if (lpre[mid] <= cb) lo = mid; else hi = mid - 1;
         }
         int j = lo;
-        int gbk[SCAN_CHUNK], nval[SCAN_CHUNK];
-        uint4 r[SCAN_CHUNK][C::NCH];
+        int gbk[CH], nval[CH];
+        uint4 r[CH][C::NCH];
 #pragma unroll
-        for (int u = 0; u < SCAN_CHUNK; ++u) {
+        for (int u = 0; u < CH; ++u) {
             const int g = cb + u;
             gbk[u] = -1;
             nval[u] = 0;
@@ -159,9 +192,9 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
         const uint32_t dmin = S.dmin;
         const int sh = S.sh;
 #pragma unroll
-        for (int u = 0; u < SCAN_CHUNK; ++u) {
+        for (int u = 0; u < CH; ++u) {
             if (gbk[u] < 0) continue;
-            const uint32_t e = adc_lane<M, BITS>(r[u], lutl);
+            const uint32_t e = adc_lane<M, BITS>(r[u], lane_base);
             const bool valid = (int)ln < nval[u];
             bool push;
             uint32_t bk = 0;
@@ -180,14 +213,13 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 if (push) {
                     const uint32_t pos = base + (uint32_t)__popc(bal & lt_mask);
-                    const uint32_t id = __ldg(ix.ids + (size_t)gbk[u] * 32 + ln);
-                    if ((int64_t)pos < a.cap) region[pos] = make_uint2(e, id);
+                    if ((int64_t)pos < a.cap) region[pos] = make_uint2(e, (uint32_t)gbk[u] * 32u + ln);
                     else atomicOr(ix.status, kStatusRegionOverrun);
                     if (MAIN) atomicAdd(&S.hist[bk], 1u);
                 }
             }
         }
-        if (MAIN) {
+        if (MAIN && (((cb - g0) / (nw * CH)) & 1) == 0) {
             const uint32_t t = warp_update(S.hist, a.m, a.kc);
             if (ln == 0 && t < *(volatile uint32_t*)&S.tau) atomicMin(&S.tau, t);
         }
@@ -195,7 +227,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
 }
 
 template <int M, int BITS>
-__global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(DevIndex ix, ScanArgs a) {
+__global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, ScanArgs a) {
     using C = ScanCfg<M, BITS>;
     extern __shared__ uint4 dsm[];
     uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
@@ -284,9 +316,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(DevIndex ix, ScanArg
         __syncthreads();
         const uint32_t dmin = S.dmin;
         const int sh = S.sh;
-        for (int64_t i = tid; i < ns; i += bs) {
-            const uint32_t e = region[i].x;
-            if (e <= dmax) atomicAdd(&S.ehist[bin_of(e, dmin, sh)], 1u);
+        for (int64_t i = tid; i < ns; i += 4 * bs) {
+            uint32_t e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0xFFFFFFFFu;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * bs < ns && e[u] <= dmax) atomicAdd(&S.ehist[bin_of(e[u], dmin, sh)], 1u);
         }
         __syncthreads();
         if (warp_id() == 0) {
@@ -305,7 +341,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(DevIndex ix, ScanArg
             }
         }
         __syncthreads();
-        for (int64_t i = tid; i < ns; i += bs) atomicAdd(&S.hist[S.bmap[bin_of(region[i].x, dmin, sh)]], 1u);
+        for (int64_t i = tid; i < ns; i += 4 * bs) {
+            uint32_t e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * bs < ns) atomicAdd(&S.hist[S.bmap[bin_of(e[u], dmin, sh)]], 1u);
+        }
         __syncthreads();
         if (warp_id() == 0) {
             const uint32_t t0 = warp_update(S.hist, a.m, a.kc);

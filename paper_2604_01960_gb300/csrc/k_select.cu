@@ -8,6 +8,9 @@
 // tau*, found by a radix select on the 64-bit key (e << 32 | id).  When fewer
 // than K_c objects were scanned, all of them are candidates.
 //
+// The region holds (e, list position); ids[position] gives the vector id, which
+// is looked up only for the K_c winners and the threshold-bucket objects.
+//
 // Why this is the exact top-K_c by (e, id): bucket ids are a monotone
 // function of e, and an object is dropped during the scan only when its
 // bucket exceeds the current tau, which never falls below tau*; so every
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
     const unsigned lt_mask = (1u << ln) - 1u;
     if (tau >= m) {
         // fewer than K_c objects: all appended objects are candidates
-        for (int64_t i = tid; i < n && i < a.kc; i += bs) cand[i] = region[i].y;
+        for (int64_t i = tid; i < n && i < a.kc; i += bs) cand[i] = ix.ids[region[i].y];
         if (tid == 0) {
             a.cand_count[qi] = n < a.kc ? n : a.kc;
             st.tau = tau;
@@ -88,27 +91,35 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
     }
     const uint32_t nt = st.hist[tau];
     const bool in_smem = nt <= (uint32_t)SELK_TCAP;
-    // pass 1: buckets < tau* go straight out; bucket tau* is staged
-    for (int64_t i0 = 0; i0 < n; i0 += bs) {
-        const int64_t i = i0 + tid;
-        uint2 v = make_uint2(0, 0);
-        uint32_t b = 0xFFFFFFFFu;
-        if (i < n) {
-            v = region[i];
-            b = sel_bucket(v.x, st, map);
+    // pass 1: buckets < tau* go straight out; bucket tau* is staged.  Four
+    // entries per thread per step, their id gathers issued together.
+    constexpr int SU = 4;
+    for (int64_t i0 = 0; i0 < n; i0 += (int64_t)SU * bs) {
+        uint2 v[SU];
+        uint32_t b[SU], idv[SU];
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int64_t i = i0 + (int64_t)u * bs + tid;
+            v[u] = i < n ? region[i] : make_uint2(0, 0);
+            b[u] = i < n ? sel_bucket(v[u].x, st, map) : 0xFFFFFFFFu;
         }
-        const bool take = b < (uint32_t)tau;
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
-        if (bal) {
-            uint32_t base = 0;
-            if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            const uint32_t pos = base + __popc(bal & lt_mask);
-            if (take && (int64_t)pos < a.kc) cand[pos] = v.y;
-        }
-        if (in_smem && b == (uint32_t)tau) {
-            const uint32_t p = atomicAdd(&s_t, 1u);
-            if (p < (uint32_t)SELK_TCAP) tkeys[p] = ((unsigned long long)v.x << 32) | v.y;
+#pragma unroll
+        for (int u = 0; u < SU; ++u) idv[u] = b[u] <= (uint32_t)tau ? ix.ids[v[u].y] : 0u;
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const bool take = b[u] < (uint32_t)tau;
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
+            if (bal) {
+                uint32_t base = 0;
+                if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                const uint32_t pos = base + __popc(bal & lt_mask);
+                if (take && (int64_t)pos < a.kc) cand[pos] = idv[u];
+            }
+            if (in_smem && b[u] == (uint32_t)tau) {
+                const uint32_t p = atomicAdd(&s_t, 1u);
+                if (p < (uint32_t)SELK_TCAP) tkeys[p] = ((unsigned long long)v[u].x << 32) | idv[u];
+            }
         }
     }
     __syncthreads();
@@ -133,7 +144,7 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
         // large threshold bucket: select straight from the region (read-only passes)
         kth = cta_select_u64(n, s - 1, [&](int64_t i) {
             const uint2 v = region[i];
-            return sel_bucket(v.x, st, map) == (uint32_t)tau ? (((unsigned long long)v.x << 32) | v.y) : ~0ull;
+            return sel_bucket(v.x, st, map) == (uint32_t)tau ? (((unsigned long long)v.x << 32) | ix.ids[v.y]) : ~0ull;
         }, hist, sc, 56);
         for (int64_t i0 = 0; i0 < n; i0 += bs) {
             const int64_t i = i0 + tid;
@@ -141,9 +152,10 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
             uint32_t id = 0;
             if (i < n) {
                 const uint2 v = region[i];
-                take = sel_bucket(v.x, st, map) == (uint32_t)tau &&
-                       (((unsigned long long)v.x << 32) | v.y) <= kth;
-                id = v.y;
+                if (sel_bucket(v.x, st, map) == (uint32_t)tau) {
+                    id = ix.ids[v.y];
+                    take = (((unsigned long long)v.x << 32) | id) <= kth;
+                }
             }
             const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
             if (bal) {

@@ -65,14 +65,56 @@ def test_lut16_bit_exact(bbc, oracle_lib, kind):
         assert np.array_equal(got[i], ref), f"query {i}"
 
 
+def _probe_eps(d, qn, cm, metric, tc):
+    """The pruning bound the selection kernel uses for the approximate scores."""
+    if not tc:
+        return (d + 4) * 2.0 ** -22 * (qn + cm) ** 2
+    rel = 3.1 * 2.0 ** -16 + 3.06 * d * 2.0 ** -23
+    if metric == "l2":
+        return 2.0 * (2.0 * rel * qn * cm + 2.0 ** -23 * (cm * cm + 2.0 * qn * cm))
+    return 2.0 * (rel * qn * cm + 2.0 ** -24 * qn * cm)
+
+
+@pytest.mark.parametrize("tc", [1, 0])
+@pytest.mark.parametrize("kind", ["tiny", "sift", "embed", "ragged"])
+def test_probe_scores_within_bound(bbc, kind, tc):
+    """Approximate scores (tensor-core BF16 split GEMM, or FP32) lie within the
+    stated bound of the FP64 score minus ||q||^2."""
+    h, idx, q = dev_index(bbc, kind)
+    bbc.bbc_set_param(h, "probe_gemm", tc)
+    try:
+        nq = len(q)
+        out = torch.empty((nq, idx.nlist), dtype=torch.float32, device="cuda")
+        bbc.bbc_probe_scores(h, cuda(q), nq, out)
+        sync_ok(bbc, h)
+    finally:
+        bbc.bbc_set_param(h, "probe_gemm", 1)
+    a = out.cpu().numpy().astype(np.float64)
+    c = idx.centroids.astype(np.float64)
+    cm = np.sqrt((c * c).sum(1)).max()
+    for i in range(nq):
+        qq = q[i].astype(np.float64)
+        if idx.metric == "l2":
+            ref = ((c - qq) ** 2).sum(1) - (qq * qq).sum()
+        else:
+            ref = -(c @ qq)
+        eps = _probe_eps(idx.d, np.sqrt((qq * qq).sum()), cm, idx.metric, tc)
+        assert np.abs(a[i] - ref).max() <= eps, (i, np.abs(a[i] - ref).max(), eps)
+
+
+@pytest.mark.parametrize("tc", [1, 0])
 @pytest.mark.parametrize("kind,nprobe", [("tiny", 1), ("tiny", 13), ("sift", 32), ("embed", 48),
                                          ("ragged", 40), ("sift4", 64)])
-def test_probe_exact_order(bbc, oracle_lib, kind, nprobe):
+def test_probe_exact_order(bbc, oracle_lib, kind, nprobe, tc):
     h, idx, q = dev_index(bbc, kind)
     nq = len(q)
     out = torch.empty((nq, nprobe), dtype=torch.int32, device="cuda")
-    bbc.bbc_probe(h, cuda(q), nq, nprobe, out)
-    sync_ok(bbc, h)
+    bbc.bbc_set_param(h, "probe_gemm", tc)
+    try:
+        bbc.bbc_probe(h, cuda(q), nq, nprobe, out)
+        sync_ok(bbc, h)
+    finally:
+        bbc.bbc_set_param(h, "probe_gemm", 1)
     got = out.cpu().numpy()
     for i in range(nq):
         ref, _ = oracle_lib.probe(q[i], idx.centroids, nprobe, idx.metric)
