@@ -9,6 +9,7 @@
 //     with no fused multiply-add.  Approximate scores only prune and order;
 //     FP64 decides wherever the approximations cannot (see the kernel).
 #include <cfloat>
+#include <algorithm>
 #include <cmath>
 
 #include "bbc_internal.cuh"
@@ -106,11 +107,40 @@ __device__ double exact_score(const float* __restrict__ q, const float* __restri
     return s;
 }
 
+// Double-FP32 ("float-float") helpers: a value is hi + lo with |lo| <= ulp(hi)/2.
+// TwoSum and the FMA-based TwoProd are error-free, so sums of exact products
+// keep about 44 bits; intrinsics keep the compiler from contracting them.
+struct ff { float hi, lo; };
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, err};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = two_sum(x.hi, y.hi);
+    const float lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return two_sum(s.hi, lo);
+}
+// exact square of a difference of two floats, as a float-float plus residue
+__device__ __forceinline__ ff ff_sqdiff(float a, float b) {
+    const ff t = two_sum(a, -b);                        // a - b = t.hi + t.lo exactly
+    const float p = __fmul_rn(t.hi, t.hi);
+    const float pe = __fmaf_rn(t.hi, t.hi, -p);         // t.hi^2 = p + pe exactly
+    const float cross = __fmul_rn(__fmul_rn(2.f, t.hi), t.lo);
+    return two_sum(p, __fadd_rn(pe, cross));            // drops t.lo^2 (< 2^-48 (a-b)^2)
+}
+__device__ __forceinline__ ff ff_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
 // Selection in three steps: (1) the approximate GEMM scores prune to every
 // list that can still reach the nprobe-th; (2) those lists are re-scored in
-// FP32 and sorted; (3) any run of neighbours whose FP32 scores are too close
-// for the FP32 error bound to order them is re-scored in FP64 and re-sorted
-// by (FP64 score, list id).  Lists outside runs are provably in exact order,
+// float-float arithmetic (about 2^-38 relative) and sorted; (3) any run of
+// neighbours whose re-scores are too close for that bound to order them is
+// re-scored in FP64 and re-sorted by (FP64 score, list id).  FP64 is slow on
+// this GPU, so it is kept to genuine near-ties.  Lists outside runs are provably in exact order,
 // so the result equals sorting every list by its FP64 score.
 __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, const float* __restrict__ q,
                                                                     int nprobe,
@@ -121,7 +151,6 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
     unsigned long long* ckey = psm;                                  // [SEL_MAXC]
     uint32_t* cval = (uint32_t*)(ckey + SEL_MAXC);                   // [SEL_MAXC]
     uint32_t* keys = cval + SEL_MAXC;                                // [L]
-    float* fsc = (float*)keys;                                       // reuses keys after step 1
     __shared__ uint32_t hist[256];
     __shared__ uint32_t sc[2];
     __shared__ float red[SEL_THREADS / 32];
@@ -176,8 +205,9 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
         if (threadIdx.x == 0) atomicOr(ix.status, kStatusSelectOverrun);
         nc = SEL_MAXC;
     }
-    // step 2: FP32 re-score (one warp per list, lanes over dimensions, so the
-    // centroid rows are read coalesced) and sort by (FP32 score, list id)
+    // step 2: near-exact re-score in float-float arithmetic (one warp per list,
+    // lanes over dimensions, so centroid rows are read coalesced), then sort by
+    // (score, list id).
     const int np2 = next_pow2(nc);
     for (int i = nc + threadIdx.x; i < np2; i += blockDim.x) {
         ckey[i] = ~0ull;
@@ -185,38 +215,41 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
     }
     for (int i = warp_id(); i < nc; i += blockDim.x / 32) {
         const float* cr = ix.centroids + (int64_t)cval[i] * d;
-        float part = 0.f;
-        if (ix.metric == BBC_METRIC_L2) {
-            for (int j = lane_id(); j < d; j += 32) {
-                const float t = qv[j] - cr[j];
-                part = fmaf(t, t, part);
-            }
-        } else {
-            for (int j = lane_id(); j < d; j += 32) part = fmaf(qv[j], cr[j], part);
+        ff part = {0.f, 0.f};
+        for (int j = lane_id(); j < d; j += 32)
+            part = ff_add(part, ix.metric == BBC_METRIC_L2 ? ff_sqdiff(qv[j], cr[j]) : ff_prod(qv[j], cr[j]));
+        for (int o = 16; o; o >>= 1) {
+            const ff other = {__shfl_xor_sync(0xFFFFFFFFu, part.hi, o), __shfl_xor_sync(0xFFFFFFFFu, part.lo, o)};
+            part = ff_add(part, other);
         }
-        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-        const float f = ix.metric == BBC_METRIC_L2 ? part : -part;
+        const double f = ix.metric == BBC_METRIC_L2 ? (double)part.hi + (double)part.lo
+                                                    : -((double)part.hi + (double)part.lo);
         if (lane_id() == 0) {
-            ckey[i] = (unsigned long long)f32_key(f);
-            atomicMax((int*)&s_fmax, __float_as_int(fabsf(f)));       // non-negative floats order as ints
+            ckey[i] = f64_key(f);
+            atomicMax((int*)&s_fmax, __float_as_int(fabsf(part.hi)));   // non-negative floats order as ints
         }
     }
     __syncthreads();
     cta_bitonic_kv(ckey, cval, np2);
-    // step 3: FP32 error bound (any summation order), uniform over the candidates:
-    //   L2: sum of squares, |f - s| <= (d + 2) 2^-24 max f;
-    //   IP: |f - s| <= (d + 2) 2^-24 ||q|| max ||c||;  safety factor 2.
-    const double e32 = (double)(d + 4) * ldexp(1.0, -23) *
-                       (ix.metric == BBC_METRIC_L2 ? (double)s_fmax : qn * cm) + 1e-30;
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) fsc[i] = key_f32((uint32_t)ckey[i]);
+    // step 3: bound on |re-score - FP64 score|, uniform over the candidates.
+    // Float-float accumulation of d exact (or 2^-47-accurate) terms loses at
+    // most about (d + 8) 2^-45 of sum |terms|; the FP64 sequential sum itself
+    // is within d 2^-53 of the real value.  Safety factor 4.
+    //   L2: sum |terms| = the score (max over candidates, +1 ulp for hi);
+    //   IP: sum |terms| <= ||q|| max ||c||.
+    const double base = ix.metric == BBC_METRIC_L2 ? (double)s_fmax * (1.0 + ldexp(1.0, -20)) : qn * cm;
+    const double e32 = 4.0 * ((double)(d + 8) * ldexp(1.0, -45) + (double)d * ldexp(1.0, -53)) * base + 1e-300;
+    // link[i]: lists i and i+1 (in re-score order) are too close to order
+    // without FP64.  Flags are computed before any run is rewritten.
+    uint8_t* link = reinterpret_cast<uint8_t*>(keys);
+    for (int i = threadIdx.x; i < nc; i += blockDim.x)
+        link[i] = (i + 1 < nc && key_f64(ckey[i + 1]) - key_f64(ckey[i]) <= 2.0 * e32) ? 1 : 0;
     __syncthreads();
     for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-        const bool link_prev = i > 0 && (double)fsc[i] - (double)fsc[i - 1] <= 2.0 * e32;
-        const bool link_next = i + 1 < nc && (double)fsc[i + 1] - (double)fsc[i] <= 2.0 * e32;
-        if (!link_prev && link_next) {
+        if ((i == 0 || !link[i - 1]) && link[i]) {
             // run [i, j]: exact FP64 scores, insertion sort by (score, list id)
             int j = i + 1;
-            while (j + 1 < nc && (double)fsc[j + 1] - (double)fsc[j] <= 2.0 * e32) ++j;
+            while (j < nc - 1 && link[j]) ++j;
             for (int t = i; t <= j; ++t)
                 ckey[t] = f64_key(exact_score(qv, ix.centroids + (int64_t)cval[t] * d, d, ix.metric));
             for (int t = i + 1; t <= j; ++t) {
