@@ -130,6 +130,16 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* value);
 int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe,
                int64_t* out_ids, float* out_dists, void* stream);
 
+/* Mixed batch (batched form with uneven shapes): query q has its own k[q]
+ * and nprobe[q] (HOST arrays of nq int32, k[q] >= 1, 1 <= nprobe[q] <= nlist)
+ * and K_c = max(k[q], ceil(kc_ratio * k[q])).  Results are packed in query
+ * order: query q's k[q] results start at sum_{j<q} k[j] in out_ids / out_dists
+ * (device arrays holding sum k entries).  Each query's results are identical
+ * to those of a bbc_search call for that query alone.  Asynchronous on
+ * `stream` (the small per-query tables are copied from host memory). */
+int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t* k, const int32_t* nprobe,
+                  int64_t* out_ids, float* out_dists, void* stream);
+
 /* Same as bbc_search with HOST query and output buffers: copies the queries
  * to the device, searches, copies the results back, and synchronises
  * `stream` before returning. */

@@ -28,7 +28,7 @@ METRICS = {"l2": 0, "ip": 1}
 
 # Exported symbols declared in include/bbc.h (checked by the ABI test).
 SYMBOLS = ["bbc_index_create", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
-           "bbc_get_param", "bbc_search", "bbc_search_host", "bbc_probe_scores", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
+           "bbc_get_param", "bbc_search", "bbc_search_ex", "bbc_search_host", "bbc_probe_scores", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
            "bbc_rerank_topk", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
 NUM_STAGES = 7
 STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk"]
@@ -95,6 +95,7 @@ def lib():
             L.bbc_get_param.argtypes = [vp, C.c_char_p, C.POINTER(C.c_double)]
             L.bbc_search.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp]
             L.bbc_search_host.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp]
+            L.bbc_search_ex.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
             L.bbc_probe.argtypes = [vp, vp, i64, i32, vp, vp]
             L.bbc_probe_scores.argtypes = [vp, vp, i64, vp, vp]
             L.bbc_lut.argtypes = [vp, vp, i64, vp, vp]
@@ -182,6 +183,14 @@ def bbc_get_param(handle: int, key: str) -> float:
 
 def bbc_search(handle: int, queries, nq: int, k: int, nprobe: int, out_ids, out_dists, stream=None) -> None:
     _check(lib().bbc_search(handle, _ptr(queries), nq, k, nprobe, _ptr(out_ids), _ptr(out_dists), _stream(stream)))
+
+
+def bbc_search_ex(handle: int, queries, nq: int, k, nprobe, out_ids, out_dists, stream=None) -> None:
+    """Mixed batch: k and nprobe are host int32 arrays of length nq; outputs packed by prefix sums of k."""
+    ka = np.ascontiguousarray(k, dtype=np.int32)
+    pa = np.ascontiguousarray(nprobe, dtype=np.int32)
+    _check(lib().bbc_search_ex(handle, _ptr(queries), nq, ka.ctypes.data, pa.ctypes.data, _ptr(out_ids),
+                               _ptr(out_dists), _stream(stream)))
 
 
 def bbc_search_host(handle: int, queries, nq: int, k: int, nprobe: int, out_ids, out_dists, stream=None) -> None:

@@ -135,16 +135,49 @@ int upload(bbc_index* ix, const T* h, size_t count, T** out) {
     return BBC_OK;
 }
 
-// Workspace arena for one chunk of queries.
+// Workspace arena for one chunk of queries.  Sizes come from per-chunk sums so
+// that uniform and mixed (per-query k / nprobe) batches share one layout.
+struct ChunkShape {
+    int64_t nq = 0;
+    int64_t sum_probe = 0, sum_cap = 0, sum_kc = 0, sum_k = 0;
+    int max_probe = 0;
+    int64_t max_kc = 0;
+    bool host_io = false;
+    bool mixed = false;
+};
+
 struct Plan {
-    int64_t chunk;        // queries per chunk
+    int64_t chunk;        // queries per chunk (uniform batches)
     int nprobe;
     int64_t kc;
     int k;
     int64_t cap;
     size_t off_scores, off_probe, off_lut, off_state, off_region, off_cand, off_count, off_cdist,
-        off_q, off_ids, off_dists, off_abf, total;
+        off_q, off_ids, off_dists, off_abf, off_keys, off_params, total;
 };
+
+constexpr int64_t kTopkSmemMax = 16384;     // K_c handled by the shared-memory top-k
+
+size_t layout(const bbc_index* ix, const ChunkShape& c, Plan& p) {
+    const DevIndex& d = ix->dev;
+    size_t o = 0;
+    p.off_scores = o; o = align_up(o + (size_t)c.nq * d.nlist * 4);
+    p.off_probe = o; o = align_up(o + (size_t)c.sum_probe * 4);
+    p.off_lut = o; o = align_up(o + (size_t)c.nq * d.M * d.K * 2);
+    p.off_state = o; o = align_up(o + (size_t)c.nq * sizeof(bbc_collector_state));
+    p.off_region = o; o = align_up(o + (size_t)c.sum_cap * 8);
+    p.off_cand = o; o = align_up(o + (size_t)c.sum_kc * 4);
+    p.off_count = o; o = align_up(o + (size_t)c.nq * 8);
+    p.off_cdist = o; o = align_up(o + (size_t)c.sum_kc * 4);
+    p.off_q = o; o = align_up(o + (c.host_io ? (size_t)c.nq * d.d * 4 : 0));
+    p.off_ids = o; o = align_up(o + (c.host_io ? (size_t)c.sum_k * 8 : 0));
+    p.off_dists = o; o = align_up(o + (c.host_io ? (size_t)c.sum_k * 4 : 0));
+    p.off_abf = o; o = align_up(o + (ix->probe_gemm ? probe_tc_workspace(d, c.nq) : 0));
+    p.off_keys = o; o = align_up(o + (c.max_kc > kTopkSmemMax ? (size_t)c.sum_kc * 8 : 0));
+    p.off_params = o; o = align_up(o + (c.mixed ? (size_t)(c.nq + 1) * 8 * 7 : 0));
+    p.total = o;
+    return o;
+}
 
 Plan make_plan(const bbc_index* ix, int64_t nq, int nprobe, int64_t kc, int k, bool host_io) {
     Plan p{};
@@ -152,28 +185,18 @@ Plan make_plan(const bbc_index* ix, int64_t nq, int nprobe, int64_t kc, int k, b
     p.kc = kc;
     p.k = k;
     p.cap = ix->cap_prefix[nprobe];
-    const DevIndex& d = ix->dev;
-    auto per_query = [&](int64_t c) {
-        size_t o = 0;
-        p.off_scores = o; o = align_up(o + (size_t)c * d.nlist * 4);
-        p.off_probe = o; o = align_up(o + (size_t)c * nprobe * 4);
-        p.off_lut = o; o = align_up(o + (size_t)c * d.M * d.K * 2);
-        p.off_state = o; o = align_up(o + (size_t)c * sizeof(bbc_collector_state));
-        p.off_region = o; o = align_up(o + (size_t)c * p.cap * 8);
-        p.off_cand = o; o = align_up(o + (size_t)c * kc * 4);
-        p.off_count = o; o = align_up(o + (size_t)c * 8);
-        p.off_cdist = o; o = align_up(o + (size_t)c * kc * 4);
-        p.off_q = o; o = align_up(o + (host_io ? (size_t)c * d.d * 4 : 0));
-        p.off_ids = o; o = align_up(o + (host_io ? (size_t)c * k * 8 : 0));
-        p.off_dists = o; o = align_up(o + (host_io ? (size_t)c * k * 4 : 0));
-        p.off_abf = o; o = align_up(o + (ix->probe_gemm ? probe_tc_workspace(d, c) : 0));
-        return o;
+    auto shape = [&](int64_t c) {
+        ChunkShape s;
+        s.nq = c; s.sum_probe = c * nprobe; s.sum_cap = c * p.cap; s.sum_kc = c * kc; s.sum_k = c * k;
+        s.max_probe = nprobe; s.max_kc = kc; s.host_io = host_io;
+        return s;
     };
     const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
     int64_t c = std::max<int64_t>(1, nq);
-    while (c > 1 && per_query(c) > budget) c = (c + 1) / 2;
+    Plan tmp = p;
+    while (c > 1 && layout(ix, shape(c), tmp) > budget) c = (c + 1) / 2;
     p.chunk = c;
-    p.total = per_query(c);
+    layout(ix, shape(c), p);
     return p;
 }
 
@@ -238,8 +261,10 @@ cudaError_t stage(bbc_index* ix, int id, cudaStream_t st, F&& launch) {
 int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc, int64_t* out_ids,
               float* out_dists, cudaStream_t st, int stop_after /* 9 = all */,
               int32_t* probe_out = nullptr, const int32_t* probe_in = nullptr, uint32_t* cand_out = nullptr,
-              int64_t* count_out = nullptr, bbc_collector_state* state_out = nullptr) {
+              int64_t* count_out = nullptr, bbc_collector_state* state_out = nullptr,
+              const QueryParams* qp_in = nullptr) {
     const DevIndex& d = ix->dev;
+    const QueryParams qp = qp_in ? *qp_in : uniform_params(p.nprobe, p.kc, p.k, p.cap);
     float* scores = reinterpret_cast<float*>(ws + p.off_scores);
     int32_t* probe = probe_out ? probe_out : reinterpret_cast<int32_t*>(ws + p.off_probe);
     uint16_t* lut = reinterpret_cast<uint16_t*>(ws + p.off_lut);
@@ -254,19 +279,20 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
         else
             CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores(d, q, nc, scores, st); }));
         CUDA_TRY(stage(ix, 1, st, [&] {
-            return launch_probe_select(d, q, nc, p.nprobe, scores, probe, ix->probe_gemm, st);
+            return launch_probe_select(d, q, nc, qp, p.nprobe, scores, probe, ix->probe_gemm, st);
         }));
     }
     if (stop_after <= 2) return BBC_OK;
     CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(d, q, nc, lut, st); }));
     ScanArgs sa{lut, probe_in ? probe_in : probe, p.nprobe, p.kc, ix->buckets, ix->sample_lists,
-                region, p.cap, state};
+                region, p.cap, state, qp};
     CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan(d, nc, sa, st); }));
-    SelectArgs se{region, p.cap, state, p.kc, cand, count, nullptr};
+    SelectArgs se{region, p.cap, state, p.kc, cand, count, nullptr, qp};
     CUDA_TRY(stage(ix, 4, st, [&] { return launch_select(d, nc, se, st); }));
     if (stop_after <= 7) return BBC_OK;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + p.off_keys);
     RerankArgs ra{q, cand, count, p.kc, ix->rerank_u8 && d.vec_u8 != nullptr, cdist, p.k, out_ids,
-                  out_dists, nullptr};
+                  out_dists, p.kc > kTopkSmemMax ? keys : nullptr, qp};
     CUDA_TRY(stage(ix, 5, st, [&] { return launch_rerank(d, nc, ra, st); }));
     CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(d, nc, ra, st); }));
     return BBC_OK;
@@ -530,7 +556,7 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     int rc = check_search_args(ix, queries, nq, k, nprobe, out_ids, out_dists);
     if (rc) return rc;
     const int64_t kc = kc_for(ix, k);
-    if (kc > 16384) return fail(BBC_ERR_UNSUPPORTED, "K_c=%lld above 16384 is not supported yet", (long long)kc);
+    if (kc > (int64_t)0x7FFFFFFF) return fail(BBC_ERR_ARG, "K_c too large");
     if (nq == 0) return BBC_OK;
     DeviceGuard g(ix->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -545,12 +571,97 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     return BBC_OK;
 }
 
+int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t* k, const int32_t* nprobe,
+                  int64_t* out_ids, float* out_dists, void* stream) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    if (nq < 0) return fail(BBC_ERR_ARG, "nq < 0");
+    if (nq == 0) return BBC_OK;
+    if (!queries || !k || !nprobe || !out_ids || !out_dists) return fail(BBC_ERR_ARG, "null buffer");
+    for (int64_t q = 0; q < nq; ++q) {
+        if (k[q] < 1) return fail(BBC_ERR_ARG, "k[%lld] = %d must be >= 1", (long long)q, k[q]);
+        if (nprobe[q] < 1 || nprobe[q] > ix->dev.nlist)
+            return fail(BBC_ERR_ARG, "nprobe[%lld] = %d outside [1, %d]", (long long)q, nprobe[q], ix->dev.nlist);
+        if (nprobe[q] > 2048) return fail(BBC_ERR_UNSUPPORTED, "nprobe %d > 2048", nprobe[q]);
+    }
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
+    int64_t out_base = 0;
+    for (int64_t q0 = 0; q0 < nq;) {
+        // greedy chunk: add queries while the workspace fits
+        ChunkShape sh;
+        sh.mixed = true;
+        Plan p{};
+        int64_t q1 = q0;
+        while (q1 < nq) {
+            ChunkShape t = sh;
+            const int64_t kc = kc_for(ix, k[q1]);
+            t.nq += 1; t.sum_probe += nprobe[q1]; t.sum_cap += ix->cap_prefix[nprobe[q1]]; t.sum_kc += kc;
+            t.sum_k += k[q1]; t.max_probe = std::max(t.max_probe, nprobe[q1]); t.max_kc = std::max(t.max_kc, kc);
+            Plan tp{};
+            if (q1 > q0 && layout(ix, t, tp) > budget) break;
+            sh = t;
+            ++q1;
+        }
+        const int64_t nc = q1 - q0;
+        layout(ix, sh, p);
+        int maxk = 0;
+        int64_t maxcap = 0;
+        // per-query tables: nprobe i32, k i32, kc i64, then four i64 offset arrays of nc + 1
+        const size_t n8 = (size_t)nc + 1;
+        std::vector<int64_t> tab(n8 * 7, 0);
+        int32_t* t_np = reinterpret_cast<int32_t*>(tab.data());
+        int32_t* t_k = reinterpret_cast<int32_t*>(tab.data() + n8);
+        int64_t* t_kc = tab.data() + 2 * n8;
+        int64_t* t_po = tab.data() + 3 * n8;
+        int64_t* t_ro = tab.data() + 4 * n8;
+        int64_t* t_co = tab.data() + 5 * n8;
+        int64_t* t_oo = tab.data() + 6 * n8;
+        for (int64_t i = 0; i < nc; ++i) {
+            const int64_t q = q0 + i;
+            t_np[i] = nprobe[q];
+            t_k[i] = k[q];
+            t_kc[i] = kc_for(ix, k[q]);
+            t_po[i + 1] = t_po[i] + nprobe[q];
+            t_ro[i + 1] = t_ro[i] + ix->cap_prefix[nprobe[q]];
+            t_co[i + 1] = t_co[i] + t_kc[i];
+            t_oo[i + 1] = t_oo[i] + k[q];
+            maxk = std::max(maxk, k[q]);
+            maxcap = std::max(maxcap, ix->cap_prefix[nprobe[q]]);
+        }
+        char* ws;
+        int rc = get_workspace(ix, st, p.total, &ws);
+        if (rc) return rc;
+        int64_t* dtab = reinterpret_cast<int64_t*>(ws + p.off_params);
+        CUDA_TRY(cudaMemcpyAsync(dtab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, st));
+        QueryParams qp{};
+        qp.nprobe = sh.max_probe; qp.kc = sh.max_kc; qp.k = maxk; qp.cap = maxcap;
+        qp.nprobe_q = reinterpret_cast<const int32_t*>(dtab);
+        qp.k_q = reinterpret_cast<const int32_t*>(dtab + n8);
+        qp.kc_q = dtab + 2 * n8;
+        qp.probe_off = dtab + 3 * n8;
+        qp.region_off = dtab + 4 * n8;
+        qp.cand_off = dtab + 5 * n8;
+        qp.out_off = dtab + 6 * n8;
+        p.nprobe = sh.max_probe;
+        p.kc = sh.max_kc;
+        p.k = maxk;
+        p.cap = maxcap;
+        rc = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, out_ids + out_base, out_dists + out_base, st, 9,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, &qp);
+        if (rc) return rc;
+        out_base += t_oo[nc];
+        q0 = q1;
+    }
+    return BBC_OK;
+}
+
 int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe, int64_t* out_ids,
                     float* out_dists, void* stream) {
     int rc = check_search_args(ix, queries, nq, k, nprobe, out_ids, out_dists);
     if (rc) return rc;
     const int64_t kc = kc_for(ix, k);
-    if (kc > 16384) return fail(BBC_ERR_UNSUPPORTED, "K_c=%lld above 16384 is not supported yet", (long long)kc);
+    if (kc > (int64_t)0x7FFFFFFF) return fail(BBC_ERR_ARG, "K_c too large");
     if (nq == 0) return BBC_OK;
     DeviceGuard g(ix->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -655,22 +766,24 @@ int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint3
     if (!ix) return fail(BBC_ERR_ARG, "null index");
     if (nq < 0 || k < 1 || kc < 1) return fail(BBC_ERR_ARG, "bad sizes");
     if (nq > 0 && (!queries || !cand_ids || !cand_count || !out_ids || !out_dists)) return fail(BBC_ERR_ARG, "null buffer");
-    if (kc > 16384) return fail(BBC_ERR_UNSUPPORTED, "kc above 16384 is not supported yet");
     if (nq == 0) return BBC_OK;
     DeviceGuard g(ix->device);
     cudaStream_t st = (cudaStream_t)stream;
-    // cdist scratch: kc floats per query, in chunks
+    // scratch per query: kc distances (+ kc keys for the large top-k)
+    const size_t per = (size_t)kc * (kc > kTopkSmemMax ? 12 : 4);
     const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
-    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(budget / ((size_t)kc * 4 + 256))));
+    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(budget / (per + 256))));
     char* ws;
-    int rc = get_workspace(ix, st, align_up((size_t)chunk * kc * 4), &ws);
+    int rc = get_workspace(ix, st, align_up((size_t)chunk * per) + 256, &ws);
     if (rc) return rc;
     const int d = ix->dev.d;
     for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
         const int64_t nc = std::min(chunk, nq - q0);
+        unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + align_up((size_t)chunk * kc * 4));
         RerankArgs ra{queries + q0 * d, cand_ids + q0 * kc, cand_count + q0, kc,
                       ix->rerank_u8 && ix->dev.vec_u8 != nullptr, reinterpret_cast<float*>(ws), k,
-                      out_ids + q0 * k, out_dists + q0 * k, nullptr};
+                      out_ids + q0 * k, out_dists + q0 * k, kc > kTopkSmemMax ? keys : nullptr,
+                      uniform_params(1, kc, k, 0)};
         CUDA_TRY(stage(ix, 5, st, [&] { return launch_rerank(ix->dev, nc, ra, st); }));
         CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(ix->dev, nc, ra, st); }));
     }

@@ -63,6 +63,42 @@ struct DevIndex {
 // power of two where that costs little, to turn the row offset into a shift).
 inline int lut_row_words(int M) { return M <= 32 ? 64 : (M <= 96 ? 128 : M + 32); }
 
+// Per-query shape of a batch.  Uniform batches leave the arrays null and use
+// the scalar values; mixed batches (different k and nprobe per query) give
+// per-query values and exclusive prefix offsets into the packed buffers.
+struct QueryParams {
+    int nprobe;                     // uniform values
+    int64_t kc;
+    int k;
+    int64_t cap;                    // region entries per query (uniform)
+    const int32_t* nprobe_q;        // [nq] or null
+    const int64_t* kc_q;            // [nq] or null
+    const int32_t* k_q;             // [nq] or null
+    const int64_t* probe_off;       // [nq + 1] offsets into probe lists, or null
+    const int64_t* region_off;      // [nq + 1] offsets into the region, or null
+    const int64_t* cand_off;        // [nq + 1] offsets into candidates, or null
+    const int64_t* out_off;         // [nq + 1] offsets into results, or null
+    __host__ __device__ int P(int64_t q) const { return nprobe_q ? nprobe_q[q] : nprobe; }
+    __host__ __device__ int64_t KC(int64_t q) const { return kc_q ? kc_q[q] : kc; }
+    __host__ __device__ int K(int64_t q) const { return k_q ? k_q[q] : k; }
+    __host__ __device__ int64_t poff(int64_t q) const { return probe_off ? probe_off[q] : q * (int64_t)nprobe; }
+    __host__ __device__ int64_t roff(int64_t q) const { return region_off ? region_off[q] : q * cap; }
+    __host__ __device__ int64_t rcap(int64_t q) const {
+        return region_off ? region_off[q + 1] - region_off[q] : cap;
+    }
+    __host__ __device__ int64_t coff(int64_t q) const { return cand_off ? cand_off[q] : q * kc; }
+    __host__ __device__ int64_t ooff(int64_t q) const { return out_off ? out_off[q] : q * (int64_t)k; }
+};
+
+inline QueryParams uniform_params(int nprobe, int64_t kc, int k, int64_t cap) {
+    QueryParams p{};
+    p.nprobe = nprobe;
+    p.kc = kc;
+    p.k = k;
+    p.cap = cap;
+    return p;
+}
+
 // ---- launchers (one per translation unit) ----
 
 // S1: approximate probe scores a[q][l] = ||c_l||^2 - 2<q,c_l> (L2) or -<q,c_l> (IP).
@@ -75,22 +111,23 @@ cudaError_t launch_probe_scores_tc(const DevIndex& ix, const float* q, int64_t n
                                    cudaStream_t st);
 // S2: exact probe selection (FP64 decides where the approximations cannot).
 // tc = 1 when the scores come from the tensor-core GEMM (wider error bound).
-cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, int nprobe,
-                                const float* scores, int32_t* lists, int tc, cudaStream_t st);
+cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, const QueryParams& qp,
+                                int max_nprobe, const float* scores, int32_t* lists, int tc, cudaStream_t st);
 // S3: uint16 PQ lookup tables [nq][M][K].
 cudaError_t launch_lut16(const DevIndex& ix, const float* q, int64_t nq, uint16_t* lut16,
                          cudaStream_t st);
 
 struct ScanArgs {
     const uint16_t* lut16;        // [nq][M][K]
-    const int32_t* lists;         // [nq][nprobe]
-    int nprobe;
-    int64_t kc;
+    const int32_t* lists;         // probe lists, packed per QueryParams::poff
+    int nprobe;                   // largest nprobe in the batch (shared-memory sizing)
+    int64_t kc;                   // uniform K_c (per-query values in qp)
     int m;                        // buckets
     int sample_min;               // minimum sampled lists
-    uint2* region;                // [nq][cap] (e, id)
-    int64_t cap;
+    uint2* region;                // appended (e, list position) pairs, per QueryParams::roff
+    int64_t cap;                  // uniform region capacity (per-query values in qp)
     bbc_collector_state* state;   // [nq]
+    QueryParams qp;
 };
 // S4-S6: sample + codebook + scan + push/update, one CTA per query.
 cudaError_t launch_scan(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st);
@@ -100,24 +137,26 @@ struct SelectArgs {
     int64_t cap;
     bbc_collector_state* state;
     int64_t kc;
-    uint32_t* cand;               // [nq][kc]
+    uint32_t* cand;               // candidates, per QueryParams::coff
     int64_t* cand_count;          // [nq]
-    uint2* spill;                 // [nq][cap] scratch for large threshold buckets
+    uint2* spill;                 // unused
+    QueryParams qp;
 };
 // S7: exact threshold bucket, compaction, top-s of the threshold bucket.
 cudaError_t launch_select(const DevIndex& ix, int64_t nq, const SelectArgs& a, cudaStream_t st);
 
 struct RerankArgs {
     const float* q;               // [nq][d]
-    const uint32_t* cand;         // [nq][kc]
+    const uint32_t* cand;         // candidates, per QueryParams::coff
     const int64_t* cand_count;    // [nq]
-    int64_t kc;
+    int64_t kc;                   // largest K_c in the batch (grid sizing)
     int use_u8;
-    float* cdist;                 // [nq][kc]
+    float* cdist;                 // per QueryParams::coff
     int k;
-    int64_t* out_ids;             // [nq][k]
-    float* out_dists;             // [nq][k]
-    unsigned long long* keys;     // [nq][kc] scratch for the final top-k
+    int64_t* out_ids;             // per QueryParams::ooff
+    float* out_dists;             // per QueryParams::ooff
+    unsigned long long* keys;     // per QueryParams::coff, scratch for large top-k
+    QueryParams qp;
 };
 // S8: exact distances of the candidates; S9: k smallest (dist, id), sorted.
 cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);

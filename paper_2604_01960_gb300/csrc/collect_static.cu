@@ -101,11 +101,12 @@ extern "C" int bbc_collect_static(bbc_index* ix, const float* queries, int64_t n
         cudaStream_t st = (cudaStream_t)stream;
         e = launch_lut16(d, queries, nq, lut, st);
         if (e == cudaSuccess) {
-            ScanArgs sa{lut, probe_lists, nprobe, kc, index_buckets(ix), index_sample_lists(ix), region, cap, state};
+            ScanArgs sa{lut, probe_lists, nprobe, kc, index_buckets(ix), index_sample_lists(ix), region, cap, state,
+                        uniform_params(nprobe, kc, 1, cap)};
             e = launch_scan(d, nq, sa, st);
         }
         if (e == cudaSuccess) {
-            SelectArgs se{region, cap, state, kc, out_ids, out_count, nullptr};
+            SelectArgs se{region, cap, state, kc, out_ids, out_count, nullptr, uniform_params(nprobe, kc, 1, cap)};
             e = launch_select(d, nq, se, st);
         }
         if (e != cudaSuccess) rc = api_error(BBC_ERR_CUDA, cudaGetErrorString(e));

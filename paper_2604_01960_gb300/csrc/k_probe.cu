@@ -143,7 +143,7 @@ __device__ __forceinline__ ff ff_prod(float a, float b) {
 // this GPU, so it is kept to genuine near-ties.  Lists outside runs are provably in exact order,
 // so the result equals sorting every list by its FP64 score.
 __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, const float* __restrict__ q,
-                                                                    int nprobe,
+                                                                    QueryParams qp,
                                                                     const float* __restrict__ scores,
                                                                     int32_t* __restrict__ lists, int tc) {
     extern __shared__ unsigned long long psm[];
@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
     __shared__ float s_fmax;
 
     const int64_t qi = blockIdx.x;
+    const int nprobe = qp.P(qi);
     const float* qv = q + qi * d;
     const float* sv = scores + qi * L;
     for (int l = threadIdx.x; l < L; l += blockDim.x) keys[l] = f32_key(sv[l]);
@@ -267,11 +268,13 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
         }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < nprobe; j += blockDim.x) lists[qi * nprobe + j] = (int32_t)cval[j];
+    int32_t* lo = lists + qp.poff(qi);
+    for (int j = threadIdx.x; j < nprobe; j += blockDim.x) lo[j] = (int32_t)cval[j];
 }
 
-cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, int nprobe,
-                                const float* scores, int32_t* lists, int tc, cudaStream_t st) {
+cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, const QueryParams& qp,
+                                int max_nprobe, const float* scores, int32_t* lists, int tc, cudaStream_t st) {
+    (void)max_nprobe;
     if (nq <= 0) return cudaSuccess;
     size_t smem = (size_t)SEL_MAXC * (8 + 4) + (size_t)ix.nlist * 4;
     static bool attr_set = false;
@@ -281,7 +284,7 @@ cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    probe_select_kernel<<<(unsigned)nq, SEL_THREADS, smem, st>>>(ix, q, nprobe, scores, lists, tc);
+    probe_select_kernel<<<(unsigned)nq, SEL_THREADS, smem, st>>>(ix, q, qp, scores, lists, tc);
     return cudaGetLastError();
 }
 

@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     const int grp = ln / G, gl = ln % G;
     const int64_t c0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
     const int64_t c1 = min(c0 + RR_CAND_PER_CTA, cnt);
-    const uint32_t* cand = a.cand + qi * a.kc;
-    float* out = a.cdist + qi * a.kc;
+    const uint32_t* cand = a.cand + a.qp.coff(qi);
+    float* out = a.cdist + a.qp.coff(qi);
     const float4* q4 = reinterpret_cast<const float4*>(rq);
     const uint4* qb = reinterpret_cast<const uint4*>(q8);
     // RR_U candidates per group per step, their row loads issued together
@@ -232,12 +232,13 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArg
     const int64_t cnt = a.cand_count[qi];
     const int n = (int)(cnt < TK_MAX ? cnt : TK_MAX);
     const int tid = threadIdx.x;
+    const int kq = a.qp.K(qi);
     if (cnt > TK_MAX && tid == 0) atomicOr(ix.status, kStatusTopkOverrun);
-    const uint32_t* cand = a.cand + qi * a.kc;
-    const float* cd = a.cdist + qi * a.kc;
-    int64_t* oid = a.out_ids + qi * a.k;
-    float* od = a.out_dists + qi * a.k;
-    for (int i = n + tid; i < a.k; i += blockDim.x) { oid[i] = -1; od[i] = INFINITY; }
+    const uint32_t* cand = a.cand + a.qp.coff(qi);
+    const float* cd = a.cdist + a.qp.coff(qi);
+    int64_t* oid = a.out_ids + a.qp.ooff(qi);
+    float* od = a.out_dists + a.qp.ooff(qi);
+    for (int i = n + tid; i < kq; i += blockDim.x) { oid[i] = -1; od[i] = INFINITY; }
     if (n == 0) return;
     if (tid == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_big = 0u; }
     for (int i = tid; i < TK_BINS; i += blockDim.x) bins[i] = 0;
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArg
             keys[i] = i < n ? (((unsigned long long)f32_key(cd[i]) << 32) | cand[i]) : ~0ull;
         __syncthreads();
         cta_bitonic_u64(keys, np2);
-        for (int i = tid; i < a.k && i < n; i += blockDim.x) {
+        for (int i = tid; i < kq && i < n; i += blockDim.x) {
             oid[i] = (int64_t)(keys[i] & 0xFFFFFFFFull);
             od[i] = key_f32((uint32_t)(keys[i] >> 32));
         }
@@ -306,7 +307,97 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArg
         int rank = 0;
         for (int j = st; j < en; ++j) rank += keys[j] < me ? 1 : 0;
         const int pos = st + rank;
-        if (pos < a.k) {
+        if (pos < kq) {
+            oid[pos] = (int64_t)(me & 0xFFFFFFFFull);
+            od[pos] = key_f32((uint32_t)(me >> 32));
+        }
+    }
+}
+
+// Same algorithm for K_c above TK_MAX: the keys stay in a global scratch
+// area (RerankArgs::keys, per QueryParams::coff) instead of shared memory.
+// Only bins up to the one holding rank k are scattered and ranked.
+__global__ void __launch_bounds__(TK_THREADS) topk_large_kernel(DevIndex ix, RerankArgs a) {
+    __shared__ uint32_t bins[TK_BINS];
+    __shared__ uint32_t wsum[TK_THREADS / 32];
+    __shared__ uint32_t s_min, s_max, s_big, s_last;
+    const int64_t qi = blockIdx.x;
+    const int64_t n = a.cand_count[qi];
+    const int tid = threadIdx.x;
+    const int kq = a.qp.K(qi);
+    const uint32_t* cand = a.cand + a.qp.coff(qi);
+    const float* cd = a.cdist + a.qp.coff(qi);
+    unsigned long long* keys = a.keys + a.qp.coff(qi);
+    int64_t* oid = a.out_ids + a.qp.ooff(qi);
+    float* od = a.out_dists + a.qp.ooff(qi);
+    for (int64_t i = n + tid; i < kq; i += blockDim.x) { oid[i] = -1; od[i] = INFINITY; }
+    if (n == 0) return;
+    if (tid == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_big = 0u; s_last = TK_BINS - 1; }
+    for (int i = tid; i < TK_BINS; i += blockDim.x) bins[i] = 0;
+    __syncthreads();
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+    for (int64_t i = tid; i < n; i += blockDim.x) {
+        const uint32_t kk = f32_key(cd[i]);
+        mn = min(mn, kk);
+        mx = max(mx, kk);
+    }
+    mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if (lane_id() == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
+    __syncthreads();
+    const uint32_t kmin = s_min;
+    const float scale = (float)TK_BINS / ((float)(s_max - kmin) + 1.0f);
+    for (int64_t i = tid; i < n; i += blockDim.x) atomicAdd(&bins[tk_bin(f32_key(cd[i]), kmin, scale)], 1u);
+    __syncthreads();
+    constexpr int PER = TK_BINS / TK_THREADS;
+    uint32_t loc[PER], tot = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) { loc[j] = bins[tid * PER + j]; tot += loc[j]; }
+    const uint32_t winc = warp_incl_scan(tot);
+    if (lane_id() == 31) wsum[warp_id()] = winc;
+    __syncthreads();
+    if (warp_id() == 0) {
+        const uint32_t v = wsum[lane_id()];
+        wsum[lane_id()] = warp_incl_scan(v) - v;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp_id()] + winc - tot;
+    const uint32_t need = (uint32_t)((int64_t)kq < n ? (int64_t)kq : n);
+    uint32_t big = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int b = tid * PER + j;
+        bins[b] = run;
+        if (run < need && run + loc[j] >= need) s_last = (uint32_t)b;      // bin holding rank need-1
+        run += loc[j];
+        big |= loc[j] > (uint32_t)TK_BIG ? 1u : 0u;
+    }
+    if (big) s_big = 1u;
+    __syncthreads();
+    if (s_big) {
+        if (tid == 0) atomicOr(ix.status, kStatusTopkOverrun);          // degenerate: refuse rather than go quadratic
+        return;
+    }
+    const uint32_t last = s_last;
+    for (int64_t i = tid; i < n; i += blockDim.x) {
+        const uint32_t kk = f32_key(cd[i]);
+        const uint32_t b = tk_bin(kk, kmin, scale);
+        if (b <= last) {
+            const uint32_t p = atomicAdd(&bins[b], 1u);
+            keys[p] = ((unsigned long long)kk << 32) | cand[i];
+        }
+    }
+    __syncthreads();
+    const uint32_t upto = bins[last];                                    // keys in bins <= last
+    for (uint32_t p = tid; p < upto; p += blockDim.x) {
+        const unsigned long long me = keys[p];
+        const uint32_t b = tk_bin((uint32_t)(me >> 32), kmin, scale);
+        const uint32_t st = b ? bins[b - 1] : 0u;
+        const uint32_t en = bins[b];
+        uint32_t rank = 0;
+        for (uint32_t j = st; j < en; ++j) rank += keys[j] < me ? 1u : 0u;
+        const uint32_t pos = st + rank;
+        if ((int)pos < kq) {
             oid[pos] = (int64_t)(me & 0xFFFFFFFFull);
             od[pos] = key_f32((uint32_t)(me >> 32));
         }
@@ -315,7 +406,11 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArg
 
 cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
-    if (a.kc > TK_MAX) return cudaErrorInvalidValue;
+    if (a.kc > TK_MAX) {
+        if (!a.keys) return cudaErrorInvalidValue;
+        topk_large_kernel<<<(unsigned)nq, TK_THREADS, 0, st>>>(ix, a);
+        return cudaGetLastError();
+    }
     const int np2 = next_pow2((int)(a.kc > 1 ? a.kc : 1));
     const size_t smem = (size_t)np2 * 8;
     static bool attr_set = false;

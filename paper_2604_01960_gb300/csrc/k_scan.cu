@@ -150,16 +150,25 @@ struct ScanShared {
     long long sq;
 };
 
+// Per-query view of the batch: this query's probe count, K_c and region.
+struct QCtx {
+    int P;
+    int64_t kc;
+    int64_t cap;
+    uint2* region;
+    const int32_t* lists;
+};
+
 template <int M, int BITS, bool MAIN>
-__device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& a, int64_t qi,
+__device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& a, const QCtx& Q,
                                             int g0, int g1, const uint32_t* lut, const int32_t* lpre,
                                             const int32_t* lblk, const int32_t* llen, ScanShared& S) {
     using C = ScanCfg<M, BITS>;
-    const int P = a.nprobe;
+    const int P = Q.P;
     const unsigned ln = lane_id();
     const int nw = blockDim.x >> 5;
     const uint32_t lane_base = (uint32_t)__cvta_generic_to_shared(lut) + 4u * ln;
-    uint2* region = a.region + qi * a.cap;
+    uint2* region = Q.region;
     const unsigned lt_mask = (1u << ln) - 1u;
     constexpr int CH = C::CHUNK;
     for (int cb = g0 + (int)warp_id() * CH; cb < g1; cb += nw * CH) {
@@ -213,14 +222,14 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 if (push) {
                     const uint32_t pos = base + (uint32_t)__popc(bal & lt_mask);
-                    if ((int64_t)pos < a.cap) region[pos] = make_uint2(e, (uint32_t)gbk[u] * 32u + ln);
+                    if ((int64_t)pos < Q.cap) region[pos] = make_uint2(e, (uint32_t)gbk[u] * 32u + ln);
                     else atomicOr(ix.status, kStatusRegionOverrun);
                     if (MAIN) atomicAdd(&S.hist[bk], 1u);
                 }
             }
         }
         if (MAIN && (((cb - g0) / (nw * CH)) & 1) == 0) {
-            const uint32_t t = warp_update(S.hist, a.m, a.kc);
+            const uint32_t t = warp_update(S.hist, a.m, Q.kc);
             if (ln == 0 && t < *(volatile uint32_t*)&S.tau) atomicMin(&S.tau, t);
         }
     }
@@ -231,12 +240,14 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
     using C = ScanCfg<M, BITS>;
     extern __shared__ uint4 dsm[];
     uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
-    const int P = a.nprobe;
-    int32_t* lpre = reinterpret_cast<int32_t*>(lut + C::LUT_WORDS);   // [P+1]
-    int32_t* lblk = lpre + (P + 1);                                    // [P]
-    int32_t* llen = lblk + P;                                          // [P]
+    const int Pmax = a.nprobe;
+    int32_t* lpre = reinterpret_cast<int32_t*>(lut + C::LUT_WORDS);   // [Pmax+1]
+    int32_t* lblk = lpre + (Pmax + 1);                                 // [Pmax]
+    int32_t* llen = lblk + Pmax;                                       // [Pmax]
     __shared__ ScanShared S;
     const int64_t qi = blockIdx.x;
+    const QCtx Q{a.qp.P(qi), a.qp.KC(qi), a.qp.rcap(qi), a.region + a.qp.roff(qi), a.lists + a.qp.poff(qi)};
+    const int P = Q.P;
     const int tid = threadIdx.x, bs = blockDim.x;
 
     // ---- Phase A: LUT staging and list layout ----
@@ -260,7 +271,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
             const int j = base + (int)ln;
             int nb = 0, nv = 0;
             if (j < P) {
-                const int l = a.lists[qi * P + j];
+                const int l = Q.lists[j];
                 nv = ix.list_len[l];
                 nb = (nv + 31) >> 5;
                 lblk[j] = ix.list_blk[l];
@@ -274,7 +285,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
         }
         if (ln == 0) lpre[0] = 0;
         // sample lists: at least min(sample_min, P), extended until min(K_c, S_q) vectors
-        const long long want = a.kc < carryv ? a.kc : carryv;
+        const long long want = Q.kc < carryv ? Q.kc : carryv;
         const int smin = a.sample_min < P ? a.sample_min : P;
         long long cum = 0;
         int nsl = P;
@@ -296,14 +307,14 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
 
     // ---- Phase B: sample ----
     const int gs = lpre[S.nsl];
-    scan_blocks<M, BITS, false>(ix, a, qi, 0, gs, lut, lpre, lblk, llen, S);
+    scan_blocks<M, BITS, false>(ix, a, Q, 0, gs, lut, lpre, lblk, llen, S);
     __syncthreads();
 
     // ---- Phase C: codebook ----
-    const uint2* region = a.region + qi * a.cap;
-    const int64_t ns = (int64_t)min((long long)S.count, (long long)a.cap);
+    const uint2* region = Q.region;
+    const int64_t ns = (int64_t)min((long long)S.count, (long long)Q.cap);
     if (ns > 0) {
-        const int64_t t = ns < a.kc ? ns : a.kc;
+        const int64_t t = ns < Q.kc ? ns : Q.kc;
         const uint32_t dmax = cta_select_u32(ns, (uint32_t)(t - 1), [&](int64_t i) { return region[i].x; },
                                              S.ehist, S.sc, 16);
         if (tid == 0) {
@@ -351,7 +362,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
         }
         __syncthreads();
         if (warp_id() == 0) {
-            const uint32_t t0 = warp_update(S.hist, a.m, a.kc);
+            const uint32_t t0 = warp_update(S.hist, a.m, Q.kc);
             if (lane_id() == 0) S.tau = t0;
         }
     } else {
@@ -361,7 +372,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
     __syncthreads();
 
     // ---- Phase D: main scan ----
-    scan_blocks<M, BITS, true>(ix, a, qi, gs, lpre[P], lut, lpre, lblk, llen, S);
+    scan_blocks<M, BITS, true>(ix, a, Q, gs, lpre[P], lut, lpre, lblk, llen, S);
     __syncthreads();
 
     // ---- state out ----
@@ -369,7 +380,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
     for (int i = tid; i < kMaxBuckets; i += bs) st->hist[i] = i < a.m ? S.hist[i] : 0u;
     for (int i = tid; i < 256; i += bs) st->map[i] = S.bmap[i];
     if (warp_id() == 0) {
-        const uint32_t t1 = warp_update(S.hist, a.m, a.kc);
+        const uint32_t t1 = warp_update(S.hist, a.m, Q.kc);
         if (lane_id() == 0) {
             st->d_min = S.dmin;
             st->d_max = S.dmax;
@@ -381,7 +392,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
             st->scanned = S.sq;
             st->pushed = (int64_t)S.count;
             st->below = 0;
-            st->kc = a.kc;
+            st->kc = Q.kc;
         }
     }
 }

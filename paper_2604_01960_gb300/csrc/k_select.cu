@@ -44,9 +44,11 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
     bbc_collector_state& st = a.state[qi];
     const int tid = threadIdx.x, bs = blockDim.x;
     const int m = st.m;
-    const int64_t n = st.pushed < a.cap ? st.pushed : a.cap;
-    const uint2* region = a.region + qi * a.cap;
-    uint32_t* cand = a.cand + qi * a.kc;
+    const int64_t kc = a.qp.KC(qi);
+    const int64_t cap = a.qp.rcap(qi);
+    const int64_t n = st.pushed < cap ? st.pushed : cap;
+    const uint2* region = a.region + a.qp.roff(qi);
+    uint32_t* cand = a.cand + a.qp.coff(qi);
     for (int i = tid; i < 256; i += bs) map[i] = st.map[i];
     if (warp_id() == 0) {
         // tau* and the count below it
@@ -59,7 +61,7 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
             s += h[i];
         }
         const unsigned long long inc = warp_incl_scan64(s);
-        const unsigned hit = __ballot_sync(0xFFFFFFFFu, inc >= (unsigned long long)a.kc);
+        const unsigned hit = __ballot_sync(0xFFFFFFFFu, inc >= (unsigned long long)kc);
         if (!hit) {
             if (ln == 0) { s_tau = m; s_below = (long long)n; }
         } else {
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
             if (ln == src) {
                 unsigned long long c = inc - s;
                 for (int i = 0; i < 8; ++i) {
-                    if (c + h[i] >= (unsigned long long)a.kc) { s_tau = (int)(ln * 8 + i); s_below = (long long)c; break; }
+                    if (c + h[i] >= (unsigned long long)kc) { s_tau = (int)(ln * 8 + i); s_below = (long long)c; break; }
                     c += h[i];
                 }
             }
@@ -81,9 +83,9 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
     const unsigned lt_mask = (1u << ln) - 1u;
     if (tau >= m) {
         // fewer than K_c objects: all appended objects are candidates
-        for (int64_t i = tid; i < n && i < a.kc; i += bs) cand[i] = ix.ids[region[i].y];
+        for (int64_t i = tid; i < n && i < kc; i += bs) cand[i] = ix.ids[region[i].y];
         if (tid == 0) {
-            a.cand_count[qi] = n < a.kc ? n : a.kc;
+            a.cand_count[qi] = n < kc ? n : kc;
             st.tau = tau;
             st.below = n;
         }
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
                 if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 const uint32_t pos = base + __popc(bal & lt_mask);
-                if (take && (int64_t)pos < a.kc) cand[pos] = idv[u];
+                if (take && (int64_t)pos < kc) cand[pos] = idv[u];
             }
             if (in_smem && b[u] == (uint32_t)tau) {
                 const uint32_t p = atomicAdd(&s_t, 1u);
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
         }
     }
     __syncthreads();
-    const uint32_t s = (uint32_t)(a.kc - below);
+    const uint32_t s = (uint32_t)(kc - below);
     unsigned long long kth;
     if (in_smem) {
         const uint32_t cnt = min(s_t, (uint32_t)SELK_TCAP);
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
                 if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 const uint32_t pos = base + __popc(bal & lt_mask);
-                if (take && (int64_t)pos < a.kc) cand[pos] = (uint32_t)(tkeys[i] & 0xFFFFFFFFu);
+                if (take && (int64_t)pos < kc) cand[pos] = (uint32_t)(tkeys[i] & 0xFFFFFFFFu);
             }
         }
     } else {
@@ -163,14 +165,14 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
                 if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 const uint32_t pos = base + __popc(bal & lt_mask);
-                if (take && (int64_t)pos < a.kc) cand[pos] = id;
+                if (take && (int64_t)pos < kc) cand[pos] = id;
             }
         }
     }
     __syncthreads();
     if (tid == 0) {
-        if ((int64_t)s_out != a.kc) atomicOr(ix.status, kStatusSelectOverrun);
-        a.cand_count[qi] = min((int64_t)s_out, a.kc);
+        if ((int64_t)s_out != kc) atomicOr(ix.status, kStatusSelectOverrun);
+        a.cand_count[qi] = min((int64_t)s_out, kc);
         st.tau = tau;
         st.below = below;
     }

@@ -43,6 +43,9 @@ def small_workload(kind: str):
     elif kind == "embed":     # unit norm, inner product, PQ 32 x 8 bit
         x, q = embedding_shaped(12000, 24, d=64)
         idx = build_ivf_pq(x, 48, 32, 8, "ip", kmeans_iters=6, pq_iters=6, pq_sample=8000)
+    elif kind == "medium":    # 60k integer vectors: enough for K_c above 16,384
+        x, q = sift_shaped(60000, 12, d=128, n_centers=1200)
+        idx = build_ivf_pq(x, 128, 32, 8, "l2", kmeans_iters=6, pq_iters=6, pq_sample=20000)
     elif kind == "ragged":    # few vectors, many short and empty lists
         x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
         idx = build_ivf_pq(x, 40, 8, 8, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700)

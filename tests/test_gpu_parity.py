@@ -292,3 +292,49 @@ def test_argument_errors(bbc):
     with pytest.raises(bbc.BBCError):
         bbc.bbc_set_param(h, "no_such_key", 1)
     bbc.bbc_search(h, qd, 0, 5, 4, ids, dd)      # nq = 0 is a no-op
+
+
+@pytest.mark.parametrize("kind", ["sift", "tiny"])
+def test_search_ex_mixed_batch_equals_alone(bbc, kind):
+    """A mixed batch (different k and nprobe per query) returns, for every
+    query, exactly what searching that query alone returns."""
+    h, idx, q = dev_index(bbc, kind)
+    bbc.bbc_set_param(h, "kc_ratio", 1.5)
+    rng = np.random.default_rng(11)
+    nq = len(q)
+    ks = rng.integers(1, 1500, size=nq).astype(np.int32)
+    ps = rng.integers(1, idx.nlist + 1, size=nq).astype(np.int32)
+    tot = int(ks.sum())
+    ids = torch.empty(tot, dtype=torch.int64, device="cuda")
+    dd = torch.empty(tot, dtype=torch.float32, device="cuda")
+    qd = cuda(q)
+    bbc.bbc_search_ex(h, qd, nq, ks, ps, ids, dd)
+    sync_ok(bbc, h)
+    gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(ks)])
+    for i in range(nq):
+        k = int(ks[i])
+        ai = torch.empty((1, k), dtype=torch.int64, device="cuda")
+        ad = torch.empty((1, k), dtype=torch.float32, device="cuda")
+        bbc.bbc_search(h, qd[i:i + 1], 1, k, int(ps[i]), ai, ad)
+        sync_ok(bbc, h)
+        assert np.array_equal(gi[off[i]:off[i + 1]], ai.cpu().numpy()[0]), f"query {i}"
+        assert np.array_equal(gd[off[i]:off[i + 1]], ad.cpu().numpy()[0]), f"query {i}"
+
+
+def test_large_candidate_pool_topk(bbc, oracle_lib):
+    """K_c above the shared-memory top-k capacity (global-scratch path), exact on integer data."""
+    h, idx, q = dev_index(bbc, "medium")
+    k, nprobe, ratio = 12000, 96, 1.5
+    bbc.bbc_set_param(h, "kc_ratio", ratio)
+    kc = int(np.ceil(ratio * k))
+    assert kc > 16384
+    nq = 6
+    ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    dd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_search(h, cuda(q[:nq]), nq, k, nprobe, ids, dd)
+    sync_ok(bbc, h)
+    oi, od = oracle_lib.search(idx, q[:nq], k, nprobe, kc, "sort")
+    gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
+    for i in range(nq):
+        _check_topk(oracle_lib, idx, q[i], gi[i], gd[i], oi[i], od[i], True)
