@@ -110,6 +110,11 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *   "workspace_mb" device workspace budget per call; queries are processed in
  *                  chunks that fit.  Default 8192.
  *   "profile"      1 = record per-stage CUDA events (see bbc_profile_read).  Default 0.
+ *   "split"        CTAs per query in the scan: 1 = one CTA owns each query, G >= 2 =
+ *                  G CTAs share each query (persistent CTAs over (query, part)
+ *                  items, collector state in global memory), 0 = automatic (split
+ *                  when the batch is too small to fill the GPU).  Same results
+ *                  either way.  Default 0.
  *   "probe_gemm"   1 = approximate probe scores on the tensor cores (tcgen05 BF16
  *                  GEMM with a 3-term split), 0 = FP32 SIMT.  Either way the
  *                  probe result is exact (see bbc_probe).  Default 1.

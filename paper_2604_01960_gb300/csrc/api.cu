@@ -96,6 +96,7 @@ struct bbc_index {
     int sample_lists = 8;
     int rerank_u8 = 1;
     int probe_gemm = 1;
+    int split = 0;            // 0 automatic, 1 one CTA per query, G >= 2 CTAs per query
     double workspace_mb = 8192.0;
     int profile = 0;
     std::mutex mu;
@@ -153,7 +154,7 @@ struct Plan {
     int k;
     int64_t cap;
     size_t off_scores, off_probe, off_lut, off_state, off_region, off_cand, off_count, off_cdist,
-        off_q, off_ids, off_dists, off_abf, off_keys, off_params, total;
+        off_q, off_ids, off_dists, off_abf, off_keys, off_params, off_counters, total;
 };
 
 constexpr int64_t kTopkSmemMax = 16384;     // K_c handled by the shared-memory top-k
@@ -175,6 +176,7 @@ size_t layout(const bbc_index* ix, const ChunkShape& c, Plan& p) {
     p.off_abf = o; o = align_up(o + (ix->probe_gemm ? probe_tc_workspace(d, c.nq) : 0));
     p.off_keys = o; o = align_up(o + (c.max_kc > kTopkSmemMax ? (size_t)c.sum_kc * 8 : 0));
     p.off_params = o; o = align_up(o + (c.mixed ? (size_t)(c.nq + 1) * 8 * 7 : 0));
+    p.off_counters = o; o = align_up(o + 16);
     p.total = o;
     return o;
 }
@@ -286,7 +288,19 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
     CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(d, q, nc, lut, st); }));
     ScanArgs sa{lut, probe_in ? probe_in : probe, p.nprobe, p.kc, ix->buckets, ix->sample_lists,
                 region, p.cap, state, qp};
-    CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan(d, nc, sa, st); }));
+    // one CTA per query when the batch fills the GPU, else G CTAs per query
+    int G = ix->split >= 2 ? ix->split : 1;
+    if (ix->split == 0) {
+        const int64_t slots = 4ll * 2 * d.num_sms;
+        if (nc < slots) G = (int)std::min<int64_t>((slots + nc - 1) / nc, std::max(1, p.nprobe));
+    }
+    if (G >= 2) {
+        unsigned int* counters = reinterpret_cast<unsigned int*>(ws + p.off_counters);
+        CUDA_TRY(cudaMemsetAsync(state, 0, (size_t)nc * sizeof(bbc_collector_state), st));
+        CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan_split(d, nc, sa, G, counters, st); }));
+    } else {
+        CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan(d, nc, sa, st); }));
+    }
     SelectArgs se{region, p.cap, state, p.kc, cand, count, nullptr, qp};
     CUDA_TRY(stage(ix, 4, st, [&] { return launch_select(d, nc, se, st); }));
     if (stop_after <= 7) return BBC_OK;
@@ -351,6 +365,11 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out) {
     D.cbp = (D.code_bytes + 15) / 16 * 16;
     D.W = lut_row_words(M);
     D.n = n;
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 1;
+        D.num_sms = sms;
+    }
 
     // block layout
     std::vector<int32_t> list_blk(L), list_len(L);
@@ -525,6 +544,9 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "workspace_mb") {
         if (!(v >= 1)) return fail(BBC_ERR_ARG, "workspace_mb must be >= 1");
         ix->workspace_mb = v;
+    } else if (k == "split") {
+        if (!(v >= 0 && v <= 65536) || v != std::floor(v)) return fail(BBC_ERR_ARG, "split must be 0 (auto), 1 or a part count");
+        ix->split = (int)v;
     } else if (k == "probe_gemm") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "probe_gemm must be 0 (FP32 SIMT) or 1 (tensor cores)");
         ix->probe_gemm = (int)v;
@@ -547,6 +569,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "workspace_mb") *v = ix->workspace_mb;
     else if (k == "profile") *v = ix->profile;
     else if (k == "probe_gemm") *v = ix->probe_gemm;
+    else if (k == "split") *v = ix->split;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }

@@ -55,6 +55,7 @@ struct DevIndex {
     unsigned int* status;
     const uint16_t* cent_b3;   // BF16 [nlist][kp]: [c_hi | c_lo | c_hi | 0-pad] for the tensor-core probe
     int kp;                    // 3d rounded up to a multiple of 64
+    int num_sms;               // streaming multiprocessors of the device
 };
 
 // Words per LUT row in shared memory: lane t at code slot s reads word t + s
@@ -131,6 +132,10 @@ struct ScanArgs {
 };
 // S4-S6: sample + codebook + scan + push/update, one CTA per query.
 cudaError_t launch_scan(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st);
+// Same result with G CTAs per query (persistent CTAs over (query, part) items);
+// counters: 2 u32 of device scratch.  The state array must be zeroed first.
+cudaError_t launch_scan_split(const DevIndex& ix, int64_t nq, const ScanArgs& a, int G, unsigned int* counters,
+                              cudaStream_t st);
 
 struct SelectArgs {
     const uint2* region;

@@ -29,6 +29,7 @@
 // (estimated distance, list position); positions become ids in k_select.cu,
 // so the hot loop never waits on an id load.  Appends are warp-
 // aggregated (ballot + one shared atomic per warp) into a contiguous region.
+#include <algorithm>
 #include <climits>
 
 #include "bbc_internal.cuh"
@@ -159,12 +160,33 @@ struct QCtx {
     const int32_t* lists;
 };
 
-template <int M, int BITS, bool MAIN>
+// Split mode: move this CTA's bucket-count deltas into the query's global
+// counts, then Update on the global counts (one warp).
+__device__ __forceinline__ void flush_and_update(ScanShared& S, bbc_collector_state* st, int m, int64_t kc) {
+    for (int b = (int)lane_id(); b < m; b += 32) {
+        const uint32_t v = atomicExch(&S.hist[b], 0u);
+        if (v) atomicAdd(&st->hist[b], v);
+    }
+    __syncwarp();
+    const uint32_t t = warp_update(st->hist, m, kc);
+    if (lane_id() == 0) {
+        atomicMin(&st->tau, (int)t);
+        atomicMin(&S.tau, t);
+    }
+}
+
+// Scans blocks [g0, g1) of the lists laid out in lpre/lblk/llen (nl lists).
+// MAIN = false: sampling (append everything); MAIN = true: Push with the
+// codebook and tau.  GLOBAL = false: the CTA owns the query (counts and
+// region cursor in shared memory); GLOBAL = true: several CTAs share the
+// query (region cursor and counts in the global state, tau cached per CTA).
+template <int M, int BITS, bool MAIN, bool GLOBAL>
 __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& a, const QCtx& Q,
-                                            int g0, int g1, const uint32_t* lut, const int32_t* lpre,
-                                            const int32_t* lblk, const int32_t* llen, ScanShared& S) {
+                                            bbc_collector_state* st, int nl, int g0, int g1,
+                                            const uint32_t* lut, const int32_t* lpre, const int32_t* lblk,
+                                            const int32_t* llen, ScanShared& S) {
     using C = ScanCfg<M, BITS>;
-    const int P = Q.P;
+    const int P = nl;
     const unsigned ln = lane_id();
     const int nw = blockDim.x >> 5;
     const uint32_t lane_base = (uint32_t)__cvta_generic_to_shared(lut) + 4u * ln;
@@ -212,13 +234,21 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                 push = valid && bk <= tau;
             } else {
                 push = valid;
-                const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, valid ? e : 0xFFFFFFFFu);
-                if (ln == 0 && mn != 0xFFFFFFFFu) atomicMin(&S.dmin, mn);
+                if (!GLOBAL) {
+                    const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, valid ? e : 0xFFFFFFFFu);
+                    if (ln == 0 && mn != 0xFFFFFFFFu) atomicMin(&S.dmin, mn);
+                }
             }
             const unsigned bal = __ballot_sync(0xFFFFFFFFu, push);
             if (bal) {
                 uint32_t base = 0;
-                if (ln == 0) base = atomicAdd(&S.count, (uint32_t)__popc(bal));
+                if (ln == 0) {
+                    if (GLOBAL)
+                        base = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(&st->pushed),
+                                                   (unsigned long long)__popc(bal));
+                    else
+                        base = atomicAdd(&S.count, (uint32_t)__popc(bal));
+                }
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 if (push) {
                     const uint32_t pos = base + (uint32_t)__popc(bal & lt_mask);
@@ -229,10 +259,80 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
             }
         }
         if (MAIN && (((cb - g0) / (nw * CH)) & 1) == 0) {
-            const uint32_t t = warp_update(S.hist, a.m, Q.kc);
-            if (ln == 0 && t < *(volatile uint32_t*)&S.tau) atomicMin(&S.tau, t);
+            if (GLOBAL) {
+                if (warp_id() == 0) flush_and_update(S, st, a.m, Q.kc);
+            } else {
+                const uint32_t t = warp_update(S.hist, a.m, Q.kc);
+                if (ln == 0 && t < *(volatile uint32_t*)&S.tau) atomicMin(&S.tau, t);
+            }
         }
     }
+}
+
+// Phase C of Algorithm 1's Collect (Section 3.2, "Codebook Generation Based
+// on Estimated Distance") over the ns sampled objects at the start of the
+// region, by the whole CTA.  On entry S.dmin holds the smallest sampled
+// estimate and S.hist is zero; on exit S holds d_max, the shift, the
+// equal-depth map, the sample's bucket counts and tau.
+__device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int m, ScanShared& S) {
+    const int tid = threadIdx.x, bs = blockDim.x;
+    if (ns > 0) {
+        const int64_t t = ns < kc ? ns : kc;
+        const uint32_t dmax = cta_select_u32(ns, (uint32_t)(t - 1), [&](int64_t i) { return region[i].x; },
+                                             S.ehist, S.sc, 16);
+        if (tid == 0) {
+            S.dmax = dmax;
+            int sh = 0;
+            while (((dmax - S.dmin) >> sh) > 255u) ++sh;
+            S.sh = sh;
+        }
+        for (int i = tid; i < 256; i += bs) S.ehist[i] = 0;
+        __syncthreads();
+        const uint32_t dmin = S.dmin;
+        const int sh = S.sh;
+        for (int64_t i = tid; i < ns; i += 4 * bs) {
+            uint32_t e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0xFFFFFFFFu;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * bs < ns && e[u] <= dmax) atomicAdd(&S.ehist[bin_of(e[u], dmin, sh)], 1u);
+        }
+        __syncthreads();
+        if (warp_id() == 0) {
+            const unsigned ln = lane_id();
+            uint32_t h[8], s = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { h[i] = S.ehist[ln * 8 + i]; s += h[i]; }
+            const unsigned long long inc = warp_incl_scan64(s);
+            const unsigned long long T = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            unsigned long long cum = inc - s;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                unsigned long long v = T ? ((unsigned long long)m * cum) / T : 0ull;
+                S.bmap[ln * 8 + i] = (uint8_t)(v > (unsigned long long)(m - 1) ? m - 1 : v);
+                cum += h[i];
+            }
+        }
+        __syncthreads();
+        for (int64_t i = tid; i < ns; i += 4 * bs) {
+            uint32_t e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * bs < ns) atomicAdd(&S.hist[S.bmap[bin_of(e[u], dmin, sh)]], 1u);
+        }
+        __syncthreads();
+        if (warp_id() == 0) {
+            const uint32_t t0 = warp_update(S.hist, m, kc);
+            if (lane_id() == 0) S.tau = t0;
+        }
+    } else {
+        if (tid == 0) { S.dmin = 0; S.dmax = 0; S.sh = 0; }
+        for (int i = tid; i < 256; i += bs) S.bmap[i] = 0;
+    }
+    __syncthreads();
 }
 
 template <int M, int BITS>
@@ -307,72 +407,14 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
 
     // ---- Phase B: sample ----
     const int gs = lpre[S.nsl];
-    scan_blocks<M, BITS, false>(ix, a, Q, 0, gs, lut, lpre, lblk, llen, S);
+    scan_blocks<M, BITS, false, false>(ix, a, Q, a.state + qi, P, 0, gs, lut, lpre, lblk, llen, S);
     __syncthreads();
 
     // ---- Phase C: codebook ----
-    const uint2* region = Q.region;
     const int64_t ns = (int64_t)min((long long)S.count, (long long)Q.cap);
-    if (ns > 0) {
-        const int64_t t = ns < Q.kc ? ns : Q.kc;
-        const uint32_t dmax = cta_select_u32(ns, (uint32_t)(t - 1), [&](int64_t i) { return region[i].x; },
-                                             S.ehist, S.sc, 16);
-        if (tid == 0) {
-            S.dmax = dmax;
-            int sh = 0;
-            while (((dmax - S.dmin) >> sh) > 255u) ++sh;
-            S.sh = sh;
-        }
-        for (int i = tid; i < 256; i += bs) S.ehist[i] = 0;
-        __syncthreads();
-        const uint32_t dmin = S.dmin;
-        const int sh = S.sh;
-        for (int64_t i = tid; i < ns; i += 4 * bs) {
-            uint32_t e[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0xFFFFFFFFu;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (i + u * bs < ns && e[u] <= dmax) atomicAdd(&S.ehist[bin_of(e[u], dmin, sh)], 1u);
-        }
-        __syncthreads();
-        if (warp_id() == 0) {
-            const unsigned ln = lane_id();
-            uint32_t h[8], s = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { h[i] = S.ehist[ln * 8 + i]; s += h[i]; }
-            const unsigned long long inc = warp_incl_scan64(s);
-            const unsigned long long T = __shfl_sync(0xFFFFFFFFu, inc, 31);
-            unsigned long long cum = inc - s;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                unsigned long long v = T ? ((unsigned long long)a.m * cum) / T : 0ull;
-                S.bmap[ln * 8 + i] = (uint8_t)(v > (unsigned long long)(a.m - 1) ? a.m - 1 : v);
-                cum += h[i];
-            }
-        }
-        __syncthreads();
-        for (int64_t i = tid; i < ns; i += 4 * bs) {
-            uint32_t e[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0u;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (i + u * bs < ns) atomicAdd(&S.hist[S.bmap[bin_of(e[u], dmin, sh)]], 1u);
-        }
-        __syncthreads();
-        if (warp_id() == 0) {
-            const uint32_t t0 = warp_update(S.hist, a.m, Q.kc);
-            if (lane_id() == 0) S.tau = t0;
-        }
-    } else {
-        if (tid == 0) { S.dmin = 0; S.dmax = 0; S.sh = 0; }
-        for (int i = tid; i < 256; i += bs) S.bmap[i] = 0;
-    }
-    __syncthreads();
-
+    build_codebook(Q.region, ns, Q.kc, a.m, S);
     // ---- Phase D: main scan ----
-    scan_blocks<M, BITS, true>(ix, a, Q, gs, lpre[P], lut, lpre, lblk, llen, S);
+    scan_blocks<M, BITS, true, false>(ix, a, Q, a.state + qi, P, gs, lpre[P], lut, lpre, lblk, llen, S);
     __syncthreads();
 
     // ---- state out ----
@@ -397,6 +439,204 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
     }
 }
 
+// ---------------------------------------------------------------------------
+// Split form: several CTAs per query.  Work items (query q, part g) come from
+// a device counter (persistent CTAs); part g of G covers a contiguous range
+// of the query's lists.  Used when a batch has too few queries to fill the
+// GPU with one CTA per query.
+//   pass 1 (MAIN = false): the sampled lists, every object appended;
+//   codebook_kernel: the codebook, counts and tau from the sampled objects;
+//   pass 2 (MAIN = true): the remaining lists with Push against tau.
+// ---------------------------------------------------------------------------
+
+// Warp 0: sampled list count (as in the fused kernel) and S_q of a query.
+__device__ void sample_plan(const DevIndex& ix, const QCtx& Q, int sample_min, int* nsl_out, long long* sq_out) {
+    const unsigned ln = lane_id();
+    const int P = Q.P;
+    long long tot = 0;
+    for (int base = 0; base < P; base += 32) {
+        const int j = base + (int)ln;
+        const unsigned long long inc = warp_incl_scan64(j < P ? (unsigned long long)ix.list_len[Q.lists[j]] : 0ull);
+        tot += (long long)__shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+    const long long want = Q.kc < tot ? Q.kc : tot;
+    const int smin = sample_min < P ? sample_min : P;
+    long long cum = 0;
+    int nsl = P;
+    for (int base = 0; base < P; base += 32) {
+        const int j = base + (int)ln;
+        const unsigned long long inc = warp_incl_scan64(j < P ? (unsigned long long)ix.list_len[Q.lists[j]] : 0ull);
+        const bool ok = j < P && (j + 1) >= smin && (long long)(cum + (long long)inc) >= want;
+        const unsigned hit = __ballot_sync(0xFFFFFFFFu, ok);
+        if (hit) { nsl = base + (int)(__ffs(hit) - 1) + 1; break; }
+        cum += (long long)__shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+    *nsl_out = nsl;
+    *sq_out = tot;
+}
+
+struct SplitArgs {
+    int G;                    // parts per query
+    unsigned int* counter;    // work counter, zero before the launch
+};
+
+template <int M, int BITS, bool MAIN>
+__global__ void __launch_bounds__(SCAN_THREADS, 2) scan_split_kernel(DevIndex ix, ScanArgs a, SplitArgs sp, int64_t nq) {
+    using C = ScanCfg<M, BITS>;
+    extern __shared__ uint4 dsm[];
+    uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
+    const int Pmax = a.nprobe;
+    int32_t* lpre = reinterpret_cast<int32_t*>(lut + C::LUT_WORDS);
+    int32_t* lblk = lpre + (Pmax + 1);
+    int32_t* llen = lblk + Pmax;
+    __shared__ ScanShared S;
+    __shared__ long long s_item, s_q;
+    __shared__ int s_nsl;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const long long total = nq * (long long)sp.G;
+    if (tid == 0) s_q = -1;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = (long long)atomicAdd(sp.counter, 1u);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        const int64_t qi = item / sp.G;
+        const int g = (int)(item % sp.G);
+        const QCtx Q{a.qp.P(qi), a.qp.KC(qi), a.qp.rcap(qi), a.region + a.qp.roff(qi), a.lists + a.qp.poff(qi)};
+        bbc_collector_state* st = a.state + qi;
+        const int P = Q.P;
+        if (MAIN) {
+            if (tid == 0) s_nsl = st->sample_lists;
+        } else if (warp_id() == 0) {
+            int nsl;
+            long long sq;
+            sample_plan(ix, Q, a.sample_min, &nsl, &sq);
+            if (lane_id() == 0) {
+                s_nsl = nsl;
+                if (g == 0) { st->sample_lists = nsl; st->scanned = sq; }
+            }
+        }
+        __syncthreads();
+        const int nsl = s_nsl;
+        int j0, j1;
+        if (MAIN) {
+            const int per = (P - nsl + sp.G - 1) / sp.G;
+            j0 = nsl + g * per;
+            j1 = min(P, j0 + per);
+        } else {
+            const int per = (nsl + sp.G - 1) / sp.G;
+            j0 = g * per;
+            j1 = min(nsl, j0 + per);
+        }
+        if (j0 >= j1) continue;
+        const int nl = j1 - j0;
+        if (s_q != qi) {
+            const uint16_t* lq = a.lut16 + qi * (int64_t)M * C::K;
+            for (int w = tid; w < C::LUT_WORDS; w += bs) {
+                const int jj = w / C::W, c = w - jj * C::W;
+                lut[w] = lq[(c % M) * C::K + jj];
+            }
+        }
+        if (warp_id() == 0) {
+            const unsigned ln = lane_id();
+            int carry = 0;
+            for (int base = 0; base < nl; base += 32) {
+                const int j = base + (int)ln;
+                int nb = 0;
+                if (j < nl) {
+                    const int l = Q.lists[j0 + j];
+                    const int nv = ix.list_len[l];
+                    nb = (nv + 31) >> 5;
+                    lblk[j] = ix.list_blk[l];
+                    llen[j] = nv;
+                }
+                const uint32_t inc = warp_incl_scan((uint32_t)nb);
+                if (j < nl) lpre[j + 1] = carry + (int)inc;
+                carry += (int)__shfl_sync(0xFFFFFFFFu, inc, 31);
+            }
+            if (ln == 0) lpre[0] = 0;
+        }
+        if (MAIN) {
+            for (int i = tid; i < 256; i += bs) {
+                S.bmap[i] = st->map[i];
+                S.hist[i] = 0u;                                  // this CTA's count deltas
+            }
+            if (tid == 0) {
+                S.dmin = st->d_min;
+                S.sh = st->sh;
+                S.tau = (uint32_t)*(volatile int*)&st->tau;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) s_q = qi;
+        scan_blocks<M, BITS, MAIN, true>(ix, a, Q, st, nl, 0, lpre[nl], lut, lpre, lblk, llen, S);
+        __syncthreads();
+        if (MAIN && warp_id() == 0) flush_and_update(S, st, a.m, Q.kc);
+    }
+}
+
+// Per query: smallest sampled estimate, then the codebook of the sample.
+__global__ void __launch_bounds__(SCAN_THREADS) codebook_kernel(ScanArgs a) {
+    __shared__ ScanShared S;
+    const int64_t qi = blockIdx.x;
+    bbc_collector_state* st = a.state + qi;
+    const int64_t cap = a.qp.rcap(qi);
+    const int64_t kc = a.qp.KC(qi);
+    const uint2* region = a.region + a.qp.roff(qi);
+    const int64_t ns = st->pushed < cap ? st->pushed : cap;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    if (tid == 0) S.dmin = 0xFFFFFFFFu;
+    for (int i = tid; i < kMaxBuckets; i += bs) S.hist[i] = 0u;
+    __syncthreads();
+    uint32_t mn = 0xFFFFFFFFu;
+    for (int64_t i = tid; i < ns; i += bs) mn = min(mn, region[i].x);
+    mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+    if (lane_id() == 0 && mn != 0xFFFFFFFFu) atomicMin(&S.dmin, mn);
+    __syncthreads();
+    build_codebook(region, ns, kc, a.m, S);
+    for (int i = tid; i < kMaxBuckets; i += bs) st->hist[i] = i < a.m ? S.hist[i] : 0u;
+    for (int i = tid; i < 256; i += bs) st->map[i] = S.bmap[i];
+    if (tid == 0) {
+        st->d_min = S.dmin;
+        st->d_max = S.dmax;
+        st->sh = S.sh;
+        st->m = a.m;
+        st->tau = (int32_t)S.tau;
+        st->sample_size = ns;
+        st->below = 0;
+        st->kc = kc;
+    }
+}
+
+template <int M, int BITS>
+static cudaError_t launch_split_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, int G, unsigned int* counters,
+                                  cudaStream_t st) {
+    using C = ScanCfg<M, BITS>;
+    const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)(3 * a.nprobe + 1) * 4;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(scan_split_kernel<M, BITS, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(scan_split_kernel<M, BITS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    const long long items = nq * (long long)G;
+    const unsigned grid = (unsigned)std::min<long long>(items, (long long)ix.num_sms * 2);
+    cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    scan_split_kernel<M, BITS, false><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters}, nq);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    codebook_kernel<<<(unsigned)nq, SCAN_THREADS, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    scan_split_kernel<M, BITS, true><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters + 1}, nq);
+    return cudaGetLastError();
+}
+
 template <int M, int BITS>
 static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st) {
     using C = ScanCfg<M, BITS>;
@@ -417,6 +657,28 @@ bool scan_supported(int M, int bits) {
     if (bits == 8) return M == 8 || M == 16 || M == 32 || M == 64 || M == 96 || M == 128;
     if (bits == 4) return M == 32 || M == 64 || M == 128;
     return false;
+}
+
+cudaError_t launch_scan_split(const DevIndex& ix, int64_t nq, const ScanArgs& a, int G, unsigned int* counters,
+                              cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    if (ix.bits == 8) {
+        switch (ix.M) {
+            case 8: return launch_split_t<8, 8>(ix, nq, a, G, counters, st);
+            case 16: return launch_split_t<16, 8>(ix, nq, a, G, counters, st);
+            case 32: return launch_split_t<32, 8>(ix, nq, a, G, counters, st);
+            case 64: return launch_split_t<64, 8>(ix, nq, a, G, counters, st);
+            case 96: return launch_split_t<96, 8>(ix, nq, a, G, counters, st);
+            case 128: return launch_split_t<128, 8>(ix, nq, a, G, counters, st);
+        }
+    } else if (ix.bits == 4) {
+        switch (ix.M) {
+            case 32: return launch_split_t<32, 4>(ix, nq, a, G, counters, st);
+            case 64: return launch_split_t<64, 4>(ix, nq, a, G, counters, st);
+            case 128: return launch_split_t<128, 4>(ix, nq, a, G, counters, st);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_scan(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st) {

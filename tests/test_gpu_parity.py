@@ -135,19 +135,22 @@ def _collect(bbc, h, idx, q, nprobe, kc):
     return lists.cpu().numpy(), ids.cpu().numpy().view(np.uint32), cnt.cpu().numpy(), state
 
 
+@pytest.mark.parametrize("split", [1, 0])
 @pytest.mark.parametrize("kind,nprobe,kc,m,smin", [
     ("tiny", 12, 300, 64, 8), ("tiny", 48, 5000, 32, 8), ("sift", 16, 900, 64, 8),
     ("sift4", 20, 1200, 256, 4), ("embed", 10, 400, 2, 8), ("ragged", 40, 300, 16, 3),
     ("ragged", 2, 1000, 64, 8), ("sift", 64, 12000, 64, 8), ("tiny", 5, 1, 64, 8)])
-def test_collect_candidates_and_state(bbc, oracle_lib, kind, nprobe, kc, m, smin):
+def test_collect_candidates_and_state(bbc, oracle_lib, kind, nprobe, kc, m, smin, split):
     h, idx, q = dev_index(bbc, kind)
     bbc.bbc_set_param(h, "buckets", m)
     bbc.bbc_set_param(h, "sample_lists", smin)
+    bbc.bbc_set_param(h, "split", split)
     try:
         lists, ids, cnt, state = _collect(bbc, h, idx, q, nprobe, kc)
     finally:
         bbc.bbc_set_param(h, "buckets", 64)
         bbc.bbc_set_param(h, "sample_lists", 8)
+        bbc.bbc_set_param(h, "split", 0)
     for i in range(len(q)):
         ol, _ = oracle_lib.probe(q[i], idx.centroids, nprobe, idx.metric)
         assert np.array_equal(lists[i], ol)
@@ -196,13 +199,15 @@ def _check_topk(oracle_lib, idx, qv, gi, gd, oi, od, exact):
         assert np.all(np.abs(dd - dk) <= 2 * RTOL * max(abs(dk), 1e-3 * scale))
 
 
+@pytest.mark.parametrize("split", [1, 0])
 @pytest.mark.parametrize("kind,k,nprobe,ratio", [("tiny", 100, 12, 2.0), ("sift", 500, 16, 1.5),
                                                  ("sift4", 300, 24, 2.0), ("embed", 200, 10, 1.5),
                                                  ("ragged", 50, 40, 1.0), ("tiny", 1, 3, 1.0),
                                                  ("sift", 4000, 64, 1.0)])
-def test_search_end_to_end(bbc, oracle_lib, kind, k, nprobe, ratio):
+def test_search_end_to_end(bbc, oracle_lib, kind, k, nprobe, ratio, split):
     h, idx, q = dev_index(bbc, kind)
     bbc.bbc_set_param(h, "kc_ratio", ratio)
+    bbc.bbc_set_param(h, "split", split)
     kc = max(k, int(np.ceil(ratio * k - 1e-9)))
     nq = len(q)
     ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
@@ -210,6 +215,7 @@ def test_search_end_to_end(bbc, oracle_lib, kind, k, nprobe, ratio):
     bbc.bbc_search(h, cuda(q), nq, k, nprobe, ids, dd)
     sync_ok(bbc, h)
     gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
+    bbc.bbc_set_param(h, "split", 0)
     oi, od = oracle_lib.search(idx, q, k, nprobe, kc, "sort")
     exact = kind in ("sift", "sift4")
     for i in range(nq):
@@ -338,3 +344,34 @@ def test_large_candidate_pool_topk(bbc, oracle_lib):
     gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
     for i in range(nq):
         _check_topk(oracle_lib, idx, q[i], gi[i], gd[i], oi[i], od[i], True)
+
+
+@pytest.mark.parametrize("kind", ["tiny", "sift", "ragged"])
+def test_split_scan_equals_one_cta_per_query(bbc, kind):
+    """Several CTAs per query (persistent (query, part) items, global collector
+    state) give exactly the candidates, threshold and results of one CTA per query."""
+    h, idx, q = dev_index(bbc, kind)
+    nq, k, nprobe = len(q), 150, min(idx.nlist, 24)
+    bbc.bbc_set_param(h, "kc_ratio", 2.0)
+    outs = {}
+    try:
+        for split in (1, 2, 7, 64):
+            bbc.bbc_set_param(h, "split", split)
+            lists, ids, cnt, state = _collect(bbc, h, idx, q, nprobe, 2 * k)
+            ri = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+            rd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+            bbc.bbc_search(h, cuda(q), nq, k, nprobe, ri, rd)
+            sync_ok(bbc, h)
+            cands = [np.sort(ids[i, :cnt[i]]) for i in range(nq)]
+            outs[split] = (cands, cnt, state, ri.cpu().numpy(), rd.cpu().numpy())
+    finally:
+        bbc.bbc_set_param(h, "split", 0)
+    ref = outs[1]
+    for split in (2, 7, 64):
+        got = outs[split]
+        assert np.array_equal(got[1], ref[1])
+        for i in range(nq):
+            assert np.array_equal(got[0][i], ref[0][i]), (split, i)
+        for f in ("d_min", "d_max", "sh", "sample_lists", "sample_size", "scanned", "tau", "below"):
+            assert np.array_equal(got[2][f], ref[2][f]), (split, f)
+        assert np.array_equal(got[3], ref[3]) and np.array_equal(got[4], ref[4]), split
