@@ -115,6 +115,10 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  items, collector state in global memory), 0 = automatic (split
  *                  when the batch is too small to fill the GPU).  Same results
  *                  either way.  Default 0.
+ *   "graphs"       1 = bbc_search captures the launch sequence of each call shape
+ *                  (pointers, sizes, parameters, stream) into a CUDA graph the
+ *                  first time and replays it afterwards (not on the legacy
+ *                  default stream).  Default 0.
  *   "probe_gemm"   1 = approximate probe scores on the tensor cores (tcgen05 BF16
  *                  GEMM with a 3-term split), 0 = FP32 SIMT.  Either way the
  *                  probe result is exact (see bbc_probe).  Default 1.
@@ -150,6 +154,18 @@ int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t
  * `stream` before returning. */
 int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe,
                     int64_t* out_ids, float* out_dists, void* stream);
+
+/* Autotuner for the batched form: times candidate values of "split" (CTAs
+ * per query in the scan) and then "buckets" (m, the result buffer's bucket
+ * count) for this call shape on `nq` device queries, and keeps the fastest
+ * on the index.  With cache_path (may be NULL) the choice is looked up in,
+ * or appended to, a JSON-lines file keyed by the index shape and the call
+ * shape, so later processes skip the timing.  Allocates its own output
+ * buffers and synchronises `stream`.  out_ms (host, may be NULL) receives
+ * the best time per call (0 when taken from the cache).  The results of a
+ * search never depend on these settings, only its speed. */
+int bbc_autotune(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe,
+                 const char* cache_path, double* out_ms, void* stream);
 
 /* ---- stage entry points (each one row of the hot path; device pointers) ---- */
 

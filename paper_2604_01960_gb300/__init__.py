@@ -29,7 +29,7 @@ METRICS = {"l2": 0, "ip": 1}
 # Exported symbols declared in include/bbc.h (checked by the ABI test).
 SYMBOLS = ["bbc_index_create", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
            "bbc_get_param", "bbc_search", "bbc_search_ex", "bbc_search_host", "bbc_probe_scores", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
-           "bbc_rerank_topk", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
+           "bbc_rerank_topk", "bbc_autotune", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
 NUM_STAGES = 7
 STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk"]
 
@@ -104,6 +104,7 @@ def lib():
             L.bbc_rerank_topk.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, vp, vp]
             L.bbc_stream_status.argtypes = [vp, vp]
             L.bbc_profile_read.argtypes = [vp, vp, vp, C.c_int]
+            L.bbc_autotune.argtypes = [vp, vp, i64, i32, i32, C.c_char_p, vp, vp]
             for name in SYMBOLS:
                 if getattr(L, name).restype is None and name not in ("bbc_last_error", "bbc_version"):
                     getattr(L, name).restype = C.c_int
@@ -237,6 +238,15 @@ def bbc_profile_read(handle: int, reset: bool = True):
     n = C.c_int64()
     _check(lib().bbc_profile_read(handle, ms, C.byref(n), 1 if reset else 0))
     return dict(zip(STAGES, list(ms))), n.value
+
+
+def bbc_autotune(handle: int, queries, nq: int, k: int, nprobe: int, cache_path: str | None = None,
+                 stream=None) -> float:
+    """Pick 'split' and 'buckets' for this call shape; returns the best ms per call (0 if cached)."""
+    ms = C.c_double()
+    _check(lib().bbc_autotune(handle, _ptr(queries), nq, k, nprobe, cache_path.encode() if cache_path else None,
+                              C.byref(ms), _stream(stream)))
+    return ms.value
 
 
 def bbc_stream_status(handle: int, stream=None) -> None:

@@ -16,6 +16,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "bbc_internal.cuh"
@@ -66,6 +67,7 @@ struct Workspace {
 };
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+constexpr int BBC_ERR_STATE_CAPTURE = BBC_ERR_BUSY;
 
 // FP32 -> BF16, round to nearest even (NaN kept quiet).
 uint16_t f32_to_bf16(float f) {
@@ -97,6 +99,20 @@ struct bbc_index {
     int rerank_u8 = 1;
     int probe_gemm = 1;
     int split = 0;            // 0 automatic, 1 one CTA per query, G >= 2 CTAs per query
+    int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
+    bool capturing = false;
+    struct GraphKey {
+        const void* q; int64_t nq; int k; int nprobe; void* oi; void* od; cudaStream_t st;
+        double kc_ratio; int buckets, sample_lists, split, probe_gemm, rerank;
+        bool operator<(const GraphKey& o) const {
+            return std::tie(q, nq, k, nprobe, oi, od, st, kc_ratio, buckets, sample_lists, split, probe_gemm, rerank) <
+                   std::tie(o.q, o.nq, o.k, o.nprobe, o.oi, o.od, o.st, o.kc_ratio, o.buckets, o.sample_lists, o.split,
+                            o.probe_gemm, o.rerank);
+        }
+    };
+    struct GraphEntry { cudaGraphExec_t exec; int64_t launches; };
+    std::map<GraphKey, GraphEntry> graph_cache;
+    std::mutex graph_mu;
     double workspace_mb = 8192.0;
     int profile = 0;
     std::mutex mu;
@@ -111,6 +127,7 @@ struct bbc_index {
         int prev = -1;
         cudaGetDevice(&prev);
         cudaSetDevice(device);
+        for (auto& kv : graph_cache) cudaGraphExecDestroy(kv.second.exec);
         for (auto& kv : ws) cudaFree(kv.second.base);
         for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (void* p : owned) cudaFree(p);
@@ -213,6 +230,9 @@ int get_workspace(bbc_index* ix, cudaStream_t st, size_t bytes, char** base) {
             w.base = nullptr;
             w.bytes = 0;
         }
+        if (ix->capturing) return fail(BBC_ERR_STATE_CAPTURE, "workspace growth during graph capture");
+        for (auto& kv : ix->graph_cache) cudaGraphExecDestroy(kv.second.exec);
+        ix->graph_cache.clear();
         void* p = nullptr;
         cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) return fail(BBC_ERR_OOM, "workspace cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
@@ -243,7 +263,7 @@ int check_search_args(const bbc_index* ix, const void* queries, int64_t nq, int 
 template <typename F>
 cudaError_t stage(bbc_index* ix, int id, cudaStream_t st, F&& launch) {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (ix->profile) {
+    if (ix->profile && !ix->capturing) {
         if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return cudaErrorMemoryAllocation;
         cudaEventRecord(a, st);
     }
@@ -251,7 +271,7 @@ cudaError_t stage(bbc_index* ix, int id, cudaStream_t st, F&& launch) {
     {
         std::lock_guard<std::mutex> lk(ix->prof_mu);
         ix->launches += 1;
-        if (ix->profile) {
+        if (ix->profile && !ix->capturing) {
             cudaEventRecord(b, st);
             ix->recs.push_back({id, a, b});
         }
@@ -544,6 +564,9 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "workspace_mb") {
         if (!(v >= 1)) return fail(BBC_ERR_ARG, "workspace_mb must be >= 1");
         ix->workspace_mb = v;
+    } else if (k == "graphs") {
+        if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "graphs must be 0 or 1");
+        ix->graphs = (int)v;
     } else if (k == "split") {
         if (!(v >= 0 && v <= 65536) || v != std::floor(v)) return fail(BBC_ERR_ARG, "split must be 0 (auto), 1 or a part count");
         ix->split = (int)v;
@@ -570,6 +593,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "profile") *v = ix->profile;
     else if (k == "probe_gemm") *v = ix->probe_gemm;
     else if (k == "split") *v = ix->split;
+    else if (k == "graphs") *v = ix->graphs;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -586,10 +610,51 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     Plan p = make_plan(ix, nq, nprobe, kc, k, false);
     char* ws;
     if ((rc = get_workspace(ix, st, p.total, &ws))) return rc;
-    for (int64_t q0 = 0; q0 < nq; q0 += p.chunk) {
-        const int64_t nc = std::min(p.chunk, nq - q0);
-        rc = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, out_ids + q0 * k, out_dists + q0 * k, st, 9);
-        if (rc) return rc;
+    auto run_all = [&]() -> int {
+        for (int64_t q0 = 0; q0 < nq; q0 += p.chunk) {
+            const int64_t nc = std::min(p.chunk, nq - q0);
+            int r = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, out_ids + q0 * k, out_dists + q0 * k, st, 9);
+            if (r) return r;
+        }
+        return BBC_OK;
+    };
+    if (!ix->graphs || st == nullptr) return run_all();
+    // CUDA graph of the whole launch sequence for this call shape
+    bbc_index::GraphKey key{queries, nq, k, nprobe, out_ids, out_dists, st, ix->kc_ratio, ix->buckets,
+                            ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8};
+    std::lock_guard<std::mutex> lk(ix->graph_mu);
+    auto it = ix->graph_cache.find(key);
+    if (it == ix->graph_cache.end()) {
+        const int64_t before = ix->launches;
+        CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+        ix->capturing = true;
+        rc = run_all();
+        ix->capturing = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (rc || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc ? rc : fail(BBC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(BBC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        if (ix->graph_cache.size() >= 32) {
+            cudaGraphExecDestroy(ix->graph_cache.begin()->second.exec);
+            ix->graph_cache.erase(ix->graph_cache.begin());
+        }
+        {
+            std::lock_guard<std::mutex> pl(ix->prof_mu);
+            const int64_t n = ix->launches - before;
+            ix->launches = before;
+            it = ix->graph_cache.emplace(key, bbc_index::GraphEntry{exec, n}).first;
+        }
+    }
+    CUDA_TRY(cudaGraphLaunch(it->second.exec, st));
+    {
+        std::lock_guard<std::mutex> pl(ix->prof_mu);
+        ix->launches += it->second.launches;
     }
     return BBC_OK;
 }
@@ -721,6 +786,113 @@ int bbc_probe(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe, i
         rc = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, nullptr, nullptr, st, 2,
                        out_lists + q0 * nprobe);
         if (rc) return rc;
+    }
+    return BBC_OK;
+}
+
+int bbc_autotune(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe,
+                 const char* cache_path, double* out_ms, void* stream) {
+    int rc = check_search_args(ix, queries, nq, k, nprobe, queries, queries);
+    if (rc) return rc;
+    if (nq < 1) return fail(BBC_ERR_ARG, "autotune needs at least one query");
+    char key[512];
+    snprintf(key, sizeof(key), "n=%lld,d=%d,nlist=%d,pq=%dx%d,metric=%d,nq=%lld,k=%d,nprobe=%d,kc_ratio=%.6g",
+             (long long)ix->dev.n, ix->dev.d, ix->dev.nlist, ix->dev.M, ix->dev.bits, ix->dev.metric, (long long)nq, k,
+             nprobe, ix->kc_ratio);
+    if (out_ms) *out_ms = 0.0;
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[1024];
+            int found_split = -1, found_m = -1;
+            while (fgets(line, sizeof(line), f)) {
+                char want[600];
+                snprintf(want, sizeof(want), "\"key\": \"%s\"", key);
+                if (!strstr(line, want)) continue;
+                static const char ks[] = "\"split\": ";
+                static const char kb[] = "\"buckets\": ";
+                const char* a = strstr(line, ks);
+                const char* b = strstr(line, kb);
+                if (a && b) { found_split = atoi(a + strlen(ks)); found_m = atoi(b + strlen(kb)); }
+            }
+            fclose(f);
+            if (found_split >= 0 && found_m >= 2 && found_m <= 256) {
+                ix->split = found_split;
+                ix->buckets = found_m;
+                return BBC_OK;
+            }
+        }
+    }
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t* oi = nullptr;
+    float* od = nullptr;
+    CUDA_TRY(cudaMalloc(&oi, (size_t)nq * k * 8));
+    if (cudaMalloc(&od, (size_t)nq * k * 4) != cudaSuccess) {
+        cudaFree(oi);
+        return fail(BBC_ERR_OOM, "autotune output buffers");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved_split = ix->split, saved_m = ix->buckets, saved_graphs = ix->graphs;
+    ix->graphs = 0;
+    auto time_it = [&](double* ms) -> int {
+        int r = bbc_search(ix, queries, nq, k, nprobe, oi, od, stream);       // warm-up (allocations)
+        if (r) return r;
+        double best = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            r = bbc_search(ix, queries, nq, k, nprobe, oi, od, stream);
+            if (r) return r;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return fail(BBC_ERR_CUDA, "autotune timing");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = std::min(best, (double)t);
+        }
+        *ms = best;
+        return BBC_OK;
+    };
+    std::vector<int> splits = {1};
+    const int64_t slots = 2ll * ix->dev.num_sms;
+    for (int G : {2, 4, 8, 16, 32, 64, 128})
+        if (G <= nprobe && nq * G <= 64 * slots && nq < 8 * slots) splits.push_back(G);
+    double best_ms = 1e300;
+    int best_split = 1, best_m = ix->buckets;
+    for (int G : splits) {
+        ix->split = G;
+        double t;
+        if ((rc = time_it(&t))) break;
+        if (t < best_ms) { best_ms = t; best_split = G; }
+    }
+    if (!rc) {
+        ix->split = best_split;
+        for (int m : {32, 64, 128, 256}) {
+            ix->buckets = m;
+            double t;
+            if ((rc = time_it(&t))) break;
+            if (t < best_ms * 0.98 || (m == best_m && t < best_ms)) { best_ms = t; best_m = m; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(oi);
+    cudaFree(od);
+    ix->graphs = saved_graphs;
+    if (rc) {
+        ix->split = saved_split;
+        ix->buckets = saved_m;
+        return rc;
+    }
+    ix->split = best_split;
+    ix->buckets = best_m;
+    if (out_ms) *out_ms = best_ms;
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "{\"key\": \"%s\", \"split\": %d, \"buckets\": %d, \"ms\": %.4f}\n", key, best_split, best_m,
+                    best_ms);
+            fclose(f);
+        }
     }
     return BBC_OK;
 }

@@ -375,3 +375,66 @@ def test_split_scan_equals_one_cta_per_query(bbc, kind):
         for f in ("d_min", "d_max", "sh", "sample_lists", "sample_size", "scanned", "tau", "below"):
             assert np.array_equal(got[2][f], ref[2][f]), (split, f)
         assert np.array_equal(got[3], ref[3]) and np.array_equal(got[4], ref[4]), split
+
+
+def test_graph_replay_matches_eager(bbc):
+    """With 'graphs' on, the first call captures and the next ones replay; a
+    replay reads the current contents of the same query buffer."""
+    h, idx, q = dev_index(bbc, "sift")
+    bbc.bbc_set_param(h, "kc_ratio", 1.5)
+    nq, k, nprobe = len(q), 300, 16
+    side = torch.cuda.Stream()
+    qd = cuda(q)
+    eager_i = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    eager_d = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_search(h, qd, nq, k, nprobe, eager_i, eager_d, side)
+    qflip = cuda(q[::-1].copy())
+    flip_i = torch.empty_like(eager_i)
+    flip_d = torch.empty_like(eager_d)
+    bbc.bbc_search(h, qflip, nq, k, nprobe, flip_i, flip_d, side)
+    side.synchronize()
+    bbc.bbc_set_param(h, "graphs", 1)
+    try:
+        gi = torch.empty_like(eager_i)
+        gd = torch.empty_like(eager_d)
+        qbuf = qd.clone()
+        for rep in range(3):
+            bbc.bbc_search(h, qbuf, nq, k, nprobe, gi, gd, side)
+            side.synchronize()
+            assert torch.equal(gi, eager_i) and torch.equal(gd, eager_d), rep
+        qbuf.copy_(qflip)
+        torch.cuda.synchronize()
+        bbc.bbc_search(h, qbuf, nq, k, nprobe, gi, gd, side)
+        side.synchronize()
+        assert torch.equal(gi, flip_i) and torch.equal(gd, flip_d)
+    finally:
+        bbc.bbc_set_param(h, "graphs", 0)
+    bbc.bbc_stream_status(h, side)
+
+
+def test_autotune_picks_and_caches(bbc, tmp_path):
+    h, idx, q = dev_index(bbc, "tiny")
+    bbc.bbc_set_param(h, "kc_ratio", 2.0)
+    nq, k, nprobe = len(q), 100, 12
+    qd = cuda(q)
+    ref_i = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    ref_d = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_search(h, qd, nq, k, nprobe, ref_i, ref_d)
+    cache = str(tmp_path / "tune.jsonl")
+    try:
+        ms = bbc.bbc_autotune(h, qd, nq, k, nprobe, cache)
+        assert ms > 0
+        chosen = (bbc.bbc_get_param(h, "split"), bbc.bbc_get_param(h, "buckets"))
+        assert open(cache).read().count('"split"') == 1
+        bbc.bbc_set_param(h, "split", 0)
+        bbc.bbc_set_param(h, "buckets", 64)
+        assert bbc.bbc_autotune(h, qd, nq, k, nprobe, cache) == 0.0          # from the cache
+        assert (bbc.bbc_get_param(h, "split"), bbc.bbc_get_param(h, "buckets")) == chosen
+        gi = torch.empty_like(ref_i)
+        gd = torch.empty_like(ref_d)
+        bbc.bbc_search(h, qd, nq, k, nprobe, gi, gd)
+        sync_ok(bbc, h)
+        assert torch.equal(gi, ref_i) and torch.equal(gd, ref_d)
+    finally:
+        bbc.bbc_set_param(h, "split", 0)
+        bbc.bbc_set_param(h, "buckets", 64)
