@@ -246,6 +246,42 @@ int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint3
                     const int64_t* cand_count, int64_t kc, int32_t k, int64_t* out_ids,
                     float* out_dists, void* stream);
 
+/* ---- serving: continuous batching of single-query requests ----
+ * A server owns one worker thread and `streams` CUDA streams.  Requests
+ * (one query, its own k and nprobe) queue on the host; whenever a stream is
+ * free the worker admits waiting requests, oldest first, into one mixed batch
+ * (bbc_search_ex) while the batch has fewer than max_batch requests and the
+ * candidate-buffer bytes of all admitted, unfinished requests stay within
+ * cand_bytes_budget (a lone request larger than the budget is admitted when
+ * nothing else is in flight).  Batches on different streams overlap on the
+ * GPU, so requests that arrive while others run start as soon as a stream
+ * and memory free up.  Each request's result equals bbc_search on that query
+ * alone.  Candidate-buffer bytes of a request = 8 * (total length of its
+ * nprobe longest lists) + 8 * K_c. */
+typedef struct bbc_server bbc_server;
+typedef struct {
+    int32_t max_batch;            /* requests per batch, >= 1 */
+    int32_t streams;              /* batches in flight, 1..16 */
+    int64_t cand_bytes_budget;    /* admission budget in bytes, >= 1 */
+} bbc_serve_config;
+typedef struct {
+    int64_t submitted, completed, batches;
+    int64_t inflight_bytes_peak;  /* largest admitted total observed */
+    double p50_ms, p99_ms;        /* submit -> result ready, over completed requests */
+    double mean_batch;            /* requests per batch */
+    double wall_s;                /* time since start */
+} bbc_serve_stats_t;
+int bbc_serve_start(bbc_index* ix, const bbc_serve_config* cfg, bbc_server** out);
+/* host_query: d floats (copied).  Returns a ticket for bbc_serve_poll. */
+int bbc_serve_submit(bbc_server* sv, const float* host_query, int32_t k, int32_t nprobe, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for the ticket; on success copies its
+ * k ids and distances into the HOST buffers and forgets the ticket.
+ * BBC_ERR_TIMEOUT if not ready in time, BBC_ERR_ARG for an unknown ticket. */
+int bbc_serve_poll(bbc_server* sv, uint64_t ticket, int64_t* ids, float* dists, int32_t timeout_ms);
+int bbc_serve_stats(bbc_server* sv, bbc_serve_stats_t* out);
+/* Finishes in-flight batches, stops the worker and frees the server. */
+int bbc_serve_stop(bbc_server* sv);
+
 /* Per-stage timing (the GPU counterpart of the paper's time breakdown,
  * Figure 2).  With parameter "profile" = 1 the library records a CUDA event
  * pair on the launch stream around every kernel it launches.  This call

@@ -29,7 +29,8 @@ METRICS = {"l2": 0, "ip": 1}
 # Exported symbols declared in include/bbc.h (checked by the ABI test).
 SYMBOLS = ["bbc_index_create", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
            "bbc_get_param", "bbc_search", "bbc_search_ex", "bbc_search_host", "bbc_probe_scores", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
-           "bbc_rerank_topk", "bbc_autotune", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
+           "bbc_rerank_topk", "bbc_autotune", "bbc_serve_start", "bbc_serve_submit", "bbc_serve_poll",
+           "bbc_serve_stats", "bbc_serve_stop", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
 NUM_STAGES = 7
 STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk"]
 
@@ -51,6 +52,16 @@ class IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("nlist", C.c_int32), ("metric", C.c_int32),
                 ("pq_m", C.c_int32), ("pq_bits", C.c_int32), ("max_list_len", C.c_int32),
                 ("vectors_u8_exact", C.c_int32), ("device", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+class ServeConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("streams", C.c_int32), ("cand_bytes_budget", C.c_int64)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("batches", C.c_int64),
+                ("inflight_bytes_peak", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("mean_batch", C.c_double), ("wall_s", C.c_double)]
 
 
 class CollectorState(C.Structure):
@@ -105,6 +116,11 @@ def lib():
             L.bbc_stream_status.argtypes = [vp, vp]
             L.bbc_profile_read.argtypes = [vp, vp, vp, C.c_int]
             L.bbc_autotune.argtypes = [vp, vp, i64, i32, i32, C.c_char_p, vp, vp]
+            L.bbc_serve_start.argtypes = [vp, C.POINTER(ServeConfig), C.POINTER(vp)]
+            L.bbc_serve_submit.argtypes = [vp, vp, i32, i32, C.POINTER(C.c_uint64)]
+            L.bbc_serve_poll.argtypes = [vp, C.c_uint64, vp, vp, i32]
+            L.bbc_serve_stats.argtypes = [vp, C.POINTER(ServeStats)]
+            L.bbc_serve_stop.argtypes = [vp]
             for name in SYMBOLS:
                 if getattr(L, name).restype is None and name not in ("bbc_last_error", "bbc_version"):
                     getattr(L, name).restype = C.c_int
@@ -247,6 +263,38 @@ def bbc_autotune(handle: int, queries, nq: int, k: int, nprobe: int, cache_path:
     _check(lib().bbc_autotune(handle, _ptr(queries), nq, k, nprobe, cache_path.encode() if cache_path else None,
                               C.byref(ms), _stream(stream)))
     return ms.value
+
+
+def bbc_serve_start(handle: int, max_batch: int = 256, streams: int = 4, cand_bytes_budget: int = 8 << 30) -> int:
+    out = C.c_void_p()
+    cfg = ServeConfig(max_batch, streams, cand_bytes_budget)
+    _check(lib().bbc_serve_start(handle, C.byref(cfg), C.byref(out)))
+    return out.value
+
+
+def bbc_serve_submit(server: int, host_query, k: int, nprobe: int) -> int:
+    qa = np.ascontiguousarray(host_query, dtype=np.float32)
+    t = C.c_uint64()
+    _check(lib().bbc_serve_submit(server, qa.ctypes.data, k, nprobe, C.byref(t)))
+    return t.value
+
+
+def bbc_serve_poll(server: int, ticket: int, k: int, timeout_ms: int = -1):
+    """(ids int64[k], dists float32[k]) once ready; raises BBCError(-7) on timeout."""
+    ids = np.empty(k, dtype=np.int64)
+    dd = np.empty(k, dtype=np.float32)
+    _check(lib().bbc_serve_poll(server, ticket, ids.ctypes.data, dd.ctypes.data, timeout_ms))
+    return ids, dd
+
+
+def bbc_serve_stats(server: int) -> dict:
+    st = ServeStats()
+    _check(lib().bbc_serve_stats(server, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in ServeStats._fields_}
+
+
+def bbc_serve_stop(server: int) -> None:
+    _check(lib().bbc_serve_stop(server))
 
 
 def bbc_stream_status(handle: int, stream=None) -> None:

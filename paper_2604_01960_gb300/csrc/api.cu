@@ -1037,4 +1037,5 @@ int index_device(const bbc_index* ix) { return ix->device; }
 int64_t index_cap(const bbc_index* ix, int nprobe) { return ix->cap_prefix[nprobe]; }
 int index_buckets(const bbc_index* ix) { return ix->buckets; }
 int index_sample_lists(const bbc_index* ix) { return ix->sample_lists; }
+int64_t index_kc(const bbc_index* ix, int k) { return kc_for(ix, k); }
 }  // namespace bbc
