@@ -78,6 +78,15 @@ def lib():
                                                 C.POINTER(Codebook), vp, vp, vp]
             L.oracle_rerank.argtypes = [vp, vp, i32, i32, vp, i64, vp]
             L.oracle_topk_final.argtypes = [vp, vp, i64, i32, vp, vp]
+            L.oracle_bf16_bits.restype = C.c_uint16
+            L.oracle_bf16_bits.argtypes = [C.c_float]
+            L.oracle_bf16_value.restype = C.c_double
+            L.oracle_bf16_value.argtypes = [C.c_uint16]
+            L.oracle_e4m3_bits.restype = C.c_uint8
+            L.oracle_e4m3_bits.argtypes = [C.c_float]
+            L.oracle_e4m3_value.restype = C.c_double
+            L.oracle_e4m3_value.argtypes = [C.c_uint8]
+            L.oracle_prec_copy.argtypes = [vp, i64, i32, i32, i32, vp, vp]
             L.oracle_search.restype = i32
             L.oracle_search.argtypes = [C.POINTER(_Index), vp, i64, i32, i32, i64, i32, i32, i32,
                                         vp, vp, vp]
@@ -251,3 +260,43 @@ def bruteforce(queries, x, k: int, metric="l2"):
     lib().oracle_bruteforce(_p(q), q.shape[0], _p(xv), xv.shape[0], xv.shape[1], _metric(metric),
                             k, _p(oi), _p(od))
     return oi, od
+
+
+# ---------------------------------------------------------------------------
+# Low-precision copies for the precision form of the re-rank
+# ---------------------------------------------------------------------------
+def bf16_bits(x) -> np.ndarray:
+    """bfloat16 bits of each FP32 value (nearest, ties to even)."""
+    L = lib()
+    x = np.ascontiguousarray(x, dtype=np.float32).ravel()
+    return np.array([L.oracle_bf16_bits(float(v)) for v in x], dtype=np.uint16)
+
+
+def bf16_value(bits) -> np.ndarray:
+    L = lib()
+    return np.array([L.oracle_bf16_value(int(b)) for b in np.ravel(bits)], dtype=np.float64)
+
+
+def e4m3_bits(x) -> np.ndarray:
+    """OCP E4M3 bits of each FP32 value (nearest, ties to even, saturating)."""
+    L = lib()
+    x = np.ascontiguousarray(x, dtype=np.float32).ravel()
+    return np.array([L.oracle_e4m3_bits(float(v)) for v in x], dtype=np.uint8)
+
+
+def e4m3_value(bits) -> np.ndarray:
+    L = lib()
+    return np.array([L.oracle_e4m3_value(int(b)) for b in np.ravel(bits)], dtype=np.float64)
+
+
+def prec_copy(vectors: np.ndarray, prec: int, dpad: int | None = None):
+    """Low-precision copy of the vectors (prec 1 BF16, 2 E4M3 with one scale
+    per vector) and per-vector (s, e_v, ||x||, 0) in FP64.  Rows are padded
+    with zeros to dpad (default: d rounded up to 16)."""
+    v = np.ascontiguousarray(vectors, dtype=np.float32)
+    n, d = v.shape
+    dpad = dpad or (d + 15) // 16 * 16
+    rows = np.zeros((n, dpad), dtype=np.uint16 if prec == 1 else np.uint8)
+    meta = np.zeros((n, 4), dtype=np.float64)
+    lib().oracle_prec_copy(_p(v), n, d, dpad, prec, _p(rows), _p(meta))
+    return rows, meta

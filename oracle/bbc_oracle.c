@@ -29,9 +29,19 @@
  *   oracle_topk_final     the k smallest exact distances, ascending.
  *   oracle_search         the whole path for a batch of queries.
  *   oracle_bruteforce     exact kNN over the whole data set (FP64).
+ *   oracle_bf16_*, oracle_e4m3_*, oracle_prec_copy
+ *                         the low-precision copies of the vectors used by the
+ *                         precision form of the re-rank (the paper re-ranks
+ *                         "with exact distances", Section 2; the copies and
+ *                         their per-vector error e_v are this implementation's
+ *                         reading of how to do that cheaply).  Written from
+ *                         the two formats' definitions: bfloat16 = binary32
+ *                         with 7 stored fraction bits; OCP E4M3 = 4 exponent
+ *                         bits (bias 7), 3 fraction bits, largest finite 448.
  *
  * Orders: every "smallest" is by (value, id) ascending, id breaking ties.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -507,4 +517,99 @@ void oracle_bruteforce(const float* queries, int64_t nq, const float* x, int64_t
     }
     free(dist);
     free(ids);
+}
+
+/* ------------------------------------------------------------------ */
+/* low-precision copies (precision form of the re-rank)                 */
+/* ------------------------------------------------------------------ */
+/* bfloat16 bits of x: binary32's sign and 8 exponent bits with the fraction
+ * rounded to 7 bits, to nearest, ties to even.  Values below 2^-126 sit on
+ * the subnormal grid of spacing 2^-133.  NaN -> 0x7FC0. */
+uint16_t oracle_bf16_bits(float x) {
+    if (isnan(x)) return 0x7FC0;
+    const double a = fabs((double)x);
+    double r;
+    if (a == 0.0 || isinf(x)) {
+        r = a;
+    } else if (a < ldexp(1.0, -126)) {
+        r = ldexp(nearbyint(ldexp(a, 133)), -133);
+    } else {
+        int e;
+        frexp(a, &e);                                  /* a in [2^(e-1), 2^e) */
+        r = ldexp(nearbyint(ldexp(a, 8 - e)), e - 8);  /* 8 significant bits */
+    }
+    float y = r >= ldexp(1.0, 128) ? INFINITY : (float)r;   /* exact below the overflow */
+    if (signbit(x)) y = -y;
+    uint32_t u;
+    memcpy(&u, &y, 4);
+    return (uint16_t)(u >> 16);
+}
+
+double oracle_bf16_value(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* E4M3 bits of x: normals (1 + f/8) 2^(e-7), e = 1..15 (e = 15, f = 7 is
+ * NaN), subnormals f 2^-9; nearest, ties to even; |x| >= 448 saturates to
+ * 448.  NaN -> 0x7F. */
+uint8_t oracle_e4m3_bits(float x) {
+    if (isnan(x)) return 0x7F;
+    const uint8_t sgn = signbit(x) ? 0x80 : 0x00;
+    const double a = fabs((double)x);
+    if (a >= 448.0) return (uint8_t)(sgn | 0x7E);
+    if (a < ldexp(1.0, -6)) return (uint8_t)(sgn | (uint8_t)nearbyint(a * 512.0));   /* 8 -> 2^-6 */
+    int e;
+    frexp(a, &e);
+    int E = e - 1;                                     /* a = 1.f * 2^E, E >= -6 */
+    double q = nearbyint(ldexp(a, 3 - E));             /* 8..16 */
+    if (q == 16.0) { q = 8.0; E += 1; }
+    return (uint8_t)(sgn | (uint8_t)(((E + 7) << 3) | ((int)q - 8)));
+}
+
+double oracle_e4m3_value(uint8_t b) {
+    const int e = (b >> 3) & 15, f = b & 7;
+    const double v = e == 0 ? ldexp((double)f, -9) : ldexp((double)(8 + f), e - 10);
+    return (b & 0x80) ? -v : v;
+}
+
+/* Copy of n vectors [n*d] into rows [n*dpad] (zero padded): prec 1 = BF16 bits
+ * (u16), prec 2 = E4M3 bytes of x / s with s = amax / 448 in FP32 (1 when that
+ * is not a positive finite number).  meta4 per vector: s, e_v = ||x - v~||_2
+ * (v~ = the copy's value times s), ||x||_2, 0 -- FP64, not rounded. */
+void oracle_prec_copy(const float* v, int64_t n, int32_t d, int32_t dpad, int32_t prec, void* rows,
+                      double* meta4) {
+    for (int64_t i = 0; i < n; ++i) {
+        const float* x = v + (size_t)i * d;
+        float amax = 0.0f;
+        for (int32_t j = 0; j < d; ++j) amax = fabsf(x[j]) > amax ? fabsf(x[j]) : amax;
+        float s = 1.0f;
+        if (prec == 2) {
+            s = amax / 448.0f;
+            if (!(s > 0.0f) || !isfinite(s)) s = 1.0f;
+        }
+        double e2 = 0.0, n2 = 0.0;
+        for (int32_t j = 0; j < dpad; ++j) {
+            const float xj = j < d ? x[j] : 0.0f;
+            double vt;
+            if (prec == 2) {
+                const float y = xj / s;
+                const uint8_t c = oracle_e4m3_bits(y);
+                ((uint8_t*)rows)[(size_t)i * dpad + j] = c;
+                vt = oracle_e4m3_value(c) * (double)s;
+            } else {
+                const uint16_t b = oracle_bf16_bits(xj);
+                ((uint16_t*)rows)[(size_t)i * dpad + j] = b;
+                vt = oracle_bf16_value(b);
+            }
+            e2 += ((double)xj - vt) * ((double)xj - vt);
+            n2 += (double)xj * (double)xj;
+        }
+        meta4[i * 4 + 0] = s;
+        meta4[i * 4 + 1] = sqrt(e2);
+        meta4[i * 4 + 2] = sqrt(n2);
+        meta4[i * 4 + 3] = 0.0;
+    }
 }
