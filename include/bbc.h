@@ -122,6 +122,20 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *   "probe_gemm"   1 = approximate probe scores on the tensor cores (tcgen05 BF16
  *                  GEMM with a 3-term split), 0 = FP32 SIMT.  Either way the
  *                  probe result is exact (see bbc_probe).  Default 1.
+ *   "precision"    precision form of the re-rank (step S8 with a low-precision
+ *                  copy; the paper re-ranks "with exact distances", Section 2,
+ *                  and leaves their precision open): 0 = FP32 rows (default),
+ *                  1 = BF16 copy, 2 = FP8-E4M3 copy with one scale per vector.
+ *                  Setting 1 or 2 builds the copy on the device (waits for all
+ *                  work on the device first; not to be called while other
+ *                  threads search this index).  Candidates are scored from the
+ *                  copy with a rigorous per-candidate bound; only those whose
+ *                  interval straddles the k-th place are re-scored from the
+ *                  FP32 rows, and FP64 decides what FP32 cannot.  The result
+ *                  set is the same as with the FP32 re-rank decided in FP64;
+ *                  reported distances of members placed by the copy's bound
+ *                  are the copy's scores (see bbc_rerank_bounds).  Applies when
+ *                  the exact u8 re-rank is not in use.
  * Unknown key or out-of-range value: BBC_ERR_ARG. */
 int bbc_set_param(bbc_index* ix, const char* key, double value);
 int bbc_get_param(const bbc_index* ix, const char* key, double* value);
@@ -241,10 +255,34 @@ int bbc_collect_static(bbc_index* ix, const float* queries, int64_t nq, int32_t 
 
 /* Exact re-rank of candidates and final top-k (Algorithm 4, last two lines).
  *   cand_ids   device u32 [nq * kc]; cand_count device i64 [nq]
- *   out_ids / out_dists as in bbc_search. */
+ *   out_ids / out_dists as in bbc_search.
+ * With "precision" set, the precision form of the re-rank runs instead. */
 int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint32_t* cand_ids,
                     const int64_t* cand_count, int64_t kc, int32_t k, int64_t* out_ids,
                     float* out_dists, void* stream);
+
+/* First pass of the precision re-rank alone: for each candidate i < count of
+ * each query, the score d^ from the low-precision copy (squared L2, or minus
+ * the inner product) and a bound rho with |d^ - d64| <= rho, d64 being the
+ * FP64 distance of the FP32-stored vector.
+ *   cand_ids  device u32 [nq * kc]; cand_count device i64 [nq]
+ *   out_dist, out_rho  device f32 [nq * kc] (entries past count untouched)
+ * BBC_ERR_ARG when no copy has been built ("precision" 0). */
+int bbc_rerank_bounds(bbc_index* ix, const float* queries, int64_t nq, const uint32_t* cand_ids,
+                      const int64_t* cand_count, int64_t kc, float* out_dist, float* out_rho,
+                      void* stream);
+
+/* The low-precision copy itself, for inspection: out_rows device buffer of
+ * n * dpad elements (dpad = d rounded up to a multiple of 16; BF16 bits as
+ * u16 for "precision" 1, E4M3 bytes for 2; row i = vector id i, zero padded),
+ * out_meta device f32 [n * 4] = {scale s (1 for BF16), e_v = ||v - s v~||_2
+ * rounded up, ||v||_2 rounded up, 0}.  BBC_ERR_ARG without a copy. */
+int bbc_precision_copy(bbc_index* ix, void* out_rows, float* out_meta, void* stream);
+
+/* Running totals of the precision re-rank since the last reset (synchronises
+ * the device): out4[0] candidates scored from the copy, [1] candidates
+ * re-scored in FP32, [2] candidates scored in FP64, [3] final members. */
+int bbc_precision_stats(bbc_index* ix, int64_t* out4, int reset);
 
 /* ---- serving: continuous batching of single-query requests ----
  * A server owns one worker thread and `streams` CUDA streams.  Requests
@@ -290,8 +328,10 @@ int bbc_serve_stop(bbc_server* sv);
  * kernels launched since the last reset into *launches (may be NULL; counted
  * whether or not profiling is on), and clears both when reset != 0.
  * Stages: 0 probe scores, 1 probe selection, 2 lookup table, 3 scan +
- * result buffer, 4 final selection, 5 re-rank, 6 top-k. */
-#define BBC_NUM_STAGES 7
+ * result buffer, 4 final selection, 5 re-rank (the copy's scores in the
+ * precision form), 6 top-k, 7 precision classification and FP64 decision,
+ * 8 precision FP32 recheck. */
+#define BBC_NUM_STAGES 9
 int bbc_profile_read(bbc_index* ix, double* stage_ms, int64_t* launches, int reset);
 
 /* Synchronise `stream`, then read and clear the index's device status word.

@@ -29,10 +29,11 @@ METRICS = {"l2": 0, "ip": 1}
 # Exported symbols declared in include/bbc.h (checked by the ABI test).
 SYMBOLS = ["bbc_index_create", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
            "bbc_get_param", "bbc_search", "bbc_search_ex", "bbc_search_host", "bbc_probe_scores", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
-           "bbc_rerank_topk", "bbc_autotune", "bbc_serve_start", "bbc_serve_submit", "bbc_serve_poll",
+           "bbc_rerank_topk", "bbc_rerank_bounds", "bbc_precision_copy", "bbc_precision_stats", "bbc_autotune", "bbc_serve_start", "bbc_serve_submit", "bbc_serve_poll",
            "bbc_serve_stats", "bbc_serve_stop", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
-NUM_STAGES = 7
-STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk"]
+NUM_STAGES = 9
+STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk", "prec_classify",
+          "prec_recheck"]
 
 
 class BBCError(RuntimeError):
@@ -113,6 +114,9 @@ def lib():
             L.bbc_collect.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp, vp, vp]
             L.bbc_collect_static.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp, vp, vp]
             L.bbc_rerank_topk.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, vp, vp]
+            L.bbc_rerank_bounds.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, vp]
+            L.bbc_precision_copy.argtypes = [vp, vp, vp, vp]
+            L.bbc_precision_stats.argtypes = [vp, vp, C.c_int]
             L.bbc_stream_status.argtypes = [vp, vp]
             L.bbc_profile_read.argtypes = [vp, vp, vp, C.c_int]
             L.bbc_autotune.argtypes = [vp, vp, i64, i32, i32, C.c_char_p, vp, vp]
@@ -246,6 +250,24 @@ def bbc_rerank_topk(handle: int, queries, nq: int, cand_ids, cand_count, kc: int
                     stream=None) -> None:
     _check(lib().bbc_rerank_topk(handle, _ptr(queries), nq, _ptr(cand_ids), _ptr(cand_count), kc, k,
                                  _ptr(out_ids), _ptr(out_dists), _stream(stream)))
+
+
+def bbc_rerank_bounds(handle: int, queries, nq: int, cand_ids, cand_count, kc: int, out_dist, out_rho,
+                      stream=None) -> None:
+    """Scores of the candidates from the low-precision copy and their bounds."""
+    _check(lib().bbc_rerank_bounds(handle, _ptr(queries), nq, _ptr(cand_ids), _ptr(cand_count), kc,
+                                   _ptr(out_dist), _ptr(out_rho), _stream(stream)))
+
+
+def bbc_precision_copy(handle: int, out_rows, out_meta, stream=None) -> None:
+    _check(lib().bbc_precision_copy(handle, _ptr(out_rows), _ptr(out_meta), _stream(stream)))
+
+
+def bbc_precision_stats(handle: int, reset: bool = True) -> dict:
+    """Totals of the precision re-rank since the last reset."""
+    t = (C.c_int64 * 4)()
+    _check(lib().bbc_precision_stats(handle, t, 1 if reset else 0))
+    return {"scored": t[0], "fp32_rechecked": t[1], "fp64_scored": t[2], "final": t[3]}
 
 
 def bbc_profile_read(handle: int, reset: bool = True):

@@ -98,16 +98,20 @@ struct bbc_index {
     int sample_lists = 8;
     int rerank_u8 = 1;
     int probe_gemm = 1;
+    void* lp_rows = nullptr;               // low-precision copy (precision re-rank)
+    float4* lp_meta = nullptr;
+    unsigned long long* prec_totals = nullptr;   // [4] device counters of the precision re-rank
     int split = 0;            // 0 automatic, 1 one CTA per query, G >= 2 CTAs per query
     int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
     bool capturing = false;
     struct GraphKey {
         const void* q; int64_t nq; int k; int nprobe; void* oi; void* od; cudaStream_t st;
-        double kc_ratio; int buckets, sample_lists, split, probe_gemm, rerank;
+        double kc_ratio; int buckets, sample_lists, split, probe_gemm, rerank, prec;
         bool operator<(const GraphKey& o) const {
-            return std::tie(q, nq, k, nprobe, oi, od, st, kc_ratio, buckets, sample_lists, split, probe_gemm, rerank) <
+            return std::tie(q, nq, k, nprobe, oi, od, st, kc_ratio, buckets, sample_lists, split, probe_gemm, rerank,
+                            prec) <
                    std::tie(o.q, o.nq, o.k, o.nprobe, o.oi, o.od, o.st, o.kc_ratio, o.buckets, o.sample_lists, o.split,
-                            o.probe_gemm, o.rerank);
+                            o.probe_gemm, o.rerank, o.prec);
         }
     };
     struct GraphEntry { cudaGraphExec_t exec; int64_t launches; };
@@ -131,6 +135,9 @@ struct bbc_index {
         for (auto& kv : ws) cudaFree(kv.second.base);
         for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (void* p : owned) cudaFree(p);
+        cudaFree(lp_rows);
+        cudaFree(lp_meta);
+        cudaFree(prec_totals);
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
@@ -166,13 +173,49 @@ struct ChunkShape {
 
 struct Plan {
     int64_t chunk;        // queries per chunk (uniform batches)
+    int64_t chunk_slots;  // candidate slots of a mixed chunk (sum of K_c)
     int nprobe;
     int64_t kc;
     int k;
     int64_t cap;
     size_t off_scores, off_probe, off_lut, off_state, off_region, off_cand, off_count, off_cdist,
-        off_q, off_ids, off_dists, off_abf, off_keys, off_params, off_counters, total;
+        off_q, off_ids, off_dists, off_abf, off_keys, off_params, off_counters, off_prec, total;
 };
+
+// The precision re-rank runs when a low-precision copy exists and the exact u8
+// re-rank (already exact at one byte per component) is not in use.
+bool prec_active(const bbc_index* ix) {
+    return ix->dev.prec > 0 && ix->dev.vec_lp && !(ix->rerank_u8 && ix->dev.vec_u8);
+}
+
+// Scratch of the precision re-rank inside a workspace: per candidate slot
+// rho, uncertain ids, final ids / distances, band ids (4 B each) and band
+// FP64 distances (8 B); per query n_fin, n_unc, item offsets and ||q||.
+size_t prec_bytes(int64_t nq, int64_t slots) {
+    size_t o = 0;
+    for (int i = 0; i < 5; ++i) o = align_up(o + (size_t)slots * 4);
+    o = align_up(o + (size_t)slots * 8);
+    o = align_up(o + (size_t)nq * 8 * 2 + (size_t)(nq + 1) * 8 + (size_t)nq * 4);
+    return o;
+}
+PrecArgs prec_args(const bbc_index* ix, char* base, int64_t nq, int64_t slots) {
+    PrecArgs a{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { char* p = base + o; o = align_up(o + bytes); return p; };
+    a.rho = reinterpret_cast<float*>(take((size_t)slots * 4));
+    a.unc = reinterpret_cast<uint32_t*>(take((size_t)slots * 4));
+    a.fin_id = reinterpret_cast<uint32_t*>(take((size_t)slots * 4));
+    a.fin_d = reinterpret_cast<float*>(take((size_t)slots * 4));
+    a.band_id = reinterpret_cast<uint32_t*>(take((size_t)slots * 4));
+    a.band_d = reinterpret_cast<double*>(take((size_t)slots * 8));
+    char* pq = take((size_t)nq * 8 * 2 + (size_t)(nq + 1) * 8 + (size_t)nq * 4);
+    a.n_fin = reinterpret_cast<int64_t*>(pq);
+    a.n_unc = a.n_fin + nq;
+    a.item_off = a.n_unc + nq;
+    a.qnorm = reinterpret_cast<float*>(a.item_off + nq + 1);
+    a.totals = ix->prec_totals;
+    return a;
+}
 
 constexpr int64_t kTopkSmemMax = 16384;     // K_c handled by the shared-memory top-k
 
@@ -194,6 +237,7 @@ size_t layout(const bbc_index* ix, const ChunkShape& c, Plan& p) {
     p.off_keys = o; o = align_up(o + (c.max_kc > kTopkSmemMax ? (size_t)c.sum_kc * 8 : 0));
     p.off_params = o; o = align_up(o + (c.mixed ? (size_t)(c.nq + 1) * 8 * 7 : 0));
     p.off_counters = o; o = align_up(o + 16);
+    p.off_prec = o; o = align_up(o + (prec_active(ix) ? prec_bytes(c.nq, c.sum_kc) : 0));
     p.total = o;
     return o;
 }
@@ -279,6 +323,30 @@ cudaError_t stage(bbc_index* ix, int id, cudaStream_t st, F&& launch) {
     return e;
 }
 
+// S8 + S9 for a chunk: the plain re-rank and top-k, or the precision form
+// (low-precision scores, classification, FP32 recheck, FP64 decision, top-k
+// of the final members).  maxk: the largest k of the chunk.
+int run_rerank(bbc_index* ix, int64_t nc, const RerankArgs& ra, const PrecArgs* pa, int maxk, cudaStream_t st) {
+    const DevIndex& d = ix->dev;
+    if (!pa) {
+        CUDA_TRY(stage(ix, 5, st, [&] { return launch_rerank(d, nc, ra, st); }));
+        CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(d, nc, ra, st); }));
+        return BBC_OK;
+    }
+    CUDA_TRY(stage(ix, 5, st, [&] { return launch_prec_score(d, nc, ra, *pa, st); }));
+    CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_classify(d, nc, ra, *pa, st); }));
+    CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_plan(nc, *pa, st); }));
+    CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_recheck(d, nc, ra, *pa, st); }));
+    CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_finalize(d, nc, ra, *pa, st); }));
+    RerankArgs rb = ra;
+    rb.cand = pa->fin_id;
+    rb.cdist = pa->fin_d;
+    rb.cand_count = pa->n_fin;
+    rb.kc = maxk;
+    CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(d, nc, rb, st); }));
+    return BBC_OK;
+}
+
 // The launch sequence for one chunk.
 int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc, int64_t* out_ids,
               float* out_dists, cudaStream_t st, int stop_after /* 9 = all */,
@@ -327,8 +395,62 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + p.off_keys);
     RerankArgs ra{q, cand, count, p.kc, ix->rerank_u8 && d.vec_u8 != nullptr, cdist, p.k, out_ids,
                   out_dists, p.kc > kTopkSmemMax ? keys : nullptr, qp};
-    CUDA_TRY(stage(ix, 5, st, [&] { return launch_rerank(d, nc, ra, st); }));
-    CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(d, nc, ra, st); }));
+    if (prec_active(ix)) {
+        // slots of this chunk: sum of K_c (the per-query offsets index into them)
+        const int64_t slots = qp.cand_off ? p.chunk_slots : nc * p.kc;
+        const PrecArgs pa = prec_args(ix, ws + p.off_prec, nc, slots);
+        return run_rerank(ix, nc, ra, &pa, p.k, st);
+    }
+    return run_rerank(ix, nc, ra, nullptr, p.k, st);
+}
+
+// (Re)builds the low-precision copy for the precision re-rank; 0 drops it.
+// Waits for all work on the device first and drops cached graphs, which hold
+// the index's device pointers.
+int build_precision(bbc_index* ix, int prec) {
+    DeviceGuard g(ix->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    {
+        std::lock_guard<std::mutex> lk(ix->graph_mu);
+        for (auto& kv : ix->graph_cache) cudaGraphExecDestroy(kv.second.exec);
+        ix->graph_cache.clear();
+    }
+    const size_t old_es = ix->dev.prec == 1 ? 2 : 1;
+    if (ix->lp_rows) ix->info.device_bytes -= (int64_t)((size_t)ix->dev.n * ix->dev.dpad * old_es + (size_t)ix->dev.n * 16);
+    cudaFree(ix->lp_rows);
+    cudaFree(ix->lp_meta);
+    ix->lp_rows = nullptr;
+    ix->lp_meta = nullptr;
+    ix->dev.vec_lp = nullptr;
+    ix->dev.vec_meta = nullptr;
+    ix->dev.prec = 0;
+    if (prec == 0) return BBC_OK;
+    if (!ix->prec_totals) {
+        void* t = nullptr;
+        cudaError_t e = cudaMalloc(&t, 32);
+        if (e != cudaSuccess) return fail(BBC_ERR_OOM, "cudaMalloc(32): %s", cudaGetErrorString(e));
+        ix->prec_totals = static_cast<unsigned long long*>(t);
+        CUDA_TRY(cudaMemset(t, 0, 32));
+    }
+    const size_t es = prec == 1 ? 2 : 1;
+    const size_t rb = (size_t)ix->dev.n * ix->dev.dpad * es, mb = (size_t)ix->dev.n * sizeof(float4);
+    void* rows = nullptr;
+    void* meta = nullptr;
+    cudaError_t e = cudaMalloc(&rows, rb);
+    if (e != cudaSuccess) return fail(BBC_ERR_OOM, "cudaMalloc(%zu) for the low-precision copy: %s", rb, cudaGetErrorString(e));
+    e = cudaMalloc(&meta, mb);
+    if (e != cudaSuccess) {
+        cudaFree(rows);
+        return fail(BBC_ERR_OOM, "cudaMalloc(%zu) for the copy metadata: %s", mb, cudaGetErrorString(e));
+    }
+    ix->lp_rows = rows;
+    ix->lp_meta = static_cast<float4*>(meta);
+    CUDA_TRY(launch_prec_copy(ix->dev, prec, rows, ix->lp_meta, nullptr));
+    CUDA_TRY(cudaDeviceSynchronize());
+    ix->dev.vec_lp = rows;
+    ix->dev.vec_meta = ix->lp_meta;
+    ix->dev.prec = prec;
+    ix->info.device_bytes += (int64_t)(rb + mb);
     return BBC_OK;
 }
 
@@ -385,6 +507,7 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out) {
     D.cbp = (D.code_bytes + 15) / 16 * 16;
     D.W = lut_row_words(M);
     D.n = n;
+    D.dpad = (d + 15) / 16 * 16;
     {
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 1;
@@ -573,6 +696,10 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "probe_gemm") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "probe_gemm must be 0 (FP32 SIMT) or 1 (tensor cores)");
         ix->probe_gemm = (int)v;
+    } else if (k == "precision") {
+        if (v != 0 && v != 1 && v != 2)
+            return fail(BBC_ERR_ARG, "precision must be 0 (FP32 re-rank), 1 (BF16 copy) or 2 (FP8-E4M3 copy)");
+        return build_precision(ix, (int)v);
     } else if (k == "profile") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "profile must be 0 or 1");
         ix->profile = (int)v;
@@ -594,6 +721,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "probe_gemm") *v = ix->probe_gemm;
     else if (k == "split") *v = ix->split;
     else if (k == "graphs") *v = ix->graphs;
+    else if (k == "precision") *v = ix->dev.prec;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -621,7 +749,7 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     if (!ix->graphs || st == nullptr) return run_all();
     // CUDA graph of the whole launch sequence for this call shape
     bbc_index::GraphKey key{queries, nq, k, nprobe, out_ids, out_dists, st, ix->kc_ratio, ix->buckets,
-                            ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8};
+                            ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8, ix->dev.prec};
     std::lock_guard<std::mutex> lk(ix->graph_mu);
     auto it = ix->graph_cache.find(key);
     if (it == ix->graph_cache.end()) {
@@ -733,6 +861,7 @@ int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t
         qp.out_off = dtab + 6 * n8;
         p.nprobe = sh.max_probe;
         p.kc = sh.max_kc;
+        p.chunk_slots = sh.sum_kc;
         p.k = maxk;
         p.cap = maxcap;
         rc = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, out_ids + out_base, out_dists + out_base, st, 9,
@@ -960,28 +1089,85 @@ int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint3
                     void* stream) {
     if (!ix) return fail(BBC_ERR_ARG, "null index");
     if (nq < 0 || k < 1 || kc < 1) return fail(BBC_ERR_ARG, "bad sizes");
+    if (kc > (int64_t)0x7FFFFFFF) return fail(BBC_ERR_ARG, "kc too large");
     if (nq > 0 && (!queries || !cand_ids || !cand_count || !out_ids || !out_dists)) return fail(BBC_ERR_ARG, "null buffer");
     if (nq == 0) return BBC_OK;
     DeviceGuard g(ix->device);
     cudaStream_t st = (cudaStream_t)stream;
-    // scratch per query: kc distances (+ kc keys for the large top-k)
-    const size_t per = (size_t)kc * (kc > kTopkSmemMax ? 12 : 4);
+    const bool prec = prec_active(ix);
+    const bool large = kc > kTopkSmemMax || (prec && k > kTopkSmemMax);
+    // scratch per chunk: distances, keys of the large top-k, precision arrays
+    auto bytes = [&](int64_t c) {
+        size_t o = align_up((size_t)c * kc * 4);
+        o += align_up(large ? (size_t)c * kc * 8 : 0);
+        o += prec ? prec_bytes(c, c * kc) : 0;
+        return o + 256;
+    };
     const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
-    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(budget / (per + 256))));
+    int64_t chunk = nq;
+    while (chunk > 1 && bytes(chunk) > budget) chunk = (chunk + 1) / 2;
     char* ws;
-    int rc = get_workspace(ix, st, align_up((size_t)chunk * per) + 256, &ws);
+    int rc = get_workspace(ix, st, bytes(chunk), &ws);
     if (rc) return rc;
     const int d = ix->dev.d;
     for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
         const int64_t nc = std::min(chunk, nq - q0);
-        unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + align_up((size_t)chunk * kc * 4));
+        size_t o = align_up((size_t)chunk * kc * 4);
+        unsigned long long* keys = large ? reinterpret_cast<unsigned long long*>(ws + o) : nullptr;
+        o += align_up(large ? (size_t)chunk * kc * 8 : 0);
         RerankArgs ra{queries + q0 * d, cand_ids + q0 * kc, cand_count + q0, kc,
                       ix->rerank_u8 && ix->dev.vec_u8 != nullptr, reinterpret_cast<float*>(ws), k,
-                      out_ids + q0 * k, out_dists + q0 * k, kc > kTopkSmemMax ? keys : nullptr,
-                      uniform_params(1, kc, k, 0)};
-        CUDA_TRY(stage(ix, 5, st, [&] { return launch_rerank(ix->dev, nc, ra, st); }));
-        CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(ix->dev, nc, ra, st); }));
+                      out_ids + q0 * k, out_dists + q0 * k, keys, uniform_params(1, kc, k, 0)};
+        if (prec) {
+            const PrecArgs pa = prec_args(ix, ws + o, nc, nc * kc);
+            rc = run_rerank(ix, nc, ra, &pa, k, st);
+        } else {
+            rc = run_rerank(ix, nc, ra, nullptr, k, st);
+        }
+        if (rc) return rc;
     }
+    return BBC_OK;
+}
+
+int bbc_rerank_bounds(bbc_index* ix, const float* queries, int64_t nq, const uint32_t* cand_ids,
+                      const int64_t* cand_count, int64_t kc, float* out_dist, float* out_rho, void* stream) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    if (nq < 0 || kc < 1 || kc > (int64_t)0x7FFFFFFF) return fail(BBC_ERR_ARG, "bad sizes");
+    if (nq > 0 && (!queries || !cand_ids || !cand_count || !out_dist || !out_rho)) return fail(BBC_ERR_ARG, "null buffer");
+    if (ix->dev.prec == 0 || !ix->dev.vec_lp) return fail(BBC_ERR_ARG, "no low-precision copy (set \"precision\" first)");
+    if (nq == 0) return BBC_OK;
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    RerankArgs ra{queries, cand_ids, cand_count, kc, 0, out_dist, 1, nullptr, nullptr, nullptr,
+                  uniform_params(1, kc, 1, 0)};
+    PrecArgs pa{};
+    pa.rho = out_rho;
+    CUDA_TRY(stage(ix, 5, st, [&] { return launch_prec_score(ix->dev, nq, ra, pa, st); }));
+    return BBC_OK;
+}
+
+int bbc_precision_copy(bbc_index* ix, void* out_rows, float* out_meta, void* stream) {
+    if (!ix) return fail(BBC_ERR_ARG, "null index");
+    if (ix->dev.prec == 0 || !ix->dev.vec_lp) return fail(BBC_ERR_ARG, "no low-precision copy (set \"precision\" first)");
+    if (!out_rows || !out_meta) return fail(BBC_ERR_ARG, "null buffer");
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = ix->dev.prec == 1 ? 2 : 1;
+    CUDA_TRY(cudaMemcpyAsync(out_rows, ix->dev.vec_lp, (size_t)ix->dev.n * ix->dev.dpad * es, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(out_meta, ix->dev.vec_meta, (size_t)ix->dev.n * sizeof(float4), cudaMemcpyDeviceToDevice, st));
+    return BBC_OK;
+}
+
+int bbc_precision_stats(bbc_index* ix, int64_t* out4, int reset) {
+    if (!ix || !out4) return fail(BBC_ERR_ARG, "null argument");
+    for (int i = 0; i < 4; ++i) out4[i] = 0;
+    if (!ix->prec_totals) return BBC_OK;
+    DeviceGuard g(ix->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    unsigned long long t[4];
+    CUDA_TRY(cudaMemcpy(t, ix->prec_totals, sizeof(t), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i) out4[i] = (int64_t)t[i];
+    if (reset) CUDA_TRY(cudaMemset(ix->prec_totals, 0, sizeof(t)));
     return BBC_OK;
 }
 
@@ -1016,7 +1202,7 @@ int bbc_stream_status(bbc_index* ix, void* stream) {
     if (s) {
         unsigned int z = 0;
         CUDA_TRY(cudaMemcpy(ix->dev.status, &z, 4, cudaMemcpyHostToDevice));
-        return fail(BBC_ERR_CAPACITY, "device status 0x%x (1 region, 2 select, 4 top-k overrun)", s);
+        return fail(BBC_ERR_CAPACITY, "device status 0x%x (1 region, 2 select, 4 top-k overrun, 16 precision bound)", s);
     }
     return BBC_OK;
 }

@@ -17,6 +17,12 @@
 //   vectors    f32 [n][d]              by id, for the exact re-rank
 //   vec_u8     u8  [n][d]              exact copy when all components are
 //                                      integers in [0,255] (else null)
+//   vec_lp     bf16 or e4m3 [n][dpad]  low-precision copy for the precision
+//                                      re-rank (null until requested); rows
+//                                      zero-padded to dpad = d rounded up to 16
+//   vec_meta   f32x4 [n]               {FP8 scale s (1 for BF16), e_v =
+//                                      ||v - v~||_2 rounded up, ||v||_2 rounded
+//                                      up, 0} per vector
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,6 +41,7 @@ constexpr unsigned kStatusRegionOverrun = 1u;
 constexpr unsigned kStatusSelectOverrun = 2u;
 constexpr unsigned kStatusTopkOverrun = 4u;
 constexpr unsigned kStatusTimeout = 8u;
+constexpr unsigned kStatusPrecBound = 16u;   // a precision re-rank bound failed its self-check
 
 struct DevIndex {
     int d, nlist, metric, M, bits, K, dsub;
@@ -56,6 +63,10 @@ struct DevIndex {
     const uint16_t* cent_b3;   // BF16 [nlist][kp]: [c_hi | c_lo | c_hi | 0-pad] for the tensor-core probe
     int kp;                    // 3d rounded up to a multiple of 64
     int num_sms;               // streaming multiprocessors of the device
+    const void* vec_lp;        // low-precision copy (see above) or null
+    const float4* vec_meta;    // per-vector scale / error / norm, or null
+    int prec;                  // 0 none, 1 BF16 copy, 2 FP8-E4M3 copy
+    int dpad;                  // row length of the low-precision copy
 };
 
 // Words per LUT row in shared memory: lane t at code slot s reads word t + s
@@ -166,6 +177,41 @@ struct RerankArgs {
 // S8: exact distances of the candidates; S9: k smallest (dist, id), sorted.
 cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
 cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
+
+// S8, precision form: scores from the low-precision copy with a bound rho per
+// candidate, classification against the k-th place, FP32 recheck of the
+// uncertain candidates, FP64 for those the FP32 bound cannot place.  All
+// arrays are per QueryParams::coff unless noted.
+struct PrecArgs {
+    float* rho;                   // bound of each score in RerankArgs::cdist
+    uint32_t* unc;                // uncertain candidates (ids), compacted
+    uint32_t* fin_id;             // final members, compacted
+    float* fin_d;                 // their reported distances
+    uint32_t* band_id;            // members left to FP64
+    double* band_d;               // their FP64 distances
+    int64_t* n_fin;               // [nq] final members so far
+    int64_t* n_unc;               // [nq] uncertain candidates
+    int64_t* item_off;            // [nq + 1] recheck work items (prefix)
+    float* qnorm;                 // [nq] ||q||_2 rounded up (may be null for pass 1 alone)
+    unsigned long long* totals;   // [4] running totals: candidates, uncertain after the
+                                  // low-precision pass, FP64-scored, final members
+};
+constexpr int kPrecItem = 512;    // candidates per recheck work item
+// Builds the copy (prec 1 BF16, 2 FP8-E4M3) and the per-vector metadata.
+cudaError_t launch_prec_copy(const DevIndex& ix, int prec, void* rows, float4* meta, cudaStream_t st);
+// Scores and bounds of the candidates (pass 1), written to a.cdist and p.rho.
+cudaError_t launch_prec_score(const DevIndex& ix, int64_t nq, const RerankArgs& a, const PrecArgs& p,
+                              cudaStream_t st);
+// Classification (pass 2), the recheck plan and the FP32 recheck (pass 3),
+// the FP32 classification with the FP64 decision (pass 4).  Afterwards
+// p.fin_id / p.fin_d / p.n_fin hold the min(k, count) final members.
+cudaError_t launch_prec_classify(const DevIndex& ix, int64_t nq, const RerankArgs& a, const PrecArgs& p,
+                                 cudaStream_t st);
+cudaError_t launch_prec_plan(int64_t nq, const PrecArgs& p, cudaStream_t st);
+cudaError_t launch_prec_recheck(const DevIndex& ix, int64_t nq, const RerankArgs& a, const PrecArgs& p,
+                                cudaStream_t st);
+cudaError_t launch_prec_finalize(const DevIndex& ix, int64_t nq, const RerankArgs& a, const PrecArgs& p,
+                                 cudaStream_t st);
 
 }  // namespace bbc
 

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     __syncthreads();
     const bool intpath = sizeof(T) == 1 && s_int;
     const int qn2 = s_qn2;
-    const int64_t cnt = a.cand_count[qi];
+    const int64_t cnt = min(a.cand_count[qi], a.qp.KC(qi));
     const int nchunk = d * (int)sizeof(T) / 16;        // d * sizeof(T) is a multiple of 16
     int G = 1;                                         // lanes per candidate: a power of two <= 32
     while (G * 2 <= nchunk && G < 32) G *= 2;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArg
     __shared__ uint32_t wsum[TK_THREADS / 32];
     __shared__ uint32_t s_min, s_max, s_big;
     const int64_t qi = blockIdx.x;
-    const int64_t cnt = a.cand_count[qi];
+    const int64_t cnt = min(a.cand_count[qi], a.qp.KC(qi));
     const int n = (int)(cnt < TK_MAX ? cnt : TK_MAX);
     const int tid = threadIdx.x;
     const int kq = a.qp.K(qi);
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(TK_THREADS) topk_large_kernel(DevIndex ix, Rer
     __shared__ uint32_t wsum[TK_THREADS / 32];
     __shared__ uint32_t s_min, s_max, s_big, s_last;
     const int64_t qi = blockIdx.x;
-    const int64_t n = a.cand_count[qi];
+    const int64_t n = min(a.cand_count[qi], a.qp.KC(qi));
     const int tid = threadIdx.x;
     const int kq = a.qp.K(qi);
     const uint32_t* cand = a.cand + a.qp.coff(qi);
