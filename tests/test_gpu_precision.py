@@ -162,7 +162,8 @@ def test_bound_invariant(bbc, oracle_lib, kind, prec):
         # not vacuous: the bound is well below the spread of the candidates' distances
         spread = d64.max() - d64.min()
         assert np.median(rho[i, :n]) < 0.25 * spread
-    assert worst > 0.0
+    # integers in [0, 255] are exact in BF16: then the copy's scores are exact too
+    assert worst == 0.0 if (kind, prec) == ("sift", 1) else worst > 0.0
 
 
 @pytest.mark.parametrize("kind,prec", KINDS + [("sift", 1), ("sift", 2)])
