@@ -32,6 +32,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ)"
+METRICS = {"sift": METRIC, "sift4": "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ 64x4)",
+           "embed": "QPS at recall@k>=0.95 (k=50k, 10Mx768 IVF-PQ, inner product)",
+           "tiny": "QPS at recall@k>=0.95 (k=1k, 100kx128 IVF-PQ)"}
 UNIT = "queries/s"
 SMS = 152
 LOOKUPS_PER_SM_CLK = 32          # one 4-byte shared-memory word per lane per clock
@@ -58,6 +61,11 @@ def parse():
                    help="batch: the headline batched search; serve: continuous-batching server")
     p.add_argument("--requests", type=int, default=100_000, help="serve mode: requests per rate")
     p.add_argument("--rates", default="20000,50000,100000", help="serve mode: Poisson arrival rates (req/s)")
+    p.add_argument("--precision", default=None,
+                   help="re-rank precision: 0 FP32 rows (or the exact u8 copy), 1 BF16 prefilter, 2 FP8-E4M3 "
+                        "prefilter; a comma list prints one line per value (default: 0, or 2 for float data)")
+    p.add_argument("--recall-queries", type=int, default=None,
+                   help="queries whose recall is measured against exact kNN (default: all, at most 1,000)")
     return p.parse_args()
 
 
@@ -163,31 +171,40 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # recall
 # ---------------------------------------------------------------------------
-def exact_kth(x_t, q_t, k, chunk=500):
-    """k-th smallest exact squared L2 distance per query (torch on the GPU).
+def _dist_block(x_t, xn, qs, metric):
+    if metric == "ip":
+        return -(qs @ x_t.T)
+    return xn[None, :] + (qs * qs).sum(1)[:, None] - 2.0 * (qs @ x_t.T)
+
+
+def exact_kth(x_t, q_t, k, metric="l2"):
+    """k-th smallest exact distance per query (torch on the GPU, FP32).
 
     For integer components in [0, 255] and d = 128 every partial sum of the
     FP32 evaluation is an integer below 2^24, so these distances are exact."""
     import torch
     xn = (x_t * x_t).sum(1)
+    chunk = max(1, min(500, int(4e9 // (4 * x_t.shape[0]))))
     out = []
     for s in range(0, q_t.shape[0], chunk):
-        qs = q_t[s:s + chunk]
-        dd = xn[None, :] + (qs * qs).sum(1)[:, None] - 2.0 * (qs @ x_t.T)
-        out.append(torch.kthvalue(dd, k, dim=1).values)
+        out.append(torch.kthvalue(_dist_block(x_t, xn, q_t[s:s + chunk], metric), k, dim=1).values)
     return torch.cat(out)
 
 
-def recall_at_k(x_t, q_t, ids, k):
+def recall_at_k(x_t, q_t, ids, k, metric="l2"):
+    """Mean and minimum recall@k, tie-aware: a returned id counts when its exact
+    distance is <= the k-th exact distance."""
     import torch
-    dk = exact_kth(x_t, q_t, k)
+    dk = exact_kth(x_t, q_t, k, metric)
+    chunk = max(1, min(500, int(2e9 // (4 * k * x_t.shape[1]))))
     rec = []
-    for s in range(0, q_t.shape[0], 500):
-        i = ids[s:s + 500]
+    for s in range(0, q_t.shape[0], chunk):
+        i = ids[s:s + chunk]
         valid = i >= 0
         v = x_t[i.clamp(min=0)]
-        d = ((v - q_t[s:s + 500, None, :]) ** 2).sum(-1)
-        ok = (d <= dk[s:s + 500, None]) & valid
+        qs = q_t[s:s + chunk, None, :]
+        d = -(v * qs).sum(-1) if metric == "ip" else ((v - qs) ** 2).sum(-1)
+        ok = (d <= dk[s:s + chunk, None]) & valid
         rec.append(torch.clamp(ok.sum(1), max=k).double() / k)
     r = torch.cat(rec)
     return float(r.mean()), float(r.min()), dk
@@ -317,10 +334,24 @@ def main():
     dev = torch.device("cuda", local)
     bbc.build()
     w, idx, q, k, nprobe, t_build = make_inputs(args, f"cuda:{local}")
-    kc = max(k, int(math.ceil(args.kc_ratio * k - 1e-9)))
-    nq = len(q)
+    torch.cuda.empty_cache()
     index = bbc.Index(idx, device=local)
     index.set(kc_ratio=args.kc_ratio, buckets=args.buckets, workspace_mb=64 * 1024)
+    float_data = not index.info["vectors_u8_exact"]
+    precs = [int(v) for v in args.precision.split(",")] if args.precision else [2 if float_data else 0]
+    xt = torch.from_numpy(idx.vectors).to(dev)
+    for prec in precs:
+        measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt, prec)
+    index.close()
+
+
+def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt, prec):
+    """Time one configuration and print its JSON line (rank 0)."""
+    import torch
+    dev = torch.device("cuda", local)
+    index.set(precision=prec)
+    kc = max(k, int(math.ceil(args.kc_ratio * k - 1e-9)))
+    nq = len(q)
     h = index.handle
     qd = torch.from_numpy(q).to(dev)
     ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
@@ -331,17 +362,28 @@ def main():
         bbc.bbc_search(h, qd, nq, k, nprobe, ids, dists, stream)
 
     # correctness of the operating point: recall against exact kNN
+    bbc.bbc_precision_stats(h, reset=True)
     step()
     torch.cuda.synchronize()
     bbc.bbc_stream_status(h)
-    xt = torch.from_numpy(idx.vectors).to(dev)
-    rec_mean, rec_min, dk = recall_at_k(xt, qd, ids, k)
-    gt_check = None
+    pstats = bbc.bbc_precision_stats(h, reset=True) if prec else None
+    nrec = min(nq, args.recall_queries or 1000)
+    rec_mean, rec_min, dk = recall_at_k(xt, qd[:nrec], ids[:nrec], k, idx.metric)
+    gt_check, err = None, None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        bi, bd = oracle.bruteforce(q[:2], idx.vectors, k, idx.metric)
-        gt_check = bool(np.allclose(bd[:, -1], dk[:2].double().cpu().numpy(), rtol=0, atol=0))
+        if idx.n * idx.d <= (1 << 28):
+            bi, bd = oracle.bruteforce(q[:2], idx.vectors, k, idx.metric)
+            gt_check = bool(np.allclose(bd[:, -1], dk[:2].double().cpu().numpy(), rtol=0, atol=0))
+        # reported distances against FP64 on a few queries
+        gi, gd = ids[:4].cpu().numpy(), dists[:4].cpu().numpy().astype(np.float64)
+        rel = []
+        for i in range(len(gi)):
+            v = gi[i] >= 0
+            d64 = oracle.rerank(q[i], idx.vectors, gi[i][v], idx.metric)
+            rel.append(float(np.max(np.abs(gd[i][v] - d64) / np.maximum(np.abs(d64), 1e-30))))
+        err = {"max_rel_err_vs_fp64": max(rel), "queries": len(gi)}
     # collector statistics for the algorithmic work per launch (outside the timed region)
     lists = torch.empty((nq, nprobe), dtype=torch.int32, device=dev)
     bbc.bbc_probe(h, qd, nq, nprobe, lists)
@@ -397,20 +439,30 @@ def main():
     e2e = {"value": ws * nq * args.e2e_steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": int(q.nbytes), "d2h_bytes_per_step": int(nq * k * (8 + 4))}
     assert torch.equal(hi, ids.cpu()), "host entry point disagrees with the device entry point"
+    del hi, hd, hq
 
     # roofline of the dominant stage
     per = {s: stage_ms[s] / args.steps for s in stage_ms}
     peaks = _peaks()
     sm_clk = 2070.0
     lookups = float(s_q.double().sum()) * idx.pq_m
+    dpad = (idx.d + 15) // 16 * 16
+    u8 = bool(index.get("rerank"))
+    if prec:
+        rr_bytes = nq * kc * (dpad * (2 if prec == 1 else 1) + 16 + 4 + 8)
+    else:
+        rr_bytes = nq * kc * (idx.d * (1 if u8 else 4) + 4 + 4)
+    unc = (pstats["fp32_rechecked"] if pstats else 0) * args.steps / max(1, args.steps)
     work = {
         "scan": ("alu", lookups / 1e9, "Glookup/s", SMS * LOOKUPS_PER_SM_CLK * sm_clk * 1e6 / 1e9),
-        "rerank": ("hbm", nq * kc * idx.d * (1 if index.get("rerank") else 4) / 1e9, "GB/s", peaks["hbm_gbs"]),
-        "topk": ("hbm", nq * (kc * 12 + k * 12) / 1e9, "GB/s", peaks["hbm_gbs"]),
+        "rerank": ("hbm", rr_bytes / 1e9, "GB/s", peaks["hbm_gbs"]),
+        "topk": ("hbm", nq * ((k if prec else kc) * 8 + k * 12) / 1e9, "GB/s", peaks["hbm_gbs"]),
         "select": ("hbm", nq * kc * 8 * 2 / 1e9, "GB/s", peaks["hbm_gbs"]),
         "probe_scores": ("tensor", 2.0 * nq * idx.nlist * idx.d / 1e12, "TFLOP/s", peaks["bf16_tflops"]),
         "probe_select": ("hbm", nq * idx.nlist * 4 / 1e9, "GB/s", peaks["hbm_gbs"]),
         "lut": ("hbm", nq * idx.pq_m * (1 << idx.pq_bits) * 2 / 1e9, "GB/s", peaks["hbm_gbs"]),
+        "prec_classify": ("hbm", nq * kc * 8 * 5 / 1e9, "GB/s", peaks["hbm_gbs"]),
+        "prec_recheck": ("hbm", unc * (idx.d * 4 + 16) / 1e9, "GB/s", peaks["hbm_gbs"]),
     }
     dom = max(per, key=lambda s: per[s])
     bound, amount, unit, peak = work[dom]
@@ -431,17 +483,21 @@ def main():
                "sample": f"first {nsamp} of the {nq} queries on the full index, single-threaded C"}
 
     if rank == 0:
+        rerank = ["u8-exact" if u8 else "f32", "bf16-prefilter", "fp8e4m3-prefilter"][prec]
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u16/u32 ADC, f32 re-rank", "data": "synthetic",
-            "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist,
+            "metric": METRICS.get(args.workload, METRIC), "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16/u32 ADC, " + {0: "f32 re-rank", 1: "bf16+f32 re-rank (f64 at ties)",
+                                        2: "e4m3+f32 re-rank (f64 at ties)"}[prec],
+            "data": "synthetic",
+            "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "metric_space": idx.metric,
                        "pq": f"{idx.pq_m}x{idx.pq_bits}", "nq": nq, "k": k, "nprobe": nprobe, "kc": kc,
-                       "buckets": args.buckets, "rerank": "u8-exact" if index.get("rerank") else "f32",
-                       "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_tie_aware": True,
-                       "ground_truth_cpu_spotcheck": gt_check, "l2_flush_between_steps": True,
-                       "parallelism": f"replicas x{ws}", "S_q_mean": stats["S_q_mean"],
-                       "index_build_s": round(t_build, 1), "wall_s_timed": wall},
+                       "buckets": args.buckets, "rerank": rerank,
+                       "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
+                       "recall_tie_aware": True, "ground_truth_cpu_spotcheck": gt_check,
+                       "l2_flush_between_steps": True, "parallelism": f"replicas x{ws}",
+                       "S_q_mean": stats["S_q_mean"], "index_build_s": round(t_build, 1), "wall_s_timed": wall},
             "stage_ms_per_step": per,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -449,10 +505,16 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
+        if prec:
+            out["precision"] = {"per_step": pstats, "fp32_recheck_frac": pstats["fp32_rechecked"] / max(1, pstats["scored"]),
+                                "fp64_frac": pstats["fp64_scored"] / max(1, pstats["scored"])}
+        if err:
+            out["error_vs_fp64"] = err
         if rec_mean < 0.95:
             out["warning"] = "recall below 0.95 at this operating point"
         print(json.dumps(out), flush=True)
-    index.close()
+    del ids, dists, flush, qd
+    torch.cuda.empty_cache()
 
 
 def _peaks():

@@ -156,6 +156,73 @@ def _inverted_lists(assign: np.ndarray, nlist: int):
     return order.astype(np.int64), offsets
 
 
+def _nearest_dev(x, c, chunk: int):
+    """Nearest row of c for each row of x, both torch tensors on one device."""
+    import torch
+    cn = (c * c).sum(1)
+    out = torch.empty(x.shape[0], dtype=torch.int64, device=x.device)
+    for s in range(0, x.shape[0], chunk):
+        out[s:s + chunk] = torch.argmin(cn[None, :] - 2.0 * (x[s:s + chunk] @ c.T), dim=1)
+    return out
+
+
+def _kmeans_dev(train, k: int, iters: int, rng, chunk: int):
+    """Lloyd's k-means on the device; same seeded initialisation as ``kmeans``."""
+    import torch
+    nt, d = train.shape
+    if nt < k:
+        raise ValueError(f"k-means needs at least k={k} points, got {nt}")
+    pick = torch.from_numpy(rng.choice(nt, size=k, replace=False)).to(train.device)
+    cent = train[pick].clone()
+    for _ in range(iters):
+        assign = _nearest_dev(train, cent, chunk)
+        counts = torch.bincount(assign, minlength=k)
+        sums = torch.zeros((k, d), dtype=torch.float64, device=train.device)
+        for s in range(0, nt, 1 << 20):
+            sums.index_add_(0, assign[s:s + (1 << 20)], train[s:s + (1 << 20)].double())
+        nz = counts > 0
+        cent[nz] = (sums[nz] / counts[nz, None]).float()
+        empty = torch.nonzero(~nz).flatten()
+        if empty.numel():
+            repl = torch.from_numpy(rng.choice(nt, size=int(empty.numel()), replace=False)).to(train.device)
+            cent[empty] = train[repl]
+    return cent
+
+
+def _build_ivf_pq_dev(x, nlist, pq_m, pq_bits, metric, kmeans_iters, pq_iters, kmeans_sample, pq_sample):
+    """The same construction as ``build_ivf_pq`` with torch on the build device
+    (for large inputs); results are deterministic for a given machine."""
+    import torch
+    n, d = x.shape
+    dev = torch.device(_DEVICE)
+    xt = torch.from_numpy(x).to(dev)
+    rng = np.random.default_rng(SEED_KMEANS)
+    if kmeans_sample < n:
+        sel = torch.from_numpy(np.sort(rng.choice(n, size=kmeans_sample, replace=False))).to(dev)
+        train = xt[sel]
+    else:
+        train = xt
+    cent = _kmeans_dev(train, nlist, kmeans_iters, rng, 1 << 15)
+    del train
+    assign = _nearest_dev(xt, cent, 1 << 15).cpu().numpy()
+    ids, offsets = _inverted_lists(assign, nlist)
+    dsub, ksub = d // pq_m, 1 << pq_bits
+    rng = np.random.default_rng(SEED_PQ)
+    samp = xt[torch.from_numpy(np.sort(rng.choice(n, size=min(n, pq_sample), replace=False))).to(dev)]
+    books = np.empty((pq_m, ksub, dsub), dtype=np.float32)
+    codes_full = torch.empty((n, pq_m), dtype=torch.uint8, device=dev)
+    for m in range(pq_m):
+        sub = samp[:, m * dsub:(m + 1) * dsub].contiguous()
+        bk = _kmeans_dev(sub, ksub, pq_iters, np.random.default_rng(SEED_PQ + 17 * m), 1 << 20)
+        books[m] = bk.cpu().numpy()
+        codes_full[:, m] = _nearest_dev(xt[:, m * dsub:(m + 1) * dsub], bk, 1 << 20).to(torch.uint8)
+    codes_full = codes_full[torch.from_numpy(ids).to(dev)].cpu().numpy()
+    del xt, samp
+    codes = codes_full if pq_bits == 8 else _pack4(codes_full)
+    return IvfPqIndex(metric, d, nlist, pq_m, pq_bits, cent.cpu().numpy(), offsets, ids,
+                      np.ascontiguousarray(codes), books, x)
+
+
 def build_ivf_pq(x: np.ndarray, nlist: int, pq_m: int, pq_bits: int, metric: str = "l2",
                  kmeans_iters: int = 12, pq_iters: int = 12, kmeans_sample: int | None = None,
                  pq_sample: int = 65536) -> IvfPqIndex:
@@ -170,6 +237,9 @@ def build_ivf_pq(x: np.ndarray, nlist: int, pq_m: int, pq_bits: int, metric: str
         raise ValueError("4-bit PQ needs an even pq_m")
     if kmeans_sample is None:
         kmeans_sample = min(n, 256 * nlist)
+    if _DEVICE != "cpu" and n * d >= (1 << 28):
+        return _build_ivf_pq_dev(x, nlist, pq_m, pq_bits, metric, kmeans_iters, pq_iters, kmeans_sample,
+                                 pq_sample)
     cent = kmeans(x, nlist, iters=kmeans_iters, seed=SEED_KMEANS, sample=kmeans_sample)
     assign = nearest(x, cent)
     ids, offsets = _inverted_lists(assign, nlist)

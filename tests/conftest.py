@@ -49,6 +49,9 @@ def small_workload(kind: str):
     elif kind == "pad":       # d = 40: rows of the low-precision copies are zero padded to 48
         x, q = gaussian_mixture_tiny(6000, 16, d=40, n_centers=100, sigma=0.3)
         idx = build_ivf_pq(x, 32, 8, 8, "l2", kmeans_iters=6, pq_iters=6, pq_sample=6000)
+    elif kind == "wide":      # d = 768 unit norm, inner product, PQ 96 x 8 bit
+        x, q = embedding_shaped(8000, 12, d=768)
+        idx = build_ivf_pq(x, 24, 96, 8, "ip", kmeans_iters=5, pq_iters=5, pq_sample=8000)
     elif kind == "ragged":    # few vectors, many short and empty lists
         x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
         idx = build_ivf_pq(x, 40, 8, 8, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700)

@@ -48,7 +48,7 @@ def sync_ok(bbc, h):
     bbc.bbc_stream_status(h)
 
 
-KINDS = ["tiny", "sift", "sift4", "embed", "ragged"]
+KINDS = ["tiny", "sift", "sift4", "embed", "ragged", "wide"]
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -76,7 +76,7 @@ def _probe_eps(d, qn, cm, metric, tc):
 
 
 @pytest.mark.parametrize("tc", [1, 0])
-@pytest.mark.parametrize("kind", ["tiny", "sift", "embed", "ragged"])
+@pytest.mark.parametrize("kind", ["tiny", "sift", "embed", "ragged", "wide"])
 def test_probe_scores_within_bound(bbc, kind, tc):
     """Approximate scores (tensor-core BF16 split GEMM, or FP32) lie within the
     stated bound of the FP64 score minus ||q||^2."""
@@ -104,7 +104,7 @@ def test_probe_scores_within_bound(bbc, kind, tc):
 
 @pytest.mark.parametrize("tc", [1, 0])
 @pytest.mark.parametrize("kind,nprobe", [("tiny", 1), ("tiny", 13), ("sift", 32), ("embed", 48),
-                                         ("ragged", 40), ("sift4", 64)])
+                                         ("ragged", 40), ("sift4", 64), ("wide", 5)])
 def test_probe_exact_order(bbc, oracle_lib, kind, nprobe, tc):
     h, idx, q = dev_index(bbc, kind)
     nq = len(q)
@@ -203,7 +203,7 @@ def _check_topk(oracle_lib, idx, qv, gi, gd, oi, od, exact):
 @pytest.mark.parametrize("kind,k,nprobe,ratio", [("tiny", 100, 12, 2.0), ("sift", 500, 16, 1.5),
                                                  ("sift4", 300, 24, 2.0), ("embed", 200, 10, 1.5),
                                                  ("ragged", 50, 40, 1.0), ("tiny", 1, 3, 1.0),
-                                                 ("sift", 4000, 64, 1.0)])
+                                                 ("sift", 4000, 64, 1.0), ("wide", 300, 6, 2.0)])
 def test_search_end_to_end(bbc, oracle_lib, kind, k, nprobe, ratio, split):
     h, idx, q = dev_index(bbc, kind)
     bbc.bbc_set_param(h, "kc_ratio", ratio)

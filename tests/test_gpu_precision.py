@@ -122,7 +122,7 @@ def check_result(oracle_lib, bbc, h, idx, q, gi, gd, oi, kc):
         assert np.all(err <= lim), (i, float((err / lim).max()))
 
 
-KINDS = [("tiny", 1), ("tiny", 2), ("embed", 1), ("embed", 2), ("pad", 1), ("pad", 2)]
+KINDS = [("tiny", 1), ("tiny", 2), ("embed", 1), ("embed", 2), ("pad", 1), ("pad", 2), ("wide", 1), ("wide", 2)]
 
 
 @pytest.mark.parametrize("kind,prec", KINDS + [("sift", 2)])
@@ -195,7 +195,8 @@ def test_rerank_topk_equals_oracle(bbc, oracle_lib, kind, prec, k, kc):
 @pytest.mark.parametrize("kind,prec,k,nprobe,ratio", [
     ("tiny", 1, 100, 12, 2.0), ("tiny", 2, 300, 24, 3.0), ("embed", 1, 200, 10, 1.5),
     ("embed", 2, 200, 10, 4.0), ("pad", 2, 150, 8, 2.0), ("pad", 1, 1, 3, 1.0),
-    ("sift", 1, 500, 16, 1.5), ("sift", 2, 2000, 32, 1.2), ("ragged", 2, 50, 40, 1.0)])
+    ("sift", 1, 500, 16, 1.5), ("sift", 2, 2000, 32, 1.2), ("ragged", 2, 50, 40, 1.0),
+    ("wide", 1, 400, 6, 3.0), ("wide", 2, 400, 6, 3.0)])
 def test_search_end_to_end(bbc, oracle_lib, kind, prec, k, nprobe, ratio):
     h, idx, q = dev_index(bbc, kind)
     kc = max(k, int(np.ceil(ratio * k - 1e-9)))
