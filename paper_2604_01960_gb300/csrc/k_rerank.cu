@@ -205,9 +205,10 @@ cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, c
 
 // ---------------------------------------------------------------------------
 // S9 top-k.  Keys: order-preserving distance bits << 32 | id (unique).
-// 1. min / max of the distance bits over the candidates;
-// 2. histogram over TK_BINS fine bins, bin = floor((bits - min) * TK_BINS /
-//    (max - min + 1)) -- a monotone function of the distance;
+// 1. min / max of the distances over the candidates;
+// 2. histogram over TK_BINS fine bins in value space, bin =
+//    floor((dist - min) * TK_BINS / (max - min)) evaluated in FP32 -- a
+//    monotone function of the distance (rounding is monotone);
 // 3. exclusive scan -> bin starts; scatter keys into shared memory by bin;
 // 4. every key's final position = its bin's start + the number of keys of its
 //    bin that are smaller; positions < k are written straight to the output.
@@ -217,10 +218,39 @@ constexpr int TK_THREADS = 1024;
 constexpr int TK_MAX = 16384;    // candidates handled in shared memory per query
 constexpr int TK_BINS = 4096;
 constexpr int TK_BIG = 2048;
+constexpr int TK_HEAVY = 8192;   // a heavy bin of the large top-k sorted in shared memory
 
-__device__ __forceinline__ uint32_t tk_bin(uint32_t key, uint32_t kmin, float scale) {
-    uint32_t b = (uint32_t)(__uint2float_rz(key - kmin) * scale);
-    return b < (uint32_t)TK_BINS ? b : (uint32_t)(TK_BINS - 1);
+__device__ __forceinline__ float tk_scale(float vmin, float vmax) {
+    const float range = __fsub_rn(vmax, vmin);
+    return range > 0.f ? fminf((float)TK_BINS / range, 3.0e38f) : 0.f;
+}
+__device__ __forceinline__ uint32_t tk_vbin(float v, float vmin, float scale) {
+    const float t = fminf(__fmul_rn(__fsub_rn(v, vmin), scale), (float)(TK_BINS - 1));
+    return t > 0.f ? (uint32_t)t : 0u;
+}
+
+// Exclusive scan of bins[TK_BINS] in place (TK_THREADS threads); returns, per
+// thread, the counts of its PER consecutive bins in loc.
+template <int PER>
+__device__ __forceinline__ void tk_scan(uint32_t* bins, uint32_t* wsum, uint32_t (&loc)[PER]) {
+    const int tid = threadIdx.x;
+    uint32_t tot = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) { loc[j] = bins[tid * PER + j]; tot += loc[j]; }
+    const uint32_t winc = warp_incl_scan(tot);
+    if (lane_id() == 31) wsum[warp_id()] = winc;
+    __syncthreads();
+    if (warp_id() == 0) {
+        const uint32_t v = wsum[lane_id()];
+        wsum[lane_id()] = warp_incl_scan(v) - v;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp_id()] + winc - tot;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        bins[tid * PER + j] = run;
+        run += loc[j];
+    }
 }
 
 __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArgs a) {
@@ -253,31 +283,16 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArg
     mx = __reduce_max_sync(0xFFFFFFFFu, mx);
     if (lane_id() == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
     __syncthreads();
-    const uint32_t kmin = s_min;
-    const float scale = (float)TK_BINS / ((float)(s_max - kmin) + 1.0f);
-    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&bins[tk_bin(f32_key(cd[i]), kmin, scale)], 1u);
+    const float vmin = key_f32(s_min);
+    const float scale = tk_scale(vmin, key_f32(s_max));
+    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&bins[tk_vbin(cd[i], vmin, scale)], 1u);
     __syncthreads();
-    // exclusive scan of the bins: 4 consecutive bins per thread
     constexpr int PER = TK_BINS / TK_THREADS;
-    uint32_t loc[PER], tot = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) { loc[j] = bins[tid * PER + j]; tot += loc[j]; }
-    const uint32_t winc = warp_incl_scan(tot);
-    if (lane_id() == 31) wsum[warp_id()] = winc;
-    __syncthreads();
-    if (warp_id() == 0) {
-        const uint32_t v = wsum[lane_id()];
-        wsum[lane_id()] = warp_incl_scan(v) - v;
-    }
-    __syncthreads();
-    uint32_t run = wsum[warp_id()] + winc - tot;
+    uint32_t loc[PER];
+    tk_scan<PER>(bins, wsum, loc);
     uint32_t big = 0;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        bins[tid * PER + j] = run;        // start of bin; becomes its end after the scatter
-        run += loc[j];
-        big |= loc[j] > (uint32_t)TK_BIG ? 1u : 0u;
-    }
+    for (int j = 0; j < PER; ++j) big |= loc[j] > (uint32_t)TK_BIG ? 1u : 0u;
     if (big) s_big = 1u;
     __syncthreads();
     if (s_big) {
@@ -294,14 +309,13 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArg
         return;
     }
     for (int i = tid; i < n; i += blockDim.x) {
-        const uint32_t kk = f32_key(cd[i]);
-        const uint32_t p = atomicAdd(&bins[tk_bin(kk, kmin, scale)], 1u);
-        keys[p] = ((unsigned long long)kk << 32) | cand[i];
+        const uint32_t p = atomicAdd(&bins[tk_vbin(cd[i], vmin, scale)], 1u);
+        keys[p] = ((unsigned long long)f32_key(cd[i]) << 32) | cand[i];
     }
     __syncthreads();
     for (int p = tid; p < n; p += blockDim.x) {
         const unsigned long long me = keys[p];
-        const uint32_t b = tk_bin((uint32_t)(me >> 32), kmin, scale);
+        const uint32_t b = tk_vbin(key_f32((uint32_t)(me >> 32)), vmin, scale);
         const int st = b ? (int)bins[b - 1] : 0;
         const int en = (int)bins[b];
         int rank = 0;
@@ -314,13 +328,18 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArg
     }
 }
 
-// Same algorithm for K_c above TK_MAX: the keys stay in a global scratch
-// area (RerankArgs::keys, per QueryParams::coff) instead of shared memory.
-// Only bins up to the one holding rank k are scattered and ranked.
+// Same output for K_c above TK_MAX.  The distance of rank k is found first
+// (radix select); only keys at or below it are binned (value space between
+// the minimum and that distance) and scattered into a global scratch area
+// (RerankArgs::keys, per QueryParams::coff).  Bins of at most TK_BIG keys are
+// ranked in place; heavier bins (many equal distances) are sorted one at a
+// time in shared memory when they fit TK_HEAVY keys, else ranked in place.
 __global__ void __launch_bounds__(TK_THREADS) topk_large_kernel(DevIndex ix, RerankArgs a) {
+    extern __shared__ unsigned long long hsm[];       // [TK_HEAVY]
     __shared__ uint32_t bins[TK_BINS];
     __shared__ uint32_t wsum[TK_THREADS / 32];
-    __shared__ uint32_t s_min, s_max, s_big, s_last;
+    __shared__ uint32_t hist[256], sc[2];
+    __shared__ uint32_t s_min;
     const int64_t qi = blockIdx.x;
     const int64_t n = min(a.cand_count[qi], a.qp.KC(qi));
     const int tid = threadIdx.x;
@@ -332,74 +351,64 @@ __global__ void __launch_bounds__(TK_THREADS) topk_large_kernel(DevIndex ix, Rer
     float* od = a.out_dists + a.qp.ooff(qi);
     for (int64_t i = n + tid; i < kq; i += blockDim.x) { oid[i] = -1; od[i] = INFINITY; }
     if (n == 0) return;
-    if (tid == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_big = 0u; s_last = TK_BINS - 1; }
+    const int64_t kk = (int64_t)kq < n ? (int64_t)kq : n;
+    // distance key of rank kk - 1
+    const uint32_t dk = cta_select_u32(n, (uint32_t)(kk - 1), [&](int64_t i) { return f32_key(cd[i]); }, hist, sc, 24);
+    if (tid == 0) s_min = 0xFFFFFFFFu;
     for (int i = tid; i < TK_BINS; i += blockDim.x) bins[i] = 0;
     __syncthreads();
-    uint32_t mn = 0xFFFFFFFFu, mx = 0u;
-    for (int64_t i = tid; i < n; i += blockDim.x) {
-        const uint32_t kk = f32_key(cd[i]);
-        mn = min(mn, kk);
-        mx = max(mx, kk);
-    }
+    uint32_t mn = 0xFFFFFFFFu;
+    for (int64_t i = tid; i < n; i += blockDim.x) mn = min(mn, f32_key(cd[i]));
     mn = __reduce_min_sync(0xFFFFFFFFu, mn);
-    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-    if (lane_id() == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
+    if (lane_id() == 0) atomicMin(&s_min, mn);
     __syncthreads();
-    const uint32_t kmin = s_min;
-    const float scale = (float)TK_BINS / ((float)(s_max - kmin) + 1.0f);
-    for (int64_t i = tid; i < n; i += blockDim.x) atomicAdd(&bins[tk_bin(f32_key(cd[i]), kmin, scale)], 1u);
+    const float vmin = key_f32(s_min);
+    const float scale = tk_scale(vmin, key_f32(dk));
+    for (int64_t i = tid; i < n; i += blockDim.x) {
+        const float v = cd[i];
+        if (f32_key(v) <= dk) atomicAdd(&bins[tk_vbin(v, vmin, scale)], 1u);
+    }
     __syncthreads();
     constexpr int PER = TK_BINS / TK_THREADS;
-    uint32_t loc[PER], tot = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) { loc[j] = bins[tid * PER + j]; tot += loc[j]; }
-    const uint32_t winc = warp_incl_scan(tot);
-    if (lane_id() == 31) wsum[warp_id()] = winc;
+    uint32_t loc[PER];
+    tk_scan<PER>(bins, wsum, loc);
     __syncthreads();
-    if (warp_id() == 0) {
-        const uint32_t v = wsum[lane_id()];
-        wsum[lane_id()] = warp_incl_scan(v) - v;
-    }
-    __syncthreads();
-    uint32_t run = wsum[warp_id()] + winc - tot;
-    const uint32_t need = (uint32_t)((int64_t)kq < n ? (int64_t)kq : n);
-    uint32_t big = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int b = tid * PER + j;
-        bins[b] = run;
-        if (run < need && run + loc[j] >= need) s_last = (uint32_t)b;      // bin holding rank need-1
-        run += loc[j];
-        big |= loc[j] > (uint32_t)TK_BIG ? 1u : 0u;
-    }
-    if (big) s_big = 1u;
-    __syncthreads();
-    if (s_big) {
-        if (tid == 0) atomicOr(ix.status, kStatusTopkOverrun);          // degenerate: refuse rather than go quadratic
-        return;
-    }
-    const uint32_t last = s_last;
     for (int64_t i = tid; i < n; i += blockDim.x) {
-        const uint32_t kk = f32_key(cd[i]);
-        const uint32_t b = tk_bin(kk, kmin, scale);
-        if (b <= last) {
-            const uint32_t p = atomicAdd(&bins[b], 1u);
-            keys[p] = ((unsigned long long)kk << 32) | cand[i];
+        const float v = cd[i];
+        const uint32_t kv = f32_key(v);
+        if (kv <= dk) {
+            const uint32_t p = atomicAdd(&bins[tk_vbin(v, vmin, scale)], 1u);
+            keys[p] = ((unsigned long long)kv << 32) | cand[i];
         }
     }
     __syncthreads();
-    const uint32_t upto = bins[last];                                    // keys in bins <= last
+    const uint32_t upto = bins[TK_BINS - 1];                 // keys at or below the rank-k distance
     for (uint32_t p = tid; p < upto; p += blockDim.x) {
         const unsigned long long me = keys[p];
-        const uint32_t b = tk_bin((uint32_t)(me >> 32), kmin, scale);
+        const uint32_t b = tk_vbin(key_f32((uint32_t)(me >> 32)), vmin, scale);
         const uint32_t st = b ? bins[b - 1] : 0u;
         const uint32_t en = bins[b];
+        if (en - st > (uint32_t)TK_BIG && en - st <= (uint32_t)TK_HEAVY) continue;   // sorted below
         uint32_t rank = 0;
         for (uint32_t j = st; j < en; ++j) rank += keys[j] < me ? 1u : 0u;
         const uint32_t pos = st + rank;
-        if ((int)pos < kq) {
+        if ((int64_t)pos < kq) {
             oid[pos] = (int64_t)(me & 0xFFFFFFFFull);
             od[pos] = key_f32((uint32_t)(me >> 32));
+        }
+    }
+    for (int b = 0; b < TK_BINS; ++b) {                     // heavy bins, one at a time
+        const uint32_t st = b ? bins[b - 1] : 0u, en = bins[b];
+        const uint32_t cntb = en - st;
+        if (cntb <= (uint32_t)TK_BIG || cntb > (uint32_t)TK_HEAVY || (int64_t)st >= kq) continue;
+        const int np2 = next_pow2((int)cntb);
+        __syncthreads();
+        for (int i = tid; i < np2; i += blockDim.x) hsm[i] = (uint32_t)i < cntb ? keys[st + i] : ~0ull;
+        __syncthreads();
+        cta_bitonic_u64(hsm, np2);
+        for (uint32_t i = tid; i < cntb && (int64_t)(st + i) < kq; i += blockDim.x) {
+            oid[st + i] = (int64_t)(hsm[i] & 0xFFFFFFFFull);
+            od[st + i] = key_f32((uint32_t)(hsm[i] >> 32));
         }
     }
 }
@@ -408,7 +417,14 @@ cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cud
     if (nq <= 0) return cudaSuccess;
     if (a.kc > TK_MAX) {
         if (!a.keys) return cudaErrorInvalidValue;
-        topk_large_kernel<<<(unsigned)nq, TK_THREADS, 0, st>>>(ix, a);
+        static bool large_attr = false;
+        if (!large_attr) {
+            cudaError_t e = cudaFuncSetAttribute(topk_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 TK_HEAVY * 8);
+            if (e != cudaSuccess) return e;
+            large_attr = true;
+        }
+        topk_large_kernel<<<(unsigned)nq, TK_THREADS, (size_t)TK_HEAVY * 8, st>>>(ix, a);
         return cudaGetLastError();
     }
     const int np2 = next_pow2((int)(a.kc > 1 ? a.kc : 1));
