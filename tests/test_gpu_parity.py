@@ -139,7 +139,8 @@ def _collect(bbc, h, idx, q, nprobe, kc):
 @pytest.mark.parametrize("kind,nprobe,kc,m,smin", [
     ("tiny", 12, 300, 64, 8), ("tiny", 48, 5000, 32, 8), ("sift", 16, 900, 64, 8),
     ("sift4", 20, 1200, 256, 4), ("embed", 10, 400, 2, 8), ("ragged", 40, 300, 16, 3),
-    ("ragged", 2, 1000, 64, 8), ("sift", 64, 12000, 64, 8), ("tiny", 5, 1, 64, 8)])
+    ("ragged", 2, 1000, 64, 8), ("sift", 64, 12000, 64, 8), ("tiny", 5, 1, 64, 8),
+    ("wide", 6, 1500, 64, 8)])
 def test_collect_candidates_and_state(bbc, oracle_lib, kind, nprobe, kc, m, smin, split):
     h, idx, q = dev_index(bbc, kind)
     bbc.bbc_set_param(h, "buckets", m)
@@ -344,6 +345,40 @@ def test_large_candidate_pool_topk(bbc, oracle_lib):
     gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
     for i in range(nq):
         _check_topk(oracle_lib, idx, q[i], gi[i], gd[i], oi[i], od[i], True)
+
+
+@pytest.mark.parametrize("case", ["ties", "inner_product"])
+def test_large_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case):
+    """The large top-k on candidates with thousands of equal distances (one
+    block of ties above the shared-memory sort, one within it), and on inner
+    products whose distances span the sign boundary."""
+    from synth import build_ivf_pq
+    from synth.data import sift_shaped, embedding_shaped
+    if case == "ties":
+        x, q = sift_shaped(30000, 3, d=128, n_centers=200)
+        x[:10000] = x[0]
+        x[10000:15000] = x[10000]
+        idx = build_ivf_pq(x, 16, 16, 8, "l2", kmeans_iters=3, pq_iters=3, pq_sample=5000)
+        q = np.stack([x[0] + 1.0, x[10000], q[0]]).astype(np.float32)
+    else:
+        x, q = embedding_shaped(30000, 3, d=64)
+        idx = build_ivf_pq(x, 16, 16, 8, "ip", kmeans_iters=3, pq_iters=3, pq_sample=5000)
+    h = bbc.bbc_index_create(idx, 0)
+    try:
+        nq, kc, k = len(q), 30000, 20000
+        cand = np.tile(np.arange(kc, dtype=np.uint32), (nq, 1))
+        cnt = np.full(nq, kc, dtype=np.int64)
+        gi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+        gd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+        bbc.bbc_rerank_topk(h, cuda(q), nq, cuda(cand), cuda(cnt), kc, k, gi, gd)
+        sync_ok(bbc, h)
+        gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+        for i in range(nq):
+            d64 = oracle_lib.rerank(q[i], idx.vectors, cand[i].astype(np.int64), idx.metric)
+            oi, od = oracle_lib.topk_final(d64, cand[i].astype(np.int64), k)
+            _check_topk(oracle_lib, idx, q[i], gi[i], gd[i], oi, od, case == "ties")
+    finally:
+        bbc.bbc_index_free(h)
 
 
 @pytest.mark.parametrize("kind", ["tiny", "sift", "ragged"])
