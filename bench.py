@@ -50,8 +50,8 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="override data size (testing only)")
     p.add_argument("--nq", type=int, default=None)
     p.add_argument("--k", type=int, default=None)
-    p.add_argument("--nprobe", type=int, default=None)
-    p.add_argument("--kc-ratio", type=float, default=1.5)
+    p.add_argument("--nprobe", default=None, help="lists probed; a comma list prints one line per value")
+    p.add_argument("--kc-ratio", default="1.5", help="K_c / k; a comma list prints one line per value")
     p.add_argument("--buckets", type=int, default=64)
     p.add_argument("--cpu-queries", type=int, default=200, help="oracle sample for cpu_baseline")
     p.add_argument("--ref-queries", type=int, default=24, help="oracle queries per reference step")
@@ -107,7 +107,7 @@ def make_inputs(args, device):
     n = args.n or w.n
     nq = args.nq or w.nq
     k = args.k or w.k
-    nprobe = args.nprobe or w.nprobe
+    nprobe = int(str(args.nprobe).split(",")[0]) if args.nprobe else w.nprobe
     x, q = make_workload(w, n=n, nq=nq)
     set_build_device(device)
     t0 = time.time()
@@ -219,7 +219,7 @@ def run_reference(args, ws, rank):
     oracle.build()
     device = "cuda" if _cuda() else "cpu"
     w, idx, q, k, nprobe, _ = make_inputs(args, device)
-    kc = max(k, int(math.ceil(args.kc_ratio * k - 1e-9)))
+    kc = max(k, int(math.ceil(float(str(args.kc_ratio).split(",")[0]) * k - 1e-9)))
     nqs = min(args.ref_queries, len(q))
     for s in range(args.warmup):
         oracle.search(idx, q[:1], k, nprobe, kc, "sort")
@@ -254,7 +254,7 @@ def run_serve(args, ws, rank, local):
     bbc.build()
     w, idx, q, _, _, t_build = make_inputs(args, f"cuda:{local}")
     index = bbc.Index(idx, device=local)
-    index.set(kc_ratio=args.kc_ratio, workspace_mb=64 * 1024)
+    index.set(kc_ratio=float(str(args.kc_ratio).split(",")[0]), workspace_mb=64 * 1024)
     h = index.handle
     rates = [float(r) for r in args.rates.split(",")]
     lines = []
@@ -313,7 +313,7 @@ def run_serve(args, ws, rank, local):
             "value": best["completed_rps"], "unit": "requests/s", "n_gpus": ws, "higher_is_better": True,
             "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "data": "synthetic", "dtype": "u16/u32 ADC, f32 re-rank",
             "config": {"workload": "serve-" + w.name, "requests_per_rate": args.requests, "k": "log-uniform [100, 50000]",
-                       "nprobe": "uniform {32, 128, 512}", "kc_ratio": args.kc_ratio, "streams": 4,
+                       "nprobe": "uniform {32, 128, 512}", "kc_ratio": float(str(args.kc_ratio).split(",")[0]), "streams": 4,
                        "max_batch": 1024, "cand_bytes_budget": 16 << 30, "index_build_s": round(t_build, 1)},
             "rates": lines}), flush=True)
     index.close()
@@ -336,21 +336,27 @@ def main():
     w, idx, q, k, nprobe, t_build = make_inputs(args, f"cuda:{local}")
     torch.cuda.empty_cache()
     index = bbc.Index(idx, device=local)
-    index.set(kc_ratio=args.kc_ratio, buckets=args.buckets, workspace_mb=64 * 1024)
+    index.set(buckets=args.buckets, workspace_mb=64 * 1024)
     float_data = not index.info["vectors_u8_exact"]
     precs = [int(v) for v in args.precision.split(",")] if args.precision else [2 if float_data else 0]
     xt = torch.from_numpy(idx.vectors).to(dev)
+    nprobes = [int(v) for v in args.nprobe.split(",")] if args.nprobe else [nprobe]
+    ratios = [float(v) for v in str(args.kc_ratio).split(",")]
     for prec in precs:
-        measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt, prec)
+        for npb in nprobes:
+            for ratio in ratios:
+                index.set(kc_ratio=ratio)
+                measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec, ratio)
     index.close()
 
 
-def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt, prec):
+def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt, prec, ratio):
     """Time one configuration and print its JSON line (rank 0)."""
     import torch
     dev = torch.device("cuda", local)
-    index.set(precision=prec)
-    kc = max(k, int(math.ceil(args.kc_ratio * k - 1e-9)))
+    if index.get("precision") != prec:
+        index.set(precision=prec)
+    kc = max(k, int(math.ceil(ratio * k - 1e-9)))
     nq = len(q)
     h = index.handle
     qd = torch.from_numpy(q).to(dev)
@@ -493,7 +499,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
             "data": "synthetic",
             "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "metric_space": idx.metric,
                        "pq": f"{idx.pq_m}x{idx.pq_bits}", "nq": nq, "k": k, "nprobe": nprobe, "kc": kc,
-                       "buckets": args.buckets, "rerank": rerank,
+                       "kc_ratio": ratio, "buckets": args.buckets, "rerank": rerank,
                        "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
                        "recall_tie_aware": True, "ground_truth_cpu_spotcheck": gt_check,
                        "l2_flush_between_steps": True, "parallelism": f"replicas x{ws}",
