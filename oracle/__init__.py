@@ -87,6 +87,18 @@ def lib():
             L.oracle_e4m3_value.restype = C.c_double
             L.oracle_e4m3_value.argtypes = [C.c_uint8]
             L.oracle_prec_copy.argtypes = [vp, i64, i32, i32, i32, vp, vp]
+            L.oracle_sign_encode.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp, vp]
+            L.oracle_rotation_eps.restype = C.c_double
+            L.oracle_rotation_eps.argtypes = [vp, i32]
+            L.oracle_sign_bounds.argtypes = [vp, i32, vp, vp, C.c_double, vp, vp, i64, C.c_double, vp, vp]
+            L.oracle_alg2.restype = i64
+            L.oracle_alg2.argtypes = [vp, vp, vp, i64, i32, vp, vp]
+            L.oracle_obs1_count.restype = i64
+            L.oracle_obs1_count.argtypes = [vp, vp, vp, i64, i32]
+            L.oracle_rounds.restype = i64
+            L.oracle_rounds.argtypes = [vp, vp, vp, i64, i32, vp, vp]
+            L.oracle_oneshot.restype = i64
+            L.oracle_oneshot.argtypes = [vp, vp, i64, i32, vp, vp]
             L.oracle_search.restype = i32
             L.oracle_search.argtypes = [C.POINTER(_Index), vp, i64, i32, i32, i64, i32, i32, i32,
                                         vp, vp, vp]
@@ -300,3 +312,104 @@ def prec_copy(vectors: np.ndarray, prec: int, dpad: int | None = None):
     meta = np.zeros((n, 4), dtype=np.float64)
     lib().oracle_prec_copy(_p(v), n, d, dpad, prec, _p(rows), _p(meta))
     return rows, meta
+
+
+# ---------------------------------------------------------------------------
+# 1-bit sign quantizer and the bounded re-rank (Section 3.4, Obs. 1, Alg. 2)
+# ---------------------------------------------------------------------------
+def sign_encode(index):
+    """Codes (u32 [n, d/32], list order) and factors (f64 [n, 4] = alpha, e,
+    ||o - c||^2, popcount) of the rotated residuals of an IVF sign index."""
+    d = index.d
+    codes = np.zeros((index.n, d // 32), dtype=np.uint32)
+    fac = np.zeros((index.n, 4), dtype=np.float64)
+    v, c, r = _f32(index.vectors), _f32(index.centroids), _f32(index.rotation)
+    offs = np.ascontiguousarray(index.list_offsets, dtype=np.int64)
+    ids = np.ascontiguousarray(index.ids, dtype=np.int64)
+    lib().oracle_sign_encode(_p(v), d, _p(c), index.nlist, _p(offs), _p(ids), _p(r), _p(codes), _p(fac))
+    return codes, fac
+
+
+def rotation_eps(rot) -> float:
+    r = _f32(rot)
+    return float(lib().oracle_rotation_eps(_p(r), r.shape[0]))
+
+
+def sign_bounds(q, centroid, rot, eps, codes, fac, scale: float = 1.0):
+    """Bounds [lb, ub] on ||q - o||^2 for the objects whose codes / factors are given."""
+    q, c, r = _f32(q), _f32(centroid), _f32(rot)
+    codes = np.ascontiguousarray(codes, dtype=np.uint32)
+    fac = np.ascontiguousarray(fac, dtype=np.float64)
+    n = codes.shape[0]
+    lb = np.empty(n, dtype=np.float64)
+    ub = np.empty(n, dtype=np.float64)
+    lib().oracle_sign_bounds(_p(q), q.shape[0], _p(c), _p(r), eps, _p(codes), _p(fac), n, scale, _p(lb), _p(ub))
+    return lb, ub
+
+
+def alg2(lb, ub, ex, k: int):
+    """Algorithm 2: (number of exact distances computed, result indices)."""
+    lb, ub, ex = (np.ascontiguousarray(a, dtype=np.float64) for a in (lb, ub, ex))
+    n = lb.shape[0]
+    out = np.empty(max(k, 1), dtype=np.int64)
+    no = C.c_int64()
+    cnt = lib().oracle_alg2(_p(lb), _p(ub), _p(ex), n, k, _p(out), C.byref(no))
+    return int(cnt), out[:no.value].copy()
+
+
+def obs1_count(lb, ub, ex, k: int) -> int:
+    lb, ub, ex = (np.ascontiguousarray(a, dtype=np.float64) for a in (lb, ub, ex))
+    return int(lib().oracle_obs1_count(_p(lb), _p(ub), _p(ex), lb.shape[0], k))
+
+
+def oneshot(lb, ub, k: int):
+    """One-pass classification: (|S|, |certainly in|, |to decide|)."""
+    lb, ub = (np.ascontiguousarray(a, dtype=np.float64) for a in (lb, ub))
+    a, b = C.c_int64(), C.c_int64()
+    ns = lib().oracle_oneshot(_p(lb), _p(ub), lb.shape[0], k, C.byref(a), C.byref(b))
+    return int(ns), a.value, b.value
+
+
+def rounds(lb, ub, ex, k: int):
+    """Two-round bounded re-rank: (exact distances computed, result indices sorted)."""
+    lb, ub, ex = (np.ascontiguousarray(a, dtype=np.float64) for a in (lb, ub, ex))
+    out = np.empty(max(k, 1), dtype=np.int64)
+    no = C.c_int64()
+    cnt = lib().oracle_rounds(_p(lb), _p(ub), _p(ex), lb.shape[0], k, _p(out), C.byref(no))
+    return int(cnt), out[:no.value].copy()
+
+
+def sign_search(index, queries, k: int, nprobe: int, scale: float = 1.0, codes=None, fac=None):
+    """Bounded search over an IVF sign index (single-threaded).
+
+    Probe as in ``search``; bounds for every object of the probed lists; the
+    result is the k smallest (exact FP64 distance, id) of the probed lists.
+    Returns (ids [nq, k], dists [nq, k]) and per-query stats [S_q, |S|,
+    |certainly in|, |to decide|, Alg. 2 count, Obs. 1 count, two-round count]."""
+    if codes is None:
+        codes, fac = sign_encode(index)
+    eps = rotation_eps(index.rotation)
+    q = _f32(queries).reshape(-1, index.d)
+    nq = q.shape[0]
+    oi = np.empty((nq, k), dtype=np.int64)
+    od = np.empty((nq, k), dtype=np.float64)
+    st = np.zeros((nq, 7), dtype=np.int64)
+    offs = index.list_offsets
+    for i in range(nq):
+        lists, _ = probe(q[i], index.centroids, nprobe, index.metric)
+        lbs, ubs, sel = [], [], []
+        for l in lists:
+            a, b = offs[l], offs[l + 1]
+            lb, ub = sign_bounds(q[i], index.centroids[l], index.rotation, eps, codes[a:b], fac[a:b], scale)
+            lbs.append(lb); ubs.append(ub); sel.append(np.arange(a, b))
+        lb, ub, sel = np.concatenate(lbs), np.concatenate(ubs), np.concatenate(sel)
+        gid = index.ids[sel]
+        ex = rerank(q[i], index.vectors, gid, index.metric)
+        oi[i], od[i] = topk_final(ex, gid, k)
+        ns, nin, nr = oneshot(lb, ub, k)
+        a2, _ = alg2(lb, ub, ex, k)
+        rc, ridx = rounds(lb, ub, ex, k)
+        if not np.array_equal(gid[ridx], oi[i][:len(ridx)]):
+            raise AssertionError("two-round bounded re-rank disagrees with the exact top-k")
+        st[i] = [len(sel), ns, nin, nr, a2, obs1_count(lb, ub, ex, k), rc]
+    return oi, od, st

@@ -29,6 +29,15 @@
  *   oracle_topk_final     the k smallest exact distances, ascending.
  *   oracle_search         the whole path for a batch of queries.
  *   oracle_bruteforce     exact kNN over the whole data set (FP64).
+ *   oracle_sign_encode, oracle_sign_bounds, oracle_rotation_eps
+ *                         the 1-bit sign quantizer of the bounded re-rank
+ *                         (Section 3.4): codes of the rotated residual and
+ *                         hard per-object distance bounds.
+ *   oracle_alg2           Algorithm 2, minimal re-ranking with two heaps.
+ *   oracle_obs1_count     the set of Observation 1 (bounds enclosing Dist_k).
+ *   oracle_oneshot        the one-pass sure-in / sure-out classification.
+ *   oracle_rounds         the bounded re-rank in two rounds with exact
+ *                         returned distances (batched Algorithm 3).
  *   oracle_bf16_*, oracle_e4m3_*, oracle_prec_copy
  *                         the low-precision copies of the vectors used by the
  *                         precision form of the re-rank (the paper re-ranks
@@ -74,6 +83,11 @@ static int cmp_ukey(const void* a, const void* b) {
     if (x->id < y->id) return -1;
     if (x->id > y->id) return 1;
     return 0;
+}
+
+static int cmp_double(const void* a, const void* b) {
+    const double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
 }
 
 static int ukey_less(ukey a, ukey b) { return a.e < b.e || (a.e == b.e && a.id < b.id); }
@@ -612,4 +626,302 @@ void oracle_prec_copy(const float* v, int64_t n, int32_t d, int32_t dpad, int32_
         meta4[i * 4 + 2] = sqrt(n2);
         meta4[i * 4 + 3] = 0.0;
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* 1-bit sign quantizer with per-object bounds (bounded re-rank)        */
+/* ------------------------------------------------------------------ */
+/* Codes of the rotated residual (Section 2 cites RaBitQ for bounded
+ * methods without stating its estimator; this is the deterministic reading
+ * used here).  For object o in list l: u = o - c_l, r = P u (FP64, P the
+ * FP32-stored rotation), s_i = +1 if r_i > 0 else -1, alpha = <s, r> / d =
+ * mean |r_i|, e = ||r - alpha s||, un2 = ||u||^2.  Codes are d/32 words per
+ * object (bit i of word w = [r_(32w+i) > 0]), in list order.  fac[4] =
+ * {alpha, e, un2, popcount of the code}. */
+void oracle_sign_encode(const float* vectors, int32_t d, const float* centroids, int32_t nlist,
+                        const int64_t* list_offsets, const int64_t* ids, const float* rot,
+                        uint32_t* codes, double* fac) {
+    const int32_t W = d / 32;
+    double* u = (double*)malloc(sizeof(double) * (size_t)d);
+    double* r = (double*)malloc(sizeof(double) * (size_t)d);
+    for (int32_t l = 0; l < nlist; ++l) {
+        for (int64_t p = list_offsets[l]; p < list_offsets[l + 1]; ++p) {
+            const float* o = vectors + (size_t)ids[p] * d;
+            const float* c = centroids + (size_t)l * d;
+            double un2 = 0.0;
+            for (int32_t i = 0; i < d; ++i) { u[i] = (double)o[i] - (double)c[i]; un2 += u[i] * u[i]; }
+            double sabs = 0.0;
+            for (int32_t i = 0; i < d; ++i) {
+                double t = 0.0;
+                for (int32_t j = 0; j < d; ++j) t += (double)rot[(size_t)i * d + j] * u[j];
+                r[i] = t;
+                sabs += fabs(t);
+            }
+            const double alpha = sabs / d;
+            double e2 = 0.0;
+            int64_t pc = 0;
+            uint32_t* cw = codes + (size_t)p * W;
+            for (int32_t w = 0; w < W; ++w) cw[w] = 0;
+            for (int32_t i = 0; i < d; ++i) {
+                const double s = r[i] > 0.0 ? 1.0 : -1.0;
+                if (r[i] > 0.0) { cw[i / 32] |= 1u << (i % 32); ++pc; }
+                e2 += (r[i] - alpha * s) * (r[i] - alpha * s);
+            }
+            fac[p * 4 + 0] = alpha;
+            fac[p * 4 + 1] = sqrt(e2);
+            fac[p * 4 + 2] = un2;
+            fac[p * 4 + 3] = (double)pc;
+        }
+    }
+    free(u);
+    free(r);
+}
+
+/* ||P^T P - I||_F in FP64: bounds |<P t, P u> - <t, u>| <= eps ||t|| ||u||. */
+double oracle_rotation_eps(const float* rot, int32_t d) {
+    double s = 0.0;
+    for (int32_t i = 0; i < d; ++i) {
+        for (int32_t j = 0; j < d; ++j) {
+            double t = 0.0;
+            for (int32_t k = 0; k < d; ++k) t += (double)rot[(size_t)k * d + i] * (double)rot[(size_t)k * d + j];
+            if (i == j) t -= 1.0;
+            s += t * t;
+        }
+    }
+    return sqrt(s);
+}
+
+/* Bounds [lb, ub] on ||q - o||^2 for the objects of list l (positions
+ * list_offsets[l] .. list_offsets[l+1]), all in FP64:
+ *   t = q - c_l, q' = P t; 4-bit query: lo = min q', Delta = (max q' - lo) / 15,
+ *   u_i = nearest integer to (q'_i - lo) / Delta in [0, 15], q~ = lo + Delta u,
+ *   eta = ||q' - q~||;
+ *   X = <q~, s> = lo (2 pc - d) + Delta (2 sum_i u_i b_i - sum_i u_i)   (b = code bits);
+ *   <q', r> in alpha X +- (scale ||q'|| e + |alpha| eta sqrt(d));
+ *   ||q - o||^2 = ||t||^2 + ||u||^2 - 2 <t, u>, |<t, u> - <q', r>| <= eps ||t|| ||u||;
+ * plus a relative FP64 allowance of 1e-12.  scale = 1 gives hard bounds. */
+void oracle_sign_bounds(const float* q, int32_t d, const float* centroid, const float* rot, double eps,
+                        const uint32_t* codes, const double* fac, int64_t n, double scale,
+                        double* lb, double* ub) {
+    const int32_t W = d / 32;
+    double* t = (double*)malloc(sizeof(double) * (size_t)d);
+    double* qr = (double*)malloc(sizeof(double) * (size_t)d);
+    int32_t* uq = (int32_t*)malloc(sizeof(int32_t) * (size_t)d);
+    double tn2 = 0.0;
+    for (int32_t i = 0; i < d; ++i) { t[i] = (double)q[i] - (double)centroid[i]; tn2 += t[i] * t[i]; }
+    double lo = INFINITY, hi = -INFINITY, qn2 = 0.0;
+    for (int32_t i = 0; i < d; ++i) {
+        double a = 0.0;
+        for (int32_t j = 0; j < d; ++j) a += (double)rot[(size_t)i * d + j] * t[j];
+        qr[i] = a;
+        qn2 += a * a;
+        if (a < lo) lo = a;
+        if (a > hi) hi = a;
+    }
+    const double delta = (hi - lo) / 15.0;
+    double eta2 = 0.0;
+    int64_t usum = 0;
+    for (int32_t i = 0; i < d; ++i) {
+        int32_t ui = 0;
+        if (delta > 0.0) {
+            double v = nearbyint((qr[i] - lo) / delta);
+            ui = v < 0.0 ? 0 : (v > 15.0 ? 15 : (int32_t)v);
+        }
+        uq[i] = ui;
+        usum += ui;
+        const double diff = qr[i] - (lo + delta * ui);
+        eta2 += diff * diff;
+    }
+    const double eta = sqrt(eta2), qn = sqrt(qn2), tn = sqrt(tn2), sd = sqrt((double)d);
+    for (int64_t p = 0; p < n; ++p) {
+        const uint32_t* cw = codes + (size_t)p * W;
+        int64_t ub_sum = 0;
+        for (int32_t i = 0; i < d; ++i)
+            if ((cw[i / 32] >> (i % 32)) & 1u) ub_sum += uq[i];
+        const double alpha = fac[p * 4 + 0], e = fac[p * 4 + 1], un2 = fac[p * 4 + 2], pc = fac[p * 4 + 3];
+        const double X = lo * (2.0 * pc - d) + delta * (2.0 * (double)ub_sum - (double)usum);
+        const double est = alpha * X;
+        const double half = scale * qn * e + fabs(alpha) * eta * sd;
+        const double rot_err = 2.0 * eps * tn * sqrt(un2);
+        const double base = tn2 + un2;
+        const double slack = 1e-12 * (base + 2.0 * fabs(est) + 2.0 * half + rot_err);
+        double l = base - 2.0 * (est + half) - rot_err - slack;
+        lb[p] = l > 0.0 ? l : 0.0;
+        ub[p] = base - 2.0 * (est - half) + rot_err + slack;
+    }
+    free(t);
+    free(qr);
+    free(uq);
+}
+
+/* ---- binary heaps over (key, index) for Algorithm 2 ---- */
+typedef struct { double key; int64_t i; } hitem;
+static int hless(hitem a, hitem b) { return a.key < b.key || (a.key == b.key && a.i < b.i); }
+/* max-heap when mx = 1, min-heap when mx = 0 */
+static int hbefore(hitem a, hitem b, int mx) { return mx ? hless(b, a) : hless(a, b); }
+static void hpush(hitem* h, int64_t* n, hitem x, int mx) {
+    int64_t i = (*n)++;
+    h[i] = x;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!hbefore(h[i], h[p], mx)) break;
+        hitem t = h[i]; h[i] = h[p]; h[p] = t;
+        i = p;
+    }
+}
+static hitem hpop(hitem* h, int64_t* n, int mx) {
+    hitem top = h[0];
+    h[0] = h[--(*n)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, b = i;
+        if (l < *n && hbefore(h[l], h[b], mx)) b = l;
+        if (r < *n && hbefore(h[r], h[b], mx)) b = r;
+        if (b == i) break;
+        hitem t = h[i]; h[i] = h[b]; h[b] = t;
+        i = b;
+    }
+    return top;
+}
+
+/* Algorithm 2 (minimal re-ranking of a bounded method) over n objects with
+ * bounds [lb, ub] and exact distances ex (evaluated only when re-ranked).
+ * H_u is a max-heap on ub of at most k objects; H_l a min-heap on lb.  After
+ * the collection phase, the object with the smaller lower bound among the
+ * two tops is re-ranked (its bounds collapse to its exact distance) while the
+ * top upper bound of H_u exceeds the top lower bound of H_l.  Ties in keys
+ * go to the smaller index.  Writes the result (indices into the arrays, at
+ * most k) to out_idx and returns the number of exact distances computed. */
+int64_t oracle_alg2(const double* lb, const double* ub, const double* ex, int64_t n, int32_t k,
+                    int64_t* out_idx, int64_t* out_n) {
+    hitem* hu = (hitem*)malloc(sizeof(hitem) * (size_t)(k + 2));
+    hitem* hl = (hitem*)malloc(sizeof(hitem) * (size_t)(n + 2));
+    double* cl = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));   /* current lb */
+    double* cu = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));   /* current ub */
+    char* vis = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t nu = 0, nl = 0, reranked = 0;
+    for (int64_t i = 0; i < n; ++i) { cl[i] = lb[i]; cu[i] = ub[i]; }
+    for (int64_t i = 0; i < n; ++i) {
+        const double top = nu < k ? INFINITY : hu[0].key;
+        if (cu[i] < top) {
+            hitem x = {cu[i], i};
+            hpush(hu, &nu, x, 1);
+            if (nu > k) {
+                hitem m = hpop(hu, &nu, 1);
+                hitem y = {cl[m.i], m.i};
+                hpush(hl, &nl, y, 0);
+            }
+        } else if (cl[i] < top) {
+            hitem y = {cl[i], i};
+            hpush(hl, &nl, y, 0);
+        }
+    }
+    for (;;) {
+        const double utop = nu < k ? INFINITY : hu[0].key;
+        const double ltop = nl > 0 ? hl[0].key : INFINITY;
+        if (!(utop > ltop)) break;
+        /* the top of H_u with the larger upper bound, or the top of H_l */
+        int from_u = nu > 0 && !vis[hu[0].i] && cl[hu[0].i] < ltop;
+        int64_t o;
+        if (from_u) o = hpop(hu, &nu, 1).i;
+        else o = hpop(hl, &nl, 0).i;
+        if (vis[o]) continue;
+        vis[o] = 1;
+        ++reranked;
+        cl[o] = cu[o] = ex[o];
+        hitem x = {ex[o], o};
+        hpush(hu, &nu, x, 1);
+        if (nu > k) {
+            hitem m = hpop(hu, &nu, 1);
+            if (!vis[m.i]) {
+                hitem y = {cl[m.i], m.i};
+                hpush(hl, &nl, y, 0);
+            }
+        }
+    }
+    *out_n = nu;
+    for (int64_t i = 0; i < nu; ++i) out_idx[i] = hu[i].i;
+    free(hu); free(hl); free(cl); free(cu); free(vis);
+    return reranked;
+}
+
+/* Observation 1: objects whose bounds enclose Dist_k, the distance of the
+ * k-th object in (exact, index) order. */
+int64_t oracle_obs1_count(const double* lb, const double* ub, const double* ex, int64_t n, int32_t k) {
+    if (n <= k || k <= 0) return 0;
+    dkey* a = (dkey*)malloc(sizeof(dkey) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) { a[i].s = ex[i]; a[i].id = i; }
+    qsort(a, (size_t)n, sizeof(dkey), cmp_dkey);
+    const double dk = a[k - 1].s;
+    free(a);
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i) c += (lb[i] <= dk && dk <= ub[i]) ? 1 : 0;
+    return c;
+}
+
+/* The one-shot classification of the bounded re-rank: U_k = k-th smallest
+ * ub, S = {lb <= U_k}, L = (k+1)-th smallest lb over S; certainly in
+ * (ub < L), to decide (the rest of S).  Returns |S| and writes |in|, |R|. */
+int64_t oracle_oneshot(const double* lb, const double* ub, int64_t n, int32_t k, int64_t* n_in,
+                       int64_t* n_r) {
+    if (n <= k) { *n_in = n; *n_r = 0; return n; }
+    double* v = (double*)malloc(sizeof(double) * (size_t)n);
+    memcpy(v, ub, sizeof(double) * (size_t)n);
+    qsort(v, (size_t)n, sizeof(double), cmp_double);
+    const double uk = v[k - 1];
+    int64_t ns = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (lb[i] <= uk) v[ns++] = lb[i];
+    if (ns <= k) { free(v); *n_in = ns; *n_r = 0; return ns; }
+    qsort(v, (size_t)ns, sizeof(double), cmp_double);
+    const double l1 = v[k];
+    int64_t in = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (lb[i] <= uk && ub[i] < l1) ++in;
+    free(v);
+    *n_in = in;
+    *n_r = ns - in;
+    return ns;
+}
+
+/* The bounded re-rank with exact returned distances, in two rounds (the
+ * batched form of Algorithm 3's marginal re-ranking):
+ *   1. U_k = k-th smallest ub; S = {lb <= U_k}; B = the k smallest (ub, index).
+ *   2. Re-rank B; U' = the largest exact distance in B (>= Dist_k).
+ *   3. S' = {o in S \ B : lb_o <= U'}; re-rank S'.
+ *   4. Result: the k smallest (exact, index) of B u S'.
+ * Every object outside B u S' has lb > U', so k objects of B are strictly
+ * nearer.  Writes the result indices (sorted) and returns the number of exact
+ * distances computed (|B| + |S'|). */
+int64_t oracle_rounds(const double* lb, const double* ub, const double* ex, int64_t n, int32_t k,
+                      int64_t* out_idx, int64_t* out_n) {
+    dkey* a = (dkey*)malloc(sizeof(dkey) * (size_t)(n > 0 ? n : 1));
+    char* re = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t count = 0;
+    if (n <= k) {
+        for (int64_t i = 0; i < n; ++i) re[i] = 1;
+        count = n;
+    } else {
+        for (int64_t i = 0; i < n; ++i) { a[i].s = ub[i]; a[i].id = i; }
+        qsort(a, (size_t)n, sizeof(dkey), cmp_dkey);
+        const double uk = a[k - 1].s;
+        double up = -INFINITY;
+        for (int32_t j = 0; j < k; ++j) {
+            re[a[j].id] = 1;
+            if (ex[a[j].id] > up) up = ex[a[j].id];
+        }
+        count = k;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!re[i] && lb[i] <= uk && lb[i] <= up) { re[i] = 1; ++count; }
+        }
+    }
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (re[i]) { a[m].s = ex[i]; a[m].id = i; ++m; }
+    qsort(a, (size_t)m, sizeof(dkey), cmp_dkey);
+    *out_n = m < k ? m : k;
+    for (int64_t i = 0; i < *out_n; ++i) out_idx[i] = a[i].id;
+    free(a);
+    free(re);
+    return count;
 }

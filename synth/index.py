@@ -6,9 +6,10 @@ The index is an input to the search path, built once before any query runs:
   inverted list (the paper's indexing phase, Section 2 "Quantization").
 * PQ: non-residual product quantisation, M sub-spaces of d/M dimensions with
   2^b codewords each, trained by k-means on raw sub-vectors (seed 4).
-* Sign codes: a seeded random rotation (seed 5) of each vector's residual to
-  its list centroid, kept as one sign bit per dimension plus per-vector
-  scalars (see ``build_ivf_sign``).
+* Sign quantizer: IVF lists plus a seeded random rotation (seed 5); the sign
+  codes of each rotated residual and their per-vector factors are derived
+  from these by the library and by the oracle, each on its own (see
+  ``build_ivf_sign``).
 
 Lists keep vectors in ascending id order.  The canonical code layout is one
 row per vector in list order; for 8-bit PQ byte m holds sub-space m, for
@@ -280,39 +281,42 @@ def write_index(path: str, idx: IvfPqIndex) -> None:
             f.write(np.ascontiguousarray(arr, dtype=dt).tobytes())
 
 
-# Placeholders for the sign-code index are filled in by build_ivf_sign below.
 @dataclasses.dataclass
 class IvfSignIndex:
+    """IVF lists plus the seeded rotation of the 1-bit sign quantizer; the
+    codes and per-object factors are derived from these by their users."""
     metric: str
     d: int
     nlist: int
     centroids: np.ndarray       # f32 [nlist, d]
     list_offsets: np.ndarray    # i64 [nlist + 1]
     ids: np.ndarray             # i64 [n], list order
-    rotation: np.ndarray        # f32 [d, d], orthonormal
-    signs: np.ndarray           # u8 [n, d / 8], list order, bit i of byte j = sign of dim 8j+i
+    rotation: np.ndarray        # f32 [d, d], orthonormal rows (r = P u)
     vectors: np.ndarray         # f32 [n, d], id order
+
+    @property
+    def n(self) -> int:
+        return int(self.vectors.shape[0])
+
+
+def random_rotation(d: int, seed: int = SEED_ROT) -> np.ndarray:
+    """Seeded orthonormal d x d matrix (QR of a Gaussian matrix, FP64), stored FP32."""
+    rng = np.random.default_rng(seed)
+    q, r = np.linalg.qr(rng.standard_normal((d, d)))
+    q = q * np.sign(np.diag(r))[None, :]
+    return np.ascontiguousarray(q.astype(np.float32))
 
 
 def build_ivf_sign(x: np.ndarray, nlist: int, kmeans_iters: int = 12,
                    kmeans_sample: int | None = None) -> IvfSignIndex:
-    """IVF with 1-bit sign codes of the rotated residual P_rot (o - c_l)."""
+    """IVF (L2) with a seeded rotation for 1-bit sign codes of P (o - c_l)."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     n, d = x.shape
-    if d % 8:
-        raise ValueError("d must be a multiple of 8 for sign codes")
+    if d % 32:
+        raise ValueError("d must be a multiple of 32 for sign codes")
     if kmeans_sample is None:
         kmeans_sample = min(n, 256 * nlist)
     cent = kmeans(x, nlist, iters=kmeans_iters, seed=SEED_KMEANS, sample=kmeans_sample)
     assign = nearest(x, cent)
     ids, offsets = _inverted_lists(assign, nlist)
-    rng = np.random.default_rng(SEED_ROT)
-    rot, _ = np.linalg.qr(rng.standard_normal((d, d)))
-    rot = rot.astype(np.float32)
-    signs = np.empty((n, d // 8), dtype=np.uint8)
-    chunk = 1 << 16
-    for s in range(0, n, chunk):
-        sel = ids[s:s + chunk]
-        r = (x[sel] - cent[assign[sel]]) @ rot.T
-        signs[s:s + chunk] = np.packbits(r > 0, axis=1, bitorder="little")
-    return IvfSignIndex("l2", d, nlist, cent, offsets, ids, rot, signs, x)
+    return IvfSignIndex("l2", d, nlist, cent, offsets, ids, random_rotation(d), x)
