@@ -52,6 +52,7 @@ extern "C" {
 #define BBC_METRIC_L2 0
 #define BBC_METRIC_IP 1
 #define BBC_QUANT_PQ 0
+#define BBC_QUANT_SIGN 1
 
 typedef struct bbc_index bbc_index;   /* opaque, owned by the library */
 
@@ -83,6 +84,8 @@ typedef struct {
     int32_t vectors_u8_exact;  /* 1 if every component is an integer in [0,255] (exact u8 copy kept) */
     int32_t device;
     int64_t device_bytes;      /* bytes of device memory the index holds */
+    int32_t quantizer;         /* BBC_QUANT_PQ or BBC_QUANT_SIGN */
+    int32_t reserved;
 } bbc_index_info_t;
 
 /* Build a device-resident index from host arrays (copied to `device`).
@@ -94,6 +97,30 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out);
  * list_offsets, ids, codes, codebooks, vectors, each 64-byte aligned) and
  * create the device index.  BBC_ERR_IO / BBC_ERR_FORMAT on a bad file. */
 int bbc_index_load(const char* path, int device, bbc_index** out);
+
+/* Host-side description of an IVF index with the 1-bit sign quantizer of the
+ * bounded re-rank (Section 3.4; the paper cites RaBitQ without stating its
+ * estimator, so the bounds are this library's hard bounds, see bbc_search).
+ * The library derives, on the device, for every vector o of list l the codes
+ * s = sign(P (o - c_l)) and the factors alpha = mean |P (o - c_l)|_i,
+ * e = ||P (o - c_l) - alpha s||, ||o - c_l||^2.  HOST pointers, copied. */
+typedef struct {
+    int64_t n;                 /* number of vectors, 1 <= n < 2^32 - 1 */
+    int32_t d;                 /* dimension, a multiple of 32, at most 2048 */
+    int32_t nlist;
+    int32_t metric;            /* BBC_METRIC_L2 */
+    const float* centroids;    /* [nlist * d] */
+    const int64_t* list_offsets; /* [nlist + 1] */
+    const int64_t* ids;        /* [n] vector id at each list position */
+    const float* rotation;     /* [d * d] row-major P (orthonormal rows); r = P u */
+    const float* vectors;      /* [n * d] row-major by id */
+} bbc_sign_host;
+
+/* Build a device index with sign codes.  BBC_ERR_UNSUPPORTED for inner
+ * product or d not a multiple of 32 / above 2048.  On such an index
+ * bbc_search and bbc_search_host run the bounded re-rank; the other per-step
+ * calls return BBC_ERR_UNSUPPORTED. */
+int bbc_index_create_sign(const bbc_sign_host* h, int device, bbc_index** out);
 
 int bbc_index_free(bbc_index* ix);
 int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
@@ -136,6 +163,11 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  reported distances of members placed by the copy's bound
  *                  are the copy's scores (see bbc_rerank_bounds).  Applies when
  *                  the exact u8 re-rank is not in use.
+ *   "bound_scale"  sign-code indexes: factor on the residual term ||q'|| e of
+ *                  the bounds, in (0, 1].  1 (default) gives hard bounds and
+ *                  results equal to the exact top-k of the probed lists;
+ *                  smaller values narrow the intervals in the spirit of
+ *                  RaBitQ's probabilistic bound and may drop true members.
  * Unknown key or out-of-range value: BBC_ERR_ARG. */
 int bbc_set_param(bbc_index* ix, const char* key, double value);
 int bbc_get_param(const bbc_index* ix, const char* key, double* value);
@@ -278,6 +310,21 @@ int bbc_rerank_bounds(bbc_index* ix, const float* queries, int64_t nq, const uin
  * out_meta device f32 [n * 4] = {scale s (1 for BF16), e_v = ||v - s v~||_2
  * rounded up, ||v||_2 rounded up, 0}.  BBC_ERR_ARG without a copy. */
 int bbc_precision_copy(bbc_index* ix, void* out_rows, float* out_meta, void* stream);
+
+/* Bounds of the sign quantizer for every object of the probed lists, in probe
+ * order (list by list, list positions ascending): the debug form of the
+ * bounded scan.  probe_lists device i32 [nq * nprobe]; out_lb / out_ub device
+ * f32 [nq * stride]; out_count device i64 [nq] = objects scanned (entries
+ * past stride are dropped and latch a region overrun).  Bounds enclose
+ * ||q - o||^2 (with "bound_scale" 1). */
+int bbc_sign_bounds(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
+                    const int32_t* probe_lists, int64_t stride, float* out_lb, float* out_ub,
+                    int64_t* out_count, void* stream);
+
+/* Running totals of the bounded re-rank since the last reset (synchronises
+ * the device): out4[0] objects scanned, [1] objects in S = {lb <= U_k},
+ * [2] exact distances computed (both rounds), [3] queries. */
+int bbc_bounded_stats(bbc_index* ix, int64_t* out4, int reset);
 
 /* Running totals of the precision re-rank since the last reset (synchronises
  * the device): out4[0] candidates scored from the copy, [1] candidates

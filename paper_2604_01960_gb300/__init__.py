@@ -27,9 +27,9 @@ ERRORS = {-1: "BBC_ERR_ARG", -2: "BBC_ERR_IO", -3: "BBC_ERR_FORMAT", -4: "BBC_ER
 METRICS = {"l2": 0, "ip": 1}
 
 # Exported symbols declared in include/bbc.h (checked by the ABI test).
-SYMBOLS = ["bbc_index_create", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
+SYMBOLS = ["bbc_index_create", "bbc_index_create_sign", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
            "bbc_get_param", "bbc_search", "bbc_search_ex", "bbc_search_host", "bbc_probe_scores", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
-           "bbc_rerank_topk", "bbc_rerank_bounds", "bbc_precision_copy", "bbc_precision_stats", "bbc_autotune", "bbc_serve_start", "bbc_serve_submit", "bbc_serve_poll",
+           "bbc_rerank_topk", "bbc_rerank_bounds", "bbc_precision_copy", "bbc_precision_stats", "bbc_sign_bounds", "bbc_bounded_stats", "bbc_autotune", "bbc_serve_start", "bbc_serve_submit", "bbc_serve_poll",
            "bbc_serve_stats", "bbc_serve_stop", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
 NUM_STAGES = 9
 STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk", "prec_classify",
@@ -52,7 +52,14 @@ class IndexHost(C.Structure):
 class IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("nlist", C.c_int32), ("metric", C.c_int32),
                 ("pq_m", C.c_int32), ("pq_bits", C.c_int32), ("max_list_len", C.c_int32),
-                ("vectors_u8_exact", C.c_int32), ("device", C.c_int32), ("device_bytes", C.c_int64)]
+                ("vectors_u8_exact", C.c_int32), ("device", C.c_int32), ("device_bytes", C.c_int64),
+                ("quantizer", C.c_int32), ("reserved", C.c_int32)]
+
+
+class SignHost(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("nlist", C.c_int32), ("metric", C.c_int32),
+                ("centroids", C.c_void_p), ("list_offsets", C.c_void_p), ("ids", C.c_void_p),
+                ("rotation", C.c_void_p), ("vectors", C.c_void_p)]
 
 
 class ServeConfig(C.Structure):
@@ -101,6 +108,9 @@ def lib():
             L.bbc_version.restype = C.c_char_p
             L.bbc_index_create.argtypes = [C.POINTER(IndexHost), C.c_int, C.POINTER(vp)]
             L.bbc_index_load.argtypes = [C.c_char_p, C.c_int, C.POINTER(vp)]
+            L.bbc_index_create_sign.argtypes = [C.POINTER(SignHost), C.c_int, C.POINTER(vp)]
+            L.bbc_sign_bounds.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp, vp, vp]
+            L.bbc_bounded_stats.argtypes = [vp, vp, C.c_int]
             L.bbc_index_free.argtypes = [vp]
             L.bbc_index_info.argtypes = [vp, C.POINTER(IndexInfo)]
             L.bbc_set_param.argtypes = [vp, C.c_char_p, C.c_double]
@@ -159,7 +169,10 @@ def _stream(stream) -> int | None:
 # C-ABI wrappers with the C names
 # ---------------------------------------------------------------------------
 def bbc_index_create(index, device: int = 0) -> int:
-    """Create a device index from a host IVF-PQ index object (numpy arrays)."""
+    """Create a device index from a host IVF-PQ index object (numpy arrays),
+    or from an IVF sign-quantizer index (one with a ``rotation``)."""
+    if hasattr(index, "rotation"):
+        return bbc_index_create_sign(index, device)
     keep = []
 
     def arr(a, dt):
@@ -173,6 +186,23 @@ def bbc_index_create(index, device: int = 0) -> int:
                   arr(index.vectors, np.float32))
     out = C.c_void_p()
     _check(lib().bbc_index_create(C.byref(h), device, C.byref(out)))
+    return out.value
+
+
+def bbc_index_create_sign(index, device: int = 0) -> int:
+    """Create a device index with 1-bit sign codes from IVF lists and a rotation."""
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    h = SignHost(int(index.n), int(index.d), int(index.nlist), METRICS[index.metric],
+                 arr(index.centroids, np.float32), arr(index.list_offsets, np.int64), arr(index.ids, np.int64),
+                 arr(index.rotation, np.float32), arr(index.vectors, np.float32))
+    out = C.c_void_p()
+    _check(lib().bbc_index_create_sign(C.byref(h), device, C.byref(out)))
     return out.value
 
 
@@ -268,6 +298,20 @@ def bbc_precision_stats(handle: int, reset: bool = True) -> dict:
     t = (C.c_int64 * 4)()
     _check(lib().bbc_precision_stats(handle, t, 1 if reset else 0))
     return {"scored": t[0], "fp32_rechecked": t[1], "fp64_scored": t[2], "final": t[3]}
+
+
+def bbc_sign_bounds(handle: int, queries, nq: int, nprobe: int, probe_lists, stride: int, out_lb, out_ub,
+                    out_count, stream=None) -> None:
+    """Bounds of every object of the probed lists (sign-code index), probe order."""
+    _check(lib().bbc_sign_bounds(handle, _ptr(queries), nq, nprobe, _ptr(probe_lists), stride, _ptr(out_lb),
+                                 _ptr(out_ub), _ptr(out_count), _stream(stream)))
+
+
+def bbc_bounded_stats(handle: int, reset: bool = True) -> dict:
+    """Totals of the bounded re-rank since the last reset."""
+    t = (C.c_int64 * 4)()
+    _check(lib().bbc_bounded_stats(handle, t, 1 if reset else 0))
+    return {"scanned": t[0], "in_S": t[1], "exact": t[2], "queries": t[3]}
 
 
 def bbc_profile_read(handle: int, reset: bool = True):

@@ -101,6 +101,8 @@ struct bbc_index {
     void* lp_rows = nullptr;               // low-precision copy (precision re-rank)
     float4* lp_meta = nullptr;
     unsigned long long* prec_totals = nullptr;   // [4] device counters of the precision re-rank
+    unsigned long long* sign_totals = nullptr;   // [4] device counters of the bounded re-rank
+    float bound_scale = 1.f;                     // sign codes: factor on the residual term
     int split = 0;            // 0 automatic, 1 one CTA per query, G >= 2 CTAs per query
     int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
     bool capturing = false;
@@ -138,6 +140,7 @@ struct bbc_index {
         cudaFree(lp_rows);
         cudaFree(lp_meta);
         cudaFree(prec_totals);
+        cudaFree(sign_totals);
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
@@ -214,6 +217,20 @@ PrecArgs prec_args(const bbc_index* ix, char* base, int64_t nq, int64_t slots) {
     a.item_off = a.n_unc + nq;
     a.qnorm = reinterpret_cast<float*>(a.item_off + nq + 1);
     a.totals = ix->prec_totals;
+    return a;
+}
+// The precision path: the recheck reads the uncertain list and writes over the
+// dead pass-1 scores, which the finalize then reads.
+PrecArgs prec_args_rerank(const bbc_index* ix, char* base, int64_t nq, int64_t slots, float* cdist) {
+    PrecArgs a = prec_args(ix, base, nq, slots);
+    a.unc_d = cdist;
+    a.unc_r = a.rho;
+    a.copy_unc = 0;
+    a.rc_ids = a.unc;
+    a.rc_from = nullptr;
+    a.rc_count = a.n_unc;
+    a.rc_d = cdist;
+    a.rc_r = a.rho;
     return a;
 }
 
@@ -398,10 +415,155 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
     if (prec_active(ix)) {
         // slots of this chunk: sum of K_c (the per-query offsets index into them)
         const int64_t slots = qp.cand_off ? p.chunk_slots : nc * p.kc;
-        const PrecArgs pa = prec_args(ix, ws + p.off_prec, nc, slots);
+        const PrecArgs pa = prec_args_rerank(ix, ws + p.off_prec, nc, slots, cdist);
         return run_rerank(ix, nc, ra, &pa, p.k, st);
     }
     return run_rerank(ix, nc, ra, nullptr, p.k, st);
+}
+
+// ---------------------------------------------------------------------------
+// Bounded re-rank on a sign-code index (S9b): probe, rotate, scan with the
+// result buffer on the upper bound, two re-rank rounds, exact final order.
+// ---------------------------------------------------------------------------
+struct SignPlan {
+    int64_t chunk, cap;
+    size_t off_scores, off_abf, off_probe, off_qrot, off_region, off_small, off_clist, off_rkey, off_rid, off_cd,
+        off_cr, off_ud, off_ur, off_keys, off_prec, off_q, off_ids, off_dists, total;
+};
+
+size_t sign_layout(const bbc_index* ix, int64_t nc, int nprobe, int k, bool host_io, SignPlan& p) {
+    const DevIndex& d = ix->dev;
+    const int64_t cap = ix->cap_prefix[nprobe];
+    const size_t slots = (size_t)nc * (size_t)cap;
+    size_t o = 0;
+    p.cap = cap;
+    p.off_scores = o; o = align_up(o + (size_t)nc * d.nlist * 4);
+    p.off_abf = o; o = align_up(o + (ix->probe_gemm ? probe_tc_workspace(d, nc) : 0));
+    p.off_probe = o; o = align_up(o + (size_t)nc * nprobe * 4);
+    p.off_qrot = o; o = align_up(o + (size_t)nc * d.d * 8);
+    p.off_region = o; o = align_up(o + slots * 16);
+    p.off_small = o; o = align_up(o + (size_t)nc * 8 * 5);         // pushed, scanned, n_b, n_c, n_rest
+    p.off_clist = o; o = align_up(o + slots * 4);
+    p.off_rkey = o; o = align_up(o + slots * 4);
+    p.off_rid = o; o = align_up(o + slots * 4);
+    p.off_cd = o; o = align_up(o + slots * 4);
+    p.off_cr = o; o = align_up(o + slots * 4);
+    p.off_ud = o; o = align_up(o + slots * 4);
+    p.off_ur = o; o = align_up(o + slots * 4);
+    p.off_keys = o; o = align_up(o + (k > kTopkSmemMax ? slots * 8 : 0));
+    p.off_prec = o; o = align_up(o + prec_bytes(nc, (int64_t)slots));
+    p.off_q = o; o = align_up(o + (host_io ? (size_t)nc * d.d * 4 : 0));
+    p.off_ids = o; o = align_up(o + (host_io ? (size_t)nc * k * 8 : 0));
+    p.off_dists = o; o = align_up(o + (host_io ? (size_t)nc * k * 4 : 0));
+    p.total = o;
+    return o;
+}
+
+SignPlan make_sign_plan(const bbc_index* ix, int64_t nq, int nprobe, int k, bool host_io) {
+    SignPlan p{};
+    const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
+    int64_t c = std::max<int64_t>(1, nq);
+    while (c > 1 && sign_layout(ix, c, nprobe, k, host_io, p) > budget) c = (c + 1) / 2;
+    sign_layout(ix, c, nprobe, k, host_io, p);
+    p.chunk = c;
+    return p;
+}
+
+int run_sign_chunk(bbc_index* ix, const SignPlan& p, char* ws, const float* q, int64_t nc, int nprobe, int k,
+                   int64_t* out_ids, float* out_dists, cudaStream_t st) {
+    const DevIndex& d = ix->dev;
+    const int64_t cap = p.cap;
+    QueryParams qp = uniform_params(nprobe, cap, k, cap);
+    float* scores = reinterpret_cast<float*>(ws + p.off_scores);
+    int32_t* probe = reinterpret_cast<int32_t*>(ws + p.off_probe);
+    double* qrot = reinterpret_cast<double*>(ws + p.off_qrot);
+    int64_t* small = reinterpret_cast<int64_t*>(ws + p.off_small);
+    int64_t *pushed = small, *scanned = small + nc, *n_b = small + 2 * nc, *n_c = small + 3 * nc,
+            *n_rest = small + 4 * nc;
+    uint32_t* clist = reinterpret_cast<uint32_t*>(ws + p.off_clist);
+    float* cd = reinterpret_cast<float*>(ws + p.off_cd);
+    float* cr = reinterpret_cast<float*>(ws + p.off_cr);
+    if (ix->probe_gemm)
+        CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores_tc(d, q, nc, scores, ws + p.off_abf, st); }));
+    else
+        CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores(d, q, nc, scores, st); }));
+    CUDA_TRY(stage(ix, 1, st, [&] { return launch_probe_select(d, q, nc, qp, nprobe, scores, probe, ix->probe_gemm, st); }));
+    CUDA_TRY(stage(ix, 2, st, [&] { return launch_rotate_f64(q, nullptr, nullptr, nullptr, d.rot, nc, d.d, qrot, st); }));
+    SignArgs sa{};
+    sa.qrot = qrot; sa.q = q; sa.lists = probe; sa.nprobe = nprobe; sa.k = k; sa.m = ix->buckets;
+    sa.sample_min = ix->sample_lists; sa.scale = ix->bound_scale;
+    sa.region = reinterpret_cast<uint4*>(ws + p.off_region); sa.cap = cap; sa.pushed = pushed; sa.scanned = scanned;
+    sa.qp = qp;
+    CUDA_TRY(stage(ix, 3, st, [&] { return launch_sign_scan(d, nc, sa, st); }));
+    SignSelectArgs ss{};
+    ss.region = sa.region; ss.pushed = pushed; ss.scanned = scanned; ss.clist = clist; ss.n_b = n_b; ss.n_c = n_c;
+    ss.rest_key = reinterpret_cast<uint32_t*>(ws + p.off_rkey); ss.rest_id = reinterpret_cast<uint32_t*>(ws + p.off_rid);
+    ss.n_rest = n_rest; ss.cd = cd; ss.cr = cr; ss.totals = ix->sign_totals; ss.qp = qp;
+    CUDA_TRY(stage(ix, 4, st, [&] { return launch_sign_select(d, nc, ss, st); }));
+    PrecArgs pa = prec_args(ix, ws + p.off_prec, nc, nc * cap);
+    pa.rho = cr;
+    pa.unc_d = reinterpret_cast<float*>(ws + p.off_ud);
+    pa.unc_r = reinterpret_cast<float*>(ws + p.off_ur);
+    pa.copy_unc = 1;
+    pa.rc_ids = clist;
+    pa.rc_d = cd;
+    pa.rc_r = cr;
+    CUDA_TRY(cudaMemsetAsync(pa.qnorm, 0, (size_t)nc * sizeof(float), st));
+    unsigned long long* keys = k > kTopkSmemMax ? reinterpret_cast<unsigned long long*>(ws + p.off_keys) : nullptr;
+    RerankArgs ra{q, clist, n_c, cap, 0, cd, k, out_ids, out_dists, keys, qp};
+    // round 1: the k smallest upper bounds
+    pa.rc_from = nullptr;
+    pa.rc_count = n_b;
+    CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_plan(nc, pa, st); }));
+    CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_recheck(d, nc, ra, pa, st); }));
+    // round 2: the rest of S whose lower bound reaches the largest upper bound of round 1
+    CUDA_TRY(stage(ix, 4, st, [&] { return launch_sign_filter(d, nc, ss, st); }));
+    pa.rc_from = n_b;
+    pa.rc_count = n_c;
+    CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_plan(nc, pa, st); }));
+    CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_recheck(d, nc, ra, pa, st); }));
+    // exact order: FP32 with its bound, FP64 where the bound cannot decide
+    CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_classify(d, nc, ra, pa, st); }));
+    CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_finalize(d, nc, ra, pa, st); }));
+    RerankArgs rb = ra;
+    rb.cand = pa.fin_id;
+    rb.cdist = pa.fin_d;
+    rb.cand_count = pa.n_fin;
+    rb.kc = k;
+    CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(d, nc, rb, st); }));
+    return BBC_OK;
+}
+
+int search_sign(bbc_index* ix, const float* queries, int64_t nq, int k, int nprobe, int64_t* out_ids,
+                float* out_dists, cudaStream_t st, bool host_io) {
+    SignPlan p = make_sign_plan(ix, nq, nprobe, k, host_io);
+    char* ws;
+    int rc = get_workspace(ix, st, p.total, &ws);
+    if (rc) return rc;
+    const int d = ix->dev.d;
+    for (int64_t q0 = 0; q0 < nq; q0 += p.chunk) {
+        const int64_t nc = std::min(p.chunk, nq - q0);
+        if (host_io) {
+            float* dq = reinterpret_cast<float*>(ws + p.off_q);
+            int64_t* di = reinterpret_cast<int64_t*>(ws + p.off_ids);
+            float* dd = reinterpret_cast<float*>(ws + p.off_dists);
+            CUDA_TRY(cudaMemcpyAsync(dq, queries + q0 * d, (size_t)nc * d * 4, cudaMemcpyHostToDevice, st));
+            if ((rc = run_sign_chunk(ix, p, ws, dq, nc, nprobe, k, di, dd, st))) return rc;
+            CUDA_TRY(cudaMemcpyAsync(out_ids + q0 * k, di, (size_t)nc * k * 8, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(out_dists + q0 * k, dd, (size_t)nc * k * 4, cudaMemcpyDeviceToHost, st));
+        } else {
+            if ((rc = run_sign_chunk(ix, p, ws, queries + q0 * d, nc, nprobe, k, out_ids + q0 * k,
+                                     out_dists + q0 * k, st)))
+                return rc;
+        }
+    }
+    if (host_io) CUDA_TRY(cudaStreamSynchronize(st));
+    return BBC_OK;
+}
+
+int pq_only(const bbc_index* ix, const char* what) {
+    if (ix && ix->dev.quant != 0) return fail(BBC_ERR_UNSUPPORTED, "%s: not available on a sign-code index", what);
+    return BBC_OK;
 }
 
 // (Re)builds the low-precision copy for the precision re-rank; 0 drops it.
@@ -613,6 +775,188 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out) {
     bbc_index_info_t& I = ix->info;
     I.n = n; I.d = d; I.nlist = L; I.metric = h->metric; I.pq_m = M; I.pq_bits = bits;
     I.max_list_len = maxlen; I.vectors_u8_exact = u8 ? 1 : 0; I.device = device;
+    I.quantizer = BBC_QUANT_PQ;
+    *out = ix.release();
+    return BBC_OK;
+}
+
+int bbc_index_create_sign(const bbc_sign_host* h, int device, bbc_index** out) {
+    if (!h || !out) return fail(BBC_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (h->n < 1 || h->n >= (int64_t)0xFFFFFFFFll) return fail(BBC_ERR_ARG, "n=%lld outside [1, 2^32-1)", (long long)h->n);
+    if (h->metric != BBC_METRIC_L2) return fail(BBC_ERR_UNSUPPORTED, "sign codes: only the L2 metric is supported");
+    if (h->d < 32 || h->d % 32 || h->d > 2048) return fail(BBC_ERR_UNSUPPORTED, "sign codes: d=%d must be a multiple of 32 in [32, 2048]", h->d);
+    if (h->nlist < 1) return fail(BBC_ERR_ARG, "nlist must be >= 1");
+    if (!h->centroids || !h->list_offsets || !h->ids || !h->rotation || !h->vectors) return fail(BBC_ERR_ARG, "null array");
+    const int64_t n = h->n;
+    const int L = h->nlist, d = h->d, W = d / 32;
+    if (h->list_offsets[0] != 0 || h->list_offsets[L] != n) return fail(BBC_ERR_FORMAT, "list_offsets must run from 0 to n");
+    int32_t maxlen = 0;
+    for (int l = 0; l < L; ++l) {
+        const int64_t len = h->list_offsets[l + 1] - h->list_offsets[l];
+        if (len < 0 || len > (1ll << 30)) return fail(BBC_ERR_FORMAT, "list %d has bad length %lld", l, (long long)len);
+        maxlen = std::max<int32_t>(maxlen, (int32_t)len);
+    }
+    {
+        std::vector<uint8_t> seen((size_t)n, 0);
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t id = h->ids[i];
+            if (id < 0 || id >= n || seen[(size_t)id]) return fail(BBC_ERR_FORMAT, "ids are not a permutation of [0, n)");
+            seen[(size_t)id] = 1;
+        }
+    }
+    DeviceGuard g(device);
+    if (!g.ok) return fail(BBC_ERR_ARG, "cannot select device %d", device);
+    std::unique_ptr<bbc_index> ix(new bbc_index());
+    ix->device = device;
+    DevIndex& D = ix->dev;
+    D.d = d; D.nlist = L; D.metric = BBC_METRIC_L2; D.M = 0; D.bits = 0; D.K = 0; D.dsub = 0;
+    D.n = n; D.dpad = (d + 15) / 16 * 16; D.quant = BBC_QUANT_SIGN;
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 1;
+        D.num_sms = sms;
+    }
+    // 32-slot block layout shared with the PQ codes
+    std::vector<int32_t> list_blk(L), list_len(L);
+    int64_t nblocks = 0;
+    for (int l = 0; l < L; ++l) {
+        list_len[l] = (int32_t)(h->list_offsets[l + 1] - h->list_offsets[l]);
+        list_blk[l] = (int32_t)nblocks;
+        nblocks += (list_len[l] + 31) / 32;
+    }
+    if (nblocks >= (1ll << 31) / 32) return fail(BBC_ERR_UNSUPPORTED, "too many blocks");
+    const int64_t nslots = nblocks * 32;
+    std::vector<uint32_t> ids((size_t)nslots, kPadId);
+    std::vector<int64_t> rows((size_t)nslots, -1);
+    std::vector<int32_t> slot_list((size_t)nslots, 0);
+    for (int l = 0; l < L; ++l) {
+        for (int32_t p = 0; p < list_len[l]; ++p) {
+            const int64_t slot = (int64_t)list_blk[l] * 32 + p;
+            const int64_t id = h->ids[h->list_offsets[l] + p];
+            ids[(size_t)slot] = (uint32_t)id;
+            rows[(size_t)slot] = id;
+            slot_list[(size_t)slot] = l;
+        }
+    }
+    std::vector<float> cnorm(L);
+    double cmax = 0.0;
+    for (int l = 0; l < L; ++l) {
+        double s2 = 0.0;
+        for (int i = 0; i < d; ++i) s2 += (double)h->centroids[(size_t)l * d + i] * h->centroids[(size_t)l * d + i];
+        cnorm[l] = (float)s2;
+        cmax = std::max(cmax, std::sqrt(s2));
+    }
+    D.cmax = (float)(cmax * (1.0 + 1e-6));
+    int rc;
+    float *dc, *dcn, *dvec, *drot;
+    int32_t *dlb, *dll, *dsl;
+    uint32_t* did;
+    int64_t* drows;
+    unsigned int* dstat;
+    if ((rc = upload(ix.get(), h->centroids, (size_t)L * d, &dc))) return rc;
+    if ((rc = upload(ix.get(), cnorm.data(), (size_t)L, &dcn))) return rc;
+    if ((rc = upload(ix.get(), list_blk.data(), (size_t)L, &dlb))) return rc;
+    if ((rc = upload(ix.get(), list_len.data(), (size_t)L, &dll))) return rc;
+    if ((rc = upload(ix.get(), ids.data(), ids.size(), &did))) return rc;
+    if ((rc = upload(ix.get(), h->vectors, (size_t)n * d, &dvec))) return rc;
+    if ((rc = upload(ix.get(), h->rotation, (size_t)d * d, &drot))) return rc;
+    unsigned int zero = 0;
+    if ((rc = upload(ix.get(), &zero, 1, &dstat))) return rc;
+    D.kp = (3 * d + 63) / 64 * 64;
+    {
+        std::vector<uint16_t> b3((size_t)L * D.kp, 0);
+        for (int l = 0; l < L; ++l) {
+            uint16_t* r = b3.data() + (size_t)l * D.kp;
+            for (int i = 0; i < d; ++i) {
+                const float x = h->centroids[(size_t)l * d + i];
+                const uint16_t hi = f32_to_bf16(x);
+                r[i] = hi;
+                r[d + i] = f32_to_bf16(x - bf16_to_f32(hi));
+                r[2 * d + i] = hi;
+            }
+        }
+        uint16_t* db3;
+        if ((rc = upload(ix.get(), b3.data(), b3.size(), &db3))) return rc;
+        D.cent_b3 = db3;
+    }
+    D.centroids = dc; D.cnorm = dcn; D.list_blk = dlb; D.list_len = dll; D.ids = did; D.vectors = dvec;
+    D.status = dstat; D.rot = drot; D.codes = nullptr; D.books = nullptr; D.vec_u8 = nullptr;
+    // P c_l (FP64) and ||P P^T - I||_F (equal to ||P^T P - I||_F for a square P)
+    double* dcrot;
+    {
+        void* t = nullptr;
+        if (cudaMalloc(&t, (size_t)L * d * 8) != cudaSuccess) return fail(BBC_ERR_OOM, "cudaMalloc for P c_l");
+        ix->owned.push_back(t);
+        ix->info.device_bytes += (int64_t)L * d * 8;
+        dcrot = static_cast<double*>(t);
+    }
+    CUDA_TRY(launch_rotate_f64(dc, nullptr, nullptr, nullptr, drot, L, d, dcrot, nullptr));
+    {
+        double* dpp = nullptr;
+        if (cudaMalloc(&dpp, (size_t)d * d * 8) != cudaSuccess) return fail(BBC_ERR_OOM, "cudaMalloc for P P^T");
+        cudaError_t e = launch_rotate_f64(drot, nullptr, nullptr, nullptr, drot, d, d, dpp, nullptr);
+        std::vector<double> pp((size_t)d * d);
+        if (e == cudaSuccess) e = cudaMemcpy(pp.data(), dpp, pp.size() * 8, cudaMemcpyDeviceToHost);
+        cudaFree(dpp);
+        if (e != cudaSuccess) return fail(BBC_ERR_CUDA, "P P^T: %s", cudaGetErrorString(e));
+        double f = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                const double v = pp[(size_t)i * d + j] - (i == j ? 1.0 : 0.0);
+                f += v * v;
+            }
+        D.eps_p = std::sqrt(f) * (1.0 + 1e-6) + 1e-15;
+    }
+    // codes and factors, a chunk of slots at a time through the FP64 rotation
+    uint32_t* dsgn;
+    float4* dfac;
+    {
+        void* t = nullptr;
+        if (cudaMalloc(&t, (size_t)nslots * W * 4) != cudaSuccess) return fail(BBC_ERR_OOM, "cudaMalloc for sign codes");
+        ix->owned.push_back(t);
+        dsgn = static_cast<uint32_t*>(t);
+        if (cudaMalloc(&t, (size_t)nslots * 16) != cudaSuccess) return fail(BBC_ERR_OOM, "cudaMalloc for factors");
+        ix->owned.push_back(t);
+        dfac = static_cast<float4*>(t);
+        ix->info.device_bytes += (int64_t)nslots * (W * 4 + 16);
+    }
+    {
+        void *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;
+        const int64_t chunk = 65536;
+        if (cudaMalloc(&t1, (size_t)nslots * 8) != cudaSuccess || cudaMalloc(&t2, (size_t)nslots * 4) != cudaSuccess ||
+            cudaMalloc(&t3, (size_t)chunk * d * 8) != cudaSuccess) {
+            cudaFree(t1); cudaFree(t2); cudaFree(t3);
+            return fail(BBC_ERR_OOM, "cudaMalloc for the sign encoding scratch");
+        }
+        drows = static_cast<int64_t*>(t1);
+        dsl = static_cast<int32_t*>(t2);
+        double* R = static_cast<double*>(t3);
+        cudaError_t e = cudaMemcpy(drows, rows.data(), (size_t)nslots * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dsl, slot_list.data(), (size_t)nslots * 4, cudaMemcpyHostToDevice);
+        for (int64_t s0 = 0; e == cudaSuccess && s0 < nslots; s0 += chunk) {
+            const int64_t m = std::min(chunk, nslots - s0);
+            e = launch_rotate_f64(dvec, drows + s0, dsl + s0, dc, drot, m, d, R, nullptr);
+            if (e == cudaSuccess) e = launch_sign_factors(R, s0, m, d, drows, dsl, dvec, dc, dsgn, dfac, nullptr);
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(t1); cudaFree(t2); cudaFree(t3);
+        if (e != cudaSuccess) return fail(BBC_ERR_CUDA, "sign encoding: %s", cudaGetErrorString(e));
+    }
+    D.sgn = dsgn; D.sfac = dfac; D.crot = dcrot;
+    for (unsigned long long** tp : {&ix->prec_totals, &ix->sign_totals}) {
+        void* t = nullptr;
+        if (cudaMalloc(&t, 32) != cudaSuccess) return fail(BBC_ERR_OOM, "cudaMalloc(32)");
+        *tp = static_cast<unsigned long long*>(t);
+        CUDA_TRY(cudaMemset(t, 0, 32));
+    }
+    std::vector<int64_t> lens(list_len.begin(), list_len.end());
+    std::sort(lens.begin(), lens.end(), std::greater<int64_t>());
+    ix->cap_prefix.assign(L + 1, 0);
+    for (int l = 0; l < L; ++l) ix->cap_prefix[l + 1] = ix->cap_prefix[l] + lens[l];
+    bbc_index_info_t& I = ix->info;
+    I.n = n; I.d = d; I.nlist = L; I.metric = BBC_METRIC_L2; I.pq_m = 0; I.pq_bits = 0;
+    I.max_list_len = maxlen; I.vectors_u8_exact = 0; I.device = device; I.quantizer = BBC_QUANT_SIGN;
     *out = ix.release();
     return BBC_OK;
 }
@@ -696,7 +1040,11 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "probe_gemm") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "probe_gemm must be 0 (FP32 SIMT) or 1 (tensor cores)");
         ix->probe_gemm = (int)v;
+    } else if (k == "bound_scale") {
+        if (!(v > 0.0 && v <= 1.0)) return fail(BBC_ERR_ARG, "bound_scale must be in (0, 1]");
+        ix->bound_scale = (float)v;
     } else if (k == "precision") {
+        if (int rc0 = pq_only(ix, "precision")) return rc0;
         if (v != 0 && v != 1 && v != 2)
             return fail(BBC_ERR_ARG, "precision must be 0 (FP32 re-rank), 1 (BF16 copy) or 2 (FP8-E4M3 copy)");
         return build_precision(ix, (int)v);
@@ -722,6 +1070,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "split") *v = ix->split;
     else if (k == "graphs") *v = ix->graphs;
     else if (k == "precision") *v = ix->dev.prec;
+    else if (k == "bound_scale") *v = ix->bound_scale;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -735,6 +1084,7 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     if (nq == 0) return BBC_OK;
     DeviceGuard g(ix->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (ix->dev.quant == BBC_QUANT_SIGN) return search_sign(ix, queries, nq, k, nprobe, out_ids, out_dists, st, false);
     Plan p = make_plan(ix, nq, nprobe, kc, k, false);
     char* ws;
     if ((rc = get_workspace(ix, st, p.total, &ws))) return rc;
@@ -790,6 +1140,7 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
 int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t* k, const int32_t* nprobe,
                   int64_t* out_ids, float* out_dists, void* stream) {
     if (!ix) return fail(BBC_ERR_ARG, "null index");
+    if (int rc0 = pq_only(ix, "bbc_search_ex")) return rc0;
     if (nq < 0) return fail(BBC_ERR_ARG, "nq < 0");
     if (nq == 0) return BBC_OK;
     if (!queries || !k || !nprobe || !out_ids || !out_dists) return fail(BBC_ERR_ARG, "null buffer");
@@ -882,6 +1233,7 @@ int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, 
     if (nq == 0) return BBC_OK;
     DeviceGuard g(ix->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (ix->dev.quant == BBC_QUANT_SIGN) return search_sign(ix, queries, nq, k, nprobe, out_ids, out_dists, st, true);
     Plan p = make_plan(ix, nq, nprobe, kc, k, true);
     char* ws;
     if ((rc = get_workspace(ix, st, p.total, &ws))) return rc;
@@ -921,6 +1273,7 @@ int bbc_probe(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe, i
 
 int bbc_autotune(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe,
                  const char* cache_path, double* out_ms, void* stream) {
+    if (int rc0 = pq_only(ix, "bbc_autotune")) return rc0;
     int rc = check_search_args(ix, queries, nq, k, nprobe, queries, queries);
     if (rc) return rc;
     if (nq < 1) return fail(BBC_ERR_ARG, "autotune needs at least one query");
@@ -1052,6 +1405,7 @@ int bbc_probe_scores(bbc_index* ix, const float* queries, int64_t nq, float* out
 }
 
 int bbc_lut(bbc_index* ix, const float* queries, int64_t nq, uint16_t* out_lut16, void* stream) {
+    if (int rc0 = pq_only(ix, "bbc_lut")) return rc0;
     if (!ix) return fail(BBC_ERR_ARG, "null index");
     if (nq < 0 || (nq > 0 && (!queries || !out_lut16))) return fail(BBC_ERR_ARG, "bad buffers");
     if (nq == 0) return BBC_OK;
@@ -1063,6 +1417,7 @@ int bbc_lut(bbc_index* ix, const float* queries, int64_t nq, uint16_t* out_lut16
 
 int bbc_collect(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe, const int32_t* probe_lists,
                 int64_t kc, uint32_t* out_ids, int64_t* out_count, bbc_collector_state* out_state, void* stream) {
+    if (int rc0 = pq_only(ix, "bbc_collect")) return rc0;
     int rc = check_search_args(ix, queries, nq, 1, nprobe, out_ids, out_count);
     if (rc) return rc;
     if (nq > 0 && !probe_lists) return fail(BBC_ERR_ARG, "null probe_lists");
@@ -1087,6 +1442,7 @@ int bbc_collect(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
 int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint32_t* cand_ids,
                     const int64_t* cand_count, int64_t kc, int32_t k, int64_t* out_ids, float* out_dists,
                     void* stream) {
+    if (int rc0 = pq_only(ix, "bbc_rerank_topk")) return rc0;
     if (!ix) return fail(BBC_ERR_ARG, "null index");
     if (nq < 0 || k < 1 || kc < 1) return fail(BBC_ERR_ARG, "bad sizes");
     if (kc > (int64_t)0x7FFFFFFF) return fail(BBC_ERR_ARG, "kc too large");
@@ -1119,7 +1475,7 @@ int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint3
                       ix->rerank_u8 && ix->dev.vec_u8 != nullptr, reinterpret_cast<float*>(ws), k,
                       out_ids + q0 * k, out_dists + q0 * k, keys, uniform_params(1, kc, k, 0)};
         if (prec) {
-            const PrecArgs pa = prec_args(ix, ws + o, nc, nc * kc);
+            const PrecArgs pa = prec_args_rerank(ix, ws + o, nc, nc * kc, reinterpret_cast<float*>(ws));
             rc = run_rerank(ix, nc, ra, &pa, k, st);
         } else {
             rc = run_rerank(ix, nc, ra, nullptr, k, st);
@@ -1131,6 +1487,7 @@ int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint3
 
 int bbc_rerank_bounds(bbc_index* ix, const float* queries, int64_t nq, const uint32_t* cand_ids,
                       const int64_t* cand_count, int64_t kc, float* out_dist, float* out_rho, void* stream) {
+    if (int rc0 = pq_only(ix, "bbc_rerank_bounds")) return rc0;
     if (!ix) return fail(BBC_ERR_ARG, "null index");
     if (nq < 0 || kc < 1 || kc > (int64_t)0x7FFFFFFF) return fail(BBC_ERR_ARG, "bad sizes");
     if (nq > 0 && (!queries || !cand_ids || !cand_count || !out_dist || !out_rho)) return fail(BBC_ERR_ARG, "null buffer");
@@ -1168,6 +1525,43 @@ int bbc_precision_stats(bbc_index* ix, int64_t* out4, int reset) {
     CUDA_TRY(cudaMemcpy(t, ix->prec_totals, sizeof(t), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 4; ++i) out4[i] = (int64_t)t[i];
     if (reset) CUDA_TRY(cudaMemset(ix->prec_totals, 0, sizeof(t)));
+    return BBC_OK;
+}
+
+int bbc_sign_bounds(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe, const int32_t* probe_lists,
+                    int64_t stride, float* out_lb, float* out_ub, int64_t* out_count, void* stream) {
+    int rc = check_search_args(ix, queries, nq, 1, nprobe, out_lb, out_ub);
+    if (rc) return rc;
+    if (ix->dev.quant != BBC_QUANT_SIGN) return fail(BBC_ERR_UNSUPPORTED, "bbc_sign_bounds: not a sign-code index");
+    if (nq > 0 && (!probe_lists || !out_count)) return fail(BBC_ERR_ARG, "null buffer");
+    if (stride < 1) return fail(BBC_ERR_ARG, "stride must be >= 1");
+    if (nq == 0) return BBC_OK;
+    DeviceGuard g(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevIndex& d = ix->dev;
+    char* ws;
+    if ((rc = get_workspace(ix, st, align_up((size_t)nq * d.d * 8), &ws))) return rc;
+    double* qrot = reinterpret_cast<double*>(ws);
+    CUDA_TRY(stage(ix, 2, st, [&] { return launch_rotate_f64(queries, nullptr, nullptr, nullptr, d.rot, nq, d.d, qrot, st); }));
+    SignArgs sa{};
+    sa.qrot = qrot; sa.q = queries; sa.lists = probe_lists; sa.nprobe = nprobe; sa.k = 1; sa.m = ix->buckets;
+    sa.sample_min = ix->sample_lists; sa.scale = ix->bound_scale; sa.cap = stride; sa.scanned = out_count;
+    sa.dbg_lb = out_lb; sa.dbg_ub = out_ub;
+    sa.qp = uniform_params(nprobe, stride, 1, stride);
+    CUDA_TRY(stage(ix, 3, st, [&] { return launch_sign_scan(d, nq, sa, st); }));
+    return BBC_OK;
+}
+
+int bbc_bounded_stats(bbc_index* ix, int64_t* out4, int reset) {
+    if (!ix || !out4) return fail(BBC_ERR_ARG, "null argument");
+    for (int i = 0; i < 4; ++i) out4[i] = 0;
+    if (!ix->sign_totals) return BBC_OK;
+    DeviceGuard g(ix->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    unsigned long long t[4];
+    CUDA_TRY(cudaMemcpy(t, ix->sign_totals, sizeof(t), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i) out4[i] = (int64_t)t[i];
+    if (reset) CUDA_TRY(cudaMemset(ix->sign_totals, 0, sizeof(t)));
     return BBC_OK;
 }
 

@@ -67,6 +67,13 @@ struct DevIndex {
     const float4* vec_meta;    // per-vector scale / error / norm, or null
     int prec;                  // 0 none, 1 BF16 copy, 2 FP8-E4M3 copy
     int dpad;                  // row length of the low-precision copy
+    // 1-bit sign quantizer (quant = 1); codes and ids share the block layout of the PQ codes
+    int quant;                 // 0 PQ, 1 sign codes
+    const uint32_t* sgn;       // [nblocks][d/32][32] code words, word w of lane t at (b*W + w)*32 + t
+    const float4* sfac;        // [nblocks*32] {alpha, e (rounded up), ||o - c||^2, popcount}
+    const double* crot;        // [nlist][d] P c_l in FP64
+    const float* rot;          // [d][d] rotation P, row-major (r = P u)
+    double eps_p;              // ||P^T P - I||_F
 };
 
 // Words per LUT row in shared memory: lane t at code slot s reads word t + s
@@ -185,6 +192,14 @@ cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cud
 struct PrecArgs {
     float* rho;                   // bound of each score in RerankArgs::cdist
     uint32_t* unc;                // uncertain candidates (ids), compacted
+    float* unc_d;                 // FP32 distance of each uncertain candidate (finalize input)
+    float* unc_r;                 // its FP32 bound
+    int copy_unc;                 // classify copies cdist / rho of the uncertain ones to unc_d / unc_r
+    const uint32_t* rc_ids;       // ids the FP32 recheck scores, per coff
+    const int64_t* rc_from;       // [nq] first position to score (null: 0)
+    const int64_t* rc_count;      // [nq] end position
+    float* rc_d;                  // FP32 distances written by the recheck
+    float* rc_r;                  // and their bounds
     uint32_t* fin_id;             // final members, compacted
     float* fin_d;                 // their reported distances
     uint32_t* band_id;            // members left to FP64
@@ -212,6 +227,55 @@ cudaError_t launch_prec_recheck(const DevIndex& ix, int64_t nq, const RerankArgs
                                 cudaStream_t st);
 cudaError_t launch_prec_finalize(const DevIndex& ix, int64_t nq, const RerankArgs& a, const PrecArgs& p,
                                  cudaStream_t st);
+
+// ---- 1-bit sign quantizer and the bounded re-rank (S9b) ----
+// out[i][r] = sum_j P[r][j] (A[row(i)][j] - sub(i)[j]) in FP64 for rows i < n,
+// row(i) = rows ? rows[i] : i (rows < 0 are skipped), sub(i) = centroid of
+// lists[i] when lists is given.
+cudaError_t launch_rotate_f64(const float* A, const int64_t* rows, const int32_t* lists, const float* centroids,
+                              const float* P, int64_t n, int d, double* out, cudaStream_t st);
+// Codes and factors of slots [s0, s0 + n) from their rotated residuals R (FP64
+// [n][d]); rows / lists: vector id (-1 for padding) and list of every slot.
+cudaError_t launch_sign_factors(const double* R, int64_t s0, int64_t n, int d, const int64_t* rows,
+                                const int32_t* lists, const float* vec, const float* cent, uint32_t* codes,
+                                float4* fac, cudaStream_t st);
+
+struct SignArgs {
+    const double* qrot;           // [nq][d] P q in FP64
+    const float* q;               // [nq][d]
+    const int32_t* lists;         // probe lists, per QueryParams::poff
+    int nprobe;
+    int k;                        // uniform k (per-query values in qp)
+    int m;                        // buckets
+    int sample_min;               // minimum sampled lists
+    float scale;                  // scale of the residual term (1 = hard bounds)
+    uint4* region;                // {lb key, ub key, slot, 0}, per QueryParams::roff
+    int64_t cap;
+    int64_t* pushed;              // [nq]
+    int64_t* scanned;             // [nq]
+    float* dbg_lb;                // bounds of every scanned object (debug form), per roff, or null
+    float* dbg_ub;
+    QueryParams qp;
+};
+cudaError_t launch_sign_scan(const DevIndex& ix, int64_t nq, const SignArgs& a, cudaStream_t st);
+
+struct SignSelectArgs {
+    const uint4* region;
+    const int64_t* pushed;
+    const int64_t* scanned;
+    uint32_t* clist;              // ids to re-rank, per coff (capacity cap)
+    int64_t* n_b;                 // [nq] size of the first round
+    int64_t* n_c;                 // [nq] ids in clist
+    uint32_t* rest_key;           // lb keys of S minus the first round, per coff
+    uint32_t* rest_id;
+    int64_t* n_rest;              // [nq]
+    const float* cd;              // FP32 distances of clist (after the first recheck)
+    const float* cr;              // and bounds
+    unsigned long long* totals;   // [4]
+    QueryParams qp;
+};
+cudaError_t launch_sign_select(const DevIndex& ix, int64_t nq, const SignSelectArgs& a, cudaStream_t st);
+cudaError_t launch_sign_filter(const DevIndex& ix, int64_t nq, const SignSelectArgs& a, cudaStream_t st);
 
 }  // namespace bbc
 

@@ -68,6 +68,7 @@ extern "C" int bbc_collect_static(bbc_index* ix, const float* queries, int64_t n
     using namespace bbc;
     int rc = api_check_search_args(ix, queries, nq, 1, nprobe, out_ids, out_count);
     if (rc) return rc;
+    if (index_dev(ix).quant != 0) return api_error(BBC_ERR_UNSUPPORTED, "bbc_collect_static: not available on a sign-code index");
     if (nq > 0 && !probe_lists) return api_error(BBC_ERR_ARG, "null probe_lists");
     if (kc < 1 || kc > (int64_t)0x7FFFFFFF) return api_error(BBC_ERR_ARG, "kc must be in [1, 2^31)");
     if (nq == 0) return BBC_OK;

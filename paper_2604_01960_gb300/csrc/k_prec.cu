@@ -342,7 +342,10 @@ __global__ void __launch_bounds__(PC_THREADS) prec_classify_kernel(DevIndex ix, 
         const uint32_t si = warp_append(in, &s_in);
         if (in) { p.fin_id[off + si] = id; p.fin_d[off + si] = dist; }
         const uint32_t su = warp_append(unc, &s_unc);
-        if (unc) p.unc[off + su] = id;
+        if (unc) {
+            p.unc[off + su] = id;
+            if (p.copy_unc) { p.unc_d[off + su] = dist; p.unc_r[off + su] = rho[i]; }
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(PC_THREADS) prec_classify_kernel(DevIndex ix, 
     }
 }
 
-// Recheck work items: item_off[q + 1] - item_off[q] = ceil(n_unc[q] / kPrecItem).
+// Recheck work items: item_off[q + 1] - item_off[q] = ceil((rc_count[q] - rc_from[q]) / kPrecItem).
 __global__ void __launch_bounds__(1024) prec_plan_kernel(int64_t nq, PrecArgs p) {
     __shared__ unsigned long long wsum[32];
     __shared__ unsigned long long carry;
@@ -361,7 +364,8 @@ __global__ void __launch_bounds__(1024) prec_plan_kernel(int64_t nq, PrecArgs p)
     __syncthreads();
     for (int64_t base = 0; base < nq; base += blockDim.x) {
         const int64_t q = base + threadIdx.x;
-        const unsigned long long v = q < nq ? (unsigned long long)((p.n_unc[q] + kPrecItem - 1) / kPrecItem) : 0ull;
+        const int64_t span = q < nq ? p.rc_count[q] - (p.rc_from ? p.rc_from[q] : 0) : 0;
+        const unsigned long long v = span > 0 ? (unsigned long long)((span + kPrecItem - 1) / kPrecItem) : 0ull;
         const unsigned long long inc = warp_incl_scan64(v);
         if (lane_id() == 31) wsum[warp_id()] = inc;
         __syncthreads();
@@ -379,9 +383,10 @@ __global__ void __launch_bounds__(1024) prec_plan_kernel(int64_t nq, PrecArgs p)
 }
 
 // ---------------------------------------------------------------------------
-// Pass 3: FP32 recheck of the uncertain candidates.  Persistent CTAs over the
-// (query, item) work list; d32 and rho32 overwrite cdist / rho at the
-// candidate's position in the uncertain list.
+// Pass 3: FP32 recheck.  Persistent CTAs over the (query, item) work list of
+// positions [rc_from, rc_count) of rc_ids; d32 and rho32 go to rc_d / rc_r at
+// the same positions.  (Precision path: the uncertain list, written over the
+// dead pass-1 scores; bounded re-rank: the candidate list of each round.)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PR_THREADS) prec_recheck_kernel(DevIndex ix, int64_t nq, RerankArgs a,
                                                                   PrecArgs p) {
@@ -412,8 +417,9 @@ __global__ void __launch_bounds__(PR_THREADS) prec_recheck_kernel(DevIndex ix, i
         __syncthreads();
         const float qn = p.qnorm[qi];
         const int64_t off = a.qp.coff(qi);
-        const int64_t c0 = (it - p.item_off[qi]) * kPrecItem;
-        const int64_t c1 = min(c0 + kPrecItem, p.n_unc[qi]);
+        const int64_t from = p.rc_from ? p.rc_from[qi] : 0;
+        const int64_t c0 = from + (it - p.item_off[qi]) * kPrecItem;
+        const int64_t c1 = min(c0 + kPrecItem, p.rc_count[qi]);
         const float4* q4 = reinterpret_cast<const float4*>(sq);
         constexpr int PU = 4;
         const int64_t stride = (int64_t)(blockDim.x >> 5) * per_warp * PU;
@@ -424,7 +430,8 @@ __global__ void __launch_bounds__(PR_THREADS) prec_recheck_kernel(DevIndex ix, i
             for (int u = 0; u < PU; ++u) {
                 const int64_t c = cb + (int64_t)u * per_warp + grp;
                 ok[u] = c < c1;
-                id[u] = ok[u] ? p.unc[off + c] : 0u;
+                id[u] = ok[u] ? p.rc_ids[off + c] : 0u;
+                if (ok[u] && (int64_t)id[u] >= ix.n) { ok[u] = false; atomicOr(ix.status, kStatusSelectOverrun); }
             }
             float acc[PU];
 #pragma unroll
@@ -465,8 +472,8 @@ __global__ void __launch_bounds__(PR_THREADS) prec_recheck_kernel(DevIndex ix, i
                         dist = -acc[u];
                         r = g * qn * __ldg(&ix.vec_meta[id[u]].z);
                     }
-                    a.cdist[off + c] = dist;
-                    p.rho[off + c] = r * kEvalSlack + (float)(d + 2) * kTiny * (1.f + qn);
+                    p.rc_d[off + c] = dist;
+                    p.rc_r[off + c] = r * kEvalSlack + (float)(d + 2) * kTiny * (1.f + qn);
                 }
             }
         }
@@ -507,8 +514,8 @@ __global__ void __launch_bounds__(PC_THREADS) prec_finalize_kernel(DevIndex ix, 
     const int64_t nu = p.n_unc[qi];
     const int64_t need = kk - nin;
     const uint32_t* unc = p.unc + off;
-    const float* d32 = a.cdist + off;
-    const float* r32 = p.rho + off;
+    const float* d32 = p.unc_d + off;
+    const float* r32 = p.unc_r + off;
     uint32_t* fid = p.fin_id + off;
     float* fdist = p.fin_d + off;
     if (threadIdx.x == 0) { s_fin = (uint32_t)nin; s_band = 0; s_lt = 0; s_eq = 0; }

@@ -204,6 +204,7 @@ int bbc_serve_start(bbc_index* ix, const bbc_serve_config* cfg, bbc_server** out
     if (!ix || !cfg || !out) return api_error(BBC_ERR_ARG, "null argument");
     if (cfg->max_batch < 1 || cfg->streams < 1 || cfg->streams > 16 || cfg->cand_bytes_budget < 1)
         return api_error(BBC_ERR_ARG, "serve config out of range");
+    if (index_dev(ix).quant != 0) return api_error(BBC_ERR_UNSUPPORTED, "serving: not available on a sign-code index");
     auto* sv = new bbc_server();
     sv->ix = ix;
     sv->cfg = *cfg;

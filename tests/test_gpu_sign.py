@@ -1,0 +1,181 @@
+"""Bounded re-rank with the 1-bit sign quantizer (S9b) vs the CPU oracle.
+
+* Bounds: every object of the probed lists has lb <= ||q - o||^2 (FP64) <= ub,
+  and the GPU's intervals are no wider than the oracle's FP64 ones beyond
+  rounding.
+* Results: with hard bounds the result set is the exact top-k of the probed
+  lists (the oracle's brute force over them), reported distances within the
+  FP32 re-rank tolerance of FP64, sorted.
+* Counts: the set S = {lb <= U_k} the GPU keeps equals the one the oracle's
+  classification derives from the same bounds; exact distances computed lie
+  between the oracle's two-round count on those bounds and |S|.
+"""
+
+import numpy as np
+import pytest
+
+from conftest import scanned_set
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+_IDX = {}
+
+
+@pytest.fixture(scope="module")
+def bbc():
+    import paper_2604_01960_gb300 as bbc
+    bbc.build()
+    assert torch.cuda.is_available(), "CUDA device required"
+    return bbc
+
+
+def sign_index(bbc, kind="small"):
+    if kind not in _IDX:
+        from synth import build_ivf_sign
+        from synth.data import gist_shaped
+        if kind == "small":
+            x, q = gist_shaped(20000, 12, d=128, n_centers=200)
+            idx = build_ivf_sign(x, 64, kmeans_iters=5)
+        else:                                   # d = 960 as in the GIST-shaped configuration
+            x, q = gist_shaped(6000, 6, d=960, n_centers=60)
+            idx = build_ivf_sign(x, 24, kmeans_iters=4)
+        h = bbc.bbc_index_create(idx, 0)
+        _IDX[kind] = (h, idx, q)
+    return _IDX[kind]
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def sync_ok(bbc, h):
+    torch.cuda.synchronize()
+    bbc.bbc_stream_status(h)
+
+
+def gpu_bounds(bbc, h, idx, q, nprobe):
+    nq = len(q)
+    lists = torch.empty((nq, nprobe), dtype=torch.int32, device="cuda")
+    bbc.bbc_probe(h, cuda(q), nq, nprobe, lists)
+    stride = int(np.sort(np.diff(idx.list_offsets))[::-1][:nprobe].sum())
+    lb = torch.zeros((nq, stride), dtype=torch.float32, device="cuda")
+    ub = torch.zeros((nq, stride), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(nq, dtype=torch.int64, device="cuda")
+    bbc.bbc_sign_bounds(h, cuda(q), nq, nprobe, lists, stride, lb, ub, cnt)
+    sync_ok(bbc, h)
+    return lists.cpu().numpy(), lb.cpu().numpy().astype(np.float64), ub.cpu().numpy().astype(np.float64), cnt.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind,nprobe", [("small", 8), ("small", 40), ("wide", 5)])
+def test_sign_bounds_enclose_exact(bbc, oracle_lib, kind, nprobe):
+    h, idx, q = sign_index(bbc, kind)
+    lists, lb, ub, cnt = gpu_bounds(bbc, h, idx, q, nprobe)
+    codes, fac = oracle_lib.sign_encode(idx)
+    eps = oracle_lib.rotation_eps(idx.rotation)
+    for i in range(len(q)):
+        ol, _ = oracle_lib.probe(q[i], idx.centroids, nprobe, "l2")
+        assert np.array_equal(lists[i], ol)
+        sel, _ = scanned_set(idx, ol)
+        n = len(sel)
+        assert cnt[i] == n
+        ex = oracle_lib.rerank(q[i], idx.vectors, idx.ids[sel], "l2")
+        assert np.all(lb[i, :n] <= ex) and np.all(ex <= ub[i, :n])
+        olb, oub = [], []
+        for l in ol:
+            a, b = idx.list_offsets[l], idx.list_offsets[l + 1]
+            x, y = oracle_lib.sign_bounds(q[i], idx.centroids[l], idx.rotation, eps, codes[a:b], fac[a:b])
+            olb.append(x); oub.append(y)
+        w_gpu = ub[i, :n] - lb[i, :n]
+        w_ora = np.concatenate(oub) - np.concatenate(olb)
+        scale = float(ex.max())
+        assert np.all(w_gpu <= 1.01 * w_ora + 1e-4 * scale)
+
+
+@pytest.mark.parametrize("kind,k,nprobe", [("small", 1, 4), ("small", 50, 8), ("small", 600, 16),
+                                           ("small", 2000, 40), ("small", 40000, 64), ("wide", 200, 6)])
+def test_sign_search_exact_topk(bbc, oracle_lib, kind, k, nprobe):
+    h, idx, q = sign_index(bbc, kind)
+    nq = len(q)
+    gi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    gd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_bounded_stats(h, reset=True)
+    bbc.bbc_search(h, cuda(q), nq, k, nprobe, gi, gd)
+    sync_ok(bbc, h)
+    st = bbc.bbc_bounded_stats(h, reset=True)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    oi, od, ost = oracle_lib.sign_search(idx, q, k, nprobe)
+    for i in range(nq):
+        valid = oi[i] >= 0
+        assert np.array_equal(gi[i] >= 0, valid), f"query {i}: padding"
+        assert np.all(np.isinf(gd[i][~valid]))
+        assert set(gi[i][valid].tolist()) == set(oi[i][valid].tolist()), f"query {i}: result set"
+        v = gd[i][valid].astype(np.float64)
+        assert np.all(np.diff(v) >= 0)
+        d64 = oracle_lib.rerank(q[i], idx.vectors, gi[i][valid], "l2")
+        assert np.all(np.abs(v - d64) <= RTOL * np.maximum(d64, 1e-3 * float(d64.max())))
+    assert st["scanned"] == int(ost[:, 0].sum())
+    assert st["queries"] == nq
+
+
+@pytest.mark.parametrize("k,nprobe", [(50, 8), (600, 16)])
+def test_sign_counts_match_oracle_classification(bbc, oracle_lib, k, nprobe):
+    h, idx, q = sign_index(bbc)
+    nq = len(q)
+    lists, lb, ub, cnt = gpu_bounds(bbc, h, idx, q, nprobe)
+    gi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    gd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_bounded_stats(h, reset=True)
+    bbc.bbc_search(h, cuda(q), nq, k, nprobe, gi, gd)
+    sync_ok(bbc, h)
+    st = bbc.bbc_bounded_stats(h, reset=True)
+    s_total, r_total = 0, 0
+    for i in range(nq):
+        sel, _ = scanned_set(idx, lists[i])
+        n = int(cnt[i])
+        ex = oracle_lib.rerank(q[i], idx.vectors, idx.ids[sel], "l2")
+        ns, _, _ = oracle_lib.oneshot(lb[i, :n], ub[i, :n], k)
+        rc, _ = oracle_lib.rounds(lb[i, :n], ub[i, :n], ex, k)
+        s_total += ns
+        r_total += rc
+    assert st["in_S"] == s_total
+    assert r_total <= st["exact"] <= s_total
+
+
+def test_host_entry_and_bound_scale(bbc):
+    h, idx, q = sign_index(bbc)
+    nq, k, nprobe = len(q), 300, 16
+    gi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    gd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_search(h, cuda(q), nq, k, nprobe, gi, gd)
+    sync_ok(bbc, h)
+    hi = np.empty((nq, k), dtype=np.int64)
+    hd = np.empty((nq, k), dtype=np.float32)
+    bbc.bbc_search_host(h, np.ascontiguousarray(q), nq, k, nprobe, hi, hd)
+    assert np.array_equal(hi, gi.cpu().numpy()) and np.array_equal(hd, gd.cpu().numpy())
+    # a narrower residual term keeps fewer objects in S and still returns sorted valid results
+    bbc.bbc_bounded_stats(h, reset=True)
+    bbc.bbc_search(h, cuda(q), nq, k, nprobe, gi, gd)
+    sync_ok(bbc, h)
+    hard = bbc.bbc_bounded_stats(h, reset=True)
+    bbc.bbc_set_param(h, "bound_scale", 0.05)
+    try:
+        bbc.bbc_search(h, cuda(q), nq, k, nprobe, gi, gd)
+        sync_ok(bbc, h)
+        soft = bbc.bbc_bounded_stats(h, reset=True)
+    finally:
+        bbc.bbc_set_param(h, "bound_scale", 1.0)
+    assert soft["in_S"] < hard["in_S"]
+    g = gi.cpu().numpy()
+    assert np.all(g >= 0) and np.all(np.diff(gd.cpu().numpy(), axis=1) >= 0)
+
+
+def test_pq_only_calls_refuse_sign_index(bbc):
+    h, idx, q = sign_index(bbc)
+    out = torch.empty(16, dtype=torch.int16, device="cuda")
+    with pytest.raises(bbc.BBCError, match="UNSUPPORTED"):
+        bbc.bbc_lut(h, cuda(q[:1]), 1, out)
+    with pytest.raises(bbc.BBCError, match="UNSUPPORTED"):
+        bbc.bbc_set_param(h, "precision", 1)
+    assert bbc.bbc_index_info(h)["quantizer"] == 1
