@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 
 METRIC = "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ)"
 METRICS = {"sift": METRIC, "sift4": "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ 64x4)",
+           "gist": "QPS at recall@k>=0.95 (k=10k, 1Mx960 IVF + 1-bit sign codes, bounded re-rank)",
            "embed": "QPS at recall@k>=0.95 (k=50k, 10Mx768 IVF-PQ, inner product)",
            "tiny": "QPS at recall@k>=0.95 (k=1k, 100kx128 IVF-PQ)"}
 UNIT = "queries/s"
@@ -111,7 +112,12 @@ def make_inputs(args, device):
     x, q = make_workload(w, n=n, nq=nq)
     set_build_device(device)
     t0 = time.time()
-    idx = build_ivf_pq(x, w.nlist if n >= 100 * w.nlist else max(8, n // 200), w.pq_m, w.pq_bits, w.metric)
+    nlist = w.nlist if n >= 100 * w.nlist else max(8, n // 200)
+    if w.quantizer == "sign":
+        from synth import build_ivf_sign
+        idx = build_ivf_sign(x, nlist)
+    else:
+        idx = build_ivf_pq(x, nlist, w.pq_m, w.pq_bits, w.metric)
     return w, idx, q, k, nprobe, time.time() - t0
 
 
@@ -368,11 +374,14 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
         bbc.bbc_search(h, qd, nq, k, nprobe, ids, dists, stream)
 
     # correctness of the operating point: recall against exact kNN
+    is_sign = hasattr(idx, "rotation")
     bbc.bbc_precision_stats(h, reset=True)
+    bbc.bbc_bounded_stats(h, reset=True)
     step()
     torch.cuda.synchronize()
     bbc.bbc_stream_status(h)
     pstats = bbc.bbc_precision_stats(h, reset=True) if prec else None
+    bstats = bbc.bbc_bounded_stats(h, reset=True) if is_sign else None
     nrec = min(nq, args.recall_queries or 1000)
     rec_mean, rec_min, dk = recall_at_k(xt, qd[:nrec], ids[:nrec], k, idx.metric)
     gt_check, err = None, None
@@ -451,7 +460,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     per = {s: stage_ms[s] / args.steps for s in stage_ms}
     peaks = _peaks()
     sm_clk = 2070.0
-    lookups = float(s_q.double().sum()) * idx.pq_m
+    lookups = float(s_q.double().sum()) * (idx.pq_m if not is_sign else 0)
     dpad = (idx.d + 15) // 16 * 16
     u8 = bool(index.get("rerank"))
     if prec:
@@ -470,6 +479,14 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
         "prec_classify": ("hbm", nq * kc * 8 * 5 / 1e9, "GB/s", peaks["hbm_gbs"]),
         "prec_recheck": ("hbm", unc * (idx.d * 4 + 16) / 1e9, "GB/s", peaks["hbm_gbs"]),
     }
+    if is_sign:
+        # codes (d/8 bytes) + factors (16 bytes) per scanned object; rows of the exact re-rank
+        work["scan"] = ("hbm", float(s_q.double().sum()) * (idx.d // 8 + 16) / 1e9, "GB/s", peaks["hbm_gbs"])
+        work["prec_recheck"] = ("hbm", bstats["exact"] * (idx.d * 4 + 8) / 1e9, "GB/s", peaks["hbm_gbs"])
+        work["select"] = ("hbm", bstats["scanned"] * 16 * 3 / 1e9, "GB/s", peaks["hbm_gbs"])
+        work["prec_classify"] = ("hbm", bstats["exact"] * 12 * 5 / 1e9, "GB/s", peaks["hbm_gbs"])
+        work["topk"] = ("hbm", nq * k * 20 / 1e9, "GB/s", peaks["hbm_gbs"])
+        work["lut"] = ("hbm", nq * idx.d * 12 / 1e9, "GB/s", peaks["hbm_gbs"])
     dom = max(per, key=lambda s: per[s])
     bound, amount, unit, peak = work[dom]
     achieved = amount / (per[dom] / 1e3)
@@ -483,22 +500,29 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
         import oracle
         nsamp = min(args.cpu_queries, nq)
         t0 = time.perf_counter()
-        oracle.search(idx, q[:nsamp], k, nprobe, kc, "sort")
+        if is_sign:
+            oracle.sign_search(idx, q[:nsamp], k, nprobe)
+        else:
+            oracle.search(idx, q[:nsamp], k, nprobe, kc, "sort")
         tc = time.perf_counter() - t0
         cpu = {"value": nsamp / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {nsamp} of the {nq} queries on the full index, single-threaded C"}
 
     if rank == 0:
         rerank = ["u8-exact" if u8 else "f32", "bf16-prefilter", "fp8e4m3-prefilter"][prec]
+        if is_sign:
+            rerank = "bounded, two rounds, f32 (f64 at ties)"
         out = {
             "metric": METRICS.get(args.workload, METRIC), "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u16/u32 ADC, " + {0: "f32 re-rank", 1: "bf16+f32 re-rank (f64 at ties)",
-                                        2: "e4m3+f32 re-rank (f64 at ties)"}[prec],
+            "dtype": ("1-bit codes x 4-bit query planes (AND+POPC), f32 bounds, f32 re-rank (f64 at ties)" if is_sign
+                      else "u16/u32 ADC, " + {0: "f32 re-rank", 1: "bf16+f32 re-rank (f64 at ties)",
+                                              2: "e4m3+f32 re-rank (f64 at ties)"}[prec]),
             "data": "synthetic",
             "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "metric_space": idx.metric,
-                       "pq": f"{idx.pq_m}x{idx.pq_bits}", "nq": nq, "k": k, "nprobe": nprobe, "kc": kc,
+                       "pq": "sign 1-bit" if is_sign else f"{idx.pq_m}x{idx.pq_bits}", "nq": nq, "k": k,
+                       "nprobe": nprobe, "kc": None if is_sign else kc,
                        "kc_ratio": ratio, "buckets": args.buckets, "rerank": rerank,
                        "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
                        "recall_tie_aware": True, "ground_truth_cpu_spotcheck": gt_check,
@@ -511,6 +535,10 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
+        if is_sign:
+            out["bounded"] = {"per_step": bstats, "in_S_per_query": bstats["in_S"] / nq,
+                              "exact_per_query": bstats["exact"] / nq,
+                              "bound_scale": index.get("bound_scale")}
         if prec:
             out["precision"] = {"per_step": pstats, "fp32_recheck_frac": pstats["fp32_rechecked"] / max(1, pstats["scored"]),
                                 "fp64_frac": pstats["fp64_scored"] / max(1, pstats["scored"])}

@@ -316,7 +316,23 @@ def build_ivf_sign(x: np.ndarray, nlist: int, kmeans_iters: int = 12,
         raise ValueError("d must be a multiple of 32 for sign codes")
     if kmeans_sample is None:
         kmeans_sample = min(n, 256 * nlist)
-    cent = kmeans(x, nlist, iters=kmeans_iters, seed=SEED_KMEANS, sample=kmeans_sample)
-    assign = nearest(x, cent)
+    if _DEVICE != "cpu" and n * d >= (1 << 28):
+        import torch
+        dev = torch.device(_DEVICE)
+        xt = torch.from_numpy(x).to(dev)
+        rng = np.random.default_rng(SEED_KMEANS)
+        if kmeans_sample < n:
+            sel = torch.from_numpy(np.sort(rng.choice(n, size=kmeans_sample, replace=False))).to(dev)
+            train = xt[sel]
+        else:
+            train = xt
+        ct = _kmeans_dev(train, nlist, kmeans_iters, rng, 1 << 15)
+        del train
+        assign = _nearest_dev(xt, ct, 1 << 15).cpu().numpy()
+        cent = ct.cpu().numpy()
+        del xt, ct
+    else:
+        cent = kmeans(x, nlist, iters=kmeans_iters, seed=SEED_KMEANS, sample=kmeans_sample)
+        assign = nearest(x, cent)
     ids, offsets = _inverted_lists(assign, nlist)
     return IvfSignIndex("l2", d, nlist, cent, offsets, ids, random_rotation(d), x)
