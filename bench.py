@@ -477,7 +477,8 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
         "select": ("hbm", nq * kc * 8 * 2 / 1e9, "GB/s", peaks["hbm_gbs"]),
         "probe_scores": ("tensor", 2.0 * nq * idx.nlist * idx.d / 1e12, "TFLOP/s", peaks["bf16_tflops"]),
         "probe_select": ("hbm", nq * idx.nlist * 4 / 1e9, "GB/s", peaks["hbm_gbs"]),
-        "lut": ("hbm", nq * idx.pq_m * (1 << idx.pq_bits) * 2 / 1e9, "GB/s", peaks["hbm_gbs"]),
+        "lut": ("hbm", nq * getattr(idx, "pq_m", 0) * (1 << getattr(idx, "pq_bits", 0)) * 2 / 1e9, "GB/s",
+                peaks["hbm_gbs"]),
         "prec_classify": ("hbm", nq * kc * 8 * 5 / 1e9, "GB/s", peaks["hbm_gbs"]),
         "prec_recheck": ("hbm", unc * (idx.d * 4 + 16) / 1e9, "GB/s", peaks["hbm_gbs"]),
     }
