@@ -65,6 +65,9 @@ def parse():
     p.add_argument("--precision", default=None,
                    help="re-rank precision: 0 FP32 rows (or the exact u8 copy), 1 BF16 prefilter, 2 FP8-E4M3 "
                         "prefilter; a comma list prints one line per value (default: 0, or 2 for float data)")
+    p.add_argument("--bound-scale", default="1",
+                   help="sign-code indexes: factor on the worst-case bound terms (1 = hard bounds); a comma list "
+                        "prints one line per value")
     p.add_argument("--recall-queries", type=int, default=None,
                    help="queries whose recall is measured against exact kNN (default: all, at most 1,000)")
     return p.parse_args()
@@ -350,11 +353,15 @@ def main():
     xt = torch.from_numpy(idx.vectors).to(dev)
     nprobes = [int(v) for v in args.nprobe.split(",")] if args.nprobe else [nprobe]
     ratios = [float(v) for v in str(args.kc_ratio).split(",")]
+    scales = [float(v) for v in str(args.bound_scale).split(",")] if index.info["quantizer"] == 1 else [None]
     for prec in precs:
         for npb in nprobes:
             for ratio in ratios:
-                index.set(kc_ratio=ratio)
-                measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec, ratio)
+                for scale in scales:
+                    index.set(kc_ratio=ratio)
+                    if scale is not None:
+                        index.set(bound_scale=scale)
+                    measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec, ratio)
     index.close()
 
 
@@ -502,9 +509,15 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         nsamp = min(args.cpu_queries, nq)
+        if is_sign:
+            # index preparation outside the timed region: codes of the sample's probed lists, rotation error
+            probed = [oracle.probe(q[i], idx.centroids, nprobe, idx.metric)[0] for i in range(nsamp)]
+            scodes, sfac = oracle.sign_encode_lists(idx, np.concatenate(probed))
+            seps = oracle.rotation_eps(idx.rotation)
         t0 = time.perf_counter()
         if is_sign:
-            oracle.sign_search(idx, q[:nsamp], k, nprobe)
+            oracle.sign_search(idx, q[:nsamp], k, nprobe, scale=index.get("bound_scale"), codes=scodes,
+                               fac=sfac, eps=seps)
         else:
             oracle.search(idx, q[:nsamp], k, nprobe, kc, "sort")
         tc = time.perf_counter() - t0

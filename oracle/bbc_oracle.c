@@ -697,9 +697,10 @@ double oracle_rotation_eps(const float* rot, int32_t d) {
  *   u_i = nearest integer to (q'_i - lo) / Delta in [0, 15], q~ = lo + Delta u,
  *   eta = ||q' - q~||;
  *   X = <q~, s> = lo (2 pc - d) + Delta (2 sum_i u_i b_i - sum_i u_i)   (b = code bits);
- *   <q', r> in alpha X +- (scale ||q'|| e + |alpha| eta sqrt(d));
+ *   <q', r> in alpha X +- scale (||q'|| e + |alpha| eta sqrt(d));
  *   ||q - o||^2 = ||t||^2 + ||u||^2 - 2 <t, u>, |<t, u> - <q', r>| <= eps ||t|| ||u||;
- * plus a relative FP64 allowance of 1e-12.  scale = 1 gives hard bounds. */
+ * plus a relative FP64 allowance of 1e-12.  scale multiplies the two
+ * Cauchy-Schwarz terms; 1 gives hard bounds. */
 void oracle_sign_bounds(const float* q, int32_t d, const float* centroid, const float* rot, double eps,
                         const uint32_t* codes, const double* fac, int64_t n, double scale,
                         double* lb, double* ub) {
@@ -741,7 +742,7 @@ void oracle_sign_bounds(const float* q, int32_t d, const float* centroid, const 
         const double alpha = fac[p * 4 + 0], e = fac[p * 4 + 1], un2 = fac[p * 4 + 2], pc = fac[p * 4 + 3];
         const double X = lo * (2.0 * pc - d) + delta * (2.0 * (double)ub_sum - (double)usum);
         const double est = alpha * X;
-        const double half = scale * qn * e + fabs(alpha) * eta * sd;
+        const double half = scale * (qn * e + fabs(alpha) * eta * sd);
         const double rot_err = 2.0 * eps * tn * sqrt(un2);
         const double base = tn2 + un2;
         const double slack = 1e-12 * (base + 2.0 * fabs(est) + 2.0 * half + rot_err);

@@ -9,11 +9,14 @@
 //   (max q' - lo) / 15, u_i = nearest level in [0, 15], q~ = lo + Delta u,
 //   eta = ||q' - q~||;  <q~, s> = lo (2 pc - d) + Delta (2 sum_i u_i b_i - sum_i u_i)
 //   with sum_i u_i b_i from four AND + POPC bit planes (exact integers);
-//   <P t, r> in alpha <q~, s> +- (|alpha| (eta sqrt(d) + rounding of <q~, s>)
-//   + scale ||q'|| e + ||q' - P t|| ||r||),  t = q - c_l;
+//   <P t, r> in alpha <q~, s> +- (|alpha| rounding of <q~, s> + scale (|alpha| eta sqrt(d)
+//   + ||q'|| e) + ||q' - P t|| ||r||),  t = q - c_l;
 //   ||q - o||^2 = ||t||^2 + ||u||^2 - 2 <t, u>, |<t, u> - <P t, P u>| <= eps ||t|| ||u||
 //   with eps = ||P^T P - I||_F; a 2^-20 relative allowance covers the FP32
-//   evaluation.  scale = 1 gives hard bounds.
+//   evaluation.  scale = 1 gives hard bounds; both Cauchy-Schwarz terms are
+//   worst cases that a random rotation makes about sqrt(d) too wide, so
+//   scale = eps0 / sqrt(d - 1) gives intervals in the spirit of RaBitQ's
+//   probabilistic bound (not hard).
 //
 // Collection (a result buffer on the upper bound, Alg. 1 and Alg. 3): the
 // histogram counts every scanned object by the bucket of its upper bound;
@@ -270,7 +273,7 @@ __device__ __forceinline__ void sign_bound(const DevIndex& ix, int64_t slot, con
     const float alpha = f.x, e = f.y, un2 = f.z;
     const float un = sqrtf(un2) * (1.f + 2.384185791015625e-7f);
     const float est = alpha * X;
-    const float H = fabsf(alpha) * (eX + ls.eta_sd) + scale * ls.qn * e + ls.dterm * un * (1.f + eps);
+    const float H = fabsf(alpha) * eX + scale * (fabsf(alpha) * ls.eta_sd + ls.qn * e) + ls.dterm * un * (1.f + eps);
     const float base = ls.tn2 + un2;
     const float rotE = 2.f * eps * ls.tn * un;
     const float slack = 9.5367431640625e-7f * (base + 2.f * fabsf(est) + 2.f * H + rotE);   // 2^-20

@@ -64,6 +64,19 @@ def test_encode_pythagoras_random_rotation():
     assert np.all(alpha > 0) and np.all(e >= 0)
 
 
+def test_list_encoder_matches_object_encoder():
+    x, _ = gist_shaped(1500, 1, d=64, n_centers=20)
+    idx = build_ivf_sign(x, 6, kmeans_iters=3)
+    c1, f1 = oracle.sign_encode(idx)
+    c2, f2 = oracle.sign_encode_lists(idx, [0, 2, 5])
+    for l in (0, 2, 5):
+        a, b = idx.list_offsets[l], idx.list_offsets[l + 1]
+        assert np.array_equal(c1[a:b], c2[a:b])
+        assert np.allclose(f1[a:b], f2[a:b], rtol=1e-12, atol=1e-12)
+    a, b = idx.list_offsets[1], idx.list_offsets[2]
+    assert not c2[a:b].any() and not f2[a:b].any()
+
+
 def test_bounds_enclose_exact_distance():
     x, q = gist_shaped(4000, 6, d=96, n_centers=30)
     idx = build_ivf_sign(x, 12, kmeans_iters=3)
