@@ -110,10 +110,20 @@ __device__ __forceinline__ uint32_t warp_update(const uint32_t* hist, int m, int
     const unsigned ln = lane_id();
     uint32_t h[8];
     uint32_t s = 0;
+    // two 16-byte loads per lane where hist is 16-byte aligned (it is zero past m)
+    uint32_t raw[8];
+    if ((reinterpret_cast<uintptr_t>(hist) & 15u) == 0) {
+        asm volatile("ld.volatile.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(raw[0]), "=r"(raw[1]), "=r"(raw[2]), "=r"(raw[3]) : "l"(hist + ln * 8));
+        asm volatile("ld.volatile.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(raw[4]), "=r"(raw[5]), "=r"(raw[6]), "=r"(raw[7]) : "l"(hist + ln * 8 + 4));
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) raw[i] = *(volatile const uint32_t*)&hist[ln * 8 + i];
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        int b = (int)ln * 8 + i;
-        h[i] = b < m ? *(volatile const uint32_t*)&hist[b] : 0u;
+        h[i] = (int)ln * 8 + i < m ? raw[i] : 0u;
         s += h[i];
     }
     unsigned long long inc = warp_incl_scan64(s);
@@ -139,13 +149,14 @@ __device__ __forceinline__ uint32_t bin_of(uint32_t e, uint32_t dmin, int sh) {
 }
 
 struct ScanShared {
-    uint32_t hist[kMaxBuckets];
+    alignas(16) uint32_t hist[kMaxBuckets];
     uint32_t ehist[256];
-    uint8_t bmap[256];
+    alignas(16) uint8_t bmap[256];
     uint32_t sc[2];
     uint32_t count;
     uint32_t dmin, dmax;
     uint32_t tau;
+    uint32_t etau;      // largest estimate whose bucket is <= tau (the map is monotone)
     int sh;
     int nsl;
     long long sq;
@@ -160,6 +171,21 @@ struct QCtx {
     const int32_t* lists;
 };
 
+// Push test without the map: buckets are monotone in the bin, so bucket(e) <= t
+// holds exactly for bins 0 .. c-1, c = number of bins whose bucket is <= t,
+// i.e. for e <= d_min + (c << sh) - 1.  Warp-collective.
+__device__ __forceinline__ uint32_t etau_of(const ScanShared& S, uint32_t t) {
+    const unsigned ln = lane_id();
+    const uint2 w = *(const uint2*)&S.bmap[ln * 8];             // 8 map entries of this lane
+    const uint32_t tt = t > 255u ? 0xFFFFFFFFu : t * 0x01010101u;
+    // bytes <= t: per-byte unsigned compare (0xFF where true)
+    uint32_t c = t > 255u ? 8u : (uint32_t)(__popc(__vcmpleu4(w.x, tt)) + __popc(__vcmpleu4(w.y, tt))) / 8u;
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if (c >= 256u) return 0xFFFFFFFFu;
+    const unsigned long long v = (unsigned long long)S.dmin + ((unsigned long long)c << S.sh) - 1ull;
+    return v > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)v;
+}
+
 // Split mode: move this CTA's bucket-count deltas into the query's global
 // counts, then Update on the global counts (one warp).
 __device__ __forceinline__ void flush_and_update(ScanShared& S, bbc_collector_state* st, int m, int64_t kc) {
@@ -169,9 +195,11 @@ __device__ __forceinline__ void flush_and_update(ScanShared& S, bbc_collector_st
     }
     __syncwarp();
     const uint32_t t = warp_update(st->hist, m, kc);
+    const uint32_t e = etau_of(S, t);
     if (lane_id() == 0) {
         atomicMin(&st->tau, (int)t);
         atomicMin(&S.tau, t);
+        atomicMin(&S.etau, e);
     }
 }
 
@@ -193,15 +221,22 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
     uint2* region = Q.region;
     const unsigned lt_mask = (1u << ln) - 1u;
     constexpr int CH = C::CHUNK;
+    int jw = -1;                                              // list of this warp's current chunk
     for (int cb = g0 + (int)warp_id() * CH; cb < g1; cb += nw * CH) {
         const int ge = min(cb + CH, g1);
-        // list holding block cb: largest j with lpre[j] <= cb
-        int lo = 0, hi = P - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (lpre[mid] <= cb) lo = mid; else hi = mid - 1;
+        // list holding block cb: largest j with lpre[j] <= cb (binary search once,
+        // then walk forward: a warp's chunks ascend)
+        if (jw < 0) {
+            int lo = 0, hi = P - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (lpre[mid] <= cb) lo = mid; else hi = mid - 1;
+            }
+            jw = lo;
+        } else {
+            while (cb >= lpre[jw + 1]) ++jw;
         }
-        int j = lo;
+        int j = jw;
         int gbk[CH], nval[CH];
         uint4 r[CH][C::NCH];
 #pragma unroll
@@ -219,7 +254,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                 for (int c = 0; c < C::NCH; ++c) r[u][c] = __ldg(cp + c * 32);
             }
         }
-        const uint32_t tau = MAIN ? *(volatile uint32_t*)&S.tau : 0u;
+        const uint32_t etau = MAIN ? *(volatile uint32_t*)&S.etau : 0u;
         const uint32_t dmin = S.dmin;
         const int sh = S.sh;
 #pragma unroll
@@ -228,10 +263,8 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
             const uint32_t e = adc_lane<M, BITS>(r[u], lane_base);
             const bool valid = (int)ln < nval[u];
             bool push;
-            uint32_t bk = 0;
             if (MAIN) {
-                bk = S.bmap[bin_of(e, dmin, sh)];
-                push = valid && bk <= tau;
+                push = valid && e <= etau;                       // bucket(e) <= tau
             } else {
                 push = valid;
                 if (!GLOBAL) {
@@ -254,7 +287,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                     const uint32_t pos = base + (uint32_t)__popc(bal & lt_mask);
                     if ((int64_t)pos < Q.cap) region[pos] = make_uint2(e, (uint32_t)gbk[u] * 32u + ln);
                     else atomicOr(ix.status, kStatusRegionOverrun);
-                    if (MAIN) atomicAdd(&S.hist[bk], 1u);
+                    if (MAIN) atomicAdd(&S.hist[S.bmap[bin_of(e, dmin, sh)]], 1u);
                 }
             }
         }
@@ -263,7 +296,11 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                 if (warp_id() == 0) flush_and_update(S, st, a.m, Q.kc);
             } else {
                 const uint32_t t = warp_update(S.hist, a.m, Q.kc);
-                if (ln == 0 && t < *(volatile uint32_t*)&S.tau) atomicMin(&S.tau, t);
+                const uint32_t e = etau_of(S, t);
+                if (ln == 0) {
+                    atomicMin(&S.tau, t);
+                    atomicMin(&S.etau, e);
+                }
             }
         }
     }
@@ -326,10 +363,11 @@ __device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int 
         __syncthreads();
         if (warp_id() == 0) {
             const uint32_t t0 = warp_update(S.hist, m, kc);
-            if (lane_id() == 0) S.tau = t0;
+            const uint32_t e0 = etau_of(S, t0);
+            if (lane_id() == 0) { S.tau = t0; S.etau = e0; }
         }
     } else {
-        if (tid == 0) { S.dmin = 0; S.dmax = 0; S.sh = 0; }
+        if (tid == 0) { S.dmin = 0; S.dmax = 0; S.sh = 0; S.tau = (uint32_t)m; S.etau = 0xFFFFFFFFu; }
         for (int i = tid; i < 256; i += bs) S.bmap[i] = 0;
     }
     __syncthreads();
@@ -361,6 +399,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, Scan
         S.count = 0;
         S.dmin = 0xFFFFFFFFu;
         S.tau = (uint32_t)a.m;
+        S.etau = 0xFFFFFFFFu;
         S.sh = 0;
     }
     if (warp_id() == 0) {
@@ -566,6 +605,11 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_split_kernel(DevIndex ix
                 S.dmin = st->d_min;
                 S.sh = st->sh;
                 S.tau = (uint32_t)*(volatile int*)&st->tau;
+            }
+            __syncthreads();
+            if (warp_id() == 0) {
+                const uint32_t e0 = etau_of(S, S.tau);
+                if (lane_id() == 0) S.etau = e0;
             }
         }
         __syncthreads();
