@@ -118,8 +118,8 @@ typedef struct {
 
 /* Build a device index with sign codes.  BBC_ERR_UNSUPPORTED for inner
  * product or d not a multiple of 32 / above 2048.  On such an index
- * bbc_search and bbc_search_host run the bounded re-rank; the other per-step
- * calls return BBC_ERR_UNSUPPORTED. */
+ * bbc_search, bbc_search_host and bbc_search_ex run the bounded re-rank; the
+ * other per-step calls return BBC_ERR_UNSUPPORTED. */
 int bbc_index_create_sign(const bbc_sign_host* h, int device, bbc_index** out);
 
 int bbc_index_free(bbc_index* ix);

@@ -425,24 +425,27 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
 // Bounded re-rank on a sign-code index (S9b): probe, rotate, scan with the
 // result buffer on the upper bound, two re-rank rounds, exact final order.
 // ---------------------------------------------------------------------------
-struct SignPlan {
-    int64_t chunk, cap;
-    size_t off_scores, off_abf, off_probe, off_qrot, off_region, off_small, off_clist, off_rkey, off_rid, off_cd,
-        off_cr, off_ud, off_ur, off_keys, off_prec, off_q, off_ids, off_dists, total;
+struct SignShape {
+    int64_t nq = 0, sum_probe = 0, sum_cap = 0, sum_k = 0;
+    int max_probe = 0, max_k = 0;
+    bool host_io = false, mixed = false;
 };
 
-size_t sign_layout(const bbc_index* ix, int64_t nc, int nprobe, int k, bool host_io, SignPlan& p) {
+struct SignPlan {
+    size_t off_scores, off_abf, off_probe, off_qrot, off_region, off_small, off_clist, off_rkey, off_rid, off_cd,
+        off_cr, off_ud, off_ur, off_keys, off_prec, off_params, off_q, off_ids, off_dists, total;
+};
+
+size_t sign_layout(const bbc_index* ix, const SignShape& c, SignPlan& p) {
     const DevIndex& d = ix->dev;
-    const int64_t cap = ix->cap_prefix[nprobe];
-    const size_t slots = (size_t)nc * (size_t)cap;
+    const size_t slots = (size_t)c.sum_cap;
     size_t o = 0;
-    p.cap = cap;
-    p.off_scores = o; o = align_up(o + (size_t)nc * d.nlist * 4);
-    p.off_abf = o; o = align_up(o + (ix->probe_gemm ? probe_tc_workspace(d, nc) : 0));
-    p.off_probe = o; o = align_up(o + (size_t)nc * nprobe * 4);
-    p.off_qrot = o; o = align_up(o + (size_t)nc * d.d * 8);
+    p.off_scores = o; o = align_up(o + (size_t)c.nq * d.nlist * 4);
+    p.off_abf = o; o = align_up(o + (ix->probe_gemm ? probe_tc_workspace(d, c.nq) : 0));
+    p.off_probe = o; o = align_up(o + (size_t)c.sum_probe * 4);
+    p.off_qrot = o; o = align_up(o + (size_t)c.nq * d.d * 8);
     p.off_region = o; o = align_up(o + slots * 16);
-    p.off_small = o; o = align_up(o + (size_t)nc * 8 * 5);         // pushed, scanned, n_b, n_c, n_rest
+    p.off_small = o; o = align_up(o + (size_t)c.nq * 8 * 5);         // pushed, scanned, n_b, n_c, n_rest
     p.off_clist = o; o = align_up(o + slots * 4);
     p.off_rkey = o; o = align_up(o + slots * 4);
     p.off_rid = o; o = align_up(o + slots * 4);
@@ -450,30 +453,33 @@ size_t sign_layout(const bbc_index* ix, int64_t nc, int nprobe, int k, bool host
     p.off_cr = o; o = align_up(o + slots * 4);
     p.off_ud = o; o = align_up(o + slots * 4);
     p.off_ur = o; o = align_up(o + slots * 4);
-    p.off_keys = o; o = align_up(o + (k > kTopkSmemMax ? slots * 8 : 0));
-    p.off_prec = o; o = align_up(o + prec_bytes(nc, (int64_t)slots));
-    p.off_q = o; o = align_up(o + (host_io ? (size_t)nc * d.d * 4 : 0));
-    p.off_ids = o; o = align_up(o + (host_io ? (size_t)nc * k * 8 : 0));
-    p.off_dists = o; o = align_up(o + (host_io ? (size_t)nc * k * 4 : 0));
+    p.off_keys = o; o = align_up(o + (c.max_k > kTopkSmemMax ? slots * 8 : 0));
+    p.off_prec = o; o = align_up(o + prec_bytes(c.nq, (int64_t)slots));
+    p.off_params = o; o = align_up(o + (c.mixed ? (size_t)(c.nq + 1) * 8 * 7 : 0));
+    p.off_q = o; o = align_up(o + (c.host_io ? (size_t)c.nq * d.d * 4 : 0));
+    p.off_ids = o; o = align_up(o + (c.host_io ? (size_t)c.sum_k * 8 : 0));
+    p.off_dists = o; o = align_up(o + (c.host_io ? (size_t)c.sum_k * 4 : 0));
     p.total = o;
     return o;
 }
 
-SignPlan make_sign_plan(const bbc_index* ix, int64_t nq, int nprobe, int k, bool host_io) {
-    SignPlan p{};
-    const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
-    int64_t c = std::max<int64_t>(1, nq);
-    while (c > 1 && sign_layout(ix, c, nprobe, k, host_io, p) > budget) c = (c + 1) / 2;
-    sign_layout(ix, c, nprobe, k, host_io, p);
-    p.chunk = c;
-    return p;
+SignShape sign_uniform_shape(const bbc_index* ix, int64_t nc, int nprobe, int k, bool host_io) {
+    SignShape c;
+    c.nq = nc;
+    c.sum_probe = nc * nprobe;
+    c.sum_cap = nc * ix->cap_prefix[nprobe];
+    c.sum_k = nc * k;
+    c.max_probe = nprobe;
+    c.max_k = k;
+    c.host_io = host_io;
+    return c;
 }
 
-int run_sign_chunk(bbc_index* ix, const SignPlan& p, char* ws, const float* q, int64_t nc, int nprobe, int k,
-                   int64_t* out_ids, float* out_dists, cudaStream_t st) {
+// One chunk of the bounded re-rank; qp gives each query's nprobe, k, region
+// (capacity = its scanned objects at most) and result offsets.
+int run_sign_chunk(bbc_index* ix, const SignPlan& p, const SignShape& c, char* ws, const float* q, int64_t nc,
+                   const QueryParams& qp, int64_t* out_ids, float* out_dists, cudaStream_t st) {
     const DevIndex& d = ix->dev;
-    const int64_t cap = p.cap;
-    QueryParams qp = uniform_params(nprobe, cap, k, cap);
     float* scores = reinterpret_cast<float*>(ws + p.off_scores);
     int32_t* probe = reinterpret_cast<int32_t*>(ws + p.off_probe);
     double* qrot = reinterpret_cast<double*>(ws + p.off_qrot);
@@ -487,12 +493,14 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, char* ws, const float* q, i
         CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores_tc(d, q, nc, scores, ws + p.off_abf, st); }));
     else
         CUDA_TRY(stage(ix, 0, st, [&] { return launch_probe_scores(d, q, nc, scores, st); }));
-    CUDA_TRY(stage(ix, 1, st, [&] { return launch_probe_select(d, q, nc, qp, nprobe, scores, probe, ix->probe_gemm, st); }));
+    CUDA_TRY(stage(ix, 1, st, [&] {
+        return launch_probe_select(d, q, nc, qp, c.max_probe, scores, probe, ix->probe_gemm, st);
+    }));
     CUDA_TRY(stage(ix, 2, st, [&] { return launch_rotate_f64(q, nullptr, nullptr, nullptr, d.rot, nc, d.d, qrot, st); }));
     SignArgs sa{};
-    sa.qrot = qrot; sa.q = q; sa.lists = probe; sa.nprobe = nprobe; sa.k = k; sa.m = ix->buckets;
+    sa.qrot = qrot; sa.q = q; sa.lists = probe; sa.nprobe = c.max_probe; sa.k = c.max_k; sa.m = ix->buckets;
     sa.sample_min = ix->sample_lists; sa.scale = ix->bound_scale;
-    sa.region = reinterpret_cast<uint4*>(ws + p.off_region); sa.cap = cap; sa.pushed = pushed; sa.scanned = scanned;
+    sa.region = reinterpret_cast<uint4*>(ws + p.off_region); sa.cap = qp.cap; sa.pushed = pushed; sa.scanned = scanned;
     sa.qp = qp;
     CUDA_TRY(stage(ix, 3, st, [&] { return launch_sign_scan(d, nc, sa, st); }));
     SignSelectArgs ss{};
@@ -500,7 +508,7 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, char* ws, const float* q, i
     ss.rest_key = reinterpret_cast<uint32_t*>(ws + p.off_rkey); ss.rest_id = reinterpret_cast<uint32_t*>(ws + p.off_rid);
     ss.n_rest = n_rest; ss.cd = cd; ss.cr = cr; ss.totals = ix->sign_totals; ss.qp = qp;
     CUDA_TRY(stage(ix, 4, st, [&] { return launch_sign_select(d, nc, ss, st); }));
-    PrecArgs pa = prec_args(ix, ws + p.off_prec, nc, nc * cap);
+    PrecArgs pa = prec_args(ix, ws + p.off_prec, nc, c.sum_cap);
     pa.rho = cr;
     pa.unc_d = reinterpret_cast<float*>(ws + p.off_ud);
     pa.unc_r = reinterpret_cast<float*>(ws + p.off_ur);
@@ -509,8 +517,8 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, char* ws, const float* q, i
     pa.rc_d = cd;
     pa.rc_r = cr;
     CUDA_TRY(cudaMemsetAsync(pa.qnorm, 0, (size_t)nc * sizeof(float), st));
-    unsigned long long* keys = k > kTopkSmemMax ? reinterpret_cast<unsigned long long*>(ws + p.off_keys) : nullptr;
-    RerankArgs ra{q, clist, n_c, cap, 0, cd, k, out_ids, out_dists, keys, qp};
+    unsigned long long* keys = c.max_k > kTopkSmemMax ? reinterpret_cast<unsigned long long*>(ws + p.off_keys) : nullptr;
+    RerankArgs ra{q, clist, n_c, qp.kc, 0, cd, c.max_k, out_ids, out_dists, keys, qp};
     // round 1: the k smallest upper bounds
     pa.rc_from = nullptr;
     pa.rc_count = n_b;
@@ -529,35 +537,108 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, char* ws, const float* q, i
     rb.cand = pa.fin_id;
     rb.cdist = pa.fin_d;
     rb.cand_count = pa.n_fin;
-    rb.kc = k;
+    rb.kc = c.max_k;
     CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(d, nc, rb, st); }));
     return BBC_OK;
 }
 
 int search_sign(bbc_index* ix, const float* queries, int64_t nq, int k, int nprobe, int64_t* out_ids,
                 float* out_dists, cudaStream_t st, bool host_io) {
-    SignPlan p = make_sign_plan(ix, nq, nprobe, k, host_io);
+    const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
+    SignPlan p{};
+    int64_t chunk = std::max<int64_t>(1, nq);
+    while (chunk > 1 && sign_layout(ix, sign_uniform_shape(ix, chunk, nprobe, k, host_io), p) > budget)
+        chunk = (chunk + 1) / 2;
+    const SignShape c = sign_uniform_shape(ix, chunk, nprobe, k, host_io);
+    sign_layout(ix, c, p);
     char* ws;
     int rc = get_workspace(ix, st, p.total, &ws);
     if (rc) return rc;
     const int d = ix->dev.d;
-    for (int64_t q0 = 0; q0 < nq; q0 += p.chunk) {
-        const int64_t nc = std::min(p.chunk, nq - q0);
+    const int64_t cap = ix->cap_prefix[nprobe];
+    const QueryParams qp = uniform_params(nprobe, cap, k, cap);
+    for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+        const int64_t nc = std::min(chunk, nq - q0);
         if (host_io) {
             float* dq = reinterpret_cast<float*>(ws + p.off_q);
             int64_t* di = reinterpret_cast<int64_t*>(ws + p.off_ids);
             float* dd = reinterpret_cast<float*>(ws + p.off_dists);
             CUDA_TRY(cudaMemcpyAsync(dq, queries + q0 * d, (size_t)nc * d * 4, cudaMemcpyHostToDevice, st));
-            if ((rc = run_sign_chunk(ix, p, ws, dq, nc, nprobe, k, di, dd, st))) return rc;
+            if ((rc = run_sign_chunk(ix, p, c, ws, dq, nc, qp, di, dd, st))) return rc;
             CUDA_TRY(cudaMemcpyAsync(out_ids + q0 * k, di, (size_t)nc * k * 8, cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaMemcpyAsync(out_dists + q0 * k, dd, (size_t)nc * k * 4, cudaMemcpyDeviceToHost, st));
         } else {
-            if ((rc = run_sign_chunk(ix, p, ws, queries + q0 * d, nc, nprobe, k, out_ids + q0 * k,
-                                     out_dists + q0 * k, st)))
+            if ((rc = run_sign_chunk(ix, p, c, ws, queries + q0 * d, nc, qp, out_ids + q0 * k, out_dists + q0 * k, st)))
                 return rc;
         }
     }
     if (host_io) CUDA_TRY(cudaStreamSynchronize(st));
+    return BBC_OK;
+}
+
+// Mixed batch (per-query k and nprobe) on a sign-code index: greedy chunks
+// that fit the workspace, per-query tables as in the PQ mixed batch.
+int search_sign_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t* k, const int32_t* nprobe,
+                   int64_t* out_ids, float* out_dists, cudaStream_t st) {
+    const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
+    int64_t out_base = 0;
+    for (int64_t q0 = 0; q0 < nq;) {
+        SignShape c;
+        c.mixed = true;
+        int64_t q1 = q0;
+        while (q1 < nq) {
+            SignShape t = c;
+            t.nq += 1; t.sum_probe += nprobe[q1]; t.sum_cap += ix->cap_prefix[nprobe[q1]]; t.sum_k += k[q1];
+            t.max_probe = std::max(t.max_probe, nprobe[q1]); t.max_k = std::max(t.max_k, k[q1]);
+            SignPlan tp{};
+            if (q1 > q0 && sign_layout(ix, t, tp) > budget) break;
+            c = t;
+            ++q1;
+        }
+        const int64_t nc = q1 - q0;
+        SignPlan p{};
+        sign_layout(ix, c, p);
+        const size_t n8 = (size_t)nc + 1;
+        std::vector<int64_t> tab(n8 * 7, 0);
+        int32_t* t_np = reinterpret_cast<int32_t*>(tab.data());
+        int32_t* t_k = reinterpret_cast<int32_t*>(tab.data() + n8);
+        int64_t* t_kc = tab.data() + 2 * n8;
+        int64_t* t_po = tab.data() + 3 * n8;
+        int64_t* t_ro = tab.data() + 4 * n8;
+        int64_t* t_co = tab.data() + 5 * n8;
+        int64_t* t_oo = tab.data() + 6 * n8;
+        int64_t maxcap = 0;
+        for (int64_t i = 0; i < nc; ++i) {
+            const int64_t qq = q0 + i;
+            const int64_t cap = ix->cap_prefix[nprobe[qq]];
+            t_np[i] = nprobe[qq];
+            t_k[i] = k[qq];
+            t_kc[i] = cap;
+            t_po[i + 1] = t_po[i] + nprobe[qq];
+            t_ro[i + 1] = t_ro[i] + cap;
+            t_co[i + 1] = t_co[i] + cap;
+            t_oo[i + 1] = t_oo[i] + k[qq];
+            maxcap = std::max(maxcap, cap);
+        }
+        char* ws;
+        int rc = get_workspace(ix, st, p.total, &ws);
+        if (rc) return rc;
+        int64_t* dtab = reinterpret_cast<int64_t*>(ws + p.off_params);
+        CUDA_TRY(cudaMemcpyAsync(dtab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, st));
+        QueryParams qp{};
+        qp.nprobe = c.max_probe; qp.kc = maxcap; qp.k = c.max_k; qp.cap = maxcap;
+        qp.nprobe_q = reinterpret_cast<const int32_t*>(dtab);
+        qp.k_q = reinterpret_cast<const int32_t*>(dtab + n8);
+        qp.kc_q = dtab + 2 * n8;
+        qp.probe_off = dtab + 3 * n8;
+        qp.region_off = dtab + 4 * n8;
+        qp.cand_off = dtab + 5 * n8;
+        qp.out_off = dtab + 6 * n8;
+        rc = run_sign_chunk(ix, p, c, ws, queries + q0 * ix->dev.d, nc, qp, out_ids + out_base, out_dists + out_base, st);
+        if (rc) return rc;
+        out_base += t_oo[nc];
+        q0 = q1;
+    }
     return BBC_OK;
 }
 
@@ -1140,7 +1221,7 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
 int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t* k, const int32_t* nprobe,
                   int64_t* out_ids, float* out_dists, void* stream) {
     if (!ix) return fail(BBC_ERR_ARG, "null index");
-    if (int rc0 = pq_only(ix, "bbc_search_ex")) return rc0;
+
     if (nq < 0) return fail(BBC_ERR_ARG, "nq < 0");
     if (nq == 0) return BBC_OK;
     if (!queries || !k || !nprobe || !out_ids || !out_dists) return fail(BBC_ERR_ARG, "null buffer");
@@ -1152,6 +1233,7 @@ int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t
     }
     DeviceGuard g(ix->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (ix->dev.quant == BBC_QUANT_SIGN) return search_sign_ex(ix, queries, nq, k, nprobe, out_ids, out_dists, st);
     const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
     int64_t out_base = 0;
     for (int64_t q0 = 0; q0 < nq;) {

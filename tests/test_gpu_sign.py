@@ -171,6 +171,31 @@ def test_host_entry_and_bound_scale(bbc):
     assert np.all(g >= 0) and np.all(np.diff(gd.cpu().numpy(), axis=1) >= 0)
 
 
+def test_sign_mixed_batch_equals_alone(bbc):
+    """Per-query k and nprobe in one bbc_search_ex call give what each query gives alone."""
+    h, idx, q = sign_index(bbc)
+    rng = np.random.default_rng(7)
+    nq = len(q)
+    ks = rng.choice([1, 50, 300, 2500], nq).astype(np.int32)
+    nps = rng.choice([4, 16, 40], nq).astype(np.int32)
+    tot = int(ks.sum())
+    oi = torch.empty(tot, dtype=torch.int64, device="cuda")
+    od = torch.empty(tot, dtype=torch.float32, device="cuda")
+    bbc.bbc_search_ex(h, cuda(q), nq, ks, nps, oi, od)
+    sync_ok(bbc, h)
+    oi, od = oi.cpu().numpy(), od.cpu().numpy()
+    off = 0
+    for i in range(nq):
+        k = int(ks[i])
+        ai = torch.empty((1, k), dtype=torch.int64, device="cuda")
+        ad = torch.empty((1, k), dtype=torch.float32, device="cuda")
+        bbc.bbc_search(h, cuda(q[i:i + 1]), 1, k, int(nps[i]), ai, ad)
+        sync_ok(bbc, h)
+        assert np.array_equal(oi[off:off + k], ai.cpu().numpy()[0]), f"query {i}"
+        assert np.array_equal(od[off:off + k], ad.cpu().numpy()[0]), f"query {i}"
+        off += k
+
+
 def test_pq_only_calls_refuse_sign_index(bbc):
     h, idx, q = sign_index(bbc)
     out = torch.empty(16, dtype=torch.int16, device="cuda")
