@@ -348,8 +348,8 @@ def main():
     index.set(buckets=args.buckets, workspace_mb=64 * 1024)
     float_data = not index.info["vectors_u8_exact"]
     precs = [int(v) for v in args.precision.split(",")] if args.precision else [2 if float_data else 0]
-    if index.info["quantizer"] == 1:
-        precs = [0]                                      # sign codes: the bounded re-rank has its own schedule
+    if index.info["quantizer"] == 1 and not args.precision:
+        precs = [0]                                      # sign codes: FP32 rounds unless a copy is asked for
     xt = torch.from_numpy(idx.vectors).to(dev)
     nprobes = [int(v) for v in args.nprobe.split(",")] if args.nprobe else [nprobe]
     ratios = [float(v) for v in str(args.kc_ratio).split(",")]

@@ -519,20 +519,51 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, const SignShape& c, char* w
     CUDA_TRY(cudaMemsetAsync(pa.qnorm, 0, (size_t)nc * sizeof(float), st));
     unsigned long long* keys = c.max_k > kTopkSmemMax ? reinterpret_cast<unsigned long long*>(ws + p.off_keys) : nullptr;
     RerankArgs ra{q, clist, n_c, qp.kc, 0, cd, c.max_k, out_ids, out_dists, keys, qp};
-    // round 1: the k smallest upper bounds
-    pa.rc_from = nullptr;
-    pa.rc_count = n_b;
-    CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_plan(nc, pa, st); }));
-    CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_recheck(d, nc, ra, pa, st); }));
-    // round 2: the rest of S whose lower bound reaches the largest upper bound of round 1
-    CUDA_TRY(stage(ix, 4, st, [&] { return launch_sign_filter(d, nc, ss, st); }));
-    pa.rc_from = n_b;
-    pa.rc_count = n_c;
-    CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_plan(nc, pa, st); }));
-    CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_recheck(d, nc, ra, pa, st); }));
-    // exact order: FP32 with its bound, FP64 where the bound cannot decide
-    CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_classify(d, nc, ra, pa, st); }));
-    CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_finalize(d, nc, ra, pa, st); }));
+    if (d.prec > 0 && d.vec_lp) {
+        // both rounds scored from the low-precision copy with its bound; then the
+        // precision form's classification, FP32 recheck and FP64 decision
+        RerankArgs r1 = ra;
+        r1.cand_count = n_b;
+        r1.kc = c.max_k;
+        pa.sc_from = nullptr;
+        CUDA_TRY(stage(ix, 5, st, [&] { return launch_prec_score(d, nc, r1, pa, st); }));
+        CUDA_TRY(stage(ix, 4, st, [&] { return launch_sign_filter(d, nc, ss, st); }));
+        pa.sc_from = n_b;
+        CUDA_TRY(stage(ix, 5, st, [&] { return launch_prec_score(d, nc, ra, pa, st); }));
+        pa.sc_from = nullptr;
+        pa.copy_unc = 0;
+        pa.rc_ids = pa.unc;
+        pa.rc_from = nullptr;
+        pa.rc_count = pa.n_unc;
+        pa.rc_d = pa.unc_d;
+        pa.rc_r = pa.unc_r;
+        CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_classify(d, nc, ra, pa, st); }));
+        CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_plan(nc, pa, st); }));
+        CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_recheck(d, nc, ra, pa, st); }));
+        CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_finalize(d, nc, ra, pa, st); }));
+        // exact returned distances: the final members re-scored from the FP32 rows
+        RerankArgs rf = ra;
+        rf.cand = pa.fin_id;
+        rf.cand_count = pa.n_fin;
+        rf.cdist = pa.fin_d;
+        rf.kc = c.max_k;
+        CUDA_TRY(stage(ix, 8, st, [&] { return launch_rerank(d, nc, rf, st); }));
+    } else {
+        // round 1: the k smallest upper bounds
+        pa.rc_from = nullptr;
+        pa.rc_count = n_b;
+        CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_plan(nc, pa, st); }));
+        CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_recheck(d, nc, ra, pa, st); }));
+        // round 2: the rest of S whose lower bound reaches the largest upper bound of round 1
+        CUDA_TRY(stage(ix, 4, st, [&] { return launch_sign_filter(d, nc, ss, st); }));
+        pa.rc_from = n_b;
+        pa.rc_count = n_c;
+        CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_plan(nc, pa, st); }));
+        CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_recheck(d, nc, ra, pa, st); }));
+        // exact order: FP32 with its bound, FP64 where the bound cannot decide
+        CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_classify(d, nc, ra, pa, st); }));
+        CUDA_TRY(stage(ix, 7, st, [&] { return launch_prec_finalize(d, nc, ra, pa, st); }));
+    }
     RerankArgs rb = ra;
     rb.cand = pa.fin_id;
     rb.cdist = pa.fin_d;
@@ -1125,7 +1156,6 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
         if (!(v > 0.0 && v <= 1.0)) return fail(BBC_ERR_ARG, "bound_scale must be in (0, 1]");
         ix->bound_scale = (float)v;
     } else if (k == "precision") {
-        if (int rc0 = pq_only(ix, "precision")) return rc0;
         if (v != 0 && v != 1 && v != 2)
             return fail(BBC_ERR_ARG, "precision must be 0 (FP32 re-rank), 1 (BF16 copy) or 2 (FP8-E4M3 copy)");
         return build_precision(ix, (int)v);

@@ -197,6 +197,7 @@ struct PrecArgs {
     int copy_unc;                 // classify copies cdist / rho of the uncertain ones to unc_d / unc_r
     const uint32_t* rc_ids;       // ids the FP32 recheck scores, per coff
     const int64_t* rc_from;       // [nq] first position to score (null: 0)
+    const int64_t* sc_from;       // [nq] first candidate the copy scores (pass 1; null: 0)
     const int64_t* rc_count;      // [nq] end position
     float* rc_d;                  // FP32 distances written by the recheck
     float* rc_r;                  // and their bounds

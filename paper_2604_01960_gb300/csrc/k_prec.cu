@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(PS_THREADS) prec_score_kernel(DevIndex ix, Rer
     const bool l2 = ix.metric == BBC_METRIC_L2;
     const int64_t cnt = min(a.cand_count[qi], a.qp.KC(qi));
     const int ln = (int)lane_id(), grp = ln / G, gl = ln % G, per_warp = 32 / G;
-    const int64_t c0 = (int64_t)blockIdx.x * PS_CAND_PER_CTA;
+    const int64_t c0 = (p.sc_from ? p.sc_from[qi] : 0) + (int64_t)blockIdx.x * PS_CAND_PER_CTA;
     const int64_t c1 = min(c0 + PS_CAND_PER_CTA, cnt);
     const uint32_t* cand = a.cand + a.qp.coff(qi);
     float* out = a.cdist + a.qp.coff(qi);

@@ -171,6 +171,31 @@ def test_host_entry_and_bound_scale(bbc):
     assert np.all(g >= 0) and np.all(np.diff(gd.cpu().numpy(), axis=1) >= 0)
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("k,nprobe", [(50, 8), (2000, 40)])
+def test_sign_search_with_low_precision_copy(bbc, oracle_lib, prec, k, nprobe):
+    """The bounded re-rank scored from a BF16 / FP8 copy returns the same exact
+    top-k with FP32 distances."""
+    h, idx, q = sign_index(bbc)
+    nq = len(q)
+    gi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    gd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    bbc.bbc_set_param(h, "precision", prec)
+    try:
+        bbc.bbc_search(h, cuda(q), nq, k, nprobe, gi, gd)
+        sync_ok(bbc, h)
+    finally:
+        bbc.bbc_set_param(h, "precision", 0)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    oi, _, _ = oracle_lib.sign_search(idx, q, k, nprobe)
+    for i in range(nq):
+        assert set(gi[i].tolist()) == set(oi[i].tolist()), f"query {i}: result set"
+        v = gd[i].astype(np.float64)
+        assert np.all(np.diff(v) >= 0)
+        d64 = oracle_lib.rerank(q[i], idx.vectors, gi[i], "l2")
+        assert np.all(np.abs(v - d64) <= RTOL * np.maximum(d64, 1e-3 * float(d64.max())))
+
+
 def test_sign_mixed_batch_equals_alone(bbc):
     """Per-query k and nprobe in one bbc_search_ex call give what each query gives alone."""
     h, idx, q = sign_index(bbc)
@@ -201,6 +226,4 @@ def test_pq_only_calls_refuse_sign_index(bbc):
     out = torch.empty(16, dtype=torch.int16, device="cuda")
     with pytest.raises(bbc.BBCError, match="UNSUPPORTED"):
         bbc.bbc_lut(h, cuda(q[:1]), 1, out)
-    with pytest.raises(bbc.BBCError, match="UNSUPPORTED"):
-        bbc.bbc_set_param(h, "precision", 1)
     assert bbc.bbc_index_info(h)["quantizer"] == 1
