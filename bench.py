@@ -492,7 +492,12 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     if is_sign:
         # codes (d/8 bytes) + factors (16 bytes) per scanned object; rows of the exact re-rank
         work["scan"] = ("hbm", float(s_q.double().sum()) * (idx.d // 8 + 16) / 1e9, "GB/s", peaks["hbm_gbs"])
-        work["prec_recheck"] = ("hbm", bstats["exact"] * (idx.d * 4 + 8) / 1e9, "GB/s", peaks["hbm_gbs"])
+        if prec:
+            work["rerank"] = ("hbm", bstats["exact"] * (dpad * (2 if prec == 1 else 1) + 28) / 1e9, "GB/s",
+                              peaks["hbm_gbs"])
+            work["prec_recheck"] = ("hbm", (unc + nq * k) * (idx.d * 4 + 8) / 1e9, "GB/s", peaks["hbm_gbs"])
+        else:
+            work["prec_recheck"] = ("hbm", bstats["exact"] * (idx.d * 4 + 8) / 1e9, "GB/s", peaks["hbm_gbs"])
         work["select"] = ("hbm", bstats["scanned"] * 16 * 3 / 1e9, "GB/s", peaks["hbm_gbs"])
         work["prec_classify"] = ("hbm", bstats["exact"] * 12 * 5 / 1e9, "GB/s", peaks["hbm_gbs"])
         work["topk"] = ("hbm", nq * k * 20 / 1e9, "GB/s", peaks["hbm_gbs"])
@@ -527,7 +532,8 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     if rank == 0:
         rerank = ["u8-exact" if u8 else "f32", "bf16-prefilter", "fp8e4m3-prefilter"][prec]
         if is_sign:
-            rerank = "bounded, two rounds, f32 (f64 at ties)"
+            rerank = "bounded, two rounds, " + ["f32", "bf16 prefilter + f32", "e4m3 prefilter + f32"][prec] + \
+                " (f64 at ties)"
         out = {
             "metric": METRICS.get(args.workload, METRIC), "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
