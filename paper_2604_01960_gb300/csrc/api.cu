@@ -235,6 +235,7 @@ PrecArgs prec_args_rerank(const bbc_index* ix, char* base, int64_t nq, int64_t s
 }
 
 constexpr int64_t kTopkSmemMax = 16384;     // K_c handled by the shared-memory top-k
+constexpr int64_t kMaxChunkQueries = 65535;  // queries per launch (some grids index queries in y)
 
 size_t layout(const bbc_index* ix, const ChunkShape& c, Plan& p) {
     const DevIndex& d = ix->dev;
@@ -272,7 +273,7 @@ Plan make_plan(const bbc_index* ix, int64_t nq, int nprobe, int64_t kc, int k, b
         return s;
     };
     const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
-    int64_t c = std::max<int64_t>(1, nq);
+    int64_t c = std::max<int64_t>(1, std::min<int64_t>(nq, kMaxChunkQueries));
     Plan tmp = p;
     while (c > 1 && layout(ix, shape(c), tmp) > budget) c = (c + 1) / 2;
     p.chunk = c;
@@ -432,8 +433,8 @@ struct SignShape {
 };
 
 struct SignPlan {
-    size_t off_scores, off_abf, off_probe, off_qrot, off_region, off_small, off_clist, off_rkey, off_rid, off_cd,
-        off_cr, off_ud, off_ur, off_keys, off_prec, off_params, off_q, off_ids, off_dists, total;
+    size_t off_scores, off_abf, off_probe, off_qrot, off_prep, off_region, off_small, off_clist, off_rkey, off_rid,
+        off_cd, off_cr, off_ud, off_ur, off_keys, off_prec, off_params, off_q, off_ids, off_dists, total;
 };
 
 size_t sign_layout(const bbc_index* ix, const SignShape& c, SignPlan& p) {
@@ -444,6 +445,7 @@ size_t sign_layout(const bbc_index* ix, const SignShape& c, SignPlan& p) {
     p.off_abf = o; o = align_up(o + (ix->probe_gemm ? probe_tc_workspace(d, c.nq) : 0));
     p.off_probe = o; o = align_up(o + (size_t)c.sum_probe * 4);
     p.off_qrot = o; o = align_up(o + (size_t)c.nq * d.d * 8);
+    p.off_prep = o; o = align_up(o + sign_prep_bytes(d, c.sum_probe));
     p.off_region = o; o = align_up(o + slots * 16);
     p.off_small = o; o = align_up(o + (size_t)c.nq * 8 * 5);         // pushed, scanned, n_b, n_c, n_rest
     p.off_clist = o; o = align_up(o + slots * 4);
@@ -501,6 +503,7 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, const SignShape& c, char* w
     sa.qrot = qrot; sa.q = q; sa.lists = probe; sa.nprobe = c.max_probe; sa.k = c.max_k; sa.m = ix->buckets;
     sa.sample_min = ix->sample_lists; sa.scale = ix->bound_scale;
     sa.region = reinterpret_cast<uint4*>(ws + p.off_region); sa.cap = qp.cap; sa.pushed = pushed; sa.scanned = scanned;
+    sa.prep = reinterpret_cast<uint32_t*>(ws + p.off_prep);
     sa.qp = qp;
     CUDA_TRY(stage(ix, 3, st, [&] { return launch_sign_scan(d, nc, sa, st); }));
     SignSelectArgs ss{};
@@ -577,7 +580,7 @@ int search_sign(bbc_index* ix, const float* queries, int64_t nq, int k, int npro
                 float* out_dists, cudaStream_t st, bool host_io) {
     const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
     SignPlan p{};
-    int64_t chunk = std::max<int64_t>(1, nq);
+    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, kMaxChunkQueries));
     while (chunk > 1 && sign_layout(ix, sign_uniform_shape(ix, chunk, nprobe, k, host_io), p) > budget)
         chunk = (chunk + 1) / 2;
     const SignShape c = sign_uniform_shape(ix, chunk, nprobe, k, host_io);
@@ -622,7 +625,7 @@ int search_sign_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_
             t.nq += 1; t.sum_probe += nprobe[q1]; t.sum_cap += ix->cap_prefix[nprobe[q1]]; t.sum_k += k[q1];
             t.max_probe = std::max(t.max_probe, nprobe[q1]); t.max_k = std::max(t.max_k, k[q1]);
             SignPlan tp{};
-            if (q1 > q0 && sign_layout(ix, t, tp) > budget) break;
+            if (q1 > q0 && (sign_layout(ix, t, tp) > budget || t.nq > kMaxChunkQueries)) break;
             c = t;
             ++q1;
         }
@@ -1278,7 +1281,7 @@ int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t
             t.nq += 1; t.sum_probe += nprobe[q1]; t.sum_cap += ix->cap_prefix[nprobe[q1]]; t.sum_kc += kc;
             t.sum_k += k[q1]; t.max_probe = std::max(t.max_probe, nprobe[q1]); t.max_kc = std::max(t.max_kc, kc);
             Plan tp{};
-            if (q1 > q0 && layout(ix, t, tp) > budget) break;
+            if (q1 > q0 && (layout(ix, t, tp) > budget || t.nq > kMaxChunkQueries)) break;
             sh = t;
             ++q1;
         }
@@ -1572,7 +1575,7 @@ int bbc_rerank_topk(bbc_index* ix, const float* queries, int64_t nq, const uint3
         return o + 256;
     };
     const size_t budget = (size_t)(ix->workspace_mb * 1024.0 * 1024.0);
-    int64_t chunk = nq;
+    int64_t chunk = std::min<int64_t>(nq, kMaxChunkQueries);
     while (chunk > 1 && bytes(chunk) > budget) chunk = (chunk + 1) / 2;
     char* ws;
     int rc = get_workspace(ix, st, bytes(chunk), &ws);
@@ -1652,13 +1655,15 @@ int bbc_sign_bounds(bbc_index* ix, const float* queries, int64_t nq, int32_t npr
     cudaStream_t st = (cudaStream_t)stream;
     const DevIndex& d = ix->dev;
     char* ws;
-    if ((rc = get_workspace(ix, st, align_up((size_t)nq * d.d * 8), &ws))) return rc;
+    const size_t qb = align_up((size_t)nq * d.d * 8);
+    if ((rc = get_workspace(ix, st, qb + align_up(sign_prep_bytes(d, nq * (int64_t)nprobe)), &ws))) return rc;
     double* qrot = reinterpret_cast<double*>(ws);
     CUDA_TRY(stage(ix, 2, st, [&] { return launch_rotate_f64(queries, nullptr, nullptr, nullptr, d.rot, nq, d.d, qrot, st); }));
     SignArgs sa{};
     sa.qrot = qrot; sa.q = queries; sa.lists = probe_lists; sa.nprobe = nprobe; sa.k = 1; sa.m = ix->buckets;
     sa.sample_min = ix->sample_lists; sa.scale = ix->bound_scale; sa.cap = stride; sa.scanned = out_count;
     sa.dbg_lb = out_lb; sa.dbg_ub = out_ub;
+    sa.prep = reinterpret_cast<uint32_t*>(ws + qb);
     sa.qp = uniform_params(nprobe, stride, 1, stride);
     CUDA_TRY(stage(ix, 3, st, [&] { return launch_sign_scan(d, nq, sa, st); }));
     return BBC_OK;

@@ -256,8 +256,11 @@ struct SignArgs {
     int64_t* scanned;             // [nq]
     float* dbg_lb;                // bounds of every scanned object (debug form), per roff, or null
     float* dbg_ub;
+    uint32_t* prep;               // per (query, probed list) records, sign_prep_bytes(ix, sum of nprobe)
     QueryParams qp;
 };
+size_t sign_prep_bytes(const DevIndex& ix, int64_t sum_probe);
+// Query preparation per (query, probed list), then the scan with the result buffer.
 cudaError_t launch_sign_scan(const DevIndex& ix, int64_t nq, const SignArgs& a, cudaStream_t st);
 
 struct SignSelectArgs {

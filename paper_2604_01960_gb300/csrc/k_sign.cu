@@ -155,104 +155,104 @@ __global__ void sign_factors_kernel(const double* __restrict__ R, int64_t s0, in
 }
 
 // ---------------------------------------------------------------------------
-// The bounds.
+// Query preparation per (query, probed list), one warp each: q' = P q - P c_l
+// (FP64 difference rounded to FP32), its 4-bit levels as four bit planes, and
+// the list's scalars, written as one record of R = 4W + 8 words:
+//   [plane j word w] (j-major), lo, Delta, ||t||^2, ||t|| (up), eta sqrt(d)
+//   (up), ||q'|| (up), dterm, sum u.
+// Sums are FP32; each carries its rounding: a sum of squares of n terms
+// evaluated with chains of at most c roundings is within 2 c 2^-24 of the
+// exact value (relative), c = W + 8 here.
 // ---------------------------------------------------------------------------
 struct ListSetup {
     float lo, delta, tn2, tn, eta_sd, qn, dterm;
     int usum;
 };
 
-// Per-list query preparation (all threads of the CTA): q' in sq, the four bit
-// planes, and the list's scalars.  qnorm = ||q||.
-__device__ void sign_list_setup(const DevIndex& ix, const double* __restrict__ qrot, const float* __restrict__ q,
-                                float qnorm, int l, float* sq, uint32_t (*planes)[SG_MAXW], ListSetup* ls,
-                                double* redd, float* redf, int* redi) {
+__host__ __device__ inline int sign_rec_words(int d) { return 4 * (d / 32) + 8; }
+
+__global__ void sign_prep_kernel(DevIndex ix, SignArgs a, uint32_t* __restrict__ rec) {
+    const int64_t qi = blockIdx.y;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    const int P = a.qp.P(qi);
+    if (j >= P) return;
     const int d = ix.d, W = d / 32;
-    const int tid = threadIdx.x, nw = blockDim.x >> 5;
+    const unsigned ln = lane_id();
+    const int l = a.lists[a.qp.poff(qi) + j];
+    const double* qr = a.qrot + qi * d;
     const double* cr = ix.crot + (int64_t)l * d;
+    const float* q = a.q + qi * d;
     const float* c = ix.centroids + (int64_t)l * d;
-    double tn2 = 0.0, qn2 = 0.0;
-    float lo = INFINITY, hi = -INFINITY;
-    for (int i = tid; i < d; i += blockDim.x) {
-        const float f = (float)(qrot[i] - cr[i]);
-        sq[i] = f;
-        qn2 += (double)f * (double)f;
-        const double t = (double)q[i] - (double)c[i];
-        tn2 += t * t;
+    float qf[SG_MAXW];
+    float lo = INFINITY, hi = -INFINITY, qn2 = 0.f, tn2 = 0.f, qq2 = 0.f;
+#pragma unroll 4
+    for (int w = 0; w < W; ++w) {
+        const int i = w * 32 + (int)ln;
+        const float f = (float)(qr[i] - cr[i]);
+        qf[w] = f;
         lo = fminf(lo, f);
         hi = fmaxf(hi, f);
+        qn2 = fmaf(f, f, qn2);
+        const float t = q[i] - c[i];
+        tn2 = fmaf(t, t, tn2);
+        qq2 = fmaf(q[i], q[i], qq2);
     }
-    for (int s = 16; s; s >>= 1) {
-        tn2 += __shfl_xor_sync(0xFFFFFFFFu, tn2, s);
-        qn2 += __shfl_xor_sync(0xFFFFFFFFu, qn2, s);
-        lo = fminf(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, s));
-        hi = fmaxf(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, s));
+    for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+        qn2 += __shfl_xor_sync(0xFFFFFFFFu, qn2, o);
+        tn2 += __shfl_xor_sync(0xFFFFFFFFu, tn2, o);
+        qq2 += __shfl_xor_sync(0xFFFFFFFFu, qq2, o);
     }
-    if (lane_id() == 0) {
-        redd[warp_id() * 3 + 0] = tn2;
-        redd[warp_id() * 3 + 1] = qn2;
-        redf[warp_id() * 2 + 0] = lo;
-        redf[warp_id() * 2 + 1] = hi;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        float l0 = INFINITY, h0 = -INFINITY;
-        for (int w = 0; w < nw; ++w) {
-            a += redd[w * 3 + 0];
-            b += redd[w * 3 + 1];
-            l0 = fminf(l0, redf[w * 2 + 0]);
-            h0 = fmaxf(h0, redf[w * 2 + 1]);
-        }
-        ls->lo = l0;
-        ls->delta = (h0 - l0) / 15.f;
-        ls->tn2 = (float)a;
-        ls->tn = __double2float_ru(sqrt(a) * (1.0 + 1e-12));
-        ls->qn = __double2float_ru(sqrt(b) * (1.0 + 1e-12));
-        // ||q' - P t||: FP32 rounding of q' plus the FP64 products (about d^1.5 2^-53 (||q|| + ||c||))
-        ls->dterm = 2.384185791015625e-7f * ls->qn + 1e-10f * (qnorm + sqrtf(ix.cnorm[l]));
-    }
-    __syncthreads();
-    const float lo0 = ls->lo, dl = ls->delta;
-    double eta2 = 0.0;
+    const float g = 2.f * (float)(W + 8) * 5.9604644775390625e-8f;
+    const float delta = (hi - lo) / 15.f;
+    const float inv = delta > 0.f ? 1.f / delta : 0.f;
+    uint32_t* out = rec + (a.qp.poff(qi) + j) * (int64_t)sign_rec_words(d);
+    float e2 = 0.f;
     int usum = 0;
-    for (int w = warp_id(); w < W; w += nw) {
-        const int i = w * 32 + lane_id();
-        const float f = sq[i];
+#pragma unroll 4
+    for (int w = 0; w < W; ++w) {
         int u = 0;
-        if (dl > 0.f) {
-            const float v = rintf((f - lo0) / dl);
+        if (delta > 0.f) {
+            const float v = rintf((qf[w] - lo) * inv);
             u = v < 0.f ? 0 : (v > 15.f ? 15 : (int)v);
         }
-        const double df = (double)f - ((double)lo0 + (double)dl * (double)u);
-        eta2 += df * df;
+        const float df = qf[w] - fmaf(delta, (float)u, lo);
+        e2 = fmaf(df, df, e2);
         usum += u;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const unsigned bits = __ballot_sync(0xFFFFFFFFu, (u >> j) & 1);
-            if (lane_id() == 0) planes[j][w] = bits;
+        for (int jj = 0; jj < 4; ++jj) {
+            const unsigned bits = __ballot_sync(0xFFFFFFFFu, (u >> jj) & 1);
+            if (ln == (unsigned)(w & 31)) out[jj * W + w] = bits;
         }
     }
-    for (int s = 16; s; s >>= 1) {
-        eta2 += __shfl_xor_sync(0xFFFFFFFFu, eta2, s);
-        usum += __shfl_xor_sync(0xFFFFFFFFu, usum, s);
+    for (int o = 16; o; o >>= 1) {
+        e2 += __shfl_xor_sync(0xFFFFFFFFu, e2, o);
+        usum += __shfl_xor_sync(0xFFFFFFFFu, usum, o);
     }
-    if (lane_id() == 0) { redd[warp_id() * 3 + 2] = eta2; redi[warp_id()] = usum; }
-    __syncthreads();
-    if (tid == 0) {
-        double e = 0.0;
-        int us = 0;
-        for (int w = 0; w < nw; ++w) { e += redd[w * 3 + 2]; us += redi[w]; }
-        ls->eta_sd = __double2float_ru(sqrt(e * (double)d) * (1.0 + 1e-12));
-        ls->usum = us;
+    if (ln == 0) {
+        const float up = 1.f + 2.384185791015625e-7f;                    // 1 + 2^-22 for the square roots
+        const float qn = sqrtf(qn2 * (1.f + g)) * up;
+        // eta = ||q' - (lo + Delta u)||: each difference carries two roundings
+        const float eta = sqrtf(e2 * (1.f + g)) * (1.f + 2.5e-7f) + 2.5e-7f * qn;
+        float* fo = reinterpret_cast<float*>(out + 4 * W);
+        fo[0] = lo;
+        fo[1] = delta;
+        fo[2] = tn2;
+        fo[3] = sqrtf(tn2 * (1.f + g)) * up;
+        fo[4] = eta * sqrtf((float)d) * up;
+        fo[5] = qn;
+        // ||q' - P t||: FP32 rounding of q' plus the FP64 products (about d^1.5 2^-53 (||q|| + ||c||))
+        fo[6] = 2.384185791015625e-7f * qn + 1e-10f * (sqrtf(qq2) * up + sqrtf(ix.cnorm[l]) * up);
+        reinterpret_cast<int*>(out)[4 * W + 7] = usum;
     }
-    __syncthreads();
 }
 
-// Bounds of the object in slot (codes in the block layout), with the planes
-// and scalars of its list.
-__device__ __forceinline__ void sign_bound(const DevIndex& ix, int64_t slot, const uint32_t (*planes)[SG_MAXW],
-                                           const ListSetup& ls, float scale, float eps, float& lb, float& ub) {
+// Bounds of the object in slot (codes in the block layout) against the
+// prepared list (planes in this warp's shared memory, scalars in registers).
+__device__ __forceinline__ void sign_bound(const DevIndex& ix, int64_t slot, const uint32_t* planes,
+                                           const ListSetup& ls, float scale, float eps, float g_t, float& lb,
+                                           float& ub) {
     const int W = ix.d >> 5;
     const int64_t blk = slot >> 5;
     const int t = (int)(slot & 31);
@@ -261,8 +261,8 @@ __device__ __forceinline__ void sign_bound(const DevIndex& ix, int64_t slot, con
 #pragma unroll 6
     for (int w = 0; w < W; ++w) {
         const uint32_t c = __ldg(cw + w * 32);
-        s2 += __popc(planes[0][w] & c) + 2 * __popc(planes[1][w] & c) + 4 * __popc(planes[2][w] & c) +
-              8 * __popc(planes[3][w] & c);
+        s2 += __popc(planes[w] & c) + 2 * __popc(planes[W + w] & c) + 4 * __popc(planes[2 * W + w] & c) +
+              8 * __popc(planes[3 * W + w] & c);
     }
     const float4 f = __ldg(ix.sfac + slot);
     const float S1 = 2.f * f.w - (float)ix.d;
@@ -276,7 +276,8 @@ __device__ __forceinline__ void sign_bound(const DevIndex& ix, int64_t slot, con
     const float H = fabsf(alpha) * eX + scale * (fabsf(alpha) * ls.eta_sd + ls.qn * e) + ls.dterm * un * (1.f + eps);
     const float base = ls.tn2 + un2;
     const float rotE = 2.f * eps * ls.tn * un;
-    const float slack = 9.5367431640625e-7f * (base + 2.f * fabsf(est) + 2.f * H + rotE);   // 2^-20
+    // 2^-20 relative for the FP32 evaluation here, g_t for the FP32 sum ||t||^2
+    const float slack = 9.5367431640625e-7f * (base + 2.f * fabsf(est) + 2.f * H + rotE) + g_t * ls.tn2;
     lb = fmaxf(base - 2.f * (est + H) - rotE - slack, 0.f);
     ub = base - 2.f * (est - H) + rotE + slack;
 }
@@ -296,42 +297,58 @@ __device__ __forceinline__ uint32_t sg_append(bool take, uint32_t* counter) {
     return base + __popc(m & ((1u << ln) - 1u));
 }
 
+// This warp takes list j: planes into its shared slot, scalars into registers.
+__device__ __forceinline__ ListSetup sign_load_list(const uint32_t* __restrict__ rec, int R, int W, uint32_t* planes) {
+    for (int w = (int)lane_id(); w < 4 * W; w += 32) planes[w] = rec[w];
+    const float* fo = reinterpret_cast<const float*>(rec + 4 * W);
+    ListSetup ls;
+    ls.lo = fo[0]; ls.delta = fo[1]; ls.tn2 = fo[2]; ls.tn = fo[3]; ls.eta_sd = fo[4]; ls.qn = fo[5]; ls.dterm = fo[6];
+    ls.usum = reinterpret_cast<const int*>(rec)[4 * W + 7];
+    __syncwarp();
+    (void)R;
+    return ls;
+}
+
+// Largest key whose bucket is <= t (buckets are monotone in the bin).
+__device__ __forceinline__ uint32_t sg_key_tau(const uint8_t* map, uint32_t dmin, int sh, uint32_t t) {
+    const unsigned ln = lane_id();
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c += map[ln * 8 + i] <= t ? 1u : 0u;
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if (c >= 256u) return 0xFFFFFFFFu;
+    const unsigned long long v = (unsigned long long)dmin + ((unsigned long long)c << sh) - 1ull;
+    return v > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)v;
+}
+
 // ---------------------------------------------------------------------------
-// Scan + result buffer on the upper bounds (one CTA per query).  DEBUG: write
-// the bounds of every scanned object in probe order instead.
+// Scan + result buffer on the upper bounds (one CTA per query, one warp per
+// list at a time).  DEBUG: write the bounds of every scanned object in probe
+// order instead.
 // ---------------------------------------------------------------------------
 template <bool DEBUG>
-__global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, SignArgs a) {
-    extern __shared__ float sq[];                          // d floats
-    __shared__ uint32_t planes[4][SG_MAXW];
-    __shared__ ListSetup ls;
-    __shared__ double redd[(SG_THREADS / 32) * 3];
-    __shared__ float redf[(SG_THREADS / 32) * 2];
-    __shared__ int redi[SG_THREADS / 32];
+__global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, SignArgs a, const uint32_t* rec) {
+    extern __shared__ uint32_t spl[];                      // [warps][4W] planes, then [P + 1] prefixes (DEBUG)
     __shared__ uint32_t hist[256];
     __shared__ uint32_t sc[2];
     __shared__ uint8_t smap[256];
-    __shared__ uint32_t s_cnt, s_tau, s_dmin, s_over;
+    __shared__ uint32_t s_cnt, s_tau, s_ktau, s_dmin, s_over;
     __shared__ int s_sh, s_ns;
     __shared__ int64_t s_sq;
-    __shared__ float s_qnorm;
     const int64_t qi = blockIdx.x;
-    const int d = ix.d;
+    const int d = ix.d, W = d / 32, R = sign_rec_words(d);
     const int P = a.qp.P(qi);
     const int kq = a.qp.K(qi);
     const int m = a.m;
     const int32_t* lists = a.lists + a.qp.poff(qi);
+    const uint32_t* qrec = rec + a.qp.poff(qi) * (int64_t)R;
     uint4* region = a.region + a.qp.roff(qi);
     const int64_t cap = a.qp.rcap(qi);
-    const double* qrot = a.qrot + qi * d;
-    const float* q = a.q + qi * d;
     const float eps = (float)(ix.eps_p * (1.0 + 1e-6)) + 1e-12f;
+    const float g_t = 2.f * (float)(W + 8) * 5.9604644775390625e-8f;
     const int tid = threadIdx.x, nw = blockDim.x >> 5;
+    uint32_t* planes = spl + warp_id() * 4 * W;
     if (tid == 0) {
-        double qq = 0.0;
-        for (int i = 0; i < d; ++i) qq += (double)q[i] * (double)q[i];
-        s_qnorm = __double2float_ru(sqrt(qq) * (1.0 + 1e-12));
-        // sample plan: at least min(sample_min, P) lists, extended to min(k, S_q) objects
         int64_t sqn = 0;
         for (int j = 0; j < P; ++j) sqn += ix.list_len[lists[j]];
         s_sq = sqn;
@@ -344,25 +361,30 @@ __global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, Sign
         s_cnt = 0;
         s_over = 0;
         s_tau = (uint32_t)m;
+        s_ktau = 0xFFFFFFFFu;
+        if (DEBUG) {
+            int64_t* pre = reinterpret_cast<int64_t*>(spl + nw * 4 * W + (nw * 4 * W) % 2);
+            int64_t b = 0;
+            for (int j = 0; j < P; ++j) { pre[j] = b; b += ix.list_len[lists[j]]; }
+        }
     }
     __syncthreads();
-    const float qnorm = s_qnorm;
     if (DEBUG) {
-        int64_t base = 0;
-        for (int j = 0; j < P; ++j) {
+        const int64_t* pre = reinterpret_cast<const int64_t*>(spl + nw * 4 * W + (nw * 4 * W) % 2);
+        for (int j = warp_id(); j < P; j += nw) {
             const int l = lists[j];
-            sign_list_setup(ix, qrot, q, qnorm, l, sq, planes, &ls, redd, redf, redi);
+            const ListSetup ls = sign_load_list(qrec + (int64_t)j * R, R, W, planes);
             const int len = ix.list_len[l];
             const int64_t b0 = ix.list_blk[l];
-            for (int p = tid; p < len; p += blockDim.x) {
+            for (int p = (int)lane_id(); p < len; p += 32) {
                 float lb, ub;
-                sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, lb, ub);
-                if (base + p < cap) {
-                    a.dbg_lb[a.qp.roff(qi) + base + p] = lb;
-                    a.dbg_ub[a.qp.roff(qi) + base + p] = ub;
+                sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, g_t, lb, ub);
+                if (pre[j] + p < cap) {
+                    a.dbg_lb[a.qp.roff(qi) + pre[j] + p] = lb;
+                    a.dbg_ub[a.qp.roff(qi) + pre[j] + p] = ub;
                 }
             }
-            base += len;
+            __syncwarp();
         }
         if (tid == 0) {
             a.scanned[qi] = s_sq;
@@ -372,22 +394,22 @@ __global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, Sign
     }
     // ---- sample: upper-bound keys of the first lists ----
     const int ns = s_ns;
-    for (int j = 0; j < ns; ++j) {
+    for (int j = warp_id(); j < ns; j += nw) {
         const int l = lists[j];
-        sign_list_setup(ix, qrot, q, qnorm, l, sq, planes, &ls, redd, redf, redi);
+        const ListSetup ls = sign_load_list(qrec + (int64_t)j * R, R, W, planes);
         const int len = ix.list_len[l];
         const int64_t b0 = ix.list_blk[l];
-        const int nb = (len + 31) >> 5;
-        for (int b = warp_id(); b < nb; b += nw) {
-            const int p = b * 32 + (int)lane_id();
+        for (int b = 0; b < len; b += 32) {
+            const int p = b + (int)lane_id();
             const bool valid = p < len;
             float lb = 0.f, ub = 0.f;
-            if (valid) sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, lb, ub);
+            if (valid) sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, g_t, lb, ub);
             const uint32_t pos = sg_append(valid, &s_cnt);
             if (valid && pos < cap) region[pos] = make_uint4(0u, f32_key(ub), 0u, 0u);
         }
-        __syncthreads();
+        __syncwarp();
     }
+    __syncthreads();
     // ---- codebook: d_min, d_max = t-th smallest sampled key, equal-depth map ----
     const int64_t nsamp = min((int64_t)s_cnt, cap);
     if (nsamp > 0) {
@@ -432,43 +454,59 @@ __global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, Sign
         __syncthreads();
     }
     for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
-    if (tid == 0) { s_cnt = 0; s_tau = (uint32_t)m; }
+    if (tid == 0) { s_cnt = 0; s_tau = (uint32_t)m; s_ktau = 0xFFFFFFFFu; }
     __syncthreads();
     const uint32_t dmin = s_dmin;
     const int sh = s_sh;
     // ---- main pass: histogram on the upper bound, push on the lower bound ----
-    for (int j = 0; j < P; ++j) {
+    for (int j = warp_id(); j < P; j += nw) {
         const int l = lists[j];
-        sign_list_setup(ix, qrot, q, qnorm, l, sq, planes, &ls, redd, redf, redi);
+        const ListSetup ls = sign_load_list(qrec + (int64_t)j * R, R, W, planes);
         const int len = ix.list_len[l];
         const int64_t b0 = ix.list_blk[l];
-        const int nb = (len + 31) >> 5;
-        const uint32_t tau = s_tau;
-        for (int b = warp_id(); b < nb; b += nw) {
-            const int p = b * 32 + (int)lane_id();
+        const uint32_t ktau = *(volatile uint32_t*)&s_ktau;
+        for (int b = 0; b < len; b += 32) {
+            const int p = b + (int)lane_id();
             const bool valid = p < len;
             float lb = 0.f, ub = 0.f;
-            if (valid) sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, lb, ub);
+            if (valid) sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, g_t, lb, ub);
             const uint32_t ubk = f32_key(ub), lbk = f32_key(lb);
             if (valid) atomicAdd(&hist[sg_bucket(ubk, dmin, sh, smap)], 1u);
-            const bool push = valid && sg_bucket(lbk, dmin, sh, smap) <= tau;
+            const bool push = valid && lbk <= ktau;         // bucket(lb) <= tau
             const uint32_t pos = sg_append(push, &s_cnt);
             if (push) {
                 if (pos < cap) region[pos] = make_uint4(lbk, ubk, (uint32_t)(b0 * 32 + p), 0u);
                 else s_over = 1;
             }
         }
-        __syncthreads();
-        if (tid == 0) {                                     // Update: first bucket reaching k
-            uint32_t run = 0, t = (uint32_t)m;
-            for (int i = 0; i < m; ++i) {
-                run += hist[i];
-                if (run >= (uint32_t)kq) { t = (uint32_t)i; break; }
-            }
-            s_tau = min(s_tau, t);
+        // Update from the shared counts (this warp), then the push threshold
+        uint32_t h8[8], s = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int bk = (int)lane_id() * 8 + i;
+            h8[i] = bk < m ? *(volatile uint32_t*)&hist[bk] : 0u;
+            s += h8[i];
         }
-        __syncthreads();
+        const uint32_t inc = warp_incl_scan(s);
+        const unsigned hit = __ballot_sync(0xFFFFFFFFu, inc >= (uint32_t)kq);
+        uint32_t t = (uint32_t)m;
+        if (hit) {
+            const unsigned src = __ffs(hit) - 1;
+            uint32_t bk = 0;
+            if (lane_id() == src) {
+                uint32_t cum = inc - s;
+                for (int i = 0; i < 8; ++i) {
+                    cum += h8[i];
+                    if (cum >= (uint32_t)kq) { bk = lane_id() * 8 + i; break; }
+                }
+            }
+            t = __shfl_sync(0xFFFFFFFFu, bk, src);
+        }
+        const uint32_t kt = sg_key_tau(smap, dmin, sh, t);
+        if (lane_id() == 0) { atomicMin(&s_tau, t); atomicMin(&s_ktau, kt); }
+        __syncwarp();
     }
+    __syncthreads();
     if (tid == 0) {
         a.pushed[qi] = min((int64_t)s_cnt, cap);
         a.scanned[qi] = s_sq;
@@ -572,12 +610,31 @@ cudaError_t launch_sign_factors(const double* R, int64_t s0, int64_t n, int d, c
     return cudaGetLastError();
 }
 
+size_t sign_prep_bytes(const DevIndex& ix, int64_t sum_probe) {
+    return (size_t)sum_probe * (size_t)sign_rec_words(ix.d) * 4;
+}
+
 cudaError_t launch_sign_scan(const DevIndex& ix, int64_t nq, const SignArgs& a, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
-    if (ix.d % 32 || ix.d > 32 * SG_MAXW) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)ix.d * sizeof(float);
-    if (a.dbg_lb) sign_scan_kernel<true><<<(unsigned)nq, SG_THREADS, smem, st>>>(ix, a);
-    else sign_scan_kernel<false><<<(unsigned)nq, SG_THREADS, smem, st>>>(ix, a);
+    if (ix.d % 32 || ix.d > 32 * SG_MAXW || !a.prep) return cudaErrorInvalidValue;
+    const int wpb = 8;
+    dim3 pg((unsigned)((a.nprobe + wpb - 1) / wpb), (unsigned)nq);
+    sign_prep_kernel<<<pg, 32 * wpb, 0, st>>>(ix, a, a.prep);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nw = SG_THREADS / 32;
+    size_t smem = (size_t)nw * 4 * (ix.d / 32) * 4 + 8;
+    if (a.dbg_lb) smem += (size_t)(a.nprobe + 1) * 8;
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(sign_scan_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(sign_scan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (smem > 64 * 1024) return cudaErrorInvalidValue;
+    if (a.dbg_lb) sign_scan_kernel<true><<<(unsigned)nq, SG_THREADS, smem, st>>>(ix, a, a.prep);
+    else sign_scan_kernel<false><<<(unsigned)nq, SG_THREADS, smem, st>>>(ix, a, a.prep);
     return cudaGetLastError();
 }
 
