@@ -520,22 +520,35 @@ __global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, Sign
 __global__ void __launch_bounds__(SG_THREADS) sign_select_kernel(DevIndex ix, SignSelectArgs a) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t sc[2];
-    __shared__ uint32_t s_b, s_r;
+    __shared__ uint32_t s_b, s_r, s_lt, s_eq;
     const int64_t qi = blockIdx.x;
     const int64_t n = a.pushed[qi];
     const int64_t kq = a.qp.K(qi);
     const int64_t off = a.qp.coff(qi);
     const uint4* reg = a.region + a.qp.roff(qi);
-    if (threadIdx.x == 0) { s_b = 0; s_r = 0; }
+    if (threadIdx.x == 0) { s_b = 0; s_r = 0; s_lt = 0; s_eq = 0; }
     __syncthreads();
     const bool all = a.scanned[qi] <= kq;                   // every scanned object is a result
-    uint32_t uk = 0xFFFFFFFFu;
-    unsigned long long kth = ~0ull;
+    uint32_t uk = 0xFFFFFFFFu, slot_cut = 0xFFFFFFFFu;
     if (!all && n > 0) {
+        // U_k, then the k smallest (ub, slot): all of ub < U_k and, among ub == U_k,
+        // the smallest slots (selected only when U_k is shared)
         const uint32_t r = (uint32_t)(min(n, kq) - 1);
         uk = cta_select_u32(n, r, [&](int64_t i) { return reg[i].y; }, hist, sc, 24);
-        kth = cta_select_u64(n, r, [&](int64_t i) { return ((unsigned long long)reg[i].y << 32) | reg[i].z; },
-                             hist, sc, 56);
+        uint32_t lt = 0, eq = 0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t y = reg[i].y;
+            lt += y < uk ? 1u : 0u;
+            eq += y == uk ? 1u : 0u;
+        }
+        lt = __reduce_add_sync(0xFFFFFFFFu, lt);
+        eq = __reduce_add_sync(0xFFFFFFFFu, eq);
+        if (lane_id() == 0) { atomicAdd(&s_lt, lt); atomicAdd(&s_eq, eq); }
+        __syncthreads();
+        const uint32_t want = r + 1 - s_lt;                 // >= 1: members taken at U_k
+        if (want < s_eq)
+            slot_cut = cta_select_u32(n, want - 1, [&](int64_t i) { return reg[i].y == uk ? reg[i].z : 0xFFFFFFFFu; },
+                                      hist, sc, 24);
     }
     const int64_t n_pad = (n + 31) / 32 * 32;
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
@@ -543,7 +556,7 @@ __global__ void __launch_bounds__(SG_THREADS) sign_select_kernel(DevIndex ix, Si
         uint4 e = make_uint4(0, 0, 0, 0);
         if (i < n) {
             e = reg[i];
-            inb = all || (((unsigned long long)e.y << 32) | e.z) <= kth;
+            inb = all || e.y < uk || (e.y == uk && e.z <= slot_cut);
             inr = !inb && e.x <= uk;
         }
         const uint32_t sb = sg_append(inb, &s_b);
