@@ -128,6 +128,7 @@ struct bbc_index {
     std::vector<Rec> recs;
     int64_t launches = 0;
     std::map<cudaStream_t, Workspace> ws;
+    cudaStream_t copy_stream = nullptr;   // host entry points: results copied out while the next part computes
 
     ~bbc_index() {
         int prev = -1;
@@ -135,6 +136,7 @@ struct bbc_index {
         cudaSetDevice(device);
         for (auto& kv : graph_cache) cudaGraphExecDestroy(kv.second.exec);
         for (auto& kv : ws) cudaFree(kv.second.base);
+        if (copy_stream) cudaStreamDestroy(copy_stream);
         for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (void* p : owned) cudaFree(p);
         cudaFree(lp_rows);
@@ -1353,18 +1355,56 @@ int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, 
     char* ws;
     if ((rc = get_workspace(ix, st, p.total, &ws))) return rc;
     const int d = ix->dev.d;
-    float* dq = reinterpret_cast<float*>(ws + p.off_q);
-    int64_t* di = reinterpret_cast<int64_t*>(ws + p.off_ids);
-    float* dd = reinterpret_cast<float*>(ws + p.off_dists);
-    for (int64_t q0 = 0; q0 < nq; q0 += p.chunk) {
-        const int64_t nc = std::min(p.chunk, nq - q0);
-        CUDA_TRY(cudaMemcpyAsync(dq, queries + q0 * d, (size_t)nc * d * 4, cudaMemcpyHostToDevice, st));
-        rc = run_chunk(ix, p, ws, dq, nc, di, dd, st, 9);
-        if (rc) return rc;
-        CUDA_TRY(cudaMemcpyAsync(out_ids + q0 * k, di, (size_t)nc * k * 8, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(cudaMemcpyAsync(out_dists + q0 * k, dd, (size_t)nc * k * 4, cudaMemcpyDeviceToHost, st));
+    // Sub-batches whose results go back on a second stream while the next
+    // sub-batch computes: a sub-batch keeps >= 8 queries per SM (one CTA per
+    // query fills the GPU), two result buffers alternate.
+    int64_t sb = std::max<int64_t>(8ll * ix->dev.num_sms, (nq + 3) / 4);
+    sb = std::min<int64_t>(sb, std::max<int64_t>(1, p.chunk / 2));
+    const int nbuf = 2 * sb <= p.chunk ? 2 : 1;
+    if (nbuf == 1) sb = p.chunk;
+    {
+        std::lock_guard<std::mutex> lk(ix->mu);
+        if (!ix->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&ix->copy_stream, cudaStreamNonBlocking));
     }
-    CUDA_TRY(cudaStreamSynchronize(st));
+    cudaStream_t cs = ix->copy_stream;
+    cudaEvent_t done[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    auto cleanup = [&]() {
+        for (int b = 0; b < 2; ++b) {
+            if (done[b]) cudaEventDestroy(done[b]);
+            if (freed[b]) cudaEventDestroy(freed[b]);
+        }
+    };
+    for (int b = 0; b < nbuf; ++b) {
+        if (cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&freed[b], cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return fail(BBC_ERR_CUDA, "event creation failed");
+        }
+    }
+    int it = 0;
+    for (int64_t q0 = 0; q0 < nq; q0 += sb, ++it) {
+        const int64_t nc = std::min(sb, nq - q0);
+        const int b = it % nbuf;
+        float* dq = reinterpret_cast<float*>(ws + p.off_q) + (size_t)b * sb * d;
+        int64_t* di = reinterpret_cast<int64_t*>(ws + p.off_ids) + (size_t)b * sb * k;
+        float* dd = reinterpret_cast<float*>(ws + p.off_dists) + (size_t)b * sb * k;
+        cudaError_t e = cudaSuccess;
+        if (it >= nbuf) e = cudaStreamWaitEvent(st, freed[b], 0);       // buffer b copied out
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dq, queries + q0 * d, (size_t)nc * d * 4, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { cleanup(); return fail(BBC_ERR_CUDA, "copy-in: %s", cudaGetErrorString(e)); }
+        rc = run_chunk(ix, p, ws, dq, nc, di, dd, st, 9);
+        if (rc) { cleanup(); return rc; }
+        e = cudaEventRecord(done[b], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, done[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out_ids + q0 * k, di, (size_t)nc * k * 8, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out_dists + q0 * k, dd, (size_t)nc * k * 4, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(freed[b], cs);
+        if (e != cudaSuccess) { cleanup(); return fail(BBC_ERR_CUDA, "copy-out: %s", cudaGetErrorString(e)); }
+    }
+    cudaError_t e = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return fail(BBC_ERR_CUDA, "synchronise: %s", cudaGetErrorString(e));
     return BBC_OK;
 }
 

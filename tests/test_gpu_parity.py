@@ -274,6 +274,16 @@ def test_host_entry_point_matches_device(bbc):
     bbc.bbc_search_host(h, hq, nq, k, 16, hi, hd)
     sync_ok(bbc, h)
     assert torch.equal(hi, ids.cpu()) and torch.equal(hd, dd.cpu())
+    # a small workspace: many sub-batches whose result buffers alternate while copies overlap
+    bbc.bbc_set_param(h, "workspace_mb", 8)
+    try:
+        hi2 = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+        hd2 = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+        bbc.bbc_search_host(h, hq, nq, k, 16, hi2, hd2)
+        sync_ok(bbc, h)
+    finally:
+        bbc.bbc_set_param(h, "workspace_mb", 8192)
+    assert torch.equal(hi2, ids.cpu()) and torch.equal(hd2, dd.cpu())
 
 
 def test_chunked_workspace_same_result(bbc):
