@@ -275,7 +275,7 @@ def test_host_entry_point_matches_device(bbc):
     sync_ok(bbc, h)
     assert torch.equal(hi, ids.cpu()) and torch.equal(hd, dd.cpu())
     # a small workspace: many sub-batches whose result buffers alternate while copies overlap
-    bbc.bbc_set_param(h, "workspace_mb", 8)
+    bbc.bbc_set_param(h, "workspace_mb", 1)
     try:
         hi2 = torch.empty((nq, k), dtype=torch.int64).pin_memory()
         hd2 = torch.empty((nq, k), dtype=torch.float32).pin_memory()
