@@ -49,7 +49,10 @@ struct ScanCfg {
     static constexpr int CBP = (CB + 15) / 16 * 16;
     static constexpr int NCH = CBP / 16;
     static constexpr int LUT_WORDS = K * W;
-    static constexpr int CHUNK = NCH <= 2 ? 4 : (NCH <= 4 ? 2 : 1);
+    // 32-vector blocks per warp iteration (their code loads in flight together)
+    static constexpr int CHUNK = NCH <= 2 ? 4 : (NCH <= 6 ? 2 : 1);
+    // CTAs per SM the shared-memory table allows (the launch bound for registers)
+    static constexpr int MIN_CTAS = K * W * 4 <= 100 * 1024 ? 2 : 1;
 };
 
 __device__ __forceinline__ uint32_t word_of(const uint4& v, int wi) {
@@ -374,7 +377,7 @@ __device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int 
 }
 
 template <int M, int BITS>
-__global__ void __launch_bounds__(SCAN_THREADS, 2) scan_kernel(DevIndex ix, ScanArgs a) {
+__global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan_kernel(DevIndex ix, ScanArgs a) {
     using C = ScanCfg<M, BITS>;
     extern __shared__ uint4 dsm[];
     uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
