@@ -104,7 +104,16 @@ def max_over_ranks(ws, v: float) -> float:
     return float(t.item())
 
 
-def make_inputs(args, device):
+def shard_rows(n_total: int, rank: int, ws: int):
+    """Contiguous shard [lo, hi) of n_total rows for rank of ws (the last may be shorter)."""
+    per = (n_total + ws - 1) // ws
+    lo = min(n_total, rank * per)
+    return lo, min(n_total, lo + per)
+
+
+def make_inputs(args, device, rank: int = 0, ws: int = 1):
+    """Data, index and this rank's queries: with ws ranks the batch is a disjoint shard of a
+    ws x nq query set (weak scaling: nq queries per rank, no data-path collective)."""
     from synth import WORKLOADS, make_workload, build_ivf_pq
     from synth.index import set_build_device
     w = WORKLOADS[args.workload]
@@ -112,7 +121,9 @@ def make_inputs(args, device):
     nq = args.nq or w.nq
     k = args.k or w.k
     nprobe = int(str(args.nprobe).split(",")[0]) if args.nprobe else w.nprobe
-    x, q = make_workload(w, n=n, nq=nq)
+    x, q = make_workload(w, n=n, nq=nq * ws)
+    lo, hi = shard_rows(len(q), rank, ws)
+    q = np.ascontiguousarray(q[lo:hi])
     set_build_device(device)
     t0 = time.time()
     nlist = w.nlist if n >= 100 * w.nlist else max(8, n // 200)
@@ -342,7 +353,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     bbc.build()
-    w, idx, q, k, nprobe, t_build = make_inputs(args, f"cuda:{local}")
+    w, idx, q, k, nprobe, t_build = make_inputs(args, f"cuda:{local}", rank, ws)
     torch.cuda.empty_cache()
     index = bbc.Index(idx, device=local)
     index.set(buckets=args.buckets, workspace_mb=64 * 1024)
