@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--k", type=int, default=None)
     p.add_argument("--nprobe", default=None, help="lists probed; a comma list prints one line per value")
     p.add_argument("--kc-ratio", default="1.5", help="K_c / k; a comma list prints one line per value")
-    p.add_argument("--buckets", type=int, default=64)
+    p.add_argument("--buckets", default="64", help="bucket count m; a comma list prints one line per value")
     p.add_argument("--cpu-queries", type=int, default=200, help="oracle sample for cpu_baseline")
     p.add_argument("--ref-queries", type=int, default=24, help="oracle queries per reference step")
     p.add_argument("--e2e-steps", type=int, default=10)
@@ -356,7 +356,7 @@ def main():
     w, idx, q, k, nprobe, t_build = make_inputs(args, f"cuda:{local}", rank, ws)
     torch.cuda.empty_cache()
     index = bbc.Index(idx, device=local)
-    index.set(buckets=args.buckets, workspace_mb=64 * 1024)
+    index.set(workspace_mb=64 * 1024)
     float_data = not index.info["vectors_u8_exact"]
     precs = [int(v) for v in args.precision.split(",")] if args.precision else [2 if float_data else 0]
     if index.info["quantizer"] == 1 and not args.precision:
@@ -365,18 +365,20 @@ def main():
     nprobes = [int(v) for v in args.nprobe.split(",")] if args.nprobe else [nprobe]
     ratios = [float(v) for v in str(args.kc_ratio).split(",")]
     scales = [float(v) for v in str(args.bound_scale).split(",")] if index.info["quantizer"] == 1 else [None]
+    buckets = [int(v) for v in str(args.buckets).split(",")]
     for prec in precs:
         for npb in nprobes:
             for ratio in ratios:
-                for scale in scales:
-                    index.set(kc_ratio=ratio)
-                    if scale is not None:
-                        index.set(bound_scale=scale)
-                    measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec, ratio)
+                for m in buckets:
+                    for scale in scales:
+                        index.set(kc_ratio=ratio, buckets=m)
+                        if scale is not None:
+                            index.set(bound_scale=scale)
+                        measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec, ratio, m)
     index.close()
 
 
-def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt, prec, ratio):
+def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt, prec, ratio, m):
     """Time one configuration and print its JSON line (rank 0)."""
     import torch
     dev = torch.device("cuda", local)
@@ -560,7 +562,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
             "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "metric_space": idx.metric,
                        "pq": "sign 1-bit" if is_sign else f"{idx.pq_m}x{idx.pq_bits}", "nq": nq, "k": k,
                        "nprobe": nprobe, "kc": None if is_sign else kc,
-                       "kc_ratio": ratio, "buckets": args.buckets, "rerank": rerank,
+                       "kc_ratio": ratio, "buckets": m, "rerank": rerank,
                        "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
                        "recall_tie_aware": True, "ground_truth_cpu_spotcheck": gt_check,
                        "l2_flush_between_steps": True, "parallelism": f"replicas x{ws}",

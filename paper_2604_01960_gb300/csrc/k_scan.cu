@@ -31,6 +31,7 @@
 // aggregated (ballot + one shared atomic per warp) into a contiguous region.
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 #include "bbc_internal.cuh"
 #include "dev_util.cuh"
@@ -145,6 +146,41 @@ __device__ __forceinline__ uint32_t warp_update(const uint32_t* hist, int m, int
     return __shfl_sync(0xFFFFFFFFu, bk, src);
 }
 
+// Update on bin counts by one warp.  Buckets are unions of consecutive bins
+// (the map is monotone), so the first bin b whose running count reaches kc
+// lies in the first bucket whose running count reaches kc: tau = map[b];
+// m when the total is below kc.  bh is 16-byte aligned shared memory.
+__device__ __forceinline__ uint32_t warp_update_bins(const uint32_t* bh, const uint8_t* bmap, int m, int64_t kc) {
+    const unsigned ln = lane_id();
+    uint32_t h[8];
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(bh + ln * 8);
+    asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]) : "r"(sa));
+    asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4+16];"
+                 : "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7]) : "r"(sa));
+    const uint32_t k32 = kc >= 0xFFFFFFFFll ? 0xFFFFFFFFu : (kc < 0 ? 0u : (uint32_t)kc);
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += h[i];
+    const uint32_t inc = warp_incl_scan(s);
+    const unsigned hit = __ballot_sync(0xFFFFFFFFu, inc >= k32);
+    if (!hit) return (uint32_t)m;
+    const unsigned src = __ffs(hit) - 1;
+    uint32_t b = 0;
+    if (ln == src) {
+        // smallest i with (count before this lane) + h[0] + ... + h[i] >= kc
+        uint32_t run = inc - s;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            run += h[i];
+            if (run >= k32) { b = (uint32_t)i; break; }
+        }
+        b += ln * 8;
+    }
+    b = __shfl_sync(0xFFFFFFFFu, b, src);
+    return bmap[b];
+}
+
 __device__ __forceinline__ uint32_t bin_of(uint32_t e, uint32_t dmin, int sh) {
     if (e <= dmin) return 0u;
     uint32_t b = (e - dmin) >> sh;
@@ -152,7 +188,8 @@ __device__ __forceinline__ uint32_t bin_of(uint32_t e, uint32_t dmin, int sh) {
 }
 
 struct ScanShared {
-    alignas(16) uint32_t hist[kMaxBuckets];
+    alignas(16) uint32_t hist[kMaxBuckets];   // bucket counts (state in / out)
+    alignas(16) uint32_t bh[256];             // counts of pushed objects per bin
     uint32_t ehist[256];
     alignas(16) uint8_t bmap[256];
     uint32_t sc[2];
@@ -162,6 +199,8 @@ struct ScanShared {
     uint32_t etau;      // largest estimate whose bucket is <= tau (the map is monotone)
     int sh;
     int nsl;
+    int gs;             // layout blocks of the sampled lists
+    int gtot;           // layout blocks of all probed lists
     long long sq;
 };
 
@@ -189,12 +228,12 @@ __device__ __forceinline__ uint32_t etau_of(const ScanShared& S, uint32_t t) {
     return v > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)v;
 }
 
-// Split mode: move this CTA's bucket-count deltas into the query's global
-// counts, then Update on the global counts (one warp).
+// Split mode: move this CTA's per-bin count deltas into the query's global
+// bucket counts, then Update on the global counts (one warp).
 __device__ __forceinline__ void flush_and_update(ScanShared& S, bbc_collector_state* st, int m, int64_t kc) {
-    for (int b = (int)lane_id(); b < m; b += 32) {
-        const uint32_t v = atomicExch(&S.hist[b], 0u);
-        if (v) atomicAdd(&st->hist[b], v);
+    for (int b = (int)lane_id(); b < 256; b += 32) {
+        const uint32_t v = atomicExch(&S.bh[b], 0u);
+        if (v) atomicAdd(&st->hist[S.bmap[b]], v);
     }
     __syncwarp();
     const uint32_t t = warp_update(st->hist, m, kc);
@@ -206,103 +245,197 @@ __device__ __forceinline__ void flush_and_update(ScanShared& S, bbc_collector_st
     }
 }
 
-// Scans blocks [g0, g1) of the lists laid out in lpre/lblk/llen (nl lists).
+// Bucket counts from the per-bin counts: hist[map[b]] += bh[b] (whole CTA;
+// S.hist is overwritten).
+__device__ void bins_to_buckets(ScanShared& S) {
+    for (int i = threadIdx.x; i < kMaxBuckets; i += blockDim.x) S.hist[i] = 0u;
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x)
+        if (S.bh[b]) atomicAdd(&S.hist[S.bmap[b]], S.bh[b]);
+    __syncthreads();
+}
+
+// Load of list descriptor j from the descriptor array at shared address d0.
+__device__ __forceinline__ int4 ld_desc(uint32_t d0, int j) {
+    int4 v;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(d0 + 16u * (uint32_t)j));
+    return v;
+}
+
+// Warp-collective: lay out lists[0..nl) in probe order as consecutive
+// 32-vector blocks.  ldesc[j] = {first layout block, end layout block,
+// code block minus layout block, 32 * first layout block + list length}, so
+// layout block g of list j is code block g + ldesc[j].z and its lane t holds
+// a vector when 32 g + t < ldesc[j].w.  Returns the number of layout blocks;
+// *nvec = the number of vectors.
+__device__ int build_layout(const DevIndex& ix, const int32_t* lists, int nl, int4* ldesc, long long* nvec) {
+    const unsigned ln = lane_id();
+    int carry = 0;
+    long long carryv = 0;
+    for (int base = 0; base < nl; base += 32) {
+        const int j = base + (int)ln;
+        int nb = 0, nv = 0, blk = 0;
+        if (j < nl) {
+            const int l = lists[j];
+            nv = ix.list_len[l];
+            nb = (nv + 31) >> 5;
+            blk = ix.list_blk[l];
+        }
+        const uint32_t inc = warp_incl_scan((uint32_t)nb);
+        const unsigned long long incv = warp_incl_scan64((unsigned long long)nv);
+        if (j < nl) {
+            const int lo = carry + (int)inc - nb;
+            ldesc[j] = make_int4(lo, lo + nb, blk - lo, 32 * lo + nv);
+        }
+        carry += (int)__shfl_sync(0xFFFFFFFFu, inc, 31);
+        carryv += (long long)__shfl_sync(0xFFFFFFFFu, incv, 31);
+    }
+    *nvec = carryv;
+    return carry;
+}
+
+// Phase A's table staging: the query's uint16 table [M][K] from global
+// memory into the scan layout (row = code, word c = entry of sub-space
+// c mod M).  A thread moves 8 consecutive codes of one sub-space (one 16-byte
+// load); consecutive threads take consecutive sub-spaces, so each row store
+// of a warp covers consecutive words.
+template <int M, int BITS>
+__device__ __forceinline__ void stage_lut(const uint16_t* lq, uint32_t* lut) {
+    using C = ScanCfg<M, BITS>;
+    constexpr int K8 = C::K / 8;
+    for (int t = threadIdx.x; t < M * K8; t += blockDim.x) {
+        const int j8 = t / M, c = t - j8 * M;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(lq + c * C::K + j8 * 8));
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t wd = word_of(v, i >> 1);
+            const uint32_t val = (i & 1) ? (wd >> 16) : (wd & 0xFFFFu);
+            uint32_t* row = lut + (j8 * 8 + i) * C::W;
+#pragma unroll
+            for (int cc = c; cc < C::W; cc += M) row[cc] = val;
+        }
+    }
+}
+
+// Scans blocks [g0, g1) of the lists laid out in ldesc (nl lists).
 // MAIN = false: sampling (append everything); MAIN = true: Push with the
 // codebook and tau.  GLOBAL = false: the CTA owns the query (counts and
 // region cursor in shared memory); GLOBAL = true: several CTAs share the
 // query (region cursor and counts in the global state, tau cached per CTA).
+//
+// Warps take chunks of CHUNK consecutive blocks in turn, so the CTA moves
+// through the lists in probe order.  A warp keeps the descriptor of its
+// current list in registers and walks forward (its chunks ascend); the
+// appends of a chunk take one cursor atomic.
 template <int M, int BITS, bool MAIN, bool GLOBAL>
 __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& a, const QCtx& Q,
                                             bbc_collector_state* st, int nl, int g0, int g1,
-                                            const uint32_t* lut, const int32_t* lpre, const int32_t* lblk,
-                                            const int32_t* llen, ScanShared& S) {
+                                            const uint32_t* lut, const int4* ldesc, ScanShared& S) {
     using C = ScanCfg<M, BITS>;
-    const int P = nl;
+    using Pos = typename std::conditional<GLOBAL, unsigned long long, uint32_t>::type;
+    constexpr int CH = C::CHUNK;
     const unsigned ln = lane_id();
     const int nw = blockDim.x >> 5;
     const uint32_t lane_base = (uint32_t)__cvta_generic_to_shared(lut) + 4u * ln;
     uint2* region = Q.region;
     const unsigned lt_mask = (1u << ln) - 1u;
-    constexpr int CH = C::CHUNK;
-    int jw = -1;                                              // list of this warp's current chunk
-    for (int cb = g0 + (int)warp_id() * CH; cb < g1; cb += nw * CH) {
-        const int ge = min(cb + CH, g1);
-        // list holding block cb: largest j with lpre[j] <= cb (binary search once,
-        // then walk forward: a warp's chunks ascend)
-        if (jw < 0) {
-            int lo = 0, hi = P - 1;
+    const Pos cap = GLOBAL ? (Pos)Q.cap : (Pos)(Q.cap < 0xFFFFFFFFll ? Q.cap : 0xFFFFFFFFll);
+    const uint4* codes = reinterpret_cast<const uint4*>(ix.codes) + ln;
+    const uint32_t dmin = S.dmin;                             // fixed once the codebook exists
+    const int sh = S.sh;
+    // current list j of this warp (descriptor fields in registers)
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(ldesc);
+    int j = -1, jhi = 0, jb = 0, jend = 0;
+    auto seek = [&](int g) {
+        int4 d;
+        if (j < 0) {
+            int lo = 0, hi = nl - 1;
             while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (lpre[mid] <= cb) lo = mid; else hi = mid - 1;
+                const int mid = (lo + hi + 1) >> 1;
+                if (ld_desc(d0, mid).x <= g) lo = mid; else hi = mid - 1;
             }
-            jw = lo;
+            j = lo;
+            d = ld_desc(d0, j);
         } else {
-            while (cb >= lpre[jw + 1]) ++jw;
+            do { d = ld_desc(d0, ++j); } while (g >= d.y);
         }
-        int j = jw;
-        int gbk[CH], nval[CH];
+        jhi = d.y;
+        jb = d.z;
+        jend = d.w;
+    };
+    int it = 0;
+    for (int cb = g0 + (int)warp_id() * CH; cb < g1; cb += nw * CH, ++it) {
+        const int nb = min(CH, g1 - cb);                      // blocks in this chunk (warp-uniform)
+        int gbk[CH];
+        uint32_t vbits = 0;                                   // bit u: this lane holds a vector of block u
         uint4 r[CH][C::NCH];
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
-            const int g = cb + u;
-            gbk[u] = -1;
-            nval[u] = 0;
-            if (g < ge) {
-                while (g >= lpre[j + 1]) ++j;
-                const int b = g - lpre[j];
-                gbk[u] = lblk[j] + b;
-                nval[u] = min(32, llen[j] - 32 * b);
-                const uint4* cp = reinterpret_cast<const uint4*>(ix.codes + (size_t)gbk[u] * 32 * C::CBP) + ln;
+            gbk[u] = 0;
+            if (u < nb) {
+                const int g = cb + u;
+                if (g >= jhi) seek(g);
+                gbk[u] = jb + g;
+                vbits |= (uint32_t)((int)ln < jend - 32 * g) << u;
+                const uint4* cp = codes + (size_t)gbk[u] * (32 * C::NCH);
 #pragma unroll
                 for (int c = 0; c < C::NCH; ++c) r[u][c] = __ldg(cp + c * 32);
             }
         }
         const uint32_t etau = MAIN ? *(volatile uint32_t*)&S.etau : 0u;
-        const uint32_t dmin = S.dmin;
-        const int sh = S.sh;
+        uint32_t e[CH];
+        unsigned bal[CH];
+        uint32_t tot = 0;
+        uint32_t mn = 0xFFFFFFFFu;
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
-            if (gbk[u] < 0) continue;
-            const uint32_t e = adc_lane<M, BITS>(r[u], lane_base);
-            const bool valid = (int)ln < nval[u];
-            bool push;
-            if (MAIN) {
-                push = valid && e <= etau;                       // bucket(e) <= tau
-            } else {
-                push = valid;
-                if (!GLOBAL) {
-                    const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, valid ? e : 0xFFFFFFFFu);
-                    if (ln == 0 && mn != 0xFFFFFFFFu) atomicMin(&S.dmin, mn);
-                }
-            }
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, push);
-            if (bal) {
-                uint32_t base = 0;
-                if (ln == 0) {
-                    if (GLOBAL)
-                        base = (uint32_t)atomicAdd(reinterpret_cast<unsigned long long*>(&st->pushed),
-                                                   (unsigned long long)__popc(bal));
-                    else
-                        base = atomicAdd(&S.count, (uint32_t)__popc(bal));
-                }
-                base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                if (push) {
-                    const uint32_t pos = base + (uint32_t)__popc(bal & lt_mask);
-                    if ((int64_t)pos < Q.cap) region[pos] = make_uint2(e, (uint32_t)gbk[u] * 32u + ln);
-                    else atomicOr(ix.status, kStatusRegionOverrun);
-                    if (MAIN) atomicAdd(&S.hist[S.bmap[bin_of(e, dmin, sh)]], 1u);
-                }
+            e[u] = 0;
+            bal[u] = 0;
+            if (u < nb) {
+                e[u] = adc_lane<M, BITS>(r[u], lane_base);
+                const bool valid = (vbits >> u) & 1u;
+                const bool push = MAIN ? (valid && e[u] <= etau) : valid;    // bucket(e) <= tau
+                bal[u] = __ballot_sync(0xFFFFFFFFu, push);
+                tot += (uint32_t)__popc(bal[u]);
+                if (!MAIN && valid) mn = min(mn, e[u]);
             }
         }
-        if (MAIN && (((cb - g0) / (nw * CH)) & 1) == 0) {
+        if (!MAIN && !GLOBAL) {
+            mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+            if (ln == 0 && mn != 0xFFFFFFFFu) atomicMin(&S.dmin, mn);
+        }
+        if (tot) {
+            Pos base = 0;
+            if (ln == 0) {
+                if (GLOBAL)
+                    base = (Pos)atomicAdd(reinterpret_cast<unsigned long long*>(&st->pushed),
+                                          (unsigned long long)tot);
+                else
+                    base = (Pos)atomicAdd(&S.count, tot);
+            }
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if ((bal[u] >> ln) & 1u) {
+                    const Pos pos = base + (Pos)__popc(bal[u] & lt_mask);
+                    if (pos < cap) region[pos] = make_uint2(e[u], (uint32_t)gbk[u] * 32u + ln);
+                    else atomicOr(ix.status, kStatusRegionOverrun);
+                    if (MAIN) atomicAdd(&S.bh[bin_of(e[u], dmin, sh)], 1u);
+                }
+                base += (Pos)__popc(bal[u]);
+            }
+        }
+        if (MAIN && (it & 1) == 0) {
             if (GLOBAL) {
                 if (warp_id() == 0) flush_and_update(S, st, a.m, Q.kc);
             } else {
-                const uint32_t t = warp_update(S.hist, a.m, Q.kc);
-                const uint32_t e = etau_of(S, t);
+                const uint32_t t = warp_update_bins(S.bh, S.bmap, a.m, Q.kc);
+                const uint32_t et = etau_of(S, t);
                 if (ln == 0) {
                     atomicMin(&S.tau, t);
-                    atomicMin(&S.etau, e);
+                    atomicMin(&S.etau, et);
                 }
             }
         }
@@ -312,7 +445,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
 // Phase C of Algorithm 1's Collect (Section 3.2, "Codebook Generation Based
 // on Estimated Distance") over the ns sampled objects at the start of the
 // region, by the whole CTA.  On entry S.dmin holds the smallest sampled
-// estimate and S.hist is zero; on exit S holds d_max, the shift, the
+// estimate and S.bh is zero; on exit S holds d_max, the shift, the
 // equal-depth map, the sample's bucket counts and tau.
 __device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int m, ScanShared& S) {
     const int tid = threadIdx.x, bs = blockDim.x;
@@ -361,11 +494,11 @@ __device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int 
             for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0u;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (i + u * bs < ns) atomicAdd(&S.hist[S.bmap[bin_of(e[u], dmin, sh)]], 1u);
+                if (i + u * bs < ns) atomicAdd(&S.bh[bin_of(e[u], dmin, sh)], 1u);
         }
         __syncthreads();
         if (warp_id() == 0) {
-            const uint32_t t0 = warp_update(S.hist, m, kc);
+            const uint32_t t0 = warp_update_bins(S.bh, S.bmap, m, kc);
             const uint32_t e0 = etau_of(S, t0);
             if (lane_id() == 0) { S.tau = t0; S.etau = e0; }
         }
@@ -381,10 +514,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan
     using C = ScanCfg<M, BITS>;
     extern __shared__ uint4 dsm[];
     uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
-    const int Pmax = a.nprobe;
-    int32_t* lpre = reinterpret_cast<int32_t*>(lut + C::LUT_WORDS);   // [Pmax+1]
-    int32_t* lblk = lpre + (Pmax + 1);                                 // [Pmax]
-    int32_t* llen = lblk + Pmax;                                       // [Pmax]
+    int4* ldesc = reinterpret_cast<int4*>(lut + C::LUT_WORDS);         // [nprobe]
     __shared__ ScanShared S;
     const int64_t qi = blockIdx.x;
     const QCtx Q{a.qp.P(qi), a.qp.KC(qi), a.qp.rcap(qi), a.region + a.qp.roff(qi), a.lists + a.qp.poff(qi)};
@@ -392,12 +522,8 @@ __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan
     const int tid = threadIdx.x, bs = blockDim.x;
 
     // ---- Phase A: LUT staging and list layout ----
-    const uint16_t* lq = a.lut16 + qi * (int64_t)M * C::K;
-    for (int w = tid; w < C::LUT_WORDS; w += bs) {
-        const int jj = w / C::W, c = w - jj * C::W;
-        lut[w] = lq[(c % M) * C::K + jj];
-    }
-    for (int i = tid; i < kMaxBuckets; i += bs) S.hist[i] = 0;
+    stage_lut<M, BITS>(a.lut16 + qi * (int64_t)M * C::K, lut);
+    for (int i = tid; i < 256; i += bs) S.bh[i] = 0;
     if (tid == 0) {
         S.count = 0;
         S.dmin = 0xFFFFFFFFu;
@@ -407,25 +533,9 @@ __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan
     }
     if (warp_id() == 0) {
         const unsigned ln = lane_id();
-        int carry = 0;
-        long long carryv = 0;
-        for (int base = 0; base < P; base += 32) {
-            const int j = base + (int)ln;
-            int nb = 0, nv = 0;
-            if (j < P) {
-                const int l = Q.lists[j];
-                nv = ix.list_len[l];
-                nb = (nv + 31) >> 5;
-                lblk[j] = ix.list_blk[l];
-                llen[j] = nv;
-            }
-            const uint32_t inc = warp_incl_scan((uint32_t)nb);
-            const unsigned long long incv = warp_incl_scan64((unsigned long long)nv);
-            if (j < P) lpre[j + 1] = carry + (int)inc;
-            carry += (int)__shfl_sync(0xFFFFFFFFu, inc, 31);
-            carryv += (long long)__shfl_sync(0xFFFFFFFFu, incv, 31);
-        }
-        if (ln == 0) lpre[0] = 0;
+        long long carryv;
+        const int gtot = build_layout(ix, Q.lists, P, ldesc, &carryv);
+        __syncwarp();
         // sample lists: at least min(sample_min, P), extended until min(K_c, S_q) vectors
         const long long want = Q.kc < carryv ? Q.kc : carryv;
         const int smin = a.sample_min < P ? a.sample_min : P;
@@ -433,7 +543,11 @@ __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan
         int nsl = P;
         for (int base = 0; base < P; base += 32) {
             const int j = base + (int)ln;
-            const int nv = j < P ? llen[j] : 0;
+            int nv = 0;
+            if (j < P) {
+                const int4 d = ldesc[j];
+                nv = d.w - 32 * d.x;
+            }
             const unsigned long long incv = warp_incl_scan64((unsigned long long)nv);
             const bool ok = j < P && (j + 1) >= smin && (long long)(cum + (long long)incv) >= want;
             const unsigned hit = __ballot_sync(0xFFFFFFFFu, ok);
@@ -443,28 +557,31 @@ __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan
         if (ln == 0) {
             S.nsl = nsl;
             S.sq = carryv;
+            S.gs = nsl > 0 ? ldesc[nsl - 1].y : 0;
+            S.gtot = gtot;
         }
     }
     __syncthreads();
 
     // ---- Phase B: sample ----
-    const int gs = lpre[S.nsl];
-    scan_blocks<M, BITS, false, false>(ix, a, Q, a.state + qi, P, 0, gs, lut, lpre, lblk, llen, S);
+    const int gs = S.gs;
+    scan_blocks<M, BITS, false, false>(ix, a, Q, a.state + qi, P, 0, gs, lut, ldesc, S);
     __syncthreads();
 
     // ---- Phase C: codebook ----
     const int64_t ns = (int64_t)min((long long)S.count, (long long)Q.cap);
     build_codebook(Q.region, ns, Q.kc, a.m, S);
     // ---- Phase D: main scan ----
-    scan_blocks<M, BITS, true, false>(ix, a, Q, a.state + qi, P, gs, lpre[P], lut, lpre, lblk, llen, S);
+    scan_blocks<M, BITS, true, false>(ix, a, Q, a.state + qi, P, gs, S.gtot, lut, ldesc, S);
     __syncthreads();
 
     // ---- state out ----
     bbc_collector_state* st = a.state + qi;
+    bins_to_buckets(S);
     for (int i = tid; i < kMaxBuckets; i += bs) st->hist[i] = i < a.m ? S.hist[i] : 0u;
     for (int i = tid; i < 256; i += bs) st->map[i] = S.bmap[i];
     if (warp_id() == 0) {
-        const uint32_t t1 = warp_update(S.hist, a.m, Q.kc);
+        const uint32_t t1 = warp_update_bins(S.bh, S.bmap, a.m, Q.kc);
         if (lane_id() == 0) {
             st->d_min = S.dmin;
             st->d_max = S.dmax;
@@ -523,14 +640,11 @@ struct SplitArgs {
 };
 
 template <int M, int BITS, bool MAIN>
-__global__ void __launch_bounds__(SCAN_THREADS, 2) scan_split_kernel(DevIndex ix, ScanArgs a, SplitArgs sp, int64_t nq) {
+__global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan_split_kernel(DevIndex ix, ScanArgs a, SplitArgs sp, int64_t nq) {
     using C = ScanCfg<M, BITS>;
     extern __shared__ uint4 dsm[];
     uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
-    const int Pmax = a.nprobe;
-    int32_t* lpre = reinterpret_cast<int32_t*>(lut + C::LUT_WORDS);
-    int32_t* lblk = lpre + (Pmax + 1);
-    int32_t* llen = lblk + Pmax;
+    int4* ldesc = reinterpret_cast<int4*>(lut + C::LUT_WORDS);
     __shared__ ScanShared S;
     __shared__ long long s_item, s_q;
     __shared__ int s_nsl;
@@ -573,36 +687,16 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_split_kernel(DevIndex ix
         }
         if (j0 >= j1) continue;
         const int nl = j1 - j0;
-        if (s_q != qi) {
-            const uint16_t* lq = a.lut16 + qi * (int64_t)M * C::K;
-            for (int w = tid; w < C::LUT_WORDS; w += bs) {
-                const int jj = w / C::W, c = w - jj * C::W;
-                lut[w] = lq[(c % M) * C::K + jj];
-            }
-        }
+        if (s_q != qi) stage_lut<M, BITS>(a.lut16 + qi * (int64_t)M * C::K, lut);
         if (warp_id() == 0) {
-            const unsigned ln = lane_id();
-            int carry = 0;
-            for (int base = 0; base < nl; base += 32) {
-                const int j = base + (int)ln;
-                int nb = 0;
-                if (j < nl) {
-                    const int l = Q.lists[j0 + j];
-                    const int nv = ix.list_len[l];
-                    nb = (nv + 31) >> 5;
-                    lblk[j] = ix.list_blk[l];
-                    llen[j] = nv;
-                }
-                const uint32_t inc = warp_incl_scan((uint32_t)nb);
-                if (j < nl) lpre[j + 1] = carry + (int)inc;
-                carry += (int)__shfl_sync(0xFFFFFFFFu, inc, 31);
-            }
-            if (ln == 0) lpre[0] = 0;
+            long long nv;
+            const int nb = build_layout(ix, Q.lists + j0, nl, ldesc, &nv);
+            if (lane_id() == 0) S.gtot = nb;
         }
         if (MAIN) {
             for (int i = tid; i < 256; i += bs) {
                 S.bmap[i] = st->map[i];
-                S.hist[i] = 0u;                                  // this CTA's count deltas
+                S.bh[i] = 0u;                                    // this CTA's count deltas per bin
             }
             if (tid == 0) {
                 S.dmin = st->d_min;
@@ -617,7 +711,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 2) scan_split_kernel(DevIndex ix
         }
         __syncthreads();
         if (tid == 0) s_q = qi;
-        scan_blocks<M, BITS, MAIN, true>(ix, a, Q, st, nl, 0, lpre[nl], lut, lpre, lblk, llen, S);
+        scan_blocks<M, BITS, MAIN, true>(ix, a, Q, st, nl, 0, S.gtot, lut, ldesc, S);
         __syncthreads();
         if (MAIN && warp_id() == 0) flush_and_update(S, st, a.m, Q.kc);
     }
@@ -634,7 +728,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) codebook_kernel(ScanArgs a) {
     const int64_t ns = st->pushed < cap ? st->pushed : cap;
     const int tid = threadIdx.x, bs = blockDim.x;
     if (tid == 0) S.dmin = 0xFFFFFFFFu;
-    for (int i = tid; i < kMaxBuckets; i += bs) S.hist[i] = 0u;
+    for (int i = tid; i < 256; i += bs) S.bh[i] = 0u;
     __syncthreads();
     uint32_t mn = 0xFFFFFFFFu;
     for (int64_t i = tid; i < ns; i += bs) mn = min(mn, region[i].x);
@@ -642,6 +736,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) codebook_kernel(ScanArgs a) {
     if (lane_id() == 0 && mn != 0xFFFFFFFFu) atomicMin(&S.dmin, mn);
     __syncthreads();
     build_codebook(region, ns, kc, a.m, S);
+    bins_to_buckets(S);
     for (int i = tid; i < kMaxBuckets; i += bs) st->hist[i] = i < a.m ? S.hist[i] : 0u;
     for (int i = tid; i < 256; i += bs) st->map[i] = S.bmap[i];
     if (tid == 0) {
@@ -660,7 +755,7 @@ template <int M, int BITS>
 static cudaError_t launch_split_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, int G, unsigned int* counters,
                                   cudaStream_t st) {
     using C = ScanCfg<M, BITS>;
-    const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)(3 * a.nprobe + 1) * 4;
+    const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)a.nprobe * sizeof(int4);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(scan_split_kernel<M, BITS, false>,
@@ -673,7 +768,7 @@ static cudaError_t launch_split_t(const DevIndex& ix, int64_t nq, const ScanArgs
     }
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     const long long items = nq * (long long)G;
-    const unsigned grid = (unsigned)std::min<long long>(items, (long long)ix.num_sms * 2);
+    const unsigned grid = (unsigned)std::min<long long>(items, (long long)ix.num_sms * C::MIN_CTAS);
     cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     scan_split_kernel<M, BITS, false><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters}, nq);
@@ -687,7 +782,7 @@ static cudaError_t launch_split_t(const DevIndex& ix, int64_t nq, const ScanArgs
 template <int M, int BITS>
 static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st) {
     using C = ScanCfg<M, BITS>;
-    const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)(3 * a.nprobe + 1) * 4;
+    const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)a.nprobe * sizeof(int4);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(scan_kernel<M, BITS>,
