@@ -62,22 +62,28 @@ __device__ __forceinline__ uint32_t word_of(const uint4& v, int wi) {
 
 // Shared-memory byte address of the LUT entry for code slot S of this lane,
 // without the slot's own offset 4 * S (added as the load's immediate):
-// code * ROWB + lane_base, lane_base = LUT base + 4 * lane.  For 8-bit codes
-// with 256-byte rows one byte permute yields code << 8 directly.
+// LUT base + code * ROWB + 4 * lane (lane4 = 4 * lane, base = LUT base,
+// warp-uniform).  For 8-bit codes with 256-byte rows one byte permute yields
+// code << 8 | 4 * lane directly.
 template <int M, int BITS, int S>
-__device__ __forceinline__ uint32_t slot_addr(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane_base) {
+__device__ __forceinline__ uint32_t slot_addr(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane4, uint32_t base) {
     using C = ScanCfg<M, BITS>;
     if (BITS == 8) {
         const uint32_t w = word_of(r[S >> 4], (S >> 2) & 3);
+        if (C::ROWB == 256) {
+            // one byte permute yields code << 8 | 4 * lane (bytes 2, 3 of lane4 are zero)
+            const uint32_t x = __byte_perm(w, lane4, 0x7604u | ((uint32_t)(S & 3) << 4));
+            return x + base;
+        }
         const uint32_t x = __byte_perm(w, 0u, 0x4404u | ((uint32_t)(S & 3) << 4));   // code << 8
-        if (C::ROWB == 256) return x + lane_base;
+        const uint32_t lane_base = base + lane4;
         if (C::ROWB == 512) return (x << 1) + lane_base;
         return (x >> 8) * (uint32_t)C::ROWB + lane_base;
     } else {
         const int byte = S >> 1;
         const uint32_t w = word_of(r[byte >> 4], (byte >> 2) & 3);
         const uint32_t code = (w >> (8 * (byte & 3) + 4 * (S & 1))) & 0xFu;
-        return code * (uint32_t)C::ROWB + lane_base;
+        return code * (uint32_t)C::ROWB + base + lane4;
     }
 }
 
@@ -90,22 +96,25 @@ __device__ __forceinline__ uint32_t lds(uint32_t addr) {
 
 template <int M, int BITS, int S>
 struct AdcUnroll {
-    static __device__ __forceinline__ uint32_t run(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane_base) {
+    static __device__ __forceinline__ uint32_t run(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane4,
+                                                   uint32_t base) {
         // two lookups per step, summed with one three-input add
-        const uint32_t v0 = lds<4 * S>(slot_addr<M, BITS, S>(r, lane_base));
-        const uint32_t v1 = lds<4 * (S + 1)>(slot_addr<M, BITS, S + 1>(r, lane_base));
-        return v0 + v1 + AdcUnroll<M, BITS, S + 2>::run(r, lane_base);
+        const uint32_t v0 = lds<4 * S>(slot_addr<M, BITS, S>(r, lane4, base));
+        const uint32_t v1 = lds<4 * (S + 1)>(slot_addr<M, BITS, S + 1>(r, lane4, base));
+        return v0 + v1 + AdcUnroll<M, BITS, S + 2>::run(r, lane4, base);
     }
 };
 template <int M, int BITS>
 struct AdcUnroll<M, BITS, M> {
-    static __device__ __forceinline__ uint32_t run(const uint4 (&)[ScanCfg<M, BITS>::NCH], uint32_t) { return 0u; }
+    static __device__ __forceinline__ uint32_t run(const uint4 (&)[ScanCfg<M, BITS>::NCH], uint32_t, uint32_t) {
+        return 0u;
+    }
 };
 
 // Estimated distance of this lane's vector: sum over sub-spaces of its LUT entries.
 template <int M, int BITS>
-__device__ __forceinline__ uint32_t adc_lane(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane_base) {
-    return AdcUnroll<M, BITS, 0>::run(r, lane_base);
+__device__ __forceinline__ uint32_t adc_lane(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane4, uint32_t base) {
+    return AdcUnroll<M, BITS, 0>::run(r, lane4, base);
 }
 
 // Update on the shared bucket counts by one warp: first bucket whose running
@@ -338,7 +347,8 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
     constexpr int CH = C::CHUNK;
     const unsigned ln = lane_id();
     const int nw = blockDim.x >> 5;
-    const uint32_t lane_base = (uint32_t)__cvta_generic_to_shared(lut) + 4u * ln;
+    const uint32_t lut_s = (uint32_t)__cvta_generic_to_shared(lut);   // warp-uniform
+    const uint32_t lane4 = 4u * ln;
     uint2* region = Q.region;
     const unsigned lt_mask = (1u << ln) - 1u;
     const Pos cap = GLOBAL ? (Pos)Q.cap : (Pos)(Q.cap < 0xFFFFFFFFll ? Q.cap : 0xFFFFFFFFll);
@@ -394,7 +404,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
             e[u] = 0;
             bal[u] = 0;
             if (u < nb) {
-                e[u] = adc_lane<M, BITS>(r[u], lane_base);
+                e[u] = adc_lane<M, BITS>(r[u], lane4, lut_s);
                 const bool valid = (vbits >> u) & 1u;
                 const bool push = MAIN ? (valid && e[u] <= etau) : valid;    // bucket(e) <= tau
                 bal[u] = __ballot_sync(0xFFFFFFFFu, push);
