@@ -135,13 +135,15 @@ __device__ __forceinline__ ff ff_prod(float a, float b) {
     return {p, __fmaf_rn(a, b, -p)};
 }
 
-// Selection in three steps: (1) the approximate GEMM scores prune to every
-// list that can still reach the nprobe-th; (2) those lists are re-scored in
-// float-float arithmetic (about 2^-38 relative) and sorted; (3) any run of
-// neighbours whose re-scores are too close for that bound to order them is
-// re-scored in FP64 and re-sorted by (FP64 score, list id).  FP64 is slow on
-// this GPU, so it is kept to genuine near-ties.  Lists outside runs are provably in exact order,
-// so the result equals sorting every list by its FP64 score.
+// Selection in steps of rising precision: (1) the approximate GEMM scores
+// prune to every list that can still reach the nprobe-th; (2) those lists
+// are re-scored in FP32 with a rigorous error bound and sorted; lists closer
+// than that bound to a neighbour are re-scored in float-float arithmetic
+// (about 2^-38 relative) and re-sorted; (3) any run of neighbours whose
+// float-float scores are too close to order is re-scored in FP64 and
+// re-sorted by (FP64 score, list id).  FP64 is slow on this GPU, so it is
+// kept to genuine near-ties.  Every pair outside a run is provably in exact
+// order, so the result equals sorting every list by its FP64 score.
 __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, const float* __restrict__ q,
                                                                     QueryParams qp,
                                                                     const float* __restrict__ scores,
@@ -155,7 +157,10 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
     __shared__ uint32_t sc[2];
     __shared__ float red[SEL_THREADS / 32];
     __shared__ uint32_t ncand;
-    __shared__ float s_fmax;
+    __shared__ float s_fmax, s_smax;
+    __shared__ int s_any;
+    __shared__ uint32_t s_thr;
+    __shared__ double s_qn, s_eps;   // per-query scalars, computed once (FP64 is slow here)
 
     const int64_t qi = blockIdx.x;
     const int nprobe = qp.P(qi);
@@ -167,11 +172,13 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
     for (int i = threadIdx.x; i < d; i += blockDim.x) acc = fmaf(qv[i], qv[i], acc);
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if (lane_id() == 0) red[warp_id()] = acc;
-    if (threadIdx.x == 0) { ncand = 0; s_fmax = 0.f; }
+    if (threadIdx.x == 0) { ncand = 0; s_fmax = 0.f; s_smax = 0.f; s_any = 0; }
     __syncthreads();
-    float qn2 = 0.f;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) qn2 += red[w];
-    const double qn = sqrt((double)qn2);
+    if (threadIdx.x == 0) {
+        float qn2 = 0.f;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) qn2 += red[w];
+        s_qn = sqrt((double)qn2);
+    }
 
     // step 1: prune with the approximate scores
     const uint32_t kth = cta_select_u32(L, (uint32_t)(nprobe - 1), [&](int64_t i) { return keys[i]; },
@@ -184,18 +191,25 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
     //    3.06 d 2^-23 ||q|| ||c||, doubled for the factor 2 of the L2 score,
     //    plus ||c||^2 and subtraction rounding; safety factor 2.
     const double cm = (double)ix.cmax;
-    double eps;
-    if (!tc) {
-        eps = (double)(d + 4) * ldexp(1.0, -22) * (qn + cm) * (qn + cm);
-    } else {
-        const double rel = 3.1 * ldexp(1.0, -16) + 3.06 * (double)d * ldexp(1.0, -23);
-        eps = ix.metric == BBC_METRIC_L2
-                  ? 2.0 * (2.0 * rel * qn * cm + ldexp(1.0, -23) * (cm * cm + 2.0 * qn * cm))
-                  : 2.0 * (rel * qn * cm + ldexp(1.0, -24) * qn * cm);
+    if (threadIdx.x == 0) {
+        const double qn = s_qn;
+        double eps;
+        if (!tc) {
+            eps = (double)(d + 4) * ldexp(1.0, -22) * (qn + cm) * (qn + cm);
+        } else {
+            const double rel = 3.1 * ldexp(1.0, -16) + 3.06 * (double)d * ldexp(1.0, -23);
+            eps = ix.metric == BBC_METRIC_L2
+                      ? 2.0 * (2.0 * rel * qn * cm + ldexp(1.0, -23) * (cm * cm + 2.0 * qn * cm))
+                      : 2.0 * (rel * qn * cm + ldexp(1.0, -24) * qn * cm);
+        }
+        // a float x satisfies x <= thr exactly when x <= thr rounded down to float
+        s_thr = f32_key(__double2float_rd((double)key_f32(kth) + 2.0 * eps));
     }
-    const double thr = (double)key_f32(kth) + 2.0 * eps;
+    __syncthreads();
+    const double qn = s_qn;
+    const uint32_t thr = s_thr;
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
-        if ((double)key_f32(keys[l]) <= thr) {
+        if (keys[l] <= thr) {
             uint32_t p = atomicAdd(&ncand, 1u);
             if (p < SEL_MAXC) cval[p] = (uint32_t)l;
         }
@@ -206,15 +220,58 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
         if (threadIdx.x == 0) atomicOr(ix.status, kStatusSelectOverrun);
         nc = SEL_MAXC;
     }
-    // step 2: near-exact re-score in float-float arithmetic (one warp per list,
-    // lanes over dimensions, so centroid rows are read coalesced), then sort by
-    // (score, list id).
+    // step 2: FP32 re-score (one warp per list, lanes over dimensions, so
+    // centroid rows are read coalesced), then sort by (score, list id).  A
+    // term passes through at most nr = ceil(d / 32) + 5 roundings once formed
+    // (the fused multiply-add chain of its lane, then the five shuffle-tree
+    // additions); forming (q - c)^2 adds 2u + u^2 (u = 2^-24).  So
+    //   L2: |fl - s| <= (nr + 3) u s,   IP: |fl - s| <= nr u ||q|| max ||c||,
+    // taken with a 2 % margin.
     const int np2 = next_pow2(nc);
+    const int nw = blockDim.x / 32;
     for (int i = nc + threadIdx.x; i < np2; i += blockDim.x) {
         ckey[i] = ~0ull;
         cval[i] = 0xFFFFFFFFu;
     }
-    for (int i = warp_id(); i < nc; i += blockDim.x / 32) {
+    for (int i = warp_id(); i < nc; i += nw) {
+        const float* cr = ix.centroids + (int64_t)cval[i] * d;
+        float acc = 0.f;
+        if (ix.metric == BBC_METRIC_L2) {
+            for (int j = lane_id(); j < d; j += 32) {
+                const float t = __fsub_rn(qv[j], cr[j]);
+                acc = __fmaf_rn(t, t, acc);
+            }
+        } else {
+            for (int j = lane_id(); j < d; j += 32) acc = __fmaf_rn(qv[j], cr[j], acc);
+        }
+        for (int o = 16; o; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));
+        if (lane_id() == 0) {
+            ckey[i] = f64_key(ix.metric == BBC_METRIC_L2 ? (double)acc : -(double)acc);
+            if (ix.metric == BBC_METRIC_L2) atomicMax((int*)&s_smax, __float_as_int(acc));   // acc >= 0
+        }
+    }
+    __syncthreads();
+    cta_bitonic_kv(ckey, cval, np2);
+    if (threadIdx.x == 0) {
+        const double u24 = ldexp(1.0, -24);
+        const double nr = (double)((d + 31) / 32 + 5);
+        s_eps = ix.metric == BBC_METRIC_L2 ? 1.02 * (nr + 3.0) * u24 * (double)s_smax * (1.0 + 16.0 * u24)
+                                           : 1.02 * nr * u24 * qn * cm;
+    }
+    __syncthreads();
+    const double eps1 = s_eps;
+    // Lists within 2 eps1 of a neighbour are re-scored in float-float
+    // arithmetic (about 2^-38 relative), then everything is re-sorted.  The
+    // others keep their FP32 score: their order against every other list is
+    // already certain, and a float-float score stays within eps1 + its own
+    // bound of the FP32 one, so no such pair comes closer than the link bound
+    // of step 3.
+    uint8_t* link = reinterpret_cast<uint8_t*>(keys);
+    for (int i = threadIdx.x; i < nc; i += blockDim.x)
+        link[i] = (i + 1 < nc && key_f64(ckey[i + 1]) - key_f64(ckey[i]) <= 2.0 * eps1) ? 1 : 0;
+    __syncthreads();
+    for (int i = warp_id(); i < nc; i += nw) {
+        if (!link[i] && !(i > 0 && link[i - 1])) continue;
         const float* cr = ix.centroids + (int64_t)cval[i] * d;
         ff part = {0.f, 0.f};
         for (int j = lane_id(); j < d; j += 32)
@@ -228,21 +285,27 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
         if (lane_id() == 0) {
             ckey[i] = f64_key(f);
             atomicMax((int*)&s_fmax, __float_as_int(fabsf(part.hi)));   // non-negative floats order as ints
+            s_any = 1;
         }
     }
     __syncthreads();
-    cta_bitonic_kv(ckey, cval, np2);
-    // step 3: bound on |re-score - FP64 score|, uniform over the candidates.
-    // Float-float accumulation of d exact (or 2^-47-accurate) terms loses at
-    // most about (d + 8) 2^-45 of sum |terms|; the FP64 sequential sum itself
-    // is within d 2^-53 of the real value.  Safety factor 4.
-    //   L2: sum |terms| = the score (max over candidates, +1 ulp for hi);
+    if (s_any) cta_bitonic_kv(ckey, cval, np2);
+    // step 3: bound on |float-float score - FP64 score|, uniform over the
+    // re-scored lists.  Float-float accumulation of d exact (or
+    // 2^-47-accurate) terms loses at most about (d + 8) 2^-45 of sum |terms|;
+    // the FP64 sequential sum itself is within d 2^-53 of the real value.
+    // Safety factor 4.
+    //   L2: sum |terms| = the score (max over re-scored lists, +1 ulp for hi);
     //   IP: sum |terms| <= ||q|| max ||c||.
-    const double base = ix.metric == BBC_METRIC_L2 ? (double)s_fmax * (1.0 + ldexp(1.0, -20)) : qn * cm;
-    const double e32 = 4.0 * ((double)(d + 8) * ldexp(1.0, -45) + (double)d * ldexp(1.0, -53)) * base + 1e-300;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double base = ix.metric == BBC_METRIC_L2 ? (double)s_fmax * (1.0 + ldexp(1.0, -20)) : qn * cm;
+        s_eps = 4.0 * ((double)(d + 8) * ldexp(1.0, -45) + (double)d * ldexp(1.0, -53)) * base + 1e-300;
+    }
+    __syncthreads();
+    const double e32 = s_eps;
     // link[i]: lists i and i+1 (in re-score order) are too close to order
     // without FP64.  Flags are computed before any run is rewritten.
-    uint8_t* link = reinterpret_cast<uint8_t*>(keys);
     for (int i = threadIdx.x; i < nc; i += blockDim.x)
         link[i] = (i + 1 < nc && key_f64(ckey[i + 1]) - key_f64(ckey[i]) <= 2.0 * e32) ? 1 : 0;
     __syncthreads();

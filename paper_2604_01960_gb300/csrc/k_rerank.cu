@@ -12,6 +12,7 @@
 // Top-k: one CTA per query orders 64-bit keys (order-preserving distance bits
 // << 32 | id) with a counting sort into fine distance bins followed by exact
 // ranking inside each bin, and writes the first k.
+#include <algorithm>
 #include <cfloat>
 
 #include "bbc_internal.cuh"
@@ -68,8 +69,17 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     float* rq = reinterpret_cast<float*>(rsm);                 // d floats
     uint8_t* q8 = reinterpret_cast<uint8_t*>(rsm + d / 4);     // d bytes (u8 rows only)
     __shared__ int s_int, s_qn2;
+    __shared__ uint32_t sid[RR_CAND_PER_CTA];                  // this CTA's candidate ids
     const int64_t qi = blockIdx.y;
     if (threadIdx.x == 0) { s_int = 1; s_qn2 = 0; }
+    {
+        // ids staged with coalesced loads, so row gathers wait on one latency
+        const int64_t cn = min(a.cand_count[qi], a.qp.KC(qi));
+        const int64_t b0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
+        const uint32_t* cp = a.cand + a.qp.coff(qi);
+        for (int i = threadIdx.x; i < RR_CAND_PER_CTA; i += blockDim.x)
+            sid[i] = b0 + i < cn ? cp[b0 + i] : 0u;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < d; i += blockDim.x) {
         const float v = a.q[qi * d + i];
@@ -93,7 +103,6 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     const int grp = ln / G, gl = ln % G;
     const int64_t c0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
     const int64_t c1 = min(c0 + RR_CAND_PER_CTA, cnt);
-    const uint32_t* cand = a.cand + a.qp.coff(qi);
     float* out = a.cdist + a.qp.coff(qi);
     const float4* q4 = reinterpret_cast<const float4*>(rq);
     const uint4* qb = reinterpret_cast<const uint4*>(q8);
@@ -107,7 +116,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
         for (int u = 0; u < RR_U; ++u) {
             const int64_t c = cb + (int64_t)u * per_warp + grp;
             const bool live = c < c1;
-            id[u] = live ? cand[c] : 0u;
+            id[u] = live ? sid[c - c0] : 0u;
             ok[u] = live && (int64_t)id[u] < ix.n;
             if (live && !ok[u]) atomicOr(ix.status, kStatusSelectOverrun);   // never expected
         }
@@ -229,9 +238,10 @@ __device__ __forceinline__ uint32_t tk_vbin(float v, float vmin, float scale) {
     return t > 0.f ? (uint32_t)t : 0u;
 }
 
-// Exclusive scan of bins[TK_BINS] in place (TK_THREADS threads); returns, per
-// thread, the counts of its PER consecutive bins in loc.
-template <int PER>
+// Exclusive scan of bins[NB] in place (blockDim.x == THREADS threads, NB =
+// PER * THREADS); returns, per thread, the counts of its PER consecutive
+// bins in loc.
+template <int PER, int THREADS = TK_THREADS>
 __device__ __forceinline__ void tk_scan(uint32_t* bins, uint32_t* wsum, uint32_t (&loc)[PER]) {
     const int tid = threadIdx.x;
     uint32_t tot = 0;
@@ -241,8 +251,9 @@ __device__ __forceinline__ void tk_scan(uint32_t* bins, uint32_t* wsum, uint32_t
     if (lane_id() == 31) wsum[warp_id()] = winc;
     __syncthreads();
     if (warp_id() == 0) {
-        const uint32_t v = wsum[lane_id()];
-        wsum[lane_id()] = warp_incl_scan(v) - v;
+        const uint32_t v = lane_id() < THREADS / 32 ? wsum[lane_id()] : 0u;
+        const uint32_t x = warp_incl_scan(v) - v;
+        if (lane_id() < THREADS / 32) wsum[lane_id()] = x;
     }
     __syncthreads();
     uint32_t run = wsum[warp_id()] + winc - tot;
@@ -253,11 +264,51 @@ __device__ __forceinline__ void tk_scan(uint32_t* bins, uint32_t* wsum, uint32_t
     }
 }
 
-__global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArgs a) {
-    extern __shared__ unsigned long long keys[];   // [TK_MAX]
-    __shared__ uint32_t bins[TK_BINS];
-    __shared__ uint32_t wsum[TK_THREADS / 32];
-    __shared__ uint32_t s_min, s_max, s_big;
+// In-place ascending sort of n 64-bit keys (any n) with a bitonic network
+// whose merges all run ascending: the first step of a merge of blocks of size
+// kb pairs i with i ^ (kb - 1), the later steps pair i with i ^ j.  Places
+// past n then act as +infinity, so their compare-exchanges are skipped.
+__device__ void cta_sort_any_u64(unsigned long long* a, int n) {
+    const int np2 = next_pow2(n);
+    for (int kb = 2; kb <= np2; kb <<= 1) {
+        for (int j = kb >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                const int p = j == (kb >> 1) ? (i ^ (kb - 1)) : (i ^ j);
+                if (p > i && p < n) {
+                    const unsigned long long x = a[i], y = a[p];
+                    if (x > y) { a[i] = y; a[p] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Top-k for K_c <= TK_MAX, one CTA per query, two CTAs per SM.
+// 1. min / max of the distances; histogram over TKS_BINS bins in value space
+//    (bin = floor((dist - min) * TKS_BINS / (max - min)) in FP32, a monotone
+//    function of the distance); exclusive scan -> bin starts;
+// 2. the bin b_k holding rank kk - 1 (kk = min(k, candidates)); when it has
+//    more than TKS_BIG keys, the (kk - start)-th smallest key of that bin T
+//    (radix select on (distance key << 32 | id));
+// 3. keys of the bins below b_k, and of b_k up to T, are scattered into shared
+//    memory by bin (at most k - 1 + TKS_BIG keys);
+// 4. a key of a bin with at most TKS_BIG keys takes position bin start + the
+//    number of smaller keys in its bin; larger bins are sorted in place.
+// Positions below k go to the output.
+constexpr int TKS_THREADS = 512;
+constexpr int TKS_BINS = 2048;
+constexpr int TKS_BIG = 1024;
+constexpr int TKS_MAXHEAVY = 64;
+constexpr int TKS_U = 8;
+
+__global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, RerankArgs a, int kcap) {
+    extern __shared__ unsigned long long keys[];   // [kcap]
+    __shared__ uint32_t bins[TKS_BINS];
+    __shared__ uint32_t wsum[TKS_THREADS / 32];
+    __shared__ uint32_t hist[256], sc[2];
+    __shared__ uint32_t heavy[TKS_MAXHEAVY];
+    __shared__ uint32_t s_min, s_max, s_bk, s_nheavy;
     const int64_t qi = blockIdx.x;
     const int64_t cnt = min(a.cand_count[qi], a.qp.KC(qi));
     const int n = (int)(cnt < TK_MAX ? cnt : TK_MAX);
@@ -269,61 +320,128 @@ __global__ void __launch_bounds__(TK_THREADS) topk_kernel(DevIndex ix, RerankArg
     int64_t* oid = a.out_ids + a.qp.ooff(qi);
     float* od = a.out_dists + a.qp.ooff(qi);
     for (int i = n + tid; i < kq; i += blockDim.x) { oid[i] = -1; od[i] = INFINITY; }
-    if (n == 0) return;
-    if (tid == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_big = 0u; }
-    for (int i = tid; i < TK_BINS; i += blockDim.x) bins[i] = 0;
+    if (n == 0 || kq <= 0) return;
+    const uint32_t kk = (uint32_t)(kq < n ? kq : n);
+    if (tid == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_nheavy = 0u; }
+    for (int i = tid; i < TKS_BINS; i += blockDim.x) bins[i] = 0;
     __syncthreads();
+    // passes over the candidates load TKS_U values per thread before using them
+    constexpr int U = TKS_U;
+    const int step = U * TKS_THREADS;
     uint32_t mn = 0xFFFFFFFFu, mx = 0u;
-    for (int i = tid; i < n; i += blockDim.x) {
-        const uint32_t kk = f32_key(cd[i]);
-        mn = min(mn, kk);
-        mx = max(mx, kk);
+    for (int i0 = tid; i0 < n; i0 += step) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = i0 + u * TKS_THREADS < n ? cd[i0 + u * TKS_THREADS] : 0.f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * TKS_THREADS < n) {
+                const uint32_t kv = f32_key(v[u]);
+                mn = min(mn, kv);
+                mx = max(mx, kv);
+            }
+        }
     }
     mn = __reduce_min_sync(0xFFFFFFFFu, mn);
     mx = __reduce_max_sync(0xFFFFFFFFu, mx);
     if (lane_id() == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
     __syncthreads();
     const float vmin = key_f32(s_min);
-    const float scale = tk_scale(vmin, key_f32(s_max));
-    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&bins[tk_vbin(cd[i], vmin, scale)], 1u);
-    __syncthreads();
-    constexpr int PER = TK_BINS / TK_THREADS;
-    uint32_t loc[PER];
-    tk_scan<PER>(bins, wsum, loc);
-    uint32_t big = 0;
+    const float range = __fsub_rn(key_f32(s_max), vmin);
+    const float scale = range > 0.f ? fminf((float)TKS_BINS / range, 3.0e38f) : 0.f;
+    auto vbin = [&](float v) -> uint32_t {
+        const float t = fminf(__fmul_rn(__fsub_rn(v, vmin), scale), (float)(TKS_BINS - 1));
+        return t > 0.f ? (uint32_t)t : 0u;
+    };
+    for (int i0 = tid; i0 < n; i0 += step) {
+        float v[U];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) big |= loc[j] > (uint32_t)TK_BIG ? 1u : 0u;
-    if (big) s_big = 1u;
+        for (int u = 0; u < U; ++u) v[u] = i0 + u * TKS_THREADS < n ? cd[i0 + u * TKS_THREADS] : 0.f;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * TKS_THREADS < n) atomicAdd(&bins[vbin(v[u])], 1u);
+    }
     __syncthreads();
-    if (s_big) {
-        // degenerate distribution: full bitonic sort of the n keys
-        const int np2 = next_pow2(n);
-        for (int i = tid; i < np2; i += blockDim.x)
-            keys[i] = i < n ? (((unsigned long long)f32_key(cd[i]) << 32) | cand[i]) : ~0ull;
-        __syncthreads();
-        cta_bitonic_u64(keys, np2);
-        for (int i = tid; i < kq && i < n; i += blockDim.x) {
-            oid[i] = (int64_t)(keys[i] & 0xFFFFFFFFull);
-            od[i] = key_f32((uint32_t)(keys[i] >> 32));
+    constexpr int PER = TKS_BINS / TKS_THREADS;
+    uint32_t loc[PER];
+    tk_scan<PER, TKS_THREADS>(bins, wsum, loc);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint32_t b = (uint32_t)tid * PER + j;
+        const uint32_t st = bins[b];
+        if (loc[j] && st <= kk - 1 && kk - 1 < st + loc[j]) s_bk = b;
+    }
+    __syncthreads();
+    const uint32_t bk = s_bk;
+    const uint32_t stk = bins[bk];
+    const uint32_t nbk = (bk + 1 < (uint32_t)TKS_BINS ? bins[bk + 1] : (uint32_t)n) - stk;
+    unsigned long long T = ~0ull;
+    if (nbk > (uint32_t)TKS_BIG) {
+        T = cta_select_u64(n, kk - 1 - stk, [&](int64_t i) {
+            const float v = cd[i];
+            return vbin(v) == bk ? (((unsigned long long)f32_key(v) << 32) | cand[i]) : ~0ull;
+        }, hist, sc, 56);
+    }
+    for (int i0 = tid; i0 < n; i0 += step) {
+        float v[U];
+        uint32_t c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool in = i0 + u * TKS_THREADS < n;
+            v[u] = in ? cd[i0 + u * TKS_THREADS] : 0.f;
+            c[u] = in ? cand[i0 + u * TKS_THREADS] : 0u;
         }
-        return;
-    }
-    for (int i = tid; i < n; i += blockDim.x) {
-        const uint32_t p = atomicAdd(&bins[tk_vbin(cd[i], vmin, scale)], 1u);
-        keys[p] = ((unsigned long long)f32_key(cd[i]) << 32) | cand[i];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * TKS_THREADS >= n) continue;
+            const uint32_t b = vbin(v[u]);
+            const unsigned long long key = ((unsigned long long)f32_key(v[u]) << 32) | c[u];
+            if (b < bk || (b == bk && key <= T)) {
+                const uint32_t p = atomicAdd(&bins[b], 1u);
+                if (p < (uint32_t)kcap) keys[p] = key;
+                else atomicOr(ix.status, kStatusTopkOverrun);
+            }
+        }
     }
     __syncthreads();
-    for (int p = tid; p < n; p += blockDim.x) {
+    // bins[b] now ends bin b (b <= bk); bin b starts at bins[b - 1]
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint32_t b = (uint32_t)tid * PER + j;
+        if (b <= bk) {
+            const uint32_t st = b ? bins[b - 1] : 0u;
+            if (bins[b] - st > (uint32_t)TKS_BIG) {
+                const uint32_t h = atomicAdd(&s_nheavy, 1u);
+                if (h < (uint32_t)TKS_MAXHEAVY) heavy[h] = b;
+            }
+        }
+    }
+    const uint32_t nkeep = min(bins[bk], (uint32_t)kcap);
+    for (uint32_t p = tid; p < nkeep; p += blockDim.x) {
         const unsigned long long me = keys[p];
-        const uint32_t b = tk_vbin(key_f32((uint32_t)(me >> 32)), vmin, scale);
-        const int st = b ? (int)bins[b - 1] : 0;
-        const int en = (int)bins[b];
-        int rank = 0;
-        for (int j = st; j < en; ++j) rank += keys[j] < me ? 1 : 0;
-        const int pos = st + rank;
-        if (pos < kq) {
+        const uint32_t b = vbin(key_f32((uint32_t)(me >> 32)));
+        const uint32_t st = b ? bins[b - 1] : 0u;
+        const uint32_t en = bins[b];
+        if (en - st > (uint32_t)TKS_BIG) continue;                // sorted below
+        uint32_t rank = 0;
+        for (uint32_t j = st; j < en; ++j) rank += keys[j] < me ? 1u : 0u;
+        const uint32_t pos = st + rank;
+        if ((int)pos < kq) {
             oid[pos] = (int64_t)(me & 0xFFFFFFFFull);
             od[pos] = key_f32((uint32_t)(me >> 32));
+        }
+    }
+    __syncthreads();
+    const uint32_t nh = min(s_nheavy, (uint32_t)TKS_MAXHEAVY);
+    if (s_nheavy > (uint32_t)TKS_MAXHEAVY && tid == 0) atomicOr(ix.status, kStatusTopkOverrun);
+    for (uint32_t h = 0; h < nh; ++h) {
+        const uint32_t b = heavy[h];
+        const uint32_t st = b ? bins[b - 1] : 0u;
+        const uint32_t en = min(bins[b], (uint32_t)kcap);
+        cta_sort_any_u64(keys + st, (int)(en - st));
+        for (uint32_t i = st + tid; i < en && (int)i < kq; i += blockDim.x) {
+            oid[i] = (int64_t)(keys[i] & 0xFFFFFFFFull);
+            od[i] = key_f32((uint32_t)(keys[i] >> 32));
         }
     }
 }
@@ -427,8 +545,9 @@ cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cud
         topk_large_kernel<<<(unsigned)nq, TK_THREADS, (size_t)TK_HEAVY * 8, st>>>(ix, a);
         return cudaGetLastError();
     }
-    const int np2 = next_pow2((int)(a.kc > 1 ? a.kc : 1));
-    const size_t smem = (size_t)np2 * 8;
+    // keys held per query: all candidates, or at most k - 1 + TKS_BIG of them
+    const long long kcap = std::min<long long>(std::min<long long>(a.kc, TK_MAX), (long long)a.k + TKS_BIG);
+    const size_t smem = (size_t)std::max<long long>(kcap, 1) * 8;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -436,8 +555,7 @@ cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cud
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    (void)smem;
-    topk_kernel<<<(unsigned)nq, TK_THREADS, (size_t)TK_MAX * 8, st>>>(ix, a);
+    topk_kernel<<<(unsigned)nq, TKS_THREADS, smem, st>>>(ix, a, (int)std::max<long long>(kcap, 1));
     return cudaGetLastError();
 }
 

@@ -364,11 +364,16 @@ def test_large_candidate_pool_topk(bbc, oracle_lib):
         _check_topk(oracle_lib, idx, q[i], gi[i], gd[i], oi[i], od[i], True)
 
 
-@pytest.mark.parametrize("case", ["ties", "inner_product"])
-def test_large_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case):
-    """The large top-k on candidates with thousands of equal distances (one
-    block of ties above the shared-memory sort, one within it), and on inner
-    products whose distances span the sign boundary."""
+@pytest.mark.parametrize("case,kc,k", [("ties", 30000, 20000), ("inner_product", 30000, 20000),
+                                       ("ties", 12000, 5000), ("ties", 12000, 11500), ("ties", 12000, 1),
+                                       ("inner_product", 12000, 3000)])
+def test_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case, kc, k):
+    """Top-k on candidates with thousands of equal distances and on inner
+    products whose distances span the sign boundary.  K_c = 30,000 takes the
+    global-scratch form (one block of ties above its shared-memory sort, one
+    within it); K_c = 12,000 the shared-memory form, where a block of ties
+    holds the k-th place (k = 5,000: selected inside the bin) or lies below it
+    (k = 11,500: the bin is sorted in place)."""
     from synth import build_ivf_pq
     from synth.data import sift_shaped, embedding_shaped
     if case == "ties":
@@ -382,7 +387,7 @@ def test_large_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case):
         idx = build_ivf_pq(x, 16, 16, 8, "ip", kmeans_iters=3, pq_iters=3, pq_sample=5000)
     h = bbc.bbc_index_create(idx, 0)
     try:
-        nq, kc, k = len(q), 30000, 20000
+        nq = len(q)
         cand = np.tile(np.arange(kc, dtype=np.uint32), (nq, 1))
         cnt = np.full(nq, kc, dtype=np.int64)
         gi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
