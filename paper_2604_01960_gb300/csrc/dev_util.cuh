@@ -27,6 +27,25 @@ __device__ __forceinline__ unsigned long long f64_key(double f) {
     return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
 
+// f64_key((double)x) for a float x built with integer instructions (double
+// precision is slow on this GPU); subnormals, infinities and NaN take the
+// double path.
+__device__ __forceinline__ unsigned long long f64_key_f32(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    const uint32_t m = b & 0x7FFFFFu;
+    unsigned long long db;
+    if (e == 0u && m == 0u) {
+        db = 0ull;                                               // -0 orders as +0
+    } else if (e == 0u || e == 0xFFu) {
+        return f64_key((double)x);
+    } else {
+        db = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+             ((unsigned long long)m << 29);
+    }
+    return (db & 0x8000000000000000ull) ? ~db : (db | 0x8000000000000000ull);
+}
+
 __device__ __forceinline__ double key_f64(unsigned long long k) {
     unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
     return __longlong_as_double((long long)b);

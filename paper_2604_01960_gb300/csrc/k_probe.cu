@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(SEL_THREADS) probe_select_kernel(DevIndex ix, 
         }
         for (int o = 16; o; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));
         if (lane_id() == 0) {
-            ckey[i] = f64_key(ix.metric == BBC_METRIC_L2 ? (double)acc : -(double)acc);
+            ckey[i] = f64_key_f32(ix.metric == BBC_METRIC_L2 ? acc : -acc);
             if (ix.metric == BBC_METRIC_L2) atomicMax((int*)&s_smax, __float_as_int(acc));   // acc >= 0
         }
     }

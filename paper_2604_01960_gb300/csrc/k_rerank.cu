@@ -58,6 +58,85 @@ __device__ __forceinline__ void add_chunk_u8f(const uint4 raw, const float4* q4,
     }
 }
 
+// ||q - v||^2 = ||q||^2 + ||v||^2 - 2 <q, v> for integer rows, rounded once to
+// FP32.  The value is below d * 255^2, so for d * 255^2 < 2^32 it is formed
+// in 32-bit modular arithmetic and converted from 32 bits (the 64-bit
+// integer conversion runs on the slow double-precision pipe of this GPU).
+__device__ __forceinline__ float u8_dist(int qn2, unsigned vv, unsigned qv, int d) {
+    if (d <= 66051) return __uint2float_rn((unsigned)qn2 + vv - 2u * qv);
+    return (float)((long long)qn2 + (long long)vv - 2ll * (long long)qv);
+}
+
+// Rows of a fixed shape (G * CPL 16-byte chunks): G lanes per candidate, each
+// lane CPL consecutive chunks, the query's chunks held in registers, the
+// lane reduction unrolled; four candidates per lane group in flight.
+template <typename T, int G, int CPL, bool INT>
+__device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restrict__ vec, int d,
+                                            const uint32_t* sid, int64_t c0, int64_t c1, float* out,
+                                            const float4* q4, const uint4* qb, int qn2) {
+    constexpr int PW = 32 / G;
+    constexpr int U = 4;
+    const int ln = (int)lane_id(), grp = ln / G, gl = ln % G;
+    const int nwarp = blockDim.x / 32;
+    uint4 qq[CPL];
+    float4 qf[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        if (INT) qq[c] = qb[gl * CPL + c];
+        else qf[c] = q4[gl * CPL + c];
+    }
+    for (int64_t cb = c0 + (int64_t)warp_id() * PW * U; cb < c1; cb += (int64_t)nwarp * PW * U) {
+        uint32_t id[U];
+        bool live[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t c = cb + (int64_t)u * PW + grp;
+            live[u] = c < c1;
+            id[u] = live[u] ? sid[c - c0] : 0u;
+            if (live[u] && (int64_t)id[u] >= ix.n) {
+                atomicOr(ix.status, kStatusSelectOverrun);   // never expected
+                live[u] = false;
+            }
+        }
+        uint4 v[U][CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint4* row = reinterpret_cast<const uint4*>(vec + (size_t)id[u] * d) + gl * CPL;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) v[u][c] = live[u] ? __ldg(row + c) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float dist;
+            if (INT) {
+                unsigned qv = 0, vv = 0;
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    qv = __dp4a(v[u][c].x, qq[c].x, qv); qv = __dp4a(v[u][c].y, qq[c].y, qv);
+                    qv = __dp4a(v[u][c].z, qq[c].z, qv); qv = __dp4a(v[u][c].w, qq[c].w, qv);
+                    vv = __dp4a(v[u][c].x, v[u][c].x, vv); vv = __dp4a(v[u][c].y, v[u][c].y, vv);
+                    vv = __dp4a(v[u][c].z, v[u][c].z, vv); vv = __dp4a(v[u][c].w, v[u][c].w, vv);
+                }
+#pragma unroll
+                for (int o = G >> 1; o; o >>= 1) {
+                    qv += __shfl_xor_sync(0xFFFFFFFFu, qv, o);
+                    vv += __shfl_xor_sync(0xFFFFFFFFu, vv, o);
+                }
+                dist = ix.metric == BBC_METRIC_L2 ? u8_dist(qn2, vv, qv, d) : -(float)qv;
+            } else {
+                float acc = 0.f;
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) add_chunk_f32(v[u][c], qf[c], ix.metric, acc);
+#pragma unroll
+                for (int o = G >> 1; o; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+                dist = ix.metric == BBC_METRIC_L2 ? acc : -acc;
+            }
+            const int64_t c = cb + (int64_t)u * PW + grp;
+            if (c < c1 && gl == 0) out[c] = dist;
+        }
+    }
+}
+
 // One group of G lanes per candidate row; rows gathered with 16-byte loads.
 // Exact-u8 rows with a query whose components are integers in [0, 255] take
 // the integer path: <q, v> and <v, v> with dp4a, ||q - v||^2 = ||q||^2 +
@@ -96,6 +175,19 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     const int qn2 = s_qn2;
     const int64_t cnt = min(a.cand_count[qi], a.qp.KC(qi));
     const int nchunk = d * (int)sizeof(T) / 16;        // d * sizeof(T) is a multiple of 16
+    const int64_t cf0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
+    const int64_t cf1 = min(cf0 + RR_CAND_PER_CTA, cnt);
+    // the common row shapes: 128-byte integer rows, 512-byte FP32 rows
+    if (sizeof(T) == 1 && intpath && nchunk == 8) {
+        rerank_rows<T, 4, 2, true>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
+                                   reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2);
+        return;
+    }
+    if (sizeof(T) == 4 && nchunk == 32) {
+        rerank_rows<T, 16, 2, false>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
+                                     reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2);
+        return;
+    }
     int G = 1;                                         // lanes per candidate: a power of two <= 32
     while (G * 2 <= nchunk && G < 32) G *= 2;
     const int per_warp = 32 / G;
@@ -142,7 +234,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
                         vv += __shfl_xor_sync(0xFFFFFFFFu, vv, o);
                     }
                     dist[u] = ix.metric == BBC_METRIC_L2
-                                  ? (float)((long long)qn2 + (long long)vv - 2ll * (long long)qv)
+                                  ? u8_dist(qn2, vv, qv, d)
                                   : -(float)qv;
                 }
             } else {
@@ -177,7 +269,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
                         vv += __shfl_xor_sync(0xFFFFFFFFu, vv, o);
                     }
                     dist[u] = ix.metric == BBC_METRIC_L2
-                                  ? (float)((long long)qn2 + (long long)vv - 2ll * (long long)qv)
+                                  ? u8_dist(qn2, vv, qv, d)
                                   : -(float)qv;
                 } else {
                     float acc = 0.f;

@@ -95,14 +95,26 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
     const bool in_smem = nt <= (uint32_t)SELK_TCAP;
     // pass 1: buckets < tau* go straight out; bucket tau* is staged.  Four
     // entries per thread per step, their id gathers issued together.
+    // (the next step's entries are loaded while this step's ids are gathered)
     constexpr int SU = 4;
+    uint2 vn[SU];
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+        const int64_t i = (int64_t)u * bs + tid;
+        vn[u] = i < n ? region[i] : make_uint2(0, 0);
+    }
     for (int64_t i0 = 0; i0 < n; i0 += (int64_t)SU * bs) {
         uint2 v[SU];
         uint32_t b[SU], idv[SU];
 #pragma unroll
         for (int u = 0; u < SU; ++u) {
+            v[u] = vn[u];
+            const int64_t inext = i0 + (int64_t)(SU + u) * bs + tid;
+            vn[u] = inext < n ? region[inext] : make_uint2(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
             const int64_t i = i0 + (int64_t)u * bs + tid;
-            v[u] = i < n ? region[i] : make_uint2(0, 0);
             b[u] = i < n ? sel_bucket(v[u].x, st, map) : 0xFFFFFFFFu;
         }
 #pragma unroll
