@@ -54,6 +54,10 @@ struct ScanCfg {
     static constexpr int CHUNK = NCH <= 2 ? 4 : (NCH <= 6 ? 2 : 1);
     // CTAs per SM the shared-memory table allows (the launch bound for registers)
     static constexpr int MIN_CTAS = K * W * 4 <= 100 * 1024 ? 2 : 1;
+    // estimates are below M * 65535 < 2^EB; the sample's coarse histogram
+    // counts e >> SHC (2^11 bins), the fine one e mod 2^SHC
+    static constexpr int EB = M <= 8 ? 19 : (M <= 16 ? 20 : (M <= 32 ? 21 : (M <= 64 ? 22 : 23)));
+    static constexpr int SHC = EB - 11;
 };
 
 __device__ __forceinline__ uint32_t word_of(const uint4& v, int wi) {
@@ -341,7 +345,8 @@ __device__ __forceinline__ void stage_lut(const uint16_t* lq, uint32_t* lut) {
 template <int M, int BITS, bool MAIN, bool GLOBAL>
 __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& a, const QCtx& Q,
                                             bbc_collector_state* st, int nl, int g0, int g1,
-                                            const uint32_t* lut, const int4* ldesc, ScanShared& S) {
+                                            const uint32_t* lut, const int4* ldesc, ScanShared& S,
+                                            uint32_t* cf = nullptr) {
     using C = ScanCfg<M, BITS>;
     using Pos = typename std::conditional<GLOBAL, unsigned long long, uint32_t>::type;
     constexpr int CH = C::CHUNK;
@@ -433,6 +438,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                     if (pos < cap) region[pos] = make_uint2(e[u], (uint32_t)gbk[u] * 32u + ln);
                     else atomicOr(ix.status, kStatusRegionOverrun);
                     if (MAIN) atomicAdd(&S.bh[bin_of(e[u], dmin, sh)], 1u);
+                    else if (!GLOBAL) atomicAdd(&cf[e[u] >> C::SHC], 1u);     // coarse histogram of the sample
                 }
                 base += (Pos)__popc(bal[u]);
             }
@@ -452,66 +458,145 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
     }
 }
 
+// CTA-wide: the bin holding rank r (0-based) of the counts h[0..nb), nb <=
+// 8 * blockDim.x: res[0] = that bin, res[1] = r minus the count of the bins
+// before it.  Requires sum(h) > r.  wsum: 32 words of shared scratch.
+__device__ void cta_rank_bin(const uint32_t* h, int nb, uint32_t r, uint32_t* wsum, uint32_t* res) {
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int per = (nb + bs - 1) / bs;
+    uint32_t loc[8], tot = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int b = tid * per + j;
+        loc[j] = (j < per && b < nb) ? h[b] : 0u;
+        tot += loc[j];
+    }
+    const uint32_t winc = warp_incl_scan(tot);
+    if (lane_id() == 31) wsum[warp_id()] = winc;
+    __syncthreads();
+    if (warp_id() == 0) {
+        const int nw = bs >> 5;
+        const uint32_t v = (int)lane_id() < nw ? wsum[lane_id()] : 0u;
+        const uint32_t x = warp_incl_scan(v) - v;
+        if ((int)lane_id() < nw) wsum[lane_id()] = x;
+    }
+    __syncthreads();
+    uint32_t c = wsum[warp_id()] + winc - tot;
+    if (c <= r && r < c + tot) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j < per && r < c + loc[j]) {
+                res[0] = (uint32_t)(tid * per + j);
+                res[1] = r - c;
+                break;
+            }
+            c += loc[j];
+        }
+    }
+    __syncthreads();
+}
+
 // Phase C of Algorithm 1's Collect (Section 3.2, "Codebook Generation Based
 // on Estimated Distance") over the ns sampled objects at the start of the
-// region, by the whole CTA.  On entry S.dmin holds the smallest sampled
-// estimate and S.bh is zero; on exit S holds d_max, the shift, the
-// equal-depth map, the sample's bucket counts and tau.
+// region, by the whole CTA, given d_max (the t-th smallest sampled estimate,
+// t = min(K_c, ns)).  On entry S.dmin holds the smallest sampled estimate and
+// S.bh is zero; on exit S holds d_max, the shift, the equal-depth map, the
+// sample's counts per bin and tau.  One pass over the sample counts both the
+// bins of the objects at or below d_max (for the map) and the bins of all of
+// them (the counts Update works on).
+__device__ void codebook_from_dmax(const uint2* region, int64_t ns, int64_t kc, int m, uint32_t dmax,
+                                   ScanShared& S) {
+    const int tid = threadIdx.x, bs = blockDim.x;
+    if (tid == 0) {
+        S.dmax = dmax;
+        int sh = 0;
+        while (((dmax - S.dmin) >> sh) > 255u) ++sh;
+        S.sh = sh;
+    }
+    for (int i = tid; i < 256; i += bs) S.ehist[i] = 0;
+    __syncthreads();
+    const uint32_t dmin = S.dmin;
+    const int sh = S.sh;
+    for (int64_t i = tid; i < ns; i += 4 * bs) {
+        uint32_t e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i + u * bs < ns) {
+                const uint32_t b = bin_of(e[u], dmin, sh);
+                atomicAdd(&S.bh[b], 1u);
+                if (e[u] <= dmax) atomicAdd(&S.ehist[b], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    if (warp_id() == 0) {
+        const unsigned ln = lane_id();
+        uint32_t h[8], s = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { h[i] = S.ehist[ln * 8 + i]; s += h[i]; }
+        const unsigned long long inc = warp_incl_scan64(s);
+        const unsigned long long T = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        unsigned long long cum = inc - s;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            unsigned long long v = T ? ((unsigned long long)m * cum) / T : 0ull;
+            S.bmap[ln * 8 + i] = (uint8_t)(v > (unsigned long long)(m - 1) ? m - 1 : v);
+            cum += h[i];
+        }
+    }
+    __syncthreads();
+    if (warp_id() == 0) {
+        const uint32_t t0 = warp_update_bins(S.bh, S.bmap, m, kc);
+        const uint32_t e0 = etau_of(S, t0);
+        if (lane_id() == 0) { S.tau = t0; S.etau = e0; }
+    }
+    __syncthreads();
+}
+
+// Codebook when the sampling pass counted e >> shc into cf[0..2048): d_max
+// from that coarse histogram and one pass for the low shc bits.  cf (at least
+// max(2048, 2^shc) words) is overwritten.
+__device__ void build_codebook_hist(const uint2* region, int64_t ns, int64_t kc, int m, ScanShared& S,
+                                    uint32_t* cf, int shc) {
+    const int tid = threadIdx.x, bs = blockDim.x;
+    if (ns <= 0) {
+        if (tid == 0) { S.dmin = 0; S.dmax = 0; S.sh = 0; S.tau = (uint32_t)m; S.etau = 0xFFFFFFFFu; }
+        for (int i = tid; i < 256; i += bs) S.bmap[i] = 0;
+        __syncthreads();
+        return;
+    }
+    const int64_t t = ns < kc ? ns : kc;
+    __shared__ uint32_t wsum[32];
+    cta_rank_bin(cf, 2048, (uint32_t)(t - 1), wsum, S.sc);
+    const uint32_t hi = S.sc[0], r1 = S.sc[1];
+    const int nf = 1 << shc;
+    for (int i = tid; i < nf; i += bs) cf[i] = 0u;
+    __syncthreads();
+    for (int64_t i = tid; i < ns; i += 4 * bs) {
+        uint32_t e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i + u * bs < ns && (e[u] >> shc) == hi) atomicAdd(&cf[e[u] & (uint32_t)(nf - 1)], 1u);
+    }
+    __syncthreads();
+    cta_rank_bin(cf, nf, r1, wsum, S.sc);
+    codebook_from_dmax(region, ns, kc, m, (hi << shc) | S.sc[0], S);
+}
+
+// Codebook when d_max is found by a radix select over the sample (no
+// histogram gathered while sampling).
 __device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int m, ScanShared& S) {
     const int tid = threadIdx.x, bs = blockDim.x;
     if (ns > 0) {
         const int64_t t = ns < kc ? ns : kc;
         const uint32_t dmax = cta_select_u32(ns, (uint32_t)(t - 1), [&](int64_t i) { return region[i].x; },
                                              S.ehist, S.sc, 16);
-        if (tid == 0) {
-            S.dmax = dmax;
-            int sh = 0;
-            while (((dmax - S.dmin) >> sh) > 255u) ++sh;
-            S.sh = sh;
-        }
-        for (int i = tid; i < 256; i += bs) S.ehist[i] = 0;
-        __syncthreads();
-        const uint32_t dmin = S.dmin;
-        const int sh = S.sh;
-        for (int64_t i = tid; i < ns; i += 4 * bs) {
-            uint32_t e[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0xFFFFFFFFu;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (i + u * bs < ns && e[u] <= dmax) atomicAdd(&S.ehist[bin_of(e[u], dmin, sh)], 1u);
-        }
-        __syncthreads();
-        if (warp_id() == 0) {
-            const unsigned ln = lane_id();
-            uint32_t h[8], s = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { h[i] = S.ehist[ln * 8 + i]; s += h[i]; }
-            const unsigned long long inc = warp_incl_scan64(s);
-            const unsigned long long T = __shfl_sync(0xFFFFFFFFu, inc, 31);
-            unsigned long long cum = inc - s;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                unsigned long long v = T ? ((unsigned long long)m * cum) / T : 0ull;
-                S.bmap[ln * 8 + i] = (uint8_t)(v > (unsigned long long)(m - 1) ? m - 1 : v);
-                cum += h[i];
-            }
-        }
-        __syncthreads();
-        for (int64_t i = tid; i < ns; i += 4 * bs) {
-            uint32_t e[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = i + u * bs < ns ? region[i + u * bs].x : 0u;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (i + u * bs < ns) atomicAdd(&S.bh[bin_of(e[u], dmin, sh)], 1u);
-        }
-        __syncthreads();
-        if (warp_id() == 0) {
-            const uint32_t t0 = warp_update_bins(S.bh, S.bmap, m, kc);
-            const uint32_t e0 = etau_of(S, t0);
-            if (lane_id() == 0) { S.tau = t0; S.etau = e0; }
-        }
+        codebook_from_dmax(region, ns, kc, m, dmax, S);
+        return;
     } else {
         if (tid == 0) { S.dmin = 0; S.dmax = 0; S.sh = 0; S.tau = (uint32_t)m; S.etau = 0xFFFFFFFFu; }
         for (int i = tid; i < 256; i += bs) S.bmap[i] = 0;
@@ -526,6 +611,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan
     uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
     int4* ldesc = reinterpret_cast<int4*>(lut + C::LUT_WORDS);         // [nprobe]
     __shared__ ScanShared S;
+    __shared__ uint32_t cf[2048 > (1 << C::SHC) ? 2048 : (1 << C::SHC)];   // sample histograms
     const int64_t qi = blockIdx.x;
     const QCtx Q{a.qp.P(qi), a.qp.KC(qi), a.qp.rcap(qi), a.region + a.qp.roff(qi), a.lists + a.qp.poff(qi)};
     const int P = Q.P;
@@ -534,6 +620,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan
     // ---- Phase A: LUT staging and list layout ----
     stage_lut<M, BITS>(a.lut16 + qi * (int64_t)M * C::K, lut);
     for (int i = tid; i < 256; i += bs) S.bh[i] = 0;
+    for (int i = tid; i < 2048; i += bs) cf[i] = 0;
     if (tid == 0) {
         S.count = 0;
         S.dmin = 0xFFFFFFFFu;
@@ -575,12 +662,12 @@ __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan
 
     // ---- Phase B: sample ----
     const int gs = S.gs;
-    scan_blocks<M, BITS, false, false>(ix, a, Q, a.state + qi, P, 0, gs, lut, ldesc, S);
+    scan_blocks<M, BITS, false, false>(ix, a, Q, a.state + qi, P, 0, gs, lut, ldesc, S, cf);
     __syncthreads();
 
     // ---- Phase C: codebook ----
     const int64_t ns = (int64_t)min((long long)S.count, (long long)Q.cap);
-    build_codebook(Q.region, ns, Q.kc, a.m, S);
+    build_codebook_hist(Q.region, ns, Q.kc, a.m, S, cf, C::SHC);
     // ---- Phase D: main scan ----
     scan_blocks<M, BITS, true, false>(ix, a, Q, a.state + qi, P, gs, S.gtot, lut, ldesc, S);
     __syncthreads();
@@ -761,22 +848,33 @@ __global__ void __launch_bounds__(SCAN_THREADS) codebook_kernel(ScanArgs a) {
     }
 }
 
+// Largest dynamic shared memory a kernel can take next to its static shared
+// memory (227 KB per block in all).
+template <typename F>
+static int max_dyn_smem(F kernel) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 0;
+    return 227 * 1024 - (int)fa.sharedSizeBytes;
+}
+
 template <int M, int BITS>
 static cudaError_t launch_split_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, int G, unsigned int* counters,
                                   cudaStream_t st) {
     using C = ScanCfg<M, BITS>;
     const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)a.nprobe * sizeof(int4);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static int lim = -1;
+    if (lim < 0) {
+        const int l0 = max_dyn_smem(scan_split_kernel<M, BITS, false>);
+        const int l1 = max_dyn_smem(scan_split_kernel<M, BITS, true>);
+        const int l = l0 < l1 ? l0 : l1;
         cudaError_t e = cudaFuncSetAttribute(scan_split_kernel<M, BITS, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, l);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(scan_split_kernel<M, BITS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     220 * 1024);
+            e = cudaFuncSetAttribute(scan_split_kernel<M, BITS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, l);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        lim = l;
     }
-    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (smem > (size_t)lim) return cudaErrorInvalidValue;
     const long long items = nq * (long long)G;
     const unsigned grid = (unsigned)std::min<long long>(items, (long long)ix.num_sms * C::MIN_CTAS);
     cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned int), st);
@@ -793,14 +891,14 @@ template <int M, int BITS>
 static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st) {
     using C = ScanCfg<M, BITS>;
     const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)a.nprobe * sizeof(int4);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(scan_kernel<M, BITS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    static int lim = -1;
+    if (lim < 0) {
+        const int l = max_dyn_smem(scan_kernel<M, BITS>);
+        cudaError_t e = cudaFuncSetAttribute(scan_kernel<M, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, l);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        lim = l;
     }
-    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (smem > (size_t)lim) return cudaErrorInvalidValue;
     scan_kernel<M, BITS><<<(unsigned)nq, SCAN_THREADS, smem, st>>>(ix, a);
     return cudaGetLastError();
 }

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
     __shared__ uint32_t s_out, s_t;
     __shared__ int s_tau;
     __shared__ long long s_below;
+    __shared__ unsigned long long s_kmin, s_kmax;
     const int64_t qi = blockIdx.x;
     bbc_collector_state& st = a.state[qi];
     const int tid = threadIdx.x, bs = blockDim.x;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
                 }
             }
         }
-        if (ln == 0) { s_out = 0; s_t = 0; }
+        if (ln == 0) { s_out = 0; s_t = 0; s_kmin = ~0ull; s_kmax = 0ull; }
     }
     __syncthreads();
     const int tau = s_tau;
@@ -141,7 +142,32 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
     unsigned long long kth;
     if (in_smem) {
         const uint32_t cnt = min(s_t, (uint32_t)SELK_TCAP);
-        kth = cta_select_u64(cnt, s - 1, [&](int64_t i) { return tkeys[i]; }, hist, sc, 56);
+        // the staged keys share their bits above the highest bit where the
+        // smallest and largest differ: the radix select starts below them
+        unsigned long long kmn = ~0ull, kmx = 0ull;
+        for (uint32_t i = tid; i < cnt; i += bs) {
+            kmn = min(kmn, tkeys[i]);
+            kmx = max(kmx, tkeys[i]);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            kmn = min(kmn, (unsigned long long)__shfl_xor_sync(0xFFFFFFFFu, kmn, o));
+            kmx = max(kmx, (unsigned long long)__shfl_xor_sync(0xFFFFFFFFu, kmx, o));
+        }
+        if (ln == 0 && kmn <= kmx) {
+            atomicMin(&s_kmin, kmn);
+            atomicMax(&s_kmax, kmx);
+        }
+        __syncthreads();
+        const unsigned long long diff = s_kmin ^ s_kmax;
+        if (diff == 0ull) {
+            kth = s_kmin;                                      // one distinct key
+        } else {
+            const int top = ((63 - __clzll((long long)diff)) / 8) * 8;
+            const unsigned long long low = top >= 56 ? ~0ull : ((1ull << (top + 8)) - 1ull);
+            const unsigned long long high = s_kmin & ~low;
+            kth = high | cta_select_u64(cnt, s - 1, [&](int64_t i) { return tkeys[i] & low; }, hist, sc, top);
+        }
         for (uint32_t i0 = 0; i0 < cnt; i0 += bs) {
             const uint32_t i = i0 + tid;
             const bool take = i < cnt && tkeys[i] <= kth;
