@@ -1,7 +1,7 @@
 """Parity at full size, in the launch configuration the benchmark times.
 
 * 1M x 128 SIFT-shaped IVF-PQ (1,024 lists, PQ 32 x 8), 10,000 queries in one
-  bbc_search call, k = 10,000, nprobe = 256, K_c = 1.5 k: sampled queries
+  bbc_search call, k = 10,000, nprobe = 256, K_c = 1.4 k: sampled queries
   (first, last and spread between) are recomputed one by one by the oracle and
   must match bit for bit (integer data: the FP32 re-rank is exact).
 * 1M x 960 GIST-shaped sign-code index (4,096 lists), 4,096 queries in one
@@ -42,7 +42,7 @@ def _build(kind):
 
 def test_sift_1m_full_batch_sampled_parity(bbc, oracle_lib):
     w, idx, q = _build("sift")
-    k, nprobe, ratio = w.k, w.nprobe, 1.5
+    k, nprobe, ratio = w.k, w.nprobe, 1.4
     kc = int(np.ceil(ratio * k - 1e-9))
     h = bbc.bbc_index_create(idx, 0)
     try:
