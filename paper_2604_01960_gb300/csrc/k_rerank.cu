@@ -141,7 +141,11 @@ __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restr
 // Exact-u8 rows with a query whose components are integers in [0, 255] take
 // the integer path: <q, v> and <v, v> with dp4a, ||q - v||^2 = ||q||^2 +
 // ||v||^2 - 2 <q, v> in exact integer arithmetic.
-template <typename T>
+// FAST: rows of the two common shapes (128-byte integer rows with an integer
+// query, 512-byte FP32 rows) take the fixed-shape path.  Other shapes use the
+// FAST = false instantiation, whose general loop then keeps its own register
+// allocation and schedule.
+template <typename T, bool FAST>
 __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankArgs a, const T* __restrict__ vec) {
     extern __shared__ uint4 rsm[];
     const int d = ix.d;
@@ -178,12 +182,12 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     const int64_t cf0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
     const int64_t cf1 = min(cf0 + RR_CAND_PER_CTA, cnt);
     // the common row shapes: 128-byte integer rows, 512-byte FP32 rows
-    if (sizeof(T) == 1 && intpath && nchunk == 8) {
+    if (FAST && sizeof(T) == 1 && intpath && nchunk == 8) {
         rerank_rows<T, 4, 2, true>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
                                    reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2);
         return;
     }
-    if (sizeof(T) == 4 && nchunk == 32) {
+    if (FAST && sizeof(T) == 4 && nchunk == 32) {
         rerank_rows<T, 16, 2, false>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
                                      reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2);
         return;
@@ -298,9 +302,11 @@ cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, c
     dim3 grid((unsigned)((a.kc + RR_CAND_PER_CTA - 1) / RR_CAND_PER_CTA), (unsigned)nq);
     const size_t smem = sizeof(float) * ix.d + ix.d + 16;
     if (a.use_u8 && ix.vec_u8)
-        rerank_kernel<uint8_t><<<grid, RR_THREADS, smem, st>>>(ix, a, ix.vec_u8);
+        rerank_kernel<uint8_t, true><<<grid, RR_THREADS, smem, st>>>(ix, a, ix.vec_u8);
+    else if (ix.d * 4 == 32 * 16)
+        rerank_kernel<float, true><<<grid, RR_THREADS, smem, st>>>(ix, a, ix.vectors);
     else
-        rerank_kernel<float><<<grid, RR_THREADS, smem, st>>>(ix, a, ix.vectors);
+        rerank_kernel<float, false><<<grid, RR_THREADS, smem, st>>>(ix, a, ix.vectors);
     return cudaGetLastError();
 }
 
