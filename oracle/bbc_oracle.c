@@ -312,7 +312,7 @@ static int32_t bin_of(uint32_t e, const oracle_codebook* cb) {
 
 static int32_t bucket_of(uint32_t e, const oracle_codebook* cb) { return cb->map[bin_of(e, cb)]; }
 
-/* Update (Algorithm 1, lines 5-11): first bucket whose running count reaches
+/* Update (Algorithm 1): first bucket whose running count reaches
  * Kc ("reaches or exceeds", Section 3.2 text and the Figure 3 example). */
 int32_t oracle_update(const int64_t* counts, int32_t m, int64_t Kc) {
     int64_t s = 0;
@@ -360,7 +360,7 @@ void oracle_build_codebook(const uint32_t* sample_e, int64_t ns, int64_t Kc, int
     free(s);
 }
 
-/* Collect (Algorithm 1, lines 12-24) over the scanned lists in probe order.
+/* Collect (Algorithm 1) over the scanned lists in probe order.
  * e/ids hold the scanned objects list after list; list_ofs[j]..list_ofs[j+1]
  * is list j.  Outputs the Kc candidates (ascending (e, id)), the codebook,
  * the final bucket counts (counts[m]) and returns the number written. */
@@ -380,12 +380,12 @@ int64_t oracle_bucket_collect(const uint32_t* e, const int64_t* ids, const int64
     int64_t* cnt = (int64_t*)calloc((size_t)m, sizeof(int64_t));
     int64_t* cap = (int64_t*)calloc((size_t)m, sizeof(int64_t));
     ukey** B = (ukey**)calloc((size_t)m, sizeof(ukey*));
-    int32_t tau = m;                                  /* line 13: tau <- infinity */
+    int32_t tau = m;                                  /* tau starts at infinity */
     int64_t pushed = 0;
-    for (int32_t j = 0; j < nl; ++j) {                /* line 15: each cluster in probe order */
+    for (int32_t j = 0; j < nl; ++j) {                /* each cluster in probe order */
         for (int64_t i = list_ofs[j]; i < list_ofs[j + 1]; ++i) {
-            int32_t a = bucket_of(e[i], cb);           /* Push, line 2 */
-            if (a <= tau) {                            /* Push, line 3 */
+            int32_t a = bucket_of(e[i], cb);           /* Push: bucket of the estimate */
+            if (a <= tau) {                            /* Push: admitted when at or below tau */
                 if (cnt[a] == cap[a]) {
                     cap[a] = cap[a] ? 2 * cap[a] : 64;
                     B[a] = (ukey*)realloc(B[a], sizeof(ukey) * (size_t)cap[a]);
@@ -396,7 +396,7 @@ int64_t oracle_bucket_collect(const uint32_t* e, const int64_t* ids, const int64
                 ++pushed;
             }
         }
-        tau = oracle_update(cnt, m, Kc);              /* line 18 */
+        tau = oracle_update(cnt, m, Kc);              /* Update after the cluster */
     }
     int64_t nres = 0;
     if (tau >= m) {                                    /* fewer than Kc objects in total */
@@ -408,7 +408,7 @@ int64_t oracle_bucket_collect(const uint32_t* e, const int64_t* ids, const int64
         free(all);
         cb->below = nres;
     } else {
-        /* lines 19-21: buckets before tau; lines 22-23: top-s of bucket tau */
+        /* buckets before tau, then the top-s of bucket tau */
         ukey* res = (ukey*)malloc(sizeof(ukey) * (size_t)Kc);
         for (int32_t a = 0; a < tau; ++a)
             for (int64_t i = 0; i < cnt[a]; ++i) res[nres++] = B[a][i];

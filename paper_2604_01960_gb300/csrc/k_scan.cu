@@ -6,22 +6,22 @@
 // Phase B  sample: scan the first lists in probe order -- at least
 //          min(sample_min, nprobe) of them, extended until they hold
 //          min(K_c, S_q) vectors -- and append every (estimated distance, id)
-//          to the query's region (threshold = infinity, Algorithm 1 line 13).
+//          to the query's region (threshold = infinity, as Algorithm 1 starts).
 // Phase C  codebook (Section 3.2, "Codebook Generation Based on Estimated
 //          Distance"): d_min = smallest, d_max = t-th smallest sampled
 //          distance with t = min(K_c, sample size); n_ew = 256 equal-width
 //          bins of width 2^sh over [d_min, d_max]; bin(e) = clamp((e - d_min)
 //          >> sh, 0, 255) (Eq. remap); an equal-depth remap map[256] -> [0, m)
 //          from the bins' cumulative counts; bucket counts of the sample and
-//          the threshold bucket tau (Update, Algorithm 1 lines 5-11: first
+//          the threshold bucket tau (Update, Algorithm 1: first
 //          bucket whose running count reaches K_c).
 // Phase D  scan the remaining lists: per vector, estimated distance
 //          e = sum_m LUT[m][code_m], bucket a = map[bin(e)], and Push
-//          (Algorithm 1 lines 1-4): append (e, id) and count it when a <= tau.
-//          Warps refresh tau from the shared bucket counts after every chunk
+//          (Algorithm 1): append (e, id) and count it when a <= tau.
+//          Warps refresh tau from the shared counts after every fourth chunk
 //          (the paper updates once per cluster; tau only moves down, and a
 //          stale tau only admits extra objects, never drops a needed one).
-// The final selection (Algorithm 1 lines 19-23) runs in k_select.cu.
+// The final selection (the last step of Algorithm 1's Collect) runs in k_select.cu.
 //
 // GPU mapping: one lane per vector; the lane's code row sits in registers
 // (coalesced 512-byte chunk loads); each LUT read goes to bank (lane + slot)
@@ -39,6 +39,10 @@
 namespace bbc {
 
 constexpr int SCAN_THREADS = 512;
+// A warp runs Update after every kUpdateEvery-th chunk of its main scan (a
+// power of two).  A staler tau only admits extra objects; fewer Updates
+// leave more issue slots to the lookups.
+constexpr int kUpdateEvery = 4;
 
 template <int M, int BITS>
 struct ScanCfg {
@@ -443,7 +447,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                 base += (Pos)__popc(bal[u]);
             }
         }
-        if (MAIN && (it & 1) == 0) {
+        if (MAIN && (it & (kUpdateEvery - 1)) == 0) {
             if (GLOBAL) {
                 if (warp_id() == 0) flush_and_update(S, st, a.m, Q.kc);
             } else {

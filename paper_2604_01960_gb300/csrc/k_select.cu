@@ -1,4 +1,4 @@
-// S7: final collection (Algorithm 1, lines 19-23), one CTA per query.
+// S7: final collection (Algorithm 1, the last step of Collect), one CTA per query.
 //
 // The bucket counts of the appended objects give the exact threshold bucket
 // tau* = first bucket whose running count reaches K_c (Update on the final

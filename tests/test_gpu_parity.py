@@ -403,6 +403,36 @@ def test_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case, kc, k):
         bbc.bbc_index_free(h)
 
 
+@pytest.mark.parametrize("d", [128, 64])
+@pytest.mark.parametrize("frac", [0.0, 0.37])
+def test_rerank_integer_rows_integer_and_fractional_queries(bbc, oracle_lib, d, frac):
+    """Re-rank + top-k over the exact u8 copy: integer queries take the integer
+    dot-product path (bit-exact), fractional ones the FP32 path (1e-5 of FP64);
+    d = 128 runs the fixed-shape kernel, d = 64 the general one."""
+    from synth import build_ivf_pq
+    from synth.data import sift_shaped
+    x, q = sift_shaped(20000, 4, d=d, n_centers=100)
+    idx = build_ivf_pq(x, 16, d // 8, 8, "l2", kmeans_iters=3, pq_iters=3, pq_sample=5000)
+    h = bbc.bbc_index_create(idx, 0)
+    try:
+        assert bbc.bbc_index_info(h)["vectors_u8_exact"] == 1
+        q = (q + np.float32(frac)).astype(np.float32)
+        nq, kc, k = len(q), 12000, 3000
+        cand = np.tile(np.arange(kc, dtype=np.uint32), (nq, 1))
+        cnt = np.full(nq, kc, dtype=np.int64)
+        gi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+        gd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+        bbc.bbc_rerank_topk(h, cuda(q), nq, cuda(cand), cuda(cnt), kc, k, gi, gd)
+        sync_ok(bbc, h)
+        gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+        for i in range(nq):
+            d64 = oracle_lib.rerank(q[i], idx.vectors, cand[i].astype(np.int64), "l2")
+            oi, od = oracle_lib.topk_final(d64, cand[i].astype(np.int64), k)
+            _check_topk(oracle_lib, idx, q[i], gi[i], gd[i], oi, od, frac == 0.0)
+    finally:
+        bbc.bbc_index_free(h)
+
+
 @pytest.mark.parametrize("kind", ["tiny", "sift", "ragged"])
 def test_split_scan_equals_one_cta_per_query(bbc, kind):
     """Several CTAs per query (persistent (query, part) items, global collector
