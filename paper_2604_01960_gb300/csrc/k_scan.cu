@@ -18,7 +18,7 @@
 // Phase D  scan the remaining lists: per vector, estimated distance
 //          e = sum_m LUT[m][code_m], bucket a = map[bin(e)], and Push
 //          (Algorithm 1): append (e, id) and count it when a <= tau.
-//          Warps refresh tau from the shared counts after every fourth chunk
+//          Warps refresh tau from the shared counts after every eighth chunk
 //          (the paper updates once per cluster; tau only moves down, and a
 //          stale tau only admits extra objects, never drops a needed one).
 // The final selection (the last step of Algorithm 1's Collect) runs in k_select.cu.
@@ -42,7 +42,7 @@ constexpr int SCAN_THREADS = 512;
 // A warp runs Update after every kUpdateEvery-th chunk of its main scan (a
 // power of two).  A staler tau only admits extra objects; fewer Updates
 // leave more issue slots to the lookups.
-constexpr int kUpdateEvery = 4;
+constexpr int kUpdateEvery = 8;
 
 template <int M, int BITS>
 struct ScanCfg {
