@@ -1381,9 +1381,18 @@ int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, 
             return fail(BBC_ERR_CUDA, "event creation failed");
         }
     }
+    // the copy-out of the last sub-batch is not hidden behind compute: the
+    // remainder that fits one sub-batch is split in two halves
     int it = 0;
-    for (int64_t q0 = 0; q0 < nq; q0 += sb, ++it) {
-        const int64_t nc = std::min(sb, nq - q0);
+    int64_t nc = 0;
+    bool halved = false;
+    for (int64_t q0 = 0; q0 < nq; q0 += nc, ++it) {
+        const int64_t rem = nq - q0;
+        nc = std::min(sb, rem);
+        if (nbuf == 2 && !halved && it > 0 && rem <= sb && rem >= 4ll * ix->dev.num_sms) {
+            nc = (rem + 1) / 2;
+            halved = true;
+        }
         const int b = it % nbuf;
         float* dq = reinterpret_cast<float*>(ws + p.off_q) + (size_t)b * sb * d;
         int64_t* di = reinterpret_cast<int64_t*>(ws + p.off_ids) + (size_t)b * sb * k;
