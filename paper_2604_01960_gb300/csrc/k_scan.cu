@@ -55,7 +55,7 @@ struct ScanCfg {
     static constexpr int NCH = CBP / 16;
     static constexpr int LUT_WORDS = K * W;
     // 32-vector blocks per warp iteration (their code loads in flight together)
-    static constexpr int CHUNK = NCH <= 2 ? 4 : (NCH <= 6 ? 2 : 1);
+    static constexpr int CHUNK = NCH <= 2 ? 3 : (NCH <= 6 ? 2 : 1);
     // CTAs per SM the shared-memory table allows (the launch bound for registers)
     static constexpr int MIN_CTAS = K * W * 4 <= 100 * 1024 ? 2 : 1;
     // estimates are below M * 65535 < 2^EB; the sample's coarse histogram
