@@ -522,7 +522,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     # DRAM bytes per launch from an ncu capture of the current kernel (profiles/), scaled by queries
     traffic = None
     if dom == "scan" and w.name == "ivfpq-sift-1m-d128" and idx.pq_m == 32 and nprobe == 256:
-        traffic = (73.31e6 + 322.80e6) / 1300 * nq          # scan_kernel<32, 8>, 1,300-query capture
+        traffic = (69.20e6 + 349.11e6) / 1300 * nq          # scan_kernel<32, 8>, 1,300-query capture
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": "152 SMs x 32 four-byte shared-memory lookups per clock x 2070 MHz" if dom == "scan"
