@@ -12,15 +12,19 @@
 //          distance with t = min(K_c, sample size); n_ew = 256 equal-width
 //          bins of width 2^sh over [d_min, d_max]; bin(e) = clamp((e - d_min)
 //          >> sh, 0, 255) (Eq. remap); an equal-depth remap map[256] -> [0, m)
-//          from the bins' cumulative counts; bucket counts of the sample and
-//          the threshold bucket tau (Update, Algorithm 1: first
-//          bucket whose running count reaches K_c).
+//          from the bins' cumulative counts; counts of the sample and the
+//          threshold bucket tau (Update, Algorithm 1: first bucket whose
+//          running count reaches K_c).  d_max comes from a coarse histogram
+//          of e counted while sampling plus one pass for the low bits.
 // Phase D  scan the remaining lists: per vector, estimated distance
 //          e = sum_m LUT[m][code_m], bucket a = map[bin(e)], and Push
-//          (Algorithm 1): append (e, id) and count it when a <= tau.
-//          Warps refresh tau from the shared counts after every eighth chunk
-//          (the paper updates once per cluster; tau only moves down, and a
-//          stale tau only admits extra objects, never drops a needed one).
+//          (Algorithm 1): append (e, id) and count it when a <= tau.  The
+//          counts are kept per bin (a bucket is a union of consecutive bins,
+//          so Update on them gives the same tau), and a <= tau is tested as
+//          e <= the largest estimate whose bucket is <= tau.  Warps refresh
+//          tau after every eighth chunk (the paper updates once per cluster;
+//          tau only moves down, and a stale tau only admits extra objects,
+//          never drops a needed one).
 // The final selection (the last step of Algorithm 1's Collect) runs in k_select.cu.
 //
 // GPU mapping: one lane per vector; the lane's code row sits in registers
@@ -28,7 +32,8 @@
 // mod 32, so the 32 reads of a warp never conflict.  The region stores
 // (estimated distance, list position); positions become ids in k_select.cu,
 // so the hot loop never waits on an id load.  Appends are warp-
-// aggregated (ballot + one shared atomic per warp) into a contiguous region.
+// aggregated (ballots + one shared atomic per warp and chunk) into a
+// contiguous region.
 #include <algorithm>
 #include <climits>
 #include <type_traits>
@@ -54,10 +59,13 @@ struct ScanCfg {
     static constexpr int CBP = (CB + 15) / 16 * 16;
     static constexpr int NCH = CBP / 16;
     static constexpr int LUT_WORDS = K * W;
-    // 32-vector blocks per warp iteration (their code loads in flight together)
-    static constexpr int CHUNK = NCH <= 2 ? 3 : (NCH <= 6 ? 2 : 1);
     // CTAs per SM the shared-memory table allows (the launch bound for registers)
     static constexpr int MIN_CTAS = K * W * 4 <= 100 * 1024 ? 2 : 1;
+    // threads of the one-CTA-per-query kernel: a table too large for two
+    // CTAs per SM gets 32 warps in one CTA
+    static constexpr int THREADS = MIN_CTAS == 2 ? 512 : 1024;
+    // 32-vector blocks per warp iteration (their code loads in flight together)
+    static constexpr int CHUNK = NCH <= 2 ? 3 : (NCH <= 6 && THREADS == 512 ? 2 : 1);
     // estimates are below M * 65535 < 2^EB; the sample's coarse histogram
     // counts e >> SHC (2^11 bins), the fine one e mod 2^SHC
     static constexpr int EB = M <= 8 ? 19 : (M <= 16 ? 20 : (M <= 32 ? 21 : (M <= 64 ? 22 : 23)));
@@ -609,7 +617,7 @@ __device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int 
 }
 
 template <int M, int BITS>
-__global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan_kernel(DevIndex ix, ScanArgs a) {
+__global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan_kernel(DevIndex ix, ScanArgs a) {
     using C = ScanCfg<M, BITS>;
     extern __shared__ uint4 dsm[];
     uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
@@ -903,7 +911,7 @@ static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs&
         lim = l;
     }
     if (smem > (size_t)lim) return cudaErrorInvalidValue;
-    scan_kernel<M, BITS><<<(unsigned)nq, SCAN_THREADS, smem, st>>>(ix, a);
+    scan_kernel<M, BITS><<<(unsigned)nq, C::THREADS, smem, st>>>(ix, a);
     return cudaGetLastError();
 }
 
