@@ -1,7 +1,7 @@
-// S8: exact distances of the collected candidates (the re-rank of Section 2,
-// "unbounded methods ... gather n_cand candidates ... which are then
-// re-ranked"); S9: the k smallest (distance, id), ascending (Algorithm 4,
-// last line).
+// S8: exact distances of the collected candidates (the re-rank of Section 2:
+// methods without an error bound collect n_cand candidates by estimated
+// distance and compute their exact distances); S9: the k smallest
+// (distance, id), ascending (the result Algorithm 4 returns).
 //
 // Re-rank: a group of G lanes gathers one candidate row with 16-byte loads
 // (G = row bytes / 16, at most 32) and reduces with shuffles.  Rows come from
@@ -311,16 +311,14 @@ cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, c
 }
 
 // ---------------------------------------------------------------------------
-// S9 top-k.  Keys: order-preserving distance bits << 32 | id (unique).
-// 1. min / max of the distances over the candidates;
-// 2. histogram over TK_BINS fine bins in value space, bin =
-//    floor((dist - min) * TK_BINS / (max - min)) evaluated in FP32 -- a
-//    monotone function of the distance (rounding is monotone);
-// 3. exclusive scan -> bin starts; scatter keys into shared memory by bin;
-// 4. every key's final position = its bin's start + the number of keys of its
-//    bin that are smaller; positions < k are written straight to the output.
-// A bin with more than TK_BIG keys (many exactly equal distances) would make
-// step 4 quadratic; then the CTA sorts all keys with a bitonic network instead.
+// S9 top-k.  Keys: order-preserving distance bits << 32 | id (unique).  Both
+// forms count keys into fine bins in value space, bin = floor((dist - min) *
+// bins / (max - min)) evaluated in FP32 -- a monotone function of the
+// distance (rounding is monotone) -- scatter them by bin and give each key
+// its bin's start plus the number of smaller keys in its bin; bins with many
+// keys (many equal distances) are sorted instead.  The constants below belong
+// to the form for K_c above TK_MAX (global scratch); the shared-memory form
+// has its own (TKS_*).
 constexpr int TK_THREADS = 1024;
 constexpr int TK_MAX = 16384;    // candidates handled in shared memory per query
 constexpr int TK_BINS = 4096;
