@@ -1356,20 +1356,22 @@ int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, 
     if ((rc = get_workspace(ix, st, p.total, &ws))) return rc;
     const int d = ix->dev.d;
     // Sub-batches whose results go back on a second stream while the next
-    // sub-batch computes: a sub-batch keeps >= 8 queries per SM (one CTA per
-    // query fills the GPU), two result buffers alternate.
+    // sub-batches compute: a sub-batch keeps >= 8 queries per SM (one CTA per
+    // query fills the GPU), up to three result buffers rotate so that a slow
+    // copy-out does not hold up the next sub-batch.
     int64_t sb = std::max<int64_t>(8ll * ix->dev.num_sms, (nq + 3) / 4);
     sb = std::min<int64_t>(sb, std::max<int64_t>(1, p.chunk / 2));
-    const int nbuf = 2 * sb <= p.chunk ? 2 : 1;
+    int nbuf = 2 * sb <= p.chunk ? 2 : 1;
+    if (nbuf == 2 && 3 * sb <= p.chunk) nbuf = 3;
     if (nbuf == 1) sb = p.chunk;
     {
         std::lock_guard<std::mutex> lk(ix->mu);
         if (!ix->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&ix->copy_stream, cudaStreamNonBlocking));
     }
     cudaStream_t cs = ix->copy_stream;
-    cudaEvent_t done[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    cudaEvent_t done[3] = {nullptr, nullptr, nullptr}, freed[3] = {nullptr, nullptr, nullptr};
     auto cleanup = [&]() {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 3; ++b) {
             if (done[b]) cudaEventDestroy(done[b]);
             if (freed[b]) cudaEventDestroy(freed[b]);
         }
@@ -1389,7 +1391,7 @@ int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, 
     for (int64_t q0 = 0; q0 < nq; q0 += nc, ++it) {
         const int64_t rem = nq - q0;
         nc = std::min(sb, rem);
-        if (nbuf == 2 && !halved && it > 0 && rem <= sb && rem >= 4ll * ix->dev.num_sms) {
+        if (nbuf >= 2 && !halved && it > 0 && rem <= sb && rem >= 4ll * ix->dev.num_sms) {
             nc = (rem + 1) / 2;
             halved = true;
         }
