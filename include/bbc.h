@@ -93,9 +93,16 @@ typedef struct {
  * permutation, pq shape supported): BBC_ERR_FORMAT / BBC_ERR_ARG otherwise. */
 int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out);
 
-/* Read an index file ("BBCIDX01" format: 64-byte header, then centroids,
- * list_offsets, ids, codes, codebooks, vectors, each 64-byte aligned) and
- * create the device index.  BBC_ERR_IO / BBC_ERR_FORMAT on a bad file. */
+/* Read an index file and create the device index (the paper's indexing
+ * phase, Section 2, done offline; this call only loads its result).  Format
+ * "BBCIDX01", little-endian: a 64-byte header {magic[8], u32 version = 1,
+ * u32 quantizer, u32 metric, u32 d, u64 n, u32 nlist, u32 pq_m, u32 pq_bits},
+ * then arrays each starting on a 64-byte boundary.  Quantizer BBC_QUANT_PQ:
+ * centroids, list_offsets, ids, codes, codebooks, vectors, laid out as in
+ * bbc_index_host.  Quantizer BBC_QUANT_SIGN (pq_m = pq_bits = 0):
+ * centroids, list_offsets, ids, rotation, vectors, as in bbc_sign_host.
+ * BBC_ERR_IO when the file cannot be opened, BBC_ERR_FORMAT on a bad or
+ * truncated file, and the errors of bbc_index_create(_sign). */
 int bbc_index_load(const char* path, int device, bbc_index** out);
 
 /* Host-side description of an IVF index with the 1-bit sign quantizer of the
@@ -163,6 +170,13 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  reported distances of members placed by the copy's bound
  *                  are the copy's scores (see bbc_rerank_bounds).  Applies when
  *                  the exact u8 re-rank is not in use.
+ *   "region_cap"   entries of each query's collector region (the buffer the
+ *                  scan appends (estimated distance, position) pairs to).
+ *                  0 (default) = the total length of the nprobe longest lists,
+ *                  which holds every scanned object.  A smaller value bounds
+ *                  the workspace; appends past it are dropped and latch
+ *                  BBC_ERR_CAPACITY in the status word (bbc_stream_status),
+ *                  and that call's results are then incomplete.
  *   "bound_scale"  sign-code indexes: factor on the residual term ||q'|| e of
  *                  the bounds, in (0, 1].  1 (default) gives hard bounds and
  *                  results equal to the exact top-k of the probed lists;
@@ -277,9 +291,13 @@ int bbc_collect(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
  * more scratch than that -- about nq * (2 * pq_m * 2^pq_bits + 1344 +
  * 8 * cap) bytes, cap = total length of the nprobe longest lists -- returns
  * BBC_ERR_ARG before launching anything.  The first call on a device looks
- * up the array's device address with that device current; make that first
- * call before any stream capture.  All calls share the array, so calls whose
- * kernels overlap on the GPU race: order them on one stream. */
+ * up the array's device address with that device current and keeps it for
+ * the life of the process; make that first call before any stream capture,
+ * and do not use this entry point after cudaDeviceReset (the array may move).
+ * All calls share the array, so calls whose kernels overlap on the GPU race:
+ * order them on one stream.  The scan always runs one CTA per query (the
+ * split form needs zeroed counters), so small batches run slower than with
+ * bbc_collect, and these calls are not recorded by bbc_profile_read. */
 #define BBC_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 int bbc_collect_static(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
                        const int32_t* probe_lists, int64_t kc, uint32_t* out_ids, int64_t* out_count,

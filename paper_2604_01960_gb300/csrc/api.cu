@@ -15,6 +15,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -23,6 +24,20 @@
 
 namespace bbc {
 bool scan_supported(int M, int bits);
+
+cudaError_t smem_attr_once(const void* kernel, int bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::set<std::tuple<const void*, int, int>> done;
+    const auto key = std::make_tuple(kernel, dev, bytes);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(key)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
 }
 
 using namespace bbc;
@@ -92,6 +107,14 @@ struct bbc_index {
     DevIndex dev{};
     std::vector<void*> owned;
     std::vector<int64_t> cap_prefix;     // cap_prefix[p] = sum of the p longest lists
+    int64_t region_cap = 0;              // entries of a query's collector region; 0 = cap_prefix[nprobe]
+    // Capacity of the collector region of a query probing nprobe lists: every
+    // scanned object fits unless "region_cap" lowers it (appends past the
+    // capacity are dropped and latch a region overrun).
+    int64_t cap_for(int nprobe) const {
+        const int64_t c = cap_prefix[nprobe];
+        return region_cap > 0 && region_cap < c ? region_cap : c;
+    }
     // parameters
     double kc_ratio = 1.5;
     int buckets = 64;
@@ -109,11 +132,12 @@ struct bbc_index {
     struct GraphKey {
         const void* q; int64_t nq; int k; int nprobe; void* oi; void* od; cudaStream_t st;
         double kc_ratio; int buckets, sample_lists, split, probe_gemm, rerank, prec;
+        int64_t rcap;
         bool operator<(const GraphKey& o) const {
             return std::tie(q, nq, k, nprobe, oi, od, st, kc_ratio, buckets, sample_lists, split, probe_gemm, rerank,
-                            prec) <
+                            prec, rcap) <
                    std::tie(o.q, o.nq, o.k, o.nprobe, o.oi, o.od, o.st, o.kc_ratio, o.buckets, o.sample_lists, o.split,
-                            o.probe_gemm, o.rerank, o.prec);
+                            o.probe_gemm, o.rerank, o.prec, o.rcap);
         }
     };
     struct GraphEntry { cudaGraphExec_t exec; int64_t launches; };
@@ -267,7 +291,7 @@ Plan make_plan(const bbc_index* ix, int64_t nq, int nprobe, int64_t kc, int k, b
     p.nprobe = nprobe;
     p.kc = kc;
     p.k = k;
-    p.cap = ix->cap_prefix[nprobe];
+    p.cap = ix->cap_for(nprobe);
     auto shape = [&](int64_t c) {
         ChunkShape s;
         s.nq = c; s.sum_probe = c * nprobe; s.sum_cap = c * p.cap; s.sum_kc = c * kc; s.sum_k = c * k;
@@ -471,7 +495,7 @@ SignShape sign_uniform_shape(const bbc_index* ix, int64_t nc, int nprobe, int k,
     SignShape c;
     c.nq = nc;
     c.sum_probe = nc * nprobe;
-    c.sum_cap = nc * ix->cap_prefix[nprobe];
+    c.sum_cap = nc * ix->cap_for(nprobe);
     c.sum_k = nc * k;
     c.max_probe = nprobe;
     c.max_k = k;
@@ -591,7 +615,7 @@ int search_sign(bbc_index* ix, const float* queries, int64_t nq, int k, int npro
     int rc = get_workspace(ix, st, p.total, &ws);
     if (rc) return rc;
     const int d = ix->dev.d;
-    const int64_t cap = ix->cap_prefix[nprobe];
+    const int64_t cap = ix->cap_for(nprobe);
     const QueryParams qp = uniform_params(nprobe, cap, k, cap);
     for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
         const int64_t nc = std::min(chunk, nq - q0);
@@ -624,7 +648,7 @@ int search_sign_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_
         int64_t q1 = q0;
         while (q1 < nq) {
             SignShape t = c;
-            t.nq += 1; t.sum_probe += nprobe[q1]; t.sum_cap += ix->cap_prefix[nprobe[q1]]; t.sum_k += k[q1];
+            t.nq += 1; t.sum_probe += nprobe[q1]; t.sum_cap += ix->cap_for(nprobe[q1]); t.sum_k += k[q1];
             t.max_probe = std::max(t.max_probe, nprobe[q1]); t.max_k = std::max(t.max_k, k[q1]);
             SignPlan tp{};
             if (q1 > q0 && (sign_layout(ix, t, tp) > budget || t.nq > kMaxChunkQueries)) break;
@@ -646,7 +670,7 @@ int search_sign_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_
         int64_t maxcap = 0;
         for (int64_t i = 0; i < nc; ++i) {
             const int64_t qq = q0 + i;
-            const int64_t cap = ix->cap_prefix[nprobe[qq]];
+            const int64_t cap = ix->cap_for(nprobe[qq]);
             t_np[i] = nprobe[qq];
             t_k[i] = k[qq];
             t_kc[i] = cap;
@@ -1092,17 +1116,32 @@ int bbc_index_load(const char* path, int device, bbc_index** out) {
     memcpy(&d, hdr + 20, 4); memcpy(&n, hdr + 24, 8); memcpy(&nlist, hdr + 32, 4);
     memcpy(&pq_m, hdr + 36, 4); memcpy(&pq_bits, hdr + 40, 4);
     if (version != 1) return fail(BBC_ERR_FORMAT, "unsupported version %u", version);
-    if (quant != BBC_QUANT_PQ) return fail(BBC_ERR_UNSUPPORTED, "quantizer %u not supported by this loader", quant);
-    if (d == 0 || d > 65536 || nlist == 0 || nlist > (1u << 24) || n == 0 || n >= 0xFFFFFFFFull ||
-        pq_m == 0 || pq_m > d || (pq_bits != 4 && pq_bits != 8))
+    if (quant != BBC_QUANT_PQ && quant != BBC_QUANT_SIGN) return fail(BBC_ERR_FORMAT, "unknown quantizer %u", quant);
+    if (d == 0 || d > 65536 || nlist == 0 || nlist > (1u << 24) || n == 0 || n >= 0xFFFFFFFFull)
         return fail(BBC_ERR_FORMAT, "header fields out of range");
-    const size_t cb = (size_t)pq_m * pq_bits / 8;
+    if (quant == BBC_QUANT_PQ && (pq_m == 0 || pq_m > d || (pq_bits != 4 && pq_bits != 8)))
+        return fail(BBC_ERR_FORMAT, "PQ header fields out of range");
     auto rd = [&](void* dst, size_t bytes) -> bool {
         long pos = ftell(f);
         long pad = (64 - pos % 64) % 64;
         if (pad && fseek(f, pad, SEEK_CUR) != 0) return false;
         return fread(dst, 1, bytes, f) == bytes;
     };
+    if (quant == BBC_QUANT_SIGN) {
+        // centroids, list offsets, ids, rotation P [d][d], vectors
+        std::vector<float> cent((size_t)nlist * d);
+        std::vector<int64_t> offs(nlist + 1);
+        std::vector<int64_t> ids(n);
+        std::vector<float> rot((size_t)d * d);
+        std::vector<float> vecs(n * d);
+        if (!rd(cent.data(), cent.size() * 4) || !rd(offs.data(), offs.size() * 8) || !rd(ids.data(), ids.size() * 8) ||
+            !rd(rot.data(), rot.size() * 4) || !rd(vecs.data(), vecs.size() * 4))
+            return fail(BBC_ERR_FORMAT, "truncated index file");
+        bbc_sign_host h{(int64_t)n, (int32_t)d, (int32_t)nlist, (int32_t)metric, cent.data(), offs.data(), ids.data(),
+                        rot.data(), vecs.data()};
+        return bbc_index_create_sign(&h, device, out);
+    }
+    const size_t cb = (size_t)pq_m * pq_bits / 8;
     std::vector<float> cent((size_t)nlist * d);
     std::vector<int64_t> offs(nlist + 1);
     std::vector<int64_t> ids(n);
@@ -1167,6 +1206,9 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "profile") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "profile must be 0 or 1");
         ix->profile = (int)v;
+    } else if (k == "region_cap") {
+        if (!(v >= 0 && v <= 9.0e15) || v != std::floor(v)) return fail(BBC_ERR_ARG, "region_cap must be 0 (automatic) or a positive integer");
+        ix->region_cap = (int64_t)v;
     } else {
         return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     }
@@ -1187,6 +1229,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "graphs") *v = ix->graphs;
     else if (k == "precision") *v = ix->dev.prec;
     else if (k == "bound_scale") *v = ix->bound_scale;
+    else if (k == "region_cap") *v = (double)ix->region_cap;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -1215,7 +1258,8 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     if (!ix->graphs || st == nullptr) return run_all();
     // CUDA graph of the whole launch sequence for this call shape
     bbc_index::GraphKey key{queries, nq, k, nprobe, out_ids, out_dists, st, ix->kc_ratio, ix->buckets,
-                            ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8, ix->dev.prec};
+                            ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8, ix->dev.prec,
+                            ix->region_cap};
     std::lock_guard<std::mutex> lk(ix->graph_mu);
     auto it = ix->graph_cache.find(key);
     if (it == ix->graph_cache.end()) {
@@ -1280,7 +1324,7 @@ int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t
         while (q1 < nq) {
             ChunkShape t = sh;
             const int64_t kc = kc_for(ix, k[q1]);
-            t.nq += 1; t.sum_probe += nprobe[q1]; t.sum_cap += ix->cap_prefix[nprobe[q1]]; t.sum_kc += kc;
+            t.nq += 1; t.sum_probe += nprobe[q1]; t.sum_cap += ix->cap_for(nprobe[q1]); t.sum_kc += kc;
             t.sum_k += k[q1]; t.max_probe = std::max(t.max_probe, nprobe[q1]); t.max_kc = std::max(t.max_kc, kc);
             Plan tp{};
             if (q1 > q0 && (layout(ix, t, tp) > budget || t.nq > kMaxChunkQueries)) break;
@@ -1307,11 +1351,11 @@ int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t
             t_k[i] = k[q];
             t_kc[i] = kc_for(ix, k[q]);
             t_po[i + 1] = t_po[i] + nprobe[q];
-            t_ro[i + 1] = t_ro[i] + ix->cap_prefix[nprobe[q]];
+            t_ro[i + 1] = t_ro[i] + ix->cap_for(nprobe[q]);
             t_co[i + 1] = t_co[i] + t_kc[i];
             t_oo[i + 1] = t_oo[i] + k[q];
             maxk = std::max(maxk, k[q]);
-            maxcap = std::max(maxcap, ix->cap_prefix[nprobe[q]]);
+            maxcap = std::max(maxcap, ix->cap_for(nprobe[q]));
         }
         char* ws;
         int rc = get_workspace(ix, st, p.total, &ws);
@@ -1782,7 +1826,7 @@ int api_check_search_args(const bbc_index* ix, const void* queries, int64_t nq, 
 }
 const DevIndex& index_dev(const bbc_index* ix) { return ix->dev; }
 int index_device(const bbc_index* ix) { return ix->device; }
-int64_t index_cap(const bbc_index* ix, int nprobe) { return ix->cap_prefix[nprobe]; }
+int64_t index_cap(const bbc_index* ix, int nprobe) { return ix->cap_for(nprobe); }
 int index_buckets(const bbc_index* ix) { return ix->buckets; }
 int index_sample_lists(const bbc_index* ix) { return ix->sample_lists; }
 int64_t index_kc(const bbc_index* ix, int k) { return kc_for(ix, k); }

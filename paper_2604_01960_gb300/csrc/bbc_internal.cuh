@@ -118,6 +118,12 @@ inline QueryParams uniform_params(int nprobe, int64_t kc, int k, int64_t cap) {
     return p;
 }
 
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per (kernel, device, bytes): the attribute belongs to the
+// kernel on one device, so a process that searches on several devices sets
+// it on each.  Thread-safe.
+cudaError_t smem_attr_once(const void* kernel, int bytes);
+
 // ---- launchers (one per translation unit) ----
 
 // S1: approximate probe scores a[q][l] = ||c_l||^2 - 2<q,c_l> (L2) or -<q,c_l> (IP).

@@ -86,13 +86,8 @@ cudaError_t launch_lut16(const DevIndex& ix, const float* q, int64_t nq, uint16_
                          cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
     size_t smem = sizeof(float) * ((size_t)ix.M * ix.K + ix.d + 2 * ix.M);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(lut16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = smem_attr_once((const void*)lut16_kernel, 200 * 1024);
+    if (e != cudaSuccess) return e;
     lut16_kernel<<<(unsigned)nq, LUT_THREADS, smem, st>>>(ix, q, lut16);
     return cudaGetLastError();
 }

@@ -340,13 +340,8 @@ cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, 
     (void)max_nprobe;
     if (nq <= 0) return cudaSuccess;
     size_t smem = (size_t)SEL_MAXC * (8 + 4) + (size_t)ix.nlist * 4;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(probe_select_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = smem_attr_once((const void*)probe_select_kernel, 200 * 1024);
+    if (e != cudaSuccess) return e;
     probe_select_kernel<<<(unsigned)nq, SEL_THREADS, smem, st>>>(ix, q, qp, scores, lists, tc);
     return cudaGetLastError();
 }

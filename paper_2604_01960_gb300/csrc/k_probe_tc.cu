@@ -281,12 +281,7 @@ cudaError_t launch_probe_scores_tc(const DevIndex& ix, const float* q, int64_t n
     CUtensorMap ta, tb;
     if ((e = make_map(&ta, a, (uint64_t)ix.kp, (uint64_t)nq, TC_BM)) != cudaSuccess) return e;
     if ((e = make_map(&tb, ix.cent_b3, (uint64_t)ix.kp, (uint64_t)ix.nlist, TC_BN)) != cudaSuccess) return e;
-    static bool attr_set = false;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(probe_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    if ((e = smem_attr_once((const void*)probe_gemm_tc_kernel, TC_SMEM)) != cudaSuccess) return e;
     dim3 grid((unsigned)((ix.nlist + TC_BN - 1) / TC_BN), (unsigned)((nq + TC_BM - 1) / TC_BM));
     probe_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(ta, tb, ix.cnorm, nq, ix.nlist, ix.kp / TC_BK,
                                                             ix.metric, scores, ix.status);

@@ -631,26 +631,16 @@ cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cud
     if (nq <= 0) return cudaSuccess;
     if (a.kc > TK_MAX) {
         if (!a.keys) return cudaErrorInvalidValue;
-        static bool large_attr = false;
-        if (!large_attr) {
-            cudaError_t e = cudaFuncSetAttribute(topk_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 TK_HEAVY * 8);
-            if (e != cudaSuccess) return e;
-            large_attr = true;
-        }
+        cudaError_t e = smem_attr_once((const void*)topk_large_kernel, TK_HEAVY * 8);
+        if (e != cudaSuccess) return e;
         topk_large_kernel<<<(unsigned)nq, TK_THREADS, (size_t)TK_HEAVY * 8, st>>>(ix, a);
         return cudaGetLastError();
     }
     // keys held per query: all candidates, or at most k - 1 + TKS_BIG of them
     const long long kcap = std::min<long long>(std::min<long long>(a.kc, TK_MAX), (long long)a.k + TKS_BIG);
     const size_t smem = (size_t)std::max<long long>(kcap, 1) * 8;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             TK_MAX * 8);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = smem_attr_once((const void*)topk_kernel, TK_MAX * 8);
+    if (e != cudaSuccess) return e;
     topk_kernel<<<(unsigned)nq, TKS_THREADS, smem, st>>>(ix, a, (int)std::max<long long>(kcap, 1));
     return cudaGetLastError();
 }

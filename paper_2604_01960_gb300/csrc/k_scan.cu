@@ -874,22 +874,16 @@ static cudaError_t launch_split_t(const DevIndex& ix, int64_t nq, const ScanArgs
                                   cudaStream_t st) {
     using C = ScanCfg<M, BITS>;
     const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)a.nprobe * sizeof(int4);
-    static int lim = -1;
-    if (lim < 0) {
-        const int l0 = max_dyn_smem(scan_split_kernel<M, BITS, false>);
-        const int l1 = max_dyn_smem(scan_split_kernel<M, BITS, true>);
-        const int l = l0 < l1 ? l0 : l1;
-        cudaError_t e = cudaFuncSetAttribute(scan_split_kernel<M, BITS, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, l);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(scan_split_kernel<M, BITS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, l);
-        if (e != cudaSuccess) return e;
-        lim = l;
-    }
+    // a property of the compiled kernels (the same on every device); thread-safe initialisation
+    static const int lim = std::min(max_dyn_smem(scan_split_kernel<M, BITS, false>),
+                                    max_dyn_smem(scan_split_kernel<M, BITS, true>));
+    cudaError_t e = smem_attr_once((const void*)scan_split_kernel<M, BITS, false>, lim);
+    if (e == cudaSuccess) e = smem_attr_once((const void*)scan_split_kernel<M, BITS, true>, lim);
+    if (e != cudaSuccess) return e;
     if (smem > (size_t)lim) return cudaErrorInvalidValue;
     const long long items = nq * (long long)G;
     const unsigned grid = (unsigned)std::min<long long>(items, (long long)ix.num_sms * C::MIN_CTAS);
-    cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned int), st);
+    e = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     scan_split_kernel<M, BITS, false><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters}, nq);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -903,13 +897,9 @@ template <int M, int BITS>
 static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st) {
     using C = ScanCfg<M, BITS>;
     const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)a.nprobe * sizeof(int4);
-    static int lim = -1;
-    if (lim < 0) {
-        const int l = max_dyn_smem(scan_kernel<M, BITS>);
-        cudaError_t e = cudaFuncSetAttribute(scan_kernel<M, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, l);
-        if (e != cudaSuccess) return e;
-        lim = l;
-    }
+    static const int lim = max_dyn_smem(scan_kernel<M, BITS>);   // a property of the compiled kernel
+    cudaError_t e = smem_attr_once((const void*)scan_kernel<M, BITS>, lim);
+    if (e != cudaSuccess) return e;
     if (smem > (size_t)lim) return cudaErrorInvalidValue;
     scan_kernel<M, BITS><<<(unsigned)nq, C::THREADS, smem, st>>>(ix, a);
     return cudaGetLastError();

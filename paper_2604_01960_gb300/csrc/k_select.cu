@@ -219,13 +219,8 @@ __global__ void __launch_bounds__(SELK_THREADS) select_kernel(DevIndex ix, Selec
 cudaError_t launch_select(const DevIndex& ix, int64_t nq, const SelectArgs& a, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
     const size_t smem = (size_t)SELK_TCAP * 8;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = smem_attr_once((const void*)select_kernel, (int)smem);
+    if (e != cudaSuccess) return e;
     select_kernel<<<(unsigned)nq, SELK_THREADS, smem, st>>>(ix, a);
     return cudaGetLastError();
 }

@@ -638,13 +638,9 @@ cudaError_t launch_sign_scan(const DevIndex& ix, int64_t nq, const SignArgs& a, 
     const int nw = SG_THREADS / 32;
     size_t smem = (size_t)nw * 4 * (ix.d / 32) * 4 + 8;
     if (a.dbg_lb) smem += (size_t)(a.nprobe + 1) * 8;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(sign_scan_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(sign_scan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    e = smem_attr_once((const void*)sign_scan_kernel<true>, 64 * 1024);
+    if (e == cudaSuccess) e = smem_attr_once((const void*)sign_scan_kernel<false>, 64 * 1024);
+    if (e != cudaSuccess) return e;
     if (smem > 64 * 1024) return cudaErrorInvalidValue;
     if (a.dbg_lb) sign_scan_kernel<true><<<(unsigned)nq, SG_THREADS, smem, st>>>(ix, a, a.prep);
     else sign_scan_kernel<false><<<(unsigned)nq, SG_THREADS, smem, st>>>(ix, a, a.prep);

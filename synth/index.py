@@ -22,7 +22,9 @@ File format (little-endian, written by ``write_index``): a 64-byte header
 followed by the arrays, each starting on a 64-byte boundary, in this order:
 centroids f32[nlist*d], list_offsets i64[nlist+1], ids i64[n] (list order),
 codes u8[n*code_bytes] (list order), codebooks f32[pq_m*2^b*(d/pq_m)],
-vectors f32[n*d] (id order).
+vectors f32[n*d] (id order).  A sign-quantizer index (quantizer 1, pq_m and
+pq_bits 0, written by ``write_sign_index``) stores centroids, list_offsets,
+ids, the rotation f32[d*d] (row-major, r = P u) and vectors, in that order.
 """
 
 from __future__ import annotations
@@ -277,6 +279,17 @@ def write_index(path: str, idx: IvfPqIndex) -> None:
         for arr, dt in ((idx.centroids, np.float32), (idx.list_offsets, np.int64),
                         (idx.ids, np.int64), (idx.codes, np.uint8),
                         (idx.codebooks, np.float32), (idx.vectors, np.float32)):
+            _align(f)
+            f.write(np.ascontiguousarray(arr, dtype=dt).tobytes())
+
+
+def write_sign_index(path: str, idx: "IvfSignIndex") -> None:
+    """Write an IVF index with the 1-bit sign quantizer in the BBCIDX01 format."""
+    with open(path, "wb") as f:
+        hdr = struct.pack(HEADER_FMT, MAGIC, 1, 1, 0, idx.d, idx.n, idx.nlist, 0, 0)
+        f.write(hdr + b"\0" * (HEADER_BYTES - len(hdr)))
+        for arr, dt in ((idx.centroids, np.float32), (idx.list_offsets, np.int64),
+                        (idx.ids, np.int64), (idx.rotation, np.float32), (idx.vectors, np.float32)):
             _align(f)
             f.write(np.ascontiguousarray(arr, dtype=dt).tobytes())
 

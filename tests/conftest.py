@@ -75,3 +75,42 @@ def scanned_set(idx, lists):
     lofs = np.zeros(len(sel) + 1, dtype=np.int64)
     lofs[1:] = np.cumsum([len(s) for s in sel])
     return (np.concatenate(sel) if sel else np.zeros(0, np.int64)), lofs
+
+
+def check_topk(oracle_lib, idx, qv, gi, gd, oi, od, exact, rtol=1e-5):
+    """One query's GPU result (gi, gd) against the oracle's (oi, od).
+
+    exact: integer data, where the FP32 re-rank is exact, so ids and distances
+    match bit for bit.  Otherwise every reported distance is within rtol of
+    the FP64 distance of its id (relative to itself for squared L2, to
+    ||q|| ||v||_max for inner products), the two lists agree as order
+    statistics, and ids differ only among objects tied with the k-th distance
+    within that tolerance."""
+    k = len(oi)
+    valid = oi >= 0
+    assert np.array_equal(gi >= 0, valid)
+    assert np.all(np.isinf(gd[~valid]))
+    if exact:
+        assert np.array_equal(gi, oi)
+        assert np.array_equal(gd[valid].astype(np.float64), od[valid])
+        return
+    g = gi[valid]
+    d64 = oracle_lib.rerank(qv, idx.vectors, g, idx.metric)
+    if idx.metric == "ip":
+        # -<q, v> near 0 has no relative accuracy: measure against ||q|| ||v||
+        qn = float(np.linalg.norm(qv.astype(np.float64)))
+        vmax = float(np.linalg.norm(idx.vectors.astype(np.float64), axis=1).max())
+        floor = qn * vmax
+    else:
+        # a squared L2 distance is a sum of non-negative terms: its FP32 value is
+        # within a small multiple of 2^-24 of the FP64 one relative to itself, so
+        # the tolerance is purely relative (no absolute floor)
+        floor = 0.0
+    tol = rtol * np.maximum(np.abs(d64), floor)
+    assert np.all(np.abs(gd[valid] - d64) <= tol)                      # FP32 vs FP64 per result
+    assert np.all(np.abs(d64 - od[valid]) <= 2 * tol + rtol * np.abs(od[valid]))   # same order statistics
+    diff = set(g.tolist()) ^ set(oi[valid].tolist())
+    if diff:                                                           # only ties at the boundary
+        dk = od[valid][-1]
+        dd = oracle_lib.rerank(qv, idx.vectors, np.array(sorted(diff)), idx.metric)
+        assert np.all(np.abs(dd - dk) <= 2 * rtol * max(abs(dk), floor))

@@ -11,12 +11,11 @@ for bit end to end.
 import numpy as np
 import pytest
 
-from conftest import scanned_set, small_workload
+from conftest import check_topk as _check_topk, scanned_set, small_workload
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-RTOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -178,35 +177,6 @@ def test_collect_candidates_and_state(bbc, oracle_lib, kind, nprobe, kc, m, smin
         assert s["pushed"] >= min(kc, len(e))
 
 
-def _check_topk(oracle_lib, idx, qv, gi, gd, oi, od, exact):
-    k = len(oi)
-    valid = oi >= 0
-    assert np.array_equal(gi >= 0, valid)
-    assert np.all(np.isinf(gd[~valid]))
-    if exact:
-        assert np.array_equal(gi, oi)
-        assert np.array_equal(gd[valid].astype(np.float64), od[valid])
-        return
-    g = gi[valid]
-    d64 = oracle_lib.rerank(qv, idx.vectors, g, idx.metric)
-    scale = max(np.abs(od[valid]).max(), 1e-30)
-    if idx.metric == "ip":
-        # -<q, v> near 0 has no relative accuracy: measure against ||q|| ||v||
-        qn = float(np.linalg.norm(qv.astype(np.float64)))
-        vmax = float(np.linalg.norm(idx.vectors.astype(np.float64), axis=1).max())
-        floor = qn * vmax
-    else:
-        floor = 1e-3 * scale
-    tol = RTOL * np.maximum(np.abs(d64), floor)
-    assert np.all(np.abs(gd[valid] - d64) <= tol)                      # FP32 vs FP64 per result
-    assert np.all(np.abs(d64 - od[valid]) <= 2 * tol + RTOL * np.abs(od[valid]))   # same order statistics
-    diff = set(g.tolist()) ^ set(oi[valid].tolist())
-    if diff:                                                           # only ties at the boundary
-        dk = od[valid][-1]
-        dd = oracle_lib.rerank(qv, idx.vectors, np.array(sorted(diff)), idx.metric)
-        assert np.all(np.abs(dd - dk) <= 2 * RTOL * max(abs(dk), floor))
-
-
 @pytest.mark.parametrize("split", [1, 0])
 @pytest.mark.parametrize("kind,k,nprobe,ratio", [("tiny", 100, 12, 2.0), ("sift", 500, 16, 1.5),
                                                  ("sift4", 300, 24, 2.0), ("embed", 200, 10, 1.5),
@@ -318,12 +288,15 @@ def test_argument_errors(bbc):
     bbc.bbc_search(h, qd, 0, 5, 4, ids, dd)      # nq = 0 is a no-op
 
 
-@pytest.mark.parametrize("kind", ["sift", "tiny"])
-def test_search_ex_mixed_batch_equals_alone(bbc, kind):
+@pytest.mark.parametrize("kind", ["sift", "tiny", "sift4", "embed"])
+def test_search_ex_mixed_batch_equals_alone(bbc, oracle_lib, kind):
     """A mixed batch (different k and nprobe per query) returns, for every
-    query, exactly what searching that query alone returns."""
+    query, the oracle's result at that query's own k, nprobe and K_c
+    (Algorithm 1's candidate set re-ranked), and exactly what searching that
+    query alone returns."""
     h, idx, q = dev_index(bbc, kind)
-    bbc.bbc_set_param(h, "kc_ratio", 1.5)
+    ratio = 1.5
+    bbc.bbc_set_param(h, "kc_ratio", ratio)
     rng = np.random.default_rng(11)
     nq = len(q)
     ks = rng.integers(1, 1500, size=nq).astype(np.int32)
@@ -336,8 +309,12 @@ def test_search_ex_mixed_batch_equals_alone(bbc, kind):
     sync_ok(bbc, h)
     gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
     off = np.concatenate([[0], np.cumsum(ks)])
+    exact = kind in ("sift", "sift4")
     for i in range(nq):
         k = int(ks[i])
+        kc = max(k, int(np.ceil(ratio * k - 1e-9)))
+        oi, od = oracle_lib.search(idx, q[i:i + 1], k, int(ps[i]), kc, "sort")
+        _check_topk(oracle_lib, idx, q[i], gi[off[i]:off[i + 1]], gd[off[i]:off[i + 1]], oi[0], od[0], exact)
         ai = torch.empty((1, k), dtype=torch.int64, device="cuda")
         ad = torch.empty((1, k), dtype=torch.float32, device="cuda")
         bbc.bbc_search(h, qd[i:i + 1], 1, k, int(ps[i]), ai, ad)

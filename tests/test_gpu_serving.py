@@ -1,13 +1,14 @@
 """Serving: continuous batching of single-query requests (different k and
 nprobe per request) with admission by candidate-buffer bytes.  Every result
-must equal searching that query alone, whatever batch it ran in."""
+must equal the oracle's result for that request (its own k, nprobe and K_c)
+and searching that query alone, whatever batch it ran in."""
 
 import threading
 
 import numpy as np
 import pytest
 
-from conftest import small_workload
+from conftest import check_topk, small_workload
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -32,7 +33,7 @@ def _alone(bbc, h, qv, k, nprobe):
 
 @pytest.mark.parametrize("kind,budget_mb,streams,max_batch", [("sift", 1, 3, 5), ("tiny", 64, 4, 64),
                                                                ("medium", 4, 2, 8)])
-def test_serving_results_equal_alone(bbc, kind, budget_mb, streams, max_batch):
+def test_serving_results_equal_alone(bbc, oracle_lib, kind, budget_mb, streams, max_batch):
     idx, q = small_workload(kind)
     h = bbc.bbc_index_create(idx, 0)
     try:
@@ -63,7 +64,12 @@ def test_serving_results_equal_alone(bbc, kind, budget_mb, streams, max_batch):
         cap = np.sort(np.diff(idx.list_offsets))[::-1].cumsum()
         largest = max(8 * int(cap[p - 1]) + 8 * int(np.ceil(1.5 * k)) for k, p in zip(ks, ps))
         assert st["inflight_bytes_peak"] <= max(budget, largest)
+        exact = kind in ("sift", "medium")
         for i in range(n):
+            k = int(ks[i])
+            kc = max(k, int(np.ceil(1.5 * k - 1e-9)))
+            oi, od = oracle_lib.search(idx, qs[i:i + 1], k, int(ps[i]), kc, "sort")
+            check_topk(oracle_lib, idx, qs[i], got[i][0], got[i][1], oi[0], od[0], exact)
             ai, ad = _alone(bbc, h, qs[i], int(ks[i]), int(ps[i]))
             assert np.array_equal(got[i][0], ai), i
             assert np.array_equal(got[i][1], ad), i
