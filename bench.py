@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--nprobe", default=None, help="lists probed; a comma list prints one line per value")
     p.add_argument("--kc-ratio", default="1.4", help="K_c / k; a comma list prints one line per value")
     p.add_argument("--buckets", default="64", help="bucket count m; a comma list prints one line per value")
+    p.add_argument("--pair", default="0",
+                   help="scan schedule: 1 two queries per CTA (pair form), 0 one; a comma list prints one line per value")
     p.add_argument("--cpu-queries", type=int, default=200, help="oracle sample for cpu_baseline")
     p.add_argument("--ref-queries", type=int, default=24, help="oracle queries per reference step")
     p.add_argument("--e2e-steps", type=int, default=10)
@@ -367,15 +369,18 @@ def main():
     ratios = [float(v) for v in str(args.kc_ratio).split(",")]
     scales = [float(v) for v in str(args.bound_scale).split(",")] if index.info["quantizer"] == 1 else [None]
     buckets = [int(v) for v in str(args.buckets).split(",")]
+    pairs = [int(v) for v in str(args.pair).split(",")]
     for prec in precs:
         for npb in nprobes:
             for ratio in ratios:
                 for m in buckets:
                     for scale in scales:
-                        index.set(kc_ratio=ratio, buckets=m)
-                        if scale is not None:
-                            index.set(bound_scale=scale)
-                        measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec, ratio, m)
+                        for pair in pairs:
+                            index.set(kc_ratio=ratio, buckets=m, pair=pair)
+                            if scale is not None:
+                                index.set(bound_scale=scale)
+                            measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec, ratio,
+                                    m)
     index.close()
 
 
@@ -564,6 +569,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
                        "pq": "sign 1-bit" if is_sign else f"{idx.pq_m}x{idx.pq_bits}", "nq": nq, "k": k,
                        "nprobe": nprobe, "kc": None if is_sign else kc,
                        "kc_ratio": ratio, "buckets": m, "rerank": rerank,
+                       "scan_schedule": "pair" if index.get("pair") else "one query per CTA",
                        "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
                        "recall_tie_aware": True, "ground_truth_cpu_spotcheck": gt_check,
                        "l2_flush_between_steps": True, "parallelism": f"replicas x{ws}",

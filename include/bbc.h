@@ -149,6 +149,14 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  items, collector state in global memory), 0 = automatic (split
  *                  when the batch is too small to fill the GPU).  Same results
  *                  either way.  Default 0.
+ *   "pair"         1 = the scan runs two queries per CTA where the table shape
+ *                  allows it (8-bit codes with pq_m <= 32, 4-bit with pq_m <= 64):
+ *                  queries are paired by nearest list and vector distance, the
+ *                  two uint16 tables share one shared-memory table (one in the
+ *                  low, one in the high half of each word) and the union of
+ *                  their probed lists is streamed once, so a code row serves
+ *                  both queries.  0 = one query per CTA.  Applies when "split"
+ *                  gives one CTA per query.  Same results either way.  Default 0.
  *   "graphs"       1 = bbc_search captures the launch sequence of each call shape
  *                  (pointers, sizes, parameters, stream) into a CUDA graph the
  *                  first time and replays it afterwards (not on the legacy
@@ -215,9 +223,10 @@ int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t
 int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32_t nprobe,
                     int64_t* out_ids, float* out_dists, void* stream);
 
-/* Autotuner for the batched form: times candidate values of "split" (CTAs
- * per query in the scan) and then "buckets" (m, the result buffer's bucket
- * count) for this call shape on `nq` device queries, and keeps the fastest
+/* Autotuner for the batched form: times the scan schedules ("split", CTAs
+ * per query, and "pair", two queries per CTA) and then "buckets" (m, the
+ * result buffer's bucket count) for this call shape on `nq` device queries,
+ * and keeps the fastest
  * on the index.  With cache_path (may be NULL) the choice is looked up in,
  * or appended to, a JSON-lines file keyed by the index shape and the call
  * shape, so later processes skip the timing.  Allocates its own output

@@ -127,17 +127,19 @@ struct bbc_index {
     unsigned long long* sign_totals = nullptr;   // [4] device counters of the bounded re-rank
     float bound_scale = 1.f;                     // sign codes: factor on the residual term
     int split = 0;            // 0 automatic, 1 one CTA per query, G >= 2 CTAs per query
+    int pair = 0;             // 1: two queries per CTA (pair form) where supported, 0: one
     int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
     bool capturing = false;
     struct GraphKey {
         const void* q; int64_t nq; int k; int nprobe; void* oi; void* od; cudaStream_t st;
         double kc_ratio; int buckets, sample_lists, split, probe_gemm, rerank, prec;
         int64_t rcap;
+        int pair;
         bool operator<(const GraphKey& o) const {
             return std::tie(q, nq, k, nprobe, oi, od, st, kc_ratio, buckets, sample_lists, split, probe_gemm, rerank,
-                            prec, rcap) <
+                            prec, rcap, pair) <
                    std::tie(o.q, o.nq, o.k, o.nprobe, o.oi, o.od, o.st, o.kc_ratio, o.buckets, o.sample_lists, o.split,
-                            o.probe_gemm, o.rerank, o.prec, o.rcap);
+                            o.probe_gemm, o.rerank, o.prec, o.rcap, o.pair);
         }
     };
     struct GraphEntry { cudaGraphExec_t exec; int64_t launches; };
@@ -208,7 +210,7 @@ struct Plan {
     int k;
     int64_t cap;
     size_t off_scores, off_probe, off_lut, off_state, off_region, off_cand, off_count, off_cdist,
-        off_q, off_ids, off_dists, off_abf, off_keys, off_params, off_counters, off_prec, total;
+        off_q, off_ids, off_dists, off_abf, off_keys, off_params, off_counters, off_prec, off_pair, total;
 };
 
 // The precision re-rank runs when a low-precision copy exists and the exact u8
@@ -282,6 +284,7 @@ size_t layout(const bbc_index* ix, const ChunkShape& c, Plan& p) {
     p.off_params = o; o = align_up(o + (c.mixed ? (size_t)(c.nq + 1) * 8 * 7 : 0));
     p.off_counters = o; o = align_up(o + 16);
     p.off_prec = o; o = align_up(o + (prec_active(ix) ? prec_bytes(c.nq, c.sum_kc) : 0));
+    p.off_pair = o; o = align_up(o + (ix->pair ? pair_plan_bytes(c.nq) : 0));
     p.total = o;
     return o;
 }
@@ -430,6 +433,13 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
         unsigned int* counters = reinterpret_cast<unsigned int*>(ws + p.off_counters);
         CUDA_TRY(cudaMemsetAsync(state, 0, (size_t)nc * sizeof(bbc_collector_state), st));
         CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan_split(d, nc, sa, G, counters, st); }));
+    } else if (ix->pair && nc >= 2 && scan_pair_supported(d, p.nprobe)) {
+        // two queries per CTA: the pairing plan, then the pair form of the scan
+        int32_t* perm = reinterpret_cast<int32_t*>(ws + p.off_pair) + 3 * nc;
+        CUDA_TRY(stage(ix, 3, st, [&] {
+            return launch_pair_plan(q, d.d, nc, qp, sa.lists, ws + p.off_pair, perm, st);
+        }));
+        CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan_pair(d, nc, sa, perm, st); }));
     } else {
         CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan(d, nc, sa, st); }));
     }
@@ -1206,6 +1216,9 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "profile") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "profile must be 0 or 1");
         ix->profile = (int)v;
+    } else if (k == "pair") {
+        if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "pair must be 0 (one query per CTA) or 1 (two)");
+        ix->pair = (int)v;
     } else if (k == "region_cap") {
         if (!(v >= 0 && v <= 9.0e15) || v != std::floor(v)) return fail(BBC_ERR_ARG, "region_cap must be 0 (automatic) or a positive integer");
         ix->region_cap = (int64_t)v;
@@ -1230,6 +1243,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "precision") *v = ix->dev.prec;
     else if (k == "bound_scale") *v = ix->bound_scale;
     else if (k == "region_cap") *v = (double)ix->region_cap;
+    else if (k == "pair") *v = ix->pair;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -1259,7 +1273,7 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     // CUDA graph of the whole launch sequence for this call shape
     bbc_index::GraphKey key{queries, nq, k, nprobe, out_ids, out_dists, st, ix->kc_ratio, ix->buckets,
                             ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8, ix->dev.prec,
-                            ix->region_cap};
+                            ix->region_cap, ix->pair};
     std::lock_guard<std::mutex> lk(ix->graph_mu);
     auto it = ix->graph_cache.find(key);
     if (it == ix->graph_cache.end()) {
@@ -1495,21 +1509,28 @@ int bbc_autotune(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
             char line[1024];
-            int found_split = -1, found_m = -1;
+            int found_split = -1, found_m = -1, found_pair = 0;
             while (fgets(line, sizeof(line), f)) {
                 char want[600];
                 snprintf(want, sizeof(want), "\"key\": \"%s\"", key);
                 if (!strstr(line, want)) continue;
                 static const char ks[] = "\"split\": ";
                 static const char kb[] = "\"buckets\": ";
+                static const char kp[] = "\"pair\": ";
                 const char* a = strstr(line, ks);
                 const char* b = strstr(line, kb);
-                if (a && b) { found_split = atoi(a + strlen(ks)); found_m = atoi(b + strlen(kb)); }
+                const char* c = strstr(line, kp);
+                if (a && b) {
+                    found_split = atoi(a + strlen(ks));
+                    found_m = atoi(b + strlen(kb));
+                    found_pair = c ? (atoi(c + strlen(kp)) ? 1 : 0) : 0;
+                }
             }
             fclose(f);
             if (found_split >= 0 && found_m >= 2 && found_m <= 256) {
                 ix->split = found_split;
                 ix->buckets = found_m;
+                ix->pair = found_pair;
                 return BBC_OK;
             }
         }
@@ -1526,7 +1547,7 @@ int bbc_autotune(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int saved_split = ix->split, saved_m = ix->buckets, saved_graphs = ix->graphs;
+    const int saved_split = ix->split, saved_m = ix->buckets, saved_graphs = ix->graphs, saved_pair = ix->pair;
     ix->graphs = 0;
     auto time_it = [&](double* ms) -> int {
         int r = bbc_search(ix, queries, nq, k, nprobe, oi, od, stream);       // warm-up (allocations)
@@ -1545,20 +1566,25 @@ int bbc_autotune(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int
         *ms = best;
         return BBC_OK;
     };
-    std::vector<int> splits = {1};
+    // schedules: (split, pair) = one CTA per query, two queries per CTA (pair
+    // form, where supported), G CTAs per query for batches too small to fill the GPU
+    std::vector<std::pair<int, int>> scheds = {{1, 0}};
+    if (nq >= 2 && scan_pair_supported(ix->dev, nprobe)) scheds.push_back({1, 1});
     const int64_t slots = 2ll * ix->dev.num_sms;
     for (int G : {2, 4, 8, 16, 32, 64, 128})
-        if (G <= nprobe && nq * G <= 64 * slots && nq < 8 * slots) splits.push_back(G);
+        if (G <= nprobe && nq * G <= 64 * slots && nq < 8 * slots) scheds.push_back({G, 0});
     double best_ms = 1e300;
-    int best_split = 1, best_m = ix->buckets;
-    for (int G : splits) {
-        ix->split = G;
+    int best_split = 1, best_m = ix->buckets, best_pair = 0;
+    for (const auto& sc : scheds) {
+        ix->split = sc.first;
+        ix->pair = sc.second;
         double t;
         if ((rc = time_it(&t))) break;
-        if (t < best_ms) { best_ms = t; best_split = G; }
+        if (t < best_ms) { best_ms = t; best_split = sc.first; best_pair = sc.second; }
     }
     if (!rc) {
         ix->split = best_split;
+        ix->pair = best_pair;
         for (int m : {32, 64, 128, 256}) {
             ix->buckets = m;
             double t;
@@ -1574,15 +1600,17 @@ int bbc_autotune(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int
     if (rc) {
         ix->split = saved_split;
         ix->buckets = saved_m;
+        ix->pair = saved_pair;
         return rc;
     }
     ix->split = best_split;
     ix->buckets = best_m;
+    ix->pair = best_pair;
     if (out_ms) *out_ms = best_ms;
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "a")) {
-            fprintf(f, "{\"key\": \"%s\", \"split\": %d, \"buckets\": %d, \"ms\": %.4f}\n", key, best_split, best_m,
-                    best_ms);
+            fprintf(f, "{\"key\": \"%s\", \"split\": %d, \"pair\": %d, \"buckets\": %d, \"ms\": %.4f}\n", key,
+                    best_split, best_pair, best_m, best_ms);
             fclose(f);
         }
     }

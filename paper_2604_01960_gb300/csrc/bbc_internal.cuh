@@ -161,6 +161,20 @@ cudaError_t launch_scan(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaS
 cudaError_t launch_scan_split(const DevIndex& ix, int64_t nq, const ScanArgs& a, int G, unsigned int* counters,
                               cudaStream_t st);
 
+// Pair form of the scan (batched, two queries per CTA sharing one packed
+// table and the union of their lists); perm from launch_pair_plan.  Same
+// results as launch_scan.  Supported for 8-bit tables with M <= 32 and 4-bit
+// tables with M <= 64 when its shared memory allows two CTAs per SM.
+bool scan_pair_supported(const DevIndex& ix, int nprobe);
+cudaError_t launch_scan_pair(const DevIndex& ix, int64_t nq, const ScanArgs& a, const int32_t* perm,
+                             cudaStream_t st);
+// Pairing plan (k_pair.cu): perm[nq] (query of CTA i at 2i and 2i + 1), from
+// the probe lists and the query vectors; scratch holds pair_plan_bytes(nq)
+// bytes, perm included (the last quarter).
+size_t pair_plan_bytes(int64_t nq);
+cudaError_t launch_pair_plan(const float* q, int d, int64_t nq, const QueryParams& qp, const int32_t* lists,
+                             void* scratch, int32_t* perm, cudaStream_t st);
+
 struct SelectArgs {
     const uint2* region;
     int64_t cap;

@@ -66,6 +66,8 @@ struct ScanCfg {
     static constexpr int THREADS = MIN_CTAS == 2 ? 512 : 1024;
     // 32-vector blocks per warp iteration (their code loads in flight together)
     static constexpr int CHUNK = NCH <= 2 ? 3 : (NCH <= 6 && THREADS == 512 ? 2 : 1);
+    // the same for the pair form, which keeps two estimates per vector
+    static constexpr int PCHUNK = NCH <= 2 ? 2 : 1;
     // estimates are below M * 65535 < 2^EB; the sample's coarse histogram
     // counts e >> SHC (2^11 bins), the fine one e mod 2^SHC
     static constexpr int EB = M <= 8 ? 19 : (M <= 16 ? 20 : (M <= 32 ? 21 : (M <= 64 ? 22 : 23)));
@@ -131,6 +133,41 @@ struct AdcUnroll<M, BITS, M> {
 template <int M, int BITS>
 __device__ __forceinline__ uint32_t adc_lane(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane4, uint32_t base) {
     return AdcUnroll<M, BITS, 0>::run(r, lane4, base);
+}
+
+// Packed table of the pair form: word (code j, column c) holds query a's
+// entry LUT_a[c mod M][j] in its low and query b's LUT_b[c mod M][j] in its
+// high 16 bits.  With A = the sum of a lane's words (mod 2^32) and B = the
+// sum of their high halves, e_b = B and e_a = A - 2^16 B exactly: both true
+// sums are below M * 65535 < 2^32.  B takes one two-way dot product per
+// word (dp2a.lo with weights (0, 1): B + the word's high half); the scan is
+// issue-bound, and this saves the separate shift per lookup.
+template <int M, int BITS, int S>
+struct AdcPairUnroll {
+    static __device__ __forceinline__ void run(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane4,
+                                               uint32_t base, uint32_t& A, uint32_t& B) {
+        const uint32_t v0 = lds<4 * S>(slot_addr<M, BITS, S>(r, lane4, base));
+        const uint32_t v1 = lds<4 * (S + 1)>(slot_addr<M, BITS, S + 1>(r, lane4, base));
+        A += v0 + v1;
+        B = __dp2a_lo(v0, 0x100u, B);
+        B = __dp2a_lo(v1, 0x100u, B);
+        AdcPairUnroll<M, BITS, S + 2>::run(r, lane4, base, A, B);
+    }
+};
+template <int M, int BITS>
+struct AdcPairUnroll<M, BITS, M> {
+    static __device__ __forceinline__ void run(const uint4 (&)[ScanCfg<M, BITS>::NCH], uint32_t, uint32_t,
+                                               uint32_t&, uint32_t&) {}
+};
+
+// Estimated distances of this lane's vector for both queries of a packed table.
+template <int M, int BITS>
+__device__ __forceinline__ void adc_pair(const uint4 (&r)[ScanCfg<M, BITS>::NCH], uint32_t lane4, uint32_t base,
+                                         uint32_t& ea, uint32_t& eb) {
+    uint32_t A = 0u, B = 0u;
+    AdcPairUnroll<M, BITS, 0>::run(r, lane4, base, A, B);
+    eb = B;
+    ea = A - (B << 16);
 }
 
 // Update on the shared bucket counts by one warp: first bucket whose running
@@ -354,7 +391,9 @@ __device__ __forceinline__ void stage_lut(const uint16_t* lq, uint32_t* lut) {
 // through the lists in probe order.  A warp keeps the descriptor of its
 // current list in registers and walks forward (its chunks ascend); the
 // appends of a chunk take one cursor atomic.
-template <int M, int BITS, bool MAIN, bool GLOBAL>
+// HALF = -1: the table holds one query; HALF = 0 / 1: a packed pair table,
+// of which this pass scores query a (low halves) or query b (high halves).
+template <int M, int BITS, bool MAIN, bool GLOBAL, int HALF = -1>
 __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& a, const QCtx& Q,
                                             bbc_collector_state* st, int nl, int g0, int g1,
                                             const uint32_t* lut, const int4* ldesc, ScanShared& S,
@@ -421,7 +460,13 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
             e[u] = 0;
             bal[u] = 0;
             if (u < nb) {
-                e[u] = adc_lane<M, BITS>(r[u], lane4, lut_s);
+                if (HALF < 0) {
+                    e[u] = adc_lane<M, BITS>(r[u], lane4, lut_s);
+                } else {
+                    uint32_t ea, eb;
+                    adc_pair<M, BITS>(r[u], lane4, lut_s, ea, eb);
+                    e[u] = HALF ? eb : ea;
+                }
                 const bool valid = (vbits >> u) & 1u;
                 const bool push = MAIN ? (valid && e[u] <= etau) : valid;    // bucket(e) <= tau
                 bal[u] = __ballot_sync(0xFFFFFFFFu, push);
@@ -860,6 +905,338 @@ __global__ void __launch_bounds__(SCAN_THREADS) codebook_kernel(ScanArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pair form of the batched scan: one CTA owns two queries whose probe sets
+// overlap (paired by the plan in k_pair.cu).  Their uint16 tables share one
+// shared-memory table (query a in the low, query b in the high half of each
+// word), so a code row is loaded once for both and one shared load serves
+// both queries' lookups of a vector.  Each query keeps its own sample,
+// codebook, bin counts, threshold and region; the main pass streams the
+// union of the two queries' remaining lists, each list tagged with the
+// queries that scan it there.  Candidate sets, thresholds and the counts of
+// buckets up to the threshold are those of the one-CTA-per-query form.
+// ---------------------------------------------------------------------------
+
+// Phase A's table staging for a pair (lb null: no second query, high halves 0).
+template <int M, int BITS>
+__device__ __forceinline__ void stage_lut_pair(const uint16_t* la, const uint16_t* lb, uint32_t* lut) {
+    using C = ScanCfg<M, BITS>;
+    constexpr int K8 = C::K / 8;
+    for (int t = threadIdx.x; t < M * K8; t += blockDim.x) {
+        const int j8 = t / M, c = t - j8 * M;
+        const uint4 va = __ldg(reinterpret_cast<const uint4*>(la + c * C::K + j8 * 8));
+        const uint4 vb = lb ? __ldg(reinterpret_cast<const uint4*>(lb + c * C::K + j8 * 8)) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t wa = word_of(va, i >> 1), wb = word_of(vb, i >> 1);
+            const uint32_t val = (i & 1) ? ((wa >> 16) | (wb & 0xFFFF0000u)) : ((wa & 0xFFFFu) | (wb << 16));
+            uint32_t* row = lut + (j8 * 8 + i) * C::W;
+#pragma unroll
+            for (int cc = c; cc < C::W; cc += M) row[cc] = val;
+        }
+    }
+}
+
+// Warp 0: the union of the two queries' main lists (probe ranks at or after
+// their sampled lists) laid out as consecutive 32-vector blocks, with the
+// descriptors of build_layout and lfl[j] = bit 0: query a scans list j here,
+// bit 1: query b does.  Ranks go in steps of 16 (lanes 0-15 query a, 16-31
+// query b), so the union keeps both probe orders, nearest first.  A list of
+// query b that is also one of a's main lists is laid out once, from a's side
+// (bm: the main-list bitmaps of a and b, nlw words each).  Returns the
+// number of blocks; *nlists = the number of lists.
+__device__ int build_union_layout(const DevIndex& ix, const QCtx (&Q)[2], const int (&nsl)[2], bool hb,
+                                  const uint32_t* bm, int nlw, int4* ldesc, uint8_t* lfl, int* nlists) {
+    const unsigned ln = lane_id();
+    const int h = (int)(ln >> 4), r0 = (int)(ln & 15u);
+    const unsigned lt_mask = (1u << ln) - 1u;
+    const int pmax = max(Q[0].P, hb ? Q[1].P : 0);
+    // this lane's query, selected without indexing Q by a run-time value
+    const int Ph = h ? Q[1].P : Q[0].P;
+    const int32_t* lh = h ? Q[1].lists : Q[0].lists;
+    const int nslh = h ? nsl[1] : nsl[0];
+    int carry = 0, cnt = 0;
+    for (int base = 0; base < pmax; base += 16) {
+        const int r = base + r0;
+        bool take = false;
+        int nb = 0, nv = 0, blk = 0;
+        uint32_t fl = 0;
+        if ((h == 0 || hb) && r >= nslh && r < Ph) {
+            const int l = lh[r];
+            const bool in0 = (bm[l >> 5] >> (l & 31)) & 1u;
+            const bool in1 = (bm[nlw + (l >> 5)] >> (l & 31)) & 1u;
+            take = h == 0 || !in0;
+            fl = h == 0 ? (1u | (in1 ? 2u : 0u)) : 2u;
+            if (take) {
+                nv = ix.list_len[l];
+                nb = (nv + 31) >> 5;
+                blk = ix.list_blk[l];
+            }
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
+        const uint32_t inc = warp_incl_scan((uint32_t)nb);
+        if (take) {
+            const int pos = cnt + __popc(bal & lt_mask);
+            const int lo = carry + (int)inc - nb;
+            ldesc[pos] = make_int4(lo, lo + nb, blk - lo, 32 * lo + nv);
+            lfl[pos] = (uint8_t)fl;
+        }
+        cnt += __popc(bal);
+        carry += (int)__shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+    *nlists = cnt;
+    return carry;
+}
+
+// Appends the pushed objects of one query for a chunk (see scan_blocks).
+template <int CH>
+__device__ __forceinline__ void pair_append(const DevIndex& ix, ScanShared& S, uint2* region, uint32_t cap,
+                                            const uint32_t (&e)[CH], const unsigned (&bal)[CH], const int (&gbk)[CH],
+                                            uint32_t tot, uint32_t dmin, int sh) {
+    const unsigned ln = lane_id();
+    const unsigned lt_mask = (1u << ln) - 1u;
+    uint32_t base = 0;
+    if (ln == 0) base = atomicAdd(&S.count, tot);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+        if ((bal[u] >> ln) & 1u) {
+            const uint32_t pos = base + (uint32_t)__popc(bal[u] & lt_mask);
+            if (pos < cap) region[pos] = make_uint2(e[u], (uint32_t)gbk[u] * 32u + ln);
+            else atomicOr(ix.status, kStatusRegionOverrun);
+            atomicAdd(&S.bh[bin_of(e[u], dmin, sh)], 1u);
+        }
+        base += (uint32_t)__popc(bal[u]);
+    }
+}
+
+// Main pass of the pair form over blocks [0, g1) of the union layout.
+template <int M, int BITS>
+__device__ __forceinline__ void scan_pair_main(const DevIndex& ix, const ScanArgs& a, const QCtx (&Q)[2], bool hb,
+                                               int nl, int g1, const uint32_t* lut, const int4* ldesc,
+                                               const uint8_t* lfl, ScanShared (&S)[2]) {
+    using C = ScanCfg<M, BITS>;
+    constexpr int CH = C::PCHUNK;
+    const unsigned ln = lane_id();
+    const int nw = blockDim.x >> 5;
+    const uint32_t lut_s = (uint32_t)__cvta_generic_to_shared(lut);
+    const uint32_t lane4 = 4u * ln;
+    const uint32_t cap0 = (uint32_t)(Q[0].cap < 0xFFFFFFFFll ? Q[0].cap : 0xFFFFFFFFll);
+    const uint32_t cap1 = (uint32_t)(Q[1].cap < 0xFFFFFFFFll ? Q[1].cap : 0xFFFFFFFFll);
+    const uint4* codes = reinterpret_cast<const uint4*>(ix.codes) + ln;
+    const uint32_t dmin0 = S[0].dmin, dmin1 = S[1].dmin;
+    const int sh0 = S[0].sh, sh1 = S[1].sh;
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(ldesc);
+    int j = -1, jhi = 0, jb = 0, jend = 0;
+    uint32_t jfl = 0;
+    auto seek = [&](int g) {
+        int4 d;
+        if (j < 0) {
+            int lo = 0, hi = nl - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ld_desc(d0, mid).x <= g) lo = mid; else hi = mid - 1;
+            }
+            j = lo;
+            d = ld_desc(d0, j);
+        } else {
+            do { d = ld_desc(d0, ++j); } while (g >= d.y);
+        }
+        jhi = d.y;
+        jb = d.z;
+        jend = d.w;
+        jfl = lfl[j];
+    };
+    int it = 0;
+    for (int cb = (int)warp_id() * CH; cb < g1; cb += nw * CH, ++it) {
+        const int nb = min(CH, g1 - cb);
+        int gbk[CH];
+        uint32_t v0 = 0, v1 = 0;                        // bit u: block u's lane holds a vector query a / b scans
+        uint4 r[CH][C::NCH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            gbk[u] = 0;
+            if (u < nb) {
+                const int g = cb + u;
+                if (g >= jhi) seek(g);
+                gbk[u] = jb + g;
+                const uint32_t has = (uint32_t)((int)ln < jend - 32 * g);
+                v0 |= (has & jfl) << u;
+                v1 |= (has & (jfl >> 1)) << u;
+                const uint4* cp = codes + (size_t)gbk[u] * (32 * C::NCH);
+#pragma unroll
+                for (int c = 0; c < C::NCH; ++c) r[u][c] = __ldg(cp + c * 32);
+            }
+        }
+        const uint32_t et0 = *(volatile uint32_t*)&S[0].etau;
+        const uint32_t et1 = *(volatile uint32_t*)&S[1].etau;
+        uint32_t e0[CH], e1[CH];
+        unsigned b0[CH], b1[CH];
+        uint32_t t0 = 0, t1 = 0;
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            e0[u] = 0; e1[u] = 0; b0[u] = 0; b1[u] = 0;
+            if (u < nb) {
+                adc_pair<M, BITS>(r[u], lane4, lut_s, e0[u], e1[u]);
+                b0[u] = __ballot_sync(0xFFFFFFFFu, ((v0 >> u) & 1u) && e0[u] <= et0);
+                b1[u] = __ballot_sync(0xFFFFFFFFu, ((v1 >> u) & 1u) && e1[u] <= et1);
+                t0 += (uint32_t)__popc(b0[u]);
+                t1 += (uint32_t)__popc(b1[u]);
+            }
+        }
+        if (t0) pair_append<CH>(ix, S[0], Q[0].region, cap0, e0, b0, gbk, t0, dmin0, sh0);
+        if (t1) pair_append<CH>(ix, S[1], Q[1].region, cap1, e1, b1, gbk, t1, dmin1, sh1);
+        if ((it & (kUpdateEvery - 1)) == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && !hb) break;
+                const uint32_t t = warp_update_bins(S[h].bh, S[h].bmap, a.m, Q[h].kc);
+                const uint32_t et = etau_of(S[h], t);
+                if (ln == 0) {
+                    atomicMin(&S[h].tau, t);
+                    atomicMin(&S[h].etau, et);
+                }
+            }
+        }
+    }
+}
+
+// Bytes of dynamic shared memory of the pair form: the table, 2 nprobe list
+// descriptors and flags, and the two main-list bitmaps.
+__host__ __device__ inline size_t pair_smem_bytes(int lut_words, int nprobe, int nlist) {
+    const size_t fl = ((size_t)2 * nprobe + 15) / 16 * 16;
+    return (size_t)lut_words * 4 + (size_t)2 * nprobe * 16 + fl + (size_t)2 * ((nlist + 31) / 32) * 4;
+}
+
+template <int M, int BITS>
+__global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS)
+scan_pair_kernel(DevIndex ix, ScanArgs a, const int32_t* __restrict__ perm, int64_t nq) {
+    using C = ScanCfg<M, BITS>;
+    extern __shared__ uint4 dsm[];
+    uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
+    int4* ldesc = reinterpret_cast<int4*>(lut + C::LUT_WORDS);                       // [2 nprobe]
+    uint8_t* lfl = reinterpret_cast<uint8_t*>(ldesc + 2 * a.nprobe);                  // [2 nprobe]
+    const int nlw = (ix.nlist + 31) / 32;
+    uint32_t* bm = reinterpret_cast<uint32_t*>(lfl + ((2 * a.nprobe + 15) / 16) * 16);  // [2][nlw]
+    __shared__ ScanShared S[2];
+    __shared__ uint32_t cf[2048 > (1 << C::SHC) ? 2048 : (1 << C::SHC)];
+    __shared__ int s_nsl[2], s_gu, s_nu;
+    __shared__ long long s_ns[2];
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const bool hb = 2 * (int64_t)blockIdx.x + 1 < nq;
+    const int64_t qid[2] = {perm[2 * (int64_t)blockIdx.x], hb ? perm[2 * (int64_t)blockIdx.x + 1] : perm[2 * (int64_t)blockIdx.x]};
+    QCtx Q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        Q[h] = QCtx{a.qp.P(qid[h]), a.qp.KC(qid[h]), a.qp.rcap(qid[h]), a.region + a.qp.roff(qid[h]),
+                    a.lists + a.qp.poff(qid[h])};
+
+    // ---- Phase A: the packed table, per-query state ----
+    stage_lut_pair<M, BITS>(a.lut16 + qid[0] * (int64_t)M * C::K, hb ? a.lut16 + qid[1] * (int64_t)M * C::K : nullptr,
+                            lut);
+    for (int i = tid; i < 2 * nlw; i += bs) bm[i] = 0u;
+    for (int i = tid; i < 256; i += bs) { S[0].bh[i] = 0u; S[1].bh[i] = 0u; }
+    if (tid < 2) {
+        S[tid].count = 0;
+        S[tid].dmin = 0xFFFFFFFFu;
+        S[tid].tau = (uint32_t)a.m;
+        S[tid].etau = 0xFFFFFFFFu;
+        S[tid].sh = 0;
+    }
+    // ---- Phases B and C per query: sample of its nearest lists, codebook ----
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !hb) break;
+        for (int i = tid; i < (int)(sizeof(cf) / 4); i += bs) cf[i] = 0u;
+        __syncthreads();
+        if (warp_id() == 0) {
+            const unsigned ln = lane_id();
+            long long carryv;
+            const int P = Q[h].P;
+            const int gtot = build_layout(ix, Q[h].lists, P, ldesc, &carryv);
+            __syncwarp();
+            const long long want = Q[h].kc < carryv ? Q[h].kc : carryv;
+            const int smin = a.sample_min < P ? a.sample_min : P;
+            long long cum = 0;
+            int nsl = P;
+            for (int base = 0; base < P; base += 32) {
+                const int j = base + (int)ln;
+                int nv = 0;
+                if (j < P) {
+                    const int4 d = ldesc[j];
+                    nv = d.w - 32 * d.x;
+                }
+                const unsigned long long incv = warp_incl_scan64((unsigned long long)nv);
+                const bool ok = j < P && (j + 1) >= smin && (long long)(cum + (long long)incv) >= want;
+                const unsigned hit = __ballot_sync(0xFFFFFFFFu, ok);
+                if (hit) { nsl = base + (int)(__ffs(hit) - 1) + 1; break; }
+                cum += (long long)__shfl_sync(0xFFFFFFFFu, incv, 31);
+            }
+            if (ln == 0) {
+                S[h].nsl = nsl;
+                S[h].sq = carryv;
+                S[h].gs = nsl > 0 ? ldesc[nsl - 1].y : 0;
+                S[h].gtot = gtot;
+                s_nsl[h] = nsl;
+            }
+        }
+        __syncthreads();
+        if (h == 0)
+            scan_blocks<M, BITS, false, false, 0>(ix, a, Q[0], a.state + qid[0], Q[0].P, 0, S[0].gs, lut, ldesc, S[0], cf);
+        else
+            scan_blocks<M, BITS, false, false, 1>(ix, a, Q[1], a.state + qid[1], Q[1].P, 0, S[1].gs, lut, ldesc, S[1], cf);
+        __syncthreads();
+        const int64_t ns = (int64_t)min((long long)S[h].count, (long long)Q[h].cap);
+        if (tid == 0) s_ns[h] = ns;
+        build_codebook_hist(Q[h].region, ns, Q[h].kc, a.m, S[h], cf, C::SHC);
+    }
+    // ---- Phase D: the union of the main lists, both queries per lookup ----
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !hb) break;
+        for (int j = s_nsl[h] + tid; j < Q[h].P; j += bs) {
+            const int l = Q[h].lists[j];
+            atomicOr(&bm[h * nlw + (l >> 5)], 1u << (l & 31));
+        }
+    }
+    __syncthreads();
+    if (warp_id() == 0) {
+        int nu;
+        const int gu = build_union_layout(ix, Q, s_nsl, hb, bm, nlw, ldesc, lfl, &nu);
+        if (lane_id() == 0) { s_gu = gu; s_nu = nu; }
+    }
+    __syncthreads();
+    if (s_nu > 0) scan_pair_main<M, BITS>(ix, a, Q, hb, s_nu, s_gu, lut, ldesc, lfl, S);
+    __syncthreads();
+
+    // ---- state out ----
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !hb) break;
+        bbc_collector_state* st = a.state + qid[h];
+        bins_to_buckets(S[h]);
+        for (int i = tid; i < kMaxBuckets; i += bs) st->hist[i] = i < a.m ? S[h].hist[i] : 0u;
+        for (int i = tid; i < 256; i += bs) st->map[i] = S[h].bmap[i];
+        if (warp_id() == 0) {
+            const uint32_t t1 = warp_update_bins(S[h].bh, S[h].bmap, a.m, Q[h].kc);
+            if (lane_id() == 0) {
+                st->d_min = S[h].dmin;
+                st->d_max = S[h].dmax;
+                st->sh = S[h].sh;
+                st->m = a.m;
+                st->sample_lists = S[h].nsl;
+                st->tau = (int32_t)t1;
+                st->sample_size = s_ns[h];
+                st->scanned = S[h].sq;
+                st->pushed = (int64_t)S[h].count;
+                st->below = 0;
+                st->kc = Q[h].kc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Largest dynamic shared memory a kernel can take next to its static shared
 // memory (227 KB per block in all).
 template <typename F>
@@ -903,6 +1280,48 @@ static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs&
     if (smem > (size_t)lim) return cudaErrorInvalidValue;
     scan_kernel<M, BITS><<<(unsigned)nq, C::THREADS, smem, st>>>(ix, a);
     return cudaGetLastError();
+}
+
+template <int M, int BITS>
+static cudaError_t launch_pair_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, const int32_t* perm,
+                                 cudaStream_t st) {
+    using C = ScanCfg<M, BITS>;
+    const size_t smem = pair_smem_bytes(C::LUT_WORDS, a.nprobe, ix.nlist);
+    static const int lim = max_dyn_smem(scan_pair_kernel<M, BITS>);   // a property of the compiled kernel
+    cudaError_t e = smem_attr_once((const void*)scan_pair_kernel<M, BITS>, lim);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)lim) return cudaErrorInvalidValue;
+    scan_pair_kernel<M, BITS><<<(unsigned)((nq + 1) / 2), SCAN_THREADS, smem, st>>>(ix, a, perm, nq);
+    return cudaGetLastError();
+}
+
+// The pair form runs for tables that allow two 512-thread CTAs per SM, and
+// only when its shared memory (table, list descriptors, bitmaps) still does.
+bool scan_pair_supported(const DevIndex& ix, int nprobe) {
+    int lut_words = 0;
+    if (ix.bits == 8 && (ix.M == 8 || ix.M == 16 || ix.M == 32)) lut_words = 256 * 64;
+    else if (ix.bits == 4 && (ix.M == 32 || ix.M == 64)) lut_words = 16 * (ix.M <= 32 ? 64 : 128);
+    else return false;
+    return pair_smem_bytes(lut_words, nprobe, ix.nlist) + 24 * 1024 <= 110 * 1024;
+}
+
+cudaError_t launch_scan_pair(const DevIndex& ix, int64_t nq, const ScanArgs& a, const int32_t* perm,
+                             cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    if (!scan_pair_supported(ix, a.nprobe)) return cudaErrorInvalidValue;
+    if (ix.bits == 8) {
+        switch (ix.M) {
+            case 8: return launch_pair_t<8, 8>(ix, nq, a, perm, st);
+            case 16: return launch_pair_t<16, 8>(ix, nq, a, perm, st);
+            case 32: return launch_pair_t<32, 8>(ix, nq, a, perm, st);
+        }
+    } else if (ix.bits == 4) {
+        switch (ix.M) {
+            case 32: return launch_pair_t<32, 4>(ix, nq, a, perm, st);
+            case 64: return launch_pair_t<64, 4>(ix, nq, a, perm, st);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 bool scan_supported(int M, int bits) {

@@ -134,23 +134,35 @@ def _collect(bbc, h, idx, q, nprobe, kc):
     return lists.cpu().numpy(), ids.cpu().numpy().view(np.uint32), cnt.cpu().numpy(), state
 
 
-@pytest.mark.parametrize("split", [1, 0])
+# scan schedules: one CTA per query, two queries per CTA (pair form), several CTAs per query
+MODES = {"single": (1, 0), "pair": (1, 1), "split": (0, 0)}
+
+
+def set_mode(bbc, h, mode):
+    split, pair = MODES[mode]
+    bbc.bbc_set_param(h, "split", split)
+    bbc.bbc_set_param(h, "pair", pair)
+
+
+@pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("kind,nprobe,kc,m,smin", [
     ("tiny", 12, 300, 64, 8), ("tiny", 48, 5000, 32, 8), ("sift", 16, 900, 64, 8),
     ("sift4", 20, 1200, 256, 4), ("embed", 10, 400, 2, 8), ("ragged", 40, 300, 16, 3),
     ("ragged", 2, 1000, 64, 8), ("sift", 64, 12000, 64, 8), ("tiny", 5, 1, 64, 8),
     ("wide", 6, 1500, 64, 8)])
-def test_collect_candidates_and_state(bbc, oracle_lib, kind, nprobe, kc, m, smin, split):
+def test_collect_candidates_and_state(bbc, oracle_lib, kind, nprobe, kc, m, smin, mode):
     h, idx, q = dev_index(bbc, kind)
     bbc.bbc_set_param(h, "buckets", m)
     bbc.bbc_set_param(h, "sample_lists", smin)
-    bbc.bbc_set_param(h, "split", split)
+    set_mode(bbc, h, mode)
+    if mode == "pair":
+        q = q[:len(q) - 1]                                # an odd batch: one CTA holds a single query
     try:
         lists, ids, cnt, state = _collect(bbc, h, idx, q, nprobe, kc)
     finally:
         bbc.bbc_set_param(h, "buckets", 64)
         bbc.bbc_set_param(h, "sample_lists", 8)
-        bbc.bbc_set_param(h, "split", 0)
+        set_mode(bbc, h, "split")
     for i in range(len(q)):
         ol, _ = oracle_lib.probe(q[i], idx.centroids, nprobe, idx.metric)
         assert np.array_equal(lists[i], ol)
@@ -177,15 +189,15 @@ def test_collect_candidates_and_state(bbc, oracle_lib, kind, nprobe, kc, m, smin
         assert s["pushed"] >= min(kc, len(e))
 
 
-@pytest.mark.parametrize("split", [1, 0])
+@pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("kind,k,nprobe,ratio", [("tiny", 100, 12, 2.0), ("sift", 500, 16, 1.5),
                                                  ("sift4", 300, 24, 2.0), ("embed", 200, 10, 1.5),
                                                  ("ragged", 50, 40, 1.0), ("tiny", 1, 3, 1.0),
                                                  ("sift", 4000, 64, 1.0), ("wide", 300, 6, 2.0)])
-def test_search_end_to_end(bbc, oracle_lib, kind, k, nprobe, ratio, split):
+def test_search_end_to_end(bbc, oracle_lib, kind, k, nprobe, ratio, mode):
     h, idx, q = dev_index(bbc, kind)
     bbc.bbc_set_param(h, "kc_ratio", ratio)
-    bbc.bbc_set_param(h, "split", split)
+    set_mode(bbc, h, mode)
     kc = max(k, int(np.ceil(ratio * k - 1e-9)))
     nq = len(q)
     ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
@@ -193,7 +205,7 @@ def test_search_end_to_end(bbc, oracle_lib, kind, k, nprobe, ratio, split):
     bbc.bbc_search(h, cuda(q), nq, k, nprobe, ids, dd)
     sync_ok(bbc, h)
     gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
-    bbc.bbc_set_param(h, "split", 0)
+    set_mode(bbc, h, "split")
     oi, od = oracle_lib.search(idx, q, k, nprobe, kc, "sort")
     exact = kind in ("sift", "sift4")
     for i in range(nq):
@@ -288,8 +300,9 @@ def test_argument_errors(bbc):
     bbc.bbc_search(h, qd, 0, 5, 4, ids, dd)      # nq = 0 is a no-op
 
 
+@pytest.mark.parametrize("mode", ["pair", "split"])
 @pytest.mark.parametrize("kind", ["sift", "tiny", "sift4", "embed"])
-def test_search_ex_mixed_batch_equals_alone(bbc, oracle_lib, kind):
+def test_search_ex_mixed_batch_equals_alone(bbc, oracle_lib, kind, mode):
     """A mixed batch (different k and nprobe per query) returns, for every
     query, the oracle's result at that query's own k, nprobe and K_c
     (Algorithm 1's candidate set re-ranked), and exactly what searching that
@@ -305,8 +318,12 @@ def test_search_ex_mixed_batch_equals_alone(bbc, oracle_lib, kind):
     ids = torch.empty(tot, dtype=torch.int64, device="cuda")
     dd = torch.empty(tot, dtype=torch.float32, device="cuda")
     qd = cuda(q)
-    bbc.bbc_search_ex(h, qd, nq, ks, ps, ids, dd)
-    sync_ok(bbc, h)
+    set_mode(bbc, h, mode)
+    try:
+        bbc.bbc_search_ex(h, qd, nq, ks, ps, ids, dd)
+        sync_ok(bbc, h)
+    finally:
+        set_mode(bbc, h, "split")
     gi, gd = ids.cpu().numpy(), dd.cpu().numpy()
     off = np.concatenate([[0], np.cumsum(ks)])
     exact = kind in ("sift", "sift4")
@@ -413,14 +430,16 @@ def test_rerank_integer_rows_integer_and_fractional_queries(bbc, oracle_lib, d, 
 @pytest.mark.parametrize("kind", ["tiny", "sift", "ragged"])
 def test_split_scan_equals_one_cta_per_query(bbc, kind):
     """Several CTAs per query (persistent (query, part) items, global collector
-    state) give exactly the candidates, threshold and results of one CTA per query."""
+    state) and two queries per CTA (pair form) give exactly the candidates,
+    threshold and results of one CTA per query."""
     h, idx, q = dev_index(bbc, kind)
     nq, k, nprobe = len(q), 150, min(idx.nlist, 24)
     bbc.bbc_set_param(h, "kc_ratio", 2.0)
     outs = {}
     try:
-        for split in (1, 2, 7, 64):
-            bbc.bbc_set_param(h, "split", split)
+        for split in (1, 2, 7, 64, "pair"):
+            bbc.bbc_set_param(h, "pair", 1 if split == "pair" else 0)
+            bbc.bbc_set_param(h, "split", 1 if split == "pair" else split)
             lists, ids, cnt, state = _collect(bbc, h, idx, q, nprobe, 2 * k)
             ri = torch.empty((nq, k), dtype=torch.int64, device="cuda")
             rd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
@@ -430,8 +449,9 @@ def test_split_scan_equals_one_cta_per_query(bbc, kind):
             outs[split] = (cands, cnt, state, ri.cpu().numpy(), rd.cpu().numpy())
     finally:
         bbc.bbc_set_param(h, "split", 0)
+        bbc.bbc_set_param(h, "pair", 0)
     ref = outs[1]
-    for split in (2, 7, 64):
+    for split in (2, 7, 64, "pair"):
         got = outs[split]
         assert np.array_equal(got[1], ref[1])
         for i in range(nq):
@@ -488,12 +508,13 @@ def test_autotune_picks_and_caches(bbc, tmp_path):
     try:
         ms = bbc.bbc_autotune(h, qd, nq, k, nprobe, cache)
         assert ms > 0
-        chosen = (bbc.bbc_get_param(h, "split"), bbc.bbc_get_param(h, "buckets"))
+        chosen = (bbc.bbc_get_param(h, "split"), bbc.bbc_get_param(h, "buckets"), bbc.bbc_get_param(h, "pair"))
         assert open(cache).read().count('"split"') == 1
         bbc.bbc_set_param(h, "split", 0)
         bbc.bbc_set_param(h, "buckets", 64)
+        bbc.bbc_set_param(h, "pair", 1 - chosen[2])
         assert bbc.bbc_autotune(h, qd, nq, k, nprobe, cache) == 0.0          # from the cache
-        assert (bbc.bbc_get_param(h, "split"), bbc.bbc_get_param(h, "buckets")) == chosen
+        assert (bbc.bbc_get_param(h, "split"), bbc.bbc_get_param(h, "buckets"), bbc.bbc_get_param(h, "pair")) == chosen
         gi = torch.empty_like(ref_i)
         gd = torch.empty_like(ref_d)
         bbc.bbc_search(h, qd, nq, k, nprobe, gi, gd)
@@ -502,3 +523,64 @@ def test_autotune_picks_and_caches(bbc, tmp_path):
     finally:
         bbc.bbc_set_param(h, "split", 0)
         bbc.bbc_set_param(h, "buckets", 64)
+        bbc.bbc_set_param(h, "pair", 0)
+
+
+@pytest.mark.parametrize("nq", [2, 3, 5, 33])
+def test_pair_form_small_and_degenerate_batches(bbc, oracle_lib, nq):
+    """The pair form on tiny batches (an odd query left alone), on duplicated
+    queries (a pair at distance 0) and on queries far apart (nearly disjoint
+    probe sets): candidates equal the oracle's top-K_c and the one-CTA form's."""
+    h, idx, q = dev_index(bbc, "sift")
+    rng = np.random.default_rng(nq)
+    sel = rng.integers(0, len(q), size=nq)
+    qs = q[sel].copy()
+    if nq >= 3:
+        qs[1] = qs[0]                                     # identical queries
+        qs[2] = 255.0 - qs[0]                             # a query far from the others
+    nprobe, kc = 20, 700
+    outs = []
+    try:
+        for pair in (0, 1):
+            bbc.bbc_set_param(h, "split", 1)
+            bbc.bbc_set_param(h, "pair", pair)
+            outs.append(_collect(bbc, h, idx, qs, nprobe, kc))
+    finally:
+        bbc.bbc_set_param(h, "split", 0)
+        bbc.bbc_set_param(h, "pair", 0)
+    (l0, i0, c0, s0), (l1, i1, c1, s1) = outs
+    assert np.array_equal(c0, c1)
+    for f in ("d_min", "d_max", "sh", "sample_lists", "sample_size", "scanned", "tau", "below"):
+        assert np.array_equal(s0[f], s1[f]), f
+    for i in range(nq):
+        assert np.array_equal(np.sort(i0[i, :c0[i]]), np.sort(i1[i, :c1[i]])), i
+        sel_pos, _ = scanned_set(idx, l1[i])
+        t16 = oracle_lib.lut16(qs[i], idx.codebooks, idx.metric)
+        e = oracle_lib.adc(t16, idx.codes[sel_pos], idx.pq_m, idx.pq_bits)
+        ref_ids, _ = oracle_lib.topkc(e, idx.ids[sel_pos], kc, "sort")
+        assert np.array_equal(np.sort(i1[i, :c1[i]].astype(np.int64)), np.sort(ref_ids)), i
+
+
+def test_pair_form_many_plan_blocks(bbc):
+    """More queries than one pairing block (16,384): pairs never cross blocks and
+    every query's candidates equal those of the one-CTA form."""
+    h, idx, q = dev_index(bbc, "tiny")
+    rng = np.random.default_rng(3)
+    nq = 16384 + 1001
+    qs = (q[rng.integers(0, len(q), size=nq)] + rng.normal(0, 0.05, size=(nq, idx.d))).astype(np.float32)
+    nprobe, kc = 6, 200
+    outs = []
+    try:
+        for pair in (0, 1):
+            bbc.bbc_set_param(h, "split", 1)
+            bbc.bbc_set_param(h, "pair", pair)
+            outs.append(_collect(bbc, h, idx, qs, nprobe, kc))
+    finally:
+        bbc.bbc_set_param(h, "split", 0)
+        bbc.bbc_set_param(h, "pair", 0)
+    (_, i0, c0, s0), (_, i1, c1, s1) = outs
+    assert np.array_equal(c0, c1)
+    assert np.array_equal(s0["tau"], s1["tau"]) and np.array_equal(s0["below"], s1["below"])
+    a = np.sort(np.where(np.arange(kc)[None, :] < c0[:, None], i0, 0xFFFFFFFF), axis=1)
+    b = np.sort(np.where(np.arange(kc)[None, :] < c1[:, None], i1, 0xFFFFFFFF), axis=1)
+    assert np.array_equal(a, b)
