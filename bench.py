@@ -47,7 +47,9 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference", "plain"],
+                   help="gb300: the batched path; reference: the CPU oracle; plain: the FP32 single-query GPU "
+                        "form (one bbc_search per query, FP32 rows)")
     p.add_argument("--workload", default="sift")
     p.add_argument("--n", type=int, default=None, help="override data size (testing only)")
     p.add_argument("--nq", type=int, default=None)
@@ -58,6 +60,13 @@ def parse():
     p.add_argument("--pair", default="0",
                    help="scan schedule: 1 two queries per CTA (pair form), 0 one; a comma list prints one line per value")
     p.add_argument("--cpu-queries", type=int, default=200, help="oracle sample for cpu_baseline")
+    p.add_argument("--cpu-mt-queries", type=int, default=None,
+                   help="oracle sample for the all-cores baseline (default: 64 per host core)")
+    p.add_argument("--plain-queries", type=int, default=1000, help="--impl plain: queries per step")
+    p.add_argument("--mixed-k", default=None,
+                   help="mixed batch: per-query k drawn uniformly (seed 7) from this comma list; the step is one "
+                        "bbc_search_ex call")
+    p.add_argument("--mixed-nprobe", default=None, help="mixed batch: per-query nprobe drawn from this comma list")
     p.add_argument("--ref-queries", type=int, default=24, help="oracle queries per reference step")
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -351,6 +360,9 @@ def main():
     if args.mode == "serve":
         run_serve(args, ws, rank, local)
         return
+    if args.impl == "plain":
+        run_plain(args, ws, rank, local)
+        return
     import torch
     import paper_2604_01960_gb300 as bbc
     torch.cuda.set_device(local)
@@ -370,6 +382,13 @@ def main():
     scales = [float(v) for v in str(args.bound_scale).split(",")] if index.info["quantizer"] == 1 else [None]
     buckets = [int(v) for v in str(args.buckets).split(",")]
     pairs = [int(v) for v in str(args.pair).split(",")]
+    if args.mixed_k:
+        index.set(kc_ratio=ratios[0], buckets=buckets[0], pair=pairs[0])
+        if scales[0] is not None:
+            index.set(bound_scale=scales[0])
+        measure_mixed(args, ws, rank, local, bbc, index, w, idx, q, t_build, xt, precs[0], ratios[0])
+        index.close()
+        return
     for prec in precs:
         for npb in nprobes:
             for ratio in ratios:
@@ -382,6 +401,201 @@ def main():
                             measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec, ratio,
                                     m)
     index.close()
+
+
+def run_plain(args, ws, rank, local):
+    """The plain FP32 single-query GPU form: one bbc_search per query (probe,
+    table, scan, selection, re-rank from the FP32 rows, top-k), the queries one
+    after another on one stream: no batching across queries, no CUDA graphs, no
+    u8 or low-precision copy.  A step is --plain-queries such searches."""
+    import torch
+    import paper_2604_01960_gb300 as bbc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bbc.build()
+    w, idx, q, k, nprobe, t_build = make_inputs(args, f"cuda:{local}", rank, ws)
+    torch.cuda.empty_cache()
+    index = bbc.Index(idx, device=local)
+    ratio = float(str(args.kc_ratio).split(",")[0])
+    index.set(workspace_mb=64 * 1024, kc_ratio=ratio, graphs=0, pair=0, split=0, buckets=int(str(args.buckets).split(",")[0]))
+    if index.info["vectors_u8_exact"]:
+        index.set(rerank=0)
+    if index.get("precision"):
+        index.set(precision=0)
+    h = index.handle
+    nsel = min(args.plain_queries, len(q))
+    qd = torch.from_numpy(np.ascontiguousarray(q[:nsel])).to(dev)
+    ids = torch.empty((nsel, k), dtype=torch.int64, device=dev)
+    dists = torch.empty((nsel, k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    L = bbc.lib()
+    qp, ip, dp, sp, d = qd.data_ptr(), ids.data_ptr(), dists.data_ptr(), stream.cuda_stream, idx.d
+
+    def step():
+        for i in range(nsel):
+            rc = L.bbc_search(h, qp + 4 * d * i, 1, k, nprobe, ip + 8 * k * i, dp + 4 * k * i, sp)
+            if rc:
+                raise bbc.BBCError(rc, L.bbc_last_error().decode())
+
+    step()
+    torch.cuda.synchronize()
+    bbc.bbc_stream_status(h)
+    xt = torch.from_numpy(idx.vectors).to(dev)
+    nrec = min(nsel, args.recall_queries or 1000)
+    rec_mean, rec_min, _ = recall_at_k(xt, qd[:nrec], ids[:nrec], k, idx.metric)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(ws)
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    t = max_over_ranks(ws, sum(a.elapsed_time(b) for a, b in evs) / 1e3)
+    if rank == 0:
+        print(json.dumps({
+            "impl": "plain", "metric": METRICS.get(args.workload, METRIC), "value": ws * nsel * args.steps / t,
+            "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16/u32 ADC, f32 re-rank from the FP32 rows", "data": "synthetic",
+            "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist,
+                       "pq": "sign 1-bit" if hasattr(idx, "rotation") else f"{idx.pq_m}x{idx.pq_bits}",
+                       "queries_per_step": nsel, "k": k, "nprobe": nprobe, "kc_ratio": ratio,
+                       "form": "one bbc_search per query, FP32 rows, no graphs",
+                       "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
+                       "l2_flush_between_steps": True, "index_build_s": round(t_build, 1)},
+            "clocks": clocks}), flush=True)
+    index.close()
+
+
+def measure_mixed(args, ws, rank, local, bbc, index, w, idx, q, t_build, xt, prec, ratio):
+    """One bbc_search_ex call over the whole batch with per-query k and nprobe
+    drawn uniformly (seed 7) from --mixed-k and --mixed-nprobe."""
+    import torch
+    dev = torch.device("cuda", local)
+    if index.get("precision") != prec:
+        index.set(precision=prec)
+    rng = np.random.default_rng(7)
+    kset = [int(v) for v in args.mixed_k.split(",")]
+    pset = [int(v) for v in (args.mixed_nprobe or str(w.nprobe)).split(",")]
+    nq = len(q)
+    ks = rng.choice(np.asarray(kset, dtype=np.int32), nq)
+    ps = rng.choice(np.asarray(pset, dtype=np.int32), nq)
+    off = np.concatenate([[0], np.cumsum(ks.astype(np.int64))])
+    tot = int(off[-1])
+    h = index.handle
+    qd = torch.from_numpy(q).to(dev)
+    ids = torch.empty(tot, dtype=torch.int64, device=dev)
+    dists = torch.empty(tot, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    is_sign = hasattr(idx, "rotation")
+
+    def step(qsrc=None):
+        bbc.bbc_search_ex(h, qd if qsrc is None else qsrc, nq, ks, ps, ids, dists, stream)
+
+    bbc.bbc_bounded_stats(h, reset=True)
+    step()
+    torch.cuda.synchronize()
+    bbc.bbc_stream_status(h)
+    bstats = bbc.bbc_bounded_stats(h, reset=True) if is_sign else None
+    # recall per k value, on up to --recall-queries queries of each
+    nrec_each = args.recall_queries or 250
+    rec_by_k, rec_by_p, rec_all = {}, {}, []
+    for kv in kset:
+        sel = np.nonzero(ks == kv)[0][:nrec_each]
+        if len(sel) == 0:
+            continue
+        rows = torch.stack([ids[off[i]:off[i] + kv] for i in sel])
+        dk = exact_kth(xt, qd[sel], kv, idx.metric)
+        v = xt[rows.clamp(min=0)]
+        qs = qd[sel][:, None, :]
+        dd = -(v * qs).sum(-1) if idx.metric == "ip" else ((v - qs) ** 2).sum(-1)
+        r = (torch.clamp(((dd <= dk[:, None]) & (rows >= 0)).sum(1), max=kv).double() / kv).cpu().numpy()
+        rec_by_k[kv] = float(r.mean())
+        for i, ri in zip(sel, r):
+            rec_all.append(ri)
+            rec_by_p.setdefault(int(ps[i]), []).append(ri)
+        del v, dd
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    bbc.bbc_set_param(h, "profile", 1)
+    bbc.bbc_profile_read(h, reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    stage_ms, launches = bbc.bbc_profile_read(h, reset=True)
+    bbc.bbc_set_param(h, "profile", 0)
+    t_dev = max_over_ranks(ws, sum(a.elapsed_time(b) for a, b in evs) / 1e3)
+    # end to end: pinned host queries copied in, results copied out, every step
+    hq = torch.from_numpy(q).pin_memory()
+    hi = torch.empty(tot, dtype=torch.int64).pin_memory()
+    hd = torch.empty(tot, dtype=torch.float32).pin_memory()
+    qbuf = torch.empty_like(qd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        qbuf.copy_(hq, non_blocking=True)
+        step(qbuf)
+        hi.copy_(ids, non_blocking=True)
+        hd.copy_(dists, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = max_over_ranks(ws, time.perf_counter() - t0)
+    cpu, cpu_mt = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, cpu_mt = cpu_baselines(args, idx, q, ks, ps, kc_ratio=ratio,
+                                    scale=index.get("bound_scale") if is_sign else None)
+    if rank == 0:
+        per = {s_: stage_ms[s_] / args.steps for s_ in stage_ms}
+        out = {
+            "metric": METRICS.get(args.workload, METRIC) + ", mixed k and nprobe",
+            "value": ws * nq * args.steps / t_dev, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("1-bit codes x 4-bit query planes (AND+POPC), f32 bounds, f32 re-rank (f64 at ties)" if is_sign
+                      else "u16/u32 ADC, f32 re-rank"), "data": "synthetic",
+            "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "nq": nq,
+                       "k": f"uniform over {kset} (seed 7)", "nprobe": f"uniform over {pset} (seed 7)",
+                       "one_call": "bbc_search_ex", "kc_ratio": None if is_sign else ratio,
+                       "recall_at_k": float(np.mean(rec_all)), "recall_by_k": rec_by_k,
+                       "recall_by_nprobe": {p_: float(np.mean(v)) for p_, v in sorted(rec_by_p.items())},
+                       "recall_queries_per_k": nrec_each, "recall_tie_aware": True,
+                       "l2_flush_between_steps": True, "index_build_s": round(t_build, 1)},
+            "stage_ms_per_step": per,
+            "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_mt,
+            "e2e": {"value": ws * nq * args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(q.nbytes),
+                    "d2h_bytes_per_step": int(tot * 12)},
+            "gpu_launches": int(launches), "clocks": clocks}
+        if is_sign:
+            out["bounded"] = {"per_step": bstats, "in_S_per_query": bstats["in_S"] / nq,
+                              "exact_per_query": bstats["exact"] / nq, "scanned_per_query": bstats["scanned"] / nq}
+        print(json.dumps(out), flush=True)
+    del ids, dists, flush, qd
 
 
 def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt, prec, ratio, m):
@@ -487,7 +701,8 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     # roofline of the dominant stage
     per = {s: stage_ms[s] / args.steps for s in stage_ms}
     peaks = _peaks()
-    sm_clk = 2070.0
+    # the lookup peak at the SM clock sampled during the timed region (maximum clock if none was sampled)
+    sm_clk = clocks.get("sm_mhz") or 2070.0
     lookups = float(s_q.double().sum()) * (idx.pq_m if not is_sign else 0)
     dpad = (idx.d + 15) // 16 * 16
     u8 = bool(index.get("rerank"))
@@ -524,33 +739,17 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     dom = max(per, key=lambda s: per[s])
     bound, amount, unit, peak = work[dom]
     achieved = amount / (per[dom] / 1e3)
-    # DRAM bytes per launch from an ncu capture of the current kernel (profiles/), scaled by queries
-    traffic = None
-    if dom == "scan" and w.name == "ivfpq-sift-1m-d128" and idx.pq_m == 32 and nprobe == 256:
-        traffic = (69.20e6 + 349.11e6) / 1300 * nq          # scan_kernel<32, 8>, 1,300-query capture
+    traffic, traffic_src = captured_traffic(dom, w.name, nprobe, kc, nq, bool(index.get("pair")))
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": traffic,
-            "peak_source": "152 SMs x 32 four-byte shared-memory lookups per clock x 2070 MHz" if dom == "scan"
-            else "MEASURED_PEAKS.json"}
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+            "peak_source": (f"152 SMs x 32 four-byte shared-memory lookups per clock x {sm_clk:.0f} MHz "
+                            "(median SM clock sampled during the timed region)") if dom == "scan"
+            else "MEASURED_PEAKS.json (measured copy / cuBLAS BF16 burst)"}
 
-    cpu = None
+    cpu, cpu_mt = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        nsamp = min(args.cpu_queries, nq)
-        if is_sign:
-            # index preparation outside the timed region: codes of the sample's probed lists, rotation error
-            probed = [oracle.probe(q[i], idx.centroids, nprobe, idx.metric)[0] for i in range(nsamp)]
-            scodes, sfac = oracle.sign_encode_lists(idx, np.concatenate(probed))
-            seps = oracle.rotation_eps(idx.rotation)
-        t0 = time.perf_counter()
-        if is_sign:
-            oracle.sign_search(idx, q[:nsamp], k, nprobe, scale=index.get("bound_scale"), codes=scodes,
-                               fac=sfac, eps=seps)
-        else:
-            oracle.search(idx, q[:nsamp], k, nprobe, kc, "sort")
-        tc = time.perf_counter() - t0
-        cpu = {"value": nsamp / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {nsamp} of the {nq} queries on the full index, single-threaded C"}
+        cpu, cpu_mt = cpu_baselines(args, idx, q, [k] * nq, [nprobe] * nq, kc_ratio=ratio,
+                                    scale=index.get("bound_scale") if is_sign else None)
 
     if rank == 0:
         rerank = ["u8-exact" if u8 else "f32", "bf16-prefilter", "fp8e4m3-prefilter"][prec]
@@ -577,6 +776,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
             "stage_ms_per_step": per,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_mt,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
@@ -595,6 +795,88 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
         print(json.dumps(out), flush=True)
     del ids, dists, flush, qd
     torch.cuda.empty_cache()
+
+
+def cpu_baselines(args, idx, q, ks, ps, kc_ratio=None, scale=None):
+    """The oracle, as it stands, timed on the host: single-threaded on the first
+    --cpu-queries queries, and on all host cores over a larger sample split
+    across threads (ctypes releases the interpreter lock during the C call, so
+    each thread runs one oracle call on its own query shard).  ks / ps: k and
+    nprobe of every query."""
+    import concurrent.futures as cf
+    import oracle
+    oracle.build()
+    is_sign = hasattr(idx, "rotation")
+    nq = len(q)
+    cores = os.cpu_count() or 1
+    seps = oracle.rotation_eps(idx.rotation) if is_sign else None
+
+    def kc_of(k):
+        return max(k, int(math.ceil(kc_ratio * k - 1e-9)))
+
+    def prepare(sel):
+        # index preparation outside the timed region: sign codes of the probed lists
+        if not is_sign:
+            return None
+        probed = [oracle.probe(q[i], idx.centroids, int(ps[i]), idx.metric)[0] for i in sel]
+        return oracle.sign_encode_lists(idx, np.concatenate(probed))
+
+    def run(sel, prep):
+        # queries of equal (k, nprobe) go through one oracle call
+        groups = {}
+        for i in sel:
+            groups.setdefault((int(ks[i]), int(ps[i])), []).append(i)
+        for (k, p), ii in groups.items():
+            if is_sign:
+                oracle.sign_search(idx, q[ii], k, p, scale=scale, codes=prep[0], fac=prep[1], eps=seps)
+            else:
+                oracle.search(idx, q[ii], k, p, kc_of(k), "sort")
+
+    n1 = min(args.cpu_queries, nq)
+    sel1 = list(range(n1))
+    prep1 = prepare(sel1)
+    t0 = time.perf_counter()
+    run(sel1, prep1)
+    t1 = time.perf_counter() - t0
+    single = {"value": n1 / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"first {n1} of the {nq} queries on the full index, single-threaded C"}
+    nm = min(args.cpu_mt_queries or 64 * cores, nq)
+    shards = [list(range(nm))[c::cores] for c in range(cores)]
+    shards = [sh for sh in shards if sh]
+    preps = [prepare(sh) for sh in shards]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=len(shards)) as ex:
+        list(ex.map(lambda a: run(*a), zip(shards, preps)))
+    tm = time.perf_counter() - t0
+    allc = {"value": nm / tm, "unit": UNIT, "cores": len(shards), "kind": "oracle, threaded over queries",
+            "sample": f"first {nm} of the {nq} queries on the full index, one oracle call per thread and shard"}
+    return single, allc
+
+
+def _source_sha(rel):
+    import hashlib
+    try:
+        return hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()
+    except OSError:
+        return None
+
+
+def captured_traffic(kernel, workload, nprobe, kc, nq, pair):
+    """DRAM bytes per launch of the dominant kernel from the ncu capture recorded in
+    profiles/traffic.json, scaled to this launch by queries, or None when no capture
+    matches this workload or the kernel's source has changed since the capture."""
+    try:
+        table = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None, "no capture"
+    for e in table.get("captures", []):
+        if (e.get("stage") == kernel and e.get("workload") == workload and e.get("nprobe") == nprobe
+                and e.get("kc") == kc and bool(e.get("pair", False)) == pair):
+            if _source_sha(e["source"]) != e.get("source_sha256"):
+                return None, f"{e['kernel']}: source changed since the capture"
+            return e["dram_bytes"] / e["queries"] * nq, (f"{e['kernel']}, ncu capture of {e['queries']} queries "
+                                                        f"scaled by queries ({e['file']})")
+    return None, "no capture of this kernel and workload"
 
 
 def _peaks():
