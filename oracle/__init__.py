@@ -91,6 +91,7 @@ def lib():
             L.oracle_rotation_eps.restype = C.c_double
             L.oracle_rotation_eps.argtypes = [vp, i32]
             L.oracle_sign_bounds.argtypes = [vp, i32, vp, vp, C.c_double, vp, vp, i64, C.c_double, vp, vp]
+            L.oracle_sign_bounds_rq.argtypes = [vp, i32, vp, vp, C.c_double, vp, vp, i64, C.c_double, vp, vp]
             L.oracle_alg2.restype = i64
             L.oracle_alg2.argtypes = [vp, vp, vp, i64, i32, vp, vp]
             L.oracle_obs1_count.restype = i64
@@ -347,6 +348,19 @@ def sign_bounds(q, centroid, rot, eps, codes, fac, scale: float = 1.0):
     return lb, ub
 
 
+def sign_bounds_rq(q, centroid, rot, eps, codes, fac, eps0: float = 1.9):
+    """Bounds [lb, ub] on ||q - o||^2 from the RaBitQ estimator and its
+    probabilistic error bound (epsilon_0 = eps0), for the given objects."""
+    q, c, r = _f32(q), _f32(centroid), _f32(rot)
+    codes = np.ascontiguousarray(codes, dtype=np.uint32)
+    fac = np.ascontiguousarray(fac, dtype=np.float64)
+    n = codes.shape[0]
+    lb = np.empty(n, dtype=np.float64)
+    ub = np.empty(n, dtype=np.float64)
+    lib().oracle_sign_bounds_rq(_p(q), q.shape[0], _p(c), _p(r), eps, _p(codes), _p(fac), n, eps0, _p(lb), _p(ub))
+    return lb, ub
+
+
 def alg2(lb, ub, ex, k: int):
     """Algorithm 2: (number of exact distances computed, result indices)."""
     lb, ub, ex = (np.ascontiguousarray(a, dtype=np.float64) for a in (lb, ub, ex))
@@ -403,13 +417,19 @@ def sign_encode_lists(index, lists):
     return codes, fac
 
 
-def sign_search(index, queries, k: int, nprobe: int, scale: float = 1.0, codes=None, fac=None, eps=None):
+def sign_search(index, queries, k: int, nprobe: int, scale: float = 1.0, codes=None, fac=None, eps=None,
+                estimator: int = 0, eps0: float = 1.9):
     """Bounded search over an IVF sign index (single-threaded).
 
-    Probe as in ``search``; bounds for every object of the probed lists; the
-    result is the k smallest (exact FP64 distance, id) of the probed lists.
-    Returns (ids [nq, k], dists [nq, k]) and per-query stats [S_q, |S|,
-    |certainly in|, |to decide|, Alg. 2 count, Obs. 1 count, two-round count]."""
+    Probe as in ``search``; bounds for every object of the probed lists
+    (estimator 0: the hard bounds, scaled by ``scale``; 1: the RaBitQ
+    estimator's probabilistic bounds with epsilon_0 = eps0).  With hard bounds
+    the result is the k smallest (exact FP64 distance, id) of the probed lists;
+    with the estimator's bounds it is what the two-round bounded re-rank
+    returns on them (which differs from the exact top-k only where a bound
+    fails).  Returns (ids [nq, k], dists [nq, k]) and per-query stats [S_q,
+    |S|, |certainly in|, |to decide|, Alg. 2 count, Obs. 1 count, two-round
+    count]."""
     if codes is None:
         codes, fac = sign_encode(index)
     if eps is None:
@@ -425,7 +445,10 @@ def sign_search(index, queries, k: int, nprobe: int, scale: float = 1.0, codes=N
         lbs, ubs, sel = [], [], []
         for l in lists:
             a, b = offs[l], offs[l + 1]
-            lb, ub = sign_bounds(q[i], index.centroids[l], index.rotation, eps, codes[a:b], fac[a:b], scale)
+            if estimator:
+                lb, ub = sign_bounds_rq(q[i], index.centroids[l], index.rotation, eps, codes[a:b], fac[a:b], eps0)
+            else:
+                lb, ub = sign_bounds(q[i], index.centroids[l], index.rotation, eps, codes[a:b], fac[a:b], scale)
             lbs.append(lb); ubs.append(ub); sel.append(np.arange(a, b))
         lb, ub, sel = np.concatenate(lbs), np.concatenate(ubs), np.concatenate(sel)
         gid = index.ids[sel]
@@ -434,7 +457,13 @@ def sign_search(index, queries, k: int, nprobe: int, scale: float = 1.0, codes=N
         ns, nin, nr = oneshot(lb, ub, k)
         a2, _ = alg2(lb, ub, ex, k)
         rc, ridx = rounds(lb, ub, ex, k)
-        if scale >= 1.0 and not np.array_equal(gid[ridx], oi[i][:len(ridx)]):
+        if scale >= 1.0 and not estimator and not np.array_equal(gid[ridx], oi[i][:len(ridx)]):
             raise AssertionError("two-round bounded re-rank disagrees with the exact top-k")
+        if estimator:
+            # the bounded procedure's own result on the estimator's bounds
+            oi[i] = -1
+            od[i] = np.inf
+            oi[i][:len(ridx)] = gid[ridx]
+            od[i][:len(ridx)] = ex[ridx]
         st[i] = [len(sel), ns, nin, nr, a2, obs1_count(lb, ub, ex, k), rc]
     return oi, od, st

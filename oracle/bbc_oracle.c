@@ -33,6 +33,11 @@
  *                         the 1-bit sign quantizer of the bounded re-rank
  *                         (Section 3.4): codes of the rotated residual and
  *                         hard per-object distance bounds.
+ *   oracle_sign_bounds_rq the same objects' bounds from the RaBitQ estimator
+ *                         and its probabilistic error bound (the method
+ *                         Section 3.4 builds on, with the Section 4.1 setting
+ *                         epsilon_0 = 1.9): not hard; the true distance lies
+ *                         inside with high probability.
  *   oracle_alg2           Algorithm 2, minimal re-ranking with two heaps.
  *   oracle_obs1_count     the set of Observation 1 (bounds enclosing Dist_k).
  *   oracle_oneshot        the one-pass sure-in / sure-out classification.
@@ -744,6 +749,92 @@ void oracle_sign_bounds(const float* q, int32_t d, const float* centroid, const 
         const double est = alpha * X;
         const double half = scale * (qn * e + fabs(alpha) * eta * sd);
         const double rot_err = 2.0 * eps * tn * sqrt(un2);
+        const double base = tn2 + un2;
+        const double slack = 1e-12 * (base + 2.0 * fabs(est) + 2.0 * half + rot_err);
+        double l = base - 2.0 * (est + half) - rot_err - slack;
+        lb[p] = l > 0.0 ? l : 0.0;
+        ub[p] = base - 2.0 * (est - half) + rot_err + slack;
+    }
+    free(t);
+    free(qr);
+    free(uq);
+}
+
+/* Bounds on ||q - o||^2 from the RaBitQ estimator, FP64, for the objects of
+ * list l (same inputs and 4-bit query as oracle_sign_bounds).  In RaBitQ's
+ * notation, with unit vectors o_r = r / ||r|| (r = P u, u = o - c_l),
+ * q_r = q' / ||q'|| and the quantised unit vector o_bar = s / sqrt(d):
+ *   <o_bar, o_r> = <s, r> / (sqrt(d) ||r||) = alpha sqrt(d) / ||r||;
+ *   estimator   <o_r, q_r> ~ <o_bar, q_r> / <o_bar, o_r>;
+ *   error bound |estimate - <o_r, q_r>| <= sqrt((1 - <o_bar, o_r>^2) / <o_bar, o_r>^2)
+ *                                          * epsilon_0 / sqrt(d - 1)
+ * with high probability over the random rotation.  Here ||r|| is taken as
+ * ||u|| (the rotation is orthonormal up to eps) and q_r is replaced by the
+ * 4-bit query q~.  Under the random rotation <s, q' - q~> behaves like a sum
+ * of d terms of random sign, standard deviation ||q' - q~|| = eta, so its
+ * share of the error is taken at the same confidence, epsilon_0 eta (the
+ * worst case is sqrt(d) eta).  The estimate of <q', r> = ||q'|| ||r|| <o_r, q_r>
+ * then gives
+ *   <q', r> in ||r||^2 / (d alpha) <s, q~>
+ *              +- ( ||q'|| ||r|| sqrt(1 / <o_bar, o_r>^2 - 1) epsilon_0 / sqrt(d - 1)
+ *                   + ||r||^2 / (d alpha) epsilon_0 eta ).
+ * The distance then follows as in oracle_sign_bounds.  An object with
+ * alpha = 0 (o at its centroid) keeps the hard bound. */
+void oracle_sign_bounds_rq(const float* q, int32_t d, const float* centroid, const float* rot, double eps,
+                           const uint32_t* codes, const double* fac, int64_t n, double eps0,
+                           double* lb, double* ub) {
+    const int32_t W = d / 32;
+    double* t = (double*)malloc(sizeof(double) * (size_t)d);
+    double* qr = (double*)malloc(sizeof(double) * (size_t)d);
+    int32_t* uq = (int32_t*)malloc(sizeof(int32_t) * (size_t)d);
+    double tn2 = 0.0;
+    for (int32_t i = 0; i < d; ++i) { t[i] = (double)q[i] - (double)centroid[i]; tn2 += t[i] * t[i]; }
+    double lo = INFINITY, hi = -INFINITY, qn2 = 0.0;
+    for (int32_t i = 0; i < d; ++i) {
+        double a = 0.0;
+        for (int32_t j = 0; j < d; ++j) a += (double)rot[(size_t)i * d + j] * t[j];
+        qr[i] = a;
+        qn2 += a * a;
+        if (a < lo) lo = a;
+        if (a > hi) hi = a;
+    }
+    const double delta = (hi - lo) / 15.0;
+    double eta2 = 0.0;
+    int64_t usum = 0;
+    for (int32_t i = 0; i < d; ++i) {
+        int32_t ui = 0;
+        if (delta > 0.0) {
+            double v = nearbyint((qr[i] - lo) / delta);
+            ui = v < 0.0 ? 0 : (v > 15.0 ? 15 : (int32_t)v);
+        }
+        uq[i] = ui;
+        usum += ui;
+        const double diff = qr[i] - (lo + delta * ui);
+        eta2 += diff * diff;
+    }
+    const double eta = sqrt(eta2), qn = sqrt(qn2), tn = sqrt(tn2), sd = sqrt((double)d);
+    const double tail = eps0 / sqrt((double)(d > 1 ? d - 1 : 1));
+    for (int64_t p = 0; p < n; ++p) {
+        const uint32_t* cw = codes + (size_t)p * W;
+        int64_t ub_sum = 0;
+        for (int32_t i = 0; i < d; ++i)
+            if ((cw[i / 32] >> (i % 32)) & 1u) ub_sum += uq[i];
+        const double alpha = fac[p * 4 + 0], e = fac[p * 4 + 1], un2 = fac[p * 4 + 2], pc = fac[p * 4 + 3];
+        const double X = lo * (2.0 * pc - d) + delta * (2.0 * (double)ub_sum - (double)usum);   /* <s, q~> */
+        const double rn = sqrt(un2);
+        double est, half;
+        if (alpha > 0.0 && rn > 0.0) {
+            const double ip_bar = alpha * sd / rn;                     /* <o_bar, o_r> */
+            double spread = 1.0 / (ip_bar * ip_bar) - 1.0;             /* (1 - ip^2) / ip^2 */
+            if (spread < 0.0) spread = 0.0;
+            const double kappa = un2 / ((double)d * alpha);            /* ||r||^2 / (d alpha) */
+            est = kappa * X;
+            half = qn * rn * sqrt(spread) * tail + kappa * eps0 * eta;
+        } else {
+            est = alpha * X;
+            half = qn * e + fabs(alpha) * eta * sd;
+        }
+        const double rot_err = 2.0 * eps * tn * rn;
         const double base = tn2 + un2;
         const double slack = 1e-12 * (base + 2.0 * fabs(est) + 2.0 * half + rot_err);
         double l = base - 2.0 * (est + half) - rot_err - slack;

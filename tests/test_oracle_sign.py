@@ -155,3 +155,74 @@ def test_alg2_oneshot_rounds_random(seed):
     cr, rres = oracle.rounds(lb, ub, ex, k)
     assert np.array_equal(rres, exact)
     assert m <= cr <= ns
+
+
+# ---- the RaBitQ estimator's probabilistic bounds ----------------------------
+
+def test_rq_bounds_collapse_closed_form():
+    """Identity rotation, o = alpha s (e = 0, so <o_bar, o_r> = 1) and a query on
+    the 4-bit grid (eta = 0): the estimator ||r||^2 / (d alpha) <s, q~> equals
+    alpha <s, q> = <q, o> exactly and the interval collapses to ||q - o||^2.
+    alpha != 1 separates ||r||^2 / (d alpha) from ||r||^2 / (d alpha^2)."""
+    d = 64
+    rng = np.random.default_rng(5)
+    s = np.where(rng.random((6, d)) < 0.5, -1.0, 1.0)
+    alpha = np.array([0.5, 2.0, 3.0, 0.25, 1.5, 7.0])
+    o = alpha[:, None] * s
+    q = rng.integers(0, 16, size=d).astype(np.float64)
+    q[0], q[1] = 0.0, 15.0                           # lo = 0, Delta = 1: every component on the grid
+    codes = np.packbits(s > 0, axis=1, bitorder="little").view(np.uint32)
+    fac = np.stack([alpha, np.zeros(6), (o * o).sum(1), (s > 0).sum(1)], axis=1)
+    lb, ub = oracle.sign_bounds_rq(q.astype(np.float32), np.zeros(d, np.float32), np.eye(d, dtype=np.float32),
+                                   0.0, codes, fac, eps0=1.9)
+    exact = ((q[None, :] - o) ** 2).sum(1)
+    assert np.allclose(lb, exact, rtol=1e-10, atol=0) and np.allclose(ub, exact, rtol=1e-10, atol=0)
+
+
+def _rq_instance(d, n, seed):
+    rng = np.random.default_rng(seed)
+    rot = random_rotation(d, seed=seed)
+    c = rng.standard_normal(d).astype(np.float32)
+    x = (c + rng.standard_normal((n, d))).astype(np.float32)
+    q = (c + 0.8 * rng.standard_normal(d)).astype(np.float32)
+    idx = _single_list_index(x, c, rot)
+    codes, fac = oracle.sign_encode(idx)
+    eps = oracle.rotation_eps(idx.rotation)
+    exact = oracle.rerank(q, idx.vectors, idx.ids, "l2")
+    return idx, q, codes, fac, eps, exact
+
+
+@pytest.mark.parametrize("d", [128, 256])
+def test_rq_bounds_cover_with_high_probability(d):
+    """On Gaussian residuals under a random rotation the estimator's intervals
+    (epsilon_0 = 1.9, about 1.9 standard deviations of the estimator) hold the
+    exact distance for most objects, are much narrower than the hard bounds,
+    and the estimator is unbiased: the mean error of the interval centres is
+    within four standard errors of 0."""
+    idx, q, codes, fac, eps, exact = _rq_instance(d, 4000, seed=d)
+    lb, ub = oracle.sign_bounds_rq(q, idx.centroids[0], idx.rotation, eps, codes, fac, eps0=1.9)
+    hl, hu = oracle.sign_bounds(q, idx.centroids[0], idx.rotation, eps, codes, fac, 1.0)
+    assert np.all((hl <= exact) & (exact <= hu))                     # hard bounds: always
+    inside = (lb <= exact) & (exact <= ub)
+    assert 0.90 <= inside.mean() < 1.0
+    assert np.median((hu - hl) / (ub - lb)) > 3.0
+    err = 0.5 * (lb + ub) - exact
+    assert abs(err.mean()) <= 4.0 * err.std() / np.sqrt(len(err))
+
+
+def test_rq_search_equals_rounds_on_its_bounds_and_recall():
+    """With the estimator's bounds the oracle's result is the two-round re-rank
+    on those bounds: k distinct ids, exact distances, ascending; most of the
+    exact top-k of the probed lists is kept."""
+    x, q = gist_shaped(8000, 4, d=128, n_centers=60)
+    idx = build_ivf_sign(x, 16, kmeans_iters=3)
+    k, nprobe = 200, 6
+    hi_, hd_, _ = oracle.sign_search(idx, q, k, nprobe)
+    ri, rd, st = oracle.sign_search(idx, q, k, nprobe, estimator=1, eps0=1.9)
+    for i in range(len(q)):
+        v = ri[i] >= 0
+        assert len(set(ri[i][v].tolist())) == v.sum() == k
+        assert np.all(np.diff(rd[i][v]) >= 0)
+        assert np.allclose(rd[i][v], oracle.rerank(q[i], idx.vectors, ri[i][v], "l2"), rtol=0, atol=0)
+        assert len(set(ri[i].tolist()) & set(hi_[i].tolist())) >= 0.9 * k
+        assert st[i, 1] < st[i, 0]                                   # S smaller than the scanned set
