@@ -74,12 +74,17 @@ def parse():
                    help="batch: the headline batched search; serve: continuous-batching server")
     p.add_argument("--requests", type=int, default=100_000, help="serve mode: requests per rate")
     p.add_argument("--rates", default="20000,50000,100000", help="serve mode: Poisson arrival rates (req/s)")
+    p.add_argument("--serve-nprobe", default="32,128,512", help="serve mode: nprobe drawn uniformly from this list")
     p.add_argument("--precision", default=None,
                    help="re-rank precision: 0 FP32 rows (or the exact u8 copy), 1 BF16 prefilter, 2 FP8-E4M3 "
                         "prefilter; a comma list prints one line per value (default: 0, or 2 for float data)")
     p.add_argument("--bound-scale", default="1",
                    help="sign-code indexes: factor on the worst-case bound terms (1 = hard bounds); a comma list "
                         "prints one line per value")
+    p.add_argument("--estimator", default="0",
+                   help="sign-code indexes: 0 hard bounds, 1 the RaBitQ estimator's probabilistic bounds; a comma "
+                        "list prints one line per value")
+    p.add_argument("--epsilon0", type=float, default=1.9, help="epsilon_0 of the estimator bounds")
     p.add_argument("--recall-queries", type=int, default=None,
                    help="queries whose recall is measured against exact kNN (default: all, at most 1,000)")
     return p.parse_args()
@@ -289,12 +294,15 @@ def run_serve(args, ws, rank, local):
     index.set(kc_ratio=float(str(args.kc_ratio).split(",")[0]), workspace_mb=64 * 1024)
     h = index.handle
     rates = [float(r) for r in args.rates.split(",")]
+    pset = tuple(int(v) for v in args.serve_nprobe.split(","))
+    nrec = min(args.requests, args.recall_queries or 2000)
+    every = max(1, args.requests // nrec)
     lines = []
     for rate in rates:
-        arr, ks, ps, qi = request_stream(args.requests, rate, len(q), seed=6)
+        arr, ks, ps, qi = request_stream(args.requests, rate, len(q), seed=6, nprobes=pset)
         sv = bbc.bbc_serve_start(h, max_batch=1024, streams=4, cand_bytes_budget=16 << 30)
         # warm-up: one request of each nprobe, largest k
-        for p_ in (32, 128, 512):
+        for p_ in pset:
             t = bbc.bbc_serve_submit(sv, q[0], 50000, p_)
             bbc.bbc_serve_poll(sv, t, 50000, -1)
         bbc.bbc_serve_stop(sv)
@@ -308,7 +316,7 @@ def run_serve(args, ws, rank, local):
                 while tickets[i] == 0:
                     time.sleep(0.0001)
                 r = bbc.bbc_serve_poll(sv, tickets[i], int(ks[i]), -1)
-                if i < 256:
+                if i % every == 0:
                     results[i] = r
             done.set()
 
@@ -323,7 +331,7 @@ def run_serve(args, ws, rank, local):
         wall = time.perf_counter() - t0
         st = bbc.bbc_serve_stats(sv)
         bbc.bbc_serve_stop(sv)
-        # recall on the first 256 requests (tie-aware, exact kNN on the GPU)
+        # recall on every (requests / recall sample)-th request (tie-aware, exact kNN on the GPU)
         xt = torch.from_numpy(idx.vectors).cuda()
         recs = []
         for i, (ri, rd) in results.items():
@@ -333,11 +341,16 @@ def run_serve(args, ws, rank, local):
             d = ((v - qv) ** 2).sum(-1)
             ok = (d <= dk) & (torch.from_numpy(ri).cuda() >= 0)
             recs.append((int(ps[i]), min(int(ks[i]), int(ok.sum())) / int(ks[i])))
-        by_p = {p_: float(np.mean([r for pp, r in recs if pp == p_])) for p_ in (32, 128, 512)
+        by_p = {p_: float(np.mean([r for pp, r in recs if pp == p_])) for p_ in pset
                 if any(pp == p_ for pp, _ in recs)}
+        # requests served at recall@k >= 0.95: those whose nprobe reaches it on the sample
+        ok_p = [p_ for p_, r in by_p.items() if r >= 0.95]
+        frac_ok = float(np.mean(np.isin(ps, ok_p))) if ok_p else 0.0
         lines.append({"offered_rps": rate, "completed_rps": len(arr) / wall, "p50_ms": st["p50_ms"],
                       "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"], "batches": st["batches"],
-                      "inflight_bytes_peak": st["inflight_bytes_peak"], "recall_by_nprobe": by_p})
+                      "inflight_bytes_peak": st["inflight_bytes_peak"], "recall_by_nprobe": by_p,
+                      "recall_sample": len(recs), "nprobe_at_recall_0.95": ok_p,
+                      "completed_rps_at_recall_0.95": frac_ok * len(arr) / wall, "wall_s": wall})
     if rank == 0:
         best = max(lines, key=lambda r: r["completed_rps"])
         print(json.dumps({
@@ -345,7 +358,7 @@ def run_serve(args, ws, rank, local):
             "value": best["completed_rps"], "unit": "requests/s", "n_gpus": ws, "higher_is_better": True,
             "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "data": "synthetic", "dtype": "u16/u32 ADC, f32 re-rank",
             "config": {"workload": "serve-" + w.name, "requests_per_rate": args.requests, "k": "log-uniform [100, 50000]",
-                       "nprobe": "uniform {32, 128, 512}", "kc_ratio": float(str(args.kc_ratio).split(",")[0]), "streams": 4,
+                       "nprobe": f"uniform {list(pset)}", "kc_ratio": float(str(args.kc_ratio).split(",")[0]), "streams": 4,
                        "max_batch": 1024, "cand_bytes_budget": 16 << 30, "index_build_s": round(t_build, 1)},
             "rates": lines}), flush=True)
     index.close()
@@ -380,12 +393,15 @@ def main():
     nprobes = [int(v) for v in args.nprobe.split(",")] if args.nprobe else [nprobe]
     ratios = [float(v) for v in str(args.kc_ratio).split(",")]
     scales = [float(v) for v in str(args.bound_scale).split(",")] if index.info["quantizer"] == 1 else [None]
+    ests = [int(v) for v in str(args.estimator).split(",")] if index.info["quantizer"] == 1 else [None]
+    if ests[0] is not None:
+        index.set(epsilon0=args.epsilon0)
     buckets = [int(v) for v in str(args.buckets).split(",")]
     pairs = [int(v) for v in str(args.pair).split(",")]
     if args.mixed_k:
         index.set(kc_ratio=ratios[0], buckets=buckets[0], pair=pairs[0])
         if scales[0] is not None:
-            index.set(bound_scale=scales[0])
+            index.set(bound_scale=scales[0], estimator=ests[0])
         measure_mixed(args, ws, rank, local, bbc, index, w, idx, q, t_build, xt, precs[0], ratios[0])
         index.close()
         return
@@ -394,12 +410,13 @@ def main():
             for ratio in ratios:
                 for m in buckets:
                     for scale in scales:
-                        for pair in pairs:
-                            index.set(kc_ratio=ratio, buckets=m, pair=pair)
-                            if scale is not None:
-                                index.set(bound_scale=scale)
-                            measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec, ratio,
-                                    m)
+                        for est in ests:
+                            for pair in pairs:
+                                index.set(kc_ratio=ratio, buckets=m, pair=pair)
+                                if scale is not None:
+                                    index.set(bound_scale=scale, estimator=est)
+                                measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec,
+                                        ratio, m)
     index.close()
 
 
@@ -569,7 +586,9 @@ def measure_mixed(args, ws, rank, local, bbc, index, w, idx, q, t_build, xt, pre
     cpu, cpu_mt = None, None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, cpu_mt = cpu_baselines(args, idx, q, ks, ps, kc_ratio=ratio,
-                                    scale=index.get("bound_scale") if is_sign else None)
+                                    scale=index.get("bound_scale") if is_sign else None,
+                                    estimator=int(index.get("estimator")) if is_sign else 0,
+                                    eps0=index.get("epsilon0") if is_sign else 1.9)
     if rank == 0:
         per = {s_: stage_ms[s_] / args.steps for s_ in stage_ms}
         out = {
@@ -593,7 +612,9 @@ def measure_mixed(args, ws, rank, local, bbc, index, w, idx, q, t_build, xt, pre
             "gpu_launches": int(launches), "clocks": clocks}
         if is_sign:
             out["bounded"] = {"per_step": bstats, "in_S_per_query": bstats["in_S"] / nq,
-                              "exact_per_query": bstats["exact"] / nq, "scanned_per_query": bstats["scanned"] / nq}
+                              "exact_per_query": bstats["exact"] / nq, "scanned_per_query": bstats["scanned"] / nq,
+                              "bounds": "RaBitQ estimator, probabilistic" if index.get("estimator") else "hard",
+                              "epsilon0": index.get("epsilon0") if index.get("estimator") else None}
         print(json.dumps(out), flush=True)
     del ids, dists, flush, qd
 
@@ -749,7 +770,9 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     cpu, cpu_mt = None, None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, cpu_mt = cpu_baselines(args, idx, q, [k] * nq, [nprobe] * nq, kc_ratio=ratio,
-                                    scale=index.get("bound_scale") if is_sign else None)
+                                    scale=index.get("bound_scale") if is_sign else None,
+                                    estimator=int(index.get("estimator")) if is_sign else 0,
+                                    eps0=index.get("epsilon0") if is_sign else 1.9)
 
     if rank == 0:
         rerank = ["u8-exact" if u8 else "f32", "bf16-prefilter", "fp8e4m3-prefilter"][prec]
@@ -784,7 +807,9 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
         if is_sign:
             out["bounded"] = {"per_step": bstats, "in_S_per_query": bstats["in_S"] / nq,
                               "exact_per_query": bstats["exact"] / nq,
-                              "bound_scale": index.get("bound_scale")}
+                              "bound_scale": index.get("bound_scale"),
+                              "bounds": "RaBitQ estimator, probabilistic" if index.get("estimator") else "hard",
+                              "epsilon0": index.get("epsilon0") if index.get("estimator") else None}
         if prec:
             out["precision"] = {"per_step": pstats, "fp32_recheck_frac": pstats["fp32_rechecked"] / max(1, pstats["scored"]),
                                 "fp64_frac": pstats["fp64_scored"] / max(1, pstats["scored"])}
@@ -797,7 +822,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     torch.cuda.empty_cache()
 
 
-def cpu_baselines(args, idx, q, ks, ps, kc_ratio=None, scale=None):
+def cpu_baselines(args, idx, q, ks, ps, kc_ratio=None, scale=None, estimator=0, eps0=1.9):
     """The oracle, as it stands, timed on the host: single-threaded on the first
     --cpu-queries queries, and on all host cores over a larger sample split
     across threads (ctypes releases the interpreter lock during the C call, so
@@ -828,7 +853,8 @@ def cpu_baselines(args, idx, q, ks, ps, kc_ratio=None, scale=None):
             groups.setdefault((int(ks[i]), int(ps[i])), []).append(i)
         for (k, p), ii in groups.items():
             if is_sign:
-                oracle.sign_search(idx, q[ii], k, p, scale=scale, codes=prep[0], fac=prep[1], eps=seps)
+                oracle.sign_search(idx, q[ii], k, p, scale=scale, codes=prep[0], fac=prep[1], eps=seps,
+                                   estimator=estimator, eps0=eps0)
             else:
                 oracle.search(idx, q[ii], k, p, kc_of(k), "sort")
 
@@ -843,7 +869,8 @@ def cpu_baselines(args, idx, q, ks, ps, kc_ratio=None, scale=None):
     nm = min(args.cpu_mt_queries or 64 * cores, nq)
     shards = [list(range(nm))[c::cores] for c in range(cores)]
     shards = [sh for sh in shards if sh]
-    preps = [prepare(sh) for sh in shards]
+    prep_all = prepare(list(range(nm)))                 # one encoding of all probed lists, shared
+    preps = [prep_all] * len(shards)
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=len(shards)) as ex:
         list(ex.map(lambda a: run(*a), zip(shards, preps)))

@@ -190,6 +190,23 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  results equal to the exact top-k of the probed lists;
  *                  smaller values narrow the intervals in the spirit of
  *                  RaBitQ's probabilistic bound and may drop true members.
+ *   "estimator"    sign-code indexes: 0 (default) = hard bounds (above); 1 =
+ *                  the RaBitQ estimator of <q', r> (Section 3.4 builds on it;
+ *                  Section 4.1 runs it with epsilon_0 = 1.9): the estimate
+ *                  ||r||^2 / (d alpha) <s, q~> with the probabilistic bound
+ *                  epsilon_0 / sqrt(d - 1) ||q'|| ||r|| sqrt(1 - <o_bar, o_r>^2)
+ *                  / <o_bar, o_r> plus the 4-bit query's share at the same
+ *                  confidence.  The true distance lies inside with high
+ *                  probability, not always; the result is the two-round
+ *                  bounded re-rank on these bounds (exact distances returned).
+ *   "epsilon0"     epsilon_0 of the estimator mode, in (0, 100].  Default 1.9.
+ *   "first_round"  sign-code indexes: the bounded re-rank's first round
+ *                  re-ranks the first_round * k objects of S = {lb <= U_k}
+ *                  with the smallest interval centres, in [1, 64]; the second
+ *                  round takes the rest of S whose lb is <= the k-th smallest
+ *                  upper bound of the first round's distances.  Default 2.
+ *                  Results never depend on it (with hard bounds), only the
+ *                  number of exact distances computed.
  * Unknown key or out-of-range value: BBC_ERR_ARG. */
 int bbc_set_param(bbc_index* ix, const char* key, double value);
 int bbc_get_param(const bbc_index* ix, const char* key, double* value);

@@ -97,7 +97,7 @@ def lib():
             L.oracle_obs1_count.restype = i64
             L.oracle_obs1_count.argtypes = [vp, vp, vp, i64, i32]
             L.oracle_rounds.restype = i64
-            L.oracle_rounds.argtypes = [vp, vp, vp, i64, i32, vp, vp]
+            L.oracle_rounds.argtypes = [vp, vp, vp, i64, i32, C.c_double, vp, vp]
             L.oracle_oneshot.restype = i64
             L.oracle_oneshot.argtypes = [vp, vp, i64, i32, vp, vp]
             L.oracle_search.restype = i32
@@ -384,12 +384,13 @@ def oneshot(lb, ub, k: int):
     return int(ns), a.value, b.value
 
 
-def rounds(lb, ub, ex, k: int):
-    """Two-round bounded re-rank: (exact distances computed, result indices sorted)."""
+def rounds(lb, ub, ex, k: int, first: float = 2.0):
+    """Two-round bounded re-rank (first round: the first * k smallest interval
+    centres of S): (exact distances computed, result indices sorted)."""
     lb, ub, ex = (np.ascontiguousarray(a, dtype=np.float64) for a in (lb, ub, ex))
     out = np.empty(max(k, 1), dtype=np.int64)
     no = C.c_int64()
-    cnt = lib().oracle_rounds(_p(lb), _p(ub), _p(ex), lb.shape[0], k, _p(out), C.byref(no))
+    cnt = lib().oracle_rounds(_p(lb), _p(ub), _p(ex), lb.shape[0], k, float(first), _p(out), C.byref(no))
     return int(cnt), out[:no.value].copy()
 
 
@@ -418,7 +419,7 @@ def sign_encode_lists(index, lists):
 
 
 def sign_search(index, queries, k: int, nprobe: int, scale: float = 1.0, codes=None, fac=None, eps=None,
-                estimator: int = 0, eps0: float = 1.9):
+                estimator: int = 0, eps0: float = 1.9, first: float = 2.0):
     """Bounded search over an IVF sign index (single-threaded).
 
     Probe as in ``search``; bounds for every object of the probed lists
@@ -456,7 +457,7 @@ def sign_search(index, queries, k: int, nprobe: int, scale: float = 1.0, codes=N
         oi[i], od[i] = topk_final(ex, gid, k)
         ns, nin, nr = oneshot(lb, ub, k)
         a2, _ = alg2(lb, ub, ex, k)
-        rc, ridx = rounds(lb, ub, ex, k)
+        rc, ridx = rounds(lb, ub, ex, k, first)
         if scale >= 1.0 and not estimator and not np.array_equal(gid[ridx], oi[i][:len(ridx)]):
             raise AssertionError("two-round bounded re-rank disagrees with the exact top-k")
         if estimator:

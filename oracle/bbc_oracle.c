@@ -768,9 +768,10 @@ void oracle_sign_bounds(const float* q, int32_t d, const float* centroid, const 
  *   estimator   <o_r, q_r> ~ <o_bar, q_r> / <o_bar, o_r>;
  *   error bound |estimate - <o_r, q_r>| <= sqrt((1 - <o_bar, o_r>^2) / <o_bar, o_r>^2)
  *                                          * epsilon_0 / sqrt(d - 1)
- * with high probability over the random rotation.  Here ||r|| is taken as
- * ||u|| (the rotation is orthonormal up to eps) and q_r is replaced by the
- * 4-bit query q~.  Under the random rotation <s, q' - q~> behaves like a sum
+ * with high probability over the random rotation.  Since alpha is the mean
+ * |r_i|, r - alpha s is orthogonal to s and ||r||^2 = e^2 + d alpha^2 (e =
+ * ||r - alpha s||), so <o_bar, o_r> and ||r|| come from the stored factors;
+ * q_r is replaced by the 4-bit query q~.  Under the random rotation <s, q' - q~> behaves like a sum
  * of d terms of random sign, standard deviation ||q' - q~|| = eta, so its
  * share of the error is taken at the same confidence, epsilon_0 eta (the
  * worst case is sqrt(d) eta).  The estimate of <q', r> = ||q'|| ||r|| <o_r, q_r>
@@ -821,20 +822,20 @@ void oracle_sign_bounds_rq(const float* q, int32_t d, const float* centroid, con
             if ((cw[i / 32] >> (i % 32)) & 1u) ub_sum += uq[i];
         const double alpha = fac[p * 4 + 0], e = fac[p * 4 + 1], un2 = fac[p * 4 + 2], pc = fac[p * 4 + 3];
         const double X = lo * (2.0 * pc - d) + delta * (2.0 * (double)ub_sum - (double)usum);   /* <s, q~> */
-        const double rn = sqrt(un2);
+        const double rn = sqrt(e * e + (double)d * alpha * alpha);    /* ||r|| */
         double est, half;
         if (alpha > 0.0 && rn > 0.0) {
             const double ip_bar = alpha * sd / rn;                     /* <o_bar, o_r> */
-            double spread = 1.0 / (ip_bar * ip_bar) - 1.0;             /* (1 - ip^2) / ip^2 */
+            double spread = (1.0 - ip_bar * ip_bar) / (ip_bar * ip_bar);
             if (spread < 0.0) spread = 0.0;
-            const double kappa = un2 / ((double)d * alpha);            /* ||r||^2 / (d alpha) */
+            const double kappa = rn * rn / ((double)d * alpha);        /* ||r||^2 / (d alpha) */
             est = kappa * X;
             half = qn * rn * sqrt(spread) * tail + kappa * eps0 * eta;
         } else {
             est = alpha * X;
             half = qn * e + fabs(alpha) * eta * sd;
         }
-        const double rot_err = 2.0 * eps * tn * rn;
+        const double rot_err = 2.0 * eps * tn * sqrt(un2);
         const double base = tn2 + un2;
         const double slack = 1e-12 * (base + 2.0 * fabs(est) + 2.0 * half + rot_err);
         double l = base - 2.0 * (est + half) - rot_err - slack;
@@ -978,14 +979,19 @@ int64_t oracle_oneshot(const double* lb, const double* ub, int64_t n, int32_t k,
 
 /* The bounded re-rank with exact returned distances, in two rounds (the
  * batched form of Algorithm 3's marginal re-ranking):
- *   1. U_k = k-th smallest ub; S = {lb <= U_k}; B = the k smallest (ub, index).
- *   2. Re-rank B; U' = the largest exact distance in B (>= Dist_k).
+ *   1. U_k = k-th smallest ub; S = {lb <= U_k} (every member of the top-k).
+ *   2. B = the ceil(first * k) members of S with the smallest interval
+ *      centre (lb + ub) / 2 (index breaking ties), all of S when it is not
+ *      larger; re-rank B; U' = the k-th smallest exact distance in B, an
+ *      upper bound of Dist_k (any k objects have a k-th smallest >= Dist_k).
  *   3. S' = {o in S \ B : lb_o <= U'}; re-rank S'.
  *   4. Result: the k smallest (exact, index) of B u S'.
- * Every object outside B u S' has lb > U', so k objects of B are strictly
- * nearer.  Writes the result indices (sorted) and returns the number of exact
+ * Every object outside B u S' has lb > U' >= Dist_k, so it is not among the
+ * top k.  The centres pick, among objects whose intervals all reach below
+ * U_k, the likeliest members first, so U' lands near Dist_k and S' stays
+ * small.  Writes the result indices (sorted) and returns the number of exact
  * distances computed (|B| + |S'|). */
-int64_t oracle_rounds(const double* lb, const double* ub, const double* ex, int64_t n, int32_t k,
+int64_t oracle_rounds(const double* lb, const double* ub, const double* ex, int64_t n, int32_t k, double first,
                       int64_t* out_idx, int64_t* out_n) {
     dkey* a = (dkey*)malloc(sizeof(dkey) * (size_t)(n > 0 ? n : 1));
     char* re = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
@@ -997,12 +1003,18 @@ int64_t oracle_rounds(const double* lb, const double* ub, const double* ex, int6
         for (int64_t i = 0; i < n; ++i) { a[i].s = ub[i]; a[i].id = i; }
         qsort(a, (size_t)n, sizeof(dkey), cmp_dkey);
         const double uk = a[k - 1].s;
-        double up = -INFINITY;
-        for (int32_t j = 0; j < k; ++j) {
-            re[a[j].id] = 1;
-            if (ex[a[j].id] > up) up = ex[a[j].id];
-        }
-        count = k;
+        int64_t ns = 0;                                    /* S, ordered by (centre, index) */
+        for (int64_t i = 0; i < n; ++i)
+            if (lb[i] <= uk) { a[ns].s = 0.5 * (lb[i] + ub[i]); a[ns].id = i; ++ns; }
+        qsort(a, (size_t)ns, sizeof(dkey), cmp_dkey);
+        int64_t nb = (int64_t)ceil(first * (double)k);
+        if (nb > ns) nb = ns;
+        double* eb = (double*)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+        for (int64_t j = 0; j < nb; ++j) { re[a[j].id] = 1; eb[j] = ex[a[j].id]; }
+        qsort(eb, (size_t)nb, sizeof(double), cmp_double);
+        const double up = eb[(k < nb ? k : nb) - 1];
+        free(eb);
+        count = nb;
         for (int64_t i = 0; i < n; ++i) {
             if (!re[i] && lb[i] <= uk && lb[i] <= up) { re[i] = 1; ++count; }
         }

@@ -126,6 +126,9 @@ struct bbc_index {
     unsigned long long* prec_totals = nullptr;   // [4] device counters of the precision re-rank
     unsigned long long* sign_totals = nullptr;   // [4] device counters of the bounded re-rank
     float bound_scale = 1.f;                     // sign codes: factor on the residual term
+    int estimator = 0;                           // sign codes: 0 hard bounds, 1 RaBitQ estimator
+    float eps0 = 1.9f;                           // its confidence parameter epsilon_0
+    float first_round = 2.f;                     // sign codes: first re-rank round, a multiple of k
     int split = 0;            // 0 automatic, 1 one CTA per query, G >= 2 CTAs per query
     int pair = 0;             // 1: two queries per CTA (pair form) where supported, 0: one
     int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
@@ -422,7 +425,7 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
     if (stop_after <= 2) return BBC_OK;
     CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(d, q, nc, lut, st); }));
     ScanArgs sa{lut, probe_in ? probe_in : probe, p.nprobe, p.kc, ix->buckets, ix->sample_lists,
-                region, p.cap, state, qp};
+                region, p.cap, state, qp, 0, SelectArgs{}};
     // one CTA per query when the batch fills the GPU, else G CTAs per query
     int G = ix->split >= 2 ? ix->split : 1;
     if (ix->split == 0) {
@@ -441,10 +444,15 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
         }));
         CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan_pair(d, nc, sa, perm, st); }));
     } else {
+        // one CTA per query: the selection (S7) runs in the scan's tail
+        sa.fuse_select = 1;
+        sa.sel = SelectArgs{region, p.cap, state, p.kc, cand, count, nullptr, qp};
         CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan(d, nc, sa, st); }));
     }
-    SelectArgs se{region, p.cap, state, p.kc, cand, count, nullptr, qp};
-    CUDA_TRY(stage(ix, 4, st, [&] { return launch_select(d, nc, se, st); }));
+    if (!sa.fuse_select) {
+        SelectArgs se{region, p.cap, state, p.kc, cand, count, nullptr, qp};
+        CUDA_TRY(stage(ix, 4, st, [&] { return launch_select(d, nc, se, st); }));
+    }
     if (stop_after <= 7) return BBC_OK;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + p.off_keys);
     RerankArgs ra{q, cand, count, p.kc, ix->rerank_u8 && d.vec_u8 != nullptr, cdist, p.k, out_ids,
@@ -537,7 +545,7 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, const SignShape& c, char* w
     CUDA_TRY(stage(ix, 2, st, [&] { return launch_rotate_f64(q, nullptr, nullptr, nullptr, d.rot, nc, d.d, qrot, st); }));
     SignArgs sa{};
     sa.qrot = qrot; sa.q = q; sa.lists = probe; sa.nprobe = c.max_probe; sa.k = c.max_k; sa.m = ix->buckets;
-    sa.sample_min = ix->sample_lists; sa.scale = ix->bound_scale;
+    sa.sample_min = ix->sample_lists; sa.scale = ix->bound_scale; sa.est = ix->estimator; sa.eps0 = ix->eps0;
     sa.region = reinterpret_cast<uint4*>(ws + p.off_region); sa.cap = qp.cap; sa.pushed = pushed; sa.scanned = scanned;
     sa.prep = reinterpret_cast<uint32_t*>(ws + p.off_prep);
     sa.qp = qp;
@@ -545,7 +553,7 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, const SignShape& c, char* w
     SignSelectArgs ss{};
     ss.region = sa.region; ss.pushed = pushed; ss.scanned = scanned; ss.clist = clist; ss.n_b = n_b; ss.n_c = n_c;
     ss.rest_key = reinterpret_cast<uint32_t*>(ws + p.off_rkey); ss.rest_id = reinterpret_cast<uint32_t*>(ws + p.off_rid);
-    ss.n_rest = n_rest; ss.cd = cd; ss.cr = cr; ss.totals = ix->sign_totals; ss.qp = qp;
+    ss.n_rest = n_rest; ss.cd = cd; ss.cr = cr; ss.totals = ix->sign_totals; ss.qp = qp; ss.first = ix->first_round;
     CUDA_TRY(stage(ix, 4, st, [&] { return launch_sign_select(d, nc, ss, st); }));
     PrecArgs pa = prec_args(ix, ws + p.off_prec, nc, c.sum_cap);
     pa.rho = cr;
@@ -563,7 +571,8 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, const SignShape& c, char* w
         // precision form's classification, FP32 recheck and FP64 decision
         RerankArgs r1 = ra;
         r1.cand_count = n_b;
-        r1.kc = c.max_k;
+        // grid sizing: the first round holds up to ceil(first_round * k) objects
+        r1.kc = std::min<int64_t>(qp.kc, (int64_t)std::ceil((double)ix->first_round * c.max_k));
         pa.sc_from = nullptr;
         CUDA_TRY(stage(ix, 5, st, [&] { return launch_prec_score(d, nc, r1, pa, st); }));
         CUDA_TRY(stage(ix, 4, st, [&] { return launch_sign_filter(d, nc, ss, st); }));
@@ -588,12 +597,12 @@ int run_sign_chunk(bbc_index* ix, const SignPlan& p, const SignShape& c, char* w
         rf.kc = c.max_k;
         CUDA_TRY(stage(ix, 8, st, [&] { return launch_rerank(d, nc, rf, st); }));
     } else {
-        // round 1: the k smallest upper bounds
+        // round 1: the first_round * k smallest interval centres of S
         pa.rc_from = nullptr;
         pa.rc_count = n_b;
         CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_plan(nc, pa, st); }));
         CUDA_TRY(stage(ix, 8, st, [&] { return launch_prec_recheck(d, nc, ra, pa, st); }));
-        // round 2: the rest of S whose lower bound reaches the largest upper bound of round 1
+        // round 2: the rest of S whose lower bound reaches the k-th smallest upper bound of round 1
         CUDA_TRY(stage(ix, 4, st, [&] { return launch_sign_filter(d, nc, ss, st); }));
         pa.rc_from = n_b;
         pa.rc_count = n_c;
@@ -1209,6 +1218,15 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "bound_scale") {
         if (!(v > 0.0 && v <= 1.0)) return fail(BBC_ERR_ARG, "bound_scale must be in (0, 1]");
         ix->bound_scale = (float)v;
+    } else if (k == "estimator") {
+        if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "estimator must be 0 (hard bounds) or 1 (RaBitQ)");
+        ix->estimator = (int)v;
+    } else if (k == "first_round") {
+        if (!(v >= 1.0 && v <= 64.0)) return fail(BBC_ERR_ARG, "first_round must be in [1, 64]");
+        ix->first_round = (float)v;
+    } else if (k == "epsilon0") {
+        if (!(v > 0.0 && v <= 100.0)) return fail(BBC_ERR_ARG, "epsilon0 must be in (0, 100]");
+        ix->eps0 = (float)v;
     } else if (k == "precision") {
         if (v != 0 && v != 1 && v != 2)
             return fail(BBC_ERR_ARG, "precision must be 0 (FP32 re-rank), 1 (BF16 copy) or 2 (FP8-E4M3 copy)");
@@ -1242,6 +1260,9 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "graphs") *v = ix->graphs;
     else if (k == "precision") *v = ix->dev.prec;
     else if (k == "bound_scale") *v = ix->bound_scale;
+    else if (k == "estimator") *v = ix->estimator;
+    else if (k == "epsilon0") *v = ix->eps0;
+    else if (k == "first_round") *v = ix->first_round;
     else if (k == "region_cap") *v = (double)ix->region_cap;
     else if (k == "pair") *v = ix->pair;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
@@ -1784,7 +1805,7 @@ int bbc_sign_bounds(bbc_index* ix, const float* queries, int64_t nq, int32_t npr
     CUDA_TRY(stage(ix, 2, st, [&] { return launch_rotate_f64(queries, nullptr, nullptr, nullptr, d.rot, nq, d.d, qrot, st); }));
     SignArgs sa{};
     sa.qrot = qrot; sa.q = queries; sa.lists = probe_lists; sa.nprobe = nprobe; sa.k = 1; sa.m = ix->buckets;
-    sa.sample_min = ix->sample_lists; sa.scale = ix->bound_scale; sa.cap = stride; sa.scanned = out_count;
+    sa.sample_min = ix->sample_lists; sa.scale = ix->bound_scale; sa.est = ix->estimator; sa.eps0 = ix->eps0; sa.cap = stride; sa.scanned = out_count;
     sa.dbg_lb = out_lb; sa.dbg_ub = out_ub;
     sa.prep = reinterpret_cast<uint32_t*>(ws + qb);
     sa.qp = uniform_params(nprobe, stride, 1, stride);

@@ -142,6 +142,17 @@ cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, 
 cudaError_t launch_lut16(const DevIndex& ix, const float* q, int64_t nq, uint16_t* lut16,
                          cudaStream_t st);
 
+struct SelectArgs {
+    const uint2* region;
+    int64_t cap;
+    bbc_collector_state* state;
+    int64_t kc;
+    uint32_t* cand;               // candidates, per QueryParams::coff
+    int64_t* cand_count;          // [nq]
+    uint2* spill;                 // unused
+    QueryParams qp;
+    uint32_t tcap = 0;            // set by the fused launch: threshold-bucket keys in shared memory
+};
 struct ScanArgs {
     const uint16_t* lut16;        // [nq][M][K]
     const int32_t* lists;         // probe lists, packed per QueryParams::poff
@@ -153,8 +164,11 @@ struct ScanArgs {
     int64_t cap;                  // uniform region capacity (per-query values in qp)
     bbc_collector_state* state;   // [nq]
     QueryParams qp;
+    int fuse_select;              // 1: the one-CTA-per-query scan runs S7 in its tail (outputs in sel)
+    SelectArgs sel;
 };
-// S4-S6: sample + codebook + scan + push/update, one CTA per query.
+// S4-S6: sample + codebook + scan + push/update, one CTA per query (and S7
+// in its tail when fuse_select is set).
 cudaError_t launch_scan(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st);
 // Same result with G CTAs per query (persistent CTAs over (query, part) items);
 // counters: 2 u32 of device scratch.  The state array must be zeroed first.
@@ -175,16 +189,6 @@ size_t pair_plan_bytes(int64_t nq);
 cudaError_t launch_pair_plan(const float* q, int d, int64_t nq, const QueryParams& qp, const int32_t* lists,
                              void* scratch, int32_t* perm, cudaStream_t st);
 
-struct SelectArgs {
-    const uint2* region;
-    int64_t cap;
-    bbc_collector_state* state;
-    int64_t kc;
-    uint32_t* cand;               // candidates, per QueryParams::coff
-    int64_t* cand_count;          // [nq]
-    uint2* spill;                 // unused
-    QueryParams qp;
-};
 // S7: exact threshold bucket, compaction, top-s of the threshold bucket.
 cudaError_t launch_select(const DevIndex& ix, int64_t nq, const SelectArgs& a, cudaStream_t st);
 
@@ -270,6 +274,8 @@ struct SignArgs {
     int m;                        // buckets
     int sample_min;               // minimum sampled lists
     float scale;                  // scale of the residual term (1 = hard bounds)
+    int est;                      // 0: hard bounds; 1: the RaBitQ estimator's probabilistic bounds
+    float eps0;                   // its confidence parameter epsilon_0
     uint4* region;                // {lb key, ub key, slot, 0}, per QueryParams::roff
     int64_t cap;
     int64_t* pushed;              // [nq]
@@ -297,6 +303,7 @@ struct SignSelectArgs {
     const float* cr;              // and bounds
     unsigned long long* totals;   // [4]
     QueryParams qp;
+    float first = 2.f;            // first-round size, a multiple of k
 };
 cudaError_t launch_sign_select(const DevIndex& ix, int64_t nq, const SignSelectArgs& a, cudaStream_t st);
 cudaError_t launch_sign_filter(const DevIndex& ix, int64_t nq, const SignSelectArgs& a, cudaStream_t st);

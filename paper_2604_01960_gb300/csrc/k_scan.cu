@@ -40,6 +40,7 @@
 
 #include "bbc_internal.cuh"
 #include "dev_util.cuh"
+#include "select_body.cuh"
 
 namespace bbc {
 
@@ -750,6 +751,12 @@ __global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::M
             st->kc = Q.kc;
         }
     }
+    // ---- S7 in the tail: the query's region is still in L2; the table's
+    // shared memory (dead now) holds the threshold bucket's keys ----
+    if (a.fuse_select) {
+        __syncthreads();
+        select_query(ix, a.sel, qi, reinterpret_cast<unsigned long long*>(dsm), a.sel.tcap);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1270,10 +1277,18 @@ static cudaError_t launch_split_t(const DevIndex& ix, int64_t nq, const ScanArgs
     return cudaGetLastError();
 }
 
+// Threshold-bucket keys the fused selection holds in shared memory at least.
+constexpr size_t kFusedSelectKeys = 8192;
+
 template <int M, int BITS>
-static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, cudaStream_t st) {
+static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs& a0, cudaStream_t st) {
     using C = ScanCfg<M, BITS>;
-    const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)a.nprobe * sizeof(int4);
+    ScanArgs a = a0;
+    size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)a.nprobe * sizeof(int4);
+    if (a.fuse_select) {
+        smem = std::max(smem, kFusedSelectKeys * 8);
+        a.sel.tcap = (uint32_t)(smem / 8);
+    }
     static const int lim = max_dyn_smem(scan_kernel<M, BITS>);   // a property of the compiled kernel
     cudaError_t e = smem_attr_once((const void*)scan_kernel<M, BITS>, lim);
     if (e != cudaSuccess) return e;

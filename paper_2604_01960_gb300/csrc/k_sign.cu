@@ -18,16 +18,27 @@
 //   scale = eps0 / sqrt(d - 1) gives intervals in the spirit of RaBitQ's
 //   probabilistic bound (not hard).
 //
+// Estimator mode (est = 1): RaBitQ's estimator and its probabilistic bound.
+//   <o_bar, o_r> = alpha sqrt(d) / ||r|| with ||r||^2 = e^2 + d alpha^2 (r -
+//   alpha s is orthogonal to s); the estimate of <q', r> is kappa <q~, s>,
+//   kappa = ||r||^2 / (d alpha), within
+//     eps0 / sqrt(d - 1) ||q'|| ||r|| e / (alpha sqrt(d))   (the estimator's bound)
+//     + kappa eps0 eta                                      (the 4-bit query, same confidence)
+//   with high probability over the random rotation; the rest as above.
+//
 // Collection (a result buffer on the upper bound, Alg. 1 and Alg. 3): the
 // histogram counts every scanned object by the bucket of its upper bound;
 // tau (Update, >= k) therefore bounds the bucket of U_k, the k-th smallest
 // upper bound, and an object is appended when the bucket of its lower bound
 // is <= tau, which keeps every object of S = {lb <= U_k}.
 //
-// Re-rank in two rounds with exact returned distances: B = the k smallest
-// (ub, slot) of S are re-ranked first; U' = the largest upper FP32 bound in
-// B (>= Dist_k); then S' = {o in S \ B : lb <= U'}; the final k come from
-// B u S' in exact order (FP32 with its bound, FP64 at ties).
+// Re-rank in two rounds with exact returned distances: B = the ceil(f k)
+// members of S with the smallest interval centre (lb + ub) / 2 (slot breaking
+// ties) are re-ranked first; U' = the k-th smallest FP32 upper bound of their
+// distances (>= Dist_k: any k objects have a k-th smallest >= Dist_k); then
+// S' = {o in S \ B : lb <= U'}; the final k come from B u S' in exact order
+// (FP32 with its bound, FP64 at ties).  Centres put the likeliest members
+// first, so U' lands near Dist_k and S' stays small.
 #include "bbc_internal.cuh"
 #include "dev_util.cuh"
 
@@ -167,6 +178,7 @@ __global__ void sign_factors_kernel(const double* __restrict__ R, int64_t s0, in
 struct ListSetup {
     float lo, delta, tn2, tn, eta_sd, qn, dterm;
     int usum;
+    float eta;          // eta itself (rounded up), for the estimator mode
 };
 
 __host__ __device__ inline int sign_rec_words(int d) { return 4 * (d / 32) + 8; }
@@ -252,7 +264,7 @@ __global__ void sign_prep_kernel(DevIndex ix, SignArgs a, uint32_t* __restrict__
 // prepared list (planes in this warp's shared memory, scalars in registers).
 __device__ __forceinline__ void sign_bound(const DevIndex& ix, int64_t slot, const uint32_t* planes,
                                            const ListSetup& ls, float scale, float eps, float g_t, float& lb,
-                                           float& ub) {
+                                           float& ub, int est_mode = 0, float eps0 = 0.f, float tail = 0.f) {
     const int W = ix.d >> 5;
     const int64_t blk = slot >> 5;
     const int t = (int)(slot & 31);
@@ -272,8 +284,19 @@ __device__ __forceinline__ void sign_bound(const DevIndex& ix, int64_t slot, con
     const float eX = 2.384185791015625e-7f * (fabsf(x1) + fabsf(x2));       // 2^-22 (|x1| + |x2|)
     const float alpha = f.x, e = f.y, un2 = f.z;
     const float un = sqrtf(un2) * (1.f + 2.384185791015625e-7f);
-    const float est = alpha * X;
-    const float H = fabsf(alpha) * eX + scale * (fabsf(alpha) * ls.eta_sd + ls.qn * e) + ls.dterm * un * (1.f + eps);
+    float est, H;
+    if (est_mode && alpha > 0.f) {
+        const float dd = (float)ix.d;
+        const float rn2 = fmaf(e, e, dd * alpha * alpha);                   // ||r||^2
+        const float kap = rn2 / (dd * alpha);
+        const float rn = sqrtf(rn2) * (1.f + 2.384185791015625e-7f);
+        const float spread = e / (alpha * sqrtf(dd));                         // sqrt((1 - ip^2) / ip^2)
+        est = kap * X;
+        H = kap * eX + tail * ls.qn * rn * spread + kap * eps0 * ls.eta + ls.dterm * un * (1.f + eps);
+    } else {
+        est = alpha * X;
+        H = fabsf(alpha) * eX + scale * (fabsf(alpha) * ls.eta_sd + ls.qn * e) + ls.dterm * un * (1.f + eps);
+    }
     const float base = ls.tn2 + un2;
     const float rotE = 2.f * eps * ls.tn * un;
     // 2^-20 relative for the FP32 evaluation here, g_t for the FP32 sum ||t||^2
@@ -304,6 +327,7 @@ __device__ __forceinline__ ListSetup sign_load_list(const uint32_t* __restrict__
     ListSetup ls;
     ls.lo = fo[0]; ls.delta = fo[1]; ls.tn2 = fo[2]; ls.tn = fo[3]; ls.eta_sd = fo[4]; ls.qn = fo[5]; ls.dterm = fo[6];
     ls.usum = reinterpret_cast<const int*>(rec)[4 * W + 7];
+    ls.eta = ls.eta_sd / sqrtf((float)(32 * W)) * (1.f + 4.76837158203125e-7f);
     __syncwarp();
     (void)R;
     return ls;
@@ -346,6 +370,7 @@ __global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, Sign
     const int64_t cap = a.qp.rcap(qi);
     const float eps = (float)(ix.eps_p * (1.0 + 1e-6)) + 1e-12f;
     const float g_t = 2.f * (float)(W + 8) * 5.9604644775390625e-8f;
+    const float tail = a.eps0 / sqrtf((float)(d > 1 ? d - 1 : 1));
     const int tid = threadIdx.x, nw = blockDim.x >> 5;
     uint32_t* planes = spl + warp_id() * 4 * W;
     if (tid == 0) {
@@ -378,7 +403,7 @@ __global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, Sign
             const int64_t b0 = ix.list_blk[l];
             for (int p = (int)lane_id(); p < len; p += 32) {
                 float lb, ub;
-                sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, g_t, lb, ub);
+                sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, g_t, lb, ub, a.est, a.eps0, tail);
                 if (pre[j] + p < cap) {
                     a.dbg_lb[a.qp.roff(qi) + pre[j] + p] = lb;
                     a.dbg_ub[a.qp.roff(qi) + pre[j] + p] = ub;
@@ -403,7 +428,7 @@ __global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, Sign
             const int p = b + (int)lane_id();
             const bool valid = p < len;
             float lb = 0.f, ub = 0.f;
-            if (valid) sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, g_t, lb, ub);
+            if (valid) sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, g_t, lb, ub, a.est, a.eps0, tail);
             const uint32_t pos = sg_append(valid, &s_cnt);
             if (valid && pos < cap) region[pos] = make_uint4(0u, f32_key(ub), 0u, 0u);
         }
@@ -469,7 +494,7 @@ __global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, Sign
             const int p = b + (int)lane_id();
             const bool valid = p < len;
             float lb = 0.f, ub = 0.f;
-            if (valid) sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, g_t, lb, ub);
+            if (valid) sign_bound(ix, b0 * 32 + p, planes, ls, a.scale, eps, g_t, lb, ub, a.est, a.eps0, tail);
             const uint32_t ubk = f32_key(ub), lbk = f32_key(lb);
             if (valid) atomicAdd(&hist[sg_bucket(ubk, dmin, sh, smap)], 1u);
             const bool push = valid && lbk <= ktau;         // bucket(lb) <= tau
@@ -517,38 +542,52 @@ __global__ void __launch_bounds__(SG_THREADS) sign_scan_kernel(DevIndex ix, Sign
 // ---------------------------------------------------------------------------
 // First round: U_k, S, the k smallest (ub, slot) of S (B) and the rest of S.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sg_centre_key(const uint4& e) {
+    return f32_key(0.5f * (key_f32(e.x) + key_f32(e.y)));
+}
+
 __global__ void __launch_bounds__(SG_THREADS) sign_select_kernel(DevIndex ix, SignSelectArgs a) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t sc[2];
-    __shared__ uint32_t s_b, s_r, s_lt, s_eq;
+    __shared__ uint32_t s_b, s_r, s_lt, s_eq, s_ns;
     const int64_t qi = blockIdx.x;
     const int64_t n = a.pushed[qi];
     const int64_t kq = a.qp.K(qi);
     const int64_t off = a.qp.coff(qi);
     const uint4* reg = a.region + a.qp.roff(qi);
-    if (threadIdx.x == 0) { s_b = 0; s_r = 0; s_lt = 0; s_eq = 0; }
+    if (threadIdx.x == 0) { s_b = 0; s_r = 0; s_lt = 0; s_eq = 0; s_ns = 0; }
     __syncthreads();
     const bool all = a.scanned[qi] <= kq;                   // every scanned object is a result
-    uint32_t uk = 0xFFFFFFFFu, slot_cut = 0xFFFFFFFFu;
+    uint32_t uk = 0xFFFFFFFFu, ck = 0xFFFFFFFFu, slot_cut = 0xFFFFFFFFu;
     if (!all && n > 0) {
-        // U_k, then the k smallest (ub, slot): all of ub < U_k and, among ub == U_k,
-        // the smallest slots (selected only when U_k is shared)
+        // U_k, then S = {lb <= U_k} and its first round B: the ceil(f k)
+        // smallest (centre, slot) of S
         const uint32_t r = (uint32_t)(min(n, kq) - 1);
         uk = cta_select_u32(n, r, [&](int64_t i) { return reg[i].y; }, hist, sc, 24);
-        uint32_t lt = 0, eq = 0;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint32_t y = reg[i].y;
-            lt += y < uk ? 1u : 0u;
-            eq += y == uk ? 1u : 0u;
-        }
-        lt = __reduce_add_sync(0xFFFFFFFFu, lt);
-        eq = __reduce_add_sync(0xFFFFFFFFu, eq);
-        if (lane_id() == 0) { atomicAdd(&s_lt, lt); atomicAdd(&s_eq, eq); }
+        uint32_t ns = 0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) ns += reg[i].x <= uk ? 1u : 0u;
+        ns = __reduce_add_sync(0xFFFFFFFFu, ns);
+        if (lane_id() == 0) atomicAdd(&s_ns, ns);
         __syncthreads();
-        const uint32_t want = r + 1 - s_lt;                 // >= 1: members taken at U_k
-        if (want < s_eq)
-            slot_cut = cta_select_u32(n, want - 1, [&](int64_t i) { return reg[i].y == uk ? reg[i].z : 0xFFFFFFFFu; },
-                                      hist, sc, 24);
+        const int64_t want_b = min((int64_t)s_ns, (int64_t)ceilf(a.first * (float)kq));
+        if (want_b < (int64_t)s_ns) {
+            auto cen = [&](int64_t i) { const uint4 e = reg[i]; return e.x <= uk ? sg_centre_key(e) : 0xFFFFFFFFu; };
+            ck = cta_select_u32(n, (uint32_t)(want_b - 1), cen, hist, sc, 24);
+            uint32_t lt = 0, eq = 0;
+            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+                const uint32_t c = cen(i);
+                lt += c < ck ? 1u : 0u;
+                eq += c == ck ? 1u : 0u;
+            }
+            lt = __reduce_add_sync(0xFFFFFFFFu, lt);
+            eq = __reduce_add_sync(0xFFFFFFFFu, eq);
+            if (lane_id() == 0) { atomicAdd(&s_lt, lt); atomicAdd(&s_eq, eq); }
+            __syncthreads();
+            const uint32_t want = (uint32_t)want_b - s_lt;        // >= 1: members taken at the cut centre
+            if (want < s_eq)
+                slot_cut = cta_select_u32(n, want - 1, [&](int64_t i) { return cen(i) == ck ? reg[i].z : 0xFFFFFFFFu; },
+                                          hist, sc, 24);
+        }
     }
     const int64_t n_pad = (n + 31) / 32 * 32;
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
@@ -556,8 +595,10 @@ __global__ void __launch_bounds__(SG_THREADS) sign_select_kernel(DevIndex ix, Si
         uint4 e = make_uint4(0, 0, 0, 0);
         if (i < n) {
             e = reg[i];
-            inb = all || e.y < uk || (e.y == uk && e.z <= slot_cut);
-            inr = !inb && e.x <= uk;
+            const bool ins = all || e.x <= uk;
+            const uint32_t c = ins ? sg_centre_key(e) : 0xFFFFFFFFu;
+            inb = all || (ins && (c < ck || (c == ck && e.z <= slot_cut)));
+            inr = !inb && ins;
         }
         const uint32_t sb = sg_append(inb, &s_b);
         if (inb) a.clist[off + sb] = ix.ids[e.z];
@@ -574,21 +615,25 @@ __global__ void __launch_bounds__(SG_THREADS) sign_select_kernel(DevIndex ix, Si
     }
 }
 
-// Second round: U' = the largest FP32 upper bound in B; S' = rest with lb <= U'.
+// Second round: U' = the k-th smallest FP32 upper bound of the distances in
+// B (the largest when B holds at most k); S' = rest with lb <= U'.
 __global__ void __launch_bounds__(SG_THREADS) sign_filter_kernel(DevIndex ix, SignSelectArgs a) {
-    __shared__ uint32_t s_u, s_c;
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t sc[2];
+    __shared__ uint32_t s_c;
     const int64_t qi = blockIdx.x;
     const int64_t nb = a.n_b[qi];
     const int64_t nr = a.n_rest[qi];
+    const int64_t kq = a.qp.K(qi);
     const int64_t off = a.qp.coff(qi);
-    if (threadIdx.x == 0) { s_u = 0u; s_c = 0u; }
+    if (threadIdx.x == 0) s_c = 0u;
     __syncthreads();
-    uint32_t mx = 0u;
-    for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) mx = max(mx, f32_key(__fadd_ru(a.cd[off + i], a.cr[off + i])));
-    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-    if (lane_id() == 0) atomicMax(&s_u, mx);
-    __syncthreads();
-    const uint32_t up = s_u;
+    uint32_t up = 0u;
+    if (nb > 0) {
+        const uint32_t r = (uint32_t)(min(nb, kq) - 1);
+        up = cta_select_u32(nb, r, [&](int64_t i) { return f32_key(__fadd_ru(a.cd[off + i], a.cr[off + i])); },
+                            hist, sc, 24);
+    }
     const int64_t n_pad = (nr + 31) / 32 * 32;
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
         const bool take = i < nr && a.rest_key[off + i] <= up;
