@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--nprobe", default=None, help="lists probed; a comma list prints one line per value")
     p.add_argument("--kc-ratio", default="1.4", help="K_c / k; a comma list prints one line per value")
     p.add_argument("--buckets", default="64", help="bucket count m; a comma list prints one line per value")
+    p.add_argument("--collector", default="0",
+                   help="top-K_c collector: 0 the result buffer, 1 lazy linear buffer, 2 binary heap; a comma list "
+                        "prints one line per value")
     p.add_argument("--pair", default="0",
                    help="scan schedule: 1 two queries per CTA (pair form), 0 one; a comma list prints one line per value")
     p.add_argument("--cpu-queries", type=int, default=200, help="oracle sample for cpu_baseline")
@@ -398,6 +401,7 @@ def main():
         index.set(epsilon0=args.epsilon0)
     buckets = [int(v) for v in str(args.buckets).split(",")]
     pairs = [int(v) for v in str(args.pair).split(",")]
+    collectors = [int(v) for v in str(args.collector).split(",")]
     if args.mixed_k:
         index.set(kc_ratio=ratios[0], buckets=buckets[0], pair=pairs[0])
         if scales[0] is not None:
@@ -412,11 +416,12 @@ def main():
                     for scale in scales:
                         for est in ests:
                             for pair in pairs:
-                                index.set(kc_ratio=ratio, buckets=m, pair=pair)
-                                if scale is not None:
-                                    index.set(bound_scale=scale, estimator=est)
-                                measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec,
-                                        ratio, m)
+                                for coll in collectors:
+                                    index.set(kc_ratio=ratio, buckets=m, pair=pair, collector=coll)
+                                    if scale is not None:
+                                        index.set(bound_scale=scale, estimator=est)
+                                    measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec,
+                                            ratio, m)
     index.close()
 
 
@@ -792,6 +797,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
                        "nprobe": nprobe, "kc": None if is_sign else kc,
                        "kc_ratio": ratio, "buckets": m, "rerank": rerank,
                        "scan_schedule": "pair" if index.get("pair") else "one query per CTA",
+                       "collector": ["result buffer", "lazy linear buffer", "binary heap"][int(index.get("collector"))],
                        "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
                        "recall_tie_aware": True, "ground_truth_cpu_spotcheck": gt_check,
                        "l2_flush_between_steps": True, "parallelism": f"replicas x{ws}",

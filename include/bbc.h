@@ -157,6 +157,18 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  their probed lists is streamed once, so a code row serves
  *                  both queries.  0 = one query per CTA.  Applies when "split"
  *                  gives one CTA per query.  Same results either way.  Default 0.
+ *   "collector"    the top-K_c collector of the scan: 0 (default) = the
+ *                  bucket-based result buffer (Section 3.2, Algorithm 1); the
+ *                  baselines it is compared with (Section 4, Exp-3): 1 = a
+ *                  lazily updated linear buffer (objects below the current
+ *                  threshold appended; after each list the threshold becomes
+ *                  the K_c-th smallest buffered estimate and the buffer is
+ *                  compacted), 2 = a binary max-heap of the K_c smallest
+ *                  (estimate, id) in shared memory.  Same candidates with
+ *                  every collector; 1 and 2 run one CTA per query and take
+ *                  8-bit tables with pq_m <= 32 or 4-bit tables with pq_m <= 64
+ *                  (2 also needs the heap in shared memory: K_c up to about
+ *                  18,000), else BBC_ERR_UNSUPPORTED at search time.
  *   "graphs"       1 = bbc_search captures the launch sequence of each call shape
  *                  (pointers, sizes, parameters, stream) into a CUDA graph the
  *                  first time and replays it afterwards (not on the legacy

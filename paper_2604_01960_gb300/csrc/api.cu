@@ -131,18 +131,19 @@ struct bbc_index {
     float first_round = 2.f;                     // sign codes: first re-rank round, a multiple of k
     int split = 0;            // 0 automatic, 1 one CTA per query, G >= 2 CTAs per query
     int pair = 0;             // 1: two queries per CTA (pair form) where supported, 0: one
+    int collector = 0;        // 0 the bucket-based result buffer; 1 lazy linear buffer, 2 binary heap (baselines)
     int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
     bool capturing = false;
     struct GraphKey {
         const void* q; int64_t nq; int k; int nprobe; void* oi; void* od; cudaStream_t st;
         double kc_ratio; int buckets, sample_lists, split, probe_gemm, rerank, prec;
         int64_t rcap;
-        int pair;
+        int pair, collector;
         bool operator<(const GraphKey& o) const {
             return std::tie(q, nq, k, nprobe, oi, od, st, kc_ratio, buckets, sample_lists, split, probe_gemm, rerank,
-                            prec, rcap, pair) <
+                            prec, rcap, pair, collector) <
                    std::tie(o.q, o.nq, o.k, o.nprobe, o.oi, o.od, o.st, o.kc_ratio, o.buckets, o.sample_lists, o.split,
-                            o.probe_gemm, o.rerank, o.prec, o.rcap, o.pair);
+                            o.probe_gemm, o.rerank, o.prec, o.rcap, o.pair, o.collector);
         }
     };
     struct GraphEntry { cudaGraphExec_t exec; int64_t launches; };
@@ -432,7 +433,16 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
         const int64_t slots = 4ll * 2 * d.num_sms;
         if (nc < slots) G = (int)std::min<int64_t>((slots + nc - 1) / nc, std::max(1, p.nprobe));
     }
-    if (G >= 2) {
+    if (ix->collector) {
+        // a baseline collector in place of the result buffer: it writes the candidates itself
+        const uint32_t stage_cap = (uint32_t)((ix->info.max_list_len + 31) / 32 * 32);
+        if (!scan_collect_supported(d, ix->collector, p.nprobe, p.kc, stage_cap))
+            return fail(BBC_ERR_UNSUPPORTED, "collector %d: table shape or K_c %lld not supported", ix->collector,
+                        (long long)p.kc);
+        sa.fuse_select = 1;
+        sa.sel = SelectArgs{region, p.cap, state, p.kc, cand, count, nullptr, qp};
+        CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan_collect(d, nc, sa, ix->collector, stage_cap, st); }));
+    } else if (G >= 2) {
         unsigned int* counters = reinterpret_cast<unsigned int*>(ws + p.off_counters);
         CUDA_TRY(cudaMemsetAsync(state, 0, (size_t)nc * sizeof(bbc_collector_state), st));
         CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan_split(d, nc, sa, G, counters, st); }));
@@ -1234,6 +1244,9 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "profile") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "profile must be 0 or 1");
         ix->profile = (int)v;
+    } else if (k == "collector") {
+        if (v != 0 && v != 1 && v != 2) return fail(BBC_ERR_ARG, "collector must be 0 (result buffer), 1 (lazy) or 2 (heap)");
+        ix->collector = (int)v;
     } else if (k == "pair") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "pair must be 0 (one query per CTA) or 1 (two)");
         ix->pair = (int)v;
@@ -1265,6 +1278,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "first_round") *v = ix->first_round;
     else if (k == "region_cap") *v = (double)ix->region_cap;
     else if (k == "pair") *v = ix->pair;
+    else if (k == "collector") *v = ix->collector;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -1294,7 +1308,7 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     // CUDA graph of the whole launch sequence for this call shape
     bbc_index::GraphKey key{queries, nq, k, nprobe, out_ids, out_dists, st, ix->kc_ratio, ix->buckets,
                             ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8, ix->dev.prec,
-                            ix->region_cap, ix->pair};
+                            ix->region_cap, ix->pair, ix->collector};
     std::lock_guard<std::mutex> lk(ix->graph_mu);
     auto it = ix->graph_cache.find(key);
     if (it == ix->graph_cache.end()) {

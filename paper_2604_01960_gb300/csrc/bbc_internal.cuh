@@ -182,6 +182,13 @@ cudaError_t launch_scan_split(const DevIndex& ix, int64_t nq, const ScanArgs& a,
 bool scan_pair_supported(const DevIndex& ix, int nprobe);
 cudaError_t launch_scan_pair(const DevIndex& ix, int64_t nq, const ScanArgs& a, const int32_t* perm,
                              cudaStream_t st);
+// Baseline collectors in place of the result buffer (the comparison of
+// Section 4, Exp-3), one CTA per query, the K_c candidates written to
+// a.sel.cand / a.sel.cand_count: mode 1 a lazily updated linear buffer, mode
+// 2 a binary max-heap in shared memory (stage_cap >= the longest list).
+bool scan_collect_supported(const DevIndex& ix, int mode, int nprobe, int64_t kc, uint32_t stage_cap);
+cudaError_t launch_scan_collect(const DevIndex& ix, int64_t nq, const ScanArgs& a, int mode, uint32_t stage_cap,
+                                cudaStream_t st);
 // Pairing plan (k_pair.cu): perm[nq] (query of CTA i at 2i and 2i + 1), from
 // the probe lists and the query vectors; scratch holds pair_plan_bytes(nq)
 // bytes, perm included (the last quarter).

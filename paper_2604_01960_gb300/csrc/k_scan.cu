@@ -1244,6 +1244,209 @@ scan_pair_kernel(DevIndex ix, ScanArgs a, const int32_t* __restrict__ perm, int6
     }
 }
 
+// ---------------------------------------------------------------------------
+// Baseline collectors (the comparison of Section 4, Exp-3: a binary heap and
+// a lazily updated linear buffer in place of the bucket-based result buffer),
+// one CTA per query, lists in probe order.  Both return the same candidate
+// set as the result buffer -- the K_c smallest (estimated distance, id) of
+// the scanned objects -- and exist to measure what the collector costs.
+//   LAZY (mode 1): objects with e <= the current threshold are appended to a
+//     linear buffer; after each list, when the buffer holds more than K_c,
+//     the K_c-th smallest buffered e becomes the threshold (a CTA radix
+//     select) and the buffer is compacted to the objects at or below it.
+//   HEAP (mode 2): a binary max-heap of the K_c smallest (e, id) keys in
+//     shared memory; per list, the warps stage the objects that can enter
+//     (heap not full, or e <= the top's e) and one thread inserts them in
+//     order (replace-top and sift-down once full).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void heap_sift_down(unsigned long long* h, uint32_t n, uint32_t i) {
+    const unsigned long long x = h[i];
+    for (;;) {
+        uint32_t c = 2 * i + 1;
+        if (c >= n) break;
+        if (c + 1 < n && h[c + 1] > h[c]) ++c;
+        if (h[c] <= x) break;
+        h[i] = h[c];
+        i = c;
+    }
+    h[i] = x;
+}
+
+__device__ __forceinline__ void heap_sift_up(unsigned long long* h, uint32_t i) {
+    const unsigned long long x = h[i];
+    while (i > 0) {
+        const uint32_t p = (i - 1) / 2;
+        if (h[p] >= x) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i] = x;
+}
+
+template <int M, int BITS, int MODE>
+__global__ void __launch_bounds__(SCAN_THREADS, 1)
+scan_collect_kernel(DevIndex ix, ScanArgs a, uint32_t stage_cap) {
+    using C = ScanCfg<M, BITS>;
+    extern __shared__ uint4 dsm[];
+    uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
+    int4* ldesc = reinterpret_cast<int4*>(lut + C::LUT_WORDS);                         // [nprobe]
+    unsigned long long* heap = reinterpret_cast<unsigned long long*>(ldesc + a.nprobe); // MODE 2: [K_c]
+    unsigned long long* stage = heap + (MODE == 2 ? a.kc : 0);                          // MODE 2: [stage_cap]
+    __shared__ uint32_t hist[256], sc[2];
+    __shared__ uint32_t s_count, s_stage, s_keep, s_heapn, s_over;
+    __shared__ uint32_t s_thr;                 // LAZY: buffer threshold on e
+    __shared__ unsigned long long s_top;      // HEAP: current largest key (max when not full)
+    __shared__ long long s_sq;
+    __shared__ int s_gtot;
+    const int64_t qi = blockIdx.x;
+    const QCtx Q{a.qp.P(qi), a.qp.KC(qi), a.qp.rcap(qi), a.region + a.qp.roff(qi), a.lists + a.qp.poff(qi)};
+    const int tid = threadIdx.x, bs = blockDim.x, nw = bs >> 5;
+    const unsigned ln = lane_id(), lt_mask = (1u << ln) - 1u;
+    const uint32_t cap = (uint32_t)(Q.cap < 0xFFFFFFFFll ? Q.cap : 0xFFFFFFFFll);
+    stage_lut<M, BITS>(a.lut16 + qi * (int64_t)M * C::K, lut);
+    if (tid == 0) { s_count = 0; s_stage = 0; s_heapn = 0; s_over = 0; s_thr = 0xFFFFFFFFu; s_top = ~0ull; }
+    if (warp_id() == 0) {
+        long long nv;
+        const int g = build_layout(ix, Q.lists, Q.P, ldesc, &nv);
+        if (ln == 0) { s_gtot = g; s_sq = nv; }
+    }
+    __syncthreads();
+    const uint32_t lut_s = (uint32_t)__cvta_generic_to_shared(lut);
+    const uint4* codes = reinterpret_cast<const uint4*>(ix.codes) + ln;
+    const uint32_t kc32 = (uint32_t)min(Q.kc, (int64_t)0xFFFFFFFF);
+    for (int j = 0; j < Q.P; ++j) {
+        const int4 dj = ldesc[j];
+        const uint32_t thr = s_thr;
+        const unsigned long long top = s_top;
+        for (int g = dj.x + (int)warp_id(); g < dj.y; g += nw) {
+            const int gb = dj.z + g;
+            uint4 r[C::NCH];
+            const uint4* cp = codes + (size_t)gb * (32 * C::NCH);
+#pragma unroll
+            for (int c = 0; c < C::NCH; ++c) r[c] = __ldg(cp + c * 32);
+            const uint32_t e = adc_lane<M, BITS>(r, 4u * ln, lut_s);
+            const bool valid = (int)ln < dj.w - 32 * g;
+            const uint32_t pos = (uint32_t)gb * 32u + ln;
+            if (MODE == 1) {
+                const bool push = valid && e <= thr;
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, push);
+                if (bal) {
+                    uint32_t base = 0;
+                    if (ln == 0) base = atomicAdd(&s_count, (uint32_t)__popc(bal));
+                    base = __shfl_sync(0xFFFFFFFFu, base, 0) + (uint32_t)__popc(bal & lt_mask);
+                    if (push) {
+                        if (base < cap) Q.region[base] = make_uint2(e, pos);
+                        else atomicOr(ix.status, kStatusRegionOverrun);
+                    }
+                }
+            } else {
+                const bool push = valid && e <= (uint32_t)(top >> 32);
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, push);
+                if (bal) {
+                    uint32_t base = 0;
+                    if (ln == 0) base = atomicAdd(&s_stage, (uint32_t)__popc(bal));
+                    base = __shfl_sync(0xFFFFFFFFu, base, 0) + (uint32_t)__popc(bal & lt_mask);
+                    if (push) {
+                        if (base < stage_cap) stage[base] = ((unsigned long long)e << 32) | ix.ids[pos];
+                        else s_over = 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (MODE == 1) {
+            const uint32_t n = min(s_count, cap);
+            if (n > kc32) {
+                // threshold = the K_c-th smallest buffered e; keep e <= threshold
+                const uint32_t t = cta_select_u32(n, kc32 - 1, [&](int64_t i) { return Q.region[i].x; }, hist, sc, 24);
+                if (tid == 0) { s_keep = 0; s_thr = t; }
+                __syncthreads();
+                for (uint32_t i0 = 0; i0 < n; i0 += (uint32_t)bs) {
+                    const uint32_t i = i0 + (uint32_t)tid;
+                    const uint2 v = i < n ? Q.region[i] : make_uint2(0xFFFFFFFFu, 0u);
+                    const bool keep = i < n && v.x <= t;
+                    __syncthreads();                            // every read of this tile before any write
+                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                    uint32_t base = 0;
+                    if (ln == 0 && bal) base = atomicAdd(&s_keep, (uint32_t)__popc(bal));
+                    base = __shfl_sync(0xFFFFFFFFu, base, 0) + (uint32_t)__popc(bal & lt_mask);
+                    if (keep) Q.region[base] = v;               // base <= i: the tile's own or earlier slots
+                    __syncthreads();
+                }
+                if (tid == 0) s_count = s_keep;
+                __syncthreads();
+            }
+        } else {
+            if (tid == 0) {
+                const uint32_t ns = min(s_stage, stage_cap);
+                uint32_t hn = s_heapn;
+                for (uint32_t i = 0; i < ns; ++i) {
+                    const unsigned long long key = stage[i];
+                    if (hn < kc32) {
+                        heap[hn] = key;
+                        heap_sift_up(heap, hn);
+                        ++hn;
+                    } else if (key < heap[0]) {
+                        heap[0] = key;
+                        heap_sift_down(heap, hn, 0);
+                    }
+                }
+                s_heapn = hn;
+                s_top = hn < kc32 ? ~0ull : heap[0];
+                s_stage = 0;
+            }
+            __syncthreads();
+        }
+    }
+    // ---- the K_c candidates ----
+    uint32_t* cand = a.sel.cand + a.qp.coff(qi);
+    bbc_collector_state* st = a.state + qi;
+    if (MODE == 1) {
+        const uint32_t n = min(s_count, cap);
+        const uint32_t want = min(n, kc32);
+        unsigned long long kth = ~0ull;
+        if (want > 0 && want < n)
+            kth = cta_select_u64(n, want - 1, [&](int64_t i) {
+                const uint2 v = Q.region[i];
+                return ((unsigned long long)v.x << 32) | ix.ids[v.y];
+            }, hist, sc, 56);
+        if (tid == 0) s_keep = 0;
+        __syncthreads();
+        for (uint32_t i0 = 0; i0 < n; i0 += (uint32_t)bs) {
+            const uint32_t i = i0 + (uint32_t)tid;
+            uint32_t id = 0;
+            bool take = false;
+            if (i < n) {
+                const uint2 v = Q.region[i];
+                id = ix.ids[v.y];
+                take = (((unsigned long long)v.x << 32) | id) <= kth;
+            }
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
+            uint32_t base = 0;
+            if (ln == 0 && bal) base = atomicAdd(&s_keep, (uint32_t)__popc(bal));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0) + (uint32_t)__popc(bal & lt_mask);
+            if (take && base < kc32) cand[base] = id;
+        }
+        __syncthreads();
+        if (tid == 0) a.sel.cand_count[qi] = min(s_keep, kc32);
+    } else {
+        const uint32_t hn = s_heapn;
+        for (uint32_t i = tid; i < hn; i += bs) cand[i] = (uint32_t)(heap[i] & 0xFFFFFFFFull);
+        if (tid == 0) {
+            a.sel.cand_count[qi] = hn;
+            if (s_over) atomicOr(ix.status, kStatusRegionOverrun);
+        }
+    }
+    for (int i = tid; i < kMaxBuckets; i += bs) st->hist[i] = 0u;
+    for (int i = tid; i < 256; i += bs) st->map[i] = 0u;
+    if (tid == 0) {
+        st->d_min = 0; st->d_max = 0; st->sh = 0; st->m = 0; st->sample_lists = 0; st->tau = -1;
+        st->sample_size = 0; st->scanned = s_sq; st->pushed = MODE == 1 ? (int64_t)s_count : (int64_t)s_heapn;
+        st->below = 0; st->kc = Q.kc;
+    }
+}
+
 // Largest dynamic shared memory a kernel can take next to its static shared
 // memory (227 KB per block in all).
 template <typename F>
@@ -1337,6 +1540,62 @@ cudaError_t launch_scan_pair(const DevIndex& ix, int64_t nq, const ScanArgs& a, 
         }
     }
     return cudaErrorInvalidValue;
+}
+
+template <int M, int BITS, int MODE>
+static size_t collect_smem(int nprobe, int64_t kc, uint32_t stage_cap) {
+    using C = ScanCfg<M, BITS>;
+    size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)nprobe * sizeof(int4);
+    if (MODE == 2) smem += ((size_t)kc + stage_cap) * 8;
+    return smem;
+}
+
+template <int M, int BITS, int MODE>
+static cudaError_t launch_collect_t(const DevIndex& ix, int64_t nq, const ScanArgs& a, uint32_t stage_cap,
+                                    cudaStream_t st) {
+    const size_t smem = collect_smem<M, BITS, MODE>(a.nprobe, a.kc, stage_cap);
+    static const int lim = max_dyn_smem(scan_collect_kernel<M, BITS, MODE>);   // a property of the compiled kernel
+    cudaError_t e = smem_attr_once((const void*)scan_collect_kernel<M, BITS, MODE>, lim);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)lim) return cudaErrorInvalidValue;
+    scan_collect_kernel<M, BITS, MODE><<<(unsigned)nq, SCAN_THREADS, smem, st>>>(ix, a, stage_cap);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_collect_m(const DevIndex& ix, int64_t nq, const ScanArgs& a, uint32_t stage_cap,
+                                    cudaStream_t st) {
+    if (ix.bits == 8) {
+        switch (ix.M) {
+            case 8: return launch_collect_t<8, 8, MODE>(ix, nq, a, stage_cap, st);
+            case 16: return launch_collect_t<16, 8, MODE>(ix, nq, a, stage_cap, st);
+            case 32: return launch_collect_t<32, 8, MODE>(ix, nq, a, stage_cap, st);
+        }
+    } else if (ix.bits == 4) {
+        switch (ix.M) {
+            case 32: return launch_collect_t<32, 4, MODE>(ix, nq, a, stage_cap, st);
+            case 64: return launch_collect_t<64, 4, MODE>(ix, nq, a, stage_cap, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool scan_collect_supported(const DevIndex& ix, int mode, int nprobe, int64_t kc, uint32_t stage_cap) {
+    if (mode != 1 && mode != 2) return false;
+    int lut_words = 0;
+    if (ix.bits == 8 && (ix.M == 8 || ix.M == 16 || ix.M == 32)) lut_words = 256 * 64;
+    else if (ix.bits == 4 && (ix.M == 32 || ix.M == 64)) lut_words = 16 * (ix.M <= 32 ? 64 : 128);
+    else return false;
+    size_t smem = (size_t)lut_words * 4 + (size_t)nprobe * 16;
+    if (mode == 2) smem += ((size_t)kc + stage_cap) * 8;
+    return smem + 8 * 1024 <= 227 * 1024;
+}
+
+cudaError_t launch_scan_collect(const DevIndex& ix, int64_t nq, const ScanArgs& a, int mode, uint32_t stage_cap,
+                                cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    if (!scan_collect_supported(ix, mode, a.nprobe, a.kc, stage_cap)) return cudaErrorInvalidValue;
+    return mode == 1 ? launch_collect_m<1>(ix, nq, a, stage_cap, st) : launch_collect_m<2>(ix, nq, a, stage_cap, st);
 }
 
 bool scan_supported(int M, int bits) {

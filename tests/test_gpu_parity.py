@@ -584,3 +584,39 @@ def test_pair_form_many_plan_blocks(bbc):
     a = np.sort(np.where(np.arange(kc)[None, :] < c0[:, None], i0, 0xFFFFFFFF), axis=1)
     b = np.sort(np.where(np.arange(kc)[None, :] < c1[:, None], i1, 0xFFFFFFFF), axis=1)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("collector", [1, 2])
+@pytest.mark.parametrize("kind,nprobe,kc", [("tiny", 12, 300), ("sift", 16, 900), ("sift4", 20, 1200),
+                                            ("ragged", 40, 300), ("sift", 64, 12000), ("tiny", 5, 1)])
+def test_baseline_collectors_same_candidates(bbc, oracle_lib, kind, nprobe, kc, collector):
+    """The lazy linear buffer and the binary heap (the collectors the result
+    buffer is compared with) collect exactly the oracle's top-K_c by
+    (estimated distance, id), and the whole search returns the same results."""
+    h, idx, q = dev_index(bbc, kind)
+    bbc.bbc_set_param(h, "collector", collector)
+    try:
+        lists, ids, cnt, state = _collect(bbc, h, idx, q, nprobe, kc)
+    finally:
+        bbc.bbc_set_param(h, "collector", 0)
+    for i in range(len(q)):
+        sel, _ = scanned_set(idx, lists[i])
+        t16 = oracle_lib.lut16(q[i], idx.codebooks, idx.metric)
+        e = oracle_lib.adc(t16, idx.codes[sel], idx.pq_m, idx.pq_bits)
+        ref_ids, _ = oracle_lib.topkc(e, idx.ids[sel], kc, "sort")
+        n = int(cnt[i])
+        assert n == min(kc, len(e))
+        assert np.array_equal(np.sort(ids[i, :n].astype(np.int64)), np.sort(ref_ids)), f"query {i}"
+        assert state[i]["scanned"] == len(e)
+    k = max(1, kc // 2)
+    outs = []
+    for c in (0, collector):
+        bbc.bbc_set_param(h, "collector", c)
+        bbc.bbc_set_param(h, "kc_ratio", kc / k)
+        gi = torch.empty((len(q), k), dtype=torch.int64, device="cuda")
+        gd = torch.empty((len(q), k), dtype=torch.float32, device="cuda")
+        bbc.bbc_search(h, cuda(q), len(q), k, nprobe, gi, gd)
+        sync_ok(bbc, h)
+        outs.append((gi.cpu(), gd.cpu()))
+    bbc.bbc_set_param(h, "collector", 0)
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
