@@ -77,6 +77,8 @@ def lib():
             L.oracle_bucket_collect.argtypes = [vp, vp, vp, i32, i64, i32, i32,
                                                 C.POINTER(Codebook), vp, vp, vp]
             L.oracle_rerank.argtypes = [vp, vp, i32, i32, vp, i64, vp]
+            L.oracle_alg4.restype = i64
+            L.oracle_alg4.argtypes = [vp, vp, vp, i32, i64, i32, i32, vp, vp, vp, vp]
             L.oracle_topk_final.argtypes = [vp, vp, i64, i32, vp, vp]
             L.oracle_bf16_bits.restype = C.c_uint16
             L.oracle_bf16_bits.argtypes = [C.c_float]
@@ -209,6 +211,22 @@ def bucket_collect(e, ids, list_ofs, kc: int, m: int, sample_min: int = 8):
     c = lib().oracle_bucket_collect(_p(e), _p(ids), _p(lo), lo.shape[0] - 1, kc, m, sample_min,
                                     C.byref(cb), _p(counts), _p(oi), _p(oe))
     return oi[:c], oe[:c], cb, counts
+
+
+def alg4(e, ids, list_ofs, kc: int, m: int, sample_min: int = 8):
+    """Algorithm 4 (IVF+PQ with early re-ranking) over lists in probe order.
+
+    Returns (candidate ids ascending by (e, id), early flag per candidate,
+    objects scored early, early-scored objects among the candidates)."""
+    e = np.ascontiguousarray(e, dtype=np.uint32)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    lo = np.ascontiguousarray(list_ofs, dtype=np.int64)
+    oi = np.empty(max(kc, 1), dtype=np.int64)
+    fl = np.zeros(max(kc, 1), dtype=np.uint8)
+    ne, nec = C.c_int64(), C.c_int64()
+    c = lib().oracle_alg4(_p(e), _p(ids), _p(lo), lo.shape[0] - 1, kc, m, sample_min, _p(oi), _p(fl),
+                          C.byref(ne), C.byref(nec))
+    return oi[:c], fl[:c].astype(bool), ne.value, nec.value
 
 
 def rerank(q, vectors, ids, metric="l2"):

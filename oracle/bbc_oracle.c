@@ -25,6 +25,9 @@
  *   oracle_bucket_collect Algorithm 1 (Push, Update, Collect) with the
  *                         sampled equal-width -> equal-depth codebook of
  *                         Section 3.2 and the bucket id of Eq. (remap).
+ *   oracle_alg4           Algorithm 4 (IVF+PQ with early re-ranking) on
+ *                         Algorithm 1's buffer: which objects get their
+ *                         exact distance while their list is scanned.
  *   oracle_rerank         exact distances of the candidates (FP64).
  *   oracle_topk_final     the k smallest exact distances, ascending.
  *   oracle_search         the whole path for a batch of queries.
@@ -521,6 +524,89 @@ int oracle_search(const oracle_ivfpq* ix, const float* queries, int64_t nq, int3
     }
     free(lists); free(lut); free(e); free(sid); free(lofs); free(cand); free(cd); free(cnts);
     return 0;
+}
+
+/* Algorithm 4 (Improved Search Algorithm of IVF+PQ) on the result buffer of
+ * Algorithm 1, lists in probe order:
+ *   1-3. the sample and its codebook as in oracle_bucket_collect (the sampled
+ *        lists' objects enter the buffer with their quantised distances);
+ *   4.   tau_pred = the bucket of the r-th smallest quantised distance of the
+ *        scanned objects, r = ceil(|O_scanned| / |O| * n_cand) (at least 1),
+ *        O the objects of all probed lists;
+ *   5-13 every other list: an object whose bucket a <= tau enters the buffer;
+ *        if also a < tau_pred, its exact distance is computed now (early);
+ *   14.  after each list tau_pred (rule 4) and tau (Update) are refreshed;
+ *   15.  the candidates are Collect's n_cand (Algorithm 1), and the re-rank
+ *        computes the exact distance of those without one.
+ * Reading: the buffer orders objects by their quantised distance (the bucket
+ * ids come from it), and an early exact distance travels with its object, so
+ * the candidates are those of Algorithm 1 and the results those of the plain
+ * re-rank; what changes is when exact distances are computed.  Returns the
+ * number of candidates (written to out_ids, ascending by (e, id)); early_flag
+ * (per candidate, may be NULL) marks the early ones; *n_early = objects
+ * scored early, *n_early_cand = those among the candidates. */
+int64_t oracle_alg4(const uint32_t* e, const int64_t* ids, const int64_t* list_ofs, int32_t nl, int64_t Kc,
+                    int32_t m, int32_t sample_min, int64_t* out_ids, uint8_t* early_flag, int64_t* n_early,
+                    int64_t* n_early_cand) {
+    const int64_t Sq = list_ofs[nl] - list_ofs[0];
+    const int64_t want = Kc < Sq ? Kc : Sq;
+    int32_t ns_lists = sample_min < nl ? sample_min : nl;
+    while (ns_lists < nl && list_ofs[ns_lists] - list_ofs[0] < want) ++ns_lists;
+    const int64_t ns = list_ofs[ns_lists] - list_ofs[0];
+    oracle_codebook cb;
+    memset(&cb, 0, sizeof(cb));
+    oracle_build_codebook(e + list_ofs[0], ns, Kc, m, &cb);
+    int64_t* cnt = (int64_t*)calloc((size_t)m, sizeof(int64_t));
+    uint32_t* seen = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(Sq > 0 ? Sq : 1));
+    uint32_t* sorted = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(Sq > 0 ? Sq : 1));
+    char* early = (char*)calloc((size_t)(Sq > 0 ? Sq : 1), 1);
+    char* in_buf = (char*)calloc((size_t)(Sq > 0 ? Sq : 1), 1);
+    int64_t nseen = 0, ne = 0;
+    int32_t tau = m, tau_pred = m;
+    for (int32_t j = 0; j < nl; ++j) {
+        const int sampled = j < ns_lists;
+        for (int64_t i = list_ofs[j]; i < list_ofs[j + 1]; ++i) {
+            const int32_t a = bucket_of(e[i], &cb);
+            if (a <= tau) {
+                in_buf[i - list_ofs[0]] = 1;
+                cnt[a]++;
+                if (!sampled && a < tau_pred) { early[i - list_ofs[0]] = 1; ++ne; }
+            }
+            seen[nseen++] = e[i];
+        }
+        tau = oracle_update(cnt, m, Kc);
+        if (j + 1 >= ns_lists && nseen > 0) {
+            /* rule 4 on every object scanned so far */
+            int64_t r = (int64_t)ceil((double)nseen / (double)Sq * (double)Kc);
+            if (r < 1) r = 1;
+            if (r > nseen) r = nseen;
+            memcpy(sorted, seen, sizeof(uint32_t) * (size_t)nseen);
+            qsort(sorted, (size_t)nseen, sizeof(uint32_t), cmp_u32);
+            tau_pred = bucket_of(sorted[r - 1], &cb);
+        }
+    }
+    /* Collect: the Kc smallest (e, id) of the buffer (Algorithm 1) */
+    int64_t nb = 0;
+    ukey* all = (ukey*)malloc(sizeof(ukey) * (size_t)(Sq > 0 ? Sq : 1));
+    int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Sq > 0 ? Sq : 1));
+    for (int64_t i = 0; i < Sq; ++i)
+        if (in_buf[i]) { all[nb].e = e[list_ofs[0] + i]; all[nb].id = ids[list_ofs[0] + i]; pos[nb] = i; ++nb; }
+    /* sort by (e, id); ids are unique, so the position follows from the id */
+    qsort(all, (size_t)nb, sizeof(ukey), cmp_ukey);
+    const int64_t nc = nb < Kc ? nb : Kc;
+    int64_t nec = 0;
+    for (int64_t t = 0; t < nc; ++t) {
+        out_ids[t] = all[t].id;
+        int64_t u = 0;                                 /* the object's position among the scanned */
+        while (ids[list_ofs[0] + u] != all[t].id) ++u;
+        const int ee = early[u];
+        if (early_flag) early_flag[t] = (uint8_t)ee;
+        nec += ee;
+    }
+    *n_early = ne;
+    *n_early_cand = nec;
+    free(cnt); free(seen); free(sorted); free(early); free(in_buf); free(all); free(pos);
+    return nc;
 }
 
 /* Exact kNN over all n vectors, FP64. */
