@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--collector", default="0",
                    help="top-K_c collector: 0 the result buffer, 1 lazy linear buffer, 2 binary heap; a comma list "
                         "prints one line per value")
+    p.add_argument("--early-rerank", default="0",
+                   help="Algorithm 4's early re-rank: 1 on, 0 off; a comma list prints one line per value")
     p.add_argument("--pair", default="0",
                    help="scan schedule: 1 two queries per CTA (pair form), 0 one; a comma list prints one line per value")
     p.add_argument("--cpu-queries", type=int, default=200, help="oracle sample for cpu_baseline")
@@ -402,6 +404,7 @@ def main():
     buckets = [int(v) for v in str(args.buckets).split(",")]
     pairs = [int(v) for v in str(args.pair).split(",")]
     collectors = [int(v) for v in str(args.collector).split(",")]
+    earlys = [int(v) for v in str(args.early_rerank).split(",")]
     if args.mixed_k:
         index.set(kc_ratio=ratios[0], buckets=buckets[0], pair=pairs[0])
         if scales[0] is not None:
@@ -417,11 +420,14 @@ def main():
                         for est in ests:
                             for pair in pairs:
                                 for coll in collectors:
-                                    index.set(kc_ratio=ratio, buckets=m, pair=pair, collector=coll)
-                                    if scale is not None:
-                                        index.set(bound_scale=scale, estimator=est)
-                                    measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt, prec,
-                                            ratio, m)
+                                    for early in earlys:
+                                        index.set(kc_ratio=ratio, buckets=m, pair=pair, collector=coll)
+                                        if early != index.get("early_rerank"):
+                                            index.set(early_rerank=early)
+                                        if scale is not None:
+                                            index.set(bound_scale=scale, estimator=est)
+                                        measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt,
+                                                prec, ratio, m)
     index.close()
 
 
@@ -645,10 +651,12 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     is_sign = hasattr(idx, "rotation")
     bbc.bbc_precision_stats(h, reset=True)
     bbc.bbc_bounded_stats(h, reset=True)
+    bbc.bbc_early_stats(h, reset=True)
     step()
     torch.cuda.synchronize()
     bbc.bbc_stream_status(h)
     pstats = bbc.bbc_precision_stats(h, reset=True) if prec else None
+    estats = bbc.bbc_early_stats(h, reset=True) if index.get("early_rerank") else None
     bstats = bbc.bbc_bounded_stats(h, reset=True) if is_sign else None
     nrec = min(nq, args.recall_queries or 1000)
     rec_mean, rec_min, dk = recall_at_k(xt, qd[:nrec], ids[:nrec], k, idx.metric)
@@ -798,6 +806,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
                        "kc_ratio": ratio, "buckets": m, "rerank": rerank,
                        "scan_schedule": "pair" if index.get("pair") else "one query per CTA",
                        "collector": ["result buffer", "lazy linear buffer", "binary heap"][int(index.get("collector"))],
+                       "early_rerank": bool(index.get("early_rerank")),
                        "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
                        "recall_tie_aware": True, "ground_truth_cpu_spotcheck": gt_check,
                        "l2_flush_between_steps": True, "parallelism": f"replicas x{ws}",
@@ -816,6 +825,9 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
                               "bound_scale": index.get("bound_scale"),
                               "bounds": "RaBitQ estimator, probabilistic" if index.get("estimator") else "hard",
                               "epsilon0": index.get("epsilon0") if index.get("estimator") else None}
+        if estats:
+            out["early_rerank"] = {"scored_early_per_query": estats["scored_early"] / nq,
+                                   "used_per_query": estats["used"] / nq, "kc": kc}
         if prec:
             out["precision"] = {"per_step": pstats, "fp32_recheck_frac": pstats["fp32_rechecked"] / max(1, pstats["scored"]),
                                 "fp64_frac": pstats["fp64_scored"] / max(1, pstats["scored"])}

@@ -169,6 +169,22 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  8-bit tables with pq_m <= 32 or 4-bit tables with pq_m <= 64
  *                  (2 also needs the heap in shared memory: K_c up to about
  *                  18,000), else BBC_ERR_UNSUPPORTED at search time.
+ *   "early_rerank" 1 = the early re-ranking of Algorithm 4 (Section 3.3,
+ *                  "Integrating with IVF+PQ"): while a list is scanned, an
+ *                  appended object whose bucket lies below the predicted
+ *                  threshold bucket tau_pred (the bucket of the ceil(f n_cand)-th
+ *                  smallest estimate so far, f the scanned share of the probed
+ *                  objects) gets its exact distance at once, from a copy of
+ *                  the u8 vectors in list order (the code and vector of an
+ *                  object stored alike, read while the list is hot); the
+ *                  re-rank then skips the candidates that have one.  Setting
+ *                  it builds that copy (waits for all work on the device).
+ *                  Needs an L2 index with the exact u8 copy, d a multiple of
+ *                  16 up to 256 and a table of at most 64 KB, else
+ *                  BBC_ERR_UNSUPPORTED; applies with one CTA per query and the
+ *                  result buffer.  Candidates and results are unchanged (the
+ *                  exact distances are the u8 re-rank's, bit for bit); see
+ *                  bbc_early_stats.  Default 0.
  *   "graphs"       1 = bbc_search captures the launch sequence of each call shape
  *                  (pointers, sizes, parameters, stream) into a CUDA graph the
  *                  first time and replays it afterwards (not on the legacy
@@ -381,6 +397,11 @@ int bbc_sign_bounds(bbc_index* ix, const float* queries, int64_t nq, int32_t npr
  * the device): out4[0] objects scanned, [1] objects in S = {lb <= U_k},
  * [2] exact distances computed (both rounds), [3] queries. */
 int bbc_bounded_stats(bbc_index* ix, int64_t* out4, int reset);
+
+/* Running totals of the early re-rank ("early_rerank") since the last reset
+ * (synchronises the device): out2[0] objects given their exact distance
+ * during the scan, [1] candidates whose re-rank used one. */
+int bbc_early_stats(bbc_index* ix, int64_t* out2, int reset);
 
 /* Running totals of the precision re-rank since the last reset (synchronises
  * the device): out4[0] candidates scored from the copy, [1] candidates

@@ -29,7 +29,7 @@ METRICS = {"l2": 0, "ip": 1}
 # Exported symbols declared in include/bbc.h (checked by the ABI test).
 SYMBOLS = ["bbc_index_create", "bbc_index_create_sign", "bbc_index_load", "bbc_index_free", "bbc_index_info", "bbc_set_param",
            "bbc_get_param", "bbc_search", "bbc_search_ex", "bbc_search_host", "bbc_probe_scores", "bbc_probe", "bbc_lut", "bbc_collect", "bbc_collect_static",
-           "bbc_rerank_topk", "bbc_rerank_bounds", "bbc_precision_copy", "bbc_precision_stats", "bbc_sign_bounds", "bbc_bounded_stats", "bbc_autotune", "bbc_serve_start", "bbc_serve_submit", "bbc_serve_poll",
+           "bbc_rerank_topk", "bbc_rerank_bounds", "bbc_precision_copy", "bbc_precision_stats", "bbc_early_stats", "bbc_sign_bounds", "bbc_bounded_stats", "bbc_autotune", "bbc_serve_start", "bbc_serve_submit", "bbc_serve_poll",
            "bbc_serve_stats", "bbc_serve_stop", "bbc_profile_read", "bbc_stream_status", "bbc_last_error", "bbc_version"]
 NUM_STAGES = 9
 STAGES = ["probe_scores", "probe_select", "lut", "scan", "select", "rerank", "topk", "prec_classify",
@@ -111,6 +111,7 @@ def lib():
             L.bbc_index_create_sign.argtypes = [C.POINTER(SignHost), C.c_int, C.POINTER(vp)]
             L.bbc_sign_bounds.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp, vp, vp]
             L.bbc_bounded_stats.argtypes = [vp, vp, C.c_int]
+            L.bbc_early_stats.argtypes = [vp, vp, C.c_int]
             L.bbc_index_free.argtypes = [vp]
             L.bbc_index_info.argtypes = [vp, C.POINTER(IndexInfo)]
             L.bbc_set_param.argtypes = [vp, C.c_char_p, C.c_double]
@@ -312,6 +313,13 @@ def bbc_bounded_stats(handle: int, reset: bool = True) -> dict:
     t = (C.c_int64 * 4)()
     _check(lib().bbc_bounded_stats(handle, t, 1 if reset else 0))
     return {"scanned": t[0], "in_S": t[1], "exact": t[2], "queries": t[3]}
+
+
+def bbc_early_stats(handle: int, reset: bool = True) -> dict:
+    """Totals of the early re-rank since the last reset."""
+    t = (C.c_int64 * 2)()
+    _check(lib().bbc_early_stats(handle, t, 1 if reset else 0))
+    return {"scored_early": t[0], "used": t[1]}
 
 
 def bbc_profile_read(handle: int, reset: bool = True):

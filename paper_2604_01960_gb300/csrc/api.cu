@@ -132,18 +132,23 @@ struct bbc_index {
     int split = 0;            // 0 automatic, 1 one CTA per query, G >= 2 CTAs per query
     int pair = 0;             // 1: two queries per CTA (pair form) where supported, 0: one
     int collector = 0;        // 0 the bucket-based result buffer; 1 lazy linear buffer, 2 binary heap (baselines)
+    int early_rerank = 0;     // 1: Algorithm 4's early re-rank in the scan (exact u8 re-rank, one CTA per query)
+    int64_t nslots = 0;       // code-block slots (32 per block)
+    uint8_t* lo_rows = nullptr;                 // early re-rank: u8 rows in slot order
+    uint32_t* lo_norms = nullptr;               // and their squared norms
+    unsigned long long* early_totals = nullptr; // [2] objects scored early, early distances used
     int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
     bool capturing = false;
     struct GraphKey {
         const void* q; int64_t nq; int k; int nprobe; void* oi; void* od; cudaStream_t st;
         double kc_ratio; int buckets, sample_lists, split, probe_gemm, rerank, prec;
         int64_t rcap;
-        int pair, collector;
+        int pair, collector, early;
         bool operator<(const GraphKey& o) const {
             return std::tie(q, nq, k, nprobe, oi, od, st, kc_ratio, buckets, sample_lists, split, probe_gemm, rerank,
-                            prec, rcap, pair, collector) <
+                            prec, rcap, pair, collector, early) <
                    std::tie(o.q, o.nq, o.k, o.nprobe, o.oi, o.od, o.st, o.kc_ratio, o.buckets, o.sample_lists, o.split,
-                            o.probe_gemm, o.rerank, o.prec, o.rcap, o.pair, o.collector);
+                            o.probe_gemm, o.rerank, o.prec, o.rcap, o.pair, o.collector, o.early);
         }
     };
     struct GraphEntry { cudaGraphExec_t exec; int64_t launches; };
@@ -173,6 +178,9 @@ struct bbc_index {
         cudaFree(lp_meta);
         cudaFree(prec_totals);
         cudaFree(sign_totals);
+        cudaFree(lo_rows);
+        cudaFree(lo_norms);
+        cudaFree(early_totals);
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
@@ -214,7 +222,8 @@ struct Plan {
     int k;
     int64_t cap;
     size_t off_scores, off_probe, off_lut, off_state, off_region, off_cand, off_count, off_cdist,
-        off_q, off_ids, off_dists, off_abf, off_keys, off_params, off_counters, off_prec, off_pair, total;
+        off_q, off_ids, off_dists, off_abf, off_keys, off_params, off_counters, off_prec, off_pair, off_rdist,
+        off_cearly, total;
 };
 
 // The precision re-rank runs when a low-precision copy exists and the exact u8
@@ -222,6 +231,11 @@ struct Plan {
 bool prec_active(const bbc_index* ix) {
     return ix->dev.prec > 0 && ix->dev.vec_lp && !(ix->rerank_u8 && ix->dev.vec_u8);
 }
+
+// Algorithm 4's early re-rank runs with the exact u8 re-rank, one CTA per
+// query and the result buffer (not the precision form, the pair or split
+// scan, or a baseline collector).
+bool early_active(const bbc_index* ix);
 
 // Scratch of the precision re-rank inside a workspace: per candidate slot
 // rho, uncertain ids, final ids / distances, band ids (4 B each) and band
@@ -266,6 +280,11 @@ PrecArgs prec_args_rerank(const bbc_index* ix, char* base, int64_t nq, int64_t s
     return a;
 }
 
+bool early_active(const bbc_index* ix) {
+    return ix->early_rerank && ix->dev.vec_lo && ix->rerank_u8 && ix->dev.vec_u8 && !prec_active(ix) &&
+           ix->collector == 0;
+}
+
 constexpr int64_t kTopkSmemMax = 16384;     // K_c handled by the shared-memory top-k
 constexpr int64_t kMaxChunkQueries = 65535;  // queries per launch (some grids index queries in y)
 
@@ -289,6 +308,9 @@ size_t layout(const bbc_index* ix, const ChunkShape& c, Plan& p) {
     p.off_counters = o; o = align_up(o + 16);
     p.off_prec = o; o = align_up(o + (prec_active(ix) ? prec_bytes(c.nq, c.sum_kc) : 0));
     p.off_pair = o; o = align_up(o + (ix->pair ? pair_plan_bytes(c.nq) : 0));
+    const bool early = ix->early_rerank && ix->dev.vec_lo;
+    p.off_rdist = o; o = align_up(o + (early ? (size_t)c.sum_cap * 4 : 0));
+    p.off_cearly = o; o = align_up(o + (early ? (size_t)c.sum_kc * 4 : 0));
     p.total = o;
     return o;
 }
@@ -457,6 +479,16 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
         // one CTA per query: the selection (S7) runs in the scan's tail
         sa.fuse_select = 1;
         sa.sel = SelectArgs{region, p.cap, state, p.kc, cand, count, nullptr, qp};
+        if (early_active(ix)) {
+            // Algorithm 4: exact distances of the objects below the predicted threshold bucket
+            // are computed in the scan and carried to their candidates
+            sa.early = 1;
+            sa.q = q;
+            sa.rdist = reinterpret_cast<float*>(ws + p.off_rdist);
+            sa.early_totals = ix->early_totals;
+            sa.sel.rdist = sa.rdist;
+            sa.sel.cand_early = reinterpret_cast<float*>(ws + p.off_cearly);
+        }
         CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan(d, nc, sa, st); }));
     }
     if (!sa.fuse_select) {
@@ -467,6 +499,10 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + p.off_keys);
     RerankArgs ra{q, cand, count, p.kc, ix->rerank_u8 && d.vec_u8 != nullptr, cdist, p.k, out_ids,
                   out_dists, p.kc > kTopkSmemMax ? keys : nullptr, qp};
+    if (sa.early) {
+        ra.early = sa.sel.cand_early;
+        ra.early_totals = ix->early_totals;
+    }
     if (prec_active(ix)) {
         // slots of this chunk: sum of K_c (the per-query offsets index into them)
         const int64_t slots = qp.cand_off ? p.chunk_slots : nc * p.kc;
@@ -731,6 +767,61 @@ int search_sign_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_
     return BBC_OK;
 }
 
+// Switches Algorithm 4's early re-rank on (building the slot-ordered u8 copy
+// and its norms on the device, after waiting for all work on it) or off
+// (freeing them).  Cached graphs hold the index's pointers and are dropped.
+int set_early_rerank(bbc_index* ix, int on) {
+    DeviceGuard g(ix->device);
+    const DevIndex& d = ix->dev;
+    if (on) {
+        if (d.quant != BBC_QUANT_PQ || !d.vec_u8 || d.metric != BBC_METRIC_L2 || d.d % 16 || d.d > 256)
+            return fail(BBC_ERR_UNSUPPORTED,
+                        "early_rerank needs an L2 PQ index with the exact u8 copy and d a multiple of 16 up to 256");
+        if (d.bits == 8 ? d.M > 32 : d.M > 64)
+            return fail(BBC_ERR_UNSUPPORTED, "early_rerank needs a table of at most 64 KB (pq_m <= 32 at 8 bits)");
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    {
+        std::lock_guard<std::mutex> lk(ix->graph_mu);
+        for (auto& kv : ix->graph_cache) cudaGraphExecDestroy(kv.second.exec);
+        ix->graph_cache.clear();
+    }
+    if (ix->lo_rows) ix->info.device_bytes -= (int64_t)((size_t)ix->nslots * (d.d + 4));
+    cudaFree(ix->lo_rows);
+    cudaFree(ix->lo_norms);
+    ix->lo_rows = nullptr;
+    ix->lo_norms = nullptr;
+    ix->dev.vec_lo = nullptr;
+    ix->dev.vnorm2 = nullptr;
+    ix->early_rerank = 0;
+    if (!on) return BBC_OK;
+    void* r = nullptr;
+    void* nrm = nullptr;
+    if (cudaMalloc(&r, (size_t)ix->nslots * d.d) != cudaSuccess || cudaMalloc(&nrm, (size_t)ix->nslots * 4) != cudaSuccess) {
+        cudaFree(r);
+        return fail(BBC_ERR_OOM, "early_rerank copy");
+    }
+    if (!ix->early_totals) {
+        void* t = nullptr;
+        if (cudaMalloc(&t, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaFree(r);
+            cudaFree(nrm);
+            return fail(BBC_ERR_OOM, "early_rerank counters");
+        }
+        CUDA_TRY(cudaMemset(t, 0, 2 * sizeof(unsigned long long)));
+        ix->early_totals = static_cast<unsigned long long*>(t);
+    }
+    ix->lo_rows = static_cast<uint8_t*>(r);
+    ix->lo_norms = static_cast<uint32_t*>(nrm);
+    CUDA_TRY(launch_early_copy(d, ix->nslots, ix->lo_rows, ix->lo_norms, 0));
+    CUDA_TRY(cudaDeviceSynchronize());
+    ix->dev.vec_lo = ix->lo_rows;
+    ix->dev.vnorm2 = ix->lo_norms;
+    ix->info.device_bytes += (int64_t)((size_t)ix->nslots * (d.d + 4));
+    ix->early_rerank = 1;
+    return BBC_OK;
+}
+
 int pq_only(const bbc_index* ix, const char* what) {
     if (ix && ix->dev.quant != 0) return fail(BBC_ERR_UNSUPPORTED, "%s: not available on a sign-code index", what);
     return BBC_OK;
@@ -855,6 +946,7 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out) {
         nblocks += (list_len[l] + 31) / 32;
     }
     if (nblocks >= (1ll << 31) / 32) return fail(BBC_ERR_UNSUPPORTED, "too many blocks");
+    ix->nslots = nblocks * 32;
     std::vector<uint8_t> codes((size_t)nblocks * 32 * D.cbp, 0);
     std::vector<uint32_t> ids((size_t)nblocks * 32, kPadId);
     const int cb = D.code_bytes;
@@ -1244,6 +1336,9 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "profile") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "profile must be 0 or 1");
         ix->profile = (int)v;
+    } else if (k == "early_rerank") {
+        if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "early_rerank must be 0 or 1");
+        return set_early_rerank(ix, (int)v);
     } else if (k == "collector") {
         if (v != 0 && v != 1 && v != 2) return fail(BBC_ERR_ARG, "collector must be 0 (result buffer), 1 (lazy) or 2 (heap)");
         ix->collector = (int)v;
@@ -1279,6 +1374,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "region_cap") *v = (double)ix->region_cap;
     else if (k == "pair") *v = ix->pair;
     else if (k == "collector") *v = ix->collector;
+    else if (k == "early_rerank") *v = ix->early_rerank;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -1308,7 +1404,7 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     // CUDA graph of the whole launch sequence for this call shape
     bbc_index::GraphKey key{queries, nq, k, nprobe, out_ids, out_dists, st, ix->kc_ratio, ix->buckets,
                             ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8, ix->dev.prec,
-                            ix->region_cap, ix->pair, ix->collector};
+                            ix->region_cap, ix->pair, ix->collector, ix->early_rerank};
     std::lock_guard<std::mutex> lk(ix->graph_mu);
     auto it = ix->graph_cache.find(key);
     if (it == ix->graph_cache.end()) {
@@ -1798,6 +1894,20 @@ int bbc_precision_stats(bbc_index* ix, int64_t* out4, int reset) {
     CUDA_TRY(cudaMemcpy(t, ix->prec_totals, sizeof(t), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 4; ++i) out4[i] = (int64_t)t[i];
     if (reset) CUDA_TRY(cudaMemset(ix->prec_totals, 0, sizeof(t)));
+    return BBC_OK;
+}
+
+int bbc_early_stats(bbc_index* ix, int64_t* out2, int reset) {
+    if (!ix || !out2) return fail(BBC_ERR_ARG, "null argument");
+    out2[0] = out2[1] = 0;
+    if (!ix->early_totals) return BBC_OK;
+    DeviceGuard g(ix->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    unsigned long long t[2];
+    CUDA_TRY(cudaMemcpy(t, ix->early_totals, sizeof(t), cudaMemcpyDeviceToHost));
+    out2[0] = (int64_t)t[0];
+    out2[1] = (int64_t)t[1];
+    if (reset) CUDA_TRY(cudaMemset(ix->early_totals, 0, sizeof(t)));
     return BBC_OK;
 }
 

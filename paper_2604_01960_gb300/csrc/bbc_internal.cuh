@@ -74,6 +74,10 @@ struct DevIndex {
     const double* crot;        // [nlist][d] P c_l in FP64
     const float* rot;          // [d][d] rotation P, row-major (r = P u)
     double eps_p;              // ||P^T P - I||_F
+    // early re-rank (Algorithm 4): the exact u8 copy in code-block slot order,
+    // so a warp's 32-vector block has its rows contiguous, and ||v||^2 per slot
+    const uint8_t* vec_lo;     // [nblocks * 32][d] or null
+    const uint32_t* vnorm2;    // [nblocks * 32] or null
 };
 
 // Words per LUT row in shared memory: lane t at code slot s reads word t + s
@@ -152,6 +156,8 @@ struct SelectArgs {
     uint2* spill;                 // unused
     QueryParams qp;
     uint32_t tcap = 0;            // set by the fused launch: threshold-bucket keys in shared memory
+    const float* rdist = nullptr; // early re-rank: exact distance per region entry (< 0: none), per roff
+    float* cand_early = nullptr;  // and per candidate, per coff
 };
 struct ScanArgs {
     const uint16_t* lut16;        // [nq][M][K]
@@ -166,6 +172,10 @@ struct ScanArgs {
     QueryParams qp;
     int fuse_select;              // 1: the one-CTA-per-query scan runs S7 in its tail (outputs in sel)
     SelectArgs sel;
+    int early = 0;                // 1: Algorithm 4's early re-rank in the one-CTA-per-query scan
+    const float* q = nullptr;     // [nq][d] queries (the early re-rank's exact distances)
+    float* rdist = nullptr;       // exact distance per region entry (< 0: none), per roff
+    unsigned long long* early_totals = nullptr;   // [2]: objects scored early, early distances used
 };
 // S4-S6: sample + codebook + scan + push/update, one CTA per query (and S7
 // in its tail when fuse_select is set).
@@ -211,10 +221,15 @@ struct RerankArgs {
     float* out_dists;             // per QueryParams::ooff
     unsigned long long* keys;     // per QueryParams::coff, scratch for large top-k
     QueryParams qp;
+    const float* early = nullptr; // per QueryParams::coff: a candidate's exact distance from the scan (< 0: none)
+    unsigned long long* early_totals = nullptr;
 };
 // S8: exact distances of the candidates; S9: k smallest (dist, id), sorted.
 cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
 cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
+// The early re-rank's copy: rows[slot] = vec_u8[ids[slot]] (zero for padding
+// slots), norms[slot] = ||row||^2, for nslots = 32 * blocks slots.
+cudaError_t launch_early_copy(const DevIndex& ix, int64_t nslots, uint8_t* rows, uint32_t* norms, cudaStream_t st);
 
 // S8, precision form: scores from the low-precision copy with a bound rho per
 // candidate, classification against the k-th place, FP32 recheck of the

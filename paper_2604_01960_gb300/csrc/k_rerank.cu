@@ -70,10 +70,13 @@ __device__ __forceinline__ float u8_dist(int qn2, unsigned vv, unsigned qv, int 
 // Rows of a fixed shape (G * CPL 16-byte chunks): G lanes per candidate, each
 // lane CPL consecutive chunks, the query's chunks held in registers, the
 // lane reduction unrolled; four candidates per lane group in flight.
+// early (may be null): per candidate, an exact distance the scan already
+// computed (Algorithm 4's early re-rank; < 0: none); such rows are not read.
 template <typename T, int G, int CPL, bool INT>
 __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restrict__ vec, int d,
                                             const uint32_t* sid, int64_t c0, int64_t c1, float* out,
-                                            const float4* q4, const uint4* qb, int qn2) {
+                                            const float4* q4, const uint4* qb, int qn2,
+                                            const float* early = nullptr, unsigned long long* etot = nullptr) {
     constexpr int PW = 32 / G;
     constexpr int U = 4;
     const int ln = (int)lane_id(), grp = ln / G, gl = ln % G;
@@ -88,6 +91,7 @@ __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restr
     for (int64_t cb = c0 + (int64_t)warp_id() * PW * U; cb < c1; cb += (int64_t)nwarp * PW * U) {
         uint32_t id[U];
         bool live[U];
+        float ev[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t c = cb + (int64_t)u * PW + grp;
@@ -97,6 +101,8 @@ __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restr
                 atomicOr(ix.status, kStatusSelectOverrun);   // never expected
                 live[u] = false;
             }
+            ev[u] = (early && live[u]) ? early[c] : -1.f;
+            if (ev[u] >= 0.f) live[u] = false;              // scored in the scan: no row to read
         }
         uint4 v[U][CPL];
 #pragma unroll
@@ -132,7 +138,14 @@ __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restr
                 dist = ix.metric == BBC_METRIC_L2 ? acc : -acc;
             }
             const int64_t c = cb + (int64_t)u * PW + grp;
-            if (c < c1 && gl == 0) out[c] = dist;
+            if (c < c1 && gl == 0) out[c] = ev[u] >= 0.f ? ev[u] : dist;
+        }
+        if (etot) {
+            unsigned used = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) used += (gl == 0 && ev[u] >= 0.f) ? 1u : 0u;
+            used = __reduce_add_sync(0xFFFFFFFFu, used);
+            if (lane_id() == 0 && used) atomicAdd(etot, (unsigned long long)used);
         }
     }
 }
@@ -184,7 +197,8 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     // the common row shapes: 128-byte integer rows, 512-byte FP32 rows
     if (FAST && sizeof(T) == 1 && intpath && nchunk == 8) {
         rerank_rows<T, 4, 2, true>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
-                                   reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2);
+                                   reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2,
+                                   a.early ? a.early + a.qp.coff(qi) : nullptr, a.early ? a.early_totals + 1 : nullptr);
         return;
     }
     if (FAST && sizeof(T) == 4 && nchunk == 32) {
@@ -295,6 +309,30 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
             if (c < c1 && gl == 0) out[c] = dist[u];
         }
     }
+}
+
+// The early re-rank's slot-ordered copy: one warp per slot copies the u8 row
+// of the slot's vector (zero for padding slots) and sums its squares.
+__global__ void early_copy_kernel(const uint8_t* __restrict__ vec, const uint32_t* __restrict__ ids, int64_t nslots,
+                                  int d, uint8_t* __restrict__ rows, uint32_t* __restrict__ norms) {
+    const int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id();
+    if (slot >= nslots) return;
+    const uint32_t id = ids[slot];
+    uint32_t s2 = 0;
+    for (int i = (int)lane_id(); i < d; i += 32) {
+        const uint8_t v = id == kPadId ? (uint8_t)0 : vec[(int64_t)id * d + i];
+        rows[slot * d + i] = v;
+        s2 += (uint32_t)v * v;
+    }
+    s2 = __reduce_add_sync(0xFFFFFFFFu, s2);
+    if (lane_id() == 0) norms[slot] = s2;
+}
+
+cudaError_t launch_early_copy(const DevIndex& ix, int64_t nslots, uint8_t* rows, uint32_t* norms, cudaStream_t st) {
+    if (nslots <= 0) return cudaSuccess;
+    if (!ix.vec_u8) return cudaErrorInvalidValue;
+    early_copy_kernel<<<(unsigned)((nslots + 7) / 8), 256, 0, st>>>(ix.vec_u8, ix.ids, nslots, ix.d, rows, norms);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st) {

@@ -260,6 +260,7 @@ struct ScanShared {
     uint32_t dmin, dmax;
     uint32_t tau;
     uint32_t etau;      // largest estimate whose bucket is <= tau (the map is monotone)
+    uint32_t eearly;    // early re-rank: estimates below this are scored exactly in the scan
     int sh;
     int nsl;
     int gs;             // layout blocks of the sampled lists
@@ -274,7 +275,40 @@ struct QCtx {
     int64_t cap;
     uint2* region;
     const int32_t* lists;
+    float* rdist;       // early re-rank: exact distance per region entry, or null
 };
+
+// Early re-rank (Algorithm 4): ||q - v||^2 of the object in code-block slot
+// `slot` from the slot-ordered u8 copy, in 32-bit integers (q8: the query's
+// components as bytes; exact for integer data as the u8 re-rank).
+__device__ __forceinline__ float early_dist(const DevIndex& ix, const uint4* q8, uint32_t qn2, uint32_t slot) {
+    const int nc = ix.d >> 4;
+    const uint4* row = reinterpret_cast<const uint4*>(ix.vec_lo + (size_t)slot * ix.d);
+    uint32_t qv = 0;
+    for (int c = 0; c < nc; ++c) {
+        const uint4 v = __ldg(row + c);
+        const uint4 qq = q8[c];
+        qv = __dp4a(v.x, qq.x, qv); qv = __dp4a(v.y, qq.y, qv);
+        qv = __dp4a(v.z, qq.z, qv); qv = __dp4a(v.w, qq.w, qv);
+    }
+    return __uint2float_rn(qn2 + __ldg(ix.vnorm2 + slot) - 2u * qv);
+}
+
+// Early threshold after the objects before layout block g of S_q scanned:
+// tau_pred = the bucket of the ceil(f K_c)-th smallest estimate counted so
+// far (f = 32 g / S_q), and objects with a bucket below it, i.e. with an
+// estimate below the returned bound, are scored early.  Warp-collective.
+template <typename SS>
+__device__ __forceinline__ uint32_t early_bound(const SS& S, int m, int64_t kc, long long scanned) {
+    const long long sq = S.sq > 0 ? S.sq : 1;
+    if (scanned > sq) scanned = sq;
+    long long r = (scanned * (long long)kc + sq - 1) / sq;
+    if (r < 1) r = 1;
+    const uint32_t tp = warp_update_bins(S.bh, S.bmap, m, r);
+    if (tp == 0) return 0u;
+    const uint32_t et = etau_of(S, tp - 1);
+    return et == 0xFFFFFFFFu ? et : et + 1u;
+}
 
 // Push test without the map: buckets are monotone in the bin, so bucket(e) <= t
 // holds exactly for bins 0 .. c-1, c = number of bins whose bucket is <= t,
@@ -394,14 +428,20 @@ __device__ __forceinline__ void stage_lut(const uint16_t* lq, uint32_t* lut) {
 // appends of a chunk take one cursor atomic.
 // HALF = -1: the table holds one query; HALF = 0 / 1: a packed pair table,
 // of which this pass scores query a (low halves) or query b (high halves).
-template <int M, int BITS, bool MAIN, bool GLOBAL, int HALF = -1>
+// EARLY (one CTA per query): Algorithm 4's early re-rank -- an appended
+// object whose estimate is below S.eearly gets its exact distance now, from
+// the slot-ordered u8 copy (q8: the query as bytes, null when it is not
+// integer-valued), in Q.rdist; the other appended objects get -1 there.
+template <int M, int BITS, bool MAIN, bool GLOBAL, int HALF = -1, bool EARLY = false>
 __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& a, const QCtx& Q,
                                             bbc_collector_state* st, int nl, int g0, int g1,
                                             const uint32_t* lut, const int4* ldesc, ScanShared& S,
-                                            uint32_t* cf = nullptr) {
+                                            uint32_t* cf = nullptr, const uint4* q8 = nullptr,
+                                            uint32_t qn2 = 0) {
     using C = ScanCfg<M, BITS>;
     using Pos = typename std::conditional<GLOBAL, unsigned long long, uint32_t>::type;
-    constexpr int CH = C::CHUNK;
+    // the early re-rank's row loads need registers: two blocks per step there
+    constexpr int CH = EARLY && C::CHUNK > 2 ? 2 : C::CHUNK;
     const unsigned ln = lane_id();
     const int nw = blockDim.x >> 5;
     const uint32_t lut_s = (uint32_t)__cvta_generic_to_shared(lut);   // warp-uniform
@@ -433,6 +473,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
         jend = d.w;
     };
     int it = 0;
+    uint32_t nearly = 0;                                      // EARLY: objects this lane scored
     for (int cb = g0 + (int)warp_id() * CH; cb < g1; cb += nw * CH, ++it) {
         const int nb = min(CH, g1 - cb);                      // blocks in this chunk (warp-uniform)
         int gbk[CH];
@@ -452,6 +493,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
             }
         }
         const uint32_t etau = MAIN ? *(volatile uint32_t*)&S.etau : 0u;
+        const uint32_t eearly = (EARLY && MAIN && q8) ? *(volatile uint32_t*)&S.eearly : 0u;
         uint32_t e[CH];
         unsigned bal[CH];
         uint32_t tot = 0;
@@ -479,6 +521,10 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
             mn = __reduce_min_sync(0xFFFFFFFFu, mn);
             if (ln == 0 && mn != 0xFFFFFFFFu) atomicMin(&S.dmin, mn);
         }
+        uint32_t epos[CH];                                    // EARLY: region slot of each appended object
+        uint32_t ebits = 0;                                   // EARLY: bit u: block u's object is scored now
+#pragma unroll
+        for (int u = 0; u < CH; ++u) epos[u] = 0xFFFFFFFFu;
         if (tot) {
             Pos base = 0;
             if (ln == 0) {
@@ -493,12 +539,33 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
             for (int u = 0; u < CH; ++u) {
                 if ((bal[u] >> ln) & 1u) {
                     const Pos pos = base + (Pos)__popc(bal[u] & lt_mask);
-                    if (pos < cap) region[pos] = make_uint2(e[u], (uint32_t)gbk[u] * 32u + ln);
-                    else atomicOr(ix.status, kStatusRegionOverrun);
+                    if (pos < cap) {
+                        region[pos] = make_uint2(e[u], (uint32_t)gbk[u] * 32u + ln);
+                        if (EARLY) {
+                            epos[u] = (uint32_t)pos;
+                            if (e[u] < eearly) ebits |= 1u << u;
+                        }
+                    } else {
+                        atomicOr(ix.status, kStatusRegionOverrun);
+                    }
                     if (MAIN) atomicAdd(&S.bh[bin_of(e[u], dmin, sh)], 1u);
                     else if (!GLOBAL) atomicAdd(&cf[e[u] >> C::SHC], 1u);     // coarse histogram of the sample
                 }
                 base += (Pos)__popc(bal[u]);
+            }
+        }
+        if (EARLY) {
+            // Algorithm 4: the appended objects below the predicted threshold get their exact distance
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (epos[u] != 0xFFFFFFFFu) {
+                    float rd = -1.f;
+                    if ((ebits >> u) & 1u) {
+                        rd = early_dist(ix, q8, qn2, (uint32_t)gbk[u] * 32u + ln);
+                        ++nearly;
+                    }
+                    Q.rdist[epos[u]] = rd;
+                }
             }
         }
         if (MAIN && (it & (kUpdateEvery - 1)) == 0) {
@@ -511,8 +578,17 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                     atomicMin(&S.tau, t);
                     atomicMin(&S.etau, et);
                 }
+                if (EARLY && q8) {
+                    // tau_pred from the fraction of S_q scanned through this chunk
+                    const uint32_t ee = early_bound(S, a.m, Q.kc, 32ll * (cb + CH));
+                    if (ln == 0) S.eearly = ee;
+                }
             }
         }
+    }
+    if (EARLY && a.early_totals) {
+        const uint32_t w = __reduce_add_sync(0xFFFFFFFFu, nearly);
+        if (ln == 0 && w) atomicAdd(&a.early_totals[0], (unsigned long long)w);
     }
 }
 
@@ -662,7 +738,10 @@ __device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int 
     __syncthreads();
 }
 
-template <int M, int BITS>
+// Largest dimension of the early re-rank's in-register query bytes.
+constexpr int kEarlyMaxD = 256;
+
+template <int M, int BITS, bool EARLY = false>
 __global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan_kernel(DevIndex ix, ScanArgs a) {
     using C = ScanCfg<M, BITS>;
     extern __shared__ uint4 dsm[];
@@ -670,13 +749,30 @@ __global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::M
     int4* ldesc = reinterpret_cast<int4*>(lut + C::LUT_WORDS);         // [nprobe]
     __shared__ ScanShared S;
     __shared__ uint32_t cf[2048 > (1 << C::SHC) ? 2048 : (1 << C::SHC)];   // sample histograms
+    __shared__ uint4 sq8[EARLY ? kEarlyMaxD / 16 : 1];                   // EARLY: the query as bytes
+    __shared__ uint32_t s_qn2;
+    __shared__ int s_intq;
     const int64_t qi = blockIdx.x;
-    const QCtx Q{a.qp.P(qi), a.qp.KC(qi), a.qp.rcap(qi), a.region + a.qp.roff(qi), a.lists + a.qp.poff(qi)};
+    const QCtx Q{a.qp.P(qi), a.qp.KC(qi), a.qp.rcap(qi), a.region + a.qp.roff(qi), a.lists + a.qp.poff(qi),
+                 EARLY ? a.rdist + a.qp.roff(qi) : nullptr};
     const int P = Q.P;
     const int tid = threadIdx.x, bs = blockDim.x;
 
     // ---- Phase A: LUT staging and list layout ----
     stage_lut<M, BITS>(a.lut16 + qi * (int64_t)M * C::K, lut);
+    if (EARLY) {
+        // the query's components as bytes when they are all integers in [0, 255]
+        if (tid == 0) { s_qn2 = 0u; s_intq = 1; S.eearly = 0u; }
+        __syncthreads();
+        uint8_t* qb = reinterpret_cast<uint8_t*>(sq8);
+        for (int i = tid; i < ix.d; i += bs) {
+            const float v = a.q[qi * ix.d + i];
+            const bool ok = v >= 0.f && v <= 255.f && v == floorf(v);
+            if (!ok) s_intq = 0;
+            qb[i] = ok ? (uint8_t)v : 0;
+            if (ok) atomicAdd(&s_qn2, (uint32_t)v * (uint32_t)v);
+        }
+    }
     for (int i = tid; i < 256; i += bs) S.bh[i] = 0;
     for (int i = tid; i < 2048; i += bs) cf[i] = 0;
     if (tid == 0) {
@@ -720,14 +816,25 @@ __global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::M
 
     // ---- Phase B: sample ----
     const int gs = S.gs;
-    scan_blocks<M, BITS, false, false>(ix, a, Q, a.state + qi, P, 0, gs, lut, ldesc, S, cf);
+    const uint4* q8 = (EARLY && s_intq) ? sq8 : nullptr;
+    scan_blocks<M, BITS, false, false, -1, EARLY>(ix, a, Q, a.state + qi, P, 0, gs, lut, ldesc, S, cf, q8,
+                                                   s_qn2);
     __syncthreads();
 
     // ---- Phase C: codebook ----
     const int64_t ns = (int64_t)min((long long)S.count, (long long)Q.cap);
     build_codebook_hist(Q.region, ns, Q.kc, a.m, S, cf, C::SHC);
+    if (EARLY && q8) {
+        // Algorithm 4: the first predicted threshold from the sample's share of S_q
+        if (warp_id() == 0) {
+            const uint32_t ee = early_bound(S, a.m, Q.kc, (long long)ns);
+            if (lane_id() == 0) S.eearly = ee;
+        }
+        __syncthreads();
+    }
     // ---- Phase D: main scan ----
-    scan_blocks<M, BITS, true, false>(ix, a, Q, a.state + qi, P, gs, S.gtot, lut, ldesc, S);
+    scan_blocks<M, BITS, true, false, -1, EARLY>(ix, a, Q, a.state + qi, P, gs, S.gtot, lut, ldesc, S, nullptr, q8,
+                                                  s_qn2);
     __syncthreads();
 
     // ---- state out ----
@@ -1491,6 +1598,20 @@ static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs&
     if (a.fuse_select) {
         smem = std::max(smem, kFusedSelectKeys * 8);
         a.sel.tcap = (uint32_t)(smem / 8);
+    }
+    if (a.early) {
+        // Algorithm 4's early re-rank: tables of up to 64 KB (8-bit, M <= 32; 4-bit, M <= 64), d <= 256
+        if constexpr (C::LUT_WORDS * 4 <= 64 * 1024 && M <= 64) {
+            if (ix.d > kEarlyMaxD || ix.d % 16 || !ix.vec_lo || !a.rdist || !a.q) return cudaErrorInvalidValue;
+            static const int lim_e = max_dyn_smem(scan_kernel<M, BITS, true>);
+            cudaError_t e = smem_attr_once((const void*)scan_kernel<M, BITS, true>, lim_e);
+            if (e != cudaSuccess) return e;
+            if (smem > (size_t)lim_e) return cudaErrorInvalidValue;
+            scan_kernel<M, BITS, true><<<(unsigned)nq, C::THREADS, smem, st>>>(ix, a);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
     }
     static const int lim = max_dyn_smem(scan_kernel<M, BITS>);   // a property of the compiled kernel
     cudaError_t e = smem_attr_once((const void*)scan_kernel<M, BITS>, lim);

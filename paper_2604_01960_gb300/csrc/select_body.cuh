@@ -52,6 +52,9 @@ static __device__ void select_query(const DevIndex& ix, const SelectArgs& a, int
     const int64_t n = st.pushed < cap ? st.pushed : cap;
     const uint2* region = a.region + a.qp.roff(qi);
     uint32_t* cand = a.cand + a.qp.coff(qi);
+    // early re-rank: carry each candidate's exact distance from the scan (-1: none)
+    float* cearly = a.cand_early ? a.cand_early + a.qp.coff(qi) : nullptr;
+    const float* rdist = a.rdist ? a.rdist + a.qp.roff(qi) : nullptr;
     for (int i = tid; i < 256; i += bs) map[i] = st.map[i];
     if (warp_id() == 0) {
         // tau* and the count below it
@@ -86,7 +89,10 @@ static __device__ void select_query(const DevIndex& ix, const SelectArgs& a, int
     const unsigned lt_mask = (1u << ln) - 1u;
     if (tau >= m) {
         // fewer than K_c objects: all appended objects are candidates
-        for (int64_t i = tid; i < n && i < kc; i += bs) cand[i] = ix.ids[region[i].y];
+        for (int64_t i = tid; i < n && i < kc; i += bs) {
+            cand[i] = ix.ids[region[i].y];
+            if (cearly) cearly[i] = rdist[i];
+        }
         if (tid == 0) {
             a.cand_count[qi] = n < kc ? n : kc;
             st.tau = tau;
@@ -131,7 +137,10 @@ static __device__ void select_query(const DevIndex& ix, const SelectArgs& a, int
                 if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 const uint32_t pos = base + __popc(bal & lt_mask);
-                if (take && (int64_t)pos < kc) cand[pos] = idv[u];
+                if (take && (int64_t)pos < kc) {
+                    cand[pos] = idv[u];
+                    if (cearly) cearly[pos] = rdist[i0 + (int64_t)u * bs + tid];
+                }
             }
             if (in_smem && b[u] == (uint32_t)tau) {
                 const uint32_t p = atomicAdd(&s_t, 1u);
@@ -179,7 +188,10 @@ static __device__ void select_query(const DevIndex& ix, const SelectArgs& a, int
                 if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 const uint32_t pos = base + __popc(bal & lt_mask);
-                if (take && (int64_t)pos < kc) cand[pos] = (uint32_t)(tkeys[i] & 0xFFFFFFFFu);
+                if (take && (int64_t)pos < kc) {
+                    cand[pos] = (uint32_t)(tkeys[i] & 0xFFFFFFFFu);
+                    if (cearly) cearly[pos] = -1.f;             // the region slot is not kept here
+                }
             }
         }
     } else {
@@ -205,7 +217,10 @@ static __device__ void select_query(const DevIndex& ix, const SelectArgs& a, int
                 if (ln == 0) base = atomicAdd(&s_out, (uint32_t)__popc(bal));
                 base = __shfl_sync(0xFFFFFFFFu, base, 0);
                 const uint32_t pos = base + __popc(bal & lt_mask);
-                if (take && (int64_t)pos < kc) cand[pos] = id;
+                if (take && (int64_t)pos < kc) {
+                    cand[pos] = id;
+                    if (cearly) cearly[pos] = rdist[i];
+                }
             }
         }
     }

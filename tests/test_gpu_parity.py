@@ -620,3 +620,43 @@ def test_baseline_collectors_same_candidates(bbc, oracle_lib, kind, nprobe, kc, 
         outs.append((gi.cpu(), gd.cpu()))
     bbc.bbc_set_param(h, "collector", 0)
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("k,nprobe,ratio", [(500, 16, 1.5), (4000, 64, 1.0), (60, 3, 2.0)])
+def test_early_rerank_same_results(bbc, oracle_lib, k, nprobe, ratio):
+    """Algorithm 4's early re-rank computes some candidates' exact distances
+    during the scan; candidates and results stay the oracle's, bit for bit
+    (integer data), and the re-rank uses early distances it was given."""
+    h, idx, q = dev_index(bbc, "sift")
+    qs = q.copy()
+    qs[1] += 0.5                                         # a fractional query: nothing scored early for it
+    nq = len(qs)
+    bbc.bbc_set_param(h, "kc_ratio", ratio)
+    bbc.bbc_set_param(h, "split", 1)
+    outs = []
+    try:
+        for early in (0, 1):
+            bbc.bbc_set_param(h, "early_rerank", early)
+            bbc.bbc_early_stats(h, reset=True)
+            gi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+            gd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+            bbc.bbc_search(h, cuda(qs), nq, k, nprobe, gi, gd)
+            sync_ok(bbc, h)
+            outs.append((gi.cpu().numpy(), gd.cpu().numpy(), bbc.bbc_early_stats(h, reset=True)))
+    finally:
+        bbc.bbc_set_param(h, "early_rerank", 0)
+        bbc.bbc_set_param(h, "split", 0)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    st = outs[1][2]
+    kc = max(k, int(np.ceil(ratio * k - 1e-9)))
+    assert 0 < st["used"] <= st["scored_early"] and st["used"] <= nq * kc
+    oi, od = oracle_lib.search(idx, qs, k, nprobe, kc, "sort")
+    for i in range(nq):
+        _check_topk(oracle_lib, idx, qs[i], outs[1][0][i], outs[1][1][i], oi[i], od[i], i != 1)
+
+
+def test_early_rerank_refused_where_it_does_not_apply(bbc):
+    h, idx, q = dev_index(bbc, "tiny")                   # FP32 data: no exact u8 copy
+    with pytest.raises(bbc.BBCError) as ei:
+        bbc.bbc_set_param(h, "early_rerank", 1)
+    assert ei.value.code == -9
