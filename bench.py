@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 
 METRIC = "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ)"
 METRICS = {"sift": METRIC, "sift4": "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ 64x4)",
+           "sift_iid": "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ, i.i.d. mixture)",
            "gist": "QPS at recall@k>=0.95 (k=10k, 1Mx960 IVF + 1-bit sign codes, bounded re-rank)",
            "embed": "QPS at recall@k>=0.95 (k=50k, 10Mx768 IVF-PQ, inner product)",
            "tiny": "QPS at recall@k>=0.95 (k=1k, 100kx128 IVF-PQ)"}

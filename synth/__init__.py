@@ -15,6 +15,7 @@ from .data import (  # noqa: F401
     make_workload,
     gaussian_mixture_tiny,
     sift_shaped,
+    sift_iid_mixture,
     gist_shaped,
     embedding_shaped,
 )

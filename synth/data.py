@@ -85,6 +85,31 @@ def sift_shaped(n: int, nq: int, d: int = 128, n_centers: int = 10000, rank: int
     return draw(n, np.random.default_rng(seed + 1000)), draw(nq, np.random.default_rng(qseed))
 
 
+def sift_iid_mixture(n: int, nq: int, d: int = 128, n_centers: int = 10000, center_std: float = 40.0,
+                     point_std: float = 20.0, seed: int = SEED_DATA,
+                     qseed: int = SEED_QUERIES) -> Tuple[np.ndarray, np.ndarray]:
+    """Integer components in [0, 255] from a full-dimensional mixture: 10,000
+    centers ~ N(128, center_std^2) per component, points = center +
+    N(0, point_std^2) per component, rounded and clipped to [0, 255].  Kept
+    beside ``sift_shaped`` to show what an i.i.d. mixture does to IVF recall
+    at large k (its neighbourhoods spread over the whole space)."""
+    rc = np.random.default_rng(seed)
+    centers = (128.0 + center_std * rc.standard_normal((n_centers, d))).astype(np.float32)
+
+    def draw(m, rng, chunk=1 << 18):
+        out = np.empty((m, d), dtype=np.float32)
+        lab = rng.integers(0, n_centers, size=m)
+        for s in range(0, m, chunk):
+            e = min(m, s + chunk)
+            x = centers[lab[s:e]] + point_std * rng.standard_normal((e - s, d), dtype=np.float32)
+            np.rint(x, out=x)
+            np.clip(x, 0.0, 255.0, out=x)
+            out[s:e] = x
+        return out
+
+    return draw(n, np.random.default_rng(seed + 1000)), draw(nq, np.random.default_rng(qseed))
+
+
 def gist_shaped(n: int, nq: int, d: int = 960, n_centers: int = 4096,
                 seed: int = SEED_DATA, qseed: int = SEED_QUERIES) -> Tuple[np.ndarray, np.ndarray]:
     """Non-negative anisotropic mixture: per-dimension variance lambda_i ~ i^-0.5.
@@ -149,6 +174,9 @@ WORKLOADS = {
     # 1M x 128 integer components, 1,024 lists, PQ 32 x 8 bit, k = 10,000.
     "sift": Workload("ivfpq-sift-1m-d128", 1_000_000, 128, 1024, "l2", "pq", 32, 8,
                      10_000, 10_000, 256, sift_shaped),
+    # 1M x 128 integer components from the i.i.d. mixture (10,000 centers), same index shape.
+    "sift_iid": Workload("ivfpq-siftiid-1m-d128", 1_000_000, 128, 1024, "l2", "pq", 32, 8,
+                         10_000, 10_000, 256, sift_iid_mixture),
     # Same data, PQ 64 x 4 bit.
     "sift4": Workload("ivfpq4-sift-1m-d128", 1_000_000, 128, 1024, "l2", "pq", 64, 4,
                       10_000, 10_000, 256, sift_shaped),
