@@ -72,7 +72,7 @@ __device__ __forceinline__ float u8_dist(int qn2, unsigned vv, unsigned qv, int 
 // lane reduction unrolled; four candidates per lane group in flight.
 // early (may be null): per candidate, an exact distance the scan already
 // computed (Algorithm 4's early re-rank; < 0: none); such rows are not read.
-template <typename T, int G, int CPL, bool INT>
+template <typename T, int G, int CPL, bool INT, bool EARLY = false>
 __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restrict__ vec, int d,
                                             const uint32_t* sid, int64_t c0, int64_t c1, float* out,
                                             const float4* q4, const uint4* qb, int qn2,
@@ -101,8 +101,8 @@ __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restr
                 atomicOr(ix.status, kStatusSelectOverrun);   // never expected
                 live[u] = false;
             }
-            ev[u] = (early && live[u]) ? early[c] : -1.f;
-            if (ev[u] >= 0.f) live[u] = false;              // scored in the scan: no row to read
+            ev[u] = (EARLY && live[u]) ? early[c] : -1.f;
+            if (EARLY && ev[u] >= 0.f) live[u] = false;     // scored in the scan: no row to read
         }
         uint4 v[U][CPL];
 #pragma unroll
@@ -138,9 +138,9 @@ __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restr
                 dist = ix.metric == BBC_METRIC_L2 ? acc : -acc;
             }
             const int64_t c = cb + (int64_t)u * PW + grp;
-            if (c < c1 && gl == 0) out[c] = ev[u] >= 0.f ? ev[u] : dist;
+            if (c < c1 && gl == 0) out[c] = (EARLY && ev[u] >= 0.f) ? ev[u] : dist;
         }
-        if (etot) {
+        if (EARLY && etot) {
             unsigned used = 0;
 #pragma unroll
             for (int u = 0; u < U; ++u) used += (gl == 0 && ev[u] >= 0.f) ? 1u : 0u;
@@ -196,9 +196,13 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     const int64_t cf1 = min(cf0 + RR_CAND_PER_CTA, cnt);
     // the common row shapes: 128-byte integer rows, 512-byte FP32 rows
     if (FAST && sizeof(T) == 1 && intpath && nchunk == 8) {
-        rerank_rows<T, 4, 2, true>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
-                                   reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2,
-                                   a.early ? a.early + a.qp.coff(qi) : nullptr, a.early ? a.early_totals + 1 : nullptr);
+        if (a.early)
+            rerank_rows<T, 4, 2, true, true>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
+                                             reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8),
+                                             qn2, a.early + a.qp.coff(qi), a.early_totals ? a.early_totals + 1 : nullptr);
+        else
+            rerank_rows<T, 4, 2, true>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
+                                       reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2);
         return;
     }
     if (FAST && sizeof(T) == 4 && nchunk == 32) {
