@@ -45,7 +45,8 @@ class _Index(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("nlist", C.c_int32), ("metric", C.c_int32),
                 ("M", C.c_int32), ("bits", C.c_int32),
                 ("centroids", C.c_void_p), ("list_offsets", C.c_void_p), ("ids", C.c_void_p),
-                ("codes", C.c_void_p), ("books", C.c_void_p), ("vectors", C.c_void_p)]
+                ("codes", C.c_void_p), ("books", C.c_void_p), ("vectors", C.c_void_p),
+                ("residual", C.c_int32)]
 
 
 class Codebook(C.Structure):
@@ -67,6 +68,16 @@ def lib():
             L.oracle_lut_f32.argtypes = [vp, vp, i32, i32, i32, i32, vp]
             L.oracle_lut16.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp]
             L.oracle_adc.argtypes = [vp, vp, i64, i32, i32, vp]
+            L.oracle_lut16_scale.restype = C.c_float
+            L.oracle_lut16_scale.argtypes = [vp, vp, i32, i32, i32, i32, vp]
+            L.oracle_resid_a.restype = C.c_float
+            L.oracle_resid_a.argtypes = [vp, vp, i32, i32]
+            L.oracle_resid_base.restype = i32
+            L.oracle_resid_base.argtypes = [C.c_float, C.c_float]
+            L.oracle_resid_w.restype = i32
+            L.oracle_resid_w.argtypes = [C.c_float, C.c_float]
+            L.oracle_resid_v.argtypes = [vp, vp, i64, vp, i32, i32, i32, i32, vp]
+            L.oracle_adc_resid.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, i32, i32, C.c_float, vp]
             for f in (L.oracle_topkc_sort, L.oracle_topkc_heap):
                 f.restype = i64
                 f.argtypes = [vp, vp, i64, i64, vp, vp]
@@ -171,6 +182,58 @@ def adc(table16, codes, M: int, bits: int):
     return out
 
 
+def lut16_scale(q, books, metric="l2"):
+    """The uint16 table's scale inv (integer units per unit of distance) and
+    sum_m lo_m, the offsets the table drops."""
+    q, b = _f32(q), _f32(books)
+    M, K, ds = b.shape
+    lo = C.c_double(0.0)
+    inv = lib().oracle_lut16_scale(_p(q), _p(b), M * ds, M, int(np.log2(K)), _metric(metric), C.byref(lo))
+    return float(np.float32(inv)), lo.value
+
+
+def resid_a(q, c, metric="l2") -> float:
+    """Residual IVF-PQ: the per-(query, list) term A_ql in FP32
+    (||c||^2 - 2 <q, c> for L2, -<q, c> for IP)."""
+    q, c = _f32(q), _f32(c)
+    return float(np.float32(lib().oracle_resid_a(_p(q), _p(c), c.shape[0], _metric(metric))))
+
+
+def resid_base(a: float, inv: float) -> int:
+    """2^30 + rint(clamp(a * inv, +-2^29)) in the table's integer units."""
+    return int(lib().oracle_resid_base(C.c_float(a), C.c_float(inv)))
+
+
+def resid_w(v: float, inv: float) -> int:
+    """rint(clamp(v * inv, +-2^28)) in the table's integer units."""
+    return int(lib().oracle_resid_w(C.c_float(v), C.c_float(inv)))
+
+
+def resid_v(c, codes, books, metric="l2"):
+    """Residual IVF-PQ: the per-object term V_o = 2 <c, y_o> (L2; 0 for IP) of
+    each code row of a list with centroid c, in FP32."""
+    c, b = _f32(c), _f32(books)
+    M, K, ds = b.shape
+    cr = np.ascontiguousarray(codes, dtype=np.uint8)
+    out = np.empty(cr.shape[0], dtype=np.float32)
+    lib().oracle_resid_v(_p(c), _p(cr), cr.shape[0], _p(b), M * ds, M, int(np.log2(K)), _metric(metric),
+                         _p(out))
+    return out
+
+
+def adc_resid(table16, codes, q, c, books, inv: float, metric="l2"):
+    """Residual IVF-PQ keys of one list's code rows (the table sums plus the
+    per-list and per-object terms, integer units)."""
+    t = np.ascontiguousarray(table16, dtype=np.uint16)
+    cr = np.ascontiguousarray(codes, dtype=np.uint8)
+    q, c, b = _f32(q), _f32(c), _f32(books)
+    M, K, ds = b.shape
+    out = np.empty(cr.shape[0], dtype=np.uint32)
+    lib().oracle_adc_resid(_p(t), _p(cr), cr.shape[0], M, int(np.log2(K)), _p(q), _p(c), _p(b), M * ds,
+                           _metric(metric), C.c_float(inv), _p(out))
+    return out
+
+
 def topkc(e, ids, kc: int, how: str = "sort"):
     """The kc smallest (e, id), ascending; ``how`` = "sort" or "heap"."""
     e = np.ascontiguousarray(e, dtype=np.uint32)
@@ -270,7 +333,8 @@ def search(index, queries, k: int, nprobe: int, kc: int, collector: str = "sort"
     ix = _Index(index.n, index.d, index.nlist, _metric(index.metric), index.pq_m, index.pq_bits,
                 arr(index.centroids, np.float32), arr(index.list_offsets, np.int64),
                 arr(index.ids, np.int64), arr(index.codes, np.uint8),
-                arr(index.codebooks, np.float32), arr(index.vectors, np.float32))
+                arr(index.codebooks, np.float32), arr(index.vectors, np.float32),
+                1 if getattr(index, "residual", False) else 0)
     nq = q.shape[0]
     oi = np.empty((nq, k), dtype=np.int64)
     od = np.empty((nq, k), dtype=np.float64)

@@ -18,6 +18,11 @@
  *                         then the uint16 integer quantisation of the table.
  *   oracle_adc            step (2): estimated distance = sum over sub-spaces
  *                         of the table entry picked by the code.
+ *   oracle_lut16_scale, oracle_resid_a/_base/_w/_v, oracle_adc_resid
+ *                         the same step when the PQ codes quantise the
+ *                         residual o - c_l of each list's objects (residual
+ *                         IVF-PQ): the table plus a per-(query, list) and a
+ *                         per-object term, in the table's integer units.
  *   oracle_topkc_sort     the n_cand candidates by estimated distance
  *                         (Section 2, unbounded methods), by a full sort.
  *   oracle_topkc_heap     the same set through a binary max-heap collector,
@@ -173,12 +178,8 @@ void oracle_lut_f32(const float* q, const float* books, int32_t d, int32_t M, in
 /* uint16 table: per sub-space offset lo_m = min_j L[m][j]; one scale for the
  * query, inv = 65535 / span with span = max_m (max_j L[m][j] - lo_m);
  * entry = min(65535, floor((L - lo_m) * inv + 0.5)).  span == 0 gives zeros. */
-void oracle_lut16(const float* q, const float* books, int32_t d, int32_t M, int32_t bits,
-                  int32_t metric, uint16_t* lut16, float* lut_f32_out) {
-    const int32_t K = 1 << bits;
-    float* lut = (float*)malloc(sizeof(float) * (size_t)M * K);
-    float* lo = (float*)malloc(sizeof(float) * (size_t)M);
-    oracle_lut_f32(q, books, d, M, bits, metric, lut);
+/* lo_m and the query's scale inv of the uint16 table from the FP32 table. */
+static float lut16_offsets(const float* lut, int32_t M, int32_t K, float* lo) {
     float span = 0.0f;
     for (int32_t m = 0; m < M; ++m) {
         float mn = lut[(size_t)m * K], mx = mn;
@@ -192,6 +193,17 @@ void oracle_lut16(const float* q, const float* books, int32_t d, int32_t M, int3
         if (w > span) span = w;
     }
     float inv = span > 0.0f ? 65535.0f / span : 0.0f;
+    if (!(inv <= FLT_MAX)) inv = 0.0f;
+    return inv;
+}
+
+void oracle_lut16(const float* q, const float* books, int32_t d, int32_t M, int32_t bits,
+                  int32_t metric, uint16_t* lut16, float* lut_f32_out) {
+    const int32_t K = 1 << bits;
+    float* lut = (float*)malloc(sizeof(float) * (size_t)M * K);
+    float* lo = (float*)malloc(sizeof(float) * (size_t)M);
+    oracle_lut_f32(q, books, d, M, bits, metric, lut);
+    const float inv = lut16_offsets(lut, M, K, lo);
     for (int32_t m = 0; m < M; ++m) {
         for (int32_t j = 0; j < K; ++j) {
             float t = lut[(size_t)m * K + j] - lo[m];
@@ -224,6 +236,99 @@ void oracle_adc(const uint16_t* lut16, const uint8_t* codes, int64_t n, int32_t 
         for (int32_t m = 0; m < M; ++m) e += lut16[(size_t)m * K + code_of(row, m, bits)];
         out_e[i] = e;
     }
+}
+
+/* The query's table scale inv (integer units per unit of distance) and the
+ * per-sub-space offsets' sum, sum_m lo_m (FP64 sum of the FP32 offsets). */
+float oracle_lut16_scale(const float* q, const float* books, int32_t d, int32_t M, int32_t bits,
+                         int32_t metric, double* lo_sum) {
+    const int32_t K = 1 << bits;
+    float* lut = (float*)malloc(sizeof(float) * (size_t)M * K);
+    float* lo = (float*)malloc(sizeof(float) * (size_t)M);
+    oracle_lut_f32(q, books, d, M, bits, metric, lut);
+    const float inv = lut16_offsets(lut, M, K, lo);
+    if (lo_sum) {
+        double s = 0.0;
+        for (int32_t m = 0; m < M; ++m) s += (double)lo[m];
+        *lo_sum = s;
+    }
+    free(lut);
+    free(lo);
+    return inv;
+}
+
+/* ------------------------------------------------------------------ */
+/* Residual IVF-PQ (Section 2 "Quantization", with the codes of o - c_l) */
+/* ------------------------------------------------------------------ */
+/* An object o of list l is coded by the PQ code of its residual o - c_l;
+ * y = the code's reconstruction (codeword m of sub-space m in dimensions
+ * m*d/M ..).  Its estimated distance splits into the query's table, a
+ * per-(query, list) term and a per-object term:
+ *   L2  ||q - c_l - y||^2 = ||q - y||^2 + (||c_l||^2 - 2 <q, c_l>) + 2 <c_l, y>
+ *                        = sum_m L[m][code_m] + A_ql + V_o;
+ *   IP  -<q, c_l + y>     = sum_m L[m][code_m] + A_ql,  A_ql = -<q, c_l>, V_o = 0;
+ * L the query's table of oracle_lut_f32 (the same formula as for plain PQ).
+ * In the uint16 table's integer units (scale inv) the object's key is
+ *   key = sum_m LUT16[m][code_m] + base_ql + w_o,
+ *   base_ql = 2^30 + rint(clamp(A_ql * inv, -2^29, 2^29)),
+ *   w_o     = rint(clamp(V_o * inv, -2^28, 2^28)),
+ * i.e. (key - 2^30) / inv ~ the estimated distance minus sum_m lo_m; 2^30
+ * keeps keys positive, the clamps keep them below 2^31 (reached only when the
+ * table's span is tiny against the centroid terms).  A_ql and V_o are
+ * evaluated in FP32 with fused multiply-adds over ascending dimension, the
+ * precision in which the keys -- and so the candidate set -- are decided:
+ *   A_ql: s = sum_i q_i c_i, n = sum_i c_i c_i (each a chain of fmaf from 0),
+ *         A = fmaf(-2, s, n) (L2) or -s (IP);
+ *   V_o:  t = sum_i c_i y_i (a chain of fmaf from 0), V = 2 t (L2), 0 (IP). */
+#define RESID_BIAS 1073741824.0 /* 2^30 */
+
+static int32_t resid_round(float x, float lim) {
+    x = fmaxf(x, -lim);
+    x = fminf(x, lim);
+    return (int32_t)rintf(x);
+}
+
+float oracle_resid_a(const float* q, const float* c, int32_t d, int32_t metric) {
+    float s = 0.0f, n = 0.0f;
+    for (int32_t i = 0; i < d; ++i) {
+        s = fmaf(q[i], c[i], s);
+        n = fmaf(c[i], c[i], n);
+    }
+    return metric == ORACLE_L2 ? fmaf(-2.0f, s, n) : -s;
+}
+
+int32_t oracle_resid_base(float a, float inv) {
+    return (int32_t)RESID_BIAS + resid_round(a * inv, 536870912.0f);
+}
+
+int32_t oracle_resid_w(float v, float inv) { return resid_round(v * inv, 268435456.0f); }
+
+/* V_o of n code rows (canonical layout) of list centroid c. */
+void oracle_resid_v(const float* c, const uint8_t* codes, int64_t n, const float* books, int32_t d,
+                    int32_t M, int32_t bits, int32_t metric, float* out_v) {
+    const int32_t K = 1 << bits, ds = d / M, cb = M * bits / 8;
+    for (int64_t o = 0; o < n; ++o) {
+        const uint8_t* row = codes + (size_t)o * cb;
+        float t = 0.0f;
+        for (int32_t m = 0; m < M; ++m) {
+            const float* y = books + ((size_t)m * K + code_of(row, m, bits)) * ds;
+            for (int32_t i = 0; i < ds; ++i) t = fmaf(c[m * ds + i], y[i], t);
+        }
+        out_v[o] = metric == ORACLE_L2 ? 2.0f * t : 0.0f;
+    }
+}
+
+/* Residual keys of n objects of one list: the plain sums of oracle_adc plus
+ * base_ql and each object's w_o (see above). */
+void oracle_adc_resid(const uint16_t* lut16, const uint8_t* codes, int64_t n, int32_t M, int32_t bits,
+                      const float* q, const float* c, const float* books, int32_t d, int32_t metric,
+                      float inv, uint32_t* out_e) {
+    float* v = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    oracle_adc(lut16, codes, n, M, bits, out_e);
+    oracle_resid_v(c, codes, n, books, d, M, bits, metric, v);
+    const int64_t base = oracle_resid_base(oracle_resid_a(q, c, d, metric), inv);
+    for (int64_t o = 0; o < n; ++o) out_e[o] = (uint32_t)((int64_t)out_e[o] + base + oracle_resid_w(v[o], inv));
+    free(v);
 }
 
 /* ------------------------------------------------------------------ */
@@ -470,6 +575,7 @@ typedef struct {
     const uint8_t* codes;        /* [n*code_bytes] list order */
     const float* books;          /* [M*2^bits*d/M] */
     const float* vectors;        /* [n*d] id order */
+    int32_t residual;            /* 1: codes are PQ codes of o - c_l (residual IVF-PQ) */
 } oracle_ivfpq;
 
 /* collector: 0 = sort, 1 = heap, 2 = bucket (Algorithm 1).
@@ -498,11 +604,17 @@ int oracle_search(const oracle_ivfpq* ix, const float* queries, int64_t nq, int3
         const float* q = queries + (size_t)qi * d;
         oracle_probe(q, ix->centroids, ix->nlist, d, ix->metric, nprobe, lists, NULL);
         oracle_lut16(q, ix->books, d, ix->M, ix->bits, ix->metric, lut, NULL);
+        const float inv = ix->residual ? oracle_lut16_scale(q, ix->books, d, ix->M, ix->bits, ix->metric, NULL)
+                                       : 0.0f;
         int64_t sq = 0;
         lofs[0] = 0;
         for (int32_t j = 0; j < nprobe; ++j) {
             int64_t a = ix->list_offsets[lists[j]], b = ix->list_offsets[lists[j] + 1];
-            oracle_adc(lut, ix->codes + (size_t)a * cb, b - a, ix->M, ix->bits, e + sq);
+            if (ix->residual)
+                oracle_adc_resid(lut, ix->codes + (size_t)a * cb, b - a, ix->M, ix->bits, q,
+                                 ix->centroids + (size_t)lists[j] * d, ix->books, d, ix->metric, inv, e + sq);
+            else
+                oracle_adc(lut, ix->codes + (size_t)a * cb, b - a, ix->M, ix->bits, e + sq);
             for (int64_t i = a; i < b; ++i) sid[sq + (i - a)] = ix->ids[i];
             sq += b - a;
             lofs[j + 1] = sq;

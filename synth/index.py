@@ -4,8 +4,10 @@ The index is an input to the search path, built once before any query runs:
 
 * IVF: k-means centroids (seed 3); every vector goes to its nearest centroid's
   inverted list (the paper's indexing phase, Section 2 "Quantization").
-* PQ: non-residual product quantisation, M sub-spaces of d/M dimensions with
-  2^b codewords each, trained by k-means on raw sub-vectors (seed 4).
+* PQ: product quantisation, M sub-spaces of d/M dimensions with 2^b
+  codewords each, trained by k-means on raw sub-vectors (seed 4); or, for a
+  residual index, on the sub-vectors of o - c_l, the residual to the list's
+  centroid, which the codes then quantise.
 * Sign quantizer: IVF lists plus a seeded random rotation (seed 5); the sign
   codes of each rotated residual and their per-vector factors are derived
   from these by the library and by the oracle, each on its own (see
@@ -17,7 +19,7 @@ row per vector in list order; for 8-bit PQ byte m holds sub-space m, for
 its high nibble when m is odd.
 
 File format (little-endian, written by ``write_index``): a 64-byte header
-``b"BBCIDX01"``, u32 version, u32 quantizer (0 PQ, 1 sign), u32 metric
+``b"BBCIDX01"``, u32 version, u32 quantizer (0 PQ, 1 sign, 2 residual PQ), u32 metric
 (0 L2, 1 IP), u32 d, u64 n, u32 nlist, u32 pq_m, u32 pq_bits, then padding;
 followed by the arrays, each starting on a 64-byte boundary, in this order:
 centroids f32[nlist*d], list_offsets i64[nlist+1], ids i64[n] (list order),
@@ -121,6 +123,7 @@ class IvfPqIndex:
     codes: np.ndarray           # u8 [n, code_bytes], list order, canonical layout
     codebooks: np.ndarray       # f32 [pq_m, 2^pq_bits, d / pq_m]
     vectors: np.ndarray         # f32 [n, d], id order
+    residual: bool = False      # codes quantise o - c_l (residual IVF-PQ)
 
     @property
     def n(self) -> int:
@@ -192,7 +195,8 @@ def _kmeans_dev(train, k: int, iters: int, rng, chunk: int):
     return cent
 
 
-def _build_ivf_pq_dev(x, nlist, pq_m, pq_bits, metric, kmeans_iters, pq_iters, kmeans_sample, pq_sample):
+def _build_ivf_pq_dev(x, nlist, pq_m, pq_bits, metric, kmeans_iters, pq_iters, kmeans_sample, pq_sample,
+                      residual=False):
     """The same construction as ``build_ivf_pq`` with torch on the build device
     (for large inputs); results are deterministic for a given machine."""
     import torch
@@ -209,6 +213,8 @@ def _build_ivf_pq_dev(x, nlist, pq_m, pq_bits, metric, kmeans_iters, pq_iters, k
     del train
     assign = _nearest_dev(xt, cent, 1 << 15).cpu().numpy()
     ids, offsets = _inverted_lists(assign, nlist)
+    if residual:
+        xt = xt - cent[torch.from_numpy(assign).to(dev)]
     dsub, ksub = d // pq_m, 1 << pq_bits
     rng = np.random.default_rng(SEED_PQ)
     samp = xt[torch.from_numpy(np.sort(rng.choice(n, size=min(n, pq_sample), replace=False))).to(dev)]
@@ -223,13 +229,17 @@ def _build_ivf_pq_dev(x, nlist, pq_m, pq_bits, metric, kmeans_iters, pq_iters, k
     del xt, samp
     codes = codes_full if pq_bits == 8 else _pack4(codes_full)
     return IvfPqIndex(metric, d, nlist, pq_m, pq_bits, cent.cpu().numpy(), offsets, ids,
-                      np.ascontiguousarray(codes), books, x)
+                      np.ascontiguousarray(codes), books, x, residual)
 
 
 def build_ivf_pq(x: np.ndarray, nlist: int, pq_m: int, pq_bits: int, metric: str = "l2",
                  kmeans_iters: int = 12, pq_iters: int = 12, kmeans_sample: int | None = None,
-                 pq_sample: int = 65536) -> IvfPqIndex:
-    """Build an IVF-PQ index (non-residual PQ) over ``x`` (f32 [n, d])."""
+                 pq_sample: int = 65536, residual: bool = False) -> IvfPqIndex:
+    """Build an IVF-PQ index over ``x`` (f32 [n, d]).
+
+    ``residual`` = False: PQ of the raw vectors.  True: PQ of each vector's
+    residual to its list centroid, o - c_l (codebooks trained on sampled
+    residuals), the residual form of Section 2's "Quantization"."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     n, d = x.shape
     if d % pq_m:
@@ -242,25 +252,26 @@ def build_ivf_pq(x: np.ndarray, nlist: int, pq_m: int, pq_bits: int, metric: str
         kmeans_sample = min(n, 256 * nlist)
     if _DEVICE != "cpu" and n * d >= (1 << 28):
         return _build_ivf_pq_dev(x, nlist, pq_m, pq_bits, metric, kmeans_iters, pq_iters, kmeans_sample,
-                                 pq_sample)
+                                 pq_sample, residual)
     cent = kmeans(x, nlist, iters=kmeans_iters, seed=SEED_KMEANS, sample=kmeans_sample)
     assign = nearest(x, cent)
     ids, offsets = _inverted_lists(assign, nlist)
+    xq = (x - cent[assign]).astype(np.float32) if residual else x
 
     dsub = d // pq_m
     ksub = 1 << pq_bits
     rng = np.random.default_rng(SEED_PQ)
-    samp = x[np.sort(rng.choice(n, size=min(n, pq_sample), replace=False))]
+    samp = xq[np.sort(rng.choice(n, size=min(n, pq_sample), replace=False))]
     books = np.empty((pq_m, ksub, dsub), dtype=np.float32)
     codes_full = np.empty((n, pq_m), dtype=np.uint8)
     for m in range(pq_m):
         sub = np.ascontiguousarray(samp[:, m * dsub:(m + 1) * dsub])
         books[m] = kmeans(sub, ksub, iters=pq_iters, seed=SEED_PQ + 17 * m)
-        codes_full[:, m] = nearest(np.ascontiguousarray(x[:, m * dsub:(m + 1) * dsub]), books[m])
+        codes_full[:, m] = nearest(np.ascontiguousarray(xq[:, m * dsub:(m + 1) * dsub]), books[m])
     codes_full = codes_full[ids]
     codes = codes_full if pq_bits == 8 else _pack4(codes_full)
     return IvfPqIndex(metric, d, nlist, pq_m, pq_bits, cent, offsets, ids,
-                      np.ascontiguousarray(codes), books, x)
+                      np.ascontiguousarray(codes), books, x, residual)
 
 
 def _align(f, a: int = 64) -> None:
@@ -273,7 +284,8 @@ def _align(f, a: int = 64) -> None:
 def write_index(path: str, idx: IvfPqIndex) -> None:
     """Write an IVF-PQ index in the BBCIDX01 format described in the module docstring."""
     with open(path, "wb") as f:
-        hdr = struct.pack(HEADER_FMT, MAGIC, 1, 0, 0 if idx.metric == "l2" else 1,
+        hdr = struct.pack(HEADER_FMT, MAGIC, 1, 2 if getattr(idx, "residual", False) else 0,
+                          0 if idx.metric == "l2" else 1,
                           idx.d, idx.n, idx.nlist, idx.pq_m, idx.pq_bits)
         f.write(hdr + b"\0" * (HEADER_BYTES - len(hdr)))
         for arr, dt in ((idx.centroids, np.float32), (idx.list_offsets, np.int64),
@@ -306,6 +318,7 @@ class IvfSignIndex:
     ids: np.ndarray             # i64 [n], list order
     rotation: np.ndarray        # f32 [d, d], orthonormal rows (r = P u)
     vectors: np.ndarray         # f32 [n, d], id order
+    residual: bool = False      # codes quantise o - c_l (residual IVF-PQ)
 
     @property
     def n(self) -> int:

@@ -52,6 +52,18 @@ def small_workload(kind: str):
     elif kind == "wide":      # d = 768 unit norm, inner product, PQ 96 x 8 bit
         x, q = embedding_shaped(8000, 12, d=768)
         idx = build_ivf_pq(x, 24, 96, 8, "ip", kmeans_iters=5, pq_iters=5, pq_sample=8000)
+    elif kind == "rtiny":     # residual IVF-PQ: the tiny data, PQ 16 x 8 bit of o - c_l
+        x, q = gaussian_mixture_tiny(12000, 24, d=64, n_centers=200, sigma=0.3)
+        idx = build_ivf_pq(x, 48, 16, 8, "l2", kmeans_iters=6, pq_iters=6, pq_sample=8000, residual=True)
+    elif kind == "rsift":     # residual IVF-PQ on integer data, PQ 32 x 8 bit
+        x, q = sift_shaped(12000, 24, d=128, n_centers=300)
+        idx = build_ivf_pq(x, 64, 32, 8, "l2", kmeans_iters=6, pq_iters=6, pq_sample=8000, residual=True)
+    elif kind == "rsift4":    # residual IVF-PQ, PQ 64 x 4 bit
+        x, q = sift_shaped(12000, 24, d=128, n_centers=300)
+        idx = build_ivf_pq(x, 64, 64, 4, "l2", kmeans_iters=6, pq_iters=6, pq_sample=8000, residual=True)
+    elif kind == "rembed":    # residual IVF-PQ, inner product, PQ 32 x 8 bit
+        x, q = embedding_shaped(12000, 24, d=64)
+        idx = build_ivf_pq(x, 48, 32, 8, "ip", kmeans_iters=6, pq_iters=6, pq_sample=8000, residual=True)
     elif kind == "ragged":    # few vectors, many short and empty lists
         x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
         idx = build_ivf_pq(x, 40, 8, 8, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700)
