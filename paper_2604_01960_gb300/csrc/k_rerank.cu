@@ -158,7 +158,7 @@ __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restr
 // query, 512-byte FP32 rows) take the fixed-shape path.  Other shapes use the
 // FAST = false instantiation, whose general loop then keeps its own register
 // allocation and schedule.
-template <typename T, bool FAST>
+template <typename T, bool FAST, bool EARLY = false>
 __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankArgs a, const T* __restrict__ vec) {
     extern __shared__ uint4 rsm[];
     const int d = ix.d;
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     const int64_t cf1 = min(cf0 + RR_CAND_PER_CTA, cnt);
     // the common row shapes: 128-byte integer rows, 512-byte FP32 rows
     if (FAST && sizeof(T) == 1 && intpath && nchunk == 8) {
-        if (a.early)
+        if (EARLY)
             rerank_rows<T, 4, 2, true, true>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
                                              reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8),
                                              qn2, a.early + a.qp.coff(qi), a.early_totals ? a.early_totals + 1 : nullptr);
@@ -343,7 +343,11 @@ cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, c
     if (nq <= 0) return cudaSuccess;
     dim3 grid((unsigned)((a.kc + RR_CAND_PER_CTA - 1) / RR_CAND_PER_CTA), (unsigned)nq);
     const size_t smem = sizeof(float) * ix.d + ix.d + 16;
-    if (a.use_u8 && ix.vec_u8)
+    // the early re-rank's candidates carry exact distances from the scan: its own instantiation,
+    // so the plain kernel keeps its code
+    if (a.use_u8 && ix.vec_u8 && a.early)
+        rerank_kernel<uint8_t, true, true><<<grid, RR_THREADS, smem, st>>>(ix, a, ix.vec_u8);
+    else if (a.use_u8 && ix.vec_u8)
         rerank_kernel<uint8_t, true><<<grid, RR_THREADS, smem, st>>>(ix, a, ix.vec_u8);
     else if (ix.d * 4 == 32 * 16)
         rerank_kernel<float, true><<<grid, RR_THREADS, smem, st>>>(ix, a, ix.vectors);
