@@ -63,6 +63,8 @@ def parse():
                         "prints one line per value")
     p.add_argument("--early-rerank", default="0",
                    help="Algorithm 4's early re-rank: 1 on, 0 off; a comma list prints one line per value")
+    p.add_argument("--residual", action="store_true",
+                   help="residual IVF-PQ: the PQ codes quantise each vector's residual to its list centroid")
     p.add_argument("--pair", default="0",
                    help="scan schedule: 1 two queries per CTA (pair form), 0 one; a comma list prints one line per value")
     p.add_argument("--cpu-queries", type=int, default=200, help="oracle sample for cpu_baseline")
@@ -94,6 +96,13 @@ def parse():
     p.add_argument("--recall-queries", type=int, default=None,
                    help="queries whose recall is measured against exact kNN (default: all, at most 1,000)")
     return p.parse_args()
+
+
+def pq_desc(idx) -> str:
+    """The quantizer of an index as the bench line's config names it."""
+    if hasattr(idx, "rotation"):
+        return "sign 1-bit"
+    return f"{idx.pq_m}x{idx.pq_bits}" + (" residual" if getattr(idx, "residual", False) else "")
 
 
 def dist_setup():
@@ -154,7 +163,7 @@ def make_inputs(args, device, rank: int = 0, ws: int = 1):
         from synth import build_ivf_sign
         idx = build_ivf_sign(x, nlist)
     else:
-        idx = build_ivf_pq(x, nlist, w.pq_m, w.pq_bits, w.metric)
+        idx = build_ivf_pq(x, nlist, w.pq_m, w.pq_bits, w.metric, residual=bool(getattr(args, "residual", False)))
     return w, idx, q, k, nprobe, time.time() - t0
 
 
@@ -278,7 +287,7 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": qps, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "pq": f"{idx.pq_m}x{idx.pq_bits}",
+        "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "pq": pq_desc(idx),
                    "nq_per_step": nqs, "k": k, "nprobe": nprobe, "kc": kc},
         "cpu_baseline": {"value": qps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": qps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -499,7 +508,7 @@ def run_plain(args, ws, rank, local):
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u16/u32 ADC, f32 re-rank from the FP32 rows", "data": "synthetic",
             "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist,
-                       "pq": "sign 1-bit" if hasattr(idx, "rotation") else f"{idx.pq_m}x{idx.pq_bits}",
+                       "pq": pq_desc(idx),
                        "queries_per_step": nsel, "k": k, "nprobe": nprobe, "kc_ratio": ratio,
                        "form": "one bbc_search per query, FP32 rows, no graphs",
                        "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
@@ -802,7 +811,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
                                               2: "e4m3+f32 re-rank (f64 at ties)"}[prec]),
             "data": "synthetic",
             "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "metric_space": idx.metric,
-                       "pq": "sign 1-bit" if is_sign else f"{idx.pq_m}x{idx.pq_bits}", "nq": nq, "k": k,
+                       "pq": pq_desc(idx), "nq": nq, "k": k,
                        "nprobe": nprobe, "kc": None if is_sign else kc,
                        "kc_ratio": ratio, "buckets": m, "rerank": rerank,
                        "scan_schedule": "pair" if index.get("pair") else "one query per CTA",

@@ -53,13 +53,20 @@ extern "C" {
 #define BBC_METRIC_IP 1
 #define BBC_QUANT_PQ 0
 #define BBC_QUANT_SIGN 1
+#define BBC_QUANT_PQ_RESIDUAL 2   /* PQ codes of each object's residual o - c_l */
 
 typedef struct bbc_index bbc_index;   /* opaque, owned by the library */
 
 /* Host-side description of an IVF-PQ index (Section 2, "Quantization"):
- * nlist k-means centroids, inverted lists of vector ids, non-residual PQ with
- * pq_m sub-spaces of d/pq_m dimensions and 2^pq_bits codewords each.
- * All pointers are HOST pointers; bbc_index_create copies what it needs. */
+ * nlist k-means centroids, inverted lists of vector ids, PQ with pq_m
+ * sub-spaces of d/pq_m dimensions and 2^pq_bits codewords each, of the
+ * vectors themselves or (residual = 1) of each vector's residual o - c_l to
+ * its list's centroid.  For a residual index the estimated distance of an
+ * object is its distance from the query to c_l + y (y the code's
+ * reconstruction): the query's table sum, plus per (query, list) ||c_l||^2 -
+ * 2 <q, c_l> (L2) or -<q, c_l> (IP), plus per object 2 <c_l, y> (L2), the
+ * last computed on the device at creation.  All pointers are HOST pointers;
+ * bbc_index_create copies what it needs. */
 typedef struct {
     int64_t n;                 /* number of vectors, 1 <= n < 2^32 - 1 */
     int32_t d;                 /* dimension, multiple of pq_m */
@@ -75,6 +82,7 @@ typedef struct {
                                   for even m, high nibble for odd m */
     const float* codebooks;    /* [pq_m * 2^pq_bits * (d/pq_m)], [m][j][i] */
     const float* vectors;      /* [n * d] row-major by id (for the exact re-rank) */
+    int32_t residual;          /* 0: PQ of the vectors; 1: PQ of o - c_l (residual IVF-PQ) */
 } bbc_index_host;
 
 typedef struct {
@@ -84,7 +92,7 @@ typedef struct {
     int32_t vectors_u8_exact;  /* 1 if every component is an integer in [0,255] (exact u8 copy kept) */
     int32_t device;
     int64_t device_bytes;      /* bytes of device memory the index holds */
-    int32_t quantizer;         /* BBC_QUANT_PQ or BBC_QUANT_SIGN */
+    int32_t quantizer;         /* BBC_QUANT_PQ, BBC_QUANT_SIGN or BBC_QUANT_PQ_RESIDUAL */
     int32_t reserved;
 } bbc_index_info_t;
 
@@ -97,7 +105,8 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out);
  * phase, Section 2, done offline; this call only loads its result).  Format
  * "BBCIDX01", little-endian: a 64-byte header {magic[8], u32 version = 1,
  * u32 quantizer, u32 metric, u32 d, u64 n, u32 nlist, u32 pq_m, u32 pq_bits},
- * then arrays each starting on a 64-byte boundary.  Quantizer BBC_QUANT_PQ:
+ * then arrays each starting on a 64-byte boundary.  Quantizer BBC_QUANT_PQ
+ * (or BBC_QUANT_PQ_RESIDUAL, the same arrays with codes of o - c_l):
  * centroids, list_offsets, ids, codes, codebooks, vectors, laid out as in
  * bbc_index_host.  Quantizer BBC_QUANT_SIGN (pq_m = pq_bits = 0):
  * centroids, list_offsets, ids, rotation, vectors, as in bbc_sign_host.
@@ -343,7 +352,8 @@ int bbc_collect(bbc_index* ix, const float* queries, int64_t nq, int32_t nprobe,
  * BBC_STATIC_SCRATCH_BYTES, which every GPU that loads the library holds
  * until the process exits; the call allocates nothing.  A call that needs
  * more scratch than that -- about nq * (2 * pq_m * 2^pq_bits + 1344 +
- * 8 * cap) bytes, cap = total length of the nprobe longest lists -- returns
+ * 8 * cap) bytes, cap = total length of the nprobe longest lists, plus
+ * nq * 4 * (1 + nprobe) on a residual index -- returns
  * BBC_ERR_ARG before launching anything.  The first call on a device looks
  * up the array's device address with that device current and keeps it for
  * the life of the process; make that first call before any stream capture,

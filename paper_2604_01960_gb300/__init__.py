@@ -46,7 +46,7 @@ class IndexHost(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("nlist", C.c_int32), ("metric", C.c_int32),
                 ("pq_m", C.c_int32), ("pq_bits", C.c_int32), ("centroids", C.c_void_p),
                 ("list_offsets", C.c_void_p), ("ids", C.c_void_p), ("codes", C.c_void_p),
-                ("codebooks", C.c_void_p), ("vectors", C.c_void_p)]
+                ("codebooks", C.c_void_p), ("vectors", C.c_void_p), ("residual", C.c_int32)]
 
 
 class IndexInfo(C.Structure):
@@ -170,8 +170,9 @@ def _stream(stream) -> int | None:
 # C-ABI wrappers with the C names
 # ---------------------------------------------------------------------------
 def bbc_index_create(index, device: int = 0) -> int:
-    """Create a device index from a host IVF-PQ index object (numpy arrays),
-    or from an IVF sign-quantizer index (one with a ``rotation``)."""
+    """Create a device index from a host IVF-PQ index object (numpy arrays;
+    ``residual`` true: its codes quantise o - c_l), or from an IVF
+    sign-quantizer index (one with a ``rotation``)."""
     if hasattr(index, "rotation"):
         return bbc_index_create_sign(index, device)
     keep = []
@@ -184,7 +185,7 @@ def bbc_index_create(index, device: int = 0) -> int:
     h = IndexHost(int(index.n), int(index.d), int(index.nlist), METRICS[index.metric], int(index.pq_m),
                   int(index.pq_bits), arr(index.centroids, np.float32), arr(index.list_offsets, np.int64),
                   arr(index.ids, np.int64), arr(index.codes, np.uint8), arr(index.codebooks, np.float32),
-                  arr(index.vectors, np.float32))
+                  arr(index.vectors, np.float32), 1 if getattr(index, "residual", False) else 0)
     out = C.c_void_p()
     _check(lib().bbc_index_create(C.byref(h), device, C.byref(out)))
     return out.value

@@ -223,7 +223,7 @@ struct Plan {
     int64_t cap;
     size_t off_scores, off_probe, off_lut, off_state, off_region, off_cand, off_count, off_cdist,
         off_q, off_ids, off_dists, off_abf, off_keys, off_params, off_counters, off_prec, off_pair, off_rdist,
-        off_cearly, total;
+        off_cearly, off_qinv, off_lbase, total;
 };
 
 // The precision re-rank runs when a low-precision copy exists and the exact u8
@@ -311,6 +311,8 @@ size_t layout(const bbc_index* ix, const ChunkShape& c, Plan& p) {
     const bool early = ix->early_rerank && ix->dev.vec_lo;
     p.off_rdist = o; o = align_up(o + (early ? (size_t)c.sum_cap * 4 : 0));
     p.off_cearly = o; o = align_up(o + (early ? (size_t)c.sum_kc * 4 : 0));
+    p.off_qinv = o; o = align_up(o + (d.resid ? (size_t)c.nq * 4 : 0));
+    p.off_lbase = o; o = align_up(o + (d.resid ? (size_t)c.sum_probe * 4 : 0));
     p.total = o;
     return o;
 }
@@ -446,9 +448,17 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
         }));
     }
     if (stop_after <= 2) return BBC_OK;
-    CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(d, q, nc, lut, st); }));
+    float* qinv = d.resid ? reinterpret_cast<float*>(ws + p.off_qinv) : nullptr;
+    CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(d, q, nc, lut, st, qinv); }));
     ScanArgs sa{lut, probe_in ? probe_in : probe, p.nprobe, p.kc, ix->buckets, ix->sample_lists,
                 region, p.cap, state, qp, 0, SelectArgs{}};
+    if (d.resid) {
+        // residual IVF-PQ: each (query, probed list)'s base in the table's units
+        int32_t* lbase = reinterpret_cast<int32_t*>(ws + p.off_lbase);
+        CUDA_TRY(stage(ix, 2, st, [&] { return launch_resid_base(d, q, nc, qp, p.nprobe, sa.lists, qinv, lbase, st); }));
+        sa.qinv = qinv;
+        sa.lbase = lbase;
+    }
     // one CTA per query when the batch fills the GPU, else G CTAs per query
     int G = ix->split >= 2 ? ix->split : 1;
     if (ix->split == 0) {
@@ -459,8 +469,8 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
         // a baseline collector in place of the result buffer: it writes the candidates itself
         const uint32_t stage_cap = (uint32_t)((ix->info.max_list_len + 31) / 32 * 32);
         if (!scan_collect_supported(d, ix->collector, p.nprobe, p.kc, stage_cap))
-            return fail(BBC_ERR_UNSUPPORTED, "collector %d: table shape or K_c %lld not supported", ix->collector,
-                        (long long)p.kc);
+            return fail(BBC_ERR_UNSUPPORTED, "collector %d: table shape, K_c %lld or residual codes not supported",
+                        ix->collector, (long long)p.kc);
         sa.fuse_select = 1;
         sa.sel = SelectArgs{region, p.cap, state, p.kc, cand, count, nullptr, qp};
         CUDA_TRY(stage(ix, 3, st, [&] { return launch_scan_collect(d, nc, sa, ix->collector, stage_cap, st); }));
@@ -774,9 +784,10 @@ int set_early_rerank(bbc_index* ix, int on) {
     DeviceGuard g(ix->device);
     const DevIndex& d = ix->dev;
     if (on) {
-        if (d.quant != BBC_QUANT_PQ || !d.vec_u8 || d.metric != BBC_METRIC_L2 || d.d % 16 || d.d > 256)
+        if (d.quant != BBC_QUANT_PQ || d.resid || !d.vec_u8 || d.metric != BBC_METRIC_L2 || d.d % 16 || d.d > 256)
             return fail(BBC_ERR_UNSUPPORTED,
-                        "early_rerank needs an L2 PQ index with the exact u8 copy and d a multiple of 16 up to 256");
+                        "early_rerank needs a plain (not residual) L2 PQ index with the exact u8 copy and d a "
+                        "multiple of 16 up to 256");
         if (d.bits == 8 ? d.M > 32 : d.M > 64)
             return fail(BBC_ERR_UNSUPPORTED, "early_rerank needs a table of at most 64 KB (pq_m <= 32 at 8 bits)");
     }
@@ -896,6 +907,7 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out) {
     if (h->nlist < 1) return fail(BBC_ERR_ARG, "nlist must be >= 1");
     if (h->metric != BBC_METRIC_L2 && h->metric != BBC_METRIC_IP) return fail(BBC_ERR_ARG, "bad metric %d", h->metric);
     if (h->pq_m < 1 || h->d % h->pq_m) return fail(BBC_ERR_ARG, "pq_m=%d must divide d=%d", h->pq_m, h->d);
+    if (h->residual != 0 && h->residual != 1) return fail(BBC_ERR_ARG, "residual must be 0 or 1");
     if (!scan_supported(h->pq_m, h->pq_bits))
         return fail(BBC_ERR_UNSUPPORTED, "pq_m=%d x %d bits not supported", h->pq_m, h->pq_bits);
     if (!h->centroids || !h->list_offsets || !h->ids || !h->codes || !h->codebooks || !h->vectors)
@@ -1021,6 +1033,31 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out) {
     }
     D.centroids = dc; D.cnorm = dcn; D.list_blk = dlb; D.list_len = dll; D.codes = dcode; D.ids = did;
     D.books = dbook; D.vectors = dvec; D.status = dstat; D.vec_u8 = nullptr;
+    if (h->residual) {
+        // residual IVF-PQ: V_o per code slot and ||c_l||^2 in FP32, computed on the device from the
+        // canonical code rows (uploaded for the build only)
+        std::vector<float> zs((size_t)ix->nslots, 0.f), zl((size_t)L, 0.f);
+        float* drv;
+        float* dcn2;
+        if ((rc = upload(ix.get(), zs.data(), zs.size(), &drv))) return rc;
+        if ((rc = upload(ix.get(), zl.data(), zl.size(), &dcn2))) return rc;
+        D.resid = 1;
+        D.rv = drv;
+        D.rcn2 = dcn2;
+        void* canon = nullptr;
+        void* offs = nullptr;
+        if (cudaMalloc(&canon, std::max<size_t>((size_t)n * cb, 16)) != cudaSuccess ||
+            cudaMalloc(&offs, (size_t)(L + 1) * 8) != cudaSuccess) {
+            cudaFree(canon);
+            return fail(BBC_ERR_OOM, "residual build scratch");
+        }
+        std::unique_ptr<void, cudaError_t (*)(void*)> fc(canon, cudaFree), fo(offs, cudaFree);
+        CUDA_TRY(cudaMemcpy(canon, h->codes, (size_t)n * cb, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(offs, h->list_offsets, (size_t)(L + 1) * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY(launch_resid_v(D, static_cast<const uint8_t*>(canon), static_cast<const int64_t*>(offs), drv, dcn2,
+                                ix->nslots, 0));
+        CUDA_TRY(cudaDeviceSynchronize());
+    }
     if (u8) {
         std::vector<uint8_t> v8((size_t)n * d);
         for (size_t i = 0; i < v8.size(); ++i) v8[i] = (uint8_t)h->vectors[i];
@@ -1037,7 +1074,7 @@ int bbc_index_create(const bbc_index_host* h, int device, bbc_index** out) {
     bbc_index_info_t& I = ix->info;
     I.n = n; I.d = d; I.nlist = L; I.metric = h->metric; I.pq_m = M; I.pq_bits = bits;
     I.max_list_len = maxlen; I.vectors_u8_exact = u8 ? 1 : 0; I.device = device;
-    I.quantizer = BBC_QUANT_PQ;
+    I.quantizer = h->residual ? BBC_QUANT_PQ_RESIDUAL : BBC_QUANT_PQ;
     *out = ix.release();
     return BBC_OK;
 }
@@ -1237,10 +1274,11 @@ int bbc_index_load(const char* path, int device, bbc_index** out) {
     memcpy(&d, hdr + 20, 4); memcpy(&n, hdr + 24, 8); memcpy(&nlist, hdr + 32, 4);
     memcpy(&pq_m, hdr + 36, 4); memcpy(&pq_bits, hdr + 40, 4);
     if (version != 1) return fail(BBC_ERR_FORMAT, "unsupported version %u", version);
-    if (quant != BBC_QUANT_PQ && quant != BBC_QUANT_SIGN) return fail(BBC_ERR_FORMAT, "unknown quantizer %u", quant);
+    if (quant != BBC_QUANT_PQ && quant != BBC_QUANT_SIGN && quant != BBC_QUANT_PQ_RESIDUAL)
+        return fail(BBC_ERR_FORMAT, "unknown quantizer %u", quant);
     if (d == 0 || d > 65536 || nlist == 0 || nlist > (1u << 24) || n == 0 || n >= 0xFFFFFFFFull)
         return fail(BBC_ERR_FORMAT, "header fields out of range");
-    if (quant == BBC_QUANT_PQ && (pq_m == 0 || pq_m > d || (pq_bits != 4 && pq_bits != 8)))
+    if (quant != BBC_QUANT_SIGN && (pq_m == 0 || pq_m > d || (pq_bits != 4 && pq_bits != 8)))
         return fail(BBC_ERR_FORMAT, "PQ header fields out of range");
     auto rd = [&](void* dst, size_t bytes) -> bool {
         long pos = ftell(f);
@@ -1273,7 +1311,8 @@ int bbc_index_load(const char* path, int device, bbc_index** out) {
         !rd(codes.data(), codes.size()) || !rd(books.data(), books.size() * 4) || !rd(vecs.data(), vecs.size() * 4))
         return fail(BBC_ERR_FORMAT, "truncated index file");
     bbc_index_host h{(int64_t)n, (int32_t)d, (int32_t)nlist, (int32_t)metric, (int32_t)pq_m, (int32_t)pq_bits,
-                     cent.data(), offs.data(), ids.data(), codes.data(), books.data(), vecs.data()};
+                     cent.data(), offs.data(), ids.data(), codes.data(), books.data(), vecs.data(),
+                     quant == BBC_QUANT_PQ_RESIDUAL ? 1 : 0};
     return bbc_index_create(&h, device, out);
 }
 

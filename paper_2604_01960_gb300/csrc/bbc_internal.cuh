@@ -78,6 +78,11 @@ struct DevIndex {
     // so a warp's 32-vector block has its rows contiguous, and ||v||^2 per slot
     const uint8_t* vec_lo;     // [nblocks * 32][d] or null
     const uint32_t* vnorm2;    // [nblocks * 32] or null
+    // residual IVF-PQ: the codes quantise o - c_l; per code-block slot the
+    // object's term V_o = 2 <c_l, y_o> (L2; 0 for IP and padding slots)
+    int resid;                 // 1: residual codes
+    const float* rv;           // [nblocks * 32] or null
+    const float* rcn2;         // [nlist] ||c_l||^2 in FP32 (chain of fused multiply-adds), or null
 };
 
 // Words per LUT row in shared memory: lane t at code slot s reads word t + s
@@ -142,9 +147,22 @@ cudaError_t launch_probe_scores_tc(const DevIndex& ix, const float* q, int64_t n
 // tc = 1 when the scores come from the tensor-core GEMM (wider error bound).
 cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, const QueryParams& qp,
                                 int max_nprobe, const float* scores, int32_t* lists, int tc, cudaStream_t st);
-// S3: uint16 PQ lookup tables [nq][M][K].
+// S3: uint16 PQ lookup tables [nq][M][K]; inv (may be null): each query's
+// scale 65535 / span, the table's integer units per unit of distance.
 cudaError_t launch_lut16(const DevIndex& ix, const float* q, int64_t nq, uint16_t* lut16,
-                         cudaStream_t st);
+                         cudaStream_t st, float* inv = nullptr);
+// Residual IVF-PQ, per (query, probed list): base = 2^30 + rint(clamp(A_ql *
+// inv_q, +-2^29)), A_ql = ||c_l||^2 - 2 <q, c_l> (L2) or -<q, c_l> (IP) in FP32
+// (fused multiply-adds over ascending dimension); packed like the probe lists
+// (maxp: the largest nprobe of the batch).
+cudaError_t launch_resid_base(const DevIndex& ix, const float* q, int64_t nq, const QueryParams& qp, int maxp,
+                              const int32_t* lists, const float* inv, int32_t* base, cudaStream_t st);
+// Residual IVF-PQ index build: rv[slot] = 2 <c_l, y> (L2) or 0 (IP) for each
+// slot of list l's code blocks, y the reconstruction of the canonical code
+// row codes[off_l + p] (p = the slot's position in the list); 0 for padding;
+// cn2[l] = ||c_l||^2 in FP32.
+cudaError_t launch_resid_v(const DevIndex& ix, const uint8_t* canon_codes, const int64_t* list_off, float* rv,
+                           float* cn2, int64_t nslots, cudaStream_t st);
 
 struct SelectArgs {
     const uint2* region;
@@ -176,6 +194,9 @@ struct ScanArgs {
     const float* q = nullptr;     // [nq][d] queries (the early re-rank's exact distances)
     float* rdist = nullptr;       // exact distance per region entry (< 0: none), per roff
     unsigned long long* early_totals = nullptr;   // [2]: objects scored early, early distances used
+    // residual IVF-PQ: each query's table scale and per-(query, list) base, packed like lists
+    const float* qinv = nullptr;
+    const int32_t* lbase = nullptr;
 };
 // S4-S6: sample + codebook + scan + push/update, one CTA per query (and S7
 // in its tail when fuse_select is set).

@@ -77,7 +77,9 @@ extern "C" int bbc_collect_static(bbc_index* ix, const float* queries, int64_t n
     const size_t lut_bytes = align256((size_t)nq * d.M * d.K * 2);
     const size_t state_bytes = out_state ? 0 : align256((size_t)nq * sizeof(bbc_collector_state));
     const size_t region_bytes = align256((size_t)nq * (size_t)cap * 8);
-    const size_t need = lut_bytes + state_bytes + region_bytes;
+    // residual IVF-PQ: each query's table scale and its probed lists' bases
+    const size_t resid_bytes = d.resid ? align256((size_t)nq * 4) + align256((size_t)nq * nprobe * 4) : 0;
+    const size_t need = lut_bytes + state_bytes + region_bytes + resid_bytes;
     if (need > kStaticScratchBytes) {
         char msg[256];
         snprintf(msg, sizeof(msg),
@@ -99,11 +101,17 @@ extern "C" int bbc_collect_static(bbc_index* ix, const float* queries, int64_t n
         bbc_collector_state* state =
             out_state ? out_state : reinterpret_cast<bbc_collector_state*>(p + lut_bytes);
         uint2* region = reinterpret_cast<uint2*>(p + lut_bytes + state_bytes);
+        char* rp = p + lut_bytes + state_bytes + region_bytes;
+        float* qinv = d.resid ? reinterpret_cast<float*>(rp) : nullptr;
+        int32_t* lbase = d.resid ? reinterpret_cast<int32_t*>(rp + align256((size_t)nq * 4)) : nullptr;
         cudaStream_t st = (cudaStream_t)stream;
-        e = launch_lut16(d, queries, nq, lut, st);
+        const QueryParams qp = uniform_params(nprobe, kc, 1, cap);
+        e = launch_lut16(d, queries, nq, lut, st, qinv);
+        if (e == cudaSuccess && d.resid) e = launch_resid_base(d, queries, nq, qp, nprobe, probe_lists, qinv, lbase, st);
         if (e == cudaSuccess) {
-            ScanArgs sa{lut, probe_lists, nprobe, kc, index_buckets(ix), index_sample_lists(ix), region, cap, state,
-                        uniform_params(nprobe, kc, 1, cap)};
+            ScanArgs sa{lut, probe_lists, nprobe, kc, index_buckets(ix), index_sample_lists(ix), region, cap, state, qp};
+            sa.qinv = qinv;
+            sa.lbase = lbase;
             e = launch_scan(d, nq, sa, st);
         }
         if (e == cudaSuccess) {

@@ -276,7 +276,17 @@ struct QCtx {
     uint2* region;
     const int32_t* lists;
     float* rdist;       // early re-rank: exact distance per region entry, or null
+    const int32_t* lbase = nullptr;   // residual IVF-PQ: base of each list (indexed like lists)
+    float inv = 0.f;                  // residual IVF-PQ: the table's scale
 };
+
+// Residual IVF-PQ: the object term w_o = rint(clamp(V_o * inv, +-2^28)) in
+// the table's integer units (the per-list base is added with it).
+__device__ __forceinline__ int32_t resid_w(float v, float inv) {
+    float u = __fmul_rn(v, inv);
+    u = fminf(fmaxf(u, -268435456.f), 268435456.f);
+    return __float2int_rn(u);
+}
 
 // Early re-rank (Algorithm 4): ||q - v||^2 of the object in code-block slot
 // `slot` from the slot-ordered u8 copy, in 32-bit integers (q8: the query's
@@ -432,7 +442,10 @@ __device__ __forceinline__ void stage_lut(const uint16_t* lq, uint32_t* lut) {
 // object whose estimate is below S.eearly gets its exact distance now, from
 // the slot-ordered u8 copy (q8: the query as bytes, null when it is not
 // integer-valued), in Q.rdist; the other appended objects get -1 there.
-template <int M, int BITS, bool MAIN, bool GLOBAL, int HALF = -1, bool EARLY = false>
+// RES: residual IVF-PQ -- each estimate is the table sum plus the list's base
+// (Q.lbase) and the object's term from V_o (ix.rv); the sampling pass then
+// keeps no coarse histogram (the estimates are not bounded by M * 65535).
+template <int M, int BITS, bool MAIN, bool GLOBAL, int HALF = -1, bool EARLY = false, bool RES = false>
 __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& a, const QCtx& Q,
                                             bbc_collector_state* st, int nl, int g0, int g1,
                                             const uint32_t* lut, const int4* ldesc, ScanShared& S,
@@ -440,6 +453,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                                             uint32_t qn2 = 0) {
     using C = ScanCfg<M, BITS>;
     using Pos = typename std::conditional<GLOBAL, unsigned long long, uint32_t>::type;
+    static_assert(!(EARLY && RES), "the early re-rank takes plain PQ codes");
     // the early re-rank's row loads need registers: two blocks per step there
     constexpr int CH = EARLY && C::CHUNK > 2 ? 2 : C::CHUNK;
     const unsigned ln = lane_id();
@@ -455,6 +469,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
     // current list j of this warp (descriptor fields in registers)
     const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(ldesc);
     int j = -1, jhi = 0, jb = 0, jend = 0;
+    int32_t jbase = 0;                                        // RES: base of list j
     auto seek = [&](int g) {
         int4 d;
         if (j < 0) {
@@ -471,6 +486,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
         jhi = d.y;
         jb = d.z;
         jend = d.w;
+        if (RES) jbase = __ldg(Q.lbase + j);
     };
     int it = 0;
     uint32_t nearly = 0;                                      // EARLY: objects this lane scored
@@ -479,9 +495,13 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
         int gbk[CH];
         uint32_t vbits = 0;                                   // bit u: this lane holds a vector of block u
         uint4 r[CH][C::NCH];
+        int32_t radd[CH];                                     // RES: list base (then + the object's term)
+        float rvv[CH];                                        // RES: V_o of this lane's object
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
             gbk[u] = 0;
+            radd[u] = 0;
+            rvv[u] = 0.f;
             if (u < nb) {
                 const int g = cb + u;
                 if (g >= jhi) seek(g);
@@ -490,6 +510,10 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                 const uint4* cp = codes + (size_t)gbk[u] * (32 * C::NCH);
 #pragma unroll
                 for (int c = 0; c < C::NCH; ++c) r[u][c] = __ldg(cp + c * 32);
+                if (RES) {
+                    radd[u] = jbase;
+                    rvv[u] = __ldg(ix.rv + (size_t)gbk[u] * 32u + ln);
+                }
             }
         }
         const uint32_t etau = MAIN ? *(volatile uint32_t*)&S.etau : 0u;
@@ -510,6 +534,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                     adc_pair<M, BITS>(r[u], lane4, lut_s, ea, eb);
                     e[u] = HALF ? eb : ea;
                 }
+                if (RES) e[u] += (uint32_t)(radd[u] + resid_w(rvv[u], Q.inv));
                 const bool valid = (vbits >> u) & 1u;
                 const bool push = MAIN ? (valid && e[u] <= etau) : valid;    // bucket(e) <= tau
                 bal[u] = __ballot_sync(0xFFFFFFFFu, push);
@@ -541,7 +566,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                     const Pos pos = base + (Pos)__popc(bal[u] & lt_mask);
                     if (pos < cap) {
                         region[pos] = make_uint2(e[u], (uint32_t)gbk[u] * 32u + ln);
-                        if (EARLY) {
+                        if constexpr (EARLY) {
                             epos[u] = (uint32_t)pos;
                             if (e[u] < eearly) ebits |= 1u << u;
                         }
@@ -549,7 +574,7 @@ __device__ __forceinline__ void scan_blocks(const DevIndex& ix, const ScanArgs& 
                         atomicOr(ix.status, kStatusRegionOverrun);
                     }
                     if (MAIN) atomicAdd(&S.bh[bin_of(e[u], dmin, sh)], 1u);
-                    else if (!GLOBAL) atomicAdd(&cf[e[u] >> C::SHC], 1u);     // coarse histogram of the sample
+                    else if (!GLOBAL && !RES) atomicAdd(&cf[e[u] >> C::SHC], 1u);   // coarse histogram of the sample
                 }
                 base += (Pos)__popc(bal[u]);
             }
@@ -722,13 +747,15 @@ __device__ void build_codebook_hist(const uint2* region, int64_t ns, int64_t kc,
 }
 
 // Codebook when d_max is found by a radix select over the sample (no
-// histogram gathered while sampling).
-__device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int m, ScanShared& S) {
+// histogram gathered while sampling).  wide: the estimates may use all 32
+// bits (residual IVF-PQ); otherwise they are below M * 65535 < 2^24.
+__device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int m, ScanShared& S,
+                               bool wide = false) {
     const int tid = threadIdx.x, bs = blockDim.x;
     if (ns > 0) {
         const int64_t t = ns < kc ? ns : kc;
         const uint32_t dmax = cta_select_u32(ns, (uint32_t)(t - 1), [&](int64_t i) { return region[i].x; },
-                                             S.ehist, S.sc, 16);
+                                             S.ehist, S.sc, wide ? 24 : 16);
         codebook_from_dmax(region, ns, kc, m, dmax, S);
         return;
     } else {
@@ -741,7 +768,7 @@ __device__ void build_codebook(const uint2* region, int64_t ns, int64_t kc, int 
 // Largest dimension of the early re-rank's in-register query bytes.
 constexpr int kEarlyMaxD = 256;
 
-template <int M, int BITS, bool EARLY = false>
+template <int M, int BITS, bool EARLY = false, bool RES = false>
 __global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan_kernel(DevIndex ix, ScanArgs a) {
     using C = ScanCfg<M, BITS>;
     extern __shared__ uint4 dsm[];
@@ -754,7 +781,8 @@ __global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::M
     __shared__ int s_intq;
     const int64_t qi = blockIdx.x;
     const QCtx Q{a.qp.P(qi), a.qp.KC(qi), a.qp.rcap(qi), a.region + a.qp.roff(qi), a.lists + a.qp.poff(qi),
-                 EARLY ? a.rdist + a.qp.roff(qi) : nullptr};
+                 EARLY ? a.rdist + a.qp.roff(qi) : nullptr, RES ? a.lbase + a.qp.poff(qi) : nullptr,
+                 RES ? a.qinv[qi] : 0.f};
     const int P = Q.P;
     const int tid = threadIdx.x, bs = blockDim.x;
 
@@ -817,13 +845,14 @@ __global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::M
     // ---- Phase B: sample ----
     const int gs = S.gs;
     const uint4* q8 = (EARLY && s_intq) ? sq8 : nullptr;
-    scan_blocks<M, BITS, false, false, -1, EARLY>(ix, a, Q, a.state + qi, P, 0, gs, lut, ldesc, S, cf, q8,
-                                                   s_qn2);
+    scan_blocks<M, BITS, false, false, -1, EARLY, RES>(ix, a, Q, a.state + qi, P, 0, gs, lut, ldesc, S, cf, q8,
+                                                        s_qn2);
     __syncthreads();
 
     // ---- Phase C: codebook ----
     const int64_t ns = (int64_t)min((long long)S.count, (long long)Q.cap);
-    build_codebook_hist(Q.region, ns, Q.kc, a.m, S, cf, C::SHC);
+    if (RES) build_codebook(Q.region, ns, Q.kc, a.m, S, true);
+    else build_codebook_hist(Q.region, ns, Q.kc, a.m, S, cf, C::SHC);
     if (EARLY && q8) {
         // Algorithm 4: the first predicted threshold from the sample's share of S_q
         if (warp_id() == 0) {
@@ -833,8 +862,8 @@ __global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::M
         __syncthreads();
     }
     // ---- Phase D: main scan ----
-    scan_blocks<M, BITS, true, false, -1, EARLY>(ix, a, Q, a.state + qi, P, gs, S.gtot, lut, ldesc, S, nullptr, q8,
-                                                  s_qn2);
+    scan_blocks<M, BITS, true, false, -1, EARLY, RES>(ix, a, Q, a.state + qi, P, gs, S.gtot, lut, ldesc, S, nullptr,
+                                                       q8, s_qn2);
     __syncthreads();
 
     // ---- state out ----
@@ -907,7 +936,7 @@ struct SplitArgs {
     unsigned int* counter;    // work counter, zero before the launch
 };
 
-template <int M, int BITS, bool MAIN>
+template <int M, int BITS, bool MAIN, bool RES = false>
 __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan_split_kernel(DevIndex ix, ScanArgs a, SplitArgs sp, int64_t nq) {
     using C = ScanCfg<M, BITS>;
     extern __shared__ uint4 dsm[];
@@ -979,7 +1008,15 @@ __global__ void __launch_bounds__(SCAN_THREADS, ScanCfg<M, BITS>::MIN_CTAS) scan
         }
         __syncthreads();
         if (tid == 0) s_q = qi;
-        scan_blocks<M, BITS, MAIN, true>(ix, a, Q, st, nl, 0, S.gtot, lut, ldesc, S);
+        if (RES) {
+            // this part's lists start at probe rank j0
+            QCtx Qr = Q;
+            Qr.lbase = a.lbase + a.qp.poff(qi) + j0;
+            Qr.inv = a.qinv[qi];
+            scan_blocks<M, BITS, MAIN, true, -1, false, true>(ix, a, Qr, st, nl, 0, S.gtot, lut, ldesc, S);
+        } else {
+            scan_blocks<M, BITS, MAIN, true>(ix, a, Q, st, nl, 0, S.gtot, lut, ldesc, S);
+        }
         __syncthreads();
         if (MAIN && warp_id() == 0) flush_and_update(S, st, a.m, Q.kc);
     }
@@ -1003,7 +1040,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) codebook_kernel(ScanArgs a) {
     mn = __reduce_min_sync(0xFFFFFFFFu, mn);
     if (lane_id() == 0 && mn != 0xFFFFFFFFu) atomicMin(&S.dmin, mn);
     __syncthreads();
-    build_codebook(region, ns, kc, a.m, S);
+    build_codebook(region, ns, kc, a.m, S, a.lbase != nullptr);
     bins_to_buckets(S);
     for (int i = tid; i < kMaxBuckets; i += bs) st->hist[i] = i < a.m ? S.hist[i] : 0u;
     for (int i = tid; i < 256; i += bs) st->map[i] = S.bmap[i];
@@ -1569,21 +1606,37 @@ static cudaError_t launch_split_t(const DevIndex& ix, int64_t nq, const ScanArgs
     using C = ScanCfg<M, BITS>;
     const size_t smem = (size_t)C::LUT_WORDS * 4 + (size_t)a.nprobe * sizeof(int4);
     // a property of the compiled kernels (the same on every device); thread-safe initialisation
-    static const int lim = std::min(max_dyn_smem(scan_split_kernel<M, BITS, false>),
-                                    max_dyn_smem(scan_split_kernel<M, BITS, true>));
-    cudaError_t e = smem_attr_once((const void*)scan_split_kernel<M, BITS, false>, lim);
-    if (e == cudaSuccess) e = smem_attr_once((const void*)scan_split_kernel<M, BITS, true>, lim);
+    static const int lim = std::min(std::min(max_dyn_smem(scan_split_kernel<M, BITS, false>),
+                                             max_dyn_smem(scan_split_kernel<M, BITS, true>)),
+                                    std::min(max_dyn_smem(scan_split_kernel<M, BITS, false, true>),
+                                             max_dyn_smem(scan_split_kernel<M, BITS, true, true>)));
+    cudaError_t e;
+    if (ix.resid) {
+        e = smem_attr_once((const void*)scan_split_kernel<M, BITS, false, true>, lim);
+        if (e == cudaSuccess) e = smem_attr_once((const void*)scan_split_kernel<M, BITS, true, true>, lim);
+    } else {
+        e = smem_attr_once((const void*)scan_split_kernel<M, BITS, false>, lim);
+        if (e == cudaSuccess) e = smem_attr_once((const void*)scan_split_kernel<M, BITS, true>, lim);
+    }
     if (e != cudaSuccess) return e;
     if (smem > (size_t)lim) return cudaErrorInvalidValue;
     const long long items = nq * (long long)G;
     const unsigned grid = (unsigned)std::min<long long>(items, (long long)ix.num_sms * C::MIN_CTAS);
     e = cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    scan_split_kernel<M, BITS, false><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters}, nq);
+    if (ix.resid) {
+        if (!a.lbase || !a.qinv) return cudaErrorInvalidValue;
+        scan_split_kernel<M, BITS, false, true><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters}, nq);
+    } else {
+        scan_split_kernel<M, BITS, false><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters}, nq);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     codebook_kernel<<<(unsigned)nq, SCAN_THREADS, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    scan_split_kernel<M, BITS, true><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters + 1}, nq);
+    if (ix.resid)
+        scan_split_kernel<M, BITS, true, true><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters + 1}, nq);
+    else
+        scan_split_kernel<M, BITS, true><<<grid, SCAN_THREADS, smem, st>>>(ix, a, SplitArgs{G, counters + 1}, nq);
     return cudaGetLastError();
 }
 
@@ -1599,6 +1652,7 @@ static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs&
         smem = std::max(smem, kFusedSelectKeys * 8);
         a.sel.tcap = (uint32_t)(smem / 8);
     }
+    if (a.early && ix.resid) return cudaErrorInvalidValue;    // the early re-rank takes plain PQ codes
     if (a.early) {
         // Algorithm 4's early re-rank: tables of up to 64 KB (8-bit, M <= 32; 4-bit, M <= 64), d <= 256
         if constexpr (C::LUT_WORDS * 4 <= 64 * 1024 && M <= 64) {
@@ -1612,6 +1666,16 @@ static cudaError_t launch_scan_t(const DevIndex& ix, int64_t nq, const ScanArgs&
         } else {
             return cudaErrorInvalidValue;
         }
+    }
+    if (ix.resid) {
+        // residual IVF-PQ: the table sum plus the per-list base and the per-object term
+        if (!a.lbase || !a.qinv || !ix.rv) return cudaErrorInvalidValue;
+        static const int lim_r = max_dyn_smem(scan_kernel<M, BITS, false, true>);
+        cudaError_t e = smem_attr_once((const void*)scan_kernel<M, BITS, false, true>, lim_r);
+        if (e != cudaSuccess) return e;
+        if (smem > (size_t)lim_r) return cudaErrorInvalidValue;
+        scan_kernel<M, BITS, false, true><<<(unsigned)nq, C::THREADS, smem, st>>>(ix, a);
+        return cudaGetLastError();
     }
     static const int lim = max_dyn_smem(scan_kernel<M, BITS>);   // a property of the compiled kernel
     cudaError_t e = smem_attr_once((const void*)scan_kernel<M, BITS>, lim);
@@ -1637,6 +1701,7 @@ static cudaError_t launch_pair_t(const DevIndex& ix, int64_t nq, const ScanArgs&
 // The pair form runs for tables that allow two 512-thread CTAs per SM, and
 // only when its shared memory (table, list descriptors, bitmaps) still does.
 bool scan_pair_supported(const DevIndex& ix, int nprobe) {
+    if (ix.resid) return false;            // the pair form takes plain PQ codes
     int lut_words = 0;
     if (ix.bits == 8 && (ix.M == 8 || ix.M == 16 || ix.M == 32)) lut_words = 256 * 64;
     else if (ix.bits == 4 && (ix.M == 32 || ix.M == 64)) lut_words = 16 * (ix.M <= 32 ? 64 : 128);
@@ -1703,6 +1768,7 @@ static cudaError_t launch_collect_m(const DevIndex& ix, int64_t nq, const ScanAr
 
 bool scan_collect_supported(const DevIndex& ix, int mode, int nprobe, int64_t kc, uint32_t stage_cap) {
     if (mode != 1 && mode != 2) return false;
+    if (ix.resid) return false;            // the baseline collectors take plain PQ codes
     int lut_words = 0;
     if (ix.bits == 8 && (ix.M == 8 || ix.M == 16 || ix.M == 32)) lut_words = 256 * 64;
     else if (ix.bits == 4 && (ix.M == 32 || ix.M == 64)) lut_words = 16 * (ix.M <= 32 ? 64 : 128);

@@ -64,6 +64,9 @@ def small_workload(kind: str):
     elif kind == "rembed":    # residual IVF-PQ, inner product, PQ 32 x 8 bit
         x, q = embedding_shaped(12000, 24, d=64)
         idx = build_ivf_pq(x, 48, 32, 8, "ip", kmeans_iters=6, pq_iters=6, pq_sample=8000, residual=True)
+    elif kind == "rragged":   # residual IVF-PQ over few vectors, many short and empty lists
+        x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
+        idx = build_ivf_pq(x, 40, 8, 8, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700, residual=True)
     elif kind == "ragged":    # few vectors, many short and empty lists
         x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
         idx = build_ivf_pq(x, 40, 8, 8, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700)
