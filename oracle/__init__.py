@@ -46,7 +46,7 @@ class _Index(C.Structure):
                 ("M", C.c_int32), ("bits", C.c_int32),
                 ("centroids", C.c_void_p), ("list_offsets", C.c_void_p), ("ids", C.c_void_p),
                 ("codes", C.c_void_p), ("books", C.c_void_p), ("vectors", C.c_void_p),
-                ("residual", C.c_int32)]
+                ("residual", C.c_int32), ("lut_levels", C.c_int32)]
 
 
 class Codebook(C.Structure):
@@ -67,6 +67,7 @@ def lib():
             L.oracle_probe.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp]
             L.oracle_lut_f32.argtypes = [vp, vp, i32, i32, i32, i32, vp]
             L.oracle_lut16.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp]
+            L.oracle_lut_q.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp]
             L.oracle_adc.argtypes = [vp, vp, i64, i32, i32, vp]
             L.oracle_lut16_scale.restype = C.c_float
             L.oracle_lut16_scale.argtypes = [vp, vp, i32, i32, i32, i32, vp]
@@ -164,12 +165,17 @@ def lut_f32(q, books, metric="l2"):
     return out
 
 
-def lut16(q, books, metric="l2"):
-    """uint16-quantised lookup table (offset per sub-space, one scale per query)."""
+def lut16(q, books, metric="l2", levels: int = 65535):
+    """Integer-quantised lookup table (offset per sub-space, one scale per
+    query) with entries in [0, levels]: the uint16 table at 65535, the table
+    whose entries FP16 holds exactly at 2047."""
     q, b = _f32(q), _f32(books)
     M, K, ds = b.shape
     out = np.empty((M, K), dtype=np.uint16)
-    lib().oracle_lut16(_p(q), _p(b), M * ds, M, int(np.log2(K)), _metric(metric), _p(out), None)
+    if levels == 65535:
+        lib().oracle_lut16(_p(q), _p(b), M * ds, M, int(np.log2(K)), _metric(metric), _p(out), None)
+    else:
+        lib().oracle_lut_q(_p(q), _p(b), M * ds, M, int(np.log2(K)), _metric(metric), int(levels), _p(out), None)
     return out
 
 
@@ -315,12 +321,13 @@ COLLECTORS = {"sort": 0, "heap": 1, "bucket": 2}
 
 
 def search(index, queries, k: int, nprobe: int, kc: int, collector: str = "sort",
-           m: int = 64, sample_min: int = 8, with_stats: bool = False):
+           m: int = 64, sample_min: int = 8, with_stats: bool = False, lut_levels: int = 65535):
     """The whole search path for a batch of queries (single-threaded).
 
     ``index`` is a ``synth.IvfPqIndex``-like object.  Returns (ids [nq, k],
     dists [nq, k] FP64) and, with ``with_stats``, per-query stats
-    [S_q, candidates, tau, pushed].
+    [S_q, candidates, tau, pushed].  ``lut_levels`` is the integer table's
+    top level (65535: the uint16 table).
     """
     q = _f32(queries).reshape(-1, index.d)
     keep = []
@@ -334,7 +341,7 @@ def search(index, queries, k: int, nprobe: int, kc: int, collector: str = "sort"
                 arr(index.centroids, np.float32), arr(index.list_offsets, np.int64),
                 arr(index.ids, np.int64), arr(index.codes, np.uint8),
                 arr(index.codebooks, np.float32), arr(index.vectors, np.float32),
-                1 if getattr(index, "residual", False) else 0)
+                1 if getattr(index, "residual", False) else 0, int(lut_levels))
     nq = q.shape[0]
     oi = np.empty((nq, k), dtype=np.int64)
     od = np.empty((nq, k), dtype=np.float64)

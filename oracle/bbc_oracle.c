@@ -15,7 +15,9 @@
  *                         nearest first.  Ties go to the smaller list id.
  *   oracle_lut_f32/16     Section 2 "Quantization", step (1): distances from
  *                         the query to every codebook vector, per sub-space;
- *                         then the uint16 integer quantisation of the table.
+ *                         then the uint16 integer quantisation of the table
+ *                         (oracle_lut_q: the same recipe with a smaller top
+ *                         level, e.g. 2047, whose entries FP16 holds exactly).
  *   oracle_adc            step (2): estimated distance = sum over sub-spaces
  *                         of the table entry picked by the code.
  *   oracle_lut16_scale, oracle_resid_a/_base/_w/_v, oracle_adc_resid
@@ -175,11 +177,12 @@ void oracle_lut_f32(const float* q, const float* books, int32_t d, int32_t M, in
     }
 }
 
-/* uint16 table: per sub-space offset lo_m = min_j L[m][j]; one scale for the
- * query, inv = 65535 / span with span = max_m (max_j L[m][j] - lo_m);
- * entry = min(65535, floor((L - lo_m) * inv + 0.5)).  span == 0 gives zeros. */
-/* lo_m and the query's scale inv of the uint16 table from the FP32 table. */
-static float lut16_offsets(const float* lut, int32_t M, int32_t K, float* lo) {
+/* Integer table with top level T (65535 for the uint16 table): per
+ * sub-space offset lo_m = min_j L[m][j]; one scale for the query,
+ * inv = T / span with span = max_m (max_j L[m][j] - lo_m);
+ * entry = min(T, floor((L - lo_m) * inv + 0.5)).  span == 0 gives zeros. */
+/* lo_m and the query's scale inv of the integer table from the FP32 table. */
+static float lut_offsets(const float* lut, int32_t M, int32_t K, float top, float* lo) {
     float span = 0.0f;
     for (int32_t m = 0; m < M; ++m) {
         float mn = lut[(size_t)m * K], mx = mn;
@@ -192,30 +195,37 @@ static float lut16_offsets(const float* lut, int32_t M, int32_t K, float* lo) {
         float w = mx - mn;
         if (w > span) span = w;
     }
-    float inv = span > 0.0f ? 65535.0f / span : 0.0f;
+    float inv = span > 0.0f ? top / span : 0.0f;
     if (!(inv <= FLT_MAX)) inv = 0.0f;
     return inv;
 }
 
-void oracle_lut16(const float* q, const float* books, int32_t d, int32_t M, int32_t bits,
-                  int32_t metric, uint16_t* lut16, float* lut_f32_out) {
+/* The integer table with top level `levels` (1 .. 65535). */
+void oracle_lut_q(const float* q, const float* books, int32_t d, int32_t M, int32_t bits,
+                  int32_t metric, int32_t levels, uint16_t* lut16, float* lut_f32_out) {
     const int32_t K = 1 << bits;
+    const float top = (float)levels;
     float* lut = (float*)malloc(sizeof(float) * (size_t)M * K);
     float* lo = (float*)malloc(sizeof(float) * (size_t)M);
     oracle_lut_f32(q, books, d, M, bits, metric, lut);
-    const float inv = lut16_offsets(lut, M, K, lo);
+    const float inv = lut_offsets(lut, M, K, top, lo);
     for (int32_t m = 0; m < M; ++m) {
         for (int32_t j = 0; j < K; ++j) {
             float t = lut[(size_t)m * K + j] - lo[m];
             float u = t * inv;
             float v = floorf(u + 0.5f);
-            if (v > 65535.0f) v = 65535.0f;
+            if (v > top) v = top;
             lut16[(size_t)m * K + j] = (uint16_t)v;
         }
     }
     if (lut_f32_out) memcpy(lut_f32_out, lut, sizeof(float) * (size_t)M * K);
     free(lut);
     free(lo);
+}
+
+void oracle_lut16(const float* q, const float* books, int32_t d, int32_t M, int32_t bits,
+                  int32_t metric, uint16_t* lut16, float* lut_f32_out) {
+    oracle_lut_q(q, books, d, M, bits, metric, 65535, lut16, lut_f32_out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -246,7 +256,7 @@ float oracle_lut16_scale(const float* q, const float* books, int32_t d, int32_t 
     float* lut = (float*)malloc(sizeof(float) * (size_t)M * K);
     float* lo = (float*)malloc(sizeof(float) * (size_t)M);
     oracle_lut_f32(q, books, d, M, bits, metric, lut);
-    const float inv = lut16_offsets(lut, M, K, lo);
+    const float inv = lut_offsets(lut, M, K, 65535.0f, lo);
     if (lo_sum) {
         double s = 0.0;
         for (int32_t m = 0; m < M; ++m) s += (double)lo[m];
@@ -576,6 +586,7 @@ typedef struct {
     const float* books;          /* [M*2^bits*d/M] */
     const float* vectors;        /* [n*d] id order */
     int32_t residual;            /* 1: codes are PQ codes of o - c_l (residual IVF-PQ) */
+    int32_t lut_levels;          /* top level of the integer table (0: 65535) */
 } oracle_ivfpq;
 
 /* collector: 0 = sort, 1 = heap, 2 = bucket (Algorithm 1).
@@ -586,6 +597,9 @@ int oracle_search(const oracle_ivfpq* ix, const float* queries, int64_t nq, int3
                   int32_t nprobe, int64_t Kc, int32_t collector, int32_t m, int32_t sample_min,
                   int64_t* out_ids, double* out_d, int64_t* stats) {
     if (k <= 0 || nprobe < 1 || nprobe > ix->nlist || Kc < 1) return -1;
+    if (ix->lut_levels < 0 || ix->lut_levels > 65535) return -1;
+    /* the residual keys are defined on the uint16 table's scale */
+    if (ix->residual && ix->lut_levels != 0 && ix->lut_levels != 65535) return -1;
     const int32_t d = ix->d, K = 1 << ix->bits, cb = ix->M * ix->bits / 8;
     int32_t* lists = (int32_t*)malloc(sizeof(int32_t) * (size_t)nprobe);
     uint16_t* lut = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)ix->M * K);
@@ -603,7 +617,8 @@ int oracle_search(const oracle_ivfpq* ix, const float* queries, int64_t nq, int3
     for (int64_t qi = 0; qi < nq; ++qi) {
         const float* q = queries + (size_t)qi * d;
         oracle_probe(q, ix->centroids, ix->nlist, d, ix->metric, nprobe, lists, NULL);
-        oracle_lut16(q, ix->books, d, ix->M, ix->bits, ix->metric, lut, NULL);
+        oracle_lut_q(q, ix->books, d, ix->M, ix->bits, ix->metric, ix->lut_levels > 0 ? ix->lut_levels : 65535,
+                     lut, NULL);
         const float inv = ix->residual ? oracle_lut16_scale(q, ix->books, d, ix->M, ix->bits, ix->metric, NULL)
                                        : 0.0f;
         int64_t sq = 0;

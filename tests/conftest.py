@@ -40,6 +40,12 @@ def small_workload(kind: str):
     elif kind == "sift4":     # same data, PQ 64 x 4 bit
         x, q = sift_shaped(12000, 24, d=128, n_centers=300)
         idx = build_ivf_pq(x, 64, 64, 4, "l2", kmeans_iters=6, pq_iters=6, pq_sample=8000)
+    elif kind == "sift4m32":  # same data, PQ 32 x 4 bit (M = d / 4, the paper's PQ setting)
+        x, q = sift_shaped(12000, 24, d=128, n_centers=300)
+        idx = build_ivf_pq(x, 64, 32, 4, "l2", kmeans_iters=6, pq_iters=6, pq_sample=8000)
+    elif kind == "embed4":    # unit norm, inner product, PQ 16 x 4 bit
+        x, q = embedding_shaped(12000, 24, d=64)
+        idx = build_ivf_pq(x, 48, 16, 4, "ip", kmeans_iters=6, pq_iters=6, pq_sample=8000)
     elif kind == "embed":     # unit norm, inner product, PQ 32 x 8 bit
         x, q = embedding_shaped(12000, 24, d=64)
         idx = build_ivf_pq(x, 48, 32, 8, "ip", kmeans_iters=6, pq_iters=6, pq_sample=8000)

@@ -78,25 +78,62 @@ def test_lut_sum_equals_distance_to_reconstruction(oracle_lib, kind):
         np.testing.assert_allclose(est, ref, rtol=0, atol=1e-5 * scale)
 
 
-@pytest.mark.parametrize("kind", ["tiny", "sift", "sift4", "embed"])
-def test_uint16_table_within_rounding_bound(oracle_lib, kind):
-    """ADC over the uint16 table equals the FP32 table sum minus sum(lo_m),
-    rescaled, within M half-steps of the quantiser."""
+@pytest.mark.parametrize("levels", [65535, 2047])
+@pytest.mark.parametrize("kind", ["tiny", "sift", "sift4", "sift4m32", "embed"])
+def test_uint16_table_within_rounding_bound(oracle_lib, kind, levels):
+    """ADC over the integer table equals the FP32 table sum minus sum(lo_m),
+    rescaled, within M half-steps of the quantiser (top level 65535: the
+    uint16 table; 2047: the table whose entries FP16 holds exactly)."""
     from synth.index import unpack_codes
     idx, q = small_workload(kind)
     un = unpack_codes(idx.codes[:2000], idx.pq_m, idx.pq_bits)
     for qi in range(4):
         lut = oracle_lib.lut_f32(q[qi], idx.codebooks, idx.metric).astype(np.float64)
-        t16 = oracle_lib.lut16(q[qi], idx.codebooks, idx.metric)
-        assert t16.dtype == np.uint16 and t16.max() <= 65535
+        t16 = oracle_lib.lut16(q[qi], idx.codebooks, idx.metric, levels=levels)
+        assert t16.dtype == np.uint16 and t16.max() <= levels
         lo = lut.min(axis=1)
         span = (lut.max(axis=1) - lo).max()
-        assert (t16.max(axis=1) == 65535).any()             # the widest sub-space fills the range
+        assert (t16.max(axis=1) == levels).any()            # the widest sub-space fills the range
         assert (t16.min(axis=1) == 0).all()                 # offsets remove the minimum
         e = oracle_lib.adc(t16, idx.codes[:2000], idx.pq_m, idx.pq_bits).astype(np.float64)
         exact = (lut[np.arange(idx.pq_m)[None, :], un] - lo[None, :]).sum(axis=1)
-        step = span / 65535.0
+        step = span / levels
         assert np.abs(e * step - exact).max() <= idx.pq_m * 0.5 * step * 1.001 + 1e-6 * span
+
+
+def test_table_levels_rescale_the_same_entries(oracle_lib):
+    """The 2047-level table is the 65535-level recipe at a coarser step: each
+    entry is the FP32 value's nearest level, so rescaled it lies within one
+    coarse step (plus the FP32 rounding of the scale) of the fine table's."""
+    idx, q = small_workload("sift4")
+    for qi in range(6):
+        fine = oracle_lib.lut16(q[qi], idx.codebooks, idx.metric).astype(np.float64)
+        coarse = oracle_lib.lut16(q[qi], idx.codebooks, idx.metric, levels=2047).astype(np.float64)
+        assert np.abs(coarse * (65535.0 / 2047.0) - fine).max() <= 65535.0 / 2047.0 * 0.5 + 1.0
+
+
+@pytest.mark.parametrize("kind", ["sift4", "sift4m32", "embed4"])
+def test_fp16_holds_the_2047_level_table_and_its_sums(oracle_lib, kind):
+    """Why 2047 levels: FP16 has an 11-bit significand, so every integer in
+    [0, 2048] is exact, and a product with 0 or 1 is exact; the sum of M such
+    entries stays below 2^24, where every FP32 partial sum of integers is
+    exact in any order.  So an FP16 x FP16 -> FP32 contraction of one-hot
+    code rows with this table returns the integer ADC sum exactly."""
+    from synth.index import unpack_codes
+    idx, q = small_workload(kind)
+    un = unpack_codes(idx.codes[:1500], idx.pq_m, idx.pq_bits)
+    for qi in range(3):
+        t = oracle_lib.lut16(q[qi], idx.codebooks, idx.metric, levels=2047)
+        assert np.array_equal(t.astype(np.float16).astype(np.uint16), t)
+        assert idx.pq_m * 2047 < 2 ** 24
+        # the contraction in float32 with a shuffled summation order
+        rng = np.random.default_rng(qi)
+        order = rng.permutation(idx.pq_m)
+        acc = np.zeros(len(un), dtype=np.float32)
+        for m in order:
+            acc = acc + t[m][un[:, m]].astype(np.float16).astype(np.float32)
+        e = oracle_lib.adc(t, idx.codes[:1500], idx.pq_m, idx.pq_bits)
+        assert np.array_equal(acc.astype(np.uint32), e)
 
 
 def test_adc_is_sum_of_selected_entries_4bit_nibbles(oracle_lib):
@@ -231,6 +268,11 @@ def test_search_collectors_agree_and_pad(oracle_lib):
     idx, q = small_workload("sift")
     a = oracle_lib.search(idx, q[:6], 200, 8, 400, "sort")
     b = oracle_lib.search(idx, q[:6], 200, 8, 400, "bucket", m=64)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # the same on the 2047-level table (coarser keys, more ties)
+    idx4, q4 = small_workload("sift4")
+    a = oracle_lib.search(idx4, q4[:6], 200, 8, 400, "sort", lut_levels=2047)
+    b = oracle_lib.search(idx4, q4[:6], 200, 8, 400, "bucket", m=64, lut_levels=2047)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     # more results requested than objects scanned: padded with (-1, inf)
     idx2, q2 = small_workload("ragged")
