@@ -65,6 +65,9 @@ def parse():
                    help="Algorithm 4's early re-rank: 1 on, 0 off; a comma list prints one line per value")
     p.add_argument("--residual", action="store_true",
                    help="residual IVF-PQ: the PQ codes quantise each vector's residual to its list centroid")
+    p.add_argument("--scan-tc", default="0",
+                   help="1 = list-grouped scan on the tensor cores (4-bit codes, 2047-level tables); "
+                        "a comma list prints one line per value")
     p.add_argument("--pair", default="0",
                    help="scan schedule: 1 two queries per CTA (pair form), 0 one; a comma list prints one line per value")
     p.add_argument("--cpu-queries", type=int, default=200, help="oracle sample for cpu_baseline")
@@ -415,8 +418,11 @@ def main():
     pairs = [int(v) for v in str(args.pair).split(",")]
     collectors = [int(v) for v in str(args.collector).split(",")]
     earlys = [int(v) for v in str(args.early_rerank).split(",")]
+    tcs = [int(v) for v in str(args.scan_tc).split(",")]
     if args.mixed_k:
         index.set(kc_ratio=ratios[0], buckets=buckets[0], pair=pairs[0])
+        if tcs[0]:
+            index.set(scan_tc=1)
         if scales[0] is not None:
             index.set(bound_scale=scales[0], estimator=ests[0])
         measure_mixed(args, ws, rank, local, bbc, index, w, idx, q, t_build, xt, precs[0], ratios[0])
@@ -431,13 +437,17 @@ def main():
                             for pair in pairs:
                                 for coll in collectors:
                                     for early in earlys:
-                                        index.set(kc_ratio=ratio, buckets=m, pair=pair, collector=coll)
-                                        if early != index.get("early_rerank"):
-                                            index.set(early_rerank=early)
-                                        if scale is not None:
-                                            index.set(bound_scale=scale, estimator=est)
-                                        measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build, xt,
-                                                prec, ratio, m)
+                                        for tc in tcs:
+                                            index.set(kc_ratio=ratio, buckets=m, pair=pair, collector=coll)
+                                            if early != index.get("early_rerank"):
+                                                index.set(early_rerank=early)
+                                            if scale is not None:
+                                                index.set(bound_scale=scale, estimator=est)
+                                            index.set(scan_tc=tc)
+                                            if not tc:
+                                                index.set(lut_levels=65535)
+                                            measure(args, ws, rank, local, bbc, index, w, idx, q, k, npb, t_build,
+                                                    xt, prec, ratio, m)
     index.close()
 
 
@@ -609,7 +619,8 @@ def measure_mixed(args, ws, rank, local, bbc, index, w, idx, q, t_build, xt, pre
         cpu, cpu_mt = cpu_baselines(args, idx, q, ks, ps, kc_ratio=ratio,
                                     scale=index.get("bound_scale") if is_sign else None,
                                     estimator=int(index.get("estimator")) if is_sign else 0,
-                                    eps0=index.get("epsilon0") if is_sign else 1.9)
+                                    eps0=index.get("epsilon0") if is_sign else 1.9,
+                                    lut_levels=65535 if is_sign else int(index.get("lut_levels")))
     if rank == 0:
         per = {s_: stage_ms[s_] / args.steps for s_ in stage_ms}
         out = {
@@ -767,6 +778,12 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
         "prec_classify": ("hbm", nq * kc * 8 * 5 / 1e9, "GB/s", peaks["hbm_gbs"]),
         "prec_recheck": ("hbm", unc * (idx.d * 4 + 16) / 1e9, "GB/s", peaks["hbm_gbs"]),
     }
+    tc = bool(index.get("scan_tc")) if not is_sign else False
+    if tc:
+        # the one-hot contraction: 2 x 16 M flops per (query, scanned object) pair (K = 16 M table
+        # entries), FP16 operands, FP32 accumulation; FP16 and BF16 share the dense tensor rate
+        work["scan"] = ("tensor", float(s_q.double().sum()) * 2.0 * 16 * idx.pq_m / 1e12, "TFLOP/s",
+                        peaks["bf16_tflops"])
     if is_sign:
         # codes (d/8 bytes) + factors (16 bytes) per scanned object; rows of the exact re-rank
         work["scan"] = ("hbm", float(s_q.double().sum()) * (idx.d // 8 + 16) / 1e9, "GB/s", peaks["hbm_gbs"])
@@ -787,15 +804,20 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
             "peak_source": (f"152 SMs x 32 four-byte shared-memory lookups per clock x {sm_clk:.0f} MHz "
-                            "(median SM clock sampled during the timed region)") if dom == "scan"
+                            "(median SM clock sampled during the timed region)") if dom == "scan" and not tc
             else "MEASURED_PEAKS.json (measured copy / cuBLAS BF16 burst)"}
+    if tc and "scan" in per:
+        # the same scan as table lookups per second, beside the SIMT scan's shared-memory lookup peak
+        roof["scan_lookup_rate"] = {"achieved": lookups / 1e9 / (per["scan"] / 1e3), "unit": "Glookup/s",
+                                    "simt_lookup_peak": SMS * LOOKUPS_PER_SM_CLK * sm_clk * 1e6 / 1e9}
 
     cpu, cpu_mt = None, None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, cpu_mt = cpu_baselines(args, idx, q, [k] * nq, [nprobe] * nq, kc_ratio=ratio,
                                     scale=index.get("bound_scale") if is_sign else None,
                                     estimator=int(index.get("estimator")) if is_sign else 0,
-                                    eps0=index.get("epsilon0") if is_sign else 1.9)
+                                    eps0=index.get("epsilon0") if is_sign else 1.9,
+                                    lut_levels=65535 if is_sign else int(index.get("lut_levels")))
 
     if rank == 0:
         rerank = ["u8-exact" if u8 else "f32", "bf16-prefilter", "fp8e4m3-prefilter"][prec]
@@ -807,14 +829,17 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": ("1-bit codes x 4-bit query planes (AND+POPC), f32 bounds, f32 re-rank (f64 at ties)" if is_sign
-                      else "u16/u32 ADC, " + {0: "f32 re-rank", 1: "bf16+f32 re-rank (f64 at ties)",
-                                              2: "e4m3+f32 re-rank (f64 at ties)"}[prec]),
+                      else ("f16 one-hot x f16 table (integers <= 2047) -> f32 ADC, " if tc else "u16/u32 ADC, ") +
+                      {0: "f32 re-rank", 1: "bf16+f32 re-rank (f64 at ties)",
+                       2: "e4m3+f32 re-rank (f64 at ties)"}[prec]),
             "data": "synthetic",
             "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "metric_space": idx.metric,
                        "pq": pq_desc(idx), "nq": nq, "k": k,
                        "nprobe": nprobe, "kc": None if is_sign else kc,
                        "kc_ratio": ratio, "buckets": m, "rerank": rerank,
-                       "scan_schedule": "pair" if index.get("pair") else "one query per CTA",
+                       "scan_schedule": ("list-grouped, tensor cores" if tc else
+                                         "pair" if index.get("pair") else "one query per CTA"),
+                       "lut_levels": int(index.get("lut_levels")),
                        "collector": ["result buffer", "lazy linear buffer", "binary heap"][int(index.get("collector"))],
                        "early_rerank": bool(index.get("early_rerank")),
                        "recall_at_k": rec_mean, "recall_at_k_min": rec_min, "recall_queries": nrec,
@@ -850,7 +875,7 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     torch.cuda.empty_cache()
 
 
-def cpu_baselines(args, idx, q, ks, ps, kc_ratio=None, scale=None, estimator=0, eps0=1.9):
+def cpu_baselines(args, idx, q, ks, ps, kc_ratio=None, scale=None, estimator=0, eps0=1.9, lut_levels=65535):
     """The oracle, as it stands, timed on the host: single-threaded on the first
     --cpu-queries queries, and on all host cores over a larger sample split
     across threads (ctypes releases the interpreter lock during the C call, so
@@ -884,7 +909,7 @@ def cpu_baselines(args, idx, q, ks, ps, kc_ratio=None, scale=None, estimator=0, 
                 oracle.sign_search(idx, q[ii], k, p, scale=scale, codes=prep[0], fac=prep[1], eps=seps,
                                    estimator=estimator, eps0=eps0)
             else:
-                oracle.search(idx, q[ii], k, p, kc_of(k), "sort")
+                oracle.search(idx, q[ii], k, p, kc_of(k), "sort", lut_levels=lut_levels)
 
     n1 = min(args.cpu_queries, nq)
     sel1 = list(range(n1))

@@ -215,6 +215,26 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  reported distances of members placed by the copy's bound
  *                  are the copy's scores (see bbc_rerank_bounds).  Applies when
  *                  the exact u8 re-rank is not in use.
+ *   "lut_levels"   top level T of the integer lookup tables (step S3): entry =
+ *                  min(T, floor((L - lo_m) T / span + 0.5)), 1..65535.
+ *                  Default 65535 (the uint16 table).
+ *   "scan_tc"      1 = the list-grouped form of the scan on the tensor cores
+ *                  (plain, not residual, 4-bit PQ with pq_m = 32, 64 or 128;
+ *                  buckets <= 64): a batch's (query, probed list) pairs
+ *                  are grouped by list on the device, and a CTA stages a tile
+ *                  of 256 code rows of one list once, as one-hot FP16 rows,
+ *                  for up to 128 of the queries that probe it; tcgen05.mma
+ *                  contracts them with the queries' tables (FP32
+ *                  accumulation in tensor memory), and the result buffer's
+ *                  Push runs on the accumulators.  Setting 1 lowers
+ *                  "lut_levels" to 2047 when it is larger: such entries are
+ *                  integers FP16 holds exactly and every sum of them stays
+ *                  below 2^24, so the estimated distances equal the integer
+ *                  table sums and the candidates equal those of the one-query
+ *                  scan on the same table.  Applies with the result buffer
+ *                  ("collector" 0) and without "early_rerank"; a search whose
+ *                  index or buckets do not fit returns BBC_ERR_UNSUPPORTED.
+ *                  Default 0.
  *   "region_cap"   entries of each query's collector region (the buffer the
  *                  scan appends (estimated distance, position) pairs to).
  *                  0 (default) = the total length of the nprobe longest lists,

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbbc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["api.cu", "k_probe.cu", "k_lut.cu", "k_scan.cu", "k_select.cu", "k_rerank.cu", "k_prec.cu", "k_sign.cu", "collect_static.cu", "k_probe_tc.cu", "serve.cu", "k_pair.cu"]
+SOURCES = ["api.cu", "k_probe.cu", "k_lut.cu", "k_scan.cu", "k_select.cu", "k_rerank.cu", "k_prec.cu", "k_sign.cu", "collect_static.cu", "k_probe_tc.cu", "serve.cu", "k_pair.cu", "k_scan_tc.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -138,17 +138,20 @@ struct bbc_index {
     uint32_t* lo_norms = nullptr;               // and their squared norms
     unsigned long long* early_totals = nullptr; // [2] objects scored early, early distances used
     int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
+    int lut_levels = 65535;   // top level of the integer lookup tables
+    int scan_tc = 0;          // 1: list-grouped scan on the tensor cores (4-bit codes; tables <= 2047)
     bool capturing = false;
     struct GraphKey {
         const void* q; int64_t nq; int k; int nprobe; void* oi; void* od; cudaStream_t st;
         double kc_ratio; int buckets, sample_lists, split, probe_gemm, rerank, prec;
         int64_t rcap;
-        int pair, collector, early;
+        int pair, collector, early, lut_levels, scan_tc;
         bool operator<(const GraphKey& o) const {
             return std::tie(q, nq, k, nprobe, oi, od, st, kc_ratio, buckets, sample_lists, split, probe_gemm, rerank,
-                            prec, rcap, pair, collector, early) <
+                            prec, rcap, pair, collector, early, lut_levels, scan_tc) <
                    std::tie(o.q, o.nq, o.k, o.nprobe, o.oi, o.od, o.st, o.kc_ratio, o.buckets, o.sample_lists, o.split,
-                            o.probe_gemm, o.rerank, o.prec, o.rcap, o.pair, o.collector, o.early);
+                            o.probe_gemm, o.rerank, o.prec, o.rcap, o.pair, o.collector, o.early, o.lut_levels,
+                            o.scan_tc);
         }
     };
     struct GraphEntry { cudaGraphExec_t exec; int64_t launches; };
@@ -217,13 +220,14 @@ struct ChunkShape {
 struct Plan {
     int64_t chunk;        // queries per chunk (uniform batches)
     int64_t chunk_slots;  // candidate slots of a mixed chunk (sum of K_c)
+    int64_t chunk_probe;  // probe lists of a mixed chunk (sum of nprobe)
     int nprobe;
     int64_t kc;
     int k;
     int64_t cap;
     size_t off_scores, off_probe, off_lut, off_state, off_region, off_cand, off_count, off_cdist,
         off_q, off_ids, off_dists, off_abf, off_keys, off_params, off_counters, off_prec, off_pair, off_rdist,
-        off_cearly, off_qinv, off_lbase, total;
+        off_cearly, off_qinv, off_lbase, off_lutf16, off_tcplan, total;
 };
 
 // The precision re-rank runs when a low-precision copy exists and the exact u8
@@ -285,6 +289,11 @@ bool early_active(const bbc_index* ix) {
            ix->collector == 0;
 }
 
+// The tensor-core list-grouped scan runs when asked for, on plain 4-bit PQ
+// codes with the result buffer (not a baseline collector or the early
+// re-rank); the tables then have top level lut_levels <= 2047.
+bool tc_active(const bbc_index* ix) { return ix->scan_tc && ix->collector == 0 && !early_active(ix); }
+
 constexpr int64_t kTopkSmemMax = 16384;     // K_c handled by the shared-memory top-k
 constexpr int64_t kMaxChunkQueries = 65535;  // queries per launch (some grids index queries in y)
 
@@ -313,6 +322,9 @@ size_t layout(const bbc_index* ix, const ChunkShape& c, Plan& p) {
     p.off_cearly = o; o = align_up(o + (early ? (size_t)c.sum_kc * 4 : 0));
     p.off_qinv = o; o = align_up(o + (d.resid ? (size_t)c.nq * 4 : 0));
     p.off_lbase = o; o = align_up(o + (d.resid ? (size_t)c.sum_probe * 4 : 0));
+    const bool tc = tc_active(ix);
+    p.off_lutf16 = o; o = align_up(o + (tc ? (size_t)c.nq * d.M * d.K * 2 : 0));
+    p.off_tcplan = o; o = align_up(o + (tc ? scan_tc_plan_bytes(d, c.sum_probe) : 0));
     p.total = o;
     return o;
 }
@@ -449,7 +461,9 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
     }
     if (stop_after <= 2) return BBC_OK;
     float* qinv = d.resid ? reinterpret_cast<float*>(ws + p.off_qinv) : nullptr;
-    CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(d, q, nc, lut, st, qinv); }));
+    const bool tc = tc_active(ix);
+    uint16_t* lutf16 = tc ? reinterpret_cast<uint16_t*>(ws + p.off_lutf16) : nullptr;
+    CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(d, q, nc, lut, st, qinv, ix->lut_levels, lutf16); }));
     ScanArgs sa{lut, probe_in ? probe_in : probe, p.nprobe, p.kc, ix->buckets, ix->sample_lists,
                 region, p.cap, state, qp, 0, SelectArgs{}};
     if (d.resid) {
@@ -465,7 +479,18 @@ int run_chunk(bbc_index* ix, const Plan& p, char* ws, const float* q, int64_t nc
         const int64_t slots = 4ll * 2 * d.num_sms;
         if (nc < slots) G = (int)std::min<int64_t>((slots + nc - 1) / nc, std::max(1, p.nprobe));
     }
-    if (ix->collector) {
+    if (tc) {
+        // list-grouped form on the tensor cores: pairs grouped by list, sample pass,
+        // codebooks, main pass; the selection follows as its own kernel
+        if (!scan_tc_supported(d, ix->buckets) || ix->lut_levels > 2047)
+            return fail(BBC_ERR_UNSUPPORTED, "scan_tc: needs plain 4-bit PQ codes (M = 32, 64 or 128), "
+                        "buckets <= 64 and lut_levels <= 2047");
+        const int64_t sum_probe = qp.probe_off ? p.chunk_probe : nc * (int64_t)p.nprobe;
+        CUDA_TRY(cudaMemsetAsync(state, 0, (size_t)nc * sizeof(bbc_collector_state), st));
+        CUDA_TRY(stage(ix, 3, st, [&] {
+            return launch_scan_tc(d, nc, sa, lutf16, ws + p.off_tcplan, sum_probe, st);
+        }));
+    } else if (ix->collector) {
         // a baseline collector in place of the result buffer: it writes the candidates itself
         const uint32_t stage_cap = (uint32_t)((ix->info.max_list_len + 31) / 32 * 32);
         if (!scan_collect_supported(d, ix->collector, p.nprobe, p.kc, stage_cap))
@@ -1384,6 +1409,18 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
     } else if (k == "pair") {
         if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "pair must be 0 (one query per CTA) or 1 (two)");
         ix->pair = (int)v;
+    } else if (k == "lut_levels") {
+        if (!(v >= 1 && v <= 65535) || v != std::floor(v)) return fail(BBC_ERR_ARG, "lut_levels must be an integer in [1, 65535]");
+        if (ix->scan_tc && v > 2047) return fail(BBC_ERR_ARG, "lut_levels must be <= 2047 while scan_tc is 1");
+        ix->lut_levels = (int)v;
+    } else if (k == "scan_tc") {
+        if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "scan_tc must be 0 or 1");
+        if (v == 1 && ix->dev.quant != 0) return fail(BBC_ERR_UNSUPPORTED, "scan_tc: PQ indexes only");
+        if (v == 1 && !scan_tc_supported(ix->dev, 2))
+            return fail(BBC_ERR_UNSUPPORTED, "scan_tc: needs plain 4-bit PQ codes with M = 32, 64 or 128");
+        ix->scan_tc = (int)v;
+        // the tensor cores take tables whose entries FP16 holds exactly
+        if (v == 1 && ix->lut_levels > 2047) ix->lut_levels = 2047;
     } else if (k == "region_cap") {
         if (!(v >= 0 && v <= 9.0e15) || v != std::floor(v)) return fail(BBC_ERR_ARG, "region_cap must be 0 (automatic) or a positive integer");
         ix->region_cap = (int64_t)v;
@@ -1414,6 +1451,8 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "pair") *v = ix->pair;
     else if (k == "collector") *v = ix->collector;
     else if (k == "early_rerank") *v = ix->early_rerank;
+    else if (k == "lut_levels") *v = ix->lut_levels;
+    else if (k == "scan_tc") *v = ix->scan_tc;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -1443,7 +1482,8 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     // CUDA graph of the whole launch sequence for this call shape
     bbc_index::GraphKey key{queries, nq, k, nprobe, out_ids, out_dists, st, ix->kc_ratio, ix->buckets,
                             ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8, ix->dev.prec,
-                            ix->region_cap, ix->pair, ix->collector, ix->early_rerank};
+                            ix->region_cap, ix->pair, ix->collector, ix->early_rerank, ix->lut_levels,
+                            ix->scan_tc};
     std::lock_guard<std::mutex> lk(ix->graph_mu);
     auto it = ix->graph_cache.find(key);
     if (it == ix->graph_cache.end()) {
@@ -1558,6 +1598,7 @@ int bbc_search_ex(bbc_index* ix, const float* queries, int64_t nq, const int32_t
         p.nprobe = sh.max_probe;
         p.kc = sh.max_kc;
         p.chunk_slots = sh.sum_kc;
+        p.chunk_probe = sh.sum_probe;
         p.k = maxk;
         p.cap = maxcap;
         rc = run_chunk(ix, p, ws, queries + q0 * ix->dev.d, nc, out_ids + out_base, out_dists + out_base, st, 9,
@@ -1819,7 +1860,7 @@ int bbc_lut(bbc_index* ix, const float* queries, int64_t nq, uint16_t* out_lut16
     if (nq == 0) return BBC_OK;
     DeviceGuard g(ix->device);
     cudaStream_t st = (cudaStream_t)stream;
-    CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(ix->dev, queries, nq, out_lut16, st); }));
+    CUDA_TRY(stage(ix, 2, st, [&] { return launch_lut16(ix->dev, queries, nq, out_lut16, st, nullptr, ix->lut_levels); }));
     return BBC_OK;
 }
 
@@ -2040,6 +2081,7 @@ const DevIndex& index_dev(const bbc_index* ix) { return ix->dev; }
 int index_device(const bbc_index* ix) { return ix->device; }
 int64_t index_cap(const bbc_index* ix, int nprobe) { return ix->cap_for(nprobe); }
 int index_buckets(const bbc_index* ix) { return ix->buckets; }
+int index_lut_levels(const bbc_index* ix) { return ix->lut_levels; }
 int index_sample_lists(const bbc_index* ix) { return ix->sample_lists; }
 int64_t index_kc(const bbc_index* ix, int k) { return kc_for(ix, k); }
 }  // namespace bbc

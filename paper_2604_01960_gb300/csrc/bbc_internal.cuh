@@ -147,10 +147,12 @@ cudaError_t launch_probe_scores_tc(const DevIndex& ix, const float* q, int64_t n
 // tc = 1 when the scores come from the tensor-core GEMM (wider error bound).
 cudaError_t launch_probe_select(const DevIndex& ix, const float* q, int64_t nq, const QueryParams& qp,
                                 int max_nprobe, const float* scores, int32_t* lists, int tc, cudaStream_t st);
-// S3: uint16 PQ lookup tables [nq][M][K]; inv (may be null): each query's
-// scale 65535 / span, the table's integer units per unit of distance.
+// S3: uint16 PQ lookup tables [nq][M][K] with entries in [0, levels]; inv
+// (may be null): each query's scale levels / span, the table's integer units
+// per unit of distance; lut_f16 (may be null, levels <= 2048): the same
+// entries as FP16 bit patterns.
 cudaError_t launch_lut16(const DevIndex& ix, const float* q, int64_t nq, uint16_t* lut16,
-                         cudaStream_t st, float* inv = nullptr);
+                         cudaStream_t st, float* inv = nullptr, int levels = 65535, uint16_t* lut_f16 = nullptr);
 // Residual IVF-PQ, per (query, probed list): base = 2^30 + rint(clamp(A_ql *
 // inv_q, +-2^29)), A_ql = ||c_l||^2 - 2 <q, c_l> (L2) or -<q, c_l> (IP) in FP32
 // (fused multiply-adds over ascending dimension); packed like the probe lists
@@ -226,6 +228,21 @@ cudaError_t launch_scan_collect(const DevIndex& ix, int64_t nq, const ScanArgs& 
 size_t pair_plan_bytes(int64_t nq);
 cudaError_t launch_pair_plan(const float* q, int d, int64_t nq, const QueryParams& qp, const int32_t* lists,
                              void* scratch, int32_t* perm, cudaStream_t st);
+
+// The codebook of each query from its sampled objects at the start of its
+// region (state: pushed = sample size), with bucket counts and tau.
+cudaError_t launch_codebook(int64_t nq, const ScanArgs& a, cudaStream_t st);
+
+// List-grouped form on the tensor cores (k_scan_tc.cu): 4-bit codes, tables
+// with entries <= 2047 given as FP16 (lut_f16 [nq][16 M]), plain PQ, m <=
+// 64 buckets.  Same state and region contents (up to order) as the one-query
+// scan on the same table; the state array must be zeroed first; scratch
+// holds scan_tc_plan_bytes(ix, sum of nprobe) bytes.  The selection (S7)
+// runs after it.
+bool scan_tc_supported(const DevIndex& ix, int m);
+size_t scan_tc_plan_bytes(const DevIndex& ix, int64_t sum_probe);
+cudaError_t launch_scan_tc(const DevIndex& ix, int64_t nq, const ScanArgs& a, const uint16_t* lut_f16,
+                           void* scratch, int64_t sum_probe, cudaStream_t st);
 
 // S7: exact threshold bucket, compaction, top-s of the threshold bucket.
 cudaError_t launch_select(const DevIndex& ix, int64_t nq, const SelectArgs& a, cudaStream_t st);
@@ -362,5 +379,6 @@ const DevIndex& index_dev(const bbc_index* ix);
 int index_device(const bbc_index* ix);
 int64_t index_cap(const bbc_index* ix, int nprobe);
 int index_buckets(const bbc_index* ix);
+int index_lut_levels(const bbc_index* ix);
 int index_sample_lists(const bbc_index* ix);
 }  // namespace bbc

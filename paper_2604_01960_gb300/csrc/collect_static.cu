@@ -106,7 +106,7 @@ extern "C" int bbc_collect_static(bbc_index* ix, const float* queries, int64_t n
         int32_t* lbase = d.resid ? reinterpret_cast<int32_t*>(rp + align256((size_t)nq * 4)) : nullptr;
         cudaStream_t st = (cudaStream_t)stream;
         const QueryParams qp = uniform_params(nprobe, kc, 1, cap);
-        e = launch_lut16(d, queries, nq, lut, st, qinv);
+        e = launch_lut16(d, queries, nq, lut, st, qinv, index_lut_levels(ix));
         if (e == cudaSuccess && d.resid) e = launch_resid_base(d, queries, nq, qp, nprobe, probe_lists, qinv, lbase, st);
         if (e == cudaSuccess) {
             ScanArgs sa{lut, probe_lists, nprobe, kc, index_buckets(ix), index_sample_lists(ix), region, cap, state, qp};

@@ -6,9 +6,12 @@
 //                         -(sum_i q_i * y_{m,j,i})           (IP)
 //               with one rounding per operation (no fused multiply-add);
 // offsets       lo_m = min_j L[m][j];
-// scale         span = max_m (max_j L[m][j] - lo_m), inv = 65535 / span
+// scale         span = max_m (max_j L[m][j] - lo_m), inv = T / span
 //               (0 when span is 0 or the quotient overflows);
-// uint16 entry  min(65535, floor((L[m][j] - lo_m) * inv + 0.5)).
+// uint16 entry  min(T, floor((L[m][j] - lo_m) * inv + 0.5)),
+// with top level T = 65535, or a smaller T chosen by the caller: at T = 2047
+// every entry is an integer FP16 holds exactly, which the tensor-core scan
+// (k_scan_tc.cu) uses; the kernel then also writes the entries as FP16.
 // The per-query constant sum_m lo_m does not change any order and is dropped.
 //
 // Residual IVF-PQ (the codes quantise o - c_l, y their reconstruction): the
@@ -24,6 +27,8 @@
 // 2^30 keeps every key positive and the clamps keep it below 2^31.
 #include <cfloat>
 
+#include <cuda_fp16.h>
+
 #include "bbc_internal.cuh"
 #include "dev_util.cuh"
 
@@ -32,7 +37,8 @@ namespace bbc {
 constexpr int LUT_THREADS = 256;
 
 __global__ void __launch_bounds__(LUT_THREADS) lut16_kernel(DevIndex ix, const float* __restrict__ q,
-                                                             uint16_t* __restrict__ out, float* __restrict__ inv_out) {
+                                                             uint16_t* __restrict__ out, float* __restrict__ inv_out,
+                                                             float top, uint16_t* __restrict__ out_f16) {
     extern __shared__ float lsm[];
     const int M = ix.M, K = ix.K, ds = ix.dsub, d = ix.d;
     float* lut = lsm;                 // [M*K]
@@ -81,27 +87,30 @@ __global__ void __launch_bounds__(LUT_THREADS) lut16_kernel(DevIndex ix, const f
     __syncthreads();
     float span = 0.f;
     for (int m = 0; m < M; ++m) span = wid[m] > span ? wid[m] : span;
-    float inv = span > 0.f ? __fdiv_rn(65535.0f, span) : 0.f;
+    float inv = span > 0.f ? __fdiv_rn(top, span) : 0.f;
     if (!(inv <= FLT_MAX)) inv = 0.f;
     if (inv_out && threadIdx.x == 0) inv_out[qi] = inv;
     uint16_t* o = out + qi * MK;
+    uint16_t* oh = out_f16 ? out_f16 + qi * MK : nullptr;
     for (int e = threadIdx.x; e < MK; e += blockDim.x) {
         const int m = e / K;
         float t = __fsub_rn(lut[e], lo[m]);
         float u = __fmul_rn(t, inv);
         float v = floorf(__fadd_rn(u, 0.5f));
-        v = v > 65535.f ? 65535.f : v;
+        v = v > top ? top : v;
         o[e] = (uint16_t)v;
+        if (oh) oh[e] = __half_as_ushort(__float2half_rn(v));    // exact for v <= 2048
     }
 }
 
 cudaError_t launch_lut16(const DevIndex& ix, const float* q, int64_t nq, uint16_t* lut16,
-                         cudaStream_t st, float* inv) {
+                         cudaStream_t st, float* inv, int levels, uint16_t* lut_f16) {
     if (nq <= 0) return cudaSuccess;
+    if (levels < 1 || levels > 65535 || (lut_f16 && levels > 2048)) return cudaErrorInvalidValue;
     size_t smem = sizeof(float) * ((size_t)ix.M * ix.K + ix.d + 2 * ix.M);
     cudaError_t e = smem_attr_once((const void*)lut16_kernel, 200 * 1024);
     if (e != cudaSuccess) return e;
-    lut16_kernel<<<(unsigned)nq, LUT_THREADS, smem, st>>>(ix, q, lut16, inv);
+    lut16_kernel<<<(unsigned)nq, LUT_THREADS, smem, st>>>(ix, q, lut16, inv, (float)levels, lut_f16);
     return cudaGetLastError();
 }
 

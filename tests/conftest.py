@@ -43,9 +43,9 @@ def small_workload(kind: str):
     elif kind == "sift4m32":  # same data, PQ 32 x 4 bit (M = d / 4, the paper's PQ setting)
         x, q = sift_shaped(12000, 24, d=128, n_centers=300)
         idx = build_ivf_pq(x, 64, 32, 4, "l2", kmeans_iters=6, pq_iters=6, pq_sample=8000)
-    elif kind == "embed4":    # unit norm, inner product, PQ 16 x 4 bit
+    elif kind == "embed4":    # unit norm, inner product, PQ 32 x 4 bit
         x, q = embedding_shaped(12000, 24, d=64)
-        idx = build_ivf_pq(x, 48, 16, 4, "ip", kmeans_iters=6, pq_iters=6, pq_sample=8000)
+        idx = build_ivf_pq(x, 48, 32, 4, "ip", kmeans_iters=6, pq_iters=6, pq_sample=8000)
     elif kind == "embed":     # unit norm, inner product, PQ 32 x 8 bit
         x, q = embedding_shaped(12000, 24, d=64)
         idx = build_ivf_pq(x, 48, 32, 8, "ip", kmeans_iters=6, pq_iters=6, pq_sample=8000)
@@ -73,6 +73,13 @@ def small_workload(kind: str):
     elif kind == "rragged":   # residual IVF-PQ over few vectors, many short and empty lists
         x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
         idx = build_ivf_pq(x, 40, 8, 8, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700, residual=True)
+    elif kind == "ragged4":   # few vectors, many short and empty lists, PQ 32 x 4 bit
+        x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
+        idx = build_ivf_pq(x, 40, 32, 4, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700)
+    elif kind == "medium4":   # 60k integer vectors, 400 queries: lists of several 256-vector
+        # tiles, each list probed by more than 128 queries of a batch; PQ 32 x 4 bit
+        x, q = sift_shaped(60000, 400, d=128, n_centers=1200)
+        idx = build_ivf_pq(x, 128, 32, 4, "l2", kmeans_iters=6, pq_iters=6, pq_sample=20000)
     elif kind == "ragged":    # few vectors, many short and empty lists
         x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
         idx = build_ivf_pq(x, 40, 8, 8, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700)
