@@ -84,20 +84,26 @@ constexpr int TQ_HW = TQ_MAX_BUCKETS / 2 + 1;    // words per row of packed 16-b
 // capacity, run position, staging offset, d_min and shift; barriers
 constexpr size_t TQ_SMEM = 1024 + (size_t)TQ_STAGES * TQ_STAGE_BYTES + (size_t)TQ_BM * 256 +
                            (size_t)TQ_BM * TQ_HW * 4 + (size_t)TQ_BM * 8 * 4 + 4 * 1024 * 4 +
-                           (size_t)TQ_BM * (8 + 8 + 8 + 4 + 4 + 4) + 8 * (2 * TQ_STAGES + 5) + 16;
+                           (size_t)TQ_BM * (16 + 8 + 8 + 4) + 2 * (size_t)TQ_BM * 8 + 8 * (2 * TQ_STAGES + 5) + 16;
 
 bool scan_tc_supported(const DevIndex& ix, int m) {
     return ix.quant == 0 && ix.bits == 4 && (ix.M == 32 || ix.M == 64 || ix.M == 128) && !ix.resid &&
            m >= 1 && m <= TQ_MAX_BUCKETS;
 }
 
+// The pairs of a query fall in three groups by probe rank: its sampled lists
+// (pass 1), the nearest quarter of the others and the rest (pass 2, near
+// items first: with persistent CTAs taking items in order, the near lists are
+// scanned first, as in Algorithm 1's nearest-first order, so tau is tight
+// before most objects are scanned).
 // Plan arrays inside the scratch (int32 unless noted):
-//   cnt [2][nlist]          pairs of each list, pass 1 (sample) and pass 2
-//   fill [2][nlist]         scatter cursors
-//   seg [2 nlist + 1]       exclusive offsets into qlist ((pass, list) order)
-//   nitems [2]              items per pass
-//   qlist [sum of nprobe]   query index of each pair, grouped by (pass, list)
-//   items int4 [2][cap]     {list, first qlist index, rows, 0}
+//   cnt [3][nlist]          pairs of each list per group
+//   fill [3][nlist]         scatter cursors
+//   seg [3 nlist + 1]       exclusive offsets into qlist ((group, list) order)
+//   nitems [4]              items of pass 1, of the near group, of pass 2
+//   qlist [sum of nprobe]   query index of each pair, grouped by (group, list)
+//   items int4 [2][cap]     {list, first qlist index, rows, 0}: pass 1, then
+//                           pass 2 (near group, then the rest)
 struct TqPlan {
     int32_t* cnt;
     int32_t* fill;
@@ -108,15 +114,20 @@ struct TqPlan {
     int64_t item_cap;
 };
 
-static int64_t tq_item_cap(const DevIndex& ix, int64_t sum_probe) { return ix.nlist + (sum_probe + TQ_BM - 1) / TQ_BM; }
+static int64_t tq_item_cap(const DevIndex& ix, int64_t sum_probe) { return 2 * ix.nlist + (sum_probe + TQ_BM - 1) / TQ_BM; }
+
+// Group of the pair at probe rank j of a query with P lists, nsl of them sampled.
+__device__ __forceinline__ int tq_group(int j, int nsl, int P) {
+    return j < nsl ? 0 : (j < nsl + (P - nsl + 3) / 4 ? 1 : 2);
+}
 
 size_t scan_tc_plan_bytes(const DevIndex& ix, int64_t sum_probe) {
     const size_t L = (size_t)ix.nlist;
     size_t o = 0;
-    o += 4 * L * 2;                 // cnt
-    o += 4 * L * 2;                 // fill
-    o += 4 * (2 * L + 1);           // seg
-    o += 16;                        // nitems (+ pad)
+    o += 4 * L * 3;                 // cnt
+    o += 4 * L * 3;                 // fill
+    o += 4 * (3 * L + 1);           // seg
+    o += 16;                        // nitems
     o = (o + 15) / 16 * 16;
     o += 4 * (size_t)sum_probe;     // qlist
     o = (o + 15) / 16 * 16;
@@ -129,9 +140,9 @@ static TqPlan tq_plan(const DevIndex& ix, void* scratch, int64_t sum_probe) {
     char* b = static_cast<char*>(scratch);
     TqPlan p{};
     size_t o = 0;
-    p.cnt = reinterpret_cast<int32_t*>(b + o); o += 4 * L * 2;
-    p.fill = reinterpret_cast<int32_t*>(b + o); o += 4 * L * 2;
-    p.seg = reinterpret_cast<int32_t*>(b + o); o += 4 * (2 * L + 1);
+    p.cnt = reinterpret_cast<int32_t*>(b + o); o += 4 * L * 3;
+    p.fill = reinterpret_cast<int32_t*>(b + o); o += 4 * L * 3;
+    p.seg = reinterpret_cast<int32_t*>(b + o); o += 4 * (3 * L + 1);
     p.nitems = reinterpret_cast<int32_t*>(b + o); o += 16;
     o = (o + 15) / 16 * 16;
     p.qlist = reinterpret_cast<int32_t*>(b + o); o += 4 * (size_t)sum_probe;
@@ -181,24 +192,22 @@ __global__ void tq_count_kernel(DevIndex ix, ScanArgs a, TqPlan p, int64_t nq) {
         a.state[qi].sample_lists = nsl;
         a.state[qi].scanned = sq;
     }
-    for (int j = (int)lane_id(); j < P; j += 32) {
-        const int pass = j < nsl ? 0 : 1;
-        atomicAdd(&p.cnt[pass * ix.nlist + lists[j]], 1);
-    }
+    for (int j = (int)lane_id(); j < P; j += 32) atomicAdd(&p.cnt[tq_group(j, nsl, P) * ix.nlist + lists[j]], 1);
 }
 
 // One CTA: exclusive offsets of the (pass, list) segments and the item lists.
 __global__ void __launch_bounds__(1024) tq_offsets_kernel(DevIndex ix, TqPlan p) {
     __shared__ int32_t wsum[32];
     __shared__ int32_t carry_s;
-    const int L2 = 2 * ix.nlist;
+    const int L3 = 3 * ix.nlist;
     const int tid = threadIdx.x, bs = blockDim.x;
-    // segments over the 2 * nlist counts, then items per pass
-    for (int phase = 0; phase < 3; ++phase) {
-        // phase 0: seg over all counts; phase 1 / 2: items of pass 0 / 1
-        const int n = phase == 0 ? L2 : ix.nlist;
+    // segments over the 3 * nlist counts, then the items of each group
+    for (int phase = 0; phase < 4; ++phase) {
+        // phase 0: seg over all counts; phase 1 / 2 / 3: items of group 0 / 1 / 2
+        const int n = phase == 0 ? L3 : ix.nlist;
         const int32_t* c = phase == 0 ? p.cnt : p.cnt + (phase - 1) * ix.nlist;
-        if (tid == 0) carry_s = 0;
+        // group 2's items follow group 1's in the second item array
+        if (tid == 0) carry_s = phase == 3 ? p.nitems[1] : 0;
         __syncthreads();
         for (int base = 0; base < n; base += bs) {
             const int i = base + tid;
@@ -220,11 +229,11 @@ __global__ void __launch_bounds__(1024) tq_offsets_kernel(DevIndex ix, TqPlan p)
                     p.seg[i] = excl;
                 } else {
                     // the items of this list
-                    const int pass = phase - 1;
+                    const int grp = phase - 1;
                     const int32_t cnt = c[i];
-                    int4* it = p.items + (size_t)pass * p.item_cap;
+                    int4* it = p.items + (grp == 0 ? 0 : (size_t)p.item_cap);
                     for (int t = 0; t < v; ++t)
-                        it[excl + t] = make_int4(i, p.seg[pass * ix.nlist + i] + t * TQ_BM, min(TQ_BM, cnt - t * TQ_BM), 0);
+                        it[excl + t] = make_int4(i, p.seg[grp * ix.nlist + i] + t * TQ_BM, min(TQ_BM, cnt - t * TQ_BM), 0);
                 }
             }
             __syncthreads();
@@ -232,8 +241,8 @@ __global__ void __launch_bounds__(1024) tq_offsets_kernel(DevIndex ix, TqPlan p)
             __syncthreads();
         }
         if (tid == 0) {
-            if (phase == 0) p.seg[L2] = carry_s;
-            else p.nitems[phase - 1] = carry_s;
+            if (phase == 0) p.seg[L3] = carry_s;
+            else p.nitems[phase == 3 ? 2 : phase - 1] = carry_s;    // nitems[2]: both groups of pass 2
         }
         __syncthreads();
     }
@@ -247,7 +256,7 @@ __global__ void tq_scatter_kernel(DevIndex ix, ScanArgs a, TqPlan p, int64_t nq)
     const int32_t* lists = a.lists + a.qp.poff(qi);
     const int nsl = a.state[qi].sample_lists;
     for (int j = (int)lane_id(); j < P; j += 32) {
-        const int key = (j < nsl ? 0 : ix.nlist) + lists[j];
+        const int key = tq_group(j, nsl, P) * ix.nlist + lists[j];
         const int32_t slot = atomicAdd(&p.fill[key], 1);
         p.qlist[p.seg[key] + slot] = (int32_t)qi;
     }
@@ -305,13 +314,15 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
     uint8_t* sm = tq_raw + pad;
     const uint32_t sbase = raw + pad;
     constexpr uint32_t S = TQ_STAGES;
-    uint2** s_reg = reinterpret_cast<uint2**>(sm + S * TQ_STAGE_BYTES); // [128] region of each row's query
+    // [128] per row and group: {region address of staging entry 0 of the row's
+    // run (as an integer), entries the region still takes counted from staging
+    // entry 0, (shift << 24) | d_min}
+    uint4* s_rec = reinterpret_cast<uint4*>(sm + S * TQ_STAGE_BYTES);
+    uint2** s_reg = reinterpret_cast<uint2**>(s_rec + TQ_BM);          // [128] region of each row's query
     unsigned long long* s_cap = reinterpret_cast<unsigned long long*>(s_reg + TQ_BM);   // [128] its capacity
-    unsigned long long* s_pos = s_cap + TQ_BM;                         // [128] region position of the row's run
-    uint32_t* s_roff = reinterpret_cast<uint32_t*>(s_pos + TQ_BM);     // [128] run start in the warp's staging
-    uint32_t* s_dmin = s_roff + TQ_BM;                                 // [128] d_min of the row's query
-    uint32_t* s_sh = s_dmin + TQ_BM;                                   // [128] its bin shift
-    uint32_t* s_mk = s_sh + TQ_BM;                                     // [8][128] admitted columns per group
+    uint32_t* s_dmsh = reinterpret_cast<uint32_t*>(s_cap + TQ_BM);     // [128] (shift << 24) | d_min
+    const uint4** s_asrc = reinterpret_cast<const uint4**>(s_dmsh + TQ_BM);   // [2][128] table rows of an item
+    uint32_t* s_mk = reinterpret_cast<uint32_t*>(s_asrc + 2 * TQ_BM);  // [8][128] admitted columns per group
     uint32_t* stg = s_mk + 8 * TQ_BM;                                  // [4][1024] staged appends per warp
     uint32_t* hist = stg + 4 * 1024;                                   // [128][TQ_HW] 16-bit bucket counts
     uint8_t* smap = reinterpret_cast<uint8_t*>(hist + TQ_BM * TQ_HW);  // [128][256] bucket maps
@@ -395,58 +406,78 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
         __syncwarp();
     } else if (warp >= TQ_A_WARP0 && warp < TQ_A_WARP0 + TQ_A_WARPS) {
         // ---------------- A operand: table rows ----------------
-        // thread a moves rows a and a + 64 (128 bytes each per stage) through
-        // registers: the loads for the next stage are issued as soon as this
-        // stage is stored, so their latency overlaps the wait for the next
-        // free stage
+        // 8 consecutive lanes move one row's 128 bytes per stage (one
+        // 512-byte coalesced load per warp instruction covers 4 rows); thread
+        // a takes 16-byte unit a mod 8 of rows a / 8 + 8 k, k < 16.  The loads
+        // for the next stage are issued once this stage is stored, so their
+        // latency overlaps the wait for the next free stage.  The item's row
+        // addresses are kept in shared memory (two sets, for this item and
+        // the next).
         const int a0 = tid - 32 * TQ_A_WARP0;                 // 0..63
+        const uint32_t uj = (uint32_t)(a0 & 7), rbase = (uint32_t)(a0 >> 3);
         uint32_t g = 0;
         bool ok = true;
-        // the source rows of an item (null: a row past the item's queries)
-        auto row_src = [&](int it, int r) -> const uint4* {
+        // row addresses of item it into set h (row a0 and a0 + 64 by this thread)
+        auto set_rows = [&](int it, int h) {
             const int4 item = a.items[it];
-            return r < item.z ? reinterpret_cast<const uint4*>(a.lut_f16 + (int64_t)a.qlist[item.y + r] * KT) : nullptr;
-        };
-        uint4 cur[2][8];
-        auto fetch = [&](const uint4* s0, const uint4* s1, int i) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                cur[0][j] = s0 ? __ldg(s0 + i * (TQ_BK / 8) + j) : make_uint4(0u, 0u, 0u, 0u);
-                cur[1][j] = s1 ? __ldg(s1 + i * (TQ_BK / 8) + j) : make_uint4(0u, 0u, 0u, 0u);
+            for (int q = 0; q < 2; ++q) {
+                const int r = a0 + 64 * q;
+                s_asrc[h * TQ_BM + r] =
+                    r < item.z ? reinterpret_cast<const uint4*>(a.lut_f16 + (int64_t)a.qlist[item.y + r] * KT) : nullptr;
             }
         };
-        int it = blockIdx.x;
-        const uint4* src0 = it < n_items ? row_src(it, a0) : nullptr;
-        const uint4* src1 = it < n_items ? row_src(it, a0 + 64) : nullptr;
-        if (it < n_items) fetch(src0, src1, 0);
-        for (; it < n_items && ok; it += gridDim.x) {
+        uint4 cur[16];
+        auto fetch = [&](int h, int i) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const uint4* sp = s_asrc[h * TQ_BM + rbase + 8 * k];
+                cur[k] = sp ? __ldg(sp + i * (TQ_BK / 8) + uj) : make_uint4(0u, 0u, 0u, 0u);
+            }
+        };
+        // the 64 A threads (warps 5-6) sync among themselves with named barrier 1;
+        // each sync also agrees on whether to stop (a failed wait anywhere), so
+        // all 64 always leave the item loop together
+        auto abar = [&](bool bad) -> bool {
+            uint32_t any;
+            asm volatile(
+                "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 64, p;\n selp.u32 %0, 1, 0, q;\n}"
+                : "=r"(any)
+                : "r"((uint32_t)bad)
+                : "memory");
+            return any != 0u;
+        };
+        int it = blockIdx.x, h = 0;
+        if (it < n_items) set_rows(it, 0);
+        if (abar(false)) ok = false;
+        if (it < n_items) fetch(0, 0);
+        for (; it < n_items && ok; it += gridDim.x, h ^= 1) {
             const int len = ix.list_len[a.items[it].x];
             const int T = (len + TQ_BN - 1) / TQ_BN;
             const int nit = it + (int)gridDim.x;
-            const uint4* nsrc0 = (nit < n_items) ? row_src(nit, a0) : nullptr;
-            const uint4* nsrc1 = (nit < n_items) ? row_src(nit, a0 + 64) : nullptr;
+            if (nit < n_items) set_rows(nit, h ^ 1);
+            if (abar(*s_abort != 0)) { ok = false; break; }
             for (int t = 0; t < T && ok; ++t) {
                 for (int i = 0; i < KCH; ++i, ++g) {
                     const uint32_t s = g % S, u = g / S;
-                    if (!mbar_wait(empty(s), (u & 1u) ^ 1u) || *s_abort) { ok = false; break; }
+                    if (!mbar_wait(empty(s), (u & 1u) ^ 1u) || *s_abort) { abort_now(); ok = false; break; }
+                    const uint32_t st0 = sbase + s * TQ_STAGE_BYTES;
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint32_t r = (uint32_t)(a0 + 64 * h);
-                        const uint32_t dst = sbase + s * TQ_STAGE_BYTES + r * 128u;
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) st_shared_v4(dst + ((((uint32_t)j) ^ (r & 7u)) << 4), cur[h][j]);
+                    for (int k = 0; k < 16; ++k) {
+                        const uint32_t r = rbase + 8u * (uint32_t)k;
+                        st_shared_v4(st0 + r * 128u + ((uj ^ (r & 7u)) << 4), cur[k]);
                     }
                     fence_async_smem();
                     mbar_arrive(full(s));
                     // the next stage's row segments: the next chunk, the next tile's
                     // first chunk, or the next item's first chunk
-                    if (i + 1 < KCH) fetch(src0, src1, i + 1);
-                    else if (t + 1 < T) fetch(src0, src1, 0);
-                    else if (nit < n_items) fetch(nsrc0, nsrc1, 0);
+                    if (i + 1 < KCH) fetch(h, i + 1);
+                    else if (t + 1 < T) fetch(h, 0);
+                    else if (nit < n_items) fetch(h ^ 1, 0);
                 }
             }
-            src0 = nsrc0;
-            src1 = nsrc1;
+            // every thread is done with this item's set before it is rewritten
+            if (abar(!ok || *s_abort != 0)) ok = false;
         }
         if (!ok) abort_now();
     } else if (warp >= TQ_B_WARP0) {
@@ -553,8 +584,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
             s_reg[r] = st ? a.region + a.qp.roff(qi) : nullptr;
             s_cap[r] = st ? (unsigned long long)a.qp.rcap(qi) : 0ull;
             if (st && MAIN) {
-                s_dmin[r] = st->d_min;
-                s_sh[r] = (uint32_t)st->sh;
+                s_dmsh[r] = ((uint32_t)st->sh << 24) | st->d_min;   // d_min < 2^24 (keys are below 2^18)
                 const uint4* mp = reinterpret_cast<const uint4*>(st->map);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) reinterpret_cast<uint4*>(smap + r * 256)[i] = mp[i];
@@ -598,8 +628,16 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                     uint32_t acc[32];
                     tmem_ld32(tb + (uint32_t)(gi * 32), acc);
                     uint32_t k = inc - n;
-                    s_roff[r] = k;
-                    s_pos[r] = pos;
+                    {
+                        // region address of staging entry 0 of this run, and how many
+                        // entries (counted from staging entry 0) the region still takes
+                        const long long lim = (long long)s_cap[r] - (long long)pos + (long long)k;
+                        const unsigned long long ra = reinterpret_cast<unsigned long long>(s_reg[r]) +
+                                                      8ull * (pos - (unsigned long long)k);
+                        s_rec[r] = make_uint4((uint32_t)ra, (uint32_t)(ra >> 32),
+                                              (uint32_t)(lim < 0 ? 0 : (lim > 0x7FFFFFFF ? 0x7FFFFFFF : lim)),
+                                              MAIN ? s_dmsh[r] : 0u);
+                    }
                     pos += n;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
@@ -610,24 +648,36 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                     }
                     __syncwarp();
                     const uint32_t c0 = slot0 + (uint32_t)(t * TQ_BN + gi * 32);
-                    for (uint32_t e0 = 0; e0 < T; e0 += 32) {
-                        const uint32_t ei = e0 + rl;
-                        if (ei < T) {
-                            const uint32_t e = wstg[ei];
-                            const int rr = wr0 + (int)((e >> 5) & 31u);
-                            const uint32_t key = e >> 10;
-                            const unsigned long long p = s_pos[rr] + (unsigned long long)(ei - s_roff[rr]);
-                            if (p < s_cap[rr]) s_reg[rr][p] = make_uint2(key, c0 + (e & 31u));
-                            else atomicOr(ix.status, kStatusRegionOverrun);
-                            if (MAIN) {
-                                const uint32_t dm = s_dmin[rr];
-                                uint32_t bn = 0u;
-                                if (key > dm) {
-                                    bn = (key - dm) >> s_sh[rr];
-                                    bn = bn > 255u ? 255u : bn;
+                    for (uint32_t e0 = 0; e0 < T; e0 += 128) {
+                        // four entries per lane, their loads issued together
+                        uint32_t e[4];
+                        uint4 rc[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) e[q] = e0 + 32 * q + rl < T ? wstg[e0 + 32 * q + rl] : 0xFFFFFFFFu;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) rc[q] = s_rec[wr0 + (int)((e[q] >> 5) & 31u)];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t ei = e0 + 32 * q + rl;
+                            if (ei < T) {
+                                const uint32_t key = e[q] >> 10;
+                                if (ei < rc[q].z) {
+                                    uint2* dst = reinterpret_cast<uint2*>(((unsigned long long)rc[q].y << 32) | rc[q].x) + ei;
+                                    *dst = make_uint2(key, c0 + (e[q] & 31u));
+                                } else {
+                                    atomicOr(ix.status, kStatusRegionOverrun);
                                 }
-                                const uint32_t bk = smap[rr * 256 + bn];
-                                atomicAdd(&hist[rr * TQ_HW + (bk >> 1)], 1u << ((bk & 1u) << 4));
+                                if (MAIN) {
+                                    const uint32_t dm = rc[q].w & 0xFFFFFFu, sh = rc[q].w >> 24;
+                                    uint32_t bn = 0u;
+                                    if (key > dm) {
+                                        bn = (key - dm) >> sh;
+                                        bn = bn > 255u ? 255u : bn;
+                                    }
+                                    const int rr = wr0 + (int)((e[q] >> 5) & 31u);
+                                    const uint32_t bk = smap[rr * 256 + bn];
+                                    atomicAdd(&hist[rr * TQ_HW + (bk >> 1)], 1u << ((bk & 1u) << 4));
+                                }
                             }
                         }
                     }
@@ -692,7 +742,7 @@ static cudaError_t launch_tc_t(const DevIndex& ix, int64_t nq, const ScanArgs& s
     if ((e = smem_attr_once((const void*)scan_tc_kernel<M, false>, (int)smem)) != cudaSuccess) return e;
     if ((e = smem_attr_once((const void*)scan_tc_kernel<M, true>, (int)smem)) != cudaSuccess) return e;
     // plan: counts, offsets and items, scatter
-    if ((e = cudaMemsetAsync(p.cnt, 0, sizeof(int32_t) * 4 * (size_t)ix.nlist, st)) != cudaSuccess) return e;   // cnt + fill
+    if ((e = cudaMemsetAsync(p.cnt, 0, sizeof(int32_t) * 6 * (size_t)ix.nlist, st)) != cudaSuccess) return e;   // cnt + fill
     const unsigned wblocks = (unsigned)((nq + 7) / 8);
     tq_count_kernel<<<wblocks, 256, 0, st>>>(ix, sa, p, nq);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -706,7 +756,7 @@ static cudaError_t launch_tc_t(const DevIndex& ix, int64_t nq, const ScanArgs& s
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_codebook(nq, sa, st)) != cudaSuccess) return e;
     ta.items = p.items + p.item_cap;
-    ta.nitems = p.nitems + 1;
+    ta.nitems = p.nitems + 2;
     scan_tc_kernel<M, true><<<grid, TQ_THREADS, smem, st>>>(ix, ta);
     return cudaGetLastError();
 }
