@@ -199,6 +199,8 @@ struct ScanArgs {
     // residual IVF-PQ: each query's table scale and per-(query, list) base, packed like lists
     const float* qinv = nullptr;
     const int32_t* lbase = nullptr;
+    int sample_only = 0;          // 1: the one-CTA-per-query scan stops after the codebook (sampled
+                                  // objects appended, state written; the tensor-core scan continues)
 };
 // S4-S6: sample + codebook + scan + push/update, one CTA per query (and S7
 // in its tail when fuse_select is set).

@@ -861,6 +861,28 @@ __global__ void __launch_bounds__(ScanCfg<M, BITS>::THREADS, ScanCfg<M, BITS>::M
         }
         __syncthreads();
     }
+    if (a.sample_only) {
+        // the sampled objects are appended and the codebook built: the state
+        // as the list-grouped scan (k_scan_tc.cu) takes it over
+        bbc_collector_state* st = a.state + qi;
+        bins_to_buckets(S);
+        for (int i = tid; i < kMaxBuckets; i += bs) st->hist[i] = i < a.m ? S.hist[i] : 0u;
+        for (int i = tid; i < 256; i += bs) st->map[i] = S.bmap[i];
+        if (tid == 0) {
+            st->d_min = S.dmin;
+            st->d_max = S.dmax;
+            st->sh = S.sh;
+            st->m = a.m;
+            st->sample_lists = S.nsl;
+            st->tau = (int32_t)S.tau;
+            st->sample_size = ns;
+            st->scanned = S.sq;
+            st->pushed = (int64_t)S.count;
+            st->below = 0;
+            st->kc = Q.kc;
+        }
+        return;
+    }
     // ---- Phase D: main scan ----
     scan_blocks<M, BITS, true, false, -1, EARLY, RES>(ix, a, Q, a.state + qi, P, gs, S.gtot, lut, ldesc, S, nullptr,
                                                        q8, s_qn2);

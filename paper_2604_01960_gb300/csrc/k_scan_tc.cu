@@ -14,16 +14,17 @@
 // in any summation order: the keys, and with them the result buffer's state
 // and candidates, are those of the one-query scan on the same table.
 //
-// Work: the (query, probed list) pairs of a batch, grouped by list (a device
-// counting sort), in items of one list and up to 128 of its queries.  Pass 1
-// takes every query's sampled lists (the first lists in probe order, as in
-// k_scan.cu) and appends all their objects; the codebook kernel then builds
-// each query's codebook and threshold from its sample; pass 2 takes the other
-// lists and runs Push against the threshold (Algorithm 1), Update after each
-// item on the query's global bucket counts.  The final selection (k_select.cu)
-// computes tau* from the counts of everything appended.  tau at any time is
-// >= tau* and buckets are monotone in e, so every object of a bucket <= tau*
-// is appended under this schedule too (the argument of the one-query scan).
+// Work: first the one-query scan (k_scan.cu) scans each query's sampled lists
+// (the first lists in probe order), appends all their objects and builds the
+// query's codebook and threshold, then stops; it reads the same table, so its
+// keys are the same.  The (query, probed list) pairs of the other lists are
+// grouped by list (a device counting sort) into items of one list and up to
+// 128 of its queries, and this kernel runs Push against each query's
+// threshold (Algorithm 1) with Update after each item on the query's global
+// bucket counts.  The final selection (k_select.cu) computes tau* from the
+// counts of everything appended.  tau at any time is >= tau* and buckets are
+// monotone in e, so every object of a bucket <= tau* is appended under this
+// schedule too (the argument of the one-query scan).
 //
 // CTA (one per SM, persistent over items; 15 warps, at most 4 per SM sub-partition):
 //   warps 0-3   epilogue: thread r owns query row r (tensor-memory lane r);
@@ -192,7 +193,8 @@ __global__ void tq_count_kernel(DevIndex ix, ScanArgs a, TqPlan p, int64_t nq) {
         a.state[qi].sample_lists = nsl;
         a.state[qi].scanned = sq;
     }
-    for (int j = (int)lane_id(); j < P; j += 32) atomicAdd(&p.cnt[tq_group(j, nsl, P) * ix.nlist + lists[j]], 1);
+    // the sampled lists were scanned by the one-query kernel
+    for (int j = nsl + (int)lane_id(); j < P; j += 32) atomicAdd(&p.cnt[tq_group(j, nsl, P) * ix.nlist + lists[j]], 1);
 }
 
 // One CTA: exclusive offsets of the (pass, list) segments and the item lists.
@@ -255,7 +257,7 @@ __global__ void tq_scatter_kernel(DevIndex ix, ScanArgs a, TqPlan p, int64_t nq)
     const int P = a.qp.P(qi);
     const int32_t* lists = a.lists + a.qp.poff(qi);
     const int nsl = a.state[qi].sample_lists;
-    for (int j = (int)lane_id(); j < P; j += 32) {
+    for (int j = nsl + (int)lane_id(); j < P; j += 32) {
         const int key = tq_group(j, nsl, P) * ix.nlist + lists[j];
         const int32_t slot = atomicAdd(&p.fill[key], 1);
         p.qlist[p.seg[key] + slot] = (int32_t)qi;
@@ -299,9 +301,10 @@ struct TqArgs {
     int m;                        // buckets
 };
 
-// M: sub-spaces (4-bit codes).  MAIN = false: sampling pass (append every
-// object); true: Push against each query's threshold, counts and Update.
-template <int M, bool MAIN>
+// M: sub-spaces (4-bit codes).  Push against each query's threshold, bucket
+// counts and Update after every item (the sampled lists are scanned before,
+// by the one-query scan).
+template <int M>
 __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqArgs a) {
     constexpr int KT = 16 * M;                  // table entries per query
     constexpr int KCH = KT / TQ_BK;             // stages per tile
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                      "r"(512u));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (MAIN && warp < 4)
+    if (warp < 4)
         for (int w = 0; w < TQ_HW; ++w) hist[tid * TQ_HW + w] = 0u;
     tc_fence_before();
     __syncthreads();
@@ -583,7 +586,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
             uint32_t etau = 0xFFFFFFFFu;
             s_reg[r] = st ? a.region + a.qp.roff(qi) : nullptr;
             s_cap[r] = st ? (unsigned long long)a.qp.rcap(qi) : 0ull;
-            if (st && MAIN) {
+            if (st) {
                 s_dmsh[r] = ((uint32_t)st->sh << 24) | st->d_min;   // d_min < 2^24 (keys are below 2^18)
                 const uint4* mp = reinterpret_cast<const uint4*>(st->map);
 #pragma unroll
@@ -596,7 +599,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                 const bool got = __all_sync(0xFFFFFFFFu, mbar_wait(accf(b), v & 1u)) && !*s_abort;
                 if (!got) { ok = false; break; }
                 tc_fence_after();
-                if (MAIN && st && t > 0 && t % 255 == 0) flush_counts(st);   // 16-bit counts stay below 2^16
+                if (st && t > 0 && t % 255 == 0) flush_counts(st);   // 16-bit counts stay below 2^16
                 const int nt = min(TQ_BN, len - t * TQ_BN);
                 const int ng = (nt + 31) / 32;
                 const uint32_t tb = tl + b * (uint32_t)TQ_BN;
@@ -636,7 +639,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                                                       8ull * (pos - (unsigned long long)k);
                         s_rec[r] = make_uint4((uint32_t)ra, (uint32_t)(ra >> 32),
                                               (uint32_t)(lim < 0 ? 0 : (lim > 0x7FFFFFFF ? 0x7FFFFFFF : lim)),
-                                              MAIN ? s_dmsh[r] : 0u);
+                                              s_dmsh[r]);
                     }
                     pos += n;
 #pragma unroll
@@ -667,7 +670,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                                 } else {
                                     atomicOr(ix.status, kStatusRegionOverrun);
                                 }
-                                if (MAIN) {
+                                {
                                     const uint32_t dm = rc[q].w & 0xFFFFFFu, sh = rc[q].w >> 24;
                                     uint32_t bn = 0u;
                                     if (key > dm) {
@@ -687,7 +690,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                 mbar_arrive(acce(b));
             }
             if (!ok) break;
-            if (MAIN && st) {
+            if (st) {
                 // this item's counts into the query's state, then Update on them
                 flush_counts(st);
                 // Update: the first bucket whose running count reaches K_c, read 32
@@ -739,9 +742,13 @@ static cudaError_t launch_tc_t(const DevIndex& ix, int64_t nq, const ScanArgs& s
     const TqPlan p = tq_plan(ix, scratch, sum_probe);
     const size_t smem = TQ_SMEM;
     cudaError_t e;
-    if ((e = smem_attr_once((const void*)scan_tc_kernel<M, false>, (int)smem)) != cudaSuccess) return e;
-    if ((e = smem_attr_once((const void*)scan_tc_kernel<M, true>, (int)smem)) != cudaSuccess) return e;
-    // plan: counts, offsets and items, scatter
+    if ((e = smem_attr_once((const void*)scan_tc_kernel<M>, (int)smem)) != cudaSuccess) return e;
+    // the sample and the codebooks: the one-query scan stopped after its phase C
+    // (the same keys: it reads the same table), then the plan over the other lists
+    ScanArgs ss = sa;
+    ss.sample_only = 1;
+    ss.fuse_select = 0;
+    if ((e = launch_scan(ix, nq, ss, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.cnt, 0, sizeof(int32_t) * 6 * (size_t)ix.nlist, st)) != cudaSuccess) return e;   // cnt + fill
     const unsigned wblocks = (unsigned)((nq + 7) / 8);
     tq_count_kernel<<<wblocks, 256, 0, st>>>(ix, sa, p, nq);
@@ -752,12 +759,9 @@ static cudaError_t launch_tc_t(const DevIndex& ix, int64_t nq, const ScanArgs& s
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     TqArgs ta{lut_f16, p.items, p.nitems, p.qlist, sa.state, sa.region, sa.qp, sa.m};
     const unsigned grid = (unsigned)ix.num_sms;
-    scan_tc_kernel<M, false><<<grid, TQ_THREADS, smem, st>>>(ix, ta);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_codebook(nq, sa, st)) != cudaSuccess) return e;
     ta.items = p.items + p.item_cap;
     ta.nitems = p.nitems + 2;
-    scan_tc_kernel<M, true><<<grid, TQ_THREADS, smem, st>>>(ix, ta);
+    scan_tc_kernel<M><<<grid, TQ_THREADS, smem, st>>>(ix, ta);
     return cudaGetLastError();
 }
 
