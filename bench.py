@@ -2,12 +2,14 @@
 """Benchmark: QPS at recall@k >= 0.95 of the large-k IVF-PQ search path.
 
 Workload (default): 1,000,000 SIFT-shaped vectors (d = 128, integer components
-in [0, 255]), 1,024 IVF lists, PQ 32 x 8 bit, 10,000 queries, k = 10,000,
-nprobe = 256, K_c = 1.4 k candidates re-ranked (on this data K_c = 1.3 k gives
-recall 0.946, 1.4 k gives 0.959).  A step is one bbc_search over
-the whole 10,000-query batch (probe, LUT, scan + bucket-based result buffer,
-selection, re-rank, top-k) with queries and index resident in HBM; L2 is
-flushed between timed steps.  Recall@k is measured in the same run against
+in [0, 255]), 1,024 IVF lists, PQ 64 x 4 bit (the 4-bit variant of the
+configuration), 10,000 queries, k = 10,000, nprobe = 256, K_c = 1.5 k
+candidates re-ranked, the list-grouped scan on the tensor cores with
+2047-level tables (recall 0.958; K_c = 1.4 k gives 0.947).  --workload sift
+runs PQ 32 x 8 bit with the one-query scan (K_c = 1.4 k, recall 0.959).  A
+step is one bbc_search over the whole 10,000-query batch (probe, LUT, scan +
+bucket-based result buffer, selection, re-rank, top-k) with queries and index
+resident in HBM; L2 is flushed between timed steps.  Recall@k is measured in the same run against
 exact kNN over the whole data set (tie-aware: a returned id counts when its
 exact distance is <= the k-th exact distance).
 
@@ -34,6 +36,7 @@ if ROOT not in sys.path:
 
 METRIC = "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ)"
 METRICS = {"sift": METRIC, "sift4": "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ 64x4)",
+           "sift4m32": "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ 32x4)",
            "sift_iid": "QPS at recall@k>=0.95 (k=10k, 1Mx128 IVF-PQ, i.i.d. mixture)",
            "gist": "QPS at recall@k>=0.95 (k=10k, 1Mx960 IVF + 1-bit sign codes, bounded re-rank)",
            "embed": "QPS at recall@k>=0.95 (k=50k, 10Mx768 IVF-PQ, inner product)",
@@ -51,12 +54,14 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference", "plain"],
                    help="gb300: the batched path; reference: the CPU oracle; plain: the FP32 single-query GPU "
                         "form (one bbc_search per query, FP32 rows)")
-    p.add_argument("--workload", default="sift")
+    p.add_argument("--workload", default="sift4")
     p.add_argument("--n", type=int, default=None, help="override data size (testing only)")
     p.add_argument("--nq", type=int, default=None)
     p.add_argument("--k", type=int, default=None)
     p.add_argument("--nprobe", default=None, help="lists probed; a comma list prints one line per value")
-    p.add_argument("--kc-ratio", default="1.4", help="K_c / k; a comma list prints one line per value")
+    p.add_argument("--kc-ratio", default=None,
+                   help="K_c / k (default: the smallest tenth that reaches recall 0.95 on the workload); "
+                        "a comma list prints one line per value")
     p.add_argument("--buckets", default="64", help="bucket count m; a comma list prints one line per value")
     p.add_argument("--collector", default="0",
                    help="top-K_c collector: 0 the result buffer, 1 lazy linear buffer, 2 binary heap; a comma list "
@@ -65,9 +70,9 @@ def parse():
                    help="Algorithm 4's early re-rank: 1 on, 0 off; a comma list prints one line per value")
     p.add_argument("--residual", action="store_true",
                    help="residual IVF-PQ: the PQ codes quantise each vector's residual to its list centroid")
-    p.add_argument("--scan-tc", default="0",
-                   help="1 = list-grouped scan on the tensor cores (4-bit codes, 2047-level tables); "
-                        "a comma list prints one line per value")
+    p.add_argument("--scan-tc", default=None,
+                   help="1 = list-grouped scan on the tensor cores (4-bit codes, 2047-level tables; the default "
+                        "for 4-bit workloads); a comma list prints one line per value")
     p.add_argument("--pair", default="0",
                    help="scan schedule: 1 two queries per CTA (pair form), 0 one; a comma list prints one line per value")
     p.add_argument("--cpu-queries", type=int, default=200, help="oracle sample for cpu_baseline")
@@ -98,7 +103,16 @@ def parse():
     p.add_argument("--epsilon0", type=float, default=1.9, help="epsilon_0 of the estimator bounds")
     p.add_argument("--recall-queries", type=int, default=None,
                    help="queries whose recall is measured against exact kNN (default: all, at most 1,000)")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.kc_ratio is None:
+        a.kc_ratio = DEFAULT_KC.get(a.workload, "1.5")
+    if a.scan_tc is None:
+        a.scan_tc = "1" if a.workload in ("sift4", "sift4m32") and not a.residual else "0"
+    return a
+
+
+# K_c / k per workload: the smallest tenth whose recall@k reaches 0.95
+DEFAULT_KC = {"sift": "1.4", "sift4": "1.5"}
 
 
 def pq_desc(idx) -> str:
@@ -276,22 +290,24 @@ def run_reference(args, ws, rank):
     w, idx, q, k, nprobe, _ = make_inputs(args, device)
     kc = max(k, int(math.ceil(float(str(args.kc_ratio).split(",")[0]) * k - 1e-9)))
     nqs = min(args.ref_queries, len(q))
+    # the table the measured arm uses (2047 levels with the tensor-core scan)
+    levels = 2047 if str(args.scan_tc).split(",")[0] == "1" else 65535
     for s in range(args.warmup):
-        oracle.search(idx, q[:1], k, nprobe, kc, "sort")
+        oracle.search(idx, q[:1], k, nprobe, kc, "sort", lut_levels=levels)
     t = []
     for s in range(args.steps):
         sel = q[(s * nqs) % len(q):][:nqs]
         t0 = time.perf_counter()
-        oracle.search(idx, sel, k, nprobe, kc, "sort")
+        oracle.search(idx, sel, k, nprobe, kc, "sort", lut_levels=levels)
         t.append(time.perf_counter() - t0)
     qps = nqs * len(t) / sum(t)
     sample = f"{nqs} queries per step of the {len(q)}-query batch, full {idx.n}-vector index"
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": qps, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "impl": "reference", "metric": METRICS.get(args.workload, METRIC), "value": qps, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": idx.n, "d": idx.d, "nlist": idx.nlist, "pq": pq_desc(idx),
-                   "nq_per_step": nqs, "k": k, "nprobe": nprobe, "kc": kc},
+                   "nq_per_step": nqs, "k": k, "nprobe": nprobe, "kc": kc, "lut_levels": levels},
         "cpu_baseline": {"value": qps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": qps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)

@@ -26,7 +26,7 @@
 // monotone in e, so every object of a bucket <= tau* is appended under this
 // schedule too (the argument of the one-query scan).
 //
-// CTA (one per SM, persistent over items; 15 warps, at most 4 per SM sub-partition):
+// CTA (one per SM, persistent over items; 13 warps, at most 4 per SM sub-partition):
 //   warps 0-3   epilogue: thread r owns query row r (tensor-memory lane r);
 //               reads a tile's accumulator columns, pushes (key, slot) pairs
 //               whose key is at or below the query's current bound into its
@@ -36,12 +36,12 @@
 //               memory, and after each item adds the counts to the query's
 //               state and runs Update;
 //   warp 4      MMA issuer (one elected thread) and tensor-memory owner;
-//   warps 5-6   A operand: the item's 128 table rows (two per thread), 64
-//               entries (128 bytes) per stage, loaded one stage ahead into
-//               registers and stored in the 128-byte-swizzled K-major layout;
-//   warps 7-14  B operand: thread t builds the one-hot row of vector t of the
-//               current 256-vector tile from its code row (rotated back to
-//               sub-space order), 128 bytes per stage.
+//   warps 5-12  producers of every stage: thread t builds the one-hot row of
+//               vector t of the current 256-vector tile from its code row
+//               (rotated back to sub-space order), 128 bytes per stage (B), and
+//               moves four 16-byte units of the item's 128 table rows (A,
+//               coalesced, loaded one stage ahead into registers); both in the
+//               128-byte-swizzled K-major layout.
 // A 3-stage shared-memory ring (A 16 KB + B 32 KB per stage) feeds the MMA
 // (M = 128 query rows, N = the tile's vectors rounded up to 16, K = 16 per
 // instruction); two 256-column accumulators in tensor memory let the
@@ -66,9 +66,9 @@ constexpr int TQ_STAGES = 3;
 constexpr int TQ_A_BYTES = TQ_BM * TQ_BK * 2;
 constexpr int TQ_B_BYTES = TQ_BN * TQ_BK * 2;
 constexpr int TQ_STAGE_BYTES = TQ_A_BYTES + TQ_B_BYTES;
-constexpr int TQ_MMA_WARP = 4, TQ_A_WARP0 = 5, TQ_A_WARPS = 2, TQ_B_WARP0 = 7, TQ_B_WARPS = 8;
-constexpr int TQ_THREADS = 32 * (TQ_B_WARP0 + TQ_B_WARPS);
-constexpr uint32_t TQ_FULL_COUNT = 32u * (TQ_A_WARPS + TQ_B_WARPS);   // arrivals that fill one stage
+constexpr int TQ_MMA_WARP = 4, TQ_P_WARP0 = 5, TQ_P_WARPS = 8;
+constexpr int TQ_THREADS = 32 * (TQ_P_WARP0 + TQ_P_WARPS);
+constexpr uint32_t TQ_FULL_COUNT = 32u * TQ_P_WARPS;   // arrivals that fill one stage
 constexpr int TQ_MAX_BUCKETS = 64;              // per-row bucket counts kept in shared memory
 
 // kind::f16 instruction descriptor: FP32 accumulate, FP16 A and B, both
@@ -407,44 +407,45 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
             if (!ok) abort_now();
         }
         __syncwarp();
-    } else if (warp >= TQ_A_WARP0 && warp < TQ_A_WARP0 + TQ_A_WARPS) {
-        // ---------------- A operand: table rows ----------------
-        // 8 consecutive lanes move one row's 128 bytes per stage (one
-        // 512-byte coalesced load per warp instruction covers 4 rows); thread
-        // a takes 16-byte unit a mod 8 of rows a / 8 + 8 k, k < 16.  The loads
-        // for the next stage are issued once this stage is stored, so their
-        // latency overlaps the wait for the next free stage.  The item's row
-        // addresses are kept in shared memory (two sets, for this item and
-        // the next).
-        const int a0 = tid - 32 * TQ_A_WARP0;                 // 0..63
-        const uint32_t uj = (uint32_t)(a0 & 7), rbase = (uint32_t)(a0 >> 3);
+    } else if (warp >= TQ_P_WARP0) {
+        // ---------------- producers: both operands of every stage ----------------
+        // B: thread r builds the one-hot row of vector r of the tile.
+        // A: the item's 128 table rows, 8 consecutive lanes per 128-byte row
+        // segment (one 512-byte coalesced load per warp instruction covers 4
+        // rows): thread r moves 16-byte unit r mod 8 of rows r / 8 + 32 k,
+        // k < 4.  The A loads for the next stage are issued once this stage is
+        // stored, so their latency overlaps the wait for the next free stage.
+        // The item's row addresses are kept in shared memory (two sets, for
+        // this item and the next).
+        const int r = tid - 32 * TQ_P_WARP0;                  // 0..255
+        const uint32_t rx = (uint32_t)(r & 7);
+        const uint4* codes = reinterpret_cast<const uint4*>(ix.codes);
+        const uint32_t uj = (uint32_t)(r & 7), rb = (uint32_t)(r >> 3);
         uint32_t g = 0;
         bool ok = true;
-        // row addresses of item it into set h (row a0 and a0 + 64 by this thread)
+        // row addresses of item it into set h (threads 0..127, one row each)
         auto set_rows = [&](int it, int h) {
-            const int4 item = a.items[it];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int r = a0 + 64 * q;
+            if (r < TQ_BM) {
+                const int4 item = a.items[it];
                 s_asrc[h * TQ_BM + r] =
                     r < item.z ? reinterpret_cast<const uint4*>(a.lut_f16 + (int64_t)a.qlist[item.y + r] * KT) : nullptr;
             }
         };
-        uint4 cur[16];
+        uint4 cur[4];
         auto fetch = [&](int h, int i) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint4* sp = s_asrc[h * TQ_BM + rbase + 8 * k];
+            for (int k = 0; k < 4; ++k) {
+                const uint4* sp = s_asrc[h * TQ_BM + rb + 32 * k];
                 cur[k] = sp ? __ldg(sp + i * (TQ_BK / 8) + uj) : make_uint4(0u, 0u, 0u, 0u);
             }
         };
-        // the 64 A threads (warps 5-6) sync among themselves with named barrier 1;
+        // the 256 producer threads sync among themselves with named barrier 1;
         // each sync also agrees on whether to stop (a failed wait anywhere), so
-        // all 64 always leave the item loop together
-        auto abar = [&](bool bad) -> bool {
+        // all of them always leave the item loop together
+        auto pbar = [&](bool bad) -> bool {
             uint32_t any;
             asm volatile(
-                "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 64, p;\n selp.u32 %0, 1, 0, q;\n}"
+                "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}"
                 : "=r"(any)
                 : "r"((uint32_t)bad)
                 : "memory");
@@ -452,49 +453,17 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
         };
         int it = blockIdx.x, h = 0;
         if (it < n_items) set_rows(it, 0);
-        if (abar(false)) ok = false;
+        if (pbar(false)) ok = false;
         if (it < n_items) fetch(0, 0);
         for (; it < n_items && ok; it += gridDim.x, h ^= 1) {
-            const int len = ix.list_len[a.items[it].x];
-            const int T = (len + TQ_BN - 1) / TQ_BN;
-            const int nit = it + (int)gridDim.x;
-            if (nit < n_items) set_rows(nit, h ^ 1);
-            if (abar(*s_abort != 0)) { ok = false; break; }
-            for (int t = 0; t < T && ok; ++t) {
-                for (int i = 0; i < KCH; ++i, ++g) {
-                    const uint32_t s = g % S, u = g / S;
-                    if (!mbar_wait(empty(s), (u & 1u) ^ 1u) || *s_abort) { abort_now(); ok = false; break; }
-                    const uint32_t st0 = sbase + s * TQ_STAGE_BYTES;
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const uint32_t r = rbase + 8u * (uint32_t)k;
-                        st_shared_v4(st0 + r * 128u + ((uj ^ (r & 7u)) << 4), cur[k]);
-                    }
-                    fence_async_smem();
-                    mbar_arrive(full(s));
-                    // the next stage's row segments: the next chunk, the next tile's
-                    // first chunk, or the next item's first chunk
-                    if (i + 1 < KCH) fetch(h, i + 1);
-                    else if (t + 1 < T) fetch(h, 0);
-                    else if (nit < n_items) fetch(h ^ 1, 0);
-                }
-            }
-            // every thread is done with this item's set before it is rewritten
-            if (abar(!ok || *s_abort != 0)) ok = false;
-        }
-        if (!ok) abort_now();
-    } else if (warp >= TQ_B_WARP0) {
-        // ---------------- B operand: one-hot code rows ----------------
-        const int r = tid - 32 * TQ_B_WARP0;                  // vector row 0..255 of the tile
-        const uint32_t rx = (uint32_t)(r & 7);
-        const uint4* codes = reinterpret_cast<const uint4*>(ix.codes);
-        uint32_t g = 0;
-        bool ok = true;
-        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const int4 item = a.items[it];
             const int len = ix.list_len[item.x];
             const int blk0 = ix.list_blk[item.x];
-            for (int t = 0; t * TQ_BN < len && ok; ++t) {
+            const int T = (len + TQ_BN - 1) / TQ_BN;
+            const int nit = it + (int)gridDim.x;
+            if (nit < n_items) set_rows(nit, h ^ 1);
+            if (pbar(*s_abort != 0)) { ok = false; break; }
+            for (int t = 0; t < T && ok; ++t) {
                 const int v = t * TQ_BN + r;                  // list position
                 const int nt = min(TQ_BN, len - t * TQ_BN);
                 const bool write = r < (nt + 15) / 16 * 16;   // rows the MMA reads
@@ -529,9 +498,15 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
 #pragma unroll
                 for (int i = 0; i < KCH; ++i, ++g) {
                     const uint32_t s = g % S, u = g / S;
-                    if (!mbar_wait(empty(s), (u & 1u) ^ 1u) || *s_abort) { ok = false; break; }
+                    if (!mbar_wait(empty(s), (u & 1u) ^ 1u) || *s_abort) { abort_now(); ok = false; break; }
+                    const uint32_t st0 = sbase + s * TQ_STAGE_BYTES;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t ar = rb + 32u * (uint32_t)k;
+                        st_shared_v4(st0 + ar * 128u + ((uj ^ (ar & 7u)) << 4), cur[k]);
+                    }
                     if (write) {
-                        const uint32_t row = sbase + s * TQ_STAGE_BYTES + TQ_A_BYTES + (uint32_t)r * 128u;
+                        const uint32_t row = st0 + TQ_A_BYTES + (uint32_t)r * 128u;
                         const uint32_t h16 = (cw[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;   // sub-spaces 4i..4i+3
 #pragma unroll
                         for (int q4 = 0; q4 < 4; ++q4) {
@@ -544,11 +519,18 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                             st_shared_v4(row + ((((uint32_t)(2 * q4)) ^ rx) << 4), (c & 8u) ? z : x);
                             st_shared_v4(row + ((((uint32_t)(2 * q4 + 1)) ^ rx) << 4), (c & 8u) ? x : z);
                         }
-                        fence_async_smem();
                     }
+                    fence_async_smem();
                     mbar_arrive(full(s));
+                    // the next stage's table segments: the next chunk, the next tile's
+                    // first chunk, or the next item's first chunk
+                    if (i + 1 < KCH) fetch(h, i + 1);
+                    else if (t + 1 < T) fetch(h, 0);
+                    else if (nit < n_items) fetch(h ^ 1, 0);
                 }
             }
+            // every thread is done with this item's set before it is rewritten
+            if (pbar(!ok || *s_abort != 0)) ok = false;
         }
         if (!ok) abort_now();
     } else {

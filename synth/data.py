@@ -180,6 +180,9 @@ WORKLOADS = {
     # Same data, PQ 64 x 4 bit.
     "sift4": Workload("ivfpq4-sift-1m-d128", 1_000_000, 128, 1024, "l2", "pq", 64, 4,
                       10_000, 10_000, 256, sift_shaped),
+    # Same data, PQ 32 x 4 bit (M = d / 4, the paper's PQ setting).
+    "sift4m32": Workload("ivfpq4m32-sift-1m-d128", 1_000_000, 128, 1024, "l2", "pq", 32, 4,
+                         10_000, 10_000, 256, sift_shaped),
     # 1M x 960 non-negative, 4,096 lists, 1-bit sign codes.
     "gist": Workload("ivfsign-gist-1m-d960", 1_000_000, 960, 4096, "l2", "sign", 0, 1,
                      4096, 10_000, 256, gist_shaped),

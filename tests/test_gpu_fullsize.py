@@ -4,6 +4,9 @@
   bbc_search call, k = 10,000, nprobe = 256, K_c = 1.4 k: sampled queries
   (first, last and spread between) are recomputed one by one by the oracle and
   must match bit for bit (integer data: the FP32 re-rank is exact).
+* The same data with PQ 64 x 4 bit and the list-grouped tensor-core scan
+  (2047-level tables), K_c = 1.5 k, the benchmark's default configuration:
+  sampled queries must match the oracle's search on the same table bit for bit.
 * 1M x 960 GIST-shaped sign-code index (4,096 lists), 4,096 queries in one
   call, k = 10,000, nprobe = 256, hard bounds: sampled queries must return the
   oracle's exact top-k of their probed lists.
@@ -56,6 +59,29 @@ def test_sift_1m_full_batch_sampled_parity(bbc, oracle_lib):
         bbc.bbc_stream_status(h)
         for i in (0, 1234, 5001, 7777, nq - 1):
             oi, od = oracle_lib.search(idx, q[i:i + 1], k, nprobe, kc, "sort")
+            assert np.array_equal(ids[i].cpu().numpy(), oi[0]), f"query {i}: ids"
+            assert np.array_equal(dd[i].cpu().numpy().astype(np.float64), od[0]), f"query {i}: distances"
+    finally:
+        bbc.bbc_index_free(h)
+
+
+def test_sift4_1m_tensor_core_scan_full_batch_sampled_parity(bbc, oracle_lib):
+    w, idx, q = _build("sift4")
+    k, nprobe, ratio = w.k, w.nprobe, 1.5
+    kc = int(np.ceil(ratio * k - 1e-9))
+    h = bbc.bbc_index_create(idx, 0)
+    try:
+        bbc.bbc_set_param(h, "kc_ratio", ratio)
+        bbc.bbc_set_param(h, "workspace_mb", 64 * 1024)
+        bbc.bbc_set_param(h, "scan_tc", 1)
+        nq = len(q)
+        ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+        dd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+        bbc.bbc_search(h, torch.from_numpy(q).cuda(), nq, k, nprobe, ids, dd)
+        torch.cuda.synchronize()
+        bbc.bbc_stream_status(h)
+        for i in (0, 2222, 6001, nq - 1):
+            oi, od = oracle_lib.search(idx, q[i:i + 1], k, nprobe, kc, "sort", lut_levels=2047)
             assert np.array_equal(ids[i].cpu().numpy(), oi[0]), f"query {i}: ids"
             assert np.array_equal(dd[i].cpu().numpy().astype(np.float64), od[0]), f"query {i}: distances"
     finally:
