@@ -26,8 +26,9 @@
 // monotone in e, so every object of a bucket <= tau* is appended under this
 // schedule too (the argument of the one-query scan).
 //
-// CTA (one per SM, persistent over items; 13 warps, at most 4 per SM sub-partition):
-//   warps 0-3   epilogue: thread r owns query row r (tensor-memory lane r);
+// CTA (one per SM, persistent over items; 17 warps):
+//   warps 0-7   epilogue: row r (tensor-memory lane r) belongs to warps
+//               r / 32 and r / 32 + 4, one per half of the tile's columns;
 //               reads a tile's accumulator columns, pushes (key, slot) pairs
 //               whose key is at or below the query's current bound into its
 //               region (one 64-bit cursor atomic per tile; each 32-column
@@ -35,8 +36,8 @@
 //               contiguous run per row), counts them per bucket in shared
 //               memory, and after each item adds the counts to the query's
 //               state and runs Update;
-//   warp 4      MMA issuer (one elected thread) and tensor-memory owner;
-//   warps 5-12  producers of every stage: thread t builds the one-hot row of
+//   warp 8      MMA issuer (one elected thread) and tensor-memory owner;
+//   warps 9-16  producers of every stage: thread t builds the one-hot row of
 //               vector t of the current 256-vector tile from its code row
 //               (rotated back to sub-space order), 128 bytes per stage (B), and
 //               moves four 16-byte units of the item's 128 table rows (A,
@@ -66,7 +67,7 @@ constexpr int TQ_STAGES = 3;
 constexpr int TQ_A_BYTES = TQ_BM * TQ_BK * 2;
 constexpr int TQ_B_BYTES = TQ_BN * TQ_BK * 2;
 constexpr int TQ_STAGE_BYTES = TQ_A_BYTES + TQ_B_BYTES;
-constexpr int TQ_MMA_WARP = 4, TQ_P_WARP0 = 5, TQ_P_WARPS = 8;
+constexpr int TQ_E_WARPS = 8, TQ_MMA_WARP = 8, TQ_P_WARP0 = 9, TQ_P_WARPS = 8;
 constexpr int TQ_THREADS = 32 * (TQ_P_WARP0 + TQ_P_WARPS);
 constexpr uint32_t TQ_FULL_COUNT = 32u * TQ_P_WARPS;   // arrivals that fill one stage
 constexpr int TQ_MAX_BUCKETS = 64;              // per-row bucket counts kept in shared memory
@@ -78,14 +79,15 @@ __host__ __device__ constexpr uint32_t tq_idesc(int n) {
 }
 
 constexpr int TQ_HW = TQ_MAX_BUCKETS / 2 + 1;    // words per row of packed 16-bit bucket counts
+constexpr int TQ_STG_CAP = 512;                 // staged entries per epilogue warp
 // dynamic shared memory: alignment pad; the ring; each row's bucket map (256
 // bytes); its bucket counts as 16-bit halves of TQ_HW words; the admitted-
 // column masks of a tile (8 per row); each warp's staged appends of one
 // 32-column group (up to 32 x 32 packed entries); per-row region pointer,
 // capacity, run position, staging offset, d_min and shift; barriers
 constexpr size_t TQ_SMEM = 1024 + (size_t)TQ_STAGES * TQ_STAGE_BYTES + (size_t)TQ_BM * 256 +
-                           (size_t)TQ_BM * TQ_HW * 4 + (size_t)TQ_BM * 8 * 4 + 4 * 1024 * 4 +
-                           (size_t)TQ_BM * (16 + 8 + 8 + 4) + 2 * (size_t)TQ_BM * 8 + 8 * (2 * TQ_STAGES + 5) + 16;
+                           (size_t)TQ_BM * TQ_HW * 4 + (size_t)TQ_BM * 8 * 4 + TQ_E_WARPS * TQ_STG_CAP * 4 +
+                           (size_t)TQ_BM * (2 * 16 + 8 + 8 + 4) + 2 * (size_t)TQ_BM * 8 + 8 * (2 * TQ_STAGES + 5) + 16;
 
 bool scan_tc_supported(const DevIndex& ix, int m) {
     return ix.quant == 0 && ix.bits == 4 && (ix.M == 32 || ix.M == 64 || ix.M == 128) && !ix.resid &&
@@ -214,7 +216,8 @@ __global__ void __launch_bounds__(1024) tq_offsets_kernel(DevIndex ix, TqPlan p)
         for (int base = 0; base < n; base += bs) {
             const int i = base + tid;
             int32_t v = 0;
-            if (i < n) v = phase == 0 ? c[i] : (c[i] + TQ_BM - 1) / TQ_BM;
+            // (an empty list gets no items: every item has at least one tile)
+            if (i < n) v = phase == 0 ? c[i] : (ix.list_len[i] > 0 ? (c[i] + TQ_BM - 1) / TQ_BM : 0);
             const int32_t inc = (int32_t)warp_incl_scan((uint32_t)v);
             if (lane_id() == 31) wsum[warp_id()] = inc;
             __syncthreads();
@@ -320,14 +323,14 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
     // [128] per row and group: {region address of staging entry 0 of the row's
     // run (as an integer), entries the region still takes counted from staging
     // entry 0, (shift << 24) | d_min}
-    uint4* s_rec = reinterpret_cast<uint4*>(sm + S * TQ_STAGE_BYTES);
-    uint2** s_reg = reinterpret_cast<uint2**>(s_rec + TQ_BM);          // [128] region of each row's query
+    uint4* s_rec = reinterpret_cast<uint4*>(sm + S * TQ_STAGE_BYTES);  // [2][128]: one per column half
+    uint2** s_reg = reinterpret_cast<uint2**>(s_rec + 2 * TQ_BM);      // [128] region of each row's query
     unsigned long long* s_cap = reinterpret_cast<unsigned long long*>(s_reg + TQ_BM);   // [128] its capacity
     uint32_t* s_dmsh = reinterpret_cast<uint32_t*>(s_cap + TQ_BM);     // [128] (shift << 24) | d_min
     const uint4** s_asrc = reinterpret_cast<const uint4**>(s_dmsh + TQ_BM);   // [2][128] table rows of an item
     uint32_t* s_mk = reinterpret_cast<uint32_t*>(s_asrc + 2 * TQ_BM);  // [8][128] admitted columns per group
-    uint32_t* stg = s_mk + 8 * TQ_BM;                                  // [4][1024] staged appends per warp
-    uint32_t* hist = stg + 4 * 1024;                                   // [128][TQ_HW] 16-bit bucket counts
+    uint32_t* stg = s_mk + 8 * TQ_BM;                                  // [8][TQ_STG_CAP] staged appends per warp
+    uint32_t* hist = stg + TQ_E_WARPS * TQ_STG_CAP;                    // [128][TQ_HW] 16-bit bucket counts
     uint8_t* smap = reinterpret_cast<uint8_t*>(hist + TQ_BM * TQ_HW);  // [128][256] bucket maps
     uint64_t* bars = reinterpret_cast<uint64_t*>(smap + TQ_BM * 256);
     // bars: full[S], empty[S], accfull[2], accempty[2], done
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf(b), 1);
-            mbar_init(acce(b), 32u * 4);
+            mbar_init(acce(b), 32u * TQ_E_WARPS);
         }
         mbar_init(done, 1);
         *s_abort = 0;
@@ -431,12 +434,13 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                     r < item.z ? reinterpret_cast<const uint4*>(a.lut_f16 + (int64_t)a.qlist[item.y + r] * KT) : nullptr;
             }
         };
-        uint4 cur[4];
-        auto fetch = [&](int h, int i) {
+        // table segments of two stages in flight: even and odd stages (KCH is even)
+        uint4 cur[2][4];
+        auto fetch = [&](uint4 (&c)[4], int h, int i) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint4* sp = s_asrc[h * TQ_BM + rb + 32 * k];
-                cur[k] = sp ? __ldg(sp + i * (TQ_BK / 8) + uj) : make_uint4(0u, 0u, 0u, 0u);
+                c[k] = sp ? __ldg(sp + i * (TQ_BK / 8) + uj) : make_uint4(0u, 0u, 0u, 0u);
             }
         };
         // the 256 producer threads sync among themselves with named barrier 1;
@@ -451,41 +455,66 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                 : "memory");
             return any != 0u;
         };
+        // raw code row of this thread's vector in the next tile (loaded one tile ahead)
+        uint32_t rwn[NW];
+        auto load_codes = [&](int blk0_, int len_, int t_) {
+            const int vv = t_ * TQ_BN + r;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) rwn[w] = 0u;
+            if (vv < len_) {
+                const uint4* cp = codes + ((size_t)(blk0_ + (vv >> 5)) * NCH) * 32 + (vv & 31);
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    const uint4 x = __ldg(cp + c * 32);
+                    if (4 * c + 0 < NW) rwn[4 * c + 0] = x.x;
+                    if (4 * c + 1 < NW) rwn[4 * c + 1] = x.y;
+                    if (4 * c + 2 < NW) rwn[4 * c + 2] = x.z;
+                    if (4 * c + 3 < NW) rwn[4 * c + 3] = x.w;
+                }
+            }
+        };
+        // the code row in sub-space order: slot s of lane t holds sub-space
+        // (s + t) mod M, so rotate left by 4 (t mod M) bits; the lane of this
+        // thread's vector is r mod 32 in every tile
+        const uint32_t rot = 4u * (uint32_t)((r & 31) % M);
+        const uint32_t ws = rot >> 5, bsh = rot & 31u;
         int it = blockIdx.x, h = 0;
         if (it < n_items) set_rows(it, 0);
         if (pbar(false)) ok = false;
-        if (it < n_items) fetch(0, 0);
+        if (it < n_items) {
+            fetch(cur[0], 0, 0);
+            fetch(cur[1], 0, 1);
+            const int l0 = a.items[it].x;
+            load_codes(ix.list_blk[l0], ix.list_len[l0], 0);
+        }
         for (; it < n_items && ok; it += gridDim.x, h ^= 1) {
             const int4 item = a.items[it];
             const int len = ix.list_len[item.x];
             const int blk0 = ix.list_blk[item.x];
             const int T = (len + TQ_BN - 1) / TQ_BN;
             const int nit = it + (int)gridDim.x;
-            if (nit < n_items) set_rows(nit, h ^ 1);
+            int nblk0 = 0, nlen = 0;
+            if (nit < n_items) {
+                set_rows(nit, h ^ 1);
+                const int nl = a.items[nit].x;
+                nblk0 = ix.list_blk[nl];
+                nlen = ix.list_len[nl];
+            }
             if (pbar(*s_abort != 0)) { ok = false; break; }
             for (int t = 0; t < T && ok; ++t) {
                 const int v = t * TQ_BN + r;                  // list position
                 const int nt = min(TQ_BN, len - t * TQ_BN);
                 const bool write = r < (nt + 15) / 16 * 16;   // rows the MMA reads
-                // the code row in sub-space order: slot s of lane t holds
-                // sub-space (s + t) mod M, so rotate left by 4 (t mod M) bits
+                uint32_t rw[NW];
+#pragma unroll
+                for (int w = 0; w < NW; ++w) rw[w] = rwn[w];
+                // the next tile's code rows: this list's next tile or the next item's first
+                if (t + 1 < T) load_codes(blk0, len, t + 1);
+                else if (nit < n_items) load_codes(nblk0, nlen, 0);
                 uint32_t cw[NW];
 #pragma unroll
                 for (int w = 0; w < NW; ++w) cw[w] = 0u;
                 if (v < len) {
-                    const int ln = v & 31;
-                    const uint4* cp = codes + ((size_t)(blk0 + (v >> 5)) * NCH) * 32 + ln;
-                    uint32_t rw[NW];
-#pragma unroll
-                    for (int c = 0; c < NCH; ++c) {
-                        const uint4 x = __ldg(cp + c * 32);
-                        if (4 * c + 0 < NW) rw[4 * c + 0] = x.x;
-                        if (4 * c + 1 < NW) rw[4 * c + 1] = x.y;
-                        if (4 * c + 2 < NW) rw[4 * c + 2] = x.z;
-                        if (4 * c + 3 < NW) rw[4 * c + 3] = x.w;
-                    }
-                    const uint32_t rot = 4u * (uint32_t)(ln % M);
-                    const uint32_t ws = rot >> 5, bsh = rot & 31u;
                     // word rotation by ws (0..3) in two conditional steps
                     uint32_t t1[NW];
 #pragma unroll
@@ -503,7 +532,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const uint32_t ar = rb + 32u * (uint32_t)k;
-                        st_shared_v4(st0 + ar * 128u + ((uj ^ (ar & 7u)) << 4), cur[k]);
+                        st_shared_v4(st0 + ar * 128u + ((uj ^ (ar & 7u)) << 4), cur[i & 1][k]);
                     }
                     if (write) {
                         const uint32_t row = st0 + TQ_A_BYTES + (uint32_t)r * 128u;
@@ -522,11 +551,11 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                     }
                     fence_async_smem();
                     mbar_arrive(full(s));
-                    // the next stage's table segments: the next chunk, the next tile's
-                    // first chunk, or the next item's first chunk
-                    if (i + 1 < KCH) fetch(h, i + 1);
-                    else if (t + 1 < T) fetch(h, 0);
-                    else if (nit < n_items) fetch(h ^ 1, 0);
+                    // the table segments two stages ahead: a later chunk of this tile, one
+                    // of the next tile's first two, or of the next item's first two
+                    if (i + 2 < KCH) fetch(cur[i & 1], h, i + 2);
+                    else if (t + 1 < T) fetch(cur[i & 1], h, i + 2 - KCH);
+                    else if (nit < n_items) fetch(cur[i & 1], h ^ 1, i + 2 - KCH);
                 }
             }
             // every thread is done with this item's set before it is rewritten
@@ -534,26 +563,42 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
         }
         if (!ok) abort_now();
     } else {
-        // ---------------- epilogue: warps 0-3, row r ----------------
-        // A row's appends go to its own query's region.  Per 32-column group,
-        // the warp packs the admitted entries of its 32 rows into one list
-        // ((key << 10) | (row << 5) | column) in shared memory; the lanes then
-        // walk that list together, so each writes one entry and counts it in
-        // its row's bucket counts (16-bit halves, shared-memory atomics).
-        const int r = tid;
+        // ---------------- epilogue: warps 0-7 ----------------
+        // Warp e reads tensor-memory lanes 32 (e mod 4) .. + 31 (rows = queries)
+        // and the columns of groups 4 (e / 4) .. + 3 of each tile: two warps
+        // share a row, one per half of the tile's 256 columns.  A row's appends
+        // go to its own query's region.  Per 32-column group, the warp packs
+        // the admitted entries of its 32 rows into one list ((key << 10) | (row
+        // << 5) | column) in shared memory; the lanes then walk that list
+        // together, so each writes one entry and counts it in its row's bucket
+        // counts (16-bit halves, shared-memory atomics).  The two warps of a
+        // lane quarter meet at a named barrier (2 + quarter) at each item's
+        // start and end; each meeting also agrees on whether to stop.
+        const int qd = warp & 3, hf = warp >> 2;
+        const int r = qd * 32 + lane;                           // row (query) of this thread
         const uint32_t rl = (uint32_t)lane;                     // row within the warp
-        const int wr0 = warp * 32;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-        uint32_t* wstg = stg + warp * 1024;
+        const int wr0 = qd * 32;
+        const uint32_t tl = tmem + ((uint32_t)(qd * 32) << 16);
+        uint32_t* wstg = stg + warp * TQ_STG_CAP;
+        uint4* srec = s_rec + hf * TQ_BM;
         uint32_t* hrow = hist + r * TQ_HW;
         uint32_t tcount = 0;
         bool ok = true;
-        // the row's 16-bit counts into its query's bucket counts (thread-private row)
+        auto qbar = [&](bool bad) -> bool {
+            uint32_t any;
+            asm volatile(
+                "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 64, p;\n selp.u32 %0, 1, 0, q;\n}"
+                : "=r"(any)
+                : "r"((uint32_t)bad), "r"(2 + qd)
+                : "memory");
+            return any != 0u;
+        };
+        // the row's 16-bit counts into its query's bucket counts (read and cleared atomically:
+        // the other warp of the row may be counting into them)
         auto flush_counts = [&](bbc_collector_state* st) {
             for (int w = 0; w < TQ_HW; ++w) {
-                const uint32_t c = hrow[w];
-                if (c) {
-                    hrow[w] = 0u;
+                if (hrow[w]) {
+                    const uint32_t c = atomicExch(&hrow[w], 0u);
                     if (c & 0xFFFFu) atomicAdd(&st->hist[2 * w], c & 0xFFFFu);
                     if (c >> 16) atomicAdd(&st->hist[2 * w + 1], c >> 16);
                 }
@@ -566,29 +611,32 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
             const int64_t qi = r < item.z ? (int64_t)a.qlist[item.y + r] : -1;
             bbc_collector_state* st = qi >= 0 ? a.state + qi : nullptr;
             uint32_t etau = 0xFFFFFFFFu;
-            s_reg[r] = st ? a.region + a.qp.roff(qi) : nullptr;
-            s_cap[r] = st ? (unsigned long long)a.qp.rcap(qi) : 0ull;
-            if (st) {
-                s_dmsh[r] = ((uint32_t)st->sh << 24) | st->d_min;   // d_min < 2^24 (keys are below 2^18)
-                const uint4* mp = reinterpret_cast<const uint4*>(st->map);
+            if (hf == 0) {
+                s_reg[r] = st ? a.region + a.qp.roff(qi) : nullptr;
+                s_cap[r] = st ? (unsigned long long)a.qp.rcap(qi) : 0ull;
+                if (st) {
+                    s_dmsh[r] = ((uint32_t)st->sh << 24) | st->d_min;   // d_min < 2^24 (keys are below 2^18)
+                    const uint4* mp = reinterpret_cast<const uint4*>(st->map);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) reinterpret_cast<uint4*>(smap + r * 256)[i] = mp[i];
-                etau = tq_etau(st, (uint32_t)*(volatile int*)&st->tau);
+                    for (int i = 0; i < 16; ++i) reinterpret_cast<uint4*>(smap + r * 256)[i] = mp[i];
+                }
             }
+            if (st) etau = tq_etau(st, (uint32_t)*(volatile int*)&st->tau);
+            if (qbar(*s_abort != 0)) { ok = false; break; }    // the row's descriptors are in place
             const float etf = etau >= (1u << 24) ? 3.0e38f : (float)etau;
             for (int t = 0; t * TQ_BN < len; ++t, ++tcount) {
                 const uint32_t b = tcount & 1u, v = tcount >> 1;
                 const bool got = __all_sync(0xFFFFFFFFu, mbar_wait(accf(b), v & 1u)) && !*s_abort;
-                if (!got) { ok = false; break; }
+                if (!got) { abort_now(); ok = false; break; }
                 tc_fence_after();
-                if (st && t > 0 && t % 255 == 0) flush_counts(st);   // 16-bit counts stay below 2^16
+                if (hf == 0 && st && t > 0 && t % 255 == 0) flush_counts(st);   // 16-bit counts stay below 2^16
                 const int nt = min(TQ_BN, len - t * TQ_BN);
-                const int ng = (nt + 31) / 32;
+                const int g0 = hf * 4, g1 = min((nt + 31) / 32, g0 + 4);     // this warp's groups
                 const uint32_t tb = tl + b * (uint32_t)TQ_BN;
                 // pass 1: which columns Push admits (key <= the query's bound)
                 uint32_t tot = 0;
 #pragma unroll 1
-                for (int gi = 0; gi < ng; ++gi) {
+                for (int gi = g0; gi < g1; ++gi) {
                     uint32_t acc[32];
                     tmem_ld32(tb + (uint32_t)(gi * 32), acc);
                     const int nv = min(32, nt - gi * 32);
@@ -599,60 +647,66 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                     s_mk[gi * TQ_BM + r] = mk;
                     tot += (uint32_t)__popc(mk);
                 }
-                // one cursor atomic per tile and row
+                // one cursor atomic per tile, row and column half
                 unsigned long long pos = 0;
                 if (tot) pos = atomicAdd(reinterpret_cast<unsigned long long*>(&st->pushed), (unsigned long long)tot);
-                // pass 2, per group: pack the admitted entries, then write and count them
+                // pass 2, per group: pack the admitted entries, then write and count them;
+                // in two rounds of 16 rows when more than the staging holds
 #pragma unroll 1
-                for (int gi = 0; gi < ng; ++gi) {
+                for (int gi = g0; gi < g1; ++gi) {
                     const uint32_t mk = s_mk[gi * TQ_BM + r];
                     const uint32_t n = (uint32_t)__popc(mk);
-                    const uint32_t inc = warp_incl_scan(n);
-                    const uint32_t T = __shfl_sync(0xFFFFFFFFu, inc, 31);
-                    if (T == 0u) continue;
+                    const uint32_t Tall = __reduce_add_sync(0xFFFFFFFFu, n);
+                    if (Tall == 0u) continue;
                     uint32_t acc[32];
                     tmem_ld32(tb + (uint32_t)(gi * 32), acc);
-                    uint32_t k = inc - n;
-                    {
-                        // region address of staging entry 0 of this run, and how many
-                        // entries (counted from staging entry 0) the region still takes
-                        const long long lim = (long long)s_cap[r] - (long long)pos + (long long)k;
-                        const unsigned long long ra = reinterpret_cast<unsigned long long>(s_reg[r]) +
-                                                      8ull * (pos - (unsigned long long)k);
-                        s_rec[r] = make_uint4((uint32_t)ra, (uint32_t)(ra >> 32),
-                                              (uint32_t)(lim < 0 ? 0 : (lim > 0x7FFFFFFF ? 0x7FFFFFFF : lim)),
-                                              s_dmsh[r]);
-                    }
-                    pos += n;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if ((mk >> j) & 1u) {
-                            wstg[k] = (__float2uint_rn(__uint_as_float(acc[j])) << 10) | (rl << 5) | (uint32_t)j;
-                            ++k;
-                        }
-                    }
-                    __syncwarp();
+                    const int rounds = Tall > (uint32_t)TQ_STG_CAP ? 2 : 1;
                     const uint32_t c0 = slot0 + (uint32_t)(t * TQ_BN + gi * 32);
-                    for (uint32_t e0 = 0; e0 < T; e0 += 128) {
-                        // four entries per lane, their loads issued together
-                        uint32_t e[4];
-                        uint4 rc[4];
+#pragma unroll 1
+                    for (int rd = 0; rd < rounds; ++rd) {
+                        const bool mine = rounds == 1 || (int)(rl >> 4) == rd;
+                        const uint32_t nn = mine ? n : 0u;
+                        const uint32_t inc = warp_incl_scan(nn);
+                        const uint32_t T = __shfl_sync(0xFFFFFFFFu, inc, 31);
+                        uint32_t k = inc - nn;
+                        if (mine) {
+                            // region address of staging entry 0 of this run, and how many
+                            // entries (counted from staging entry 0) the region still takes
+                            const long long lim = (long long)s_cap[r] - (long long)pos + (long long)k;
+                            const unsigned long long ra = reinterpret_cast<unsigned long long>(s_reg[r]) +
+                                                          8ull * (pos - (unsigned long long)k);
+                            srec[r] = make_uint4((uint32_t)ra, (uint32_t)(ra >> 32),
+                                                 (uint32_t)(lim < 0 ? 0 : (lim > 0x7FFFFFFF ? 0x7FFFFFFF : lim)),
+                                                 s_dmsh[r]);
+                            pos += n;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) e[q] = e0 + 32 * q + rl < T ? wstg[e0 + 32 * q + rl] : 0xFFFFFFFFu;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) rc[q] = s_rec[wr0 + (int)((e[q] >> 5) & 31u)];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const uint32_t ei = e0 + 32 * q + rl;
-                            if (ei < T) {
-                                const uint32_t key = e[q] >> 10;
-                                if (ei < rc[q].z) {
-                                    uint2* dst = reinterpret_cast<uint2*>(((unsigned long long)rc[q].y << 32) | rc[q].x) + ei;
-                                    *dst = make_uint2(key, c0 + (e[q] & 31u));
-                                } else {
-                                    atomicOr(ix.status, kStatusRegionOverrun);
+                            for (int j = 0; j < 32; ++j) {
+                                if ((mk >> j) & 1u) {
+                                    wstg[k] = (__float2uint_rn(__uint_as_float(acc[j])) << 10) | (rl << 5) | (uint32_t)j;
+                                    ++k;
                                 }
-                                {
+                            }
+                        }
+                        __syncwarp();
+                        for (uint32_t e0 = 0; e0 < T; e0 += 128) {
+                            // four entries per lane, their loads issued together
+                            uint32_t e[4];
+                            uint4 rc[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) e[q] = e0 + 32 * q + rl < T ? wstg[e0 + 32 * q + rl] : 0xFFFFFFFFu;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) rc[q] = srec[wr0 + (int)((e[q] >> 5) & 31u)];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const uint32_t ei = e0 + 32 * q + rl;
+                                if (ei < T) {
+                                    const uint32_t key = e[q] >> 10;
+                                    if (ei < rc[q].z) {
+                                        uint2* dst = reinterpret_cast<uint2*>(((unsigned long long)rc[q].y << 32) | rc[q].x) + ei;
+                                        *dst = make_uint2(key, c0 + (e[q] & 31u));
+                                    } else {
+                                        atomicOr(ix.status, kStatusRegionOverrun);
+                                    }
                                     const uint32_t dm = rc[q].w & 0xFFFFFFu, sh = rc[q].w >> 24;
                                     uint32_t bn = 0u;
                                     if (key > dm) {
@@ -665,14 +719,16 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
                                 }
                             }
                         }
+                        __syncwarp();
                     }
-                    __syncwarp();
                 }
                 tc_fence_before();
                 mbar_arrive(acce(b));
             }
+            // both warps of the row are done with this item
+            if (qbar(!ok || *s_abort != 0)) ok = false;
             if (!ok) break;
-            if (st) {
+            if (hf == 0 && st) {
                 // this item's counts into the query's state, then Update on them
                 flush_counts(st);
                 // Update: the first bucket whose running count reaches K_c, read 32

@@ -80,6 +80,15 @@ def small_workload(kind: str):
         # tiles, each list probed by more than 128 queries of a batch; PQ 32 x 4 bit
         x, q = sift_shaped(60000, 400, d=128, n_centers=1200)
         idx = build_ivf_pq(x, 128, 32, 4, "l2", kmeans_iters=6, pq_iters=6, pq_sample=20000)
+    elif kind == "many4":     # 400 short lists, every fifth one emptied (its objects join the list
+        # before it), 320 queries: more list-grouped items than a GPU has CTAs; PQ 32 x 4 bit
+        import dataclasses
+        x, q = gaussian_mixture_tiny(6000, 320, d=32, n_centers=40, sigma=0.5)
+        idx = build_ivf_pq(x, 400, 32, 4, "l2", kmeans_iters=4, pq_iters=4, pq_sample=6000)
+        offs = idx.list_offsets.copy()
+        for l in range(5, idx.nlist, 5):
+            offs[l] = offs[l + 1]
+        idx = dataclasses.replace(idx, list_offsets=offs)
     elif kind == "ragged":    # few vectors, many short and empty lists
         x, q = gaussian_mixture_tiny(700, 8, d=32, n_centers=40, sigma=0.5)
         idx = build_ivf_pq(x, 40, 8, 8, "l2", kmeans_iters=4, pq_iters=4, pq_sample=700)

@@ -72,7 +72,8 @@ def _reset(bbc, h):
 
 CASES = [("sift4", 20, 1200, 64, 4), ("sift4", 64, 12000, 48, 8), ("sift4m32", 16, 900, 32, 8),
          ("embed4", 10, 400, 2, 8), ("ragged4", 40, 300, 16, 3), ("ragged4", 2, 1000, 64, 8),
-         ("sift4", 5, 1, 64, 8), ("medium4", 48, 3000, 64, 8), ("medium4", 128, 20000, 64, 8)]
+         ("sift4", 5, 1, 64, 8), ("medium4", 48, 3000, 64, 8), ("medium4", 128, 20000, 64, 8),
+         ("many4", 200, 600, 64, 8), ("many4", 40, 150, 16, 4)]
 
 
 @pytest.mark.parametrize("kind,nprobe,kc,m,smin", CASES)
@@ -123,7 +124,8 @@ def test_tc_collect_candidates_and_state(bbc, oracle_lib, kind, nprobe, kc, m, s
 
 @pytest.mark.parametrize("kind,k,nprobe,ratio", [("sift4", 300, 24, 2.0), ("sift4m32", 500, 16, 1.5),
                                                  ("embed4", 200, 10, 1.5), ("ragged4", 50, 40, 1.0),
-                                                 ("medium4", 2000, 64, 1.5), ("sift4", 1, 3, 1.0)])
+                                                 ("medium4", 2000, 64, 1.5), ("sift4", 1, 3, 1.0),
+                                                 ("many4", 300, 200, 1.5)])
 def test_tc_search_end_to_end(bbc, oracle_lib, kind, k, nprobe, ratio):
     h, idx, q = dev_index(bbc, kind)
     kc = max(k, int(np.ceil(ratio * k - 1e-9)))
