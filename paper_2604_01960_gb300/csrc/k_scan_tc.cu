@@ -63,7 +63,7 @@ namespace bbc {
 constexpr int TQ_BM = 128;                      // query rows per item (tensor-memory lanes)
 constexpr int TQ_BN = 256;                      // vectors per tile (accumulator columns)
 constexpr int TQ_BK = 64;                       // table entries per stage (128-byte FP16 rows)
-constexpr int TQ_STAGES = 3;
+constexpr int TQ_STAGES = 3;                   // the MMA issuer selects among 3 stage descriptors
 constexpr int TQ_A_BYTES = TQ_BM * TQ_BK * 2;
 constexpr int TQ_B_BYTES = TQ_BN * TQ_BK * 2;
 constexpr int TQ_STAGE_BYTES = TQ_A_BYTES + TQ_B_BYTES;
@@ -379,29 +379,43 @@ __global__ void __launch_bounds__(TQ_THREADS, 1) scan_tc_kernel(DevIndex ix, TqA
 
     if (warp == TQ_MMA_WARP) {
         // ---------------- MMA issuer ----------------
+        // One thread; the per-stage path is kept short: descriptors of each
+        // stage precomputed (the K step of 16 FP16 is 32 bytes, 2 in the
+        // descriptor's 16-byte address units), a wait first tried without
+        // reading the clock, and the stop flag read only after a wait failed
+        // (the other roles stop by ceasing to arrive).
         if (lane == 0) {
-            uint32_t g = 0, tcount = 0;
+            uint32_t g = 0, tcount = 0, s = 0, ph = 0;           // stage and its phase parity
             bool ok = true;
+            uint64_t ad[TQ_STAGES], bd[TQ_STAGES];
+#pragma unroll
+            for (int q = 0; q < TQ_STAGES; ++q) {
+                ad[q] = sw128_desc(sbase + q * TQ_STAGE_BYTES);
+                bd[q] = sw128_desc(sbase + q * TQ_STAGE_BYTES + TQ_A_BYTES);
+            }
+            auto wait = [&](uint32_t bar, uint32_t par) -> bool {
+                if (mbar_try_wait(bar, par)) return true;
+                return mbar_wait(bar, par) && !*s_abort;
+            };
             for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
-                const int4 item = a.items[it];
-                const int len = ix.list_len[item.x];
+                const int len = ix.list_len[a.items[it].x];
                 for (int t = 0; t * TQ_BN < len && ok; ++t, ++tcount) {
                     const uint32_t b = tcount & 1u, v = tcount >> 1;
-                    if (!mbar_wait(acce(b), (v & 1u) ^ 1u) || *s_abort) { ok = false; break; }
+                    if (!wait(acce(b), (v & 1u) ^ 1u)) { ok = false; break; }
                     tc_fence_after();
                     const int nt = min(TQ_BN, len - t * TQ_BN);
                     const uint32_t idesc = tq_idesc((nt + 15) / 16 * 16);
                     const uint32_t dcol = tmem + b * (uint32_t)TQ_BN;
                     for (int i = 0; i < KCH; ++i, ++g) {
-                        const uint32_t s = g % S, u = g / S;
-                        if (!mbar_wait(full(s), u & 1u) || *s_abort) { ok = false; break; }
+                        if (!wait(full(s), ph)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t a_s = sbase + s * TQ_STAGE_BYTES, b_s = a_s + TQ_A_BYTES;
+                        const uint64_t a0 = ad[0], a1 = ad[1], a2 = ad[2], b0 = bd[0], b1 = bd[1], b2 = bd[2];
+                        const uint64_t as = s == 0 ? a0 : (s == 1 ? a1 : a2), bs = s == 0 ? b0 : (s == 1 ? b1 : b2);
 #pragma unroll
                         for (int k = 0; k < TQ_BK / 16; ++k)
-                            tc_mma_f16(dcol, sw128_desc(a_s + 32u * k), sw128_desc(b_s + 32u * k), idesc,
-                                       (i | k) != 0 ? 1u : 0u);
+                            tc_mma_f16(dcol, as + 2u * k, bs + 2u * k, idesc, (i | k) != 0 ? 1u : 0u);
                         tc_commit(empty(s));
+                        if (++s == TQ_STAGES) { s = 0; ph ^= 1u; }
                     }
                     if (!ok) break;
                     tc_commit(accf(b));
