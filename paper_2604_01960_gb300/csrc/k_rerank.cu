@@ -363,10 +363,9 @@ cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, c
 // distance (rounding is monotone) -- scatter them by bin and give each key
 // its bin's start plus the number of smaller keys in its bin; bins with many
 // keys (many equal distances) are sorted instead.  The constants below belong
-// to the form for K_c above TK_MAX (global scratch); the shared-memory form
-// has its own (TKS_*).
+// to the form for large k (global scratch); the shared-memory form has its own
+// (TKS_*).
 constexpr int TK_THREADS = 1024;
-constexpr int TK_MAX = 16384;    // candidates handled in shared memory per query
 constexpr int TK_BINS = 4096;
 constexpr int TK_BIG = 2048;
 constexpr int TK_HEAVY = 8192;   // a heavy bin of the large top-k sorted in shared memory
@@ -426,7 +425,8 @@ __device__ void cta_sort_any_u64(unsigned long long* a, int n) {
     }
 }
 
-// Top-k for K_c <= TK_MAX, one CTA per query, two CTAs per SM.
+// Top-k of any number of candidates when k + TKS_BIG keys fit in shared memory
+// (TK_SMEM_KEYS), one CTA per query (two per SM while the keys take half of it).
 // 1. min / max of the distances; histogram over TKS_BINS bins in value space
 //    (bin = floor((dist - min) * TKS_BINS / (max - min)) in FP32, a monotone
 //    function of the distance); exclusive scan -> bin starts;
@@ -443,6 +443,7 @@ constexpr int TKS_BINS = 2048;
 constexpr int TKS_BIG = 1024;
 constexpr int TKS_MAXHEAVY = 64;
 constexpr int TKS_U = 8;
+constexpr int TK_SMEM_KEYS = 24576;   // keys of the shared-memory form: k - 1 + TKS_BIG at most
 
 __global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, RerankArgs a, int kcap) {
     extern __shared__ unsigned long long keys[];   // [kcap]
@@ -452,11 +453,9 @@ __global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, Reran
     __shared__ uint32_t heavy[TKS_MAXHEAVY];
     __shared__ uint32_t s_min, s_max, s_bk, s_nheavy;
     const int64_t qi = blockIdx.x;
-    const int64_t cnt = min(a.cand_count[qi], a.qp.KC(qi));
-    const int n = (int)(cnt < TK_MAX ? cnt : TK_MAX);
+    const int n = (int)min(a.cand_count[qi], a.qp.KC(qi));
     const int tid = threadIdx.x;
     const int kq = a.qp.K(qi);
-    if (cnt > TK_MAX && tid == 0) atomicOr(ix.status, kStatusTopkOverrun);
     const uint32_t* cand = a.cand + a.qp.coff(qi);
     const float* cd = a.cdist + a.qp.coff(qi);
     int64_t* oid = a.out_ids + a.qp.ooff(qi);
@@ -588,7 +587,8 @@ __global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, Reran
     }
 }
 
-// Same output for K_c above TK_MAX.  The distance of rank k is found first
+// Same output when k - 1 + TKS_BIG keys do not fit in shared memory.  The
+// distance of rank k is found first
 // (radix select); only keys at or below it are binned (value space between
 // the minimum and that distance) and scattered into a global scratch area
 // (RerankArgs::keys, per QueryParams::coff).  Bins of at most TK_BIG keys are
@@ -675,7 +675,8 @@ __global__ void __launch_bounds__(TK_THREADS) topk_large_kernel(DevIndex ix, Rer
 
 cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
-    if (a.kc > TK_MAX) {
+    if ((long long)a.k + TKS_BIG > TK_SMEM_KEYS) {
+        // the k kept keys do not fit in shared memory: global scratch
         if (!a.keys) return cudaErrorInvalidValue;
         cudaError_t e = smem_attr_once((const void*)topk_large_kernel, TK_HEAVY * 8);
         if (e != cudaSuccess) return e;
@@ -683,9 +684,9 @@ cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cud
         return cudaGetLastError();
     }
     // keys held per query: all candidates, or at most k - 1 + TKS_BIG of them
-    const long long kcap = std::min<long long>(std::min<long long>(a.kc, TK_MAX), (long long)a.k + TKS_BIG);
+    const long long kcap = std::min<long long>(a.kc, (long long)a.k + TKS_BIG);
     const size_t smem = (size_t)std::max<long long>(kcap, 1) * 8;
-    cudaError_t e = smem_attr_once((const void*)topk_kernel, TK_MAX * 8);
+    cudaError_t e = smem_attr_once((const void*)topk_kernel, TK_SMEM_KEYS * 8);
     if (e != cudaSuccess) return e;
     topk_kernel<<<(unsigned)nq, TKS_THREADS, smem, st>>>(ix, a, (int)std::max<long long>(kcap, 1));
     return cudaGetLastError();

@@ -341,7 +341,7 @@ def test_search_ex_mixed_batch_equals_alone(bbc, oracle_lib, kind, mode):
 
 
 def test_large_candidate_pool_topk(bbc, oracle_lib):
-    """K_c above the shared-memory top-k capacity (global-scratch path), exact on integer data."""
+    """K_c above 16,384 (more candidates than the shared-memory top-k keeps), exact on integer data."""
     h, idx, q = dev_index(bbc, "medium")
     k, nprobe, ratio = 12000, 96, 1.5
     bbc.bbc_set_param(h, "kc_ratio", ratio)
@@ -358,16 +358,19 @@ def test_large_candidate_pool_topk(bbc, oracle_lib):
         _check_topk(oracle_lib, idx, q[i], gi[i], gd[i], oi[i], od[i], True)
 
 
-@pytest.mark.parametrize("case,kc,k", [("ties", 30000, 20000), ("inner_product", 30000, 20000),
+@pytest.mark.parametrize("case,kc,k", [("ties", 30000, 25000), ("inner_product", 30000, 25000),
+                                       ("ties", 30000, 20000), ("inner_product", 30000, 20000),
                                        ("ties", 12000, 5000), ("ties", 12000, 11500), ("ties", 12000, 1),
                                        ("inner_product", 12000, 3000)])
 def test_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case, kc, k):
     """Top-k on candidates with thousands of equal distances and on inner
-    products whose distances span the sign boundary.  K_c = 30,000 takes the
-    global-scratch form (one block of ties above its shared-memory sort, one
-    within it); K_c = 12,000 the shared-memory form, where a block of ties
-    holds the k-th place (k = 5,000: selected inside the bin) or lies below it
-    (k = 11,500: the bin is sorted in place)."""
+    products whose distances span the sign boundary.  k = 25,000 takes the
+    global-scratch form (its kept keys exceed shared memory; one block of ties
+    above its shared-memory sort, one within it); k = 20,000 over 30,000
+    candidates the shared-memory form with more candidates than it keeps;
+    K_c = 12,000 the shared-memory form, where a block of ties holds the k-th
+    place (k = 5,000: selected inside the bin) or lies below it (k = 11,500:
+    the bin is sorted in place)."""
     from synth import build_ivf_pq
     from synth.data import sift_shaped, embedding_shaped
     if case == "ties":
