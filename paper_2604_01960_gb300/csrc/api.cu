@@ -1627,8 +1627,11 @@ int bbc_search_host(bbc_index* ix, const float* queries, int64_t nq, int32_t k, 
     // Sub-batches whose results go back on a second stream while the next
     // sub-batches compute: a sub-batch keeps >= 8 queries per SM (one CTA per
     // query fills the GPU), up to three result buffers rotate so that a slow
-    // copy-out does not hold up the next sub-batch.
-    int64_t sb = std::max<int64_t>(8ll * ix->dev.num_sms, (nq + 3) / 4);
+    // copy-out does not hold up the next sub-batch.  The list-grouped
+    // tensor-core scan gains from more queries per list, so its sub-batches
+    // are half the batch (the results of one copy out in less time than the
+    // next half computes).
+    int64_t sb = std::max<int64_t>(8ll * ix->dev.num_sms, tc_active(ix) ? (nq + 1) / 2 : (nq + 3) / 4);
     sb = std::min<int64_t>(sb, std::max<int64_t>(1, p.chunk / 2));
     int nbuf = 2 * sb <= p.chunk ? 2 : 1;
     if (nbuf == 2 && 3 * sb <= p.chunk) nbuf = 3;
