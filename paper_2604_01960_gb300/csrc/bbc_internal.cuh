@@ -231,16 +231,15 @@ size_t pair_plan_bytes(int64_t nq);
 cudaError_t launch_pair_plan(const float* q, int d, int64_t nq, const QueryParams& qp, const int32_t* lists,
                              void* scratch, int32_t* perm, cudaStream_t st);
 
-// The codebook of each query from its sampled objects at the start of its
-// region (state: pushed = sample size), with bucket counts and tau.
-cudaError_t launch_codebook(int64_t nq, const ScanArgs& a, cudaStream_t st);
-
 // List-grouped form on the tensor cores (k_scan_tc.cu): 4-bit codes, tables
-// with entries <= 2047 given as FP16 (lut_f16 [nq][16 M]), plain PQ, m <=
-// 64 buckets.  Same state and region contents (up to order) as the one-query
-// scan on the same table; the state array must be zeroed first; scratch
-// holds scan_tc_plan_bytes(ix, sum of nprobe) bytes.  The selection (S7)
-// runs after it.
+// with entries <= 2047 (a.lut16, and the same entries as FP16 in lut_f16
+// [nq][16 M]), plain PQ, m <= 64 buckets.  Runs the one-query scan over the
+// sampled lists first (codebooks), then the list-grouped pass.  The same
+// candidates and collector state (codebook, tau*, counts of the buckets <=
+// tau*) as the one-query scan on the same table; the region may hold more
+// appended pairs (tau is refreshed once per item).  The state array must be
+// zeroed first; scratch holds scan_tc_plan_bytes(ix, sum of nprobe) bytes.
+// The selection (S7) runs after it.
 bool scan_tc_supported(const DevIndex& ix, int m);
 size_t scan_tc_plan_bytes(const DevIndex& ix, int64_t sum_probe);
 cudaError_t launch_scan_tc(const DevIndex& ix, int64_t nq, const ScanArgs& a, const uint16_t* lut_f16,

@@ -1813,12 +1813,6 @@ bool scan_supported(int M, int bits) {
     return false;
 }
 
-cudaError_t launch_codebook(int64_t nq, const ScanArgs& a, cudaStream_t st) {
-    if (nq <= 0) return cudaSuccess;
-    codebook_kernel<<<(unsigned)nq, SCAN_THREADS, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_scan_split(const DevIndex& ix, int64_t nq, const ScanArgs& a, int G, unsigned int* counters,
                               cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
