@@ -779,6 +779,9 @@ def measure(args, ws, rank, local, bbc, index, w, idx, q, k, nprobe, t_build, xt
     u8 = bool(index.get("rerank"))
     if prec:
         rr_bytes = nq * kc * (dpad * (2 if prec == 1 else 1) + 16 + 4 + 8)
+    elif per.get("topk", 0.0) <= 0.0:
+        # re-rank and top-k in one kernel: rows and ids in, the k results out (distances stay on chip)
+        rr_bytes = nq * kc * (idx.d * (1 if u8 else 4) + 4) + nq * k * 12
     else:
         rr_bytes = nq * kc * (idx.d * (1 if u8 else 4) + 4 + 4)
     unc = (pstats["fp32_rechecked"] if pstats else 0) * args.steps / max(1, args.steps)

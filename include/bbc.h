@@ -235,6 +235,14 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  ("collector" 0) and without "early_rerank"; a search whose
  *                  index or buckets do not fit returns BBC_ERR_UNSUPPORTED.
  *                  Default 0.
+ *   "rerank_fused" 1 = the exact re-rank (step S8) and the top-k (step S9) run
+ *                  as one kernel, a CTA per query keeping its candidates'
+ *                  distances in shared memory, when the largest K_c of the
+ *                  batch and k fit there (8 K_c + 8 (k + 1024) + 5 d bytes <=
+ *                  215 KB; K_c = 15,000 with k = 10,000 does); otherwise, and
+ *                  with 0, two kernels with the distances in the workspace.
+ *                  Same results either way; with "profile" the fused kernel's
+ *                  time is the re-rank stage's.  Default 1.
  *   "region_cap"   entries of each query's collector region (the buffer the
  *                  scan appends (estimated distance, position) pairs to).
  *                  0 (default) = the total length of the nprobe longest lists,

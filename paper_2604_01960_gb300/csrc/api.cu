@@ -140,18 +140,19 @@ struct bbc_index {
     int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
     int lut_levels = 65535;   // top level of the integer lookup tables
     int scan_tc = 0;          // 1: list-grouped scan on the tensor cores (4-bit codes; tables <= 2047)
+    int rerank_fused = 1;     // 1: re-rank and top-k in one kernel where the candidates fit in shared memory
     bool capturing = false;
     struct GraphKey {
         const void* q; int64_t nq; int k; int nprobe; void* oi; void* od; cudaStream_t st;
         double kc_ratio; int buckets, sample_lists, split, probe_gemm, rerank, prec;
         int64_t rcap;
-        int pair, collector, early, lut_levels, scan_tc;
+        int pair, collector, early, lut_levels, scan_tc, rerank_fused;
         bool operator<(const GraphKey& o) const {
             return std::tie(q, nq, k, nprobe, oi, od, st, kc_ratio, buckets, sample_lists, split, probe_gemm, rerank,
-                            prec, rcap, pair, collector, early, lut_levels, scan_tc) <
+                            prec, rcap, pair, collector, early, lut_levels, scan_tc, rerank_fused) <
                    std::tie(o.q, o.nq, o.k, o.nprobe, o.oi, o.od, o.st, o.kc_ratio, o.buckets, o.sample_lists, o.split,
                             o.probe_gemm, o.rerank, o.prec, o.rcap, o.pair, o.collector, o.early, o.lut_levels,
-                            o.scan_tc);
+                            o.scan_tc, o.rerank_fused);
         }
     };
     struct GraphEntry { cudaGraphExec_t exec; int64_t launches; };
@@ -416,6 +417,11 @@ cudaError_t stage(bbc_index* ix, int id, cudaStream_t st, F&& launch) {
 int run_rerank(bbc_index* ix, int64_t nc, const RerankArgs& ra, const PrecArgs* pa, int maxk, cudaStream_t st) {
     const DevIndex& d = ix->dev;
     if (!pa) {
+        if (ix->rerank_fused && rerank_topk_fits(d, ra)) {
+            // both steps in one kernel: recorded as the re-rank stage
+            CUDA_TRY(stage(ix, 5, st, [&] { return launch_rerank_topk(d, nc, ra, st); }));
+            return BBC_OK;
+        }
         CUDA_TRY(stage(ix, 5, st, [&] { return launch_rerank(d, nc, ra, st); }));
         CUDA_TRY(stage(ix, 6, st, [&] { return launch_topk(d, nc, ra, st); }));
         return BBC_OK;
@@ -1421,6 +1427,9 @@ int bbc_set_param(bbc_index* ix, const char* key, double v) {
         ix->scan_tc = (int)v;
         // the tensor cores take tables whose entries FP16 holds exactly
         if (v == 1 && ix->lut_levels > 2047) ix->lut_levels = 2047;
+    } else if (k == "rerank_fused") {
+        if (v != 0 && v != 1) return fail(BBC_ERR_ARG, "rerank_fused must be 0 or 1");
+        ix->rerank_fused = (int)v;
     } else if (k == "region_cap") {
         if (!(v >= 0 && v <= 9.0e15) || v != std::floor(v)) return fail(BBC_ERR_ARG, "region_cap must be 0 (automatic) or a positive integer");
         ix->region_cap = (int64_t)v;
@@ -1453,6 +1462,7 @@ int bbc_get_param(const bbc_index* ix, const char* key, double* v) {
     else if (k == "early_rerank") *v = ix->early_rerank;
     else if (k == "lut_levels") *v = ix->lut_levels;
     else if (k == "scan_tc") *v = ix->scan_tc;
+    else if (k == "rerank_fused") *v = ix->rerank_fused;
     else return fail(BBC_ERR_ARG, "unknown parameter '%s'", key);
     return BBC_OK;
 }
@@ -1483,7 +1493,7 @@ int bbc_search(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int32
     bbc_index::GraphKey key{queries, nq, k, nprobe, out_ids, out_dists, st, ix->kc_ratio, ix->buckets,
                             ix->sample_lists, ix->split, ix->probe_gemm, ix->rerank_u8, ix->dev.prec,
                             ix->region_cap, ix->pair, ix->collector, ix->early_rerank, ix->lut_levels,
-                            ix->scan_tc};
+                            ix->scan_tc, ix->rerank_fused};
     std::lock_guard<std::mutex> lk(ix->graph_mu);
     auto it = ix->graph_cache.find(key);
     if (it == ix->graph_cache.end()) {

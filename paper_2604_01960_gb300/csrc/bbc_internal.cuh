@@ -266,6 +266,11 @@ struct RerankArgs {
 // S8: exact distances of the candidates; S9: k smallest (dist, id), sorted.
 cudaError_t launch_rerank(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
 cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
+// S8 + S9 in one kernel per query (distances kept in shared memory), when
+// rerank_topk_fits: the batch's largest K_c distances and ids and the k - 1 +
+// 1,024 kept keys fit in one CTA's shared memory.  Same results as the two.
+bool rerank_topk_fits(const DevIndex& ix, const RerankArgs& a);
+cudaError_t launch_rerank_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st);
 // The early re-rank's copy: rows[slot] = vec_u8[ids[slot]] (zero for padding
 // slots), norms[slot] = ||row||^2, for nslots = 32 * blocks slots.
 cudaError_t launch_early_copy(const DevIndex& ix, int64_t nslots, uint8_t* rows, uint32_t* norms, cudaStream_t st);

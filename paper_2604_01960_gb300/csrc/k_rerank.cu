@@ -150,6 +150,27 @@ __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restr
     }
 }
 
+// Stages one query row for the re-rank: rq = its FP32 components; for u8 rows
+// also q8 = the components as bytes, with *s_int cleared unless every
+// component is an integer in [0, 255] and *s_qn2 accumulating ||q||^2.  The
+// caller sets *s_int = 1 and *s_qn2 = 0 and synchronises before and after.
+template <typename T>
+__device__ __forceinline__ void rr_stage_query(const float* __restrict__ qrow, int d, float* rq, uint8_t* q8,
+                                               int* s_int, int* s_qn2) {
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        const float v = qrow[i];
+        rq[i] = v;
+        if (sizeof(T) == 1) {
+            const bool ok = v >= 0.f && v <= 255.f && v == floorf(v);
+            if (!ok) *s_int = 0;
+            q8[i] = ok ? (uint8_t)v : 0;
+            if (ok) atomicAdd(s_qn2, (int)v * (int)v);
+        }
+    }
+}
+
+// Exact distances of candidates [c0, c1) of query qi, every thread of the block
+// taking part: candidate c has id sid[c - c0] and its distance goes to out[c].
 // One group of G lanes per candidate row; rows gathered with 16-byte loads.
 // Exact-u8 rows with a query whose components are integers in [0, 255] take
 // the integer path: <q, v> and <v, v> with dp4a, ||q - v||^2 = ||q||^2 +
@@ -158,56 +179,26 @@ __device__ __forceinline__ void rerank_rows(const DevIndex& ix, const T* __restr
 // query, 512-byte FP32 rows) take the fixed-shape path.  Other shapes use the
 // FAST = false instantiation, whose general loop then keeps its own register
 // allocation and schedule.
-template <typename T, bool FAST, bool EARLY = false>
-__global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankArgs a, const T* __restrict__ vec) {
-    extern __shared__ uint4 rsm[];
+template <typename T, bool FAST, bool EARLY>
+__device__ __forceinline__ void rr_span(const DevIndex& ix, const RerankArgs& a, int64_t qi, const T* __restrict__ vec,
+                                        const uint32_t* sid, int64_t c0, int64_t c1, float* out, const float* rq,
+                                        const uint8_t* q8, bool intpath, int qn2) {
     const int d = ix.d;
-    float* rq = reinterpret_cast<float*>(rsm);                 // d floats
-    uint8_t* q8 = reinterpret_cast<uint8_t*>(rsm + d / 4);     // d bytes (u8 rows only)
-    __shared__ int s_int, s_qn2;
-    __shared__ uint32_t sid[RR_CAND_PER_CTA];                  // this CTA's candidate ids
-    const int64_t qi = blockIdx.y;
-    if (threadIdx.x == 0) { s_int = 1; s_qn2 = 0; }
-    {
-        // ids staged with coalesced loads, so row gathers wait on one latency
-        const int64_t cn = min(a.cand_count[qi], a.qp.KC(qi));
-        const int64_t b0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
-        const uint32_t* cp = a.cand + a.qp.coff(qi);
-        for (int i = threadIdx.x; i < RR_CAND_PER_CTA; i += blockDim.x)
-            sid[i] = b0 + i < cn ? cp[b0 + i] : 0u;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < d; i += blockDim.x) {
-        const float v = a.q[qi * d + i];
-        rq[i] = v;
-        if (sizeof(T) == 1) {
-            const bool ok = v >= 0.f && v <= 255.f && v == floorf(v);
-            if (!ok) s_int = 0;
-            q8[i] = ok ? (uint8_t)v : 0;
-            if (ok) atomicAdd(&s_qn2, (int)v * (int)v);
-        }
-    }
-    __syncthreads();
-    const bool intpath = sizeof(T) == 1 && s_int;
-    const int qn2 = s_qn2;
-    const int64_t cnt = min(a.cand_count[qi], a.qp.KC(qi));
     const int nchunk = d * (int)sizeof(T) / 16;        // d * sizeof(T) is a multiple of 16
-    const int64_t cf0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
-    const int64_t cf1 = min(cf0 + RR_CAND_PER_CTA, cnt);
     // the common row shapes: 128-byte integer rows, 512-byte FP32 rows
     if (FAST && sizeof(T) == 1 && intpath && nchunk == 8) {
         if (EARLY)
-            rerank_rows<T, 4, 2, true, true>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
-                                             reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8),
-                                             qn2, a.early + a.qp.coff(qi), a.early_totals ? a.early_totals + 1 : nullptr);
+            rerank_rows<T, 4, 2, true, true>(ix, vec, d, sid, c0, c1, out, reinterpret_cast<const float4*>(rq),
+                                             reinterpret_cast<const uint4*>(q8), qn2, a.early + a.qp.coff(qi),
+                                             a.early_totals ? a.early_totals + 1 : nullptr);
         else
-            rerank_rows<T, 4, 2, true>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
-                                       reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2);
+            rerank_rows<T, 4, 2, true>(ix, vec, d, sid, c0, c1, out, reinterpret_cast<const float4*>(rq),
+                                       reinterpret_cast<const uint4*>(q8), qn2);
         return;
     }
     if (FAST && sizeof(T) == 4 && nchunk == 32) {
-        rerank_rows<T, 16, 2, false>(ix, vec, d, sid, cf0, cf1, a.cdist + a.qp.coff(qi),
-                                     reinterpret_cast<const float4*>(rq), reinterpret_cast<const uint4*>(q8), qn2);
+        rerank_rows<T, 16, 2, false>(ix, vec, d, sid, c0, c1, out, reinterpret_cast<const float4*>(rq),
+                                     reinterpret_cast<const uint4*>(q8), qn2);
         return;
     }
     int G = 1;                                         // lanes per candidate: a power of two <= 32
@@ -215,9 +206,6 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
     const int per_warp = 32 / G;
     const int ln = (int)lane_id();
     const int grp = ln / G, gl = ln % G;
-    const int64_t c0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
-    const int64_t c1 = min(c0 + RR_CAND_PER_CTA, cnt);
-    float* out = a.cdist + a.qp.coff(qi);
     const float4* q4 = reinterpret_cast<const float4*>(rq);
     const uint4* qb = reinterpret_cast<const uint4*>(q8);
     // RR_U candidates per group per step, their row loads issued together
@@ -313,6 +301,33 @@ __global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankA
             if (c < c1 && gl == 0) out[c] = dist[u];
         }
     }
+}
+
+// S8 alone: a CTA per (query, RR_CAND_PER_CTA candidates); distances to RerankArgs::cdist.
+template <typename T, bool FAST, bool EARLY = false>
+__global__ void __launch_bounds__(RR_THREADS) rerank_kernel(DevIndex ix, RerankArgs a, const T* __restrict__ vec) {
+    extern __shared__ uint4 rsm[];
+    const int d = ix.d;
+    float* rq = reinterpret_cast<float*>(rsm);                 // d floats
+    uint8_t* q8 = reinterpret_cast<uint8_t*>(rsm + d / 4);     // d bytes (u8 rows only)
+    __shared__ int s_int, s_qn2;
+    __shared__ uint32_t sid[RR_CAND_PER_CTA];                  // this CTA's candidate ids
+    const int64_t qi = blockIdx.y;
+    const int64_t cnt = min(a.cand_count[qi], a.qp.KC(qi));
+    const int64_t c0 = (int64_t)blockIdx.x * RR_CAND_PER_CTA;
+    const int64_t c1 = min(c0 + RR_CAND_PER_CTA, cnt);
+    if (threadIdx.x == 0) { s_int = 1; s_qn2 = 0; }
+    {
+        // ids staged with coalesced loads, so row gathers wait on one latency
+        const uint32_t* cp = a.cand + a.qp.coff(qi);
+        for (int i = threadIdx.x; i < RR_CAND_PER_CTA; i += blockDim.x)
+            sid[i] = c0 + i < cnt ? cp[c0 + i] : 0u;
+    }
+    __syncthreads();
+    rr_stage_query<T>(a.q + qi * d, d, rq, q8, &s_int, &s_qn2);
+    __syncthreads();
+    rr_span<T, FAST, EARLY>(ix, a, qi, vec, sid, c0, c1, a.cdist + a.qp.coff(qi), rq, q8, sizeof(T) == 1 && s_int,
+                            s_qn2);
 }
 
 // The early re-rank's slot-ordered copy: one warp per slot copies the u8 row
@@ -445,19 +460,19 @@ constexpr int TKS_MAXHEAVY = 64;
 constexpr int TKS_U = 8;
 constexpr int TK_SMEM_KEYS = 24576;   // keys of the shared-memory form: k - 1 + TKS_BIG at most
 
-__global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, RerankArgs a, int kcap) {
-    extern __shared__ unsigned long long keys[];   // [kcap]
+// The body for query qi, its n candidates' distances cd[] and ids cand[] (in
+// global or shared memory), keys[kcap] in shared memory; blockDim.x == THREADS.
+template <int THREADS, int U>
+__device__ __forceinline__ void topk_query(const DevIndex& ix, const RerankArgs& a, int64_t qi, int n,
+                                           const float* cd, const uint32_t* cand, unsigned long long* keys,
+                                           int kcap) {
     __shared__ uint32_t bins[TKS_BINS];
-    __shared__ uint32_t wsum[TKS_THREADS / 32];
+    __shared__ uint32_t wsum[THREADS / 32];
     __shared__ uint32_t hist[256], sc[2];
     __shared__ uint32_t heavy[TKS_MAXHEAVY];
     __shared__ uint32_t s_min, s_max, s_bk, s_nheavy;
-    const int64_t qi = blockIdx.x;
-    const int n = (int)min(a.cand_count[qi], a.qp.KC(qi));
     const int tid = threadIdx.x;
     const int kq = a.qp.K(qi);
-    const uint32_t* cand = a.cand + a.qp.coff(qi);
-    const float* cd = a.cdist + a.qp.coff(qi);
     int64_t* oid = a.out_ids + a.qp.ooff(qi);
     float* od = a.out_dists + a.qp.ooff(qi);
     for (int i = n + tid; i < kq; i += blockDim.x) { oid[i] = -1; od[i] = INFINITY; }
@@ -466,17 +481,16 @@ __global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, Reran
     if (tid == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_nheavy = 0u; }
     for (int i = tid; i < TKS_BINS; i += blockDim.x) bins[i] = 0;
     __syncthreads();
-    // passes over the candidates load TKS_U values per thread before using them
-    constexpr int U = TKS_U;
-    const int step = U * TKS_THREADS;
+    // passes over the candidates load U values per thread before using them
+    const int step = U * THREADS;
     uint32_t mn = 0xFFFFFFFFu, mx = 0u;
     for (int i0 = tid; i0 < n; i0 += step) {
         float v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = i0 + u * TKS_THREADS < n ? cd[i0 + u * TKS_THREADS] : 0.f;
+        for (int u = 0; u < U; ++u) v[u] = i0 + u * THREADS < n ? cd[i0 + u * THREADS] : 0.f;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (i0 + u * TKS_THREADS < n) {
+            if (i0 + u * THREADS < n) {
                 const uint32_t kv = f32_key(v[u]);
                 mn = min(mn, kv);
                 mx = max(mx, kv);
@@ -497,15 +511,15 @@ __global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, Reran
     for (int i0 = tid; i0 < n; i0 += step) {
         float v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = i0 + u * TKS_THREADS < n ? cd[i0 + u * TKS_THREADS] : 0.f;
+        for (int u = 0; u < U; ++u) v[u] = i0 + u * THREADS < n ? cd[i0 + u * THREADS] : 0.f;
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (i0 + u * TKS_THREADS < n) atomicAdd(&bins[vbin(v[u])], 1u);
+            if (i0 + u * THREADS < n) atomicAdd(&bins[vbin(v[u])], 1u);
     }
     __syncthreads();
-    constexpr int PER = TKS_BINS / TKS_THREADS;
+    constexpr int PER = TKS_BINS / THREADS;
     uint32_t loc[PER];
-    tk_scan<PER, TKS_THREADS>(bins, wsum, loc);
+    tk_scan<PER, THREADS>(bins, wsum, loc);
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const uint32_t b = (uint32_t)tid * PER + j;
@@ -528,13 +542,13 @@ __global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, Reran
         uint32_t c[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const bool in = i0 + u * TKS_THREADS < n;
-            v[u] = in ? cd[i0 + u * TKS_THREADS] : 0.f;
-            c[u] = in ? cand[i0 + u * TKS_THREADS] : 0u;
+            const bool in = i0 + u * THREADS < n;
+            v[u] = in ? cd[i0 + u * THREADS] : 0.f;
+            c[u] = in ? cand[i0 + u * THREADS] : 0u;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (i0 + u * TKS_THREADS >= n) continue;
+            if (i0 + u * THREADS >= n) continue;
             const uint32_t b = vbin(v[u]);
             const unsigned long long key = ((unsigned long long)f32_key(v[u]) << 32) | c[u];
             if (b < bk || (b == bk && key <= T)) {
@@ -585,6 +599,56 @@ __global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, Reran
             od[i] = key_f32((uint32_t)(keys[i] >> 32));
         }
     }
+}
+
+__global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, RerankArgs a, int kcap) {
+    extern __shared__ unsigned long long keys[];   // [kcap]
+    const int64_t qi = blockIdx.x;
+    const int n = (int)min(a.cand_count[qi], a.qp.KC(qi));
+    topk_query<TKS_THREADS, TKS_U>(ix, a, qi, n, a.cdist + a.qp.coff(qi), a.cand + a.qp.coff(qi), keys, kcap);
+}
+
+// S8 + S9 in one kernel: a CTA per query computes the exact distances of its
+// candidates into shared memory (rr_span) and takes their top-k there
+// (topk_query), so the distances never travel to global memory and the
+// top-k's passes over the candidates read shared memory.  Applies when the
+// batch's largest K_c distances and ids and the k - 1 + TKS_BIG kept keys fit
+// in one CTA's shared memory (K_c = 15,000 with k = 10,000: 204 KB).  Same
+// arithmetic, so the same results, as rerank_kernel followed by topk_kernel.
+constexpr int RT_THREADS = 1024;
+constexpr int RT_U = 4;
+constexpr int RT_SMEM_MAX = 215 * 1024;     // dynamic part; the static part (top-k bins) is under 12 KB
+
+__host__ __device__ inline size_t rt_smem_bytes(long long kcap, long long ncap, int d) {
+    return (size_t)((kcap + 1) & ~1ll) * 8 + (size_t)((ncap + 3) & ~3ll) * 8 + (size_t)d * 5;
+}
+
+template <typename T, bool FAST, bool EARLY>
+__global__ void __launch_bounds__(RT_THREADS, 1)
+    rerank_topk_kernel(DevIndex ix, RerankArgs a, const T* __restrict__ vec, int kcap, int ncap) {
+    extern __shared__ uint4 fsm[];
+    const int d = ix.d;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(fsm);    // [kcap]
+    float* dist = reinterpret_cast<float*>(keys + ((kcap + 1) & ~1));         // [ncap]
+    uint32_t* sid = reinterpret_cast<uint32_t*>(dist + ((ncap + 3) & ~3));    // [ncap]
+    float* rq = reinterpret_cast<float*>(sid + ((ncap + 3) & ~3));           // d floats (16-byte aligned)
+    uint8_t* q8 = reinterpret_cast<uint8_t*>(rq + d);                         // d bytes (u8 rows only)
+    __shared__ int s_int, s_qn2;
+    const int64_t qi = blockIdx.x;
+    int n = (int)min(a.cand_count[qi], a.qp.KC(qi));
+    if (n > ncap) {                                                            // never expected
+        if (threadIdx.x == 0) atomicOr(ix.status, kStatusTopkOverrun);
+        n = ncap;
+    }
+    if (threadIdx.x == 0) { s_int = 1; s_qn2 = 0; }
+    const uint32_t* cp = a.cand + a.qp.coff(qi);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sid[i] = cp[i];
+    __syncthreads();
+    rr_stage_query<T>(a.q + qi * d, d, rq, q8, &s_int, &s_qn2);
+    __syncthreads();
+    rr_span<T, FAST, EARLY>(ix, a, qi, vec, sid, 0, n, dist, rq, q8, sizeof(T) == 1 && s_int, s_qn2);
+    __syncthreads();
+    topk_query<RT_THREADS, RT_U>(ix, a, qi, n, dist, sid, keys, kcap);
 }
 
 // Same output when k - 1 + TKS_BIG keys do not fit in shared memory.  The
@@ -690,6 +754,32 @@ cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cud
     if (e != cudaSuccess) return e;
     topk_kernel<<<(unsigned)nq, TKS_THREADS, smem, st>>>(ix, a, (int)std::max<long long>(kcap, 1));
     return cudaGetLastError();
+}
+
+bool rerank_topk_fits(const DevIndex& ix, const RerankArgs& a) {
+    if ((long long)a.k + TKS_BIG > TK_SMEM_KEYS) return false;
+    const long long kcap = std::max<long long>(std::min<long long>(a.kc, (long long)a.k + TKS_BIG), 1);
+    return rt_smem_bytes(kcap, std::max<long long>(a.kc, 1), ix.d) <= (size_t)RT_SMEM_MAX;
+}
+
+template <typename T, bool FAST, bool EARLY>
+static cudaError_t rt_launch(const DevIndex& ix, int64_t nq, const RerankArgs& a, const T* vec, cudaStream_t st) {
+    const long long kcap = std::max<long long>(std::min<long long>(a.kc, (long long)a.k + TKS_BIG), 1);
+    const long long ncap = std::max<long long>(a.kc, 1);
+    cudaError_t e = smem_attr_once((const void*)rerank_topk_kernel<T, FAST, EARLY>, RT_SMEM_MAX);
+    if (e != cudaSuccess) return e;
+    rerank_topk_kernel<T, FAST, EARLY><<<(unsigned)nq, RT_THREADS, rt_smem_bytes(kcap, ncap, ix.d), st>>>(
+        ix, a, vec, (int)kcap, (int)ncap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rerank_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    if (!rerank_topk_fits(ix, a)) return cudaErrorInvalidValue;
+    if (a.use_u8 && ix.vec_u8 && a.early) return rt_launch<uint8_t, true, true>(ix, nq, a, ix.vec_u8, st);
+    if (a.use_u8 && ix.vec_u8) return rt_launch<uint8_t, true, false>(ix, nq, a, ix.vec_u8, st);
+    if (ix.d * 4 == 32 * 16) return rt_launch<float, true, false>(ix, nq, a, ix.vectors, st);
+    return rt_launch<float, false, false>(ix, nq, a, ix.vectors, st);
 }
 
 }  // namespace bbc

@@ -362,7 +362,8 @@ def test_large_candidate_pool_topk(bbc, oracle_lib):
                                        ("ties", 30000, 20000), ("inner_product", 30000, 20000),
                                        ("ties", 12000, 5000), ("ties", 12000, 11500), ("ties", 12000, 1),
                                        ("inner_product", 12000, 3000)])
-def test_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case, kc, k):
+@pytest.mark.parametrize("fused", [1, 0])
+def test_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case, kc, k, fused):
     """Top-k on candidates with thousands of equal distances and on inner
     products whose distances span the sign boundary.  k = 25,000 takes the
     global-scratch form (its kept keys exceed shared memory; one block of ties
@@ -370,7 +371,8 @@ def test_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case, kc, k):
     candidates the shared-memory form with more candidates than it keeps;
     K_c = 12,000 the shared-memory form, where a block of ties holds the k-th
     place (k = 5,000: selected inside the bin) or lies below it (k = 11,500:
-    the bin is sorted in place)."""
+    the bin is sorted in place).  fused = 1: re-rank and top-k in one kernel
+    where the K_c = 12,000 candidates fit in its shared memory."""
     from synth import build_ivf_pq
     from synth.data import sift_shaped, embedding_shaped
     if case == "ties":
@@ -384,6 +386,7 @@ def test_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case, kc, k):
         idx = build_ivf_pq(x, 16, 16, 8, "ip", kmeans_iters=3, pq_iters=3, pq_sample=5000)
     h = bbc.bbc_index_create(idx, 0)
     try:
+        bbc.bbc_set_param(h, "rerank_fused", fused)
         nq = len(q)
         cand = np.tile(np.arange(kc, dtype=np.uint32), (nq, 1))
         cnt = np.full(nq, kc, dtype=np.int64)
@@ -402,7 +405,8 @@ def test_topk_heavy_bins_and_sign_span(bbc, oracle_lib, case, kc, k):
 
 @pytest.mark.parametrize("d", [128, 64])
 @pytest.mark.parametrize("frac", [0.0, 0.37])
-def test_rerank_integer_rows_integer_and_fractional_queries(bbc, oracle_lib, d, frac):
+@pytest.mark.parametrize("fused", [1, 0])
+def test_rerank_integer_rows_integer_and_fractional_queries(bbc, oracle_lib, d, frac, fused):
     """Re-rank + top-k over the exact u8 copy: integer queries take the integer
     dot-product path (bit-exact), fractional ones the FP32 path (1e-5 of FP64);
     d = 128 runs the fixed-shape kernel, d = 64 the general one."""
@@ -413,6 +417,7 @@ def test_rerank_integer_rows_integer_and_fractional_queries(bbc, oracle_lib, d, 
     h = bbc.bbc_index_create(idx, 0)
     try:
         assert bbc.bbc_index_info(h)["vectors_u8_exact"] == 1
+        bbc.bbc_set_param(h, "rerank_fused", fused)
         q = (q + np.float32(frac)).astype(np.float32)
         nq, kc, k = len(q), 12000, 3000
         cand = np.tile(np.arange(kc, dtype=np.uint32), (nq, 1))
@@ -428,6 +433,56 @@ def test_rerank_integer_rows_integer_and_fractional_queries(bbc, oracle_lib, d, 
             _check_topk(oracle_lib, idx, q[i], gi[i], gd[i], oi, od, frac == 0.0)
     finally:
         bbc.bbc_index_free(h)
+
+
+@pytest.mark.parametrize("kind,k,nprobe,ratio,rows", [("tiny", 100, 12, 2.0, "auto"), ("sift", 500, 16, 1.5, "auto"),
+                                                      ("sift", 4000, 64, 1.0, "auto"), ("sift", 500, 16, 1.5, "early"),
+                                                      ("sift", 500, 16, 1.5, "f32"), ("embed", 200, 10, 1.5, "auto"),
+                                                      ("ragged", 50, 40, 1.0, "auto"), ("wide", 300, 6, 2.0, "auto"),
+                                                      ("tiny", 1, 3, 1.0, "auto")])
+def test_rerank_fused_equals_two_kernels(bbc, oracle_lib, kind, k, nprobe, ratio, rows):
+    """The one-kernel re-rank + top-k (each query's distances kept in shared
+    memory) returns, bit for bit, what the re-rank kernel followed by the top-k
+    kernel returns: integer rows (u8 path), FP32 rows of 512 bytes and of other
+    widths (rows = "f32": the FP32 vectors of integer data), and the early
+    re-rank's variant (rows = "early").  The stage profile shows which path
+    ran (the fused kernel is timed as the re-rank stage, the top-k stage stays
+    empty)."""
+    h, idx, q = dev_index(bbc, kind)
+    bbc.bbc_set_param(h, "kc_ratio", ratio)
+    nq = len(q)
+    outs = []
+    try:
+        if rows == "early":
+            bbc.bbc_set_param(h, "split", 1)
+            bbc.bbc_set_param(h, "early_rerank", 1)
+        if rows == "f32":
+            bbc.bbc_set_param(h, "rerank", 0)
+        bbc.bbc_set_param(h, "profile", 1)
+        for fused in (0, 1):
+            bbc.bbc_set_param(h, "rerank_fused", fused)
+            bbc.bbc_profile_read(h, reset=True)
+            gi = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+            gd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+            bbc.bbc_search(h, cuda(q), nq, k, nprobe, gi, gd)
+            sync_ok(bbc, h)
+            stages, _ = bbc.bbc_profile_read(h, reset=True)
+            outs.append((gi.cpu().numpy(), gd.cpu().numpy(), stages))
+    finally:
+        bbc.bbc_set_param(h, "profile", 0)
+        bbc.bbc_set_param(h, "rerank_fused", 1)
+        if rows == "early":
+            bbc.bbc_set_param(h, "early_rerank", 0)
+            bbc.bbc_set_param(h, "split", 0)
+        if rows == "f32":
+            bbc.bbc_set_param(h, "rerank", 1)
+    assert outs[0][2]["topk"] > 0.0 and outs[1][2]["topk"] == 0.0 and outs[1][2]["rerank"] > 0.0
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    kc = max(k, int(np.ceil(ratio * k - 1e-9)))
+    oi, od = oracle_lib.search(idx, q, k, nprobe, kc, "sort")
+    exact = kind in ("sift", "sift4")
+    for i in range(nq):
+        _check_topk(oracle_lib, idx, q[i], outs[1][0][i], outs[1][1][i], oi[i], od[i], exact)
 
 
 @pytest.mark.parametrize("kind", ["tiny", "sift", "ragged"])
