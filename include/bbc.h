@@ -242,7 +242,11 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  215 KB; K_c = 15,000 with k = 10,000 does); otherwise, and
  *                  with 0, two kernels with the distances in the workspace.
  *                  Same results either way; with "profile" the fused kernel's
- *                  time is the re-rank stage's.  Default 1.
+ *                  time is the re-rank stage's.  Default 0: at K_c = 15,000
+ *                  the kernel holds one CTA per SM, which keeps half as many
+ *                  row loads in flight as the two kernels and leaves the
+ *                  memory system idle during the top-k (measured 4.6 ms
+ *                  against 3.1 ms per 10,000 queries on 1M x 128).
  *   "region_cap"   entries of each query's collector region (the buffer the
  *                  scan appends (estimated distance, position) pairs to).
  *                  0 (default) = the total length of the nprobe longest lists,

@@ -140,7 +140,7 @@ struct bbc_index {
     int graphs = 0;           // 1: capture each bbc_search shape into a CUDA graph and replay it
     int lut_levels = 65535;   // top level of the integer lookup tables
     int scan_tc = 0;          // 1: list-grouped scan on the tensor cores (4-bit codes; tables <= 2047)
-    int rerank_fused = 1;     // 1: re-rank and top-k in one kernel where the candidates fit in shared memory
+    int rerank_fused = 0;     // 1: re-rank and top-k in one kernel where the candidates fit in shared memory
     bool capturing = false;
     struct GraphKey {
         const void* q; int64_t nq; int k; int nprobe; void* oi; void* od; cudaStream_t st;

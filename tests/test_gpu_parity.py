@@ -470,7 +470,7 @@ def test_rerank_fused_equals_two_kernels(bbc, oracle_lib, kind, k, nprobe, ratio
             outs.append((gi.cpu().numpy(), gd.cpu().numpy(), stages))
     finally:
         bbc.bbc_set_param(h, "profile", 0)
-        bbc.bbc_set_param(h, "rerank_fused", 1)
+        bbc.bbc_set_param(h, "rerank_fused", 0)
         if rows == "early":
             bbc.bbc_set_param(h, "early_rerank", 0)
             bbc.bbc_set_param(h, "split", 0)
