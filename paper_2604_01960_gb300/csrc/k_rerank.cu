@@ -442,8 +442,8 @@ __device__ void cta_sort_any_u64(unsigned long long* a, int n) {
 
 // Top-k of any number of candidates when k + TKS_BIG keys fit in shared memory
 // (TK_SMEM_KEYS), one CTA per query (two per SM while the keys take half of it).
-// 1. min / max of the distances; histogram over TKS_BINS bins in value space
-//    (bin = floor((dist - min) * TKS_BINS / (max - min)) in FP32, a monotone
+// 1. min / max of the distances; histogram over BINS bins in value space
+//    (bin = floor((dist - min) * BINS / (max - min)) in FP32, a monotone
 //    function of the distance); exclusive scan -> bin starts;
 // 2. the bin b_k holding rank kk - 1 (kk = min(k, candidates)); when it has
 //    more than TKS_BIG keys, the (kk - start)-th smallest key of that bin T
@@ -455,6 +455,9 @@ __device__ void cta_sort_any_u64(unsigned long long* a, int n) {
 // Positions below k go to the output.
 constexpr int TKS_THREADS = 512;
 constexpr int TKS_BINS = 2048;
+// Bins of the standalone kernel while two CTAs per SM still fit: a key is ranked
+// against the other keys of its bin, so finer bins cut that work
+constexpr int TKS_BINS_FINE = 4096;
 constexpr int TKS_BIG = 1024;
 constexpr int TKS_MAXHEAVY = 64;
 constexpr int TKS_U = 8;
@@ -462,11 +465,11 @@ constexpr int TK_SMEM_KEYS = 24576;   // keys of the shared-memory form: k - 1 +
 
 // The body for query qi, its n candidates' distances cd[] and ids cand[] (in
 // global or shared memory), keys[kcap] in shared memory; blockDim.x == THREADS.
-template <int THREADS, int U>
+template <int THREADS, int U, int BINS>
 __device__ __forceinline__ void topk_query(const DevIndex& ix, const RerankArgs& a, int64_t qi, int n,
                                            const float* cd, const uint32_t* cand, unsigned long long* keys,
                                            int kcap) {
-    __shared__ uint32_t bins[TKS_BINS];
+    __shared__ uint32_t bins[BINS];
     __shared__ uint32_t wsum[THREADS / 32];
     __shared__ uint32_t hist[256], sc[2];
     __shared__ uint32_t heavy[TKS_MAXHEAVY];
@@ -479,7 +482,7 @@ __device__ __forceinline__ void topk_query(const DevIndex& ix, const RerankArgs&
     if (n == 0 || kq <= 0) return;
     const uint32_t kk = (uint32_t)(kq < n ? kq : n);
     if (tid == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_nheavy = 0u; }
-    for (int i = tid; i < TKS_BINS; i += blockDim.x) bins[i] = 0;
+    for (int i = tid; i < BINS; i += blockDim.x) bins[i] = 0;
     __syncthreads();
     // passes over the candidates load U values per thread before using them
     const int step = U * THREADS;
@@ -503,9 +506,9 @@ __device__ __forceinline__ void topk_query(const DevIndex& ix, const RerankArgs&
     __syncthreads();
     const float vmin = key_f32(s_min);
     const float range = __fsub_rn(key_f32(s_max), vmin);
-    const float scale = range > 0.f ? fminf((float)TKS_BINS / range, 3.0e38f) : 0.f;
+    const float scale = range > 0.f ? fminf((float)BINS / range, 3.0e38f) : 0.f;
     auto vbin = [&](float v) -> uint32_t {
-        const float t = fminf(__fmul_rn(__fsub_rn(v, vmin), scale), (float)(TKS_BINS - 1));
+        const float t = fminf(__fmul_rn(__fsub_rn(v, vmin), scale), (float)(BINS - 1));
         return t > 0.f ? (uint32_t)t : 0u;
     };
     for (int i0 = tid; i0 < n; i0 += step) {
@@ -517,7 +520,7 @@ __device__ __forceinline__ void topk_query(const DevIndex& ix, const RerankArgs&
             if (i0 + u * THREADS < n) atomicAdd(&bins[vbin(v[u])], 1u);
     }
     __syncthreads();
-    constexpr int PER = TKS_BINS / THREADS;
+    constexpr int PER = BINS / THREADS;
     uint32_t loc[PER];
     tk_scan<PER, THREADS>(bins, wsum, loc);
 #pragma unroll
@@ -529,7 +532,7 @@ __device__ __forceinline__ void topk_query(const DevIndex& ix, const RerankArgs&
     __syncthreads();
     const uint32_t bk = s_bk;
     const uint32_t stk = bins[bk];
-    const uint32_t nbk = (bk + 1 < (uint32_t)TKS_BINS ? bins[bk + 1] : (uint32_t)n) - stk;
+    const uint32_t nbk = (bk + 1 < (uint32_t)BINS ? bins[bk + 1] : (uint32_t)n) - stk;
     unsigned long long T = ~0ull;
     if (nbk > (uint32_t)TKS_BIG) {
         T = cta_select_u64(n, kk - 1 - stk, [&](int64_t i) {
@@ -601,11 +604,12 @@ __device__ __forceinline__ void topk_query(const DevIndex& ix, const RerankArgs&
     }
 }
 
+template <int BINS>
 __global__ void __launch_bounds__(TKS_THREADS, 2) topk_kernel(DevIndex ix, RerankArgs a, int kcap) {
     extern __shared__ unsigned long long keys[];   // [kcap]
     const int64_t qi = blockIdx.x;
     const int n = (int)min(a.cand_count[qi], a.qp.KC(qi));
-    topk_query<TKS_THREADS, TKS_U>(ix, a, qi, n, a.cdist + a.qp.coff(qi), a.cand + a.qp.coff(qi), keys, kcap);
+    topk_query<TKS_THREADS, TKS_U, BINS>(ix, a, qi, n, a.cdist + a.qp.coff(qi), a.cand + a.qp.coff(qi), keys, kcap);
 }
 
 // S8 + S9 in one kernel: a CTA per query computes the exact distances of its
@@ -648,7 +652,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
     __syncthreads();
     rr_span<T, FAST, EARLY>(ix, a, qi, vec, sid, 0, n, dist, rq, q8, sizeof(T) == 1 && s_int, s_qn2);
     __syncthreads();
-    topk_query<RT_THREADS, RT_U>(ix, a, qi, n, dist, sid, keys, kcap);
+    topk_query<RT_THREADS, RT_U, TKS_BINS>(ix, a, qi, n, dist, sid, keys, kcap);
 }
 
 // Same output when k - 1 + TKS_BIG keys do not fit in shared memory.  The
@@ -750,9 +754,17 @@ cudaError_t launch_topk(const DevIndex& ix, int64_t nq, const RerankArgs& a, cud
     // keys held per query: all candidates, or at most k - 1 + TKS_BIG of them
     const long long kcap = std::min<long long>(a.kc, (long long)a.k + TKS_BIG);
     const size_t smem = (size_t)std::max<long long>(kcap, 1) * 8;
-    cudaError_t e = smem_attr_once((const void*)topk_kernel, TK_SMEM_KEYS * 8);
+    // the finer bins while two CTAs (keys, bins, 2 KB of the rest and the
+    // 1 KB the SM reserves per CTA) fit in 228 KB
+    if (2 * (smem + TKS_BINS_FINE * 4 + 3 * 1024) <= 228 * 1024) {
+        cudaError_t e = smem_attr_once((const void*)topk_kernel<TKS_BINS_FINE>, TK_SMEM_KEYS * 8);
+        if (e != cudaSuccess) return e;
+        topk_kernel<TKS_BINS_FINE><<<(unsigned)nq, TKS_THREADS, smem, st>>>(ix, a, (int)std::max<long long>(kcap, 1));
+        return cudaGetLastError();
+    }
+    cudaError_t e = smem_attr_once((const void*)topk_kernel<TKS_BINS>, TK_SMEM_KEYS * 8);
     if (e != cudaSuccess) return e;
-    topk_kernel<<<(unsigned)nq, TKS_THREADS, smem, st>>>(ix, a, (int)std::max<long long>(kcap, 1));
+    topk_kernel<TKS_BINS><<<(unsigned)nq, TKS_THREADS, smem, st>>>(ix, a, (int)std::max<long long>(kcap, 1));
     return cudaGetLastError();
 }
 
