@@ -243,10 +243,11 @@ int bbc_index_info(const bbc_index* ix, bbc_index_info_t* out);
  *                  with 0, two kernels with the distances in the workspace.
  *                  Same results either way; with "profile" the fused kernel's
  *                  time is the re-rank stage's.  Default 0: at K_c = 15,000
- *                  the kernel holds one CTA per SM, which keeps half as many
- *                  row loads in flight as the two kernels and leaves the
- *                  memory system idle during the top-k (measured 4.6 ms
- *                  against 3.1 ms per 10,000 queries on 1M x 128).
+ *                  the kernel holds one CTA per SM, so each query's top-k
+ *                  phase (bound by instructions and barriers) runs with no
+ *                  other query beside it and no row loads in flight
+ *                  (measured 4.6 ms against 3.1 ms for the two kernels per
+ *                  10,000 queries on 1M x 128).
  *   "region_cap"   entries of each query's collector region (the buffer the
  *                  scan appends (estimated distance, position) pairs to).
  *                  0 (default) = the total length of the nprobe longest lists,
