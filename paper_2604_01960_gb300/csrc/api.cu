@@ -295,7 +295,11 @@ bool early_active(const bbc_index* ix) {
 // re-rank); the tables then have top level lut_levels <= 2047.
 bool tc_active(const bbc_index* ix) { return ix->scan_tc && ix->collector == 0 && !early_active(ix); }
 
-constexpr int64_t kTopkSmemMax = 16384;     // K_c handled by the shared-memory top-k
+// K_c (or k) above which the workspace holds 64-bit keys for the global-scratch
+// top-k.  That form runs only when k - 1 + 1,024 kept keys exceed shared memory
+// (k above 23,552); since K_c >= k the bound is conservative: it may reserve
+// keys the shared-memory top-k then does not use.
+constexpr int64_t kTopkSmemMax = 16384;
 constexpr int64_t kMaxChunkQueries = 65535;  // queries per launch (some grids index queries in y)
 
 size_t layout(const bbc_index* ix, const ChunkShape& c, Plan& p) {
