@@ -1806,7 +1806,7 @@ int bbc_autotune(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int
     for (const auto& sc : scheds) {
         ix->split = sc.first;
         ix->pair = sc.second;
-        double t;
+        double t = 1e300;
         if ((rc = time_it(&t))) break;
         if (t < best_ms) { best_ms = t; best_split = sc.first; best_pair = sc.second; }
     }
@@ -1815,7 +1815,7 @@ int bbc_autotune(bbc_index* ix, const float* queries, int64_t nq, int32_t k, int
         ix->pair = best_pair;
         for (int m : {32, 64, 128, 256}) {
             ix->buckets = m;
-            double t;
+            double t = 1e300;
             if ((rc = time_it(&t))) break;
             if (t < best_ms * 0.98 || (m == best_m && t < best_ms)) { best_ms = t; best_m = m; }
         }
